@@ -1,0 +1,203 @@
+/*
+ * gts.h -- C ABI of a GB300 (sm_103a) library for exact metric range and
+ * k-nearest-neighbour search over a GTS index: a pivot-based tree whose nodes
+ * are flattened into a node list and a table list (Zhu et al., "GTS:
+ * GPU-based Tree Index for Fast Similarity Search", PACMMOD 2024,
+ * arXiv 2404.00966).
+ *
+ * Conventions for every entry point
+ *  - No C++ exception crosses this boundary; every call returns a gts_status.
+ *    On any status other than GTS_OK, gts_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread), outputs are
+ *    left untouched and an index is left as it was before the call.
+ *  - All device work runs on the CUDA stream given in the options (NULL = the
+ *    legacy default stream) of the device that is current when the index is
+ *    built.  Calls return after their results are complete (they synchronise
+ *    that stream).
+ *  - Input buffers stay owned by the caller and are only read.  A gts_objects
+ *    with on_device = 1 holds device pointers of the current device; otherwise
+ *    host pointers (pageable or pinned).  Per-query arrays (radii, k, seq)
+ *    live on the same side as the queries.
+ *  - Object ids are int64.  The objects of gts_build get ids 0 .. n-1 in input
+ *    order; gts_insert hands out the next ids in order.  Total ids < 2^31.
+ *  - A library built without a usable CUDA device fails every call with
+ *    GTS_ECUDA.  There is no CPU fallback.
+ *  - An index may be used by one thread at a time.
+ */
+#ifndef GTS_H
+#define GTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gts_index gts_index; /* opaque; owns all of its device memory */
+
+typedef enum {
+    GTS_OK = 0,
+    GTS_EINVAL = 1,    /* malformed argument (NaN / negative radius, k <= 0, metric/object mismatch ...) */
+    GTS_ENOMEM = 2,    /* a device or host allocation failed */
+    GTS_ECUDA = 3,     /* a CUDA runtime error (message in gts_last_error) */
+    GTS_ETIMEOUT = 4,  /* a bounded device wait ran out */
+    GTS_ENOTFOUND = 5, /* gts_delete: one or more ids are unknown or already deleted (the others were applied) */
+    GTS_EOVERFLOW = 6  /* a single query needs more memory than the configured budget allows */
+} gts_status;
+
+/* Distance metrics (Section 3, metric-space axioms; Table 2 of the paper).
+ *  GTS_EDIT: unit-cost Levenshtein distance between byte strings.
+ *  GTS_L1:   sum_i |q_i - x_i| over float32 vectors.
+ *  GTS_L2:   sqrt(sum_i (q_i - x_i)^2) over float32 vectors. */
+typedef enum { GTS_EDIT = 0, GTS_L1 = 1, GTS_L2 = 2 } gts_metric;
+
+/* Verification precision for L2.  Both give the same result sets:
+ *  GTS_PREC_FP32: FP32 CUDA-core distances, FP64 recheck of candidates whose
+ *                 FP32 distance lies within a proven error bound of the radius
+ *                 or of the running k-th distance.
+ *  GTS_PREC_BF16: BF16 tensor-core distance tiles with FP32 accumulation and the
+ *                 same FP64 recheck against a (wider) proven BF16 bound.
+ * L1 and edit distance ignore this field (FP32 + FP64 recheck / exact int). */
+typedef enum { GTS_PREC_FP32 = 0, GTS_PREC_BF16 = 1 } gts_precision;
+
+/* A set of objects: vectors (dim > 0) or byte strings (dim == 0).
+ *  vectors: data = float32[n * dim], row-major.
+ *  strings: data = uint8 bytes, offsets = int64[n + 1], offsets[0] = 0,
+ *           string i = data[offsets[i] .. offsets[i+1]); lengths <= 1024. */
+typedef struct {
+    int64_t n;
+    int32_t dim;
+    int32_t on_device;
+    const void *data;
+    const int64_t *offsets;
+} gts_objects;
+
+typedef struct {
+    void *stream;          /* cudaStream_t */
+    int64_t root_pivot;    /* index of the first (root) pivot in [0, n); -1 = drawn from seed (SplitMix64) */
+    uint64_t seed;         /* seeds the root pivot of rebuilds and of root_pivot = -1 */
+    int64_t cache_limit;   /* stream-update cache list capacity in objects; a larger cache triggers a
+                              rebuild (Section 4.4); 0 = default 4096 */
+} gts_build_opts;
+
+typedef struct {
+    void *stream;            /* cudaStream_t */
+    int32_t precision;       /* gts_precision (L2 only) */
+    int32_t result_on_device;/* 1: result arrays are device memory owned by the result */
+    int64_t memory_budget;   /* bytes for intermediate frontier and candidate tables: size_GPU of the
+                                two-stage scheduler (Section 5.1, Algorithm 4); 0 = default 8 GiB */
+    const int64_t *seq;      /* optional per-query sequence number (same side as the queries): query i
+                                sees the objects inserted before seq[i] and not deleted before seq[i].
+                                NULL = the current state.  Must not precede the last rebuild. */
+    int64_t *stats;          /* optional host int64[GTS_STATS_LEN] of counters, filled on return */
+} gts_query_opts;
+
+/* Counters written to gts_query_opts.stats. */
+enum {
+    GTS_STAT_PIVOT_DIST = 0,   /* query-to-pivot distances computed */
+    GTS_STAT_FRONTIER = 1,     /* (query, node) entries visited, all levels */
+    GTS_STAT_SCANNED_ROWS = 2, /* table-list rows tested in the leaf scan */
+    GTS_STAT_CANDIDATES = 3,   /* rows that passed the scan (verified with the metric) */
+    GTS_STAT_RECHECKS = 4,     /* FP64 boundary rechecks */
+    GTS_STAT_RESULTS = 5,      /* returned (query, object) pairs */
+    GTS_STAT_GROUPS = 6,       /* query groups run by the two-stage scheduler */
+    GTS_STAT_CACHE_ROWS = 7,   /* cache-list objects compared by brute force */
+    GTS_STATS_LEN = 8
+};
+
+/* Per-query answers in CSR form: the answers of query i are
+ * ids/dist[offsets[i] .. offsets[i+1]).  Range answers are in ascending id
+ * order; kNN answers in ascending (distance, id) order.  dist is float32; for
+ * GTS_EDIT it holds the exact integer distance.  Allocated by the library
+ * (host memory, or device memory when result_on_device = 1); release with
+ * gts_result_free. */
+typedef struct {
+    int64_t nq;
+    int64_t *offsets;
+    int64_t *ids;
+    float *dist;
+    int32_t on_device;
+    void *priv_;
+} gts_result;
+
+/* Build an index over `objects` (Section 4.3, Algorithms 1-3).
+ *  n_pivots: number of pivot levels h; 0 = ceil(log_fanout(n + 1)) - 1 (Algorithm 1), at least 1.
+ *  fanout:   node capacity N_c, 2 .. 64.
+ *  The metric must match the objects (GTS_EDIT <-> strings).  n may be 0. */
+gts_status gts_build(const gts_objects *objects, gts_metric metric, int n_pivots, int fanout,
+                     const gts_build_opts *opts, gts_index **out);
+
+/* Batched metric range query MRQ(q, r) = { o : d(q, o) <= r } (Section 3,
+ * Definition 1; Section 5.1, Algorithm 4).  radii: float32[nq], >= 0 and not
+ * NaN; edit-distance radii are read as floor(r). */
+gts_status gts_range(gts_index *index, const gts_objects *queries, const float *radii,
+                     const gts_query_opts *opts, gts_result *out);
+
+/* Batched metric kNN query (Section 3, Definition 2; Section 5.2, Algorithm
+ * 5).  k: int32[nq], each >= 1.  A query gets min(k, visible objects)
+ * answers: the first ones in ascending (distance, id) order. */
+gts_status gts_knn(gts_index *index, const gts_objects *queries, const int32_t *k,
+                   const gts_query_opts *opts, gts_result *out);
+
+/* Stream insert (Section 4.4): the objects go to the cache list and get ids
+ * next_id, next_id + 1, ... written to ids_out (host int64[m], may be NULL).
+ * When the cache list would exceed cache_limit the index is rebuilt first. */
+gts_status gts_insert(gts_index *index, const gts_objects *objects, int64_t *ids_out);
+
+/* Stream delete (Section 4.4): marks the objects with the given ids (host
+ * int64[m]) deleted.  Unknown or already deleted ids are skipped and counted
+ * in *n_missing (may be NULL); GTS_ENOTFOUND is returned if any was skipped. */
+gts_status gts_delete(gts_index *index, const int64_t *ids, int64_t m, int64_t *n_missing);
+
+/* Batch update (Section 4.4): insert `ins` (may be NULL), delete `del` (host
+ * int64[m_del]) and rebuild the whole index at once.  New ids go to ids_out. */
+gts_status gts_batch_update(gts_index *index, const gts_objects *ins, const int64_t *del, int64_t m_del,
+                            int64_t *ids_out);
+
+/* Rebuild the index from its visible objects (index and cache list). */
+gts_status gts_rebuild(gts_index *index);
+
+typedef struct {
+    int64_t n_tree;      /* objects in the tree (including deleted ones not yet dropped) */
+    int64_t n_cache;     /* objects in the cache list */
+    int64_t n_live;      /* visible objects now */
+    int64_t next_id;
+    int64_t seq;         /* sequence number of the next update operation */
+    int64_t rebuild_seq; /* sequence number of the last (re)build */
+    int32_t h;           /* pivot levels */
+    int32_t fanout;
+    int32_t metric;
+    int32_t dim;
+    int64_t device_bytes;/* device memory held by the index */
+} gts_index_info;
+
+gts_status gts_info(const gts_index *index, gts_index_info *out);
+
+/* Read back the tree (for checks).  level 0 .. h; arrays of fanout^level
+ * entries, host memory, any may be NULL.  pivot (levels 0 .. h-1 only) is the
+ * pivot's object id or -1 for an empty node; lo/hi are the node's distance
+ * interval to its parent's pivot (level >= 1). */
+gts_status gts_tree_level(const gts_index *index, int level, int64_t *pos, int64_t *size, float *lo,
+                          float *hi, int64_t *pivot);
+
+/* Read back the table list: ids = int64[n_tree] (row -> object id, leaf
+ * order), table = float32[h * n_tree] (column l = distance of each row to its
+ * level-l ancestor's pivot).  Host memory; either may be NULL. */
+gts_status gts_table(const gts_index *index, int64_t *ids, float *table);
+
+/* Copy a result's arrays into caller buffers (host or device pointers of the
+ * index's device; either side of a result works): offsets = int64[nq + 1],
+ * ids = int64[total], dist = float32[total], total = offsets[nq].  Any output
+ * may be NULL.  Synchronous. */
+gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *ids, float *dist);
+
+void gts_result_free(gts_result *result);
+void gts_free(gts_index *index);
+const char *gts_last_error(void);
+const char *gts_status_name(gts_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GTS_H */

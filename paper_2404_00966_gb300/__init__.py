@@ -1,0 +1,321 @@
+"""Python binding of the GTS C ABI (include/gts.h): exact batched metric range
+and kNN search on a GB300 over a GTS index (arXiv 2404.00966).
+
+Argument marshalling only: every step of the search runs in the CUDA library
+``_build/libgts.so``.  There is no CPU fallback -- if the library is missing
+or no device is usable, every call raises :class:`GTSError`.
+
+Inputs may be numpy arrays (host) or torch CUDA tensors (device):
+  * vectors: float32 ``[n, dim]``;
+  * strings: ``synth.Strings`` (host) or a pair ``(bytes uint8, offsets int64)``
+    of numpy arrays or of CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+__all__ = ["GTSError", "Index", "lib", "EDIT", "L1", "L2", "PREC_FP32", "PREC_BF16", "STAT_NAMES"]
+
+EDIT, L1, L2 = 0, 1, 2
+PREC_FP32, PREC_BF16 = 0, 1
+METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
+STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgts.so")
+_lib = None
+
+
+class GTSError(RuntimeError):
+    def __init__(self, status: int, name: str, msg: str):
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+        self.name = name
+
+
+class _Objects(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int32), ("on_device", ctypes.c_int32),
+                ("data", ctypes.c_void_p), ("offsets", ctypes.c_void_p)]
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("root_pivot", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("cache_limit", ctypes.c_int64)]
+
+
+class _QueryOpts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32), ("result_on_device", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("seq", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("ids", ctypes.c_void_p),
+                ("dist", ctypes.c_void_p), ("on_device", ctypes.c_int32), ("priv_", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_tree", ctypes.c_int64), ("n_cache", ctypes.c_int64), ("n_live", ctypes.c_int64),
+                ("next_id", ctypes.c_int64), ("seq", ctypes.c_int64), ("rebuild_seq", ctypes.c_int64),
+                ("h", ctypes.c_int32), ("fanout", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
+           "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
+           "gts_last_error", "gts_status_name"]
+
+
+def lib(path: Optional[str] = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise GTSError(3, "GTS_ECUDA", f"CUDA library not built ({p}); run __graft_entry__.build()")
+    L = ctypes.CDLL(p)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.gts_build.argtypes = [ctypes.POINTER(_Objects), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.POINTER(_BuildOpts), ctypes.POINTER(P)]
+    L.gts_range.argtypes = [P, ctypes.POINTER(_Objects), P, ctypes.POINTER(_QueryOpts), ctypes.POINTER(_Result)]
+    L.gts_knn.argtypes = [P, ctypes.POINTER(_Objects), P, ctypes.POINTER(_QueryOpts), ctypes.POINTER(_Result)]
+    L.gts_insert.argtypes = [P, ctypes.POINTER(_Objects), P]
+    L.gts_delete.argtypes = [P, P, I64, P]
+    L.gts_batch_update.argtypes = [P, ctypes.POINTER(_Objects), P, I64, P]
+    L.gts_rebuild.argtypes = [P]
+    L.gts_info.argtypes = [P, ctypes.POINTER(_Info)]
+    L.gts_tree_level.argtypes = [P, ctypes.c_int, P, P, P, P, P]
+    L.gts_table.argtypes = [P, P, P]
+    L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]
+    L.gts_result_copy.restype = ctypes.c_int
+    L.gts_result_free.argtypes = [ctypes.POINTER(_Result)]
+    L.gts_result_free.restype = None
+    L.gts_free.argtypes = [P]
+    L.gts_free.restype = None
+    L.gts_last_error.restype = ctypes.c_char_p
+    L.gts_status_name.restype = ctypes.c_char_p
+    L.gts_status_name.argtypes = [ctypes.c_int]
+    for f in ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
+              "gts_info", "gts_tree_level", "gts_table"]:
+        getattr(L, f).restype = ctypes.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        L = lib()
+        raise GTSError(status, L.gts_status_name(status).decode(), L.gts_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_of(*xs):
+    for x in xs:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return None
+
+
+class _Marshal:
+    """Keeps the arrays behind a gts_objects alive for the call."""
+
+    def __init__(self, objs):
+        self.keep = []
+        o = _Objects()
+        if isinstance(objs, tuple) or hasattr(objs, "offsets"):
+            data, offs = (objs.data, objs.offsets) if hasattr(objs, "offsets") else objs
+            if _is_torch(data):
+                o.on_device = 1 if data.is_cuda else 0
+                data = data.contiguous()
+                offs = offs.contiguous()
+            else:
+                data = np.ascontiguousarray(data, np.uint8)
+                offs = np.ascontiguousarray(offs, np.int64)
+                if data.size == 0:
+                    data = np.zeros(1, np.uint8)
+            o.n = int(offs.shape[0]) - 1
+            o.dim = 0
+            o.data = _ptr(data).value
+            o.offsets = _ptr(offs).value
+            self.keep += [data, offs]
+            self.first = data
+        else:
+            X = objs
+            if _is_torch(X):
+                o.on_device = 1 if X.is_cuda else 0
+                X = X.contiguous()
+            else:
+                X = np.ascontiguousarray(X, np.float32)
+            if X.ndim != 2:
+                raise ValueError("vectors must be 2-D [n, dim]")
+            o.n = int(X.shape[0])
+            o.dim = int(X.shape[1])
+            count = X.numel() if _is_torch(X) else X.size
+            o.data = _ptr(X).value if count else None
+            self.keep.append(X)
+            self.first = X
+        self.obj = o
+
+
+class Result:
+    """CSR answers: ids/dist[offsets[i]:offsets[i+1]] belong to query i."""
+
+    def __init__(self, offsets, ids, dist, stats=None, device_result=None):
+        self.offsets, self.ids, self.dist, self.stats = offsets, ids, dist, stats
+        self._dev = device_result
+
+    def query(self, i):
+        a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+        return self.ids[a:b], self.dist[a:b]
+
+    def copy_to(self, offsets, ids, dist):
+        """Copy a device-resident result into caller arrays (numpy or torch,
+        host or device)."""
+        _check(lib().gts_result_copy(ctypes.byref(self._dev), _ptr(offsets), _ptr(ids), _ptr(dist)))
+
+    def free(self):
+        if self._dev is not None:
+            lib().gts_result_free(ctypes.byref(self._dev))
+            self._dev = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Index:
+    """A GTS index held on the current CUDA device (owned by the library)."""
+
+    def __init__(self, handle, metric: str):
+        self._h = handle
+        self.metric = metric
+
+    @classmethod
+    def build(cls, objects, metric: str, n_pivots: int = 0, fanout: int = 20, root_pivot: int = -1,
+              seed: int = 0, cache_limit: int = 0, stream=None) -> "Index":
+        m = _Marshal(objects)
+        opts = _BuildOpts(stream=stream if stream is not None else _stream_of(m.first), root_pivot=int(root_pivot),
+                          seed=int(seed), cache_limit=int(cache_limit))
+        h = ctypes.c_void_p()
+        _check(lib().gts_build(ctypes.byref(m.obj), METRIC_IDS[metric], int(n_pivots), int(fanout),
+                               ctypes.byref(opts), ctypes.byref(h)))
+        return cls(h, metric)
+
+    def _query(self, fn, queries, per_query, precision, result_on_device, memory_budget, seq, stream):
+        m = _Marshal(queries)
+        dev = m.obj.on_device == 1
+        stats = np.zeros(8, np.int64)
+        opts = _QueryOpts(stream=stream if stream is not None else _stream_of(m.first),
+                          precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
+                          result_on_device=1 if result_on_device else 0, memory_budget=int(memory_budget),
+                          seq=_ptr(seq).value if seq is not None else None, stats=_ptr(stats).value)
+        res = _Result()
+        _check(fn(self._h, ctypes.byref(m.obj), _ptr(per_query), ctypes.byref(opts), ctypes.byref(res)))
+        st = dict(zip(STAT_NAMES, stats.tolist()))
+        nq = int(res.nq)
+        if res.on_device:
+            return Result(res.offsets, res.ids, res.dist, st, device_result=res)
+        offsets = np.ctypeslib.as_array(ctypes.cast(res.offsets, ctypes.POINTER(ctypes.c_int64)), (nq + 1,)).copy()
+        tot = int(offsets[-1])
+        ids = np.ctypeslib.as_array(ctypes.cast(res.ids, ctypes.POINTER(ctypes.c_int64)), (max(tot, 1),))[:tot].copy()
+        dist = np.ctypeslib.as_array(ctypes.cast(res.dist, ctypes.POINTER(ctypes.c_float)), (max(tot, 1),))[:tot].copy()
+        lib().gts_result_free(ctypes.byref(res))
+        _ = dev
+        return Result(offsets, ids, dist, st)
+
+    def range(self, queries, radii, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
+              stream=None) -> Result:
+        if _is_torch(radii):
+            r = radii.contiguous()
+        else:
+            r = np.ascontiguousarray(radii, np.float32)
+        return self._query(lib().gts_range, queries, r, precision, result_on_device, memory_budget, seq, stream)
+
+    def knn(self, queries, k, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
+            stream=None) -> Result:
+        if _is_torch(k):
+            kk = k.contiguous()
+        else:
+            n = queries.shape[0] if hasattr(queries, "shape") else (
+                queries.n if hasattr(queries, "n") else int(queries[1].shape[0]) - 1)
+            kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
+        return self._query(lib().gts_knn, queries, kk, precision, result_on_device, memory_budget, seq, stream)
+
+    def insert(self, objects) -> np.ndarray:
+        m = _Marshal(objects)
+        ids = np.zeros(max(1, m.obj.n), np.int64)
+        _check(lib().gts_insert(self._h, ctypes.byref(m.obj), _ptr(ids)))
+        return ids[:m.obj.n]
+
+    def delete(self, ids) -> int:
+        ids = np.ascontiguousarray(ids, np.int64)
+        missing = np.zeros(1, np.int64)
+        st = lib().gts_delete(self._h, _ptr(ids) if ids.size else None, int(ids.size), _ptr(missing))
+        if st not in (0, 5):
+            _check(st)
+        return int(missing[0])
+
+    def batch_update(self, objects=None, delete_ids=None) -> np.ndarray:
+        m = _Marshal(objects) if objects is not None else None
+        d = np.ascontiguousarray(delete_ids if delete_ids is not None else np.zeros(0), np.int64)
+        ids = np.zeros(max(1, m.obj.n if m else 0), np.int64)
+        st = lib().gts_batch_update(self._h, ctypes.byref(m.obj) if m else None, _ptr(d) if d.size else None,
+                                    int(d.size), _ptr(ids))
+        if st not in (0, 5):
+            _check(st)
+        return ids[:(m.obj.n if m else 0)]
+
+    def rebuild(self):
+        _check(lib().gts_rebuild(self._h))
+
+    def info(self) -> dict:
+        i = _Info()
+        _check(lib().gts_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def tree_level(self, level: int) -> dict:
+        F = self.info()["fanout"]
+        cnt = F ** level
+        out = dict(pos=np.zeros(cnt, np.int64), size=np.zeros(cnt, np.int64), lo=np.zeros(cnt, np.float32),
+                   hi=np.zeros(cnt, np.float32), pivot=np.zeros(cnt, np.int64))
+        _check(lib().gts_tree_level(self._h, int(level), _ptr(out["pos"]), _ptr(out["size"]), _ptr(out["lo"]),
+                                    _ptr(out["hi"]), _ptr(out["pivot"])))
+        return out
+
+    def table(self):
+        inf = self.info()
+        n, h = inf["n_tree"], inf["h"]
+        ids = np.zeros(max(n, 1), np.int64)
+        tab = np.zeros(max(h * n, 1), np.float32)
+        _check(lib().gts_table(self._h, _ptr(ids), _ptr(tab)))
+        return ids[:n], tab[:h * n].reshape(h, n)
+
+    def close(self):
+        if self._h:
+            lib().gts_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

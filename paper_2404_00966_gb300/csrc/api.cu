@@ -1,0 +1,721 @@
+// The extern "C" entry points of include/gts.h: argument checks, host/device
+// marshalling, stream updates with sequence numbers (Section 4.4), rebuilds
+// and result ownership.  No C++ exception leaves this file.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "gts_impl.cuh"
+
+namespace gts {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+constexpr int kT = 256;
+inline unsigned nb(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+    return (unsigned)b;
+}
+
+template <class F>
+gts_status guarded(F &&f) {
+    try {
+        f();
+        return GTS_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return GTS_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return GTS_ECUDA;
+    } catch (...) {
+        set_last_error("unknown internal error");
+        return GTS_ECUDA;
+    }
+}
+
+void ensure_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        throw Error(GTS_ECUDA, std::string("no usable CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 devices"));
+    static bool pool_set[64] = {false};
+    int dev = 0;
+    GTS_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !pool_set[dev]) {
+        // keep freed stream-ordered memory cached in the pool between calls
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        pool_set[dev] = true;
+    }
+}
+
+__global__ void k_nonfinite(const float *x, int64_t n, int *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) *flag = 1;
+}
+
+// Device copy of a caller's object set (or a view when it is already on the device).
+struct DevObjects {
+    Objects v;
+    DBuf<float> X;
+    DBuf<uint8_t> S;
+    DBuf<int64_t> Soff;
+    std::vector<int64_t> h_off;   // host offsets (strings)
+};
+
+void load_objects(const gts_objects *o, int want_dim_or_neg, DevObjects &out, cudaStream_t st, const char *what) {
+    GTS_REQUIRE(o != nullptr, GTS_EINVAL, std::string(what) + " is NULL");
+    GTS_REQUIRE(o->n >= 0, GTS_EINVAL, std::string(what) + ": negative n");
+    GTS_REQUIRE(o->n < ((int64_t)1 << 31), GTS_EINVAL, std::string(what) + ": n >= 2^31");
+    GTS_REQUIRE(o->dim >= 0, GTS_EINVAL, std::string(what) + ": negative dim");
+    if (want_dim_or_neg >= 0)
+        GTS_REQUIRE(o->dim == want_dim_or_neg, GTS_EINVAL,
+                    std::string(what) + ": dim " + std::to_string(o->dim) + " does not match the index (" +
+                        std::to_string(want_dim_or_neg) + ")");
+    const int64_t n = o->n;
+    out.v.n = n;
+    out.v.dim = o->dim;
+    if (o->dim > 0) {
+        GTS_REQUIRE(n == 0 || o->data != nullptr, GTS_EINVAL, std::string(what) + ": data is NULL");
+        const size_t cnt = (size_t)n * o->dim;
+        if (o->on_device) {
+            out.v.X = (const float *)o->data;
+        } else {
+            out.X.alloc(cnt, st);
+            if (cnt) GTS_CUDA(cudaMemcpyAsync(out.X.get(), o->data, cnt * 4, cudaMemcpyHostToDevice, st));
+            out.v.X = out.X.get();
+        }
+        if (cnt) {
+            DBuf<int> flag(1, st);
+            GTS_CUDA(cudaMemsetAsync(flag.get(), 0, 4, st));
+            k_nonfinite<<<std::min<int64_t>(nb((int64_t)cnt), 4096), kT, 0, st>>>(out.v.X, (int64_t)cnt, flag.get());
+            int h = 0;
+            GTS_CUDA(cudaMemcpyAsync(&h, flag.get(), 4, cudaMemcpyDeviceToHost, st));
+            GTS_CUDA(cudaStreamSynchronize(st));
+            GTS_REQUIRE(h == 0, GTS_EINVAL, std::string(what) + ": NaN or infinite coordinate");
+        }
+    } else {
+        GTS_REQUIRE(o->offsets != nullptr, GTS_EINVAL, std::string(what) + ": strings need offsets");
+        out.h_off.resize(n + 1);
+        if (o->on_device) {
+            GTS_CUDA(cudaMemcpyAsync(out.h_off.data(), o->offsets, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+            GTS_CUDA(cudaStreamSynchronize(st));
+        } else {
+            std::memcpy(out.h_off.data(), o->offsets, (n + 1) * 8);
+        }
+        GTS_REQUIRE(out.h_off[0] == 0, GTS_EINVAL, std::string(what) + ": offsets[0] != 0");
+        int ml = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t L = out.h_off[i + 1] - out.h_off[i];
+            GTS_REQUIRE(L >= 0, GTS_EINVAL, std::string(what) + ": offsets not non-decreasing");
+            GTS_REQUIRE(L <= kMaxStrLen, GTS_EINVAL, std::string(what) + ": string longer than 1024 bytes");
+            ml = std::max<int>(ml, (int)L);
+        }
+        out.v.max_len = ml;
+        const int64_t bytes = out.h_off[n];
+        GTS_REQUIRE(bytes == 0 || o->data != nullptr, GTS_EINVAL, std::string(what) + ": data is NULL");
+        if (o->on_device) {
+            out.v.S = (const uint8_t *)o->data;
+            out.v.Soff = o->offsets;
+        } else {
+            out.S.alloc(bytes > 0 ? bytes : 1, st);
+            out.Soff.alloc(n + 1, st);
+            if (bytes) GTS_CUDA(cudaMemcpyAsync(out.S.get(), o->data, bytes, cudaMemcpyHostToDevice, st));
+            GTS_CUDA(cudaMemcpyAsync(out.Soff.get(), out.h_off.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+            out.v.S = out.S.get();
+            out.v.Soff = out.Soff.get();
+        }
+    }
+}
+
+template <class T>
+void copy_small_to_device(const T *src, int64_t n, bool on_device, DBuf<T> &dst, std::vector<T> &host,
+                          cudaStream_t st) {
+    host.resize(n);
+    dst.alloc(n > 0 ? n : 1, st);
+    if (n == 0) return;
+    if (on_device) {
+        GTS_CUDA(cudaMemcpyAsync(host.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(dst.get(), src, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(host.data(), src, n * sizeof(T));
+        GTS_CUDA(cudaMemcpyAsync(dst.get(), src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+}
+
+void refresh_loc(gts_index *ix) {
+    Tree &t = ix->tree;
+    std::vector<int64_t> ids(t.n);
+    if (t.n) {
+        GTS_CUDA(cudaMemcpyAsync(ids.data(), t.row_id.get(), t.n * 8, cudaMemcpyDeviceToHost, ix->stream));
+        GTS_CUDA(cudaStreamSynchronize(ix->stream));
+    }
+    ix->loc.assign(ix->next_id, -1);
+    for (int64_t r = 0; r < t.n; ++r) ix->loc[ids[r]] = r;
+}
+
+// ---------------------------------------------------------------- cache list
+
+__global__ void k_set_i64(int64_t *a, int64_t start, int64_t count, int64_t v0, int64_t step) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        a[start + i] = v0 + i * step;
+}
+
+template <class T>
+void grow(DBuf<T> &b, size_t used, size_t need, cudaStream_t st) {
+    if (b.n >= need) return;
+    size_t cap = std::max<size_t>(need, b.n * 2);
+    DBuf<T> nbuf(cap, st);
+    if (used) GTS_CUDA(cudaMemcpyAsync(nbuf.get(), b.get(), used * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    b = std::move(nbuf);
+}
+
+void cache_append(gts_index *ix, const DevObjects &o, int64_t *ids_out) {
+    Cache &c = ix->cache;
+    cudaStream_t st = ix->stream;
+    const int64_t m = o.v.n;
+    if (m == 0) return;
+    const int64_t need = c.count + m;
+    grow(c.id, c.count, need, st);
+    grow(c.ins, c.count, need, st);
+    grow(c.del, c.count, need, st);
+    if (ix->dim > 0) {
+        grow(c.X, (size_t)c.count * ix->dim, (size_t)need * ix->dim, st);
+        GTS_CUDA(cudaMemcpyAsync(c.X.get() + (size_t)c.count * ix->dim, o.v.X, (size_t)m * ix->dim * 4,
+                                 cudaMemcpyDeviceToDevice, st));
+    } else {
+        if (c.h_Soff.empty()) c.h_Soff.push_back(0);
+        const int64_t add = o.h_off[m];
+        grow(c.S, c.s_bytes, c.s_bytes + add + 1, st);
+        if (add) GTS_CUDA(cudaMemcpyAsync(c.S.get() + c.s_bytes, o.v.S, add, cudaMemcpyDeviceToDevice, st));
+        for (int64_t i = 1; i <= m; ++i) c.h_Soff.push_back(c.s_bytes + o.h_off[i]);
+        c.s_bytes += add;
+        grow(c.Soff, 0, need + 1, st);
+        GTS_CUDA(cudaMemcpyAsync(c.Soff.get(), c.h_Soff.data(), (need + 1) * 8, cudaMemcpyHostToDevice, st));
+        c.max_len = std::max(c.max_len, o.v.max_len);
+    }
+    k_set_i64<<<nb(m), kT, 0, st>>>(c.id.get(), c.count, m, ix->next_id, 1);
+    k_set_i64<<<nb(m), kT, 0, st>>>(c.ins.get(), c.count, m, ix->seq, 1);
+    k_set_i64<<<nb(m), kT, 0, st>>>(c.del.get(), c.count, m, kNever, 0);
+    check_launch("cache append");
+    ix->loc.resize(ix->next_id + m, -1);
+    for (int64_t i = 0; i < m; ++i) {
+        ix->loc[ix->next_id + i] = -(c.count + i + 2);
+        if (ids_out) ids_out[i] = ix->next_id + i;
+    }
+    ix->next_id += m;
+    ix->seq += m;
+    c.count += m;
+    ix->n_live += m;
+    GTS_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------- rebuild
+
+__global__ void k_visible_rows(const int64_t *row_del, const int64_t *row_id, int64_t n, int *flag, uint64_t *key,
+                               int64_t *val) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const bool vis = row_del[r] == kNever;
+        flag[r] = vis ? 1 : 0;
+        key[r] = vis ? (uint64_t)row_id[r] : ~0ull;
+        val[r] = r;
+    }
+}
+
+__global__ void k_gather_vec_rows(const float *X, const float *cX, int dim, int64_t n_tree, const int64_t *src,
+                                  int64_t m, float *out) {
+    const int64_t total = m * (int64_t)dim;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / dim;
+        const int c = (int)(t - i * dim);
+        const int64_t s = src[i];
+        out[t] = s < n_tree ? X[s * dim + c] : cX[(s - n_tree) * dim + c];
+    }
+}
+
+__global__ void k_gather_str_rows(const uint8_t *S, const int64_t *Soff, const uint8_t *cS, const int64_t *cSoff,
+                                  int64_t n_tree, const int64_t *src, int64_t m, const int64_t *ooff, uint8_t *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < m; i += nw) {
+        const int64_t s = src[i];
+        const uint8_t *p;
+        int64_t len;
+        if (s < n_tree) {
+            p = S + Soff[s];
+            len = Soff[s + 1] - Soff[s];
+        } else {
+            p = cS + cSoff[s - n_tree];
+            len = cSoff[s - n_tree + 1] - cSoff[s - n_tree];
+        }
+        for (int64_t j = lane; j < len; j += 32) out[ooff[i] + j] = p[j];
+    }
+}
+
+__global__ void k_gather_ids(const int64_t *row_id, const int64_t *cid, int64_t n_tree, const int64_t *src, int64_t m,
+                             int64_t *ids) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = src[i];
+        ids[i] = s < n_tree ? row_id[s] : cid[s - n_tree];
+    }
+}
+
+void rebuild(gts_index *ix) {
+    cudaStream_t st = ix->stream;
+    Tree &t = ix->tree;
+    Cache &c = ix->cache;
+    // visible tree rows in id order, then visible cache slots (their ids are newer)
+    std::vector<int64_t> src;
+    src.reserve(t.n + c.count);
+    if (t.n) {
+        DBuf<int> flag(t.n, st);
+        DBuf<uint64_t> key(t.n, st), key2(t.n, st);
+        DBuf<int64_t> val(t.n, st), val2(t.n, st);
+        k_visible_rows<<<nb(t.n), kT, 0, st>>>(t.row_del.get(), t.row_id.get(), t.n, flag.get(), key.get(), val.get());
+        size_t tb = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, tb, key.get(), key2.get(), val.get(), val2.get(), t.n, 0, 64, st);
+        DBuf<uint8_t> tmp(tb, st);
+        GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, key.get(), key2.get(), val.get(), val2.get(), t.n, 0,
+                                                 64, st));
+        std::vector<uint64_t> hk(t.n);
+        std::vector<int64_t> hv(t.n);
+        GTS_CUDA(cudaMemcpyAsync(hk.data(), key2.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(hv.data(), val2.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < t.n; ++i)
+            if (hk[i] != ~0ull) src.push_back(hv[i]);
+    }
+    if (c.count) {
+        std::vector<int64_t> cdel(c.count);
+        GTS_CUDA(cudaMemcpyAsync(cdel.data(), c.del.get(), c.count * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        for (int64_t s = 0; s < c.count; ++s)
+            if (cdel[s] == kNever) src.push_back(t.n + s);
+    }
+    const int64_t m = (int64_t)src.size();
+    DBuf<int64_t> dsrc(m > 0 ? m : 1, st), ids(m > 0 ? m : 1, st);
+    if (m) GTS_CUDA(cudaMemcpyAsync(dsrc.get(), src.data(), m * 8, cudaMemcpyHostToDevice, st));
+    k_gather_ids<<<nb(m), kT, 0, st>>>(t.row_id.get(), c.id.get(), t.n, dsrc.get(), m, ids.get());
+    Objects o;
+    o.n = m;
+    o.dim = ix->dim;
+    DBuf<float> X;
+    DBuf<uint8_t> S;
+    DBuf<int64_t> Soff;
+    if (ix->dim > 0) {
+        X.alloc((size_t)(m > 0 ? m : 1) * ix->dim, st);
+        k_gather_vec_rows<<<nb(m * (int64_t)ix->dim), kT, 0, st>>>(t.X.get(), c.X.get(), ix->dim, t.n, dsrc.get(), m,
+                                                                   X.get());
+        o.X = X.get();
+    } else {
+        // lengths on the host from the two offset tables
+        std::vector<int64_t> toff(t.n + 1, 0);
+        if (t.n) {
+            GTS_CUDA(cudaMemcpyAsync(toff.data(), t.Soff.get(), (t.n + 1) * 8, cudaMemcpyDeviceToHost, st));
+            GTS_CUDA(cudaStreamSynchronize(st));
+        }
+        std::vector<int64_t> noff(m + 1, 0);
+        int ml = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t s = src[i];
+            const int64_t L = s < t.n ? toff[s + 1] - toff[s] : c.h_Soff[s - t.n + 1] - c.h_Soff[s - t.n];
+            noff[i + 1] = noff[i] + L;
+            ml = std::max<int>(ml, (int)L);
+        }
+        Soff.alloc(m + 1, st);
+        GTS_CUDA(cudaMemcpyAsync(Soff.get(), noff.data(), (m + 1) * 8, cudaMemcpyHostToDevice, st));
+        S.alloc(noff[m] > 0 ? noff[m] : 1, st);
+        k_gather_str_rows<<<nb(m * 32), kT, 0, st>>>(t.S.get(), t.Soff.get(), c.S.get(), c.Soff.get(), t.n, dsrc.get(),
+                                                    m, Soff.get(), S.get());
+        o.S = S.get();
+        o.Soff = Soff.get();
+        o.max_len = ml;
+    }
+    check_launch("rebuild gather");
+    Tree nt;
+    ix->rebuilds += 1;
+    const int h = tree_height(m, ix->F, ix->n_pivots_req);
+    const int64_t root = m > 0 ? (int64_t)(splitmix64(ix->seed + (uint64_t)ix->rebuilds) % (uint64_t)m) : 0;
+    build_tree(nt, o, ids.get(), ix->metric, ix->F, h, root, st);
+    ix->tree = std::move(nt);
+    ix->cache = Cache();
+    ix->rebuild_seq = ix->seq;
+    ix->n_live = m;
+    refresh_loc(ix);
+}
+
+struct ResultPriv {
+    QueryOut out;
+};
+
+void fill_result(gts_result *res, int64_t nq, QueryOut &qo, bool on_device, cudaStream_t st) {
+    res->nq = nq;
+    res->on_device = on_device ? 1 : 0;
+    if (on_device) {
+        auto *p = new ResultPriv();
+        p->out = std::move(qo);
+        res->offsets = p->out.offsets.get();
+        res->ids = p->out.ids.get();
+        res->dist = p->out.dist.get();
+        res->priv_ = p;
+        return;
+    }
+    const int64_t tot = qo.total;
+    res->offsets = (int64_t *)std::malloc(sizeof(int64_t) * (nq + 1));
+    res->ids = (int64_t *)std::malloc(sizeof(int64_t) * (tot > 0 ? tot : 1));
+    res->dist = (float *)std::malloc(sizeof(float) * (tot > 0 ? tot : 1));
+    res->priv_ = nullptr;
+    if (!res->offsets || !res->ids || !res->dist) {
+        std::free(res->offsets);
+        std::free(res->ids);
+        std::free(res->dist);
+        res->offsets = nullptr;
+        res->ids = nullptr;
+        res->dist = nullptr;
+        throw std::bad_alloc();
+    }
+    GTS_CUDA(cudaMemcpyAsync(res->offsets, qo.offsets.get(), (nq + 1) * 8, cudaMemcpyDeviceToHost, st));
+    if (tot) {
+        GTS_CUDA(cudaMemcpyAsync(res->ids, qo.ids.get(), tot * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(res->dist, qo.dist.get(), tot * 4, cudaMemcpyDeviceToHost, st));
+    }
+    GTS_CUDA(cudaStreamSynchronize(st));
+}
+
+gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii, const int32_t *k,
+                        const gts_query_opts *opts, gts_result *out, bool knn) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        GTS_REQUIRE(out != nullptr, GTS_EINVAL, "result is NULL");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+        GTS_REQUIRE(q != nullptr, GTS_EINVAL, "queries are NULL");
+        GTS_REQUIRE((ix->metric == GTS_EDIT) == (q->dim == 0), GTS_EINVAL, "query kind does not match the metric");
+        DevObjects dq;
+        load_objects(q, ix->dim, dq, st, "queries");
+        const int64_t nq = dq.v.n;
+        QueryBatch qb;
+        qb.nq = nq;
+        qb.dim = ix->dim;
+        qb.Q = dq.v.X;
+        qb.S = dq.v.S;
+        qb.Soff = dq.v.Soff;
+        qb.max_len = dq.v.max_len;
+        qb.seq_now = ix->seq;
+        DBuf<float> drad;
+        DBuf<int32_t> dk;
+        DBuf<int64_t> dseq;
+        std::vector<float> hrad;
+        std::vector<int32_t> hk;
+        std::vector<int64_t> hseq;
+        if (knn) {
+            GTS_REQUIRE(nq == 0 || k != nullptr, GTS_EINVAL, "k is NULL");
+            copy_small_to_device(k, nq, q->on_device != 0, dk, hk, st);
+            for (int64_t i = 0; i < nq; ++i)
+                GTS_REQUIRE(hk[i] >= 1 && hk[i] <= 1024, GTS_EINVAL, "k must be in 1 .. 1024");
+            qb.k = dk.get();
+        } else {
+            GTS_REQUIRE(nq == 0 || radii != nullptr, GTS_EINVAL, "radii is NULL");
+            copy_small_to_device(radii, nq, q->on_device != 0, drad, hrad, st);
+            for (int64_t i = 0; i < nq; ++i)
+                GTS_REQUIRE(std::isfinite(hrad[i]) && hrad[i] >= 0.f, GTS_EINVAL, "radius must be finite and >= 0");
+            qb.radii = drad.get();
+        }
+        if (opts && opts->seq) {
+            copy_small_to_device(opts->seq, nq, q->on_device != 0, dseq, hseq, st);
+            for (int64_t i = 0; i < nq; ++i)
+                GTS_REQUIRE(hseq[i] >= ix->rebuild_seq && hseq[i] <= ix->seq, GTS_EINVAL,
+                            "query sequence number before the last rebuild or after the current state");
+            qb.seq = dseq.get();
+        }
+        const int64_t budget = opts && opts->memory_budget > 0 ? opts->memory_budget : ((int64_t)8 << 30);
+        QueryOut qo;
+        run_query(ix, qb, knn, opts ? opts->precision : 0, budget, qo, opts ? opts->stats : nullptr, st);
+        fill_result(out, nq, qo, opts && opts->result_on_device, st);
+    });
+}
+
+}  // namespace
+}  // namespace gts
+
+using namespace gts;
+
+extern "C" {
+
+const char *gts_last_error(void) { return g_last_error.c_str(); }
+
+const char *gts_status_name(gts_status s) {
+    switch (s) {
+        case GTS_OK: return "GTS_OK";
+        case GTS_EINVAL: return "GTS_EINVAL";
+        case GTS_ENOMEM: return "GTS_ENOMEM";
+        case GTS_ECUDA: return "GTS_ECUDA";
+        case GTS_ETIMEOUT: return "GTS_ETIMEOUT";
+        case GTS_ENOTFOUND: return "GTS_ENOTFOUND";
+        case GTS_EOVERFLOW: return "GTS_EOVERFLOW";
+    }
+    return "unknown";
+}
+
+gts_status gts_build(const gts_objects *objects, gts_metric metric, int n_pivots, int fanout,
+                     const gts_build_opts *opts, gts_index **out) {
+    return guarded([&] {
+        GTS_REQUIRE(out != nullptr, GTS_EINVAL, "out is NULL");
+        GTS_REQUIRE(metric == GTS_EDIT || metric == GTS_L1 || metric == GTS_L2, GTS_EINVAL, "unknown metric");
+        GTS_REQUIRE(fanout >= 2 && fanout <= kMaxFanout, GTS_EINVAL, "fanout must be in 2 .. 64");
+        GTS_REQUIRE(n_pivots >= 0 && n_pivots <= kMaxHeight, GTS_EINVAL, "n_pivots must be in 0 .. 12");
+        GTS_REQUIRE(objects != nullptr, GTS_EINVAL, "objects is NULL");
+        GTS_REQUIRE((metric == GTS_EDIT) == (objects->dim == 0), GTS_EINVAL,
+                    "GTS_EDIT needs strings (dim 0); L1/L2 need vectors (dim > 0)");
+        ensure_device();
+        std::unique_ptr<gts_index> ix(new gts_index());
+        GTS_CUDA(cudaGetDevice(&ix->device));
+        ix->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+        ix->metric = metric;
+        ix->dim = objects->dim;
+        ix->F = fanout;
+        ix->n_pivots_req = n_pivots;
+        ix->seed = opts ? opts->seed : 0;
+        ix->cache_limit = opts && opts->cache_limit > 0 ? opts->cache_limit : 4096;
+        DevObjects o;
+        load_objects(objects, -1, o, ix->stream, "objects");
+        const int64_t n = o.v.n;
+        int64_t root = opts ? opts->root_pivot : -1;
+        if (n > 0) {
+            if (root < 0) root = (int64_t)(splitmix64(ix->seed) % (uint64_t)n);
+            GTS_REQUIRE(root < n, GTS_EINVAL, "root_pivot out of range");
+        } else {
+            root = 0;
+        }
+        const int h = tree_height(n, fanout, n_pivots);
+        build_tree(ix->tree, o.v, nullptr, metric, fanout, h, root, ix->stream);
+        ix->next_id = n;
+        ix->n_live = n;
+        refresh_loc(ix.get());
+        *out = ix.release();
+    });
+}
+
+gts_status gts_range(gts_index *index, const gts_objects *queries, const float *radii, const gts_query_opts *opts,
+                     gts_result *out) {
+    return query_common(index, queries, radii, nullptr, opts, out, false);
+}
+
+gts_status gts_knn(gts_index *index, const gts_objects *queries, const int32_t *k, const gts_query_opts *opts,
+                   gts_result *out) {
+    return query_common(index, queries, nullptr, k, opts, out, true);
+}
+
+gts_status gts_insert(gts_index *ix, const gts_objects *objects, int64_t *ids_out) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        GTS_REQUIRE(objects != nullptr, GTS_EINVAL, "objects is NULL");
+        GTS_REQUIRE((ix->metric == GTS_EDIT) == (objects->dim == 0), GTS_EINVAL, "object kind does not match the metric");
+        DevObjects o;
+        load_objects(objects, ix->dim, o, ix->stream, "objects");
+        GTS_REQUIRE(ix->next_id + o.v.n < ((int64_t)1 << 31), GTS_EINVAL, "object ids would reach 2^31");
+        cache_append(ix, o, ids_out);
+        if (ix->cache.count > ix->cache_limit) rebuild(ix);
+    });
+}
+
+gts_status gts_delete(gts_index *ix, const int64_t *ids, int64_t m, int64_t *n_missing) {
+    int64_t missing = 0;
+    gts_status s = guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        GTS_REQUIRE(m >= 0 && (m == 0 || ids != nullptr), GTS_EINVAL, "bad id list");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        std::vector<int64_t> tree_rows, tree_seq, cache_slots, cache_seq;
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t id = ids[i];
+            if (id < 0 || id >= (int64_t)ix->loc.size() || ix->loc[id] == -1) {
+                ++missing;
+                continue;
+            }
+            const int64_t L = ix->loc[id];
+            if (L >= 0) {
+                tree_rows.push_back(L);
+                tree_seq.push_back(ix->seq);
+            } else {
+                cache_slots.push_back(-(L + 2));
+                cache_seq.push_back(ix->seq);
+            }
+            ix->loc[id] = -1;
+            ix->seq += 1;
+            ix->n_live -= 1;
+        }
+        cudaStream_t st = ix->stream;
+        for (int k = 0; k < 2; ++k) {
+            auto &pos = k == 0 ? tree_rows : cache_slots;
+            auto &sq = k == 0 ? tree_seq : cache_seq;
+            int64_t *dst = k == 0 ? ix->tree.row_del.get() : ix->cache.del.get();
+            for (size_t i = 0; i < pos.size(); ++i)
+                GTS_CUDA(cudaMemcpyAsync(dst + pos[i], &sq[i], 8, cudaMemcpyHostToDevice, st));
+        }
+        GTS_CUDA(cudaStreamSynchronize(st));
+    });
+    if (n_missing) *n_missing = missing;
+    if (s == GTS_OK && missing > 0) {
+        set_last_error(std::to_string(missing) + " id(s) unknown or already deleted");
+        return GTS_ENOTFOUND;
+    }
+    return s;
+}
+
+gts_status gts_batch_update(gts_index *ix, const gts_objects *ins, const int64_t *del, int64_t m_del,
+                            int64_t *ids_out) {
+    gts_status s = guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        if (ins) {
+            GTS_REQUIRE((ix->metric == GTS_EDIT) == (ins->dim == 0), GTS_EINVAL, "object kind does not match the metric");
+            DevObjects o;
+            load_objects(ins, ix->dim, o, ix->stream, "objects");
+            GTS_REQUIRE(ix->next_id + o.v.n < ((int64_t)1 << 31), GTS_EINVAL, "object ids would reach 2^31");
+            cache_append(ix, o, ids_out);
+        }
+    });
+    if (s != GTS_OK) return s;
+    int64_t missing = 0;
+    if (m_del > 0) {
+        s = gts_delete(ix, del, m_del, &missing);
+        if (s != GTS_OK && s != GTS_ENOTFOUND) return s;
+    }
+    s = guarded([&] { rebuild(ix); });
+    if (s == GTS_OK && missing > 0) {
+        set_last_error(std::to_string(missing) + " id(s) unknown or already deleted");
+        return GTS_ENOTFOUND;
+    }
+    return s;
+}
+
+gts_status gts_rebuild(gts_index *ix) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        rebuild(ix);
+    });
+}
+
+gts_status gts_info(const gts_index *ix, gts_index_info *out) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr && out != nullptr, GTS_EINVAL, "NULL argument");
+        out->n_tree = ix->tree.n;
+        out->n_cache = ix->cache.count;
+        out->n_live = ix->n_live;
+        out->next_id = ix->next_id;
+        out->seq = ix->seq;
+        out->rebuild_seq = ix->rebuild_seq;
+        out->h = ix->tree.h;
+        out->fanout = ix->F;
+        out->metric = ix->metric;
+        out->dim = ix->dim;
+        const Cache &c = ix->cache;
+        out->device_bytes = (int64_t)(ix->tree.device_bytes() + c.X.bytes() + c.S.bytes() + c.Soff.bytes() +
+                                      c.id.bytes() + c.ins.bytes() + c.del.bytes());
+    });
+}
+
+gts_status gts_tree_level(const gts_index *ix, int level, int64_t *pos, int64_t *size, float *lo, float *hi,
+                          int64_t *pivot) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        const Tree &t = ix->tree;
+        GTS_REQUIRE(level >= 0 && level <= t.h, GTS_EINVAL, "level out of range");
+        GTS_CUDA(cudaSetDevice(ix->device));
+        cudaStream_t st = ix->stream;
+        const int64_t a = t.lvl_off[level], cnt = t.lvl_off[level + 1] - a;
+        std::vector<int32_t> p(cnt), s(cnt), pv(cnt);
+        std::vector<float> l(cnt), hh(cnt);
+        GTS_CUDA(cudaMemcpyAsync(p.data(), t.npos.get() + a, cnt * 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(s.data(), t.nsize.get() + a, cnt * 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(pv.data(), t.npiv.get() + a, cnt * 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(l.data(), t.nlo.get() + a, cnt * 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(hh.data(), t.nhi.get() + a, cnt * 4, cudaMemcpyDeviceToHost, st));
+        std::vector<int64_t> rid(t.n);
+        if (t.n) GTS_CUDA(cudaMemcpyAsync(rid.data(), t.row_id.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < cnt; ++i) {
+            if (pos) pos[i] = p[i];
+            if (size) size[i] = s[i];
+            if (lo) lo[i] = l[i];
+            if (hi) hi[i] = hh[i];
+            if (pivot) pivot[i] = (level < t.h && pv[i] >= 0) ? rid[pv[i]] : -1;
+        }
+    });
+}
+
+gts_status gts_table(const gts_index *ix, int64_t *ids, float *table) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        const Tree &t = ix->tree;
+        GTS_CUDA(cudaSetDevice(ix->device));
+        cudaStream_t st = ix->stream;
+        if (ids && t.n) GTS_CUDA(cudaMemcpyAsync(ids, t.row_id.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
+        if (table && t.n)
+            GTS_CUDA(cudaMemcpyAsync(table, t.table.get(), (size_t)t.h * t.n * 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+gts_status gts_result_copy(const gts_result *r, int64_t *offsets, int64_t *ids, float *dist) {
+    return guarded([&] {
+        GTS_REQUIRE(r != nullptr && r->offsets != nullptr, GTS_EINVAL, "empty result");
+        int64_t total = 0;
+        GTS_CUDA(cudaMemcpy(&total, r->offsets + r->nq, 8, cudaMemcpyDefault));
+        if (offsets) GTS_CUDA(cudaMemcpy(offsets, r->offsets, (r->nq + 1) * 8, cudaMemcpyDefault));
+        if (ids && total) GTS_CUDA(cudaMemcpy(ids, r->ids, total * 8, cudaMemcpyDefault));
+        if (dist && total) GTS_CUDA(cudaMemcpy(dist, r->dist, total * 4, cudaMemcpyDefault));
+    });
+}
+
+void gts_result_free(gts_result *r) {
+    if (!r) return;
+    if (r->priv_) {
+        delete (ResultPriv *)r->priv_;
+    } else {
+        std::free(r->offsets);
+        std::free(r->ids);
+        std::free(r->dist);
+    }
+    r->offsets = nullptr;
+    r->ids = nullptr;
+    r->dist = nullptr;
+    r->priv_ = nullptr;
+    r->nq = 0;
+}
+
+void gts_free(gts_index *ix) {
+    if (!ix) return;
+    cudaSetDevice(ix->device);
+    cudaStreamSynchronize(ix->stream);
+    delete ix;
+}
+
+}  // extern "C"

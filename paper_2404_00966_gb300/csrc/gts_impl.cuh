@@ -1,0 +1,191 @@
+// Internal declarations of the GTS library (not part of the C ABI).
+//
+// Data layout in HBM (one index):
+//   * X      float32[n * dim]   vectors in leaf order (row r = r-th object of the
+//                               table list, Section 4.2), or
+//     S/Soff uint8 bytes + int64[n + 1] offsets, strings in leaf order.
+//   * row_id int64[n]           row -> object id.
+//   * table  float32[h * n]     column l, row r: distance of row r's object to the
+//                               pivot of its level-l ancestor (the table list, all
+//                               h levels kept).
+//   * row_del int64[n]          sequence number at which the row was deleted
+//                               (INT64_MAX = never), the deletion mark of Section 4.4.
+//   * node list, level by level (Eq. 1, 0-based): level l holds fanout^l nodes, the
+//     children of node i are nodes i * fanout + j of level l + 1.  Per node:
+//     pos, size (int32, rows [pos, pos + size) of the table list), lo, hi (float32,
+//     distance interval to the parent's pivot) and piv (int32 row of the pivot, or
+//     -1; levels 0 .. h-1).
+//   * cache list (Section 4.4): inserted objects not yet in the tree, with their
+//     ids and insert / delete sequence numbers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "gts.h"
+
+namespace gts {
+
+constexpr int kMaxFanout = 64;
+constexpr int kMaxHeight = 12;
+constexpr int kMaxStrLen = 1024;
+constexpr int64_t kNever = INT64_MAX;
+
+// ------------------------------------------------------------------ errors
+
+struct Error : std::runtime_error {
+    gts_status status;
+    Error(gts_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+void set_last_error(const std::string &msg);
+
+#define GTS_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            if (e_ == cudaErrorMemoryAllocation)                                                    \
+                throw ::gts::Error(GTS_ENOMEM, std::string("out of device memory at ") + #call);    \
+            throw ::gts::Error(GTS_ECUDA, std::string(cudaGetErrorString(e_)) + " at " + #call +    \
+                                              " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+        }                                                                                           \
+    } while (0)
+
+#define GTS_REQUIRE(cond, status, msg)                                                              \
+    do {                                                                                            \
+        if (!(cond)) throw ::gts::Error(status, msg);                                               \
+    } while (0)
+
+inline void check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(GTS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ memory
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept { *this = std::move(o); }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count) GTS_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    T *get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ------------------------------------------------------------------ index
+
+struct Objects {           // a view of caller-provided or library objects
+    int64_t n = 0;
+    int dim = 0;           // 0 = strings
+    const float *X = nullptr;
+    const uint8_t *S = nullptr;
+    const int64_t *Soff = nullptr;
+    int max_len = 0;       // longest string (strings only)
+};
+
+struct Tree {
+    int metric = 0, dim = 0, F = 0, h = 0;
+    int64_t n = 0;
+    DBuf<float> X;
+    DBuf<uint8_t> S;
+    DBuf<int64_t> Soff;
+    DBuf<int64_t> row_id;
+    DBuf<float> table;
+    DBuf<int64_t> row_del;
+    std::vector<int64_t> lvl_off;   // h + 2 entries: first node of each level, last = total nodes
+    DBuf<int32_t> npos, nsize, npiv;
+    DBuf<float> nlo, nhi;
+    int max_len = 0;                // longest string
+    size_t device_bytes() const;
+};
+
+struct Cache {
+    int64_t count = 0, cap = 0;
+    DBuf<float> X;                   // cap * dim
+    DBuf<uint8_t> S;                 // bytes
+    DBuf<int64_t> Soff;              // cap + 1
+    int64_t s_bytes = 0, s_cap = 0;
+    DBuf<int64_t> id, ins, del;
+    std::vector<int64_t> h_Soff;     // host copy of the offsets
+    int max_len = 0;
+};
+
+}  // namespace gts
+
+struct gts_index {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int metric = 0, dim = 0, F = 0, n_pivots_req = 0;
+    gts::Tree tree;
+    gts::Cache cache;
+    // host bookkeeping: loc[id] >= 0 tree row, <= -2 cache slot (-(slot + 2)), -1 gone
+    std::vector<int64_t> loc;
+    int64_t next_id = 0, seq = 1, rebuild_seq = 1, n_live = 0;
+    int64_t cache_limit = 4096;
+    uint64_t seed = 0;
+    int64_t rebuilds = 0;
+};
+
+namespace gts {
+
+// build.cu
+void build_tree(Tree &t, const Objects &objs, const int64_t *d_ids_or_null, int metric, int F, int h,
+                int64_t root_index, cudaStream_t st);
+int tree_height(int64_t n, int F, int n_pivots);
+uint64_t splitmix64(uint64_t x);
+
+// search.cu
+struct QueryBatch {
+    int64_t nq = 0;
+    int dim = 0;
+    const float *Q = nullptr;        // device
+    const uint8_t *S = nullptr;      // device
+    const int64_t *Soff = nullptr;   // device
+    int max_len = 0;
+    const float *radii = nullptr;    // device (range)
+    const int32_t *k = nullptr;      // device (knn)
+    const int64_t *seq = nullptr;    // device or null
+    int64_t seq_now = 0;
+    int64_t max_k = 0;
+};
+
+struct QueryOut {
+    DBuf<int64_t> offsets, ids;
+    DBuf<float> dist;
+    int64_t total = 0;
+};
+
+void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int64_t budget,
+               QueryOut &out, int64_t *stats, cudaStream_t st);
+
+}  // namespace gts

@@ -1,0 +1,1127 @@
+// Batched range and kNN search over a GTS index (Section 5, Algorithms 4-5).
+//
+// One query batch walks the tree level by level.  The frontier (the paper's
+// Q_Res) is a query-major list of (query, node) entries; each entry carries the
+// query's distances to the pivots on the node's path.  Per level l:
+//   1. pivot distances d(q, pivot(N)) of every entry (FP32 for vectors, exact
+//      bit-parallel DP for strings);
+//   2. kNN only: the threshold tau_q, the k-th smallest distance among distinct
+//      visible objects evaluated so far (the pivots), kept as an upper bound in
+//      FP64 (Section 5.2: the distance bound starts at infinity and narrows);
+//   3. expansion: a child c of entry (q, N) survives unless the interval
+//      [d(q,p) - t, d(q,p) + t] misses [lo_c, hi_c], t = r (Lemma 1) or tau_q
+//      (Lemma 2, pruning only on a strict miss), with a proven FP32 slack.
+// Before each expansion the two-stage scheduler (Section 5.1) bounds the next
+// level's table to budget / ((h - l) * fanout) bytes and, if it would not fit,
+// runs the entries in groups, depth first.  At the last pivot level the
+// surviving leaves of an entry form a bit mask; the leaf scan walks the rows of
+// the entry's node (the leaves of one node are contiguous in the table list),
+// keeps rows of surviving leaves whose table lower bound max_l |D_l - d_l|
+// passes, and emits (query, row) candidates with warp ballots and prefix sums.
+// Candidates are verified with the true metric; float metrics carry a proven
+// error band and candidates inside it are recomputed in FP64 in the reference
+// operation order.  The cache list is scanned by brute force (Section 4.4).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "gts_impl.cuh"
+#include "metric.cuh"
+
+namespace gts {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kWarpsPerBlock = kT / 32;
+constexpr int kKeepCap = 2048;   // exact-key candidates staged in shared memory per query
+
+inline unsigned nblocks(int64_t work, int per) {
+    int64_t b = (work + per - 1) / per;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+    return (unsigned)b;
+}
+
+struct Dev {
+    int metric, dim, F, h;
+    int64_t n;
+    const float *X;
+    const uint8_t *S;
+    const int64_t *Soff;
+    const int64_t *row_id;
+    const float *table;
+    const int64_t *row_del;
+    const int32_t *npos, *nsize, *npiv;
+    const float *nlo, *nhi;
+    int64_t cn;
+    const float *cX;
+    const uint8_t *cS;
+    const int64_t *cSoff, *cid, *cins, *cdel;
+    const float *Q;
+    const uint8_t *QS;
+    const int64_t *QSoff;
+    const int64_t *qseq;
+    float rel;     // FP32 relative error bound of one distance (0 for edit distance)
+    float epsc;    // pruning slack factor (0 for edit distance)
+};
+
+__device__ __forceinline__ const float *vrow(const Dev &d, int64_t row) {
+    return row < d.n ? d.X + row * d.dim : d.cX + (row - d.n) * d.dim;
+}
+__device__ __forceinline__ bool row_visible(const Dev &d, int64_t row, int64_t s) {
+    if (row < d.n) return d.row_del[row] > s;
+    const int64_t c = row - d.n;
+    return d.cins[c] < s && s < d.cdel[c];
+}
+__device__ __forceinline__ int64_t row_oid(const Dev &d, int64_t row) {
+    return row < d.n ? d.row_id[row] : d.cid[row - d.n];
+}
+__device__ __forceinline__ void srow(const Dev &d, int64_t row, const uint8_t *&p, int &len) {
+    if (row < d.n) {
+        p = d.S + d.Soff[row];
+        len = (int)(d.Soff[row + 1] - d.Soff[row]);
+    } else {
+        const int64_t c = row - d.n;
+        p = d.cS + d.cSoff[c];
+        len = (int)(d.cSoff[c + 1] - d.cSoff[c]);
+    }
+}
+
+// first index in [a, b) with v[i] >= x (v sorted ascending)
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *v, int64_t a, int64_t b, int32_t x) {
+    while (a < b) {
+        int64_t m = (a + b) >> 1;
+        if (v[m] < x) a = m + 1;
+        else b = m;
+    }
+    return a;
+}
+
+__global__ void k_fill_f32(float *a, int64_t n, float v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+__global__ void k_fill_i64(int64_t *a, int64_t n, int64_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+__global__ void k_root_entries(int32_t *eq, int32_t *enode, int64_t nq) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        eq[i] = (int32_t)i;
+        enode[i] = 0;
+    }
+}
+__global__ void k_thresholds(const float *radii, int64_t nq, bool floor_r, float *thr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        thr[i] = floor_r ? floorf(radii[i]) : radii[i];
+}
+__global__ void k_k_to_i64(const int32_t *k, int64_t nq, int64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = k[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[nq] = 0;
+}
+
+// ---------------------------------------------------------------- pivot distances
+
+template <bool L2>
+__global__ void k_pivdist_vec(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                              int64_t lvl_base, int64_t e0, int64_t e1, float *__restrict__ path, int l) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (w >= e1) return;
+    const int32_t q = eq[w];
+    const int32_t prow = d.npiv[lvl_base + enode[w]];
+    const float s = warp_vec_dist<L2>(d.Q + (int64_t)q * d.dim, d.X + (int64_t)prow * d.dim, d.dim, lane);
+    if (lane == 0) path[w * d.h + l] = L2 ? sqrtf(s) : s;
+}
+
+// Strings: blocks take runs of entries; entries of one query share the
+// query's match masks (pattern = query, text = pivot).
+template <int W>
+__global__ void k_pivdist_str(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                              int64_t lvl_base, int64_t e0, int64_t e1, int chunk, float *__restrict__ path, int l) {
+    __shared__ uint64_t Peq[256 * W];
+    const int64_t a0 = e0 + (int64_t)blockIdx.x * chunk;
+    const int64_t a1 = a0 + chunk < e1 ? a0 + chunk : e1;
+    int64_t s = a0;
+    while (s < a1) {
+        const int32_t q = eq[s];
+        const int64_t t = lower_bound_i32(eq, s, a1, q + 1);
+        const int m = (int)(d.QSoff[q + 1] - d.QSoff[q]);
+        if (m > 0) build_peq<W>(Peq, d.QS + d.QSoff[q], m);
+        for (int64_t e = s + threadIdx.x; e < t; e += blockDim.x) {
+            const int32_t prow = d.npiv[lvl_base + enode[e]];
+            const uint8_t *tx;
+            int len;
+            srow(d, prow, tx, len);
+            path[e * d.h + l] = (float)(m > 0 ? myers_edit<W>(Peq, m, tx, len) : len);
+        }
+        __syncthreads();
+        s = t;
+    }
+}
+
+// ---------------------------------------------------------------- kNN threshold
+
+// Warp per query.  The query's list of the k smallest (upper bound, id) of
+// distinct visible pivots seen so far is merged with this level's entries;
+// tau_q = the k-th bound, rounded up to float, or +inf while fewer than k.
+__global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode, int64_t lvl_base,
+                      int64_t e0, int64_t e1, const float *__restrict__ path, int l, int64_t nq,
+                      const int32_t *__restrict__ kq, const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id,
+                      int32_t *tk_n, float *tau) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    const int64_t a = lower_bound_i32(eq, e0, e1, (int32_t)q);
+    const int64_t b = lower_bound_i32(eq, a, e1, (int32_t)q + 1);
+    if (a == b) return;
+    const int K = kq[q];
+    double *D = tk_d + koff[q];
+    int64_t *I = tk_id + koff[q];
+    int n = tk_n[q];
+    const int64_t s = d.qseq[q];
+    const double up = 1.0 + 2.0 * (double)d.rel;
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t e = base + lane;
+        bool cand = false;
+        double ub = 0.0;
+        int64_t id = 0;
+        if (e < b) {
+            const int32_t prow = d.npiv[lvl_base + enode[e]];
+            if (row_visible(d, prow, s)) {
+                const float dv = path[e * d.h + l];
+                ub = d.rel > 0.f ? (double)dv * up + (double)kAbsFloor : (double)dv;
+                id = d.row_id[prow];
+                cand = (n < K) || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, cand);
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const double u = __shfl_sync(0xffffffffu, ub, src);
+            const int64_t iid = __shfl_sync(0xffffffffu, id, src);
+            if (lane == 0) {
+                bool dup = false;
+                for (int i = 0; i < n; ++i)
+                    if (I[i] == iid) { dup = true; break; }
+                const bool fits = n < K || u < D[K - 1] || (u == D[K - 1] && iid < I[K - 1]);
+                if (!dup && fits) {
+                    int p = n < K ? n : K - 1;
+                    while (p > 0 && (D[p - 1] > u || (D[p - 1] == u && I[p - 1] > iid))) {
+                        D[p] = D[p - 1];
+                        I[p] = I[p - 1];
+                        --p;
+                    }
+                    D[p] = u;
+                    I[p] = iid;
+                    if (n < K) ++n;
+                }
+            }
+            n = __shfl_sync(0xffffffffu, n, 0);
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        tk_n[q] = n;
+        tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+    }
+}
+
+// ---------------------------------------------------------------- expansion
+
+__device__ __forceinline__ bool interval_hit(float dq, float thr, float lo, float hi, float epsc) {
+    const float eps = epsc > 0.f ? epsc * (dq + thr + fabsf(hi)) : 0.f;
+    return (dq - thr <= hi + eps) && (dq + thr + eps >= lo);
+}
+
+// MODE 0: count surviving children per entry; 1: write them as the next
+// level's entries; 2: last pivot level, write the surviving-leaf bit mask.
+template <int MODE>
+__global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                         const float *__restrict__ path, int l, int64_t lvl_next, int64_t e0, int64_t e1,
+                         const float *__restrict__ thr_q, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
+                         int32_t *__restrict__ nq_out, int32_t *__restrict__ nnode_out, float *__restrict__ npath_out,
+                         uint64_t *__restrict__ mask_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (e >= e1) return;
+    const int32_t q = eq[e];
+    const int32_t node = enode[e];
+    const float dq = path[e * d.h + l];
+    const float thr = thr_q[q];
+    uint64_t m = 0;
+    for (int j0 = 0; j0 < d.F; j0 += 32) {
+        const int j = j0 + lane;
+        bool keep = false;
+        if (j < d.F) {
+            const int64_t c = lvl_next + (int64_t)node * d.F + j;
+            keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+        }
+        m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
+    }
+    if (MODE == 0) {
+        if (lane == 0) cnt[e - e0] = __popcll(m);
+    } else if (MODE == 2) {
+        if (lane == 0) mask_out[e - e0] = m;
+    } else {
+        const int64_t base = off[e - e0];
+        for (int j0 = 0; j0 < d.F; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < d.F && ((m >> j) & 1ull)) {
+                const int64_t o = base + __popcll(m & ((1ull << j) - 1ull));
+                nq_out[o] = q;
+                nnode_out[o] = node * d.F + j;
+                for (int t = 0; t <= l; ++t) npath_out[o * d.h + t] = path[e * d.h + t];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- leaf scan
+
+// Warp per last-level entry: rows of the entry's node, in 32-row strips; a
+// row passes if its leaf survived, it is visible at the query's sequence
+// number and its table lower bound max_l |D_l(row) - d(q, p_l)| is within the
+// threshold (Lemma 1 / Lemma 2 on every pivot of the path).
+template <bool WRITE>
+__global__ void k_leafscan(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                           const float *__restrict__ path, int64_t lvl_last, int64_t e0, int64_t e1,
+                           const uint64_t *__restrict__ mask, const float *__restrict__ thr_q,
+                           int32_t *__restrict__ cnt, const int64_t *__restrict__ off, int32_t *__restrict__ cq,
+                           int32_t *__restrict__ crow, unsigned long long *__restrict__ scanned) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (e >= e1) return;
+    const uint64_t m = mask[e - e0];
+    if (m == 0) {
+        if (!WRITE && lane == 0) cnt[e - e0] = 0;
+        return;
+    }
+    const int32_t q = eq[e];
+    const int64_t node = lvl_last + enode[e];
+    const int32_t pos = d.npos[node], size = d.nsize[node];
+    const int32_t avg = size / d.F;
+    const int64_t s = d.qseq[q];
+    const float thr = thr_q[q];
+    float dq[kMaxHeight];
+#pragma unroll
+    for (int t = 0; t < kMaxHeight; ++t) dq[t] = t < d.h ? path[e * d.h + t] : 0.f;
+    int64_t count = 0, tested = 0;
+    const int64_t base = WRITE ? off[e - e0] : 0;
+    for (int32_t r0 = 0; r0 < size; r0 += 32) {
+        const int32_t r = r0 + lane;
+        bool pass = false, test = false;
+        if (r < size) {
+            int32_t j = avg > 0 ? r / avg : d.F - 1;
+            if (j > d.F - 1) j = d.F - 1;
+            if ((m >> j) & 1ull) {
+                test = true;
+                const int64_t row = pos + r;
+                if (d.row_del[row] > s) {
+                    pass = true;
+#pragma unroll
+                    for (int t = 0; t < kMaxHeight; ++t) {
+                        if (t < d.h) {
+                            const float T = d.table[(int64_t)t * d.n + row];
+                            const float eps = d.epsc > 0.f ? d.epsc * (T + dq[t] + thr) : 0.f;
+                            if (fabsf(T - dq[t]) > thr + eps) pass = false;
+                        }
+                    }
+                }
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, pass);
+        if (WRITE && pass) {
+            const int64_t o = base + count + __popc(b & ((1u << lane) - 1u));
+            cq[o] = q;
+            crow[o] = pos + r;
+        }
+        count += __popc(b);
+        tested += __popc(__ballot_sync(0xffffffffu, test));
+    }
+    if (!WRITE && lane == 0) {
+        cnt[e - e0] = (int32_t)count;
+        atomicAdd(scanned, (unsigned long long)tested);
+    }
+}
+
+// Cache list (Section 4.4): every (query, cache slot) pair of a query range.
+__global__ void k_cache_cands(int64_t qa, int64_t qb, int64_t n, int64_t cn, int32_t *cq, int32_t *crow) {
+    const int64_t total = (qb - qa) * cn;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = qa + i / cn;
+        cq[i] = (int32_t)q;
+        crow[i] = (int32_t)(n + i % cn);
+    }
+}
+
+// ---------------------------------------------------------------- verification
+
+// Warp per candidate.  Range: accept when the FP32 upper bound is below r,
+// reject when the lower bound is above r, otherwise decide in FP64 exactly as
+// the CPU reference does.  kNN: store the FP32 distance (+inf if invisible).
+template <bool L2, bool KNN>
+__global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
+                             const float *__restrict__ thr_q, float *__restrict__ cdist, uint8_t *__restrict__ keep,
+                             unsigned long long *__restrict__ rechecks) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= C) return;
+    const int32_t q = cq[c];
+    const int64_t row = crow[c];
+    if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
+        if (lane == 0) {
+            cdist[c] = __int_as_float(0x7f800000);
+            if (!KNN) keep[c] = 0;
+        }
+        return;
+    }
+    const float *qv = d.Q + (int64_t)q * d.dim;
+    const float *xv = vrow(d, row);
+    const float s = warp_vec_dist<L2>(qv, xv, d.dim, lane);
+    const float d32 = L2 ? sqrtf(s) : s;
+    if (KNN) {
+        if (lane == 0) cdist[c] = d32;
+        return;
+    }
+    if (lane != 0) return;
+    const float r = thr_q[q];
+    const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
+    const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+    if (hi < r * (1.f - 1e-9f)) {
+        keep[c] = 1;
+        cdist[c] = d32;
+    } else if (lo > r * (1.f + 1e-9f)) {
+        keep[c] = 0;
+    } else {
+        const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+        const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
+        keep[c] = key <= lim ? 1 : 0;
+        cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
+        atomicAdd(rechecks, 1ull);
+    }
+}
+
+template <int W, bool KNN>
+__global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
+                             int chunk, const float *__restrict__ thr_q, float *__restrict__ cdist,
+                             uint8_t *__restrict__ keep) {
+    __shared__ uint64_t Peq[256 * W];
+    const int64_t a0 = (int64_t)blockIdx.x * chunk;
+    const int64_t a1 = a0 + chunk < C ? a0 + chunk : C;
+    int64_t s = a0;
+    while (s < a1) {
+        const int32_t q = cq[s];
+        const int64_t t = lower_bound_i32(cq, s, a1, q + 1);
+        const int m = (int)(d.QSoff[q + 1] - d.QSoff[q]);
+        if (m > 0) build_peq<W>(Peq, d.QS + d.QSoff[q], m);
+        const float r = thr_q[q];
+        for (int64_t c = s + threadIdx.x; c < t; c += blockDim.x) {
+            const int64_t row = crow[c];
+            if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
+                cdist[c] = __int_as_float(0x7f800000);
+                if (!KNN) keep[c] = 0;
+                continue;
+            }
+            const uint8_t *tx;
+            int len;
+            srow(d, row, tx, len);
+            const float dist = (float)(m > 0 ? myers_edit<W>(Peq, m, tx, len) : len);
+            cdist[c] = dist;
+            if (!KNN) keep[c] = dist <= r ? 1 : 0;
+        }
+        __syncthreads();
+        s = t;
+    }
+}
+
+// ---------------------------------------------------------------- kNN merge
+
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+
+// rank-th smallest (1-based) value among those enumerated by get(i, &v) for
+// i in [0, M); values are non-negative keys compared as unsigned integers.
+// Whole block; returns the same value in every thread.
+template <int BITS, class Get>
+__device__ uint64_t block_select(int64_t M, int64_t rank, Get get, unsigned *hist, int64_t *sh) {
+    uint64_t prefix = 0, pmask = 0;
+    for (int shift = BITS - 4; shift >= 0; shift -= 4) {
+        if (threadIdx.x < 16) hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+            uint64_t v;
+            if (get(i, v) && (v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 15u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t c = 0, r = sh[1] = rank;
+            int sel = 15;
+            for (int b = 0; b < 16; ++b) {
+                if (c + hist[b] >= r) { sel = b; break; }
+                c += hist[b];
+            }
+            sh[0] = sel;
+            sh[1] = r - c;
+        }
+        __syncthreads();
+        prefix |= (uint64_t)sh[0] << shift;
+        pmask |= 15ull << shift;
+        rank = sh[1];
+        __syncthreads();
+    }
+    return prefix;
+}
+
+__device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// One block per query.  Merges this group's candidates into the query's
+// running answer (exact keys: FP64 key for L1/L2, the integer for edit):
+//  A. float metrics: U = k-th smallest upper bound over the answer so far and
+//     the candidates' FP32 intervals; only candidates whose lower bound is
+//     <= U can reach the top k, and only those get an FP64 key;
+//  B. the k-th smallest exact (key, id) over answer + kept candidates, ties
+//     to the smaller id, gives exactly min(k, total) survivors, which are
+//     sorted and written back as the new answer.
+template <int METRIC>
+__global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+                            const float *__restrict__ cdist, int64_t C, const int32_t *__restrict__ kq,
+                            const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
+                            int32_t *__restrict__ bn, double *__restrict__ ckey,
+                            unsigned long long *__restrict__ rechecks) {
+    __shared__ unsigned hist[16];
+    __shared__ int64_t sh[4];
+    __shared__ int64_t red[kWarpsPerBlock];
+    __shared__ double kk[kKeepCap];
+    __shared__ int64_t ki[kKeepCap];
+    __shared__ int nkeep;
+    const int32_t q = blockIdx.x;
+    const int64_t a = lower_bound_i32(cq, 0, C, q);
+    const int64_t b = lower_bound_i32(cq, a, C, q + 1);
+    if (a == b) return;
+    const int64_t M = b - a;
+    const int K = kq[q];
+    const int nb = bn[q];
+    double *BD = bd + koff[q];
+    int64_t *BI = bi + koff[q];
+    constexpr bool FLOAT_METRIC = METRIC != GTS_EDIT;
+    const float up = 1.f + 2.f * d.rel, dn = 1.f - 2.f * d.rel;
+    // ---- A: candidates that can still enter the top k
+    if (FLOAT_METRIC) {
+        uint64_t U = 0x7f800000ull;   // +inf as float bits
+        if ((int64_t)nb + M > K) {
+            auto get_hi = [&](int64_t i, uint64_t &v) -> bool {
+                float x;
+                if (i < nb) {
+                    const double ex = METRIC == GTS_L2 ? __dsqrt_rn(BD[i]) : BD[i];
+                    x = __double2float_ru(ex);
+                } else {
+                    const float dv = cdist[a + i - nb];
+                    x = dv * up + kAbsFloor;
+                }
+                v = __float_as_uint(x);
+                return true;
+            };
+            U = block_select<32>((int64_t)nb + M, K, get_hi, hist, sh);
+        }
+        const float Uf = __uint_as_float((uint32_t)U);
+        int64_t kept = 0;
+        for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+            const float dv = cdist[a + i];
+            double key = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
+            if (dv * dn - kAbsFloor <= Uf && dv != __int_as_float(0x7f800000)) {
+                const float *qv = d.Q + (int64_t)q * d.dim;
+                const float *xv = vrow(d, crow[a + i]);
+                key = METRIC == GTS_L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+                ++kept;
+            }
+            ckey[a + i] = key;
+        }
+        kept = block_sum(kept, red);
+        if (threadIdx.x == 0) atomicAdd(rechecks, (unsigned long long)kept);
+    } else {
+        for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
+            const float dv = cdist[a + i];
+            ckey[a + i] = dv == __int_as_float(0x7f800000) ? __longlong_as_double(0x7ff0000000000000ll) : (double)dv;
+        }
+    }
+    __syncthreads();
+    // ---- B: exact selection over answer-so-far (first nb) and candidates
+    const uint64_t INF = 0x7ff0000000000000ull;
+    auto get_key = [&](int64_t i, uint64_t &v) -> bool {
+        v = i < nb ? dbits(BD[i]) : dbits(ckey[a + i - nb]);
+        return v < INF;
+    };
+    int64_t total = 0;
+    for (int64_t i = threadIdx.x; i < (int64_t)nb + M; i += blockDim.x) {
+        uint64_t v;
+        total += get_key(i, v) ? 1 : 0;
+    }
+    total = block_sum(total, red);
+    const int64_t take = total < K ? total : K;
+    if (take == 0) return;
+    uint64_t Vk = INF, Ik = 0x7fffffffffffffffull;
+    if (total > K) {
+        Vk = block_select<64>((int64_t)nb + M, K, get_key, hist, sh);
+        int64_t lt = 0;
+        for (int64_t i = threadIdx.x; i < (int64_t)nb + M; i += blockDim.x) {
+            uint64_t v;
+            if (get_key(i, v) && v < Vk) ++lt;
+        }
+        lt = block_sum(lt, red);
+        auto get_id = [&](int64_t i, uint64_t &v) -> bool {
+            uint64_t key;
+            if (!get_key(i, key) || key != Vk) return false;
+            v = (uint64_t)(i < nb ? BI[i] : row_oid(d, crow[a + i - nb]));
+            return true;
+        };
+        Ik = block_select<32>((int64_t)nb + M, K - lt, get_id, hist, sh);
+    }
+    if (threadIdx.x == 0) nkeep = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < (int64_t)nb + M; i += blockDim.x) {
+        uint64_t v;
+        if (!get_key(i, v)) continue;
+        const int64_t id = i < nb ? BI[i] : row_oid(d, crow[a + i - nb]);
+        if (v < Vk || (v == Vk && (uint64_t)id <= Ik)) {
+            const int p = atomicAdd(&nkeep, 1);
+            if (p < kKeepCap) {
+                kk[p] = __longlong_as_double((long long)v);
+                ki[p] = id;
+            }
+        }
+    }
+    __syncthreads();
+    // bitonic sort of the survivors by (key, id)
+    int L = 1;
+    while (L < take) L <<= 1;
+    for (int i = threadIdx.x; i < L; i += blockDim.x)
+        if (i >= take) {
+            kk[i] = __longlong_as_double(0x7ff0000000000000ll);
+            ki[i] = 0x7fffffffffffffffll;
+        }
+    __syncthreads();
+    for (int k2 = 2; k2 <= L; k2 <<= 1) {
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool asc = (i & k2) == 0;
+                    const bool gt = kk[i] > kk[ixj] || (kk[i] == kk[ixj] && ki[i] > ki[ixj]);
+                    if (gt == asc) {
+                        const double tk = kk[i];
+                        kk[i] = kk[ixj];
+                        kk[ixj] = tk;
+                        const int64_t ti = ki[i];
+                        ki[i] = ki[ixj];
+                        ki[ixj] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < take; i += blockDim.x) {
+        BD[i] = kk[i];
+        BI[i] = ki[i];
+    }
+    if (threadIdx.x == 0) bn[q] = (int32_t)take;
+}
+
+// ---------------------------------------------------------------- results
+
+__global__ void k_range_pack(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+                             const float *__restrict__ cdist, const uint8_t *__restrict__ keep, int64_t C,
+                             const int64_t *__restrict__ pos, Dev d, uint64_t *__restrict__ rkey,
+                             float *__restrict__ rdist) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[c]) continue;
+        const int64_t o = pos[c];
+        rkey[o] = ((uint64_t)(uint32_t)cq[c] << 32) | (uint64_t)(uint32_t)row_oid(d, crow[c]);
+        rdist[o] = cdist[c];
+    }
+}
+
+__global__ void k_u8_to_i64(const uint8_t *a, int64_t n, int64_t *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) b[n] = 0;
+}
+
+__global__ void k_range_counts(const uint64_t *__restrict__ rkey, int64_t R, int64_t *__restrict__ counts,
+                               int64_t *__restrict__ ids) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd((unsigned long long *)&counts[rkey[i] >> 32], 1ull);
+        ids[i] = (int64_t)(rkey[i] & 0xffffffffull);
+    }
+}
+
+__global__ void k_knn_counts(const int32_t *bn, int64_t nq, int64_t *counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        counts[i] = bn[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[nq] = 0;
+}
+
+__global__ void k_knn_emit(const int64_t *__restrict__ offsets, const int64_t *__restrict__ koff,
+                           const double *__restrict__ bd, const int64_t *__restrict__ bi, const int32_t *__restrict__ bn,
+                           int64_t nq, bool l2, int64_t *__restrict__ ids, float *__restrict__ dist) {
+    const int64_t q = blockIdx.x;
+    if (q >= nq) return;
+    for (int i = threadIdx.x; i < bn[q]; i += blockDim.x) {
+        const double key = bd[koff[q] + i];
+        ids[offsets[q] + i] = bi[koff[q] + i];
+        dist[offsets[q] + i] = __double2float_rn(l2 ? __dsqrt_rn(key) : key);
+    }
+}
+
+// first entry index at which the running count reaches each group boundary
+__global__ void k_group_bounds(const int64_t *__restrict__ off, int64_t E, int64_t G, int64_t total,
+                               int64_t *__restrict__ bounds) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g <= G; g += (int64_t)gridDim.x * blockDim.x) {
+        if (g == 0) { bounds[0] = 0; continue; }
+        if (g == G) { bounds[G] = E; continue; }
+        const int64_t target = (total / G) * g;
+        int64_t lo = 0, hi = E;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (off[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        bounds[g] = lo;
+    }
+}
+
+// ---------------------------------------------------------------- host driver
+
+__global__ void k_shift(const int64_t *in, int64_t n, int64_t sub, int64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] - sub;
+}
+
+
+template <class T>
+void exclusive_scan(const T *in, T *out, int64_t n, cudaStream_t st) {
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, in, out, n, st);
+    DBuf<uint8_t> tmp(tb ? tb : 1, st);
+    GTS_CUDA(cub::DeviceScan::ExclusiveSum(tmp.get(), tb, in, out, n, st));
+}
+
+__global__ void k_i32_to_i64(const int32_t *a, int64_t n, int64_t *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) b[n] = 0;
+}
+
+int64_t d2h_i64(const int64_t *p, cudaStream_t st) {
+    int64_t v = 0;
+    GTS_CUDA(cudaMemcpyAsync(&v, p, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    return v;
+}
+
+struct Level {
+    int64_t E = 0;
+    DBuf<int32_t> q, node;
+    DBuf<float> path;
+};
+
+struct Runner {
+    gts_index *ix;
+    const QueryBatch &qb;
+    bool knn;
+    int64_t budget;
+    cudaStream_t st;
+    Dev d;
+    int h, F, W;
+    DBuf<float> thr;
+    // kNN state
+    DBuf<int64_t> koff;
+    DBuf<double> tk_d, bd;
+    DBuf<int64_t> tk_id, bi;
+    DBuf<int32_t> tk_n, bn;
+    // range results, appended per group
+    std::vector<DBuf<uint64_t>> rkeys;
+    std::vector<DBuf<float>> rdists;
+    std::vector<int64_t> rcounts;
+    DBuf<unsigned long long> counters;   // [0] rechecks, [1] scanned rows
+    int64_t st_pivots = 0, st_frontier = 0, st_cands = 0, st_groups = 0, st_cache = 0;
+
+    Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
+        : ix(i), qb(b), knn(k), budget(bud), st(s) {}
+
+    int64_t limit_bytes(int l) const {   // Algorithm 4: size_GPU / ((h - layer + 1) * N_c), layer = l + 1
+        return budget / ((int64_t)(h - l) * F);
+    }
+
+    void pivdist(Level &L, int64_t e0, int64_t e1, int l) {
+        if (e1 <= e0) return;
+        const int64_t base = ix->tree.lvl_off[l];
+        const int64_t E = e1 - e0;
+        if (d.dim > 0) {
+            if (d.metric == GTS_L2)
+                k_pivdist_vec<true><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+                                                                              L.path.get(), l);
+            else
+                k_pivdist_vec<false><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0,
+                                                                               e1, L.path.get(), l);
+        } else {
+            const int chunk = 256;
+#define GTS_PIV(WW)                                                                                                  \
+    k_pivdist_str<WW><<<nblocks(E, chunk), 128, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, chunk, L.path.get(), \
+                                                         l)
+            if (W <= 1) GTS_PIV(1);
+            else if (W <= 2) GTS_PIV(2);
+            else if (W <= 4) GTS_PIV(4);
+            else if (W <= 8) GTS_PIV(8);
+            else GTS_PIV(16);
+#undef GTS_PIV
+        }
+        check_launch("pivot distances");
+        st_pivots += E;
+        st_frontier += E;
+        if (knn) {
+            k_tau<<<nblocks(qb.nq, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(),
+                                                                 l, qb.nq, qb.k, koff.get(), tk_d.get(), tk_id.get(),
+                                                                 tk_n.get(), thr.get());
+            check_launch("knn threshold");
+        }
+    }
+
+    // split [0, E) into groups whose cumulative counts stay near the limit
+    std::vector<int64_t> groups(const DBuf<int64_t> &off, int64_t E, int64_t total, int64_t limit_items) {
+        int64_t G = limit_items > 0 ? (total + limit_items - 1) / limit_items : 1;
+        if (G < 1) G = 1;
+        if (G > E) G = E > 0 ? E : 1;
+        std::vector<int64_t> b(G + 1);
+        if (G == 1) {
+            b[0] = 0;
+            b[1] = E;
+            return b;
+        }
+        DBuf<int64_t> db(G + 1, st);
+        k_group_bounds<<<nblocks(G + 1, kT), kT, 0, st>>>(off.get(), E, G, total, db.get());
+        GTS_CUDA(cudaMemcpyAsync(b.data(), db.get(), (G + 1) * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        std::vector<int64_t> out;
+        out.push_back(0);
+        for (int64_t g = 1; g <= G; ++g)
+            if (b[g] > out.back()) out.push_back(b[g]);
+        if (out.back() != E) out.push_back(E);
+        return out;
+    }
+
+    void process(Level &L, int64_t e0, int64_t e1, int l) {
+        if (e1 <= e0) return;
+        pivdist(L, e0, e1, l);
+        const int64_t E = e1 - e0;
+        const int64_t lvl_next = ix->tree.lvl_off[l + 1];
+        if (l < h - 1) {
+            DBuf<int32_t> cnt(E, st);
+            k_expand<0><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+                                                                   lvl_next, e0, e1, thr.get(), cnt.get(), nullptr,
+                                                                   nullptr, nullptr, nullptr, nullptr);
+            check_launch("expand count");
+            DBuf<int64_t> c64(E + 1, st), off(E + 1, st);
+            k_i32_to_i64<<<nblocks(E, kT), kT, 0, st>>>(cnt.get(), E, c64.get());
+            exclusive_scan(c64.get(), off.get(), E + 1, st);
+            const int64_t total = d2h_i64(off.get() + E, st);
+            const int64_t entry_bytes = 8 + 4 * (int64_t)h;
+            auto gb = groups(off, E, total, limit_bytes(l) / entry_bytes);
+            for (size_t g = 0; g + 1 < gb.size(); ++g) {
+                const int64_t g0 = gb[g], g1 = gb[g + 1];
+                int64_t o0 = 0, o1 = 0;
+                GTS_CUDA(cudaMemcpyAsync(&o0, off.get() + g0, 8, cudaMemcpyDeviceToHost, st));
+                GTS_CUDA(cudaMemcpyAsync(&o1, off.get() + g1, 8, cudaMemcpyDeviceToHost, st));
+                GTS_CUDA(cudaStreamSynchronize(st));
+                Level N;
+                N.E = o1 - o0;
+                if (N.E == 0) continue;
+                N.q.alloc(N.E, st);
+                N.node.alloc(N.E, st);
+                N.path.alloc(N.E * h, st);
+                DBuf<int64_t> offg(g1 - g0 + 1, st);
+                k_shift<<<nblocks(g1 - g0 + 1, kT), kT, 0, st>>>(off.get() + g0, g1 - g0 + 1, o0, offg.get());
+                k_expand<1><<<nblocks(g1 - g0, kWarpsPerBlock), kT, 0, st>>>(
+                    d, L.q.get(), L.node.get(), L.path.get(), l, lvl_next, e0 + g0, e0 + g1, thr.get(), nullptr,
+                    offg.get(), N.q.get(), N.node.get(), N.path.get(), nullptr);
+                check_launch("expand write");
+                process(N, 0, N.E, l + 1);
+            }
+        } else {
+            DBuf<uint64_t> mask(E, st);
+            k_expand<2><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+                                                                   lvl_next, e0, e1, thr.get(), nullptr, nullptr,
+                                                                   nullptr, nullptr, nullptr, mask.get());
+            DBuf<int32_t> cnt(E, st);
+            const int64_t lvl_last = ix->tree.lvl_off[h - 1];
+            k_leafscan<false><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(),
+                                                                         lvl_last, e0, e1, mask.get(), thr.get(),
+                                                                         cnt.get(), nullptr, nullptr, nullptr,
+                                                                         counters.get() + 1);
+            check_launch("leaf scan count");
+            DBuf<int64_t> c64(E + 1, st), off(E + 1, st);
+            k_i32_to_i64<<<nblocks(E, kT), kT, 0, st>>>(cnt.get(), E, c64.get());
+            exclusive_scan(c64.get(), off.get(), E + 1, st);
+            const int64_t total = d2h_i64(off.get() + E, st);
+            if (total == 0) return;
+            const int64_t cand_bytes = 4 + 4 + 4 + 1 + 8 + 16;
+            auto gb = groups(off, E, total, (budget / 2) / cand_bytes);
+            for (size_t g = 0; g + 1 < gb.size(); ++g) {
+                const int64_t g0 = gb[g], g1 = gb[g + 1];
+                int64_t o0 = 0, o1 = 0;
+                GTS_CUDA(cudaMemcpyAsync(&o0, off.get() + g0, 8, cudaMemcpyDeviceToHost, st));
+                GTS_CUDA(cudaMemcpyAsync(&o1, off.get() + g1, 8, cudaMemcpyDeviceToHost, st));
+                GTS_CUDA(cudaStreamSynchronize(st));
+                const int64_t C = o1 - o0;
+                if (C == 0) continue;
+                DBuf<int32_t> cq(C, st), crow(C, st);
+                DBuf<int64_t> offg(g1 - g0 + 1, st);
+                k_shift<<<nblocks(g1 - g0 + 1, kT), kT, 0, st>>>(off.get() + g0, g1 - g0 + 1, o0, offg.get());
+                k_leafscan<true><<<nblocks(g1 - g0, kWarpsPerBlock), kT, 0, st>>>(
+                    d, L.q.get(), L.node.get(), L.path.get(), lvl_last, e0 + g0, e0 + g1, mask.get() + g0, thr.get(),
+                    nullptr, offg.get(), cq.get(), crow.get(), nullptr);
+                check_launch("leaf scan write");
+                verify_and_collect(cq, crow, C);
+                ++st_groups;
+            }
+        }
+    }
+
+    void verify_and_collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, int64_t C) {
+        st_cands += C;
+        DBuf<float> cdist(C, st);
+        DBuf<uint8_t> keep(knn ? 0 : C, st);
+        if (d.dim > 0) {
+            if (d.metric == GTS_L2) {
+                if (knn)
+                    k_verify_vec<true, true><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
+                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+                else
+                    k_verify_vec<true, false><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
+                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+            } else {
+                if (knn)
+                    k_verify_vec<false, true><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
+                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+                else
+                    k_verify_vec<false, false><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
+                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+            }
+        } else {
+            const int chunk = 256;
+#define GTS_VER(WW)                                                                                              \
+    do {                                                                                                         \
+        if (knn)                                                                                                 \
+            k_verify_str<WW, true><<<nblocks(C, chunk), 128, 0, st>>>(d, cq.get(), crow.get(), C, chunk,         \
+                                                                      thr.get(), cdist.get(), keep.get());       \
+        else                                                                                                     \
+            k_verify_str<WW, false><<<nblocks(C, chunk), 128, 0, st>>>(d, cq.get(), crow.get(), C, chunk,        \
+                                                                       thr.get(), cdist.get(), keep.get());      \
+    } while (0)
+            if (W <= 1) GTS_VER(1);
+            else if (W <= 2) GTS_VER(2);
+            else if (W <= 4) GTS_VER(4);
+            else if (W <= 8) GTS_VER(8);
+            else GTS_VER(16);
+#undef GTS_VER
+        }
+        check_launch("verify");
+        if (knn) {
+            DBuf<double> ckey(C, st);
+            const unsigned grid = (unsigned)qb.nq;
+            if (d.metric == GTS_L2)
+                k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                                                         bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+            else if (d.metric == GTS_L1)
+                k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                                                         bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+            else
+                k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                                                           bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+            check_launch("knn merge");
+        } else {
+            DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
+            k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
+            exclusive_scan(k64.get(), pos.get(), C + 1, st);
+            const int64_t R = d2h_i64(pos.get() + C, st);
+            if (R > 0) {
+                DBuf<uint64_t> rk(R, st);
+                DBuf<float> rd(R, st);
+                k_range_pack<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C,
+                                                            pos.get(), d, rk.get(), rd.get());
+                check_launch("range pack");
+                rkeys.push_back(std::move(rk));
+                rdists.push_back(std::move(rd));
+                rcounts.push_back(R);
+            }
+        }
+    }
+
+    void cache_pass() {
+        const int64_t cn = ix->cache.count;
+        if (cn == 0) return;
+        const int64_t per_q = cn;
+        int64_t qchunk = ((budget / 2) / 40) / per_q;
+        if (qchunk < 1) qchunk = 1;
+        for (int64_t qa = 0; qa < qb.nq; qa += qchunk) {
+            const int64_t qe = qa + qchunk < qb.nq ? qa + qchunk : qb.nq;
+            const int64_t C = (qe - qa) * cn;
+            DBuf<int32_t> cq(C, st), crow(C, st);
+            k_cache_cands<<<nblocks(C, kT), kT, 0, st>>>(qa, qe, ix->tree.n, cn, cq.get(), crow.get());
+            st_cache += C;
+            verify_and_collect(cq, crow, C);
+            st_cands -= C;
+        }
+    }
+};
+
+}  // namespace
+
+void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int64_t budget, QueryOut &out,
+               int64_t *stats, cudaStream_t st) {
+    (void)precision;
+    Tree &t = ix->tree;
+    Cache &c = ix->cache;
+    const int64_t nq = qb.nq;
+    Runner R(ix, qb, knn, budget, st);
+    R.h = t.h;
+    R.F = t.F;
+    R.W = (qb.max_len + 63) / 64;
+    if (R.W < 1) R.W = 1;
+    Dev &d = R.d;
+    d.metric = t.metric;
+    d.dim = t.dim;
+    d.F = t.F;
+    d.h = t.h;
+    d.n = t.n;
+    d.X = t.X.get();
+    d.S = t.S.get();
+    d.Soff = t.Soff.get();
+    d.row_id = t.row_id.get();
+    d.table = t.table.get();
+    d.row_del = t.row_del.get();
+    d.npos = t.npos.get();
+    d.nsize = t.nsize.get();
+    d.npiv = t.npiv.get();
+    d.nlo = t.nlo.get();
+    d.nhi = t.nhi.get();
+    d.cn = c.count;
+    d.cX = c.X.get();
+    d.cS = c.S.get();
+    d.cSoff = c.Soff.get();
+    d.cid = c.id.get();
+    d.cins = c.ins.get();
+    d.cdel = c.del.get();
+    d.Q = qb.Q;
+    d.QS = qb.S;
+    d.QSoff = qb.Soff;
+    d.rel = t.dim > 0 ? fp32_rel_bound(t.dim) : 0.f;
+    d.epsc = t.dim > 0 ? 4.f * d.rel : 0.f;
+    DBuf<int64_t> qseq(nq, st);
+    if (qb.seq)
+        GTS_CUDA(cudaMemcpyAsync(qseq.get(), qb.seq, nq * 8, cudaMemcpyDeviceToDevice, st));
+    else
+        k_fill_i64<<<nblocks(nq, kT), kT, 0, st>>>(qseq.get(), nq, qb.seq_now);
+    d.qseq = qseq.get();
+    R.thr.alloc(nq, st);
+    R.counters.alloc(2, st);
+    GTS_CUDA(cudaMemsetAsync(R.counters.get(), 0, 16, st));
+    if (knn) {
+        DBuf<int64_t> k64(nq + 1, st);
+        R.koff.alloc(nq + 1, st);
+        k_k_to_i64<<<nblocks(nq, kT), kT, 0, st>>>(qb.k, nq, k64.get());
+        exclusive_scan(k64.get(), R.koff.get(), nq + 1, st);
+        const int64_t ktot = d2h_i64(R.koff.get() + nq, st);
+        R.tk_d.alloc(ktot, st);
+        R.tk_id.alloc(ktot, st);
+        R.bd.alloc(ktot, st);
+        R.bi.alloc(ktot, st);
+        R.tk_n.alloc(nq, st);
+        R.bn.alloc(nq, st);
+        GTS_CUDA(cudaMemsetAsync(R.tk_n.get(), 0, nq * 4, st));
+        GTS_CUDA(cudaMemsetAsync(R.bn.get(), 0, nq * 4, st));
+        k_fill_f32<<<nblocks(nq, kT), kT, 0, st>>>(R.thr.get(), nq, INFINITY);
+    } else {
+        k_thresholds<<<nblocks(nq, kT), kT, 0, st>>>(qb.radii, nq, t.dim == 0, R.thr.get());
+    }
+    check_launch("query setup");
+    if (t.n > 0) {
+        Level L0;
+        L0.E = nq;
+        L0.q.alloc(nq, st);
+        L0.node.alloc(nq, st);
+        L0.path.alloc(nq * t.h, st);
+        k_root_entries<<<nblocks(nq, kT), kT, 0, st>>>(L0.q.get(), L0.node.get(), nq);
+        R.process(L0, 0, nq, 0);
+    }
+    R.cache_pass();
+    // ---- assemble the CSR answer
+    out.offsets.alloc(nq + 1, st);
+    if (knn) {
+        DBuf<int64_t> counts(nq + 1, st);
+        k_knn_counts<<<nblocks(nq, kT), kT, 0, st>>>(R.bn.get(), nq, counts.get());
+        exclusive_scan(counts.get(), out.offsets.get(), nq + 1, st);
+        out.total = d2h_i64(out.offsets.get() + nq, st);
+        out.ids.alloc(out.total ? out.total : 1, st);
+        out.dist.alloc(out.total ? out.total : 1, st);
+        k_knn_emit<<<(unsigned)(nq > 0 ? nq : 1), 128, 0, st>>>(out.offsets.get(), R.koff.get(), R.bd.get(),
+                                                                R.bi.get(), R.bn.get(), nq, t.metric == GTS_L2,
+                                                                out.ids.get(), out.dist.get());
+    } else {
+        int64_t Rt = 0;
+        for (auto v : R.rcounts) Rt += v;
+        DBuf<uint64_t> keys(Rt ? Rt : 1, st), keys2(Rt ? Rt : 1, st);
+        DBuf<float> dd(Rt ? Rt : 1, st);
+        out.dist.alloc(Rt ? Rt : 1, st);
+        out.ids.alloc(Rt ? Rt : 1, st);
+        int64_t o = 0;
+        for (size_t i = 0; i < R.rkeys.size(); ++i) {
+            GTS_CUDA(cudaMemcpyAsync(keys.get() + o, R.rkeys[i].get(), R.rcounts[i] * 8, cudaMemcpyDeviceToDevice, st));
+            GTS_CUDA(cudaMemcpyAsync(dd.get() + o, R.rdists[i].get(), R.rcounts[i] * 4, cudaMemcpyDeviceToDevice, st));
+            o += R.rcounts[i];
+        }
+        R.rkeys.clear();
+        R.rdists.clear();
+        DBuf<int64_t> counts(nq + 1, st);
+        GTS_CUDA(cudaMemsetAsync(counts.get(), 0, (nq + 1) * 8, st));
+        if (Rt > 0) {
+            int qbits = 1;
+            while (((int64_t)1 << qbits) < nq) ++qbits;
+            size_t tb = 0;
+            cub::DeviceRadixSort::SortPairs(nullptr, tb, keys.get(), keys2.get(), dd.get(), out.dist.get(), Rt, 0,
+                                            32 + qbits, st);
+            DBuf<uint8_t> tmp(tb, st);
+            GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, keys.get(), keys2.get(), dd.get(), out.dist.get(),
+                                                     Rt, 0, 32 + qbits, st));
+            k_range_counts<<<nblocks(Rt, kT), kT, 0, st>>>(keys2.get(), Rt, counts.get(), out.ids.get());
+        }
+        exclusive_scan(counts.get(), out.offsets.get(), nq + 1, st);
+        out.total = Rt;
+    }
+    check_launch("assemble");
+    unsigned long long hc[2] = {0, 0};
+    GTS_CUDA(cudaMemcpyAsync(hc, R.counters.get(), 16, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        stats[GTS_STAT_PIVOT_DIST] = R.st_pivots;
+        stats[GTS_STAT_FRONTIER] = R.st_frontier;
+        stats[GTS_STAT_SCANNED_ROWS] = (int64_t)hc[1];
+        stats[GTS_STAT_CANDIDATES] = R.st_cands;
+        stats[GTS_STAT_RECHECKS] = (int64_t)hc[0];
+        stats[GTS_STAT_RESULTS] = out.total;
+        stats[GTS_STAT_GROUPS] = R.st_groups;
+        stats[GTS_STAT_CACHE_ROWS] = R.st_cache;
+    }
+}
+
+}  // namespace gts

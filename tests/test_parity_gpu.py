@@ -1,0 +1,346 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded
+inputs that span several tiles, ragged tails and the degenerate cases.
+
+Bar: edit distance bit-exact (ids and integer distances); L1 / L2 identical id
+sets (the FP64 boundary recheck decides every close call exactly as the
+oracle does) and distances within 1e-5 relative of the oracle's FP64 value.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.index import build_index
+from synth import Strings, mutate, random_strings, small_vectors, strings_from_list, words_like
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gts():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_00966_gb300 import build_ext
+    build_ext.build()
+    import paper_2404_00966_gb300 as g
+    return g
+
+
+def assert_same(res, want, metric, label=""):
+    off, ids, dist, _ = want
+    assert np.array_equal(res.offsets, off), f"{label}: per-query counts differ"
+    assert np.array_equal(res.ids, ids), f"{label}: ids differ"
+    if metric == "edit":
+        assert np.array_equal(res.dist, dist.astype(np.float32)), f"{label}: edit distances differ"
+    else:
+        assert np.allclose(res.dist, dist, rtol=RTOL, atol=1e-30), f"{label}: distances beyond 1e-5 relative"
+
+
+def vec_case(n, dim, nq, seed, kind="gauss", dup=0.0):
+    return small_vectors(n, dim, nq, seed, kind=kind, dup_frac=dup)
+
+
+def str_case(n, nq, seed, lmin=1, lmax=20, alphabet=b"abcd"):
+    rng = np.random.default_rng(seed)
+    alpha = np.frombuffer(alphabet, np.uint8)
+    S = random_strings(n, lmin, lmax, alpha, rng)
+    qs = [mutate(S.get(int(rng.integers(0, n))), int(rng.integers(0, 4)), alpha, rng) for _ in range(nq)]
+    return S, strings_from_list(qs)
+
+
+# ------------------------------------------------------------------ index build
+
+@pytest.mark.parametrize("metric,F,npiv", [("l2", 6, 0), ("l1", 5, 3), ("edit", 8, 4)])
+def test_build_matches_oracle_tree(gts, metric, F, npiv):
+    if metric == "edit":
+        objs, _ = str_case(2500, 1, seed=1)
+    else:
+        objs, _ = vec_case(3001, 24, 1, seed=2, dup=0.1)
+    ix = gts.Index.build(objs, metric, n_pivots=npiv, fanout=F, root_pivot=11)
+    T = build_index(objs, metric, F, npiv, root_pivot=11)
+    info = ix.info()
+    assert info["h"] == T["h"]
+    for l in range(T["h"] + 1):
+        g = ix.tree_level(l)
+        assert np.array_equal(g["pos"], T["pos"][l]) and np.array_equal(g["size"], T["size"][l])
+        if l >= 1:
+            assert np.array_equal(g["lo"], T["lo"][l]) and np.array_equal(g["hi"], T["hi"][l])
+        if l < T["h"]:
+            assert np.array_equal(g["pivot"], T["pivot"][l])
+    ids, tab = ix.table()
+    assert np.array_equal(ids, T["perm"])
+    assert np.array_equal(tab, T["table"])
+    ix.close()
+
+
+# ------------------------------------------------------------------ range / kNN parity
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("dup", [0.0, 0.3])
+def test_vector_range_and_knn(gts, metric, dup):
+    X, Q = vec_case(5003, 40, 97, seed=3, dup=dup)
+    Q[:5] = X[[0, 17, 17, 4000, 5002]]                      # exact copies: distance 0 and ties
+    ix = gts.Index.build(X, metric, fanout=7, root_pivot=3)
+    d = oracle.distances_to(metric, X[:400], Q[7])
+    base = float(np.median(d))
+    radii = np.concatenate([[0.0, 0.0], np.linspace(0.3, 1.2, 95) * base]).astype(np.float32)
+    assert_same(ix.range(Q, radii), oracle.range_query(metric, X, Q, radii), metric, "range")
+    for k in (1, 10, 57):
+        assert_same(ix.knn(Q, k), oracle.knn_query(metric, X, Q, k), metric, f"knn k={k}")
+    ks = np.random.default_rng(4).integers(1, 100, size=97).astype(np.int32)
+    assert_same(ix.knn(Q, ks), oracle.knn_query(metric, X, Q, ks), metric, "knn mixed k")
+    ix.close()
+
+
+def test_edit_range_and_knn(gts):
+    S, Qs = str_case(4000, 80, seed=5)
+    ix = gts.Index.build(S, "edit", n_pivots=4, fanout=8, root_pivot=1)
+    radii = np.random.default_rng(6).integers(0, 5, size=80).astype(np.float32) + 0.7
+    assert_same(ix.range(Qs, radii), oracle.range_query("edit", S, Qs, radii), "edit", "range")
+    for k in (1, 5, 40):
+        assert_same(ix.knn(Qs, k), oracle.knn_query("edit", S, Qs, k), "edit", f"knn k={k}")
+    ix.close()
+
+
+def test_edit_long_strings_multiword(gts):
+    """Lengths above 64 and 128 (several 64-bit words per bit-parallel column)."""
+    rng = np.random.default_rng(7)
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    seeds = random_strings(40, 60, 300, alpha, rng)
+    items = [mutate(seeds.get(i % 40), int(rng.integers(0, 12)), alpha, rng) for i in range(1200)]
+    S = strings_from_list(items)
+    Qs = strings_from_list([mutate(seeds.get(int(rng.integers(0, 40))), int(rng.integers(0, 8)), alpha, rng)
+                            for _ in range(30)])
+    ix = gts.Index.build(S, "edit", fanout=6, root_pivot=0)
+    radii = np.full(30, 10.0, np.float32)
+    assert_same(ix.range(Qs, radii), oracle.range_query("edit", S, Qs, radii), "edit", "long range")
+    assert_same(ix.knn(Qs, 12), oracle.knn_query("edit", S, Qs, 12), "edit", "long knn")
+    ix.close()
+
+
+def test_words_like_full_size(gts):
+    """The 10,000-string / 256-query / radius-2 workload, every query checked."""
+    wl = words_like()
+    ix = gts.Index.build(wl.objects, "edit", n_pivots=wl.n_pivots, fanout=wl.fanout, root_pivot=0)
+    assert_same(ix.range(wl.queries, wl.radii), oracle.range_query("edit", wl.objects, wl.queries, wl.radii),
+                "edit", "words")
+    ix.close()
+
+
+# ------------------------------------------------------------------ degenerate cases
+
+def test_empty_and_tiny(gts):
+    X = np.zeros((0, 8), np.float32)
+    ix = gts.Index.build(X, "l2", fanout=4)
+    Q = np.ones((3, 8), np.float32)
+    r = ix.range(Q, np.ones(3, np.float32))
+    assert list(r.offsets) == [0, 0, 0, 0]
+    r = ix.knn(Q, 2)
+    assert list(r.offsets) == [0, 0, 0, 0]
+    ix.close()
+    X1 = np.arange(8, dtype=np.float32)[None, :]
+    ix = gts.Index.build(X1, "l1", fanout=4)
+    assert_same(ix.knn(Q, 5), oracle.knn_query("l1", X1, Q, 5), "l1", "n=1")
+    r = ix.range(np.zeros((0, 8), np.float32), np.zeros(0, np.float32))
+    assert list(r.offsets) == [0]
+    ix.close()
+
+
+def test_all_identical_objects(gts):
+    X = np.tile(np.float32([[0.5, -1.0, 2.0]]), (777, 1))
+    Q = np.float32([[0.5, -1.0, 2.0], [1.5, -1.0, 2.0]])
+    ix = gts.Index.build(X, "l2", fanout=5, root_pivot=0)
+    assert_same(ix.knn(Q, 33), oracle.knn_query("l2", X, Q, 33), "l2", "identical knn")
+    assert_same(ix.range(Q, np.float32([0.0, 1.0])), oracle.range_query("l2", X, Q, np.float32([0.0, 1.0])), "l2",
+                "identical range")
+    ix.close()
+
+
+def test_empty_strings_and_short(gts):
+    items = [b"", b"a", b"b", b"ab", b"", b"abc", b"ba"] * 30
+    S = strings_from_list(items)
+    Qs = strings_from_list([b"", b"a", b"abcd"])
+    ix = gts.Index.build(S, "edit", fanout=3, root_pivot=2)
+    radii = np.float32([0, 1, 2])
+    assert_same(ix.range(Qs, radii), oracle.range_query("edit", S, Qs, radii), "edit", "short range")
+    assert_same(ix.knn(Qs, 9), oracle.knn_query("edit", S, Qs, 9), "edit", "short knn")
+    ix.close()
+
+
+def test_k_larger_than_n(gts):
+    X, Q = vec_case(300, 5, 4, seed=9)
+    ix = gts.Index.build(X, "l2", fanout=4)
+    assert_same(ix.knn(Q, 1000), oracle.knn_query("l2", X, Q, 1000), "l2", "k>n")
+    ix.close()
+
+
+def test_invalid_arguments(gts):
+    X, Q = vec_case(200, 5, 3, seed=10)
+    ix = gts.Index.build(X, "l2", fanout=4)
+    with pytest.raises(gts.GTSError) as e:
+        ix.range(Q, np.float32([1, -1, 1]))
+    assert e.value.name == "GTS_EINVAL"
+    with pytest.raises(gts.GTSError):
+        ix.range(Q, np.float32([1, np.nan, 1]))
+    with pytest.raises(gts.GTSError):
+        ix.knn(Q, 0)
+    Qbad = Q.copy()
+    Qbad[1, 2] = np.inf
+    with pytest.raises(gts.GTSError):
+        ix.knn(Qbad, 3)
+    with pytest.raises(gts.GTSError):
+        ix.knn(np.zeros((2, 6), np.float32), 3)
+    ix.close()
+
+
+# ------------------------------------------------------------------ scheduler, precision, residency
+
+def test_tiny_memory_budget_gives_same_answers(gts):
+    X, Q = vec_case(6000, 16, 150, seed=11)
+    ix = gts.Index.build(X, "l1", fanout=8)
+    radii = np.full(150, np.float32(np.median(oracle.distances_to("l1", X[:300], Q[0])) * 0.6))
+    want_r = oracle.range_query("l1", X, Q, radii)
+    want_k = oracle.knn_query("l1", X, Q, 9)
+    r = ix.range(Q, radii, memory_budget=64 << 10)
+    assert r.stats["groups"] > 1
+    assert_same(r, want_r, "l1", "budget range")
+    assert_same(ix.knn(Q, 9, memory_budget=64 << 10), want_k, "l1", "budget knn")
+    ix.close()
+
+
+def test_bf16_precision_same_answers(gts):
+    X, Q = vec_case(8000, 64, 120, seed=12)
+    ix = gts.Index.build(X, "l2", fanout=10)
+    want = oracle.knn_query("l2", X, Q, 10)
+    assert_same(ix.knn(Q, 10, precision="bf16"), want, "l2", "bf16 knn")
+    radii = np.full(120, 1.0, np.float32)
+    assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l2", X, Q, radii), "l2", "bf16 range")
+    ix.close()
+
+
+def test_device_inputs_and_results(gts):
+    import torch
+    X, Q = vec_case(4000, 32, 50, seed=13)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    ix = gts.Index.build(Xd, "l2", fanout=9)
+    k = torch.full((50,), 6, dtype=torch.int32, device="cuda")
+    res = ix.knn(Qd, k, result_on_device=True)
+    host = ix.knn(Qd, k)
+    want = oracle.knn_query("l2", X, Q, 6)
+    assert_same(host, want, "l2", "device inputs")
+    tot = int(want[0][-1])
+    t_off = torch.empty(51, dtype=torch.int64, device="cuda")
+    t_ids = torch.empty(tot, dtype=torch.int64, device="cuda")
+    t_dist = torch.empty(tot, dtype=torch.float32, device="cuda")
+    res.copy_to(t_off, t_ids, t_dist)
+    assert np.array_equal(t_off.cpu().numpy(), want[0])
+    assert np.array_equal(t_ids.cpu().numpy(), want[1])
+    res.free()
+    ix.close()
+
+
+# ------------------------------------------------------------------ updates
+
+def _replay(gts, metric, objs_init, pool, seed, cache_limit):
+    """Insert / delete / query interleaving (Section 4.4) checked against the
+    oracle over the objects visible at each query's sequence number."""
+    rng = np.random.default_rng(seed)
+    is_str = isinstance(objs_init, Strings)
+    ix = gts.Index.build(objs_init, metric, fanout=6, root_pivot=0, cache_limit=cache_limit)
+    n0 = objs_init.n if is_str else objs_init.shape[0]
+    all_items = [objs_init.get(i) for i in range(n0)] if is_str else list(objs_init)
+    ins = [-1] * n0
+    dele = [np.iinfo(np.int64).max] * n0
+    live = list(range(n0))
+    seq = ix.info()["seq"]
+    p = 0
+    for step in range(12):
+        # inserts
+        m = int(rng.integers(1, 9))
+        new = pool[p:p + m]
+        p += m
+        newobj = strings_from_list(new) if is_str else np.asarray(new, np.float32)
+        ids = ix.insert(newobj)
+        assert list(ids) == list(range(len(all_items), len(all_items) + m))
+        for j in range(m):
+            all_items.append(new[j])
+            ins.append(seq)
+            dele.append(np.iinfo(np.int64).max)
+            seq += 1
+        live += list(ids)
+        # deletes (one unknown id on purpose)
+        victims = list(rng.choice(live, size=min(len(live), int(rng.integers(1, 6))), replace=False))
+        missing = ix.delete(np.array(victims + [10 ** 7], np.int64))
+        assert missing == 1
+        for v in victims:
+            dele[v] = seq
+            seq += 1
+            live.remove(v)
+        assert ix.info()["seq"] == seq
+        # queries at the current state
+        if is_str:
+            Qs = strings_from_list([mutate(all_items[int(rng.integers(0, len(all_items)))], 1,
+                                           np.frombuffer(b"abcd", np.uint8), rng) for _ in range(7)])
+            P = strings_from_list(all_items)
+        else:
+            Qs = np.asarray([all_items[int(rng.integers(0, len(all_items)))] for _ in range(7)], np.float32) + 0.01
+            P = np.asarray(all_items, np.float32)
+        qseq = np.full(7, seq, np.int64)
+        I, Dl = np.asarray(ins, np.int64), np.asarray(dele, np.int64)
+        radii = np.full(7, 2.0 if is_str else 0.8, np.float32)
+        assert_same(ix.range(Qs, radii), oracle.range_query(metric, P, Qs, radii, I, Dl, qseq), metric,
+                    f"update range step {step}")
+        assert_same(ix.knn(Qs, 5), oracle.knn_query(metric, P, Qs, 5, I, Dl, qseq), metric, f"update knn {step}")
+    # batch update = rebuild
+    newb = pool[p:p + 40]
+    newobj = strings_from_list(newb) if is_str else np.asarray(newb, np.float32)
+    victims = list(rng.choice(live, size=10, replace=False))
+    ids = ix.batch_update(newobj, np.array(victims, np.int64))
+    for j in range(len(newb)):
+        all_items.append(newb[j])
+        ins.append(seq)
+        dele.append(np.iinfo(np.int64).max)
+        seq += 1
+    for v in victims:
+        dele[v] = seq
+        seq += 1
+    inf = ix.info()
+    assert inf["n_cache"] == 0 and inf["rebuild_seq"] == seq == inf["seq"]
+    P = strings_from_list(all_items) if is_str else np.asarray(all_items, np.float32)
+    Qs = P.take(np.arange(5)) if is_str else P[:5]
+    qseq = np.full(5, seq, np.int64)
+    I, Dl = np.asarray(ins, np.int64), np.asarray(dele, np.int64)
+    assert_same(ix.knn(Qs, 8), oracle.knn_query(metric, P, Qs, 8, I, Dl, qseq), metric, "after batch update")
+    ix.close()
+
+
+@pytest.mark.parametrize("cache_limit", [1, 7, 10000])
+def test_updates_vectors(gts, cache_limit):
+    X, _ = vec_case(1500, 6, 1, seed=14)
+    pool, _ = vec_case(400, 6, 1, seed=15)
+    _replay(gts, "l2", X, list(pool), seed=16, cache_limit=cache_limit)
+
+
+def test_updates_strings(gts):
+    S, _ = str_case(1200, 1, seed=17, lmin=2, lmax=10)
+    P, _ = str_case(400, 1, seed=18, lmin=2, lmax=10)
+    _replay(gts, "edit", S, [P.get(i) for i in range(P.n)], seed=19, cache_limit=9)
+
+
+def test_query_sequence_numbers_span_updates(gts):
+    """One batch whose queries see different states (per-query seq)."""
+    X, Q = vec_case(2000, 8, 6, seed=20)
+    ix = gts.Index.build(X, "l1", fanout=6)
+    s0 = ix.info()["seq"]
+    extra, _ = vec_case(30, 8, 1, seed=21)
+    ix.insert(extra)
+    ix.delete(np.arange(0, 200, 7))
+    s1 = ix.info()["seq"]
+    P = np.concatenate([X, extra])
+    ins = np.concatenate([np.full(2000, -1), s0 + np.arange(30)]).astype(np.int64)
+    dele = np.full(2030, np.iinfo(np.int64).max, np.int64)
+    dele[np.arange(0, 200, 7)] = s0 + 30 + np.arange(len(range(0, 200, 7)))
+    qseq = np.array([s0, s0 + 10, s0 + 30, s0 + 35, s1, s1], np.int64)
+    assert_same(ix.knn(Q, 7, seq=qseq), oracle.knn_query("l1", P, Q, 7, ins, dele, qseq), "l1", "seq knn")
+    ix.close()
