@@ -1,0 +1,334 @@
+"""Benchmark: batched exact L2 kNN over a GTS index on GB300.
+
+Workload (the headline configuration): 1,000,000 float32 vectors of dim 128
+from a mixture of 64 isotropic Gaussians (centres uniform in [-1, 1], sigma
+0.1, seed 0); 10,000 kNN queries, k = 10, from the same mixture (seed 1);
+node capacity 20, h = 4 (Algorithm 1).  One step = one gts_knn call over the
+whole 10,000-query batch: pivot distances, node pruning, the kNN threshold,
+the list-table scan, verification and selection, all on the GPU.
+
+Prints ONE JSON line (rank 0).  `value` is queries/s over all ranks with the
+index and queries resident in HBM; `e2e` is the same metric through the C
+ABI with pinned host queries and host results (copies inside the timed
+region).  The index (X 512 MB, table 16 MB) is larger than L2 (129 MB), so no
+explicit flush runs between steps.
+
+--impl reference: the CPU oracle (brute force, FP64, all host cores) on a
+bounded sample of the same queries per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/);
+# None once the kernel has changed since the counters were taken.
+TRAFFIC = {"kernel": None, "bytes_per_launch": None}
+
+
+def workload(scale: float = 1.0):
+    from synth import gaussian_mixture
+    n = int(1_000_000 * scale)
+    nq = max(64, int(10_000 * scale))
+    cache = os.path.join(os.environ.get("GTS_SYNTH_CACHE", "/tmp/gts_synth_cache"), f"gauss_{n}_{nq}.npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return z["X"], z["Q"], int(z["k"])
+    wl = gaussian_mixture(n=n, dim=128, n_centers=64, sigma=0.1, nq=nq, k=10)
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    try:
+        np.savez(cache, X=wl.objects, Q=wl.queries, k=10)
+    except OSError:
+        pass
+    return wl.objects, wl.queries, 10
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(X, Q, k, budget_s=12.0):
+    """The oracle as it stands (brute force, FP64) on a bounded sample of the
+    same queries, all host cores."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.knn_query("l2", X, Q[:8], k)
+    per_q = (time.perf_counter() - t0) / 8
+    m = int(max(8, min(Q.shape[0], budget_s / max(per_q, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.knn_query("l2", X, Q[8:8 + m] if 8 + m <= Q.shape[0] else Q[:m], k)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "queries/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{m} of the {Q.shape[0]} queries, full 1M x 128 dataset, brute-force FP64 kNN (k={k})"}
+
+
+def algorithmic_bytes(stage: str, st: dict, dim: int, h: int, C: int) -> float:
+    """Bytes the algorithm must move for one launch-set of a stage (see the
+    design notes for the per-unit figures)."""
+    if stage == "verify":
+        return C * (dim * 4 + 4 + 4 + 4)            # candidate row + (query, row) + distance out
+    if stage == "leaf_scan":
+        return st["scanned_rows"] * (h * 4 + 8) * 2 + C * 8   # count and write passes, + candidates out
+    if stage == "select":
+        return C * (4 + 4 + 8) + st["rechecks"] * dim * 4
+    if stage == "pivot_dist":
+        return st["pivot_dist"] * (dim * 4 + 12)
+    if stage == "expand":
+        return st["frontier"] * (4 * 4 + 20 * 12)
+    return 0.0
+
+
+def run_ours(args):
+    import torch
+    import paper_2404_00966_gb300 as gts
+    from paper_2404_00966_gb300 import build_ext
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_ext.build()
+    if dist:
+        dist.barrier()
+    X, Q, k = workload(args.scale)
+    nq, dim = Q.shape
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    Kd = torch.full((nq,), k, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = gts.Index.build(Xd, "l2", fanout=20, root_pivot=0)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = ix.info()
+    prec = args.precision
+    stream = torch.cuda.current_stream()
+
+    def step(timing=False):
+        r = ix.knn(Qd, Kd, precision=prec, result_on_device=True, timing=timing)
+        st = r.stats
+        r.free()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---- timed region: device-resident inputs
+    stage_ms, stage_launch = {}, {}
+    launches = 0
+    stats0 = None
+    with ClockSampler(local) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step(timing=True)
+            stats0 = stats0 or st
+            launches += st["launches"]
+            for kk, v in st["stage_ms"].items():
+                stage_ms[kk] = stage_ms.get(kk, 0.0) + v
+            for kk, v in st["stage_launches"].items():
+                stage_launch[kk] = stage_launch.get(kk, 0) + v
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * nq * args.steps / (ms / 1e3)
+    # ---- end to end: pinned host queries, host results
+    Qh = torch.from_numpy(Q).pin_memory()
+    Kh = torch.full((nq,), k, dtype=torch.int32).pin_memory()
+    ix.knn(Qh, Kh, precision=prec)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    tot_res = 0
+    for _ in range(args.steps):
+        r = ix.knn(Qh, Kh, precision=prec)
+        tot_res = int(r.offsets[-1])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * nq * args.steps / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": int(Qh.numel() * 4 + Kh.numel() * 4),
+           "d2h_bytes_per_step": int((nq + 1) * 8 + tot_res * 12)}
+    # ---- roofline of the dominant kernel (stage)
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    C = stats0["candidates"]
+    alg = algorithmic_bytes(dom, stats0, dim, info["h"], C)
+    dom_ms_per_step = stage_ms[dom] / args.steps
+    hbm, src = peaks()
+    achieved = alg / (dom_ms_per_step / 1e3) / 1e9 if dom_ms_per_step > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_source": src,
+            "traffic": TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel"] == dom else None,
+            "launches_per_step": stage_launch[dom] / args.steps,
+            "ms_per_step": round(dom_ms_per_step, 4)}
+    out = {
+        "metric": "kNN queries/s at oracle-exact results (L2, k=10)",
+        "value": round(value, 1), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f64" if prec == "bf16" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "gauss64_1Mx128_knn10", "n": int(X.shape[0]), "dim": int(dim), "nq": int(nq),
+                   "k": k, "fanout": 20, "h": info["h"], "precision": prec,
+                   "l2_flush": "inputs larger than L2 (vectors 512 MB + table 16 MB per step)",
+                   "parallelism": f"replicas{world}", "build_s": round(build_s, 3)},
+        "e2e": {kk: (round(v, 1) if isinstance(v, float) else v) for kk, v in e2e.items()},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "stage_ms_per_step": {kk: round(v / args.steps, 4) for kk, v in stage_ms.items()},
+        "counters_per_step": {kk: v for kk, v in stats0.items() if not isinstance(v, dict)},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(X, Q, k, budget_s=args.cpu_seconds)
+    ix.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    X, Q, k = workload(args.scale)
+    m = args.ref_sample
+    times = []
+    for i in range(args.warmup + args.steps):
+        sl = Q[(i * m) % Q.shape[0]:(i * m) % Q.shape[0] + m]
+        t0 = time.perf_counter()
+        oracle.knn_query("l2", X, sl, k)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = m * len(times) / tot
+    sample = f"{m} queries per step of the {Q.shape[0]}, full 1M x 128 dataset, brute-force FP64 kNN (k={k})"
+    out = {"impl": "reference", "metric": "kNN queries/s at oracle-exact results (L2, k=10)",
+           "value": round(value, 3), "unit": "queries/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / len(times), 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "gauss64_1Mx128_knn10", "n": int(X.shape[0]), "dim": 128, "nq": int(Q.shape[0]),
+                      "k": k},
+           "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": oracle.threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload (profiling only)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=32)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

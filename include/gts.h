@@ -91,7 +91,23 @@ typedef struct {
                                 sees the objects inserted before seq[i] and not deleted before seq[i].
                                 NULL = the current state.  Must not precede the last rebuild. */
     int64_t *stats;          /* optional host int64[GTS_STATS_LEN] of counters, filled on return */
+    double *stage_ms;        /* optional host double[GTS_STAGES_LEN]: device time per stage, measured with
+                                CUDA events around every kernel launch of the call (adds the events' cost) */
 } gts_query_opts;
+
+/* Stages reported in gts_query_opts.stage_ms (and their launch counts in
+ * stage_ms[GTS_STAGES_LEN/2 + stage] as a double). */
+enum {
+    GTS_STAGE_PIVOT_DIST = 0, /* query-to-pivot distances */
+    GTS_STAGE_THRESHOLD = 1,  /* kNN threshold update */
+    GTS_STAGE_EXPAND = 2,     /* node pruning and frontier compaction */
+    GTS_STAGE_LEAF_SCAN = 3,  /* list-table lower-bound scan and candidate emission */
+    GTS_STAGE_VERIFY = 4,     /* metric verification of candidates */
+    GTS_STAGE_SELECT = 5,     /* kNN selection with FP64 rechecks */
+    GTS_STAGE_OTHER = 6,      /* scans, sorts, result assembly */
+    GTS_STAGES = 7,
+    GTS_STAGES_LEN = 14
+};
 
 /* Counters written to gts_query_opts.stats. */
 enum {
@@ -103,7 +119,8 @@ enum {
     GTS_STAT_RESULTS = 5,      /* returned (query, object) pairs */
     GTS_STAT_GROUPS = 6,       /* query groups run by the two-stage scheduler */
     GTS_STAT_CACHE_ROWS = 7,   /* cache-list objects compared by brute force */
-    GTS_STATS_LEN = 8
+    GTS_STAT_LAUNCHES = 8,     /* kernels launched by the call */
+    GTS_STATS_LEN = 9
 };
 
 /* Per-query answers in CSR form: the answers of query i are

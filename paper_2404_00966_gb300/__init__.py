@@ -23,7 +23,9 @@ __all__ = ["GTSError", "Index", "lib", "EDIT", "L1", "L2", "PREC_FP32", "PREC_BF
 EDIT, L1, L2 = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
 METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
-STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows"]
+STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows",
+              "launches"]
+STAGE_NAMES = ["pivot_dist", "threshold", "expand", "leaf_scan", "verify", "select", "other"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgts.so")
@@ -49,7 +51,8 @@ class _BuildOpts(ctypes.Structure):
 
 class _QueryOpts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32), ("result_on_device", ctypes.c_int32),
-                ("memory_budget", ctypes.c_int64), ("seq", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
+                ("memory_budget", ctypes.c_int64), ("seq", ctypes.c_void_p), ("stats", ctypes.c_void_p),
+                ("stage_ms", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -220,17 +223,22 @@ class Index:
                                ctypes.byref(opts), ctypes.byref(h)))
         return cls(h, metric)
 
-    def _query(self, fn, queries, per_query, precision, result_on_device, memory_budget, seq, stream):
+    def _query(self, fn, queries, per_query, precision, result_on_device, memory_budget, seq, stream, timing=False):
         m = _Marshal(queries)
-        dev = m.obj.on_device == 1
-        stats = np.zeros(8, np.int64)
+        stats = np.zeros(len(STAT_NAMES), np.int64)
+        stage = np.zeros(2 * len(STAGE_NAMES), np.float64) if timing else None
         opts = _QueryOpts(stream=stream if stream is not None else _stream_of(m.first),
                           precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
                           result_on_device=1 if result_on_device else 0, memory_budget=int(memory_budget),
-                          seq=_ptr(seq).value if seq is not None else None, stats=_ptr(stats).value)
+                          seq=_ptr(seq).value if seq is not None else None, stats=_ptr(stats).value,
+                          stage_ms=_ptr(stage).value if timing else None)
         res = _Result()
         _check(fn(self._h, ctypes.byref(m.obj), _ptr(per_query), ctypes.byref(opts), ctypes.byref(res)))
         st = dict(zip(STAT_NAMES, stats.tolist()))
+        if timing:
+            k = len(STAGE_NAMES)
+            st["stage_ms"] = dict(zip(STAGE_NAMES, stage[:k].tolist()))
+            st["stage_launches"] = dict(zip(STAGE_NAMES, stage[k:].astype(int).tolist()))
         nq = int(res.nq)
         if res.on_device:
             return Result(res.offsets, res.ids, res.dist, st, device_result=res)
@@ -239,26 +247,27 @@ class Index:
         ids = np.ctypeslib.as_array(ctypes.cast(res.ids, ctypes.POINTER(ctypes.c_int64)), (max(tot, 1),))[:tot].copy()
         dist = np.ctypeslib.as_array(ctypes.cast(res.dist, ctypes.POINTER(ctypes.c_float)), (max(tot, 1),))[:tot].copy()
         lib().gts_result_free(ctypes.byref(res))
-        _ = dev
         return Result(offsets, ids, dist, st)
 
     def range(self, queries, radii, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
-              stream=None) -> Result:
+              stream=None, timing=False) -> Result:
         if _is_torch(radii):
             r = radii.contiguous()
         else:
             r = np.ascontiguousarray(radii, np.float32)
-        return self._query(lib().gts_range, queries, r, precision, result_on_device, memory_budget, seq, stream)
+        return self._query(lib().gts_range, queries, r, precision, result_on_device, memory_budget, seq, stream,
+                           timing)
 
     def knn(self, queries, k, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
-            stream=None) -> Result:
+            stream=None, timing=False) -> Result:
         if _is_torch(k):
             kk = k.contiguous()
         else:
             n = queries.shape[0] if hasattr(queries, "shape") else (
                 queries.n if hasattr(queries, "n") else int(queries[1].shape[0]) - 1)
             kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
-        return self._query(lib().gts_knn, queries, kk, precision, result_on_device, memory_budget, seq, stream)
+        return self._query(lib().gts_knn, queries, kk, precision, result_on_device, memory_budget, seq, stream,
+                           timing)
 
     def insert(self, objects) -> np.ndarray:
         m = _Marshal(objects)

@@ -451,7 +451,8 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
         }
         const int64_t budget = opts && opts->memory_budget > 0 ? opts->memory_budget : ((int64_t)8 << 30);
         QueryOut qo;
-        run_query(ix, qb, knn, opts ? opts->precision : 0, budget, qo, opts ? opts->stats : nullptr, st);
+        run_query(ix, qb, knn, opts ? opts->precision : 0, budget, qo, opts ? opts->stats : nullptr,
+                  opts ? opts->stage_ms : nullptr, st);
         fill_result(out, nq, qo, opts && opts->result_on_device, st);
     });
 }

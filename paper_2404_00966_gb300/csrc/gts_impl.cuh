@@ -154,6 +154,10 @@ struct gts_index {
     int64_t cache_limit = 4096;
     uint64_t seed = 0;
     int64_t rebuilds = 0;
+    std::vector<cudaEvent_t> events;   // reused by per-stage timing
+    ~gts_index() {
+        for (auto e : events) cudaEventDestroy(e);
+    }
 };
 
 namespace gts {
@@ -186,6 +190,6 @@ struct QueryOut {
 };
 
 void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int64_t budget,
-               QueryOut &out, int64_t *stats, cudaStream_t st);
+               QueryOut &out, int64_t *stats, double *stage_ms, cudaStream_t st);
 
 }  // namespace gts

@@ -235,19 +235,36 @@ __device__ __forceinline__ bool interval_hit(float dq, float thr, float lo, floa
     return (dq - thr <= hi + eps) && (dq + thr + eps >= lo);
 }
 
-// MODE 0: count surviving children per entry; 1: write them as the next
-// level's entries; 2: last pivot level, write the surviving-leaf bit mask.
+// MODE 0: test the children of every entry, write the survivor bit mask and
+// its population count; 1: write the survivors named by the mask as the next
+// level's entries (the mask fixes the count, whatever the threshold has
+// become since: kNN thresholds only shrink while earlier groups run); 2: last
+// pivot level, write the surviving-leaf mask only.
 template <int MODE>
 __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                          const float *__restrict__ path, int l, int64_t lvl_next, int64_t e0, int64_t e1,
                          const float *__restrict__ thr_q, int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
                          int32_t *__restrict__ nq_out, int32_t *__restrict__ nnode_out, float *__restrict__ npath_out,
-                         uint64_t *__restrict__ mask_out) {
+                         uint64_t *__restrict__ mask_io) {
     const int lane = threadIdx.x & 31;
     const int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (e >= e1) return;
     const int32_t q = eq[e];
     const int32_t node = enode[e];
+    if (MODE == 1) {
+        const uint64_t m = mask_io[e - e0];
+        const int64_t base = off[e - e0];
+        for (int j0 = 0; j0 < d.F; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < d.F && ((m >> j) & 1ull)) {
+                const int64_t o = base + __popcll(m & ((1ull << j) - 1ull));
+                nq_out[o] = q;
+                nnode_out[o] = node * d.F + j;
+                for (int t = 0; t <= l; ++t) npath_out[o * d.h + t] = path[e * d.h + t];
+            }
+        }
+        return;
+    }
     const float dq = path[e * d.h + l];
     const float thr = thr_q[q];
     uint64_t m = 0;
@@ -260,21 +277,9 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
         }
         m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
     }
-    if (MODE == 0) {
-        if (lane == 0) cnt[e - e0] = __popcll(m);
-    } else if (MODE == 2) {
-        if (lane == 0) mask_out[e - e0] = m;
-    } else {
-        const int64_t base = off[e - e0];
-        for (int j0 = 0; j0 < d.F; j0 += 32) {
-            const int j = j0 + lane;
-            if (j < d.F && ((m >> j) & 1ull)) {
-                const int64_t o = base + __popcll(m & ((1ull << j) - 1ull));
-                nq_out[o] = q;
-                nnode_out[o] = node * d.F + j;
-                for (int t = 0; t <= l; ++t) npath_out[o * d.h + t] = path[e * d.h + t];
-            }
-        }
+    if (lane == 0) {
+        mask_io[e - e0] = m;
+        if (MODE == 0) cnt[e - e0] = __popcll(m);
     }
 }
 
@@ -309,6 +314,9 @@ __global__ void k_leafscan(Dev d, const int32_t *__restrict__ eq, const int32_t 
     for (int t = 0; t < kMaxHeight; ++t) dq[t] = t < d.h ? path[e * d.h + t] : 0.f;
     int64_t count = 0, tested = 0;
     const int64_t base = WRITE ? off[e - e0] : 0;
+    // the write pass re-tests with the same thresholds as the count pass; the
+    // bound keeps every write inside this entry's slot regardless
+    const int64_t lim = WRITE ? off[e - e0 + 1] : 0;
     for (int32_t r0 = 0; r0 < size; r0 += 32) {
         const int32_t r = r0 + lane;
         bool pass = false, test = false;
@@ -334,8 +342,10 @@ __global__ void k_leafscan(Dev d, const int32_t *__restrict__ eq, const int32_t 
         const unsigned b = __ballot_sync(0xffffffffu, pass);
         if (WRITE && pass) {
             const int64_t o = base + count + __popc(b & ((1u << lane) - 1u));
-            cq[o] = q;
-            crow[o] = pos + r;
+            if (o < lim) {
+                cq[o] = q;
+                crow[o] = pos + r;
+            }
         }
         count += __popc(b);
         tested += __popc(__ballot_sync(0xffffffffu, test));
@@ -735,6 +745,58 @@ struct Level {
     DBuf<float> path;
 };
 
+// Per-stage device time: CUDA events recorded on the query stream around
+// every launch of a stage (only when the caller asks for stage times).  The
+// events come from a pool owned by the index, so timing costs one record each.
+struct StageClock {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> *pool = nullptr;
+    size_t used = 0;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    int64_t launches[GTS_STAGES] = {0};
+    int cur = -1;
+    cudaEvent_t cur_a = nullptr;
+    cudaEvent_t take() {
+        if (used == pool->size()) {
+            cudaEvent_t e;
+            GTS_CUDA(cudaEventCreate(&e));
+            pool->push_back(e);
+        }
+        return (*pool)[used++];
+    }
+    void begin(int stage, int nlaunch = 1) {
+        launches[stage] += nlaunch;
+        if (!on) return;
+        cur = stage;
+        cur_a = take();
+        GTS_CUDA(cudaEventRecord(cur_a, st));
+    }
+    void end() {
+        if (!on) return;
+        cudaEvent_t b = take();
+        GTS_CUDA(cudaEventRecord(b, st));
+        recs.push_back({cur, cur_a, b});
+    }
+    void collect(double *out) {
+        for (int i = 0; i < GTS_STAGES_LEN; ++i) out[i] = 0.0;
+        for (auto &r : recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) out[r.stage] += ms;
+        }
+        for (int s = 0; s < GTS_STAGES; ++s) out[GTS_STAGES + s] = (double)launches[s];
+    }
+    int64_t total_launches() const {
+        int64_t t = 0;
+        for (int s = 0; s < GTS_STAGES; ++s) t += launches[s];
+        return t;
+    }
+};
+
 struct Runner {
     gts_index *ix;
     const QueryBatch &qb;
@@ -755,18 +817,32 @@ struct Runner {
     std::vector<int64_t> rcounts;
     DBuf<unsigned long long> counters;   // [0] rechecks, [1] scanned rows
     int64_t st_pivots = 0, st_frontier = 0, st_cands = 0, st_groups = 0, st_cache = 0;
+    StageClock clk;
 
     Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
-        : ix(i), qb(b), knn(k), budget(bud), st(s) {}
+        : ix(i), qb(b), knn(k), budget(bud), st(s) {
+        clk.st = s;
+        clk.pool = &i->events;
+    }
 
     int64_t limit_bytes(int l) const {   // Algorithm 4: size_GPU / ((h - layer + 1) * N_c), layer = l + 1
         return budget / ((int64_t)(h - l) * F);
+    }
+
+    void scan_i32(const DBuf<int32_t> &cnt, int64_t E, DBuf<int64_t> &off) {
+        DBuf<int64_t> c64(E + 1, st);
+        off.alloc(E + 1, st);
+        clk.begin(GTS_STAGE_OTHER, 2);
+        k_i32_to_i64<<<nblocks(E, kT), kT, 0, st>>>(cnt.get(), E, c64.get());
+        exclusive_scan(c64.get(), off.get(), E + 1, st);
+        clk.end();
     }
 
     void pivdist(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
         const int64_t base = ix->tree.lvl_off[l];
         const int64_t E = e1 - e0;
+        clk.begin(GTS_STAGE_PIVOT_DIST);
         if (d.dim > 0) {
             if (d.metric == GTS_L2)
                 k_pivdist_vec<true><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
@@ -786,20 +862,23 @@ struct Runner {
             else GTS_PIV(16);
 #undef GTS_PIV
         }
+        clk.end();
         check_launch("pivot distances");
         st_pivots += E;
         st_frontier += E;
         if (knn) {
+            clk.begin(GTS_STAGE_THRESHOLD);
             k_tau<<<nblocks(qb.nq, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(),
                                                                  l, qb.nq, qb.k, koff.get(), tk_d.get(), tk_id.get(),
                                                                  tk_n.get(), thr.get());
+            clk.end();
             check_launch("knn threshold");
         }
     }
 
     // split [0, E) into groups whose cumulative counts stay near the limit
     std::vector<int64_t> groups(const DBuf<int64_t> &off, int64_t E, int64_t total, int64_t limit_items) {
-        int64_t G = limit_items > 0 ? (total + limit_items - 1) / limit_items : 1;
+        int64_t G = limit_items > 0 ? (total + limit_items - 1) / limit_items : total;
         if (G < 1) G = 1;
         if (G > E) G = E > 0 ? E : 1;
         std::vector<int64_t> b(G + 1);
@@ -809,7 +888,9 @@ struct Runner {
             return b;
         }
         DBuf<int64_t> db(G + 1, st);
+        clk.begin(GTS_STAGE_OTHER);
         k_group_bounds<<<nblocks(G + 1, kT), kT, 0, st>>>(off.get(), E, G, total, db.get());
+        clk.end();
         GTS_CUDA(cudaMemcpyAsync(b.data(), db.get(), (G + 1) * 8, cudaMemcpyDeviceToHost, st));
         GTS_CUDA(cudaStreamSynchronize(st));
         std::vector<int64_t> out;
@@ -820,6 +901,17 @@ struct Runner {
         return out;
     }
 
+    void group_range(const DBuf<int64_t> &off, int64_t g0, int64_t g1, int64_t &o0, int64_t &o1,
+                     DBuf<int64_t> &offg) {
+        GTS_CUDA(cudaMemcpyAsync(&o0, off.get() + g0, 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(&o1, off.get() + g1, 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        offg.alloc(g1 - g0 + 1, st);
+        clk.begin(GTS_STAGE_OTHER);
+        k_shift<<<nblocks(g1 - g0 + 1, kT), kT, 0, st>>>(off.get() + g0, g1 - g0 + 1, o0, offg.get());
+        clk.end();
+    }
+
     void process(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
         pivdist(L, e0, e1, l);
@@ -827,51 +919,56 @@ struct Runner {
         const int64_t lvl_next = ix->tree.lvl_off[l + 1];
         if (l < h - 1) {
             DBuf<int32_t> cnt(E, st);
+            DBuf<uint64_t> cmask(E, st);
+            clk.begin(GTS_STAGE_EXPAND);
             k_expand<0><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), cnt.get(), nullptr,
-                                                                   nullptr, nullptr, nullptr, nullptr);
+                                                                   nullptr, nullptr, nullptr, cmask.get());
+            clk.end();
             check_launch("expand count");
-            DBuf<int64_t> c64(E + 1, st), off(E + 1, st);
-            k_i32_to_i64<<<nblocks(E, kT), kT, 0, st>>>(cnt.get(), E, c64.get());
-            exclusive_scan(c64.get(), off.get(), E + 1, st);
+            DBuf<int64_t> off;
+            scan_i32(cnt, E, off);
             const int64_t total = d2h_i64(off.get() + E, st);
             const int64_t entry_bytes = 8 + 4 * (int64_t)h;
             auto gb = groups(off, E, total, limit_bytes(l) / entry_bytes);
+            if (gb.size() > 2) st_groups += (int64_t)gb.size() - 1;
             for (size_t g = 0; g + 1 < gb.size(); ++g) {
                 const int64_t g0 = gb[g], g1 = gb[g + 1];
                 int64_t o0 = 0, o1 = 0;
-                GTS_CUDA(cudaMemcpyAsync(&o0, off.get() + g0, 8, cudaMemcpyDeviceToHost, st));
-                GTS_CUDA(cudaMemcpyAsync(&o1, off.get() + g1, 8, cudaMemcpyDeviceToHost, st));
-                GTS_CUDA(cudaStreamSynchronize(st));
+                DBuf<int64_t> offg;
+                group_range(off, g0, g1, o0, o1, offg);
                 Level N;
                 N.E = o1 - o0;
                 if (N.E == 0) continue;
                 N.q.alloc(N.E, st);
                 N.node.alloc(N.E, st);
                 N.path.alloc(N.E * h, st);
-                DBuf<int64_t> offg(g1 - g0 + 1, st);
-                k_shift<<<nblocks(g1 - g0 + 1, kT), kT, 0, st>>>(off.get() + g0, g1 - g0 + 1, o0, offg.get());
+                clk.begin(GTS_STAGE_EXPAND);
                 k_expand<1><<<nblocks(g1 - g0, kWarpsPerBlock), kT, 0, st>>>(
                     d, L.q.get(), L.node.get(), L.path.get(), l, lvl_next, e0 + g0, e0 + g1, thr.get(), nullptr,
-                    offg.get(), N.q.get(), N.node.get(), N.path.get(), nullptr);
+                    offg.get(), N.q.get(), N.node.get(), N.path.get(), cmask.get() + g0);
+                clk.end();
                 check_launch("expand write");
                 process(N, 0, N.E, l + 1);
             }
         } else {
             DBuf<uint64_t> mask(E, st);
+            clk.begin(GTS_STAGE_EXPAND);
             k_expand<2><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), nullptr, nullptr,
                                                                    nullptr, nullptr, nullptr, mask.get());
+            clk.end();
             DBuf<int32_t> cnt(E, st);
             const int64_t lvl_last = ix->tree.lvl_off[h - 1];
+            clk.begin(GTS_STAGE_LEAF_SCAN);
             k_leafscan<false><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(),
                                                                          lvl_last, e0, e1, mask.get(), thr.get(),
                                                                          cnt.get(), nullptr, nullptr, nullptr,
                                                                          counters.get() + 1);
+            clk.end();
             check_launch("leaf scan count");
-            DBuf<int64_t> c64(E + 1, st), off(E + 1, st);
-            k_i32_to_i64<<<nblocks(E, kT), kT, 0, st>>>(cnt.get(), E, c64.get());
-            exclusive_scan(c64.get(), off.get(), E + 1, st);
+            DBuf<int64_t> off;
+            scan_i32(cnt, E, off);
             const int64_t total = d2h_i64(off.get() + E, st);
             if (total == 0) return;
             const int64_t cand_bytes = 4 + 4 + 4 + 1 + 8 + 16;
@@ -879,17 +976,16 @@ struct Runner {
             for (size_t g = 0; g + 1 < gb.size(); ++g) {
                 const int64_t g0 = gb[g], g1 = gb[g + 1];
                 int64_t o0 = 0, o1 = 0;
-                GTS_CUDA(cudaMemcpyAsync(&o0, off.get() + g0, 8, cudaMemcpyDeviceToHost, st));
-                GTS_CUDA(cudaMemcpyAsync(&o1, off.get() + g1, 8, cudaMemcpyDeviceToHost, st));
-                GTS_CUDA(cudaStreamSynchronize(st));
+                DBuf<int64_t> offg;
+                group_range(off, g0, g1, o0, o1, offg);
                 const int64_t C = o1 - o0;
                 if (C == 0) continue;
                 DBuf<int32_t> cq(C, st), crow(C, st);
-                DBuf<int64_t> offg(g1 - g0 + 1, st);
-                k_shift<<<nblocks(g1 - g0 + 1, kT), kT, 0, st>>>(off.get() + g0, g1 - g0 + 1, o0, offg.get());
+                clk.begin(GTS_STAGE_LEAF_SCAN);
                 k_leafscan<true><<<nblocks(g1 - g0, kWarpsPerBlock), kT, 0, st>>>(
                     d, L.q.get(), L.node.get(), L.path.get(), lvl_last, e0 + g0, e0 + g1, mask.get() + g0, thr.get(),
                     nullptr, offg.get(), cq.get(), crow.get(), nullptr);
+                clk.end();
                 check_launch("leaf scan write");
                 verify_and_collect(cq, crow, C);
                 ++st_groups;
@@ -901,6 +997,7 @@ struct Runner {
         st_cands += C;
         DBuf<float> cdist(C, st);
         DBuf<uint8_t> keep(knn ? 0 : C, st);
+        clk.begin(GTS_STAGE_VERIFY);
         if (d.dim > 0) {
             if (d.metric == GTS_L2) {
                 if (knn)
@@ -935,10 +1032,12 @@ struct Runner {
             else GTS_VER(16);
 #undef GTS_VER
         }
+        clk.end();
         check_launch("verify");
         if (knn) {
             DBuf<double> ckey(C, st);
             const unsigned grid = (unsigned)qb.nq;
+            clk.begin(GTS_STAGE_SELECT);
             if (d.metric == GTS_L2)
                 k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
                                                          bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
@@ -948,17 +1047,22 @@ struct Runner {
             else
                 k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
                                                            bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+            clk.end();
             check_launch("knn merge");
         } else {
             DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
+            clk.begin(GTS_STAGE_OTHER, 2);
             k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
             exclusive_scan(k64.get(), pos.get(), C + 1, st);
+            clk.end();
             const int64_t R = d2h_i64(pos.get() + C, st);
             if (R > 0) {
                 DBuf<uint64_t> rk(R, st);
                 DBuf<float> rd(R, st);
+                clk.begin(GTS_STAGE_OTHER);
                 k_range_pack<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C,
                                                             pos.get(), d, rk.get(), rd.get());
+                clk.end();
                 check_launch("range pack");
                 rkeys.push_back(std::move(rk));
                 rdists.push_back(std::move(rd));
@@ -970,14 +1074,15 @@ struct Runner {
     void cache_pass() {
         const int64_t cn = ix->cache.count;
         if (cn == 0) return;
-        const int64_t per_q = cn;
-        int64_t qchunk = ((budget / 2) / 40) / per_q;
+        int64_t qchunk = ((budget / 2) / 40) / cn;
         if (qchunk < 1) qchunk = 1;
         for (int64_t qa = 0; qa < qb.nq; qa += qchunk) {
             const int64_t qe = qa + qchunk < qb.nq ? qa + qchunk : qb.nq;
             const int64_t C = (qe - qa) * cn;
             DBuf<int32_t> cq(C, st), crow(C, st);
+            clk.begin(GTS_STAGE_OTHER);
             k_cache_cands<<<nblocks(C, kT), kT, 0, st>>>(qa, qe, ix->tree.n, cn, cq.get(), crow.get());
+            clk.end();
             st_cache += C;
             verify_and_collect(cq, crow, C);
             st_cands -= C;
@@ -988,12 +1093,13 @@ struct Runner {
 }  // namespace
 
 void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int64_t budget, QueryOut &out,
-               int64_t *stats, cudaStream_t st) {
+               int64_t *stats, double *stage_ms, cudaStream_t st) {
     (void)precision;
     Tree &t = ix->tree;
     Cache &c = ix->cache;
     const int64_t nq = qb.nq;
     Runner R(ix, qb, knn, budget, st);
+    R.clk.on = stage_ms != nullptr;
     R.h = t.h;
     R.F = t.F;
     R.W = (qb.max_len + 63) / 64;
@@ -1028,10 +1134,12 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     d.rel = t.dim > 0 ? fp32_rel_bound(t.dim) : 0.f;
     d.epsc = t.dim > 0 ? 4.f * d.rel : 0.f;
     DBuf<int64_t> qseq(nq, st);
+    R.clk.begin(GTS_STAGE_OTHER);
     if (qb.seq)
         GTS_CUDA(cudaMemcpyAsync(qseq.get(), qb.seq, nq * 8, cudaMemcpyDeviceToDevice, st));
     else
         k_fill_i64<<<nblocks(nq, kT), kT, 0, st>>>(qseq.get(), nq, qb.seq_now);
+    R.clk.end();
     d.qseq = qseq.get();
     R.thr.alloc(nq, st);
     R.counters.alloc(2, st);
@@ -1039,8 +1147,10 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     if (knn) {
         DBuf<int64_t> k64(nq + 1, st);
         R.koff.alloc(nq + 1, st);
+        R.clk.begin(GTS_STAGE_OTHER, 2);
         k_k_to_i64<<<nblocks(nq, kT), kT, 0, st>>>(qb.k, nq, k64.get());
         exclusive_scan(k64.get(), R.koff.get(), nq + 1, st);
+        R.clk.end();
         const int64_t ktot = d2h_i64(R.koff.get() + nq, st);
         R.tk_d.alloc(ktot, st);
         R.tk_id.alloc(ktot, st);
@@ -1050,33 +1160,43 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.bn.alloc(nq, st);
         GTS_CUDA(cudaMemsetAsync(R.tk_n.get(), 0, nq * 4, st));
         GTS_CUDA(cudaMemsetAsync(R.bn.get(), 0, nq * 4, st));
+        R.clk.begin(GTS_STAGE_OTHER);
         k_fill_f32<<<nblocks(nq, kT), kT, 0, st>>>(R.thr.get(), nq, INFINITY);
+        R.clk.end();
     } else {
+        R.clk.begin(GTS_STAGE_OTHER);
         k_thresholds<<<nblocks(nq, kT), kT, 0, st>>>(qb.radii, nq, t.dim == 0, R.thr.get());
+        R.clk.end();
     }
     check_launch("query setup");
-    if (t.n > 0) {
+    if (t.n > 0 && nq > 0) {
         Level L0;
         L0.E = nq;
         L0.q.alloc(nq, st);
         L0.node.alloc(nq, st);
         L0.path.alloc(nq * t.h, st);
+        R.clk.begin(GTS_STAGE_OTHER);
         k_root_entries<<<nblocks(nq, kT), kT, 0, st>>>(L0.q.get(), L0.node.get(), nq);
+        R.clk.end();
         R.process(L0, 0, nq, 0);
     }
-    R.cache_pass();
+    if (nq > 0) R.cache_pass();
     // ---- assemble the CSR answer
     out.offsets.alloc(nq + 1, st);
     if (knn) {
         DBuf<int64_t> counts(nq + 1, st);
+        R.clk.begin(GTS_STAGE_OTHER, 2);
         k_knn_counts<<<nblocks(nq, kT), kT, 0, st>>>(R.bn.get(), nq, counts.get());
         exclusive_scan(counts.get(), out.offsets.get(), nq + 1, st);
+        R.clk.end();
         out.total = d2h_i64(out.offsets.get() + nq, st);
         out.ids.alloc(out.total ? out.total : 1, st);
         out.dist.alloc(out.total ? out.total : 1, st);
+        R.clk.begin(GTS_STAGE_OTHER);
         k_knn_emit<<<(unsigned)(nq > 0 ? nq : 1), 128, 0, st>>>(out.offsets.get(), R.koff.get(), R.bd.get(),
                                                                 R.bi.get(), R.bn.get(), nq, t.metric == GTS_L2,
                                                                 out.ids.get(), out.dist.get());
+        R.clk.end();
     } else {
         int64_t Rt = 0;
         for (auto v : R.rcounts) Rt += v;
@@ -1101,17 +1221,22 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
             cub::DeviceRadixSort::SortPairs(nullptr, tb, keys.get(), keys2.get(), dd.get(), out.dist.get(), Rt, 0,
                                             32 + qbits, st);
             DBuf<uint8_t> tmp(tb, st);
+            R.clk.begin(GTS_STAGE_OTHER, 2);
             GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, keys.get(), keys2.get(), dd.get(), out.dist.get(),
                                                      Rt, 0, 32 + qbits, st));
             k_range_counts<<<nblocks(Rt, kT), kT, 0, st>>>(keys2.get(), Rt, counts.get(), out.ids.get());
+            R.clk.end();
         }
+        R.clk.begin(GTS_STAGE_OTHER);
         exclusive_scan(counts.get(), out.offsets.get(), nq + 1, st);
+        R.clk.end();
         out.total = Rt;
     }
     check_launch("assemble");
     unsigned long long hc[2] = {0, 0};
     GTS_CUDA(cudaMemcpyAsync(hc, R.counters.get(), 16, cudaMemcpyDeviceToHost, st));
     GTS_CUDA(cudaStreamSynchronize(st));
+    if (stage_ms) R.clk.collect(stage_ms);
     if (stats) {
         stats[GTS_STAT_PIVOT_DIST] = R.st_pivots;
         stats[GTS_STAT_FRONTIER] = R.st_frontier;
@@ -1121,6 +1246,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_RESULTS] = out.total;
         stats[GTS_STAT_GROUPS] = R.st_groups;
         stats[GTS_STAT_CACHE_ROWS] = R.st_cache;
+        stats[GTS_STAT_LAUNCHES] = R.clk.total_launches();
     }
 }
 
