@@ -34,7 +34,7 @@ uint64_t splitmix64(uint64_t x) {
 }
 
 int tree_height(int64_t n, int F, int n_pivots) {
-    if (n_pivots > 0) return n_pivots;
+    if (n_pivots > 0) return n_pivots < kMaxHeight ? n_pivots : kMaxHeight;
     // ceil(log_F(n + 1)) - 1 (Algorithm 1), in integers; at least one pivot level
     int t = 0;
     long double p = 1;
@@ -42,7 +42,9 @@ int tree_height(int64_t n, int F, int n_pivots) {
         p *= F;
         ++t;
     }
-    return t - 1 < 1 ? 1 : t - 1;
+    // at least one pivot level; at most kMaxHeight (small fanouts over large sets)
+    const int h = t - 1 < 1 ? 1 : t - 1;
+    return h < kMaxHeight ? h : kMaxHeight;
 }
 
 size_t Tree::device_bytes() const {

@@ -228,6 +228,93 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
     }
 }
 
+// Insert (u, id) into the ascending list D/I of n (<= K) distinct ids if it
+// belongs among the K smallest (u, id).  One thread.
+__device__ __forceinline__ void tau_insert(double *D, int64_t *I, int &n, int K, double u, int64_t id) {
+    for (int i = 0; i < n; ++i)
+        if (I[i] == id) return;
+    if (n >= K && !(u < D[K - 1] || (u == D[K - 1] && id < I[K - 1]))) return;
+    int p = n < K ? n : K - 1;
+    while (p > 0 && (D[p - 1] > u || (D[p - 1] == u && I[p - 1] > id))) {
+        D[p] = D[p - 1];
+        I[p] = I[p - 1];
+        --p;
+    }
+    D[p] = u;
+    I[p] = id;
+    if (n < K) ++n;
+}
+
+struct LevelOffsets {
+    int64_t v[kMaxHeight + 2];
+};
+
+// Probe for kNN (warp per query).  Section 3 notes that MkNNQ(q, k) is
+// MRQ(q, d_k) once d_k is known; the probe bounds d_k from above before the
+// batched descent: it follows one root-to-last-level path, at each level
+// taking the child whose interval [lo, hi] lies nearest to d(q, pivot) (the
+// smallest Lemma-1 lower bound), and computes the exact distances to the
+// pivots on the way and to up to `cap` rows of the last-level node reached.
+// Every visible object so evaluated enters the query's threshold list, so
+// tau_q starts at (an upper bound of) the k-th of them instead of +inf.
+template <bool L2>
+__global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, const int32_t *__restrict__ kq,
+                            const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id, int32_t *tk_n,
+                            float *tau) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    const int K = kq[q];
+    double *D = tk_d + koff[q];
+    int64_t *I = tk_id + koff[q];
+    int n = tk_n[q];
+    const int64_t s = d.qseq[q];
+    const float *qv = d.Q + q * d.dim;
+    const double up = 1.0 + 2.0 * (double)d.rel;
+    int64_t node = 0;
+    int last = d.h - 1;
+    for (int l = 0; l < d.h; ++l) {
+        const int64_t g = lo_off.v[l] + node;
+        const int32_t prow = d.npiv[g];
+        const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
+        const float dq = L2 ? sqrtf(sq) : sq;
+        if (lane == 0 && d.row_del[prow] > s) tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
+        if (l == d.h - 1) break;
+        // child with the smallest interval lower bound (ties: smallest index)
+        unsigned long long best = ~0ull;
+        for (int j = lane; j < d.F; j += 32) {
+            const int64_t c = lo_off.v[l + 1] + node * d.F + j;
+            if (d.nsize[c] > 0) {
+                const float lb = fmaxf(fmaxf(d.nlo[c] - dq, dq - d.nhi[c]), 0.f);
+                const unsigned long long key = ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)j;
+                best = key < best ? key : best;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (best == ~0ull) {   // no non-empty child (cannot happen for a non-empty node)
+            last = l;
+            break;
+        }
+        node = node * d.F + (int64_t)(best & 0xffffffffull);
+    }
+    const int64_t g = lo_off.v[last] + node;
+    const int32_t pos = d.npos[g];
+    const int32_t m = d.nsize[g] < cap ? d.nsize[g] : cap;
+    for (int32_t r = 0; r < m; ++r) {
+        const int64_t row = pos + r;
+        const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
+        const float dv = L2 ? sqrtf(sq) : sq;
+        if (lane == 0 && d.row_del[row] > s) tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
+    }
+    if (lane == 0) {
+        tk_n[q] = n;
+        tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+    }
+}
+
 // ---------------------------------------------------------------- expansion
 
 __device__ __forceinline__ bool interval_hit(float dq, float thr, float lo, float hi, float epsc) {
@@ -368,48 +455,101 @@ __global__ void k_cache_cands(int64_t qa, int64_t qb, int64_t n, int64_t cn, int
 
 // ---------------------------------------------------------------- verification
 
-// Warp per candidate.  Range: accept when the FP32 upper bound is below r,
-// reject when the lower bound is above r, otherwise decide in FP64 exactly as
-// the CPU reference does.  kNN: store the FP32 distance (+inf if invisible).
-template <bool L2, bool KNN>
+// A warp takes kVerifyGroup consecutive candidates (query-major, so they
+// mostly share a query, which then stays in registers).  Range: accept when
+// the FP32 upper bound is below r, reject when the lower bound is above r,
+// otherwise decide in FP64 exactly as the CPU reference does.  kNN: keep the
+// candidate if its lower bound is within the query's threshold tau_q (an
+// upper bound of the k-th distance; a farther candidate cannot be in the top
+// k) and store its FP32 distance.
+constexpr int kVerifyGroup = 8;
+
+template <bool L2, int NV>
+__device__ __forceinline__ float row_dist_regs(const float4 (&qr)[NV > 0 ? NV : 1], const float *xv, const float *qv,
+                                               int dim, int lane) {
+    if (NV > 0) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(xv);
+        float s = 0.f;
+#pragma unroll
+        for (int v = 0; v < (NV > 0 ? NV : 1); ++v) {
+            const float4 b = __ldg(x4 + v * 32 + lane);
+            const float4 a = qr[v];
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            if (L2) s += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            else s += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        return s;
+    }
+    return warp_vec_dist<L2>(qv, xv, dim, lane);
+}
+
+template <bool L2, bool KNN, int NV>
 __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
                              const float *__restrict__ thr_q, float *__restrict__ cdist, uint8_t *__restrict__ keep,
                              unsigned long long *__restrict__ rechecks) {
     const int lane = threadIdx.x & 31;
-    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (c >= C) return;
-    const int32_t q = cq[c];
-    const int64_t row = crow[c];
-    if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
-        if (lane == 0) {
-            cdist[c] = __int_as_float(0x7f800000);
-            if (!KNN) keep[c] = 0;
+    const int64_t c0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kVerifyGroup;
+    if (c0 >= C) return;
+    const int64_t c1 = c0 + kVerifyGroup < C ? c0 + kVerifyGroup : C;
+    int32_t cur = -1;
+    float4 qr[NV > 0 ? NV : 1];
+    const float *qv = nullptr;
+    for (int64_t c = c0; c < c1; ++c) {
+        const int32_t q = cq[c];
+        const int64_t row = crow[c];
+        if (q != cur) {
+            cur = q;
+            qv = d.Q + (int64_t)q * d.dim;
+            if (NV > 0) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+#pragma unroll
+                for (int v = 0; v < (NV > 0 ? NV : 1); ++v) qr[v] = q4[v * 32 + lane];
+            }
         }
-        return;
+        if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
+            if (lane == 0) {
+                cdist[c] = __int_as_float(0x7f800000);
+                keep[c] = 0;
+            }
+            continue;
+        }
+        const float *xv = vrow(d, row);
+        const float sq = row_dist_regs<L2, NV>(qr, xv, qv, d.dim, lane);
+        const float d32 = L2 ? sqrtf(sq) : sq;
+        if (lane != 0) continue;
+        const float r = thr_q[q];
+        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
+        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        if (KNN) {
+            cdist[c] = d32;
+            keep[c] = lo <= r ? 1 : 0;
+        } else if (hi < r * (1.f - 1e-9f)) {
+            keep[c] = 1;
+            cdist[c] = d32;
+        } else if (lo > r * (1.f + 1e-9f)) {
+            keep[c] = 0;
+        } else {
+            const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+            const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
+            keep[c] = key <= lim ? 1 : 0;
+            cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
+            atomicAdd(rechecks, 1ull);
+        }
     }
-    const float *qv = d.Q + (int64_t)q * d.dim;
-    const float *xv = vrow(d, row);
-    const float s = warp_vec_dist<L2>(qv, xv, d.dim, lane);
-    const float d32 = L2 ? sqrtf(s) : s;
-    if (KNN) {
-        if (lane == 0) cdist[c] = d32;
-        return;
-    }
-    if (lane != 0) return;
-    const float r = thr_q[q];
-    const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
-    const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
-    if (hi < r * (1.f - 1e-9f)) {
-        keep[c] = 1;
-        cdist[c] = d32;
-    } else if (lo > r * (1.f + 1e-9f)) {
-        keep[c] = 0;
-    } else {
-        const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
-        const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
-        keep[c] = key <= lim ? 1 : 0;
-        cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
-        atomicAdd(rechecks, 1ull);
+}
+
+__global__ void k_compact_cands(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+                                const float *__restrict__ cdist, const uint8_t *__restrict__ keep, int64_t C,
+                                const int64_t *__restrict__ pos, int32_t *__restrict__ oq, int32_t *__restrict__ orow,
+                                float *__restrict__ od) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[c]) continue;
+        const int64_t o = pos[c];
+        oq[o] = cq[c];
+        orow[o] = crow[c];
+        od[o] = cdist[c];
     }
 }
 
@@ -431,7 +571,7 @@ __global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_
             const int64_t row = crow[c];
             if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
                 cdist[c] = __int_as_float(0x7f800000);
-                if (!KNN) keep[c] = 0;
+                keep[c] = 0;
                 continue;
             }
             const uint8_t *tx;
@@ -439,7 +579,7 @@ __global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_
             srow(d, row, tx, len);
             const float dist = (float)(m > 0 ? myers_edit<W>(Peq, m, tx, len) : len);
             cdist[c] = dist;
-            if (!KNN) keep[c] = dist <= r ? 1 : 0;
+            keep[c] = dist <= r ? 1 : 0;   // kNN: r = tau_q, an upper bound of the k-th distance
         }
         __syncthreads();
         s = t;
@@ -993,26 +1133,38 @@ struct Runner {
         }
     }
 
+    template <bool L2, bool KNN>
+    void launch_verify_vec(const DBuf<int32_t> &cq, const DBuf<int32_t> &crow, int64_t C, DBuf<float> &cdist,
+                           DBuf<uint8_t> &keep) {
+        const int64_t warps = (C + kVerifyGroup - 1) / kVerifyGroup;
+        const unsigned grid = nblocks(warps, kWarpsPerBlock);
+        const bool aligned = ((uintptr_t)d.Q & 15) == 0;
+        const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
+#define GTS_VV(NVV)                                                                                          \
+    k_verify_vec<L2, KNN, NVV><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), \
+                                                    counters.get())
+        switch (nv) {
+            case 1: GTS_VV(1); break;
+            case 2: GTS_VV(2); break;
+            case 3: GTS_VV(3); break;
+            case 4: GTS_VV(4); break;
+            default: GTS_VV(0); break;
+        }
+#undef GTS_VV
+    }
+
     void verify_and_collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, int64_t C) {
         st_cands += C;
         DBuf<float> cdist(C, st);
-        DBuf<uint8_t> keep(knn ? 0 : C, st);
+        DBuf<uint8_t> keep(C, st);
         clk.begin(GTS_STAGE_VERIFY);
         if (d.dim > 0) {
             if (d.metric == GTS_L2) {
-                if (knn)
-                    k_verify_vec<true, true><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
-                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
-                else
-                    k_verify_vec<true, false><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
-                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+                if (knn) launch_verify_vec<true, true>(cq, crow, C, cdist, keep);
+                else launch_verify_vec<true, false>(cq, crow, C, cdist, keep);
             } else {
-                if (knn)
-                    k_verify_vec<false, true><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
-                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
-                else
-                    k_verify_vec<false, false><<<nblocks(C, kWarpsPerBlock), kT, 0, st>>>(
-                        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+                if (knn) launch_verify_vec<false, true>(cq, crow, C, cdist, keep);
+                else launch_verify_vec<false, false>(cq, crow, C, cdist, keep);
             }
         } else {
             const int chunk = 256;
@@ -1034,40 +1186,46 @@ struct Runner {
         }
         clk.end();
         check_launch("verify");
+        DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
+        clk.begin(GTS_STAGE_OTHER, 2);
+        k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
+        exclusive_scan(k64.get(), pos.get(), C + 1, st);
+        clk.end();
+        const int64_t R = d2h_i64(pos.get() + C, st);
+        if (R == 0) return;
         if (knn) {
-            DBuf<double> ckey(C, st);
+            // only candidates within tau_q can reach the top k
+            DBuf<int32_t> kq2(R, st), krow2(R, st);
+            DBuf<float> kd2(R, st);
+            clk.begin(GTS_STAGE_OTHER);
+            k_compact_cands<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C, pos.get(),
+                                                           kq2.get(), krow2.get(), kd2.get());
+            clk.end();
+            DBuf<double> ckey(R, st);
             const unsigned grid = (unsigned)qb.nq;
             clk.begin(GTS_STAGE_SELECT);
             if (d.metric == GTS_L2)
-                k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
                                                          bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
             else if (d.metric == GTS_L1)
-                k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
                                                          bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
             else
-                k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), cdist.get(), C, qb.k, koff.get(),
+                k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
                                                            bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
             clk.end();
             check_launch("knn merge");
         } else {
-            DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
-            clk.begin(GTS_STAGE_OTHER, 2);
-            k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
-            exclusive_scan(k64.get(), pos.get(), C + 1, st);
+            DBuf<uint64_t> rk(R, st);
+            DBuf<float> rd(R, st);
+            clk.begin(GTS_STAGE_OTHER);
+            k_range_pack<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C, pos.get(), d,
+                                                        rk.get(), rd.get());
             clk.end();
-            const int64_t R = d2h_i64(pos.get() + C, st);
-            if (R > 0) {
-                DBuf<uint64_t> rk(R, st);
-                DBuf<float> rd(R, st);
-                clk.begin(GTS_STAGE_OTHER);
-                k_range_pack<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C,
-                                                            pos.get(), d, rk.get(), rd.get());
-                clk.end();
-                check_launch("range pack");
-                rkeys.push_back(std::move(rk));
-                rdists.push_back(std::move(rd));
-                rcounts.push_back(R);
-            }
+            check_launch("range pack");
+            rkeys.push_back(std::move(rk));
+            rdists.push_back(std::move(rd));
+            rcounts.push_back(R);
         }
     }
 
@@ -1169,6 +1327,23 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.clk.end();
     }
     check_launch("query setup");
+    if (knn && t.n > 0 && nq > 0 && t.dim > 0) {
+        LevelOffsets lo_off;
+        for (int l = 0; l <= t.h && l < kMaxHeight + 2; ++l) lo_off.v[l] = t.lvl_off[l];
+        const int cap = 512;
+        R.clk.begin(GTS_STAGE_THRESHOLD);
+        if (t.metric == GTS_L2)
+            k_probe_vec<true><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),
+                                                                          R.tk_d.get(), R.tk_id.get(), R.tk_n.get(),
+                                                                          R.thr.get());
+        else
+            k_probe_vec<false><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),
+                                                                           R.tk_d.get(), R.tk_id.get(), R.tk_n.get(),
+                                                                           R.thr.get());
+        R.clk.end();
+        check_launch("knn probe");
+        R.st_pivots += nq * (int64_t)t.h;
+    }
     if (t.n > 0 && nq > 0) {
         Level L0;
         L0.E = nq;
