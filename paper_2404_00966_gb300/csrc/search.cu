@@ -251,12 +251,12 @@ struct LevelOffsets {
 
 // Probe for kNN (warp per query).  Section 3 notes that MkNNQ(q, k) is
 // MRQ(q, d_k) once d_k is known; the probe bounds d_k from above before the
-// batched descent: it follows one root-to-last-level path, at each level
-// taking the child whose interval [lo, hi] lies nearest to d(q, pivot) (the
-// smallest Lemma-1 lower bound), and computes the exact distances to the
-// pivots on the way and to up to `cap` rows of the last-level node reached.
-// Every visible object so evaluated enters the query's threshold list, so
-// tau_q starts at (an upper bound of) the k-th of them instead of +inf.
+// batched descent.  It follows one root-to-last-level path: at every level it
+// computes the distances from q to the pivots of all non-empty children and
+// descends into the child whose pivot is nearest, then computes the distances
+// to up to `cap` rows of the last-level node reached.  Every visible object so
+// evaluated enters the query's threshold list, so tau_q starts at (an upper
+// bound of) the k-th smallest of them instead of +inf.
 template <bool L2>
 __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id, int32_t *tk_n,
@@ -271,43 +271,55 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
     const int64_t s = d.qseq[q];
     const float *qv = d.Q + q * d.dim;
     const double up = 1.0 + 2.0 * (double)d.rel;
-    int64_t node = 0;
-    int last = d.h - 1;
-    for (int l = 0; l < d.h; ++l) {
-        const int64_t g = lo_off.v[l] + node;
-        const int32_t prow = d.npiv[g];
+    // root pivot
+    {
+        const int32_t prow = d.npiv[lo_off.v[0]];
         const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
         const float dq = L2 ? sqrtf(sq) : sq;
         if (lane == 0 && d.row_del[prow] > s) tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
-        if (l == d.h - 1) break;
-        // child with the smallest interval lower bound (ties: smallest index)
-        unsigned long long best = ~0ull;
-        for (int j = lane; j < d.F; j += 32) {
-            const int64_t c = lo_off.v[l + 1] + node * d.F + j;
-            if (d.nsize[c] > 0) {
-                const float lb = fmaxf(fmaxf(d.nlo[c] - dq, dq - d.nhi[c]), 0.f);
-                const unsigned long long key = ((unsigned long long)__float_as_uint(lb) << 32) | (unsigned)j;
-                best = key < best ? key : best;
+    }
+    int64_t node = 0;
+    if (d.h == 1) {   // one pivot level: the root's own rows
+        const int32_t m = d.nsize[lo_off.v[0]] < cap ? d.nsize[lo_off.v[0]] : cap;
+        for (int32_t r = 0; r < m; ++r) {
+            const int64_t row = d.npos[lo_off.v[0]] + r;
+            const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
+            const float dv = L2 ? sqrtf(sq) : sq;
+            if (lane == 0 && d.row_del[row] > s)
+                tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
+        }
+    }
+    for (int l = 1; l < d.h; ++l) {
+        float best = __int_as_float(0x7f800000);
+        int64_t bnode = -1;
+        for (int j = 0; j < d.F; ++j) {
+            const int64_t c = node * d.F + j;
+            const int64_t g = lo_off.v[l] + c;
+            if (d.nsize[g] == 0) continue;
+            const int32_t prow = d.npiv[g];
+            const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
+            const float dq = L2 ? sqrtf(sq) : sq;
+            if (lane == 0 && d.row_del[prow] > s)
+                tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
+            if (dq < best) {
+                best = dq;
+                bnode = c;
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-            best = other < best ? other : best;
+        if (bnode < 0) break;   // no non-empty child (cannot happen for a non-empty node)
+        node = bnode;
+        if (l == d.h - 1) {
+            const int64_t g = lo_off.v[l] + node;
+            const int32_t pos = d.npos[g];
+            const int32_t m = d.nsize[g] < cap ? d.nsize[g] : cap;
+            for (int32_t r = 0; r < m; ++r) {
+                const int64_t row = pos + r;
+                const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
+                const float dv = L2 ? sqrtf(sq) : sq;
+                if (lane == 0 && d.row_del[row] > s)
+                    tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
+            }
         }
-        if (best == ~0ull) {   // no non-empty child (cannot happen for a non-empty node)
-            last = l;
-            break;
-        }
-        node = node * d.F + (int64_t)(best & 0xffffffffull);
-    }
-    const int64_t g = lo_off.v[last] + node;
-    const int32_t pos = d.npos[g];
-    const int32_t m = d.nsize[g] < cap ? d.nsize[g] : cap;
-    for (int32_t r = 0; r < m; ++r) {
-        const int64_t row = pos + r;
-        const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
-        const float dv = L2 ? sqrtf(sq) : sq;
-        if (lane == 0 && d.row_del[row] > s) tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
     }
     if (lane == 0) {
         tk_n[q] = n;
