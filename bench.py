@@ -139,6 +139,13 @@ def cpu_baseline(X, Q, k, budget_s=12.0):
 def algorithmic_bytes(stage: str, st: dict, dim: int, h: int, C: int) -> float:
     """Bytes the algorithm must move for one launch-set of a stage (see the
     design notes for the per-unit figures)."""
+    if stage == "tile":
+        # per tile: 128 bf16 rows (dim padded to 64) + their table rows, norms and
+        # delete marks; per (query, node) entry: the FP32 query row, its path
+        # distances and metadata; per kept pair: (query, row) out
+        dim_p = (dim + 63) // 64 * 64
+        return (st["tiles"] * 128 * (dim_p * 2 + h * 4 + 4 + 8)
+                + st["tile_entries"] * (dim * 4 + h * 4 + 8 + 4 + 4 + 8 + 4) + C * 8)
     if stage == "verify":
         return C * (dim * 4 + 4 + 4 + 4)            # candidate row + (query, row) + distance out
     if stage == "leaf_scan":
@@ -184,11 +191,14 @@ def run_ours(args):
     prec = args.precision
     stream = torch.cuda.current_stream()
 
-    def step(timing=False):
-        r = ix.knn(Qd, Kd, precision=prec, result_on_device=True, timing=timing)
+    def step_prec(p, timing=False):
+        r = ix.knn(Qd, Kd, precision=p, result_on_device=True, timing=timing)
         st = r.stats
         r.free()
         return st
+
+    def step(timing=False):
+        return step_prec(prec, timing)
 
     for _ in range(args.warmup):
         step()
@@ -271,6 +281,21 @@ def run_ours(args):
         "counters_per_step": {kk: v for kk, v in stats0.items() if not isinstance(v, dict)},
         "clocks": clocks.summary(),
     }
+    if prec == "bf16" and not args.no_fp32_compare:
+        # the plain FP32 single-batch path on the same index and queries
+        for _ in range(1):
+            step_prec("fp32")
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nfs = max(1, min(3, args.steps))
+        f0.record(stream)
+        for _ in range(nfs):
+            step_prec("fp32")
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / nfs
+        out["fp32_plain"] = {"value": round(world * nq / (fms / 1e3), 1), "unit": "queries/s",
+                             "ms_per_step": round(fms, 3), "steps": nfs}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(X, Q, k, budget_s=args.cpu_seconds)
     ix.close()
@@ -318,7 +343,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload (profiling only)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

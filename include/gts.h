@@ -104,9 +104,10 @@ enum {
     GTS_STAGE_LEAF_SCAN = 3,  /* list-table lower-bound scan and candidate emission */
     GTS_STAGE_VERIFY = 4,     /* metric verification of candidates */
     GTS_STAGE_SELECT = 5,     /* kNN selection with FP64 rechecks */
-    GTS_STAGE_OTHER = 6,      /* scans, sorts, result assembly */
-    GTS_STAGES = 7,
-    GTS_STAGES_LEN = 14
+    GTS_STAGE_OTHER = 6,      /* scans, sorts, regrouping, result assembly */
+    GTS_STAGE_TILE = 7,       /* BF16 tensor-core tiles: leaf scan fused with the distance prefilter */
+    GTS_STAGES = 8,
+    GTS_STAGES_LEN = 16
 };
 
 /* Counters written to gts_query_opts.stats. */
@@ -120,7 +121,9 @@ enum {
     GTS_STAT_GROUPS = 6,       /* query groups run by the two-stage scheduler */
     GTS_STAT_CACHE_ROWS = 7,   /* cache-list objects compared by brute force */
     GTS_STAT_LAUNCHES = 8,     /* kernels launched by the call */
-    GTS_STATS_LEN = 9
+    GTS_STAT_TILES = 9,        /* BF16 tensor-core tiles (last-level node x up to 256 queries) */
+    GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries covered by those tiles */
+    GTS_STATS_LEN = 11
 };
 
 /* Per-query answers in CSR form: the answers of query i are
@@ -208,6 +211,13 @@ gts_status gts_table(const gts_index *index, int64_t *ids, float *table);
  * ids = int64[total], dist = float32[total], total = offsets[nq].  Any output
  * may be NULL.  Synchronous. */
 gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *ids, float *dist);
+
+/* Diagnostic, no counterpart in the paper: runs the tensor-core tile
+ * primitives of the BF16 L2 path (TMA load with 128-byte swizzle, tcgen05.mma
+ * with the accumulator in TMEM, tcgen05.ld) on one 128 x N x K product:
+ * D[128, N] = bf16(A[128, K]) * bf16(B[N, K])^T in FP32.  A, B, D are host
+ * row-major float32; N a multiple of 32 up to 256, K in {64, 128, 192, 256}. */
+gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *D);
 
 void gts_result_free(gts_result *result);
 void gts_free(gts_index *index);

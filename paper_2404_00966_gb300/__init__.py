@@ -24,8 +24,8 @@ EDIT, L1, L2 = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
 METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
 STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows",
-              "launches"]
-STAGE_NAMES = ["pivot_dist", "threshold", "expand", "leaf_scan", "verify", "select", "other"]
+              "launches", "tiles", "tile_entries"]
+STAGE_NAMES = ["pivot_dist", "threshold", "expand", "leaf_scan", "verify", "select", "other", "tile"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgts.so")
@@ -69,7 +69,7 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
-           "gts_last_error", "gts_status_name"]
+           "gts_last_error", "gts_status_name", "gts_selftest_tc"]
 
 
 def lib(path: Optional[str] = None):
@@ -93,6 +93,8 @@ def lib(path: Optional[str] = None):
     L.gts_info.argtypes = [P, ctypes.POINTER(_Info)]
     L.gts_tree_level.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     L.gts_table.argtypes = [P, P, P]
+    L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
+    L.gts_selftest_tc.restype = ctypes.c_int
     L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]
     L.gts_result_copy.restype = ctypes.c_int
     L.gts_result_free.argtypes = [ctypes.POINTER(_Result)]
@@ -108,6 +110,16 @@ def lib(path: Optional[str] = None):
     if path is None:
         _lib = L
     return L
+
+
+def selftest_tc(A, B):
+    """Diagnostic: D = bf16(A) @ bf16(B).T computed by the tensor-core tile
+    primitives (A: [128, K], B: [N, K] float32)."""
+    A = np.ascontiguousarray(A, np.float32)
+    B = np.ascontiguousarray(B, np.float32)
+    D = np.zeros((A.shape[0], B.shape[0]), np.float32)
+    _check(lib().gts_selftest_tc(_ptr(A), _ptr(B), B.shape[0], A.shape[1], _ptr(D)))
+    return D
 
 
 def _check(status: int):

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "gts_impl.cuh"
+#include "tile_tc.cuh"
 
 namespace gts {
 
@@ -693,6 +694,14 @@ gts_status gts_result_copy(const gts_result *r, int64_t *offsets, int64_t *ids, 
         if (offsets) GTS_CUDA(cudaMemcpy(offsets, r->offsets, (r->nq + 1) * 8, cudaMemcpyDefault));
         if (ids && total) GTS_CUDA(cudaMemcpy(ids, r->ids, total * 8, cudaMemcpyDefault));
         if (dist && total) GTS_CUDA(cudaMemcpy(dist, r->dist, total * 4, cudaMemcpyDefault));
+    });
+}
+
+gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *D) {
+    return guarded([&] {
+        GTS_REQUIRE(A && B && D, GTS_EINVAL, "NULL argument");
+        ensure_device();
+        tc_selftest(A, B, N, K, D);
     });
 }
 

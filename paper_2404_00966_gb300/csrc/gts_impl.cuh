@@ -19,6 +19,7 @@
 //     ids and insert / delete sequence numbers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -113,6 +114,17 @@ struct Objects {           // a view of caller-provided or library objects
     int max_len = 0;       // longest string (strings only)
 };
 
+// Tensor-core copy of the tree rows (built on the first BF16 query):
+// rows centred on their last-level node's centroid, rounded to bf16, padded
+// to a multiple of 64 columns; their squared norms; the TMA descriptor.
+struct TcCache {
+    bool ready = false;
+    int dim_p = 0;
+    DBuf<uint8_t> Xb;
+    DBuf<float> xn2, cent;
+    CUtensorMap map;
+};
+
 struct Tree {
     int metric = 0, dim = 0, F = 0, h = 0;
     int64_t n = 0;
@@ -126,6 +138,7 @@ struct Tree {
     DBuf<int32_t> npos, nsize, npiv;
     DBuf<float> nlo, nhi;
     int max_len = 0;                // longest string
+    TcCache tc;
     size_t device_bytes() const;
 };
 

@@ -26,6 +26,7 @@
 
 #include "gts_impl.cuh"
 #include "metric.cuh"
+#include "tile_tc.cuh"
 
 namespace gts {
 namespace {
@@ -969,7 +970,9 @@ struct Runner {
     std::vector<int64_t> rcounts;
     DBuf<unsigned long long> counters;   // [0] rechecks, [1] scanned rows
     int64_t st_pivots = 0, st_frontier = 0, st_cands = 0, st_groups = 0, st_cache = 0;
+    int64_t st_tiles = 0, st_tile_entries = 0;
     StageClock clk;
+    bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
 
     Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
         : ix(i), qb(b), knn(k), budget(bud), st(s) {
@@ -1110,6 +1113,10 @@ struct Runner {
                                                                    lvl_next, e0, e1, thr.get(), nullptr, nullptr,
                                                                    nullptr, nullptr, nullptr, mask.get());
             clk.end();
+            if (use_tc) {
+                tc_leaf(L, e0, e1, mask);
+                return;
+            }
             DBuf<int32_t> cnt(E, st);
             const int64_t lvl_last = ix->tree.lvl_off[h - 1];
             clk.begin(GTS_STAGE_LEAF_SCAN);
@@ -1142,6 +1149,51 @@ struct Runner {
                 verify_and_collect(cq, crow, C);
                 ++st_groups;
             }
+        }
+    }
+
+    // Last level on the tensor cores: regroup the entries by node, run the
+    // tiles (leaf scan + bf16 distance prefilter), then finish the kept pairs
+    // with the FP32 distance and its FP64 boundary recheck.
+    void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask) {
+        TcQuery tq;
+        tq.E = e1 - e0;
+        tq.eq = L.q.get() + e0;
+        tq.enode = L.node.get() + e0;
+        tq.path = L.path.get() + e0 * h;
+        tq.emask = mask.get();
+        tq.Q = d.Q;
+        tq.qseq = d.qseq;
+        tq.thr = thr.get();
+        tq.epsc = d.epsc;
+        TcRegroup rg;
+        clk.begin(GTS_STAGE_OTHER, 7);
+        tc_regroup(ix->tree, tq, rg, st);
+        clk.end();
+        st_tiles += rg.n_items;
+        st_tile_entries += rg.n_entries;
+        DBuf<int32_t> oq, orow;
+        int nl = 0;
+        const int64_t hint = std::max<int64_t>(1 << 20, (knn ? 64 : 256) * qb.nq);
+        clk.begin(GTS_STAGE_TILE);
+        const int64_t C = tc_run(ix->tree, ix->tree.tc, tq, rg, oq, orow, hint, &nl, st);
+        clk.end();
+        ++st_groups;
+        if (C == 0) return;
+        if (knn) {   // the selection wants query-major order
+            DBuf<int32_t> q2(C, st), r2(C, st);
+            int qbits = 1;
+            while (((int64_t)1 << qbits) < qb.nq) ++qbits;
+            size_t tb = 0;
+            cub::DeviceRadixSort::SortPairs(nullptr, tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0, qbits, st);
+            DBuf<uint8_t> tmp(tb ? tb : 1, st);
+            clk.begin(GTS_STAGE_OTHER);
+            GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0,
+                                                     qbits, st));
+            clk.end();
+            verify_and_collect(q2, r2, C);
+        } else {
+            verify_and_collect(oq, orow, C);
         }
     }
 
@@ -1264,12 +1316,15 @@ struct Runner {
 
 void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int64_t budget, QueryOut &out,
                int64_t *stats, double *stage_ms, cudaStream_t st) {
-    (void)precision;
     Tree &t = ix->tree;
     Cache &c = ix->cache;
     const int64_t nq = qb.nq;
     Runner R(ix, qb, knn, budget, st);
     R.clk.on = stage_ms != nullptr;
+    if (precision == GTS_PREC_BF16 && tc_supported(t)) {
+        tc_prepare(t, t.tc, st);
+        R.use_tc = true;
+    }
     R.h = t.h;
     R.F = t.F;
     R.W = (qb.max_len + 63) / 64;
@@ -1434,6 +1489,8 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_GROUPS] = R.st_groups;
         stats[GTS_STAT_CACHE_ROWS] = R.st_cache;
         stats[GTS_STAT_LAUNCHES] = R.clk.total_launches();
+        stats[GTS_STAT_TILES] = R.st_tiles;
+        stats[GTS_STAT_TILE_ENTRIES] = R.st_tile_entries;
     }
 }
 

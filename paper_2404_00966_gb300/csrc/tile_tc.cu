@@ -1,0 +1,604 @@
+// L2 verification on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// After the descent, the surviving (query, last-level node) entries are
+// regrouped by node.  A persistent, work-stealing kernel takes one (node,
+// chunk of up to kNQ queries) tile at a time:
+//   * TMA brings the node's rows -- stored once, centred on the node's
+//     centroid and rounded to bf16 -- into shared memory (128-byte swizzle);
+//   * the warps load the chunk's queries, centre them on the same centroid,
+//     round to bf16 and store them in the same layout;
+//   * one thread issues the K/16 tcgen05.mma (M = 128 rows, N = kNQ queries,
+//     FP32 accumulation in TMEM);
+//   * the epilogue reads the dot products from TMEM, forms
+//     d^2 = |q|^2 + |x|^2 - 2 q.x (the centred form), and keeps a (query, row)
+//     pair only if the row's leaf survived for the query, the row is visible
+//     at the query's sequence number, the table lower bound max_l |D_l - d_l|
+//     passes (Lemma 1 / 2) and a proven lower bound of the true distance is
+//     within the query's threshold (radius, or tau_q for kNN).
+// The pairs kept are a superset of the answers; they are finished by the FP32
+// distance with its FP64 boundary recheck, so results equal the plain path's.
+//
+// Lower bound of d = |q - x| from the bf16 tile (Higham, Accuracy and
+// Stability of Numerical Algorithms, 2nd ed., 3.1): with q' = q - c,
+// x' = x - c and q^, x^ their bf16 roundings (unit roundoff 2^-8),
+//   | |q^ - x^| - |q' - x'| | <= E1 = (2^-8 + 2^-22) (|q'| + |x'|),
+// and the FP32 norm form with K-term accumulation (any order, products exact,
+// sums allowed to truncate: unit 2^-23) satisfies
+//   | d~^2 - |q^ - x^|^2 | <= E2 = gamma_{K+4}(2^-23) (|q^| + |x^|)^2.
+// Hence d >= sqrt(max(0, d~^2 - E2)) - E1, shrunk by a further 2^-18
+// relative for the FP32 evaluation of the bound itself.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cub/device/device_scan.cuh>
+
+#include "gts_impl.cuh"
+#include "metric.cuh"
+#include "tc.cuh"
+#include "tile_tc.cuh"
+
+namespace gts {
+
+namespace {
+
+constexpr int kRows = 128;     // MMA M: rows of one node tile
+constexpr int kNQ = 256;       // MMA N: queries of one tile
+constexpr int kThreads = 256;  // 8 warps
+constexpr int kTmemCols = 256;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        GTS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        GTS_REQUIRE(q == cudaDriverEntryPointSuccess && p != nullptr, GTS_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// bf16 rows [rows, dim_p], box 64 columns x 128 rows, 128-byte swizzle
+CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)dim_p, (cuuint64_t)(rows > 0 ? rows : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)dim_p * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)kRows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GTS_REQUIRE(r == CUDA_SUCCESS, GTS_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return m;
+}
+
+// ---------------------------------------------------------------- preparation
+
+// centroid of every last-level node (FP32 mean of its rows)
+__global__ void k_centroids(const float *__restrict__ X, int dim, const int32_t *__restrict__ npos,
+                            const int32_t *__restrict__ nsize, int64_t nn, float *__restrict__ cent) {
+    const int64_t node = blockIdx.x;
+    if (node >= nn) return;
+    const int32_t pos = npos[node], size = nsize[node];
+    for (int c = threadIdx.x; c < dim; c += blockDim.x) {
+        float s = 0.f;
+        for (int32_t r = 0; r < size; ++r) s += X[(int64_t)(pos + r) * dim + c];
+        cent[node * dim + c] = size > 0 ? s / (float)size : 0.f;
+    }
+}
+
+// node of every row at the last pivot level, bf16 centred rows and their norms
+__global__ void k_center_rows(const float *__restrict__ X, int dim, int dim_p, int64_t n,
+                              const int32_t *__restrict__ row_node, const float *__restrict__ cent,
+                              __nv_bfloat16 *__restrict__ Xb, float *__restrict__ xn2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const float *c = cent + (int64_t)row_node[row] * dim;
+    float s = 0.f;
+    for (int k = lane; k < dim_p; k += 32) {
+        float v = 0.f;
+        if (k < dim) v = X[row * dim + k] - c[k];
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        Xb[row * dim_p + k] = b;
+        const float bf = __bfloat162float(b);
+        s += bf * bf;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xn2[row] = s;
+}
+
+__global__ void k_row_node(const int32_t *__restrict__ npos, const int32_t *__restrict__ nsize, int64_t nn,
+                           int32_t *__restrict__ row_node) {
+    const int64_t node = blockIdx.x;
+    if (node >= nn) return;
+    const int32_t pos = npos[node], size = nsize[node];
+    for (int32_t r = threadIdx.x; r < size; r += blockDim.x) row_node[pos + r] = (int32_t)node;
+}
+
+// ---------------------------------------------------------------- the tile kernel
+
+struct __align__(16) QMeta {
+    int32_t q;
+    float qn2, qn, thr;
+    int64_t s;
+    uint64_t mask;
+};
+
+__device__ __forceinline__ float bf16_lower_bound(float d2, float qn, float xn, float gK) {
+    const float sn = qn + xn;
+    const float e2 = gK * sn * sn;
+    const float e1 = 3.9139e-3f * sn;   // (2^-8 + 2^-22) / (1 - 2^-8), with margin
+    const float a = d2 - e2;
+    const float lo = (a > 0.f ? sqrtf(a) : 0.f) - e1;
+    return lo * (1.f - 3.82e-6f);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tile_l2_tc(const __grid_constant__ CUtensorMap xmap, TileArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment of the swizzled operands
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int panels = a.dim_p / 64;
+    uint8_t *sA = smem;                                   // panels x 128 rows x 128 B
+    uint8_t *sB = sA + panels * kRows * 128;              // panels x kNQ rows x 128 B
+    QMeta *meta = (QMeta *)(sB + panels * kNQ * 128);     // kNQ
+    float *spath = (float *)(meta + kNQ);                 // kNQ x h
+    float *scent = spath + kNQ * a.h;                     // dim
+    uint64_t *bars = (uint64_t *)(((uintptr_t)(scent + a.dim) + 15) & ~(uintptr_t)15);
+    uint32_t *tslot = (uint32_t *)(bars + 2);
+    int *sitem = (int *)(tslot + 1);
+    int *sabort = sitem + 1;
+    uint32_t *sphase = (uint32_t *)(sabort + 1);   // phase of the wait that gave up
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::mbar_fence_init();
+        *sabort = 0;
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) *sitem = atomicAdd(a.work_counter, 1);
+        __syncthreads();
+        const int item = *sitem;
+        if (item >= a.n_items || *sabort) break;
+        const int4 it = a.items[item];
+        const int64_t node = it.x;
+        const int start = it.y, cnt = it.z;
+        const int64_t g = a.lvl_last + node;
+        const int32_t pos = a.npos[g], size = a.nsize[g];
+        if (tid == 0) {
+            tc::mbar_expect_tx(&bars[0], (uint32_t)(panels * kRows * 128));
+            for (int p = 0; p < panels; ++p) tc::tma_load_2d(sA + p * kRows * 128, &xmap, p * 64, pos, &bars[0]);
+        }
+        for (int c = tid; c < a.dim; c += kThreads) scent[c] = a.cent[node * a.dim + c];
+        __syncthreads();
+        // ---- queries of the tile: centred, bf16, swizzled; metadata
+        for (int j = warp; j < cnt; j += kThreads / 32) {
+            const int32_t e = a.order[start + j];
+            const int32_t q = a.eq[e];
+            const float *qv = a.Q + (int64_t)q * a.dim;
+            float ss = 0.f;
+            for (int k0 = lane * 2; k0 < a.dim_p; k0 += 64) {
+                float v0 = 0.f, v1 = 0.f;
+                if (k0 < a.dim) v0 = qv[k0] - scent[k0];
+                if (k0 + 1 < a.dim) v1 = qv[k0 + 1] - scent[k0 + 1];
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                *(__nv_bfloat162 *)(sB + tc::sw128_offset(j, k0, kNQ)) = b2;
+                const float2 f = __bfloat1622float2(b2);
+                ss += f.x * f.x + f.y * f.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if (lane == 0) {
+                QMeta m;
+                m.q = q;
+                m.qn2 = ss;
+                m.qn = sqrtf(ss) * (1.f + 1e-6f);
+                m.thr = a.thr[q];
+                m.s = a.qseq[q];
+                m.mask = a.emask[e];
+                meta[j] = m;
+            }
+            if (lane < a.h) spath[j * a.h + lane] = a.path[(int64_t)e * a.h + lane];
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        // ---- MMA: one thread
+        if (tid == 0) {
+            if (!tc::mbar_wait(&bars[0], phase)) {
+                *sabort = 1;
+                *sphase = phase;
+                atomicExch(a.status, 1);
+            } else {
+                tc::tc_fence_after();
+                const uint32_t aB = tc::smem_u32(sA), bB = tc::smem_u32(sB);
+                const int ksteps = a.dim_p / 16;
+                for (int s = 0; s < ksteps; ++s) {
+                    const int p = s >> 2, w = s & 3;
+                    const uint64_t ad = tc::sdesc_k_sw128(aB + p * kRows * 128 + w * 32);
+                    const uint64_t bd = tc::sdesc_k_sw128(bB + p * kNQ * 128 + w * 32);
+                    tc::mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(&bars[1]);
+            }
+        }
+        __syncthreads();
+        if (*sabort) break;
+        // ---- epilogue: warp w reads lanes 32 (w % 4) .. +32, columns half (w / 4)
+        if (!tc::mbar_wait(&bars[1], phase)) {
+            *sabort = 1;
+            *sphase = phase;
+            atomicExch(a.status, 2);
+        }
+        tc::tc_fence_after();
+        const int quad = warp & 3, half = warp >> 2;
+        const int r = quad * 32 + lane;
+        const bool valid = r < size;
+        const int64_t row = (int64_t)pos + r;
+        const int32_t avg = size / a.F;
+        int32_t jl = avg > 0 ? r / avg : a.F - 1;
+        if (jl > a.F - 1) jl = a.F - 1;
+        float T[kMaxHeight];
+        float xn2 = 0.f, xn = 0.f;
+        int64_t rdel = 0;
+        if (valid) {
+#pragma unroll
+            for (int l = 0; l < kMaxHeight; ++l) T[l] = l < a.h ? a.table[(int64_t)l * a.n + row] : 0.f;
+            xn2 = a.xn2[row];
+            xn = sqrtf(xn2) * (1.f + 1e-6f);
+            rdel = a.row_del[row];
+        }
+        int64_t kept = 0;
+        for (int c0 = half * (kNQ / 2); c0 < (half + 1) * (kNQ / 2) && c0 < cnt; c0 += 32) {
+            uint32_t v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld_wait();
+            uint32_t passbits = 0;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+                const int j = c0 + i;
+                if (!valid || j >= cnt) continue;
+                const QMeta &m = meta[j];
+                if (!((m.mask >> jl) & 1ull) || rdel <= m.s) continue;
+                const float dot = __uint_as_float(v[i]);
+                const float d2 = m.qn2 + xn2 - 2.f * dot;
+                if (bf16_lower_bound(d2, m.qn, xn, a.gK) > m.thr) continue;
+                bool ok = true;
+                for (int l = 0; l < a.h; ++l) {
+                    const float pl = spath[j * a.h + l];
+                    const float eps = a.epsc * (T[l] + pl + m.thr);
+                    if (fabsf(T[l] - pl) > m.thr + eps) ok = false;
+                }
+                if (ok) passbits |= 1u << i;
+            }
+            const int np = __popc(passbits);
+            int incl = np;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 31 && wtot > 0) base = atomicAdd(a.out_count, (unsigned long long)wtot);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            unsigned long long o = base + (unsigned long long)(incl - np);
+            while (passbits) {
+                const int i = __ffs(passbits) - 1;
+                passbits &= passbits - 1;
+                if ((int64_t)o < a.cap) {
+                    a.out_q[o] = meta[c0 + i].q;
+                    a.out_row[o] = (int32_t)row;
+                }
+                ++o;
+            }
+            kept += np;
+        }
+        (void)kept;
+        tc::tc_fence_before();
+        __syncthreads();
+        phase ^= 1u;
+    }
+    __syncthreads();
+    if (*sabort && tid == 0) {
+        // let a TMA or MMA still in flight finish (bounded) before the
+        // shared memory and the TMEM columns are released
+        tc::mbar_wait(&bars[0], *sphase);
+        tc::mbar_wait(&bars[1], *sphase);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------- node-major regrouping
+
+__global__ void k_node_hist(const int32_t *__restrict__ enode, const uint64_t *__restrict__ emask, int64_t E,
+                            int32_t *__restrict__ ncount) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        if (emask[e]) atomicAdd(&ncount[enode[e]], 1);
+}
+
+__global__ void k_node_scatter(const int32_t *__restrict__ enode, const uint64_t *__restrict__ emask, int64_t E,
+                               const int64_t *__restrict__ noff, int32_t *__restrict__ cursor,
+                               int32_t *__restrict__ order) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!emask[e]) continue;
+        const int32_t nd = enode[e];
+        order[noff[nd] + atomicAdd(&cursor[nd], 1)] = (int32_t)e;
+    }
+}
+
+__global__ void k_items_per_node(const int32_t *__restrict__ ncount, int64_t nn, int64_t *__restrict__ nitems) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+        nitems[i] = (ncount[i] + kNQ - 1) / kNQ;
+    if (blockIdx.x == 0 && threadIdx.x == 0) nitems[nn] = 0;
+}
+
+__global__ void k_fill_items(const int32_t *__restrict__ ncount, const int64_t *__restrict__ noff,
+                             const int64_t *__restrict__ ioff, int64_t nn, int4 *__restrict__ items) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = ncount[i];
+        int64_t o = ioff[i];
+        for (int32_t s = 0; s < c; s += kNQ, ++o)
+            items[o] = make_int4((int)i, (int)(noff[i] + s), c - s < kNQ ? c - s : kNQ, 0);
+    }
+}
+
+__global__ void k_i32_to_i64_tc(const int32_t *a, int64_t n, int64_t *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) b[n] = 0;
+}
+
+template <class T>
+void exscan(const T *in, T *out, int64_t n, cudaStream_t st) {
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, in, out, n, st);
+    DBuf<uint8_t> tmp(tb ? tb : 1, st);
+    GTS_CUDA(cub::DeviceScan::ExclusiveSum(tmp.get(), tb, in, out, n, st));
+}
+
+inline unsigned nblk(int64_t n, int per = 256) {
+    int64_t b = (n + per - 1) / per;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+    return (unsigned)b;
+}
+
+size_t tile_smem_bytes(int dim_p, int h, int dim) {
+    const int panels = dim_p / 64;
+    size_t b = 1024;                                  // alignment slack
+    b += (size_t)panels * kRows * 128 + (size_t)panels * kNQ * 128;
+    b += sizeof(QMeta) * kNQ + sizeof(float) * kNQ * h + sizeof(float) * dim;
+    b += 16 + 16 + 16 + 16 + 16;
+    return b;
+}
+
+}  // namespace
+
+bool tc_supported(const Tree &t) { return t.metric == GTS_L2 && t.dim > 0 && t.dim <= 256 && t.n > 0; }
+
+void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
+    if (c.ready) return;
+    const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
+    c.dim_p = ((t.dim + 63) / 64) * 64;
+    c.cent.alloc((size_t)nn * t.dim, st);
+    c.xn2.alloc(t.n, st);
+    c.Xb.alloc((size_t)t.n * c.dim_p * 2, st);
+    DBuf<int32_t> row_node(t.n, st);
+    const int32_t *npos = t.npos.get() + t.lvl_off[t.h - 1];
+    const int32_t *nsize = t.nsize.get() + t.lvl_off[t.h - 1];
+    k_row_node<<<(unsigned)nn, 128, 0, st>>>(npos, nsize, nn, row_node.get());
+    k_centroids<<<(unsigned)nn, 128, 0, st>>>(t.X.get(), t.dim, npos, nsize, nn, c.cent.get());
+    k_center_rows<<<nblk(t.n * 32), 256, 0, st>>>(t.X.get(), t.dim, c.dim_p, t.n, row_node.get(), c.cent.get(),
+                                                (__nv_bfloat16 *)c.Xb.get(), c.xn2.get());
+    check_launch("bf16 preparation");
+    c.map = make_row_map(c.Xb.get(), t.n, c.dim_p);
+    GTS_CUDA(cudaStreamSynchronize(st));
+    c.ready = true;
+}
+
+int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st) {
+    const int64_t E = tq.E;
+    const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
+    DBuf<int32_t> ncount(nn, st), cursor(nn, st);
+    rg.order.alloc(E > 0 ? E : 1, st);
+    GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
+    GTS_CUDA(cudaMemsetAsync(cursor.get(), 0, nn * 4, st));
+    k_node_hist<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, ncount.get());
+    DBuf<int64_t> c64(nn + 1, st), noff(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
+    k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncount.get(), nn, c64.get());
+    exscan(c64.get(), noff.get(), nn + 1, st);
+    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, noff.get(), cursor.get(), rg.order.get());
+    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncount.get(), nn, nitems.get());
+    exscan(nitems.get(), ioff.get(), nn + 1, st);
+    int64_t total_items = 0, total_entries = 0;
+    GTS_CUDA(cudaMemcpyAsync(&total_items, ioff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(&total_entries, noff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    rg.n_items = total_items;
+    rg.n_entries = total_entries;
+    if (total_items > 0) {
+        rg.items.alloc(total_items, st);
+        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncount.get(), noff.get(), ioff.get(), nn, rg.items.get());
+    }
+    check_launch("tile regroup");
+    return total_items;
+}
+
+int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
+               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st) {
+    *launches = 0;
+    if (rg.n_items == 0) return 0;
+    int dev = 0, sms = 0;
+    GTS_CUDA(cudaGetDevice(&dev));
+    GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = tile_smem_bytes(c.dim_p, t.h, t.dim);
+    GTS_CUDA(cudaFuncSetAttribute(k_tile_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_l2_tc, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;   // TMEM: 2 x 256 columns per SM
+    const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
+    DBuf<int> counter(1, st), status(1, st);
+    DBuf<unsigned long long> count(1, st);
+    int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        out_q.alloc(cap, st);
+        out_row.alloc(cap, st);
+        GTS_CUDA(cudaMemsetAsync(counter.get(), 0, 4, st));
+        GTS_CUDA(cudaMemsetAsync(status.get(), 0, 4, st));
+        GTS_CUDA(cudaMemsetAsync(count.get(), 0, 8, st));
+        TileArgs a;
+        a.dim = t.dim;
+        a.dim_p = c.dim_p;
+        a.F = t.F;
+        a.h = t.h;
+        a.n = t.n;
+        a.cent = c.cent.get();
+        a.xn2 = c.xn2.get();
+        a.table = t.table.get();
+        a.row_del = t.row_del.get();
+        a.npos = t.npos.get();
+        a.nsize = t.nsize.get();
+        a.lvl_last = t.lvl_off[t.h - 1];
+        a.Q = tq.Q;
+        a.qseq = tq.qseq;
+        a.thr = tq.thr;
+        a.eq = tq.eq;
+        a.path = tq.path;
+        a.emask = tq.emask;
+        a.order = rg.order.get();
+        a.items = rg.items.get();
+        a.n_items = rg.n_items;
+        a.work_counter = counter.get();
+        a.out_q = out_q.get();
+        a.out_row = out_row.get();
+        a.cap = cap;
+        a.out_count = count.get();
+        a.status = status.get();
+        a.epsc = tq.epsc;
+        a.gK = (float)(c.dim_p + 4) * 1.1920929e-7f * 1.01f;
+        k_tile_l2_tc<<<(unsigned)grid, kThreads, smem, st>>>(c.map, a);
+        ++*launches;
+        check_launch("tensor-core tile");
+        unsigned long long hcount = 0;
+        int hstatus = 0;
+        GTS_CUDA(cudaMemcpyAsync(&hcount, count.get(), 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaMemcpyAsync(&hstatus, status.get(), 4, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        GTS_REQUIRE(hstatus == 0, GTS_ETIMEOUT,
+                    "tensor-core tile: a bounded mbarrier wait ran out (status " + std::to_string(hstatus) + ")");
+        if ((int64_t)hcount <= cap) return (int64_t)hcount;
+        cap = (int64_t)hcount;
+    }
+    throw Error(GTS_ECUDA, "tensor-core tile: output count changed between launches");
+}
+
+// ---------------------------------------------------------------- self-test
+
+namespace {
+
+__global__ void __launch_bounds__(128, 1)
+    k_selftest_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16 *__restrict__ B, int N, int K,
+                  float *__restrict__ D, int *status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int panels = K / 64;
+    uint8_t *sA = smem;
+    uint8_t *sB = sA + panels * kRows * 128;
+    uint64_t *bars = (uint64_t *)(sB + panels * kNQ * 128);
+    uint32_t *tslot = (uint32_t *)(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::mbar_fence_init();
+        tc::mbar_expect_tx(&bars[0], (uint32_t)(panels * kRows * 128));
+        for (int p = 0; p < panels; ++p) tc::tma_load_2d(sA + p * kRows * 128, &amap, p * 64, 0, &bars[0]);
+    }
+    for (int j = tid; j < N; j += blockDim.x)
+        for (int k = 0; k < K; ++k) *(__nv_bfloat16 *)(sB + tc::sw128_offset(j, k, kNQ)) = B[(int64_t)j * K + k];
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        if (!tc::mbar_wait(&bars[0], 0)) {
+            atomicExch(status, 1);
+        } else {
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+            for (int s = 0; s < K / 16; ++s) {
+                const int p = s >> 2, w = s & 3;
+                tc::mma_bf16(tmem, tc::sdesc_k_sw128(tc::smem_u32(sA) + p * kRows * 128 + w * 32),
+                             tc::sdesc_k_sw128(tc::smem_u32(sB) + p * kNQ * 128 + w * 32), idesc, s > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&bars[1]);
+        }
+    }
+    __syncthreads();
+    const bool ok = *status == 0 && tc::mbar_wait(&bars[1], 0);
+    if (!ok) atomicExch(status, 2);
+    tc::tc_fence_after();
+    if (ok) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld_wait();
+            const int r = warp * 32 + lane;
+            for (int i = 0; i < 32; ++i)
+                if (c0 + i < N) D[(int64_t)r * N + c0 + i] = __uint_as_float(v[i]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && !ok) {
+        tc::mbar_wait(&bars[0], 0);
+        tc::mbar_wait(&bars[1], 0);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+__global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+}  // namespace
+
+void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD) {
+    GTS_REQUIRE(N >= 32 && N <= kNQ && N % 32 == 0, GTS_EINVAL, "N must be a multiple of 32 in 32 .. 256");
+    GTS_REQUIRE(K >= 64 && K <= 256 && K % 64 == 0, GTS_EINVAL, "K must be 64, 128, 192 or 256");
+    cudaStream_t st = nullptr;
+    DBuf<float> fA((size_t)kRows * K, st), fB((size_t)N * K, st), D((size_t)kRows * N, st);
+    DBuf<__nv_bfloat16> bA((size_t)kRows * K, st), bB((size_t)N * K, st);
+    DBuf<int> status(1, st);
+    GTS_CUDA(cudaMemcpyAsync(fA.get(), hA, (size_t)kRows * K * 4, cudaMemcpyHostToDevice, st));
+    GTS_CUDA(cudaMemcpyAsync(fB.get(), hB, (size_t)N * K * 4, cudaMemcpyHostToDevice, st));
+    GTS_CUDA(cudaMemsetAsync(status.get(), 0, 4, st));
+    k_f32_to_bf16<<<64, 256, 0, st>>>(fA.get(), (int64_t)kRows * K, bA.get());
+    k_f32_to_bf16<<<64, 256, 0, st>>>(fB.get(), (int64_t)N * K, bB.get());
+    CUtensorMap m = make_row_map(bA.get(), kRows, K);
+    const size_t smem = 1024 + (size_t)(K / 64) * (kRows + kNQ) * 128 + 64;
+    GTS_CUDA(cudaFuncSetAttribute(k_selftest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_selftest_tc<<<1, 128, smem, st>>>(m, bB.get(), N, K, D.get(), status.get());
+    check_launch("tensor-core self-test");
+    int hs = 0;
+    GTS_CUDA(cudaMemcpyAsync(&hs, status.get(), 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(hD, D.get(), (size_t)kRows * N * 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    GTS_REQUIRE(hs == 0, GTS_ETIMEOUT, "tensor-core self-test: a bounded wait ran out");
+}
+
+}  // namespace gts

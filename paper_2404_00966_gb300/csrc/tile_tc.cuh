@@ -1,0 +1,64 @@
+// Tensor-core (tcgen05) verification tiles for L2: declarations shared by the
+// search driver and the tile kernel.
+#pragma once
+
+#include <cuda.h>
+
+#include "gts_impl.cuh"
+
+namespace gts {
+
+struct TileArgs {
+    int dim, dim_p, F, h;
+    int64_t n;
+    const float *cent;        // centroids of the last-level nodes [nodes, dim]
+    const float *xn2;         // |x^|^2 of every row (bf16 centred row)
+    const float *table;       // [h, n]
+    const int64_t *row_del;
+    const int32_t *npos, *nsize;
+    int64_t lvl_last;         // first node of the last pivot level
+    const float *Q;
+    const int64_t *qseq;
+    const float *thr;
+    const int32_t *eq;        // entries of the last pivot level (query-major)
+    const float *path;        // [E, h]
+    const uint64_t *emask;    // surviving-leaf masks
+    const int32_t *order;     // entries regrouped by node
+    const int4 *items;        // (node, first, count, 0) over `order`
+    int64_t n_items;
+    int *work_counter;
+    int32_t *out_q, *out_row;
+    int64_t cap;
+    unsigned long long *out_count;
+    int *status;
+    float epsc, gK;
+};
+
+struct TcQuery {
+    int64_t E = 0;
+    const int32_t *eq = nullptr, *enode = nullptr;
+    const float *path = nullptr;
+    const uint64_t *emask = nullptr;
+    const float *Q = nullptr;
+    const int64_t *qseq = nullptr;
+    const float *thr = nullptr;
+    float epsc = 0.f;
+};
+
+struct TcRegroup {
+    DBuf<int32_t> order;   // entry ids grouped by node
+    DBuf<int4> items;      // (node, first, count, 0)
+    int64_t n_items = 0;
+    int64_t n_entries = 0; // entries with a surviving leaf
+};
+
+bool tc_supported(const Tree &t);
+void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
+// regroup the last-level entries by node into tiles; returns the tile count
+int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st);
+// run the tiles; returns the number of (query, row) pairs written to out_q/out_row
+int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
+               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
+void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD);
+
+}  // namespace gts

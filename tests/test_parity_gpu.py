@@ -209,6 +209,41 @@ def test_tiny_memory_budget_gives_same_answers(gts):
     ix.close()
 
 
+def _bf16(x):
+    """Round float32 to bfloat16 (nearest, ties to even) and back, in numpy."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+@pytest.mark.parametrize("N,K", [(256, 128), (64, 64), (128, 256), (32, 192)])
+def test_tensor_core_tile_primitives(gts, N, K):
+    """TMA (128-byte swizzle) + tcgen05.mma (TMEM accumulator) + tcgen05.ld
+    against the FP64 product of the same bf16-rounded inputs."""
+    rng = np.random.default_rng(N * 1000 + K)
+    A = rng.standard_normal((128, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = gts.selftest_tc(A, B)
+    ref = _bf16(A).astype(np.float64) @ _bf16(B).astype(np.float64).T
+    scale = np.abs(_bf16(A)).astype(np.float64) @ np.abs(_bf16(B)).astype(np.float64).T
+    err = np.abs(D - ref)
+    assert np.all(err <= (K + 4) * 2.0 ** -23 * scale + 1e-30), float((err / scale).max())
+
+
+@pytest.mark.parametrize("dim,dup", [(128, 0.0), (100, 0.2), (256, 0.0)])
+def test_bf16_tiles_parity(gts, dim, dup):
+    X, Q = vec_case(20011, dim, 300, seed=40 + dim, dup=dup)
+    Q[:3] = X[[5, 9, 20010]]
+    ix = gts.Index.build(X, "l2", fanout=12, root_pivot=7)
+    for k in (1, 10, 33):
+        r = ix.knn(Q, k, precision="bf16")
+        assert_same(r, oracle.knn_query("l2", X, Q, k), "l2", f"bf16 tiles knn k={k}")
+    d = oracle.distances_to("l2", X[:500], Q[4])
+    radii = np.linspace(0.0, 1.0, 300).astype(np.float32) * np.float32(np.median(d))
+    assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l2", X, Q, radii), "l2", "bf16 tiles range")
+    ix.close()
+
+
 def test_bf16_precision_same_answers(gts):
     X, Q = vec_case(8000, 64, 120, seed=12)
     ix = gts.Index.build(X, "l2", fanout=10)
