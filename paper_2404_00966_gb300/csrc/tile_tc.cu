@@ -174,11 +174,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int4 it = a.items[item];
         const int64_t node = it.x;
         const int start = it.y, cnt = it.z;
+        const int rb = it.w * kRows;   // first row of this 128-row block within the node
         const int64_t g = a.lvl_last + node;
         const int32_t pos = a.npos[g], size = a.nsize[g];
         if (tid == 0) {
             tc::mbar_expect_tx(&bars[0], (uint32_t)(panels * kRows * 128));
-            for (int p = 0; p < panels; ++p) tc::tma_load_2d(sA + p * kRows * 128, &xmap, p * 64, pos, &bars[0]);
+            for (int p = 0; p < panels; ++p)
+                tc::tma_load_2d(sA + p * kRows * 128, &xmap, p * 64, pos + rb, &bars[0]);
         }
         for (int c = tid; c < a.dim; c += kThreads) scent[c] = a.cent[node * a.dim + c];
         __syncthreads();
@@ -241,11 +243,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::tc_fence_after();
         const int quad = warp & 3, half = warp >> 2;
-        const int r = quad * 32 + lane;
-        const bool valid = r < size;
-        const int64_t row = (int64_t)pos + r;
+        const int r = quad * 32 + lane;                 // TMEM lane = row of the block
+        const bool valid = rb + r < size;
+        const int64_t row = (int64_t)pos + rb + r;
         const int32_t avg = size / a.F;
-        int32_t jl = avg > 0 ? r / avg : a.F - 1;
+        int32_t jl = avg > 0 ? (rb + r) / avg : a.F - 1;
         if (jl > a.F - 1) jl = a.F - 1;
         float T[kMaxHeight];
         float xn2 = 0.f, xn = 0.f;
@@ -336,19 +338,24 @@ __global__ void k_node_scatter(const int32_t *__restrict__ enode, const uint64_t
     }
 }
 
-__global__ void k_items_per_node(const int32_t *__restrict__ ncount, int64_t nn, int64_t *__restrict__ nitems) {
+// tiles of a node: 128-row blocks of its rows x chunks of kNQ of its queries
+__global__ void k_items_per_node(const int32_t *__restrict__ ncount, const int32_t *__restrict__ nsize, int64_t nn,
+                                 int64_t *__restrict__ nitems) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
-        nitems[i] = (ncount[i] + kNQ - 1) / kNQ;
+        nitems[i] = (int64_t)((ncount[i] + kNQ - 1) / kNQ) * ((nsize[i] + kRows - 1) / kRows);
     if (blockIdx.x == 0 && threadIdx.x == 0) nitems[nn] = 0;
 }
 
-__global__ void k_fill_items(const int32_t *__restrict__ ncount, const int64_t *__restrict__ noff,
-                             const int64_t *__restrict__ ioff, int64_t nn, int4 *__restrict__ items) {
+__global__ void k_fill_items(const int32_t *__restrict__ ncount, const int32_t *__restrict__ nsize,
+                             const int64_t *__restrict__ noff, const int64_t *__restrict__ ioff, int64_t nn,
+                             int4 *__restrict__ items) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = ncount[i];
+        const int32_t blocks = (nsize[i] + kRows - 1) / kRows;
         int64_t o = ioff[i];
-        for (int32_t s = 0; s < c; s += kNQ, ++o)
-            items[o] = make_int4((int)i, (int)(noff[i] + s), c - s < kNQ ? c - s : kNQ, 0);
+        for (int32_t b = 0; b < blocks; ++b)
+            for (int32_t s = 0; s < c; s += kNQ, ++o)
+                items[o] = make_int4((int)i, (int)(noff[i] + s), c - s < kNQ ? c - s : kNQ, b);
     }
 }
 
@@ -418,7 +425,8 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncount.get(), nn, c64.get());
     exscan(c64.get(), noff.get(), nn + 1, st);
     k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, noff.get(), cursor.get(), rg.order.get());
-    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncount.get(), nn, nitems.get());
+    const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
+    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncount.get(), lsize, nn, nitems.get());
     exscan(nitems.get(), ioff.get(), nn + 1, st);
     int64_t total_items = 0, total_entries = 0;
     GTS_CUDA(cudaMemcpyAsync(&total_items, ioff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
@@ -428,7 +436,7 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     rg.n_entries = total_entries;
     if (total_items > 0) {
         rg.items.alloc(total_items, st);
-        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncount.get(), noff.get(), ioff.get(), nn, rg.items.get());
+        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncount.get(), lsize, noff.get(), ioff.get(), nn, rg.items.get());
     }
     check_launch("tile regroup");
     return total_items;
