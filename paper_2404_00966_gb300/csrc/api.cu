@@ -562,6 +562,7 @@ gts_status gts_delete(gts_index *ix, const int64_t *ids, int64_t m, int64_t *n_m
             if (L >= 0) {
                 tree_rows.push_back(L);
                 tree_seq.push_back(ix->seq);
+                ix->tree.n_deleted += 1;
             } else {
                 cache_slots.push_back(-(L + 2));
                 cache_seq.push_back(ix->seq);

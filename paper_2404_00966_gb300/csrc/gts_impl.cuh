@@ -138,6 +138,7 @@ struct Tree {
     DBuf<int32_t> npos, nsize, npiv;
     DBuf<float> nlo, nhi;
     int max_len = 0;                // longest string
+    int64_t n_deleted = 0;          // rows carrying a delete mark
     TcCache tc;
     size_t device_bytes() const;
 };

@@ -1166,6 +1166,7 @@ struct Runner {
         tq.qseq = d.qseq;
         tq.thr = thr.get();
         tq.epsc = d.epsc;
+        tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
         TcRegroup rg;
         clk.begin(GTS_STAGE_OTHER, 7);
         tc_regroup(ix->tree, tq, rg, st);

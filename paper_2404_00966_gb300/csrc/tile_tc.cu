@@ -119,21 +119,12 @@ __global__ void k_row_node(const int32_t *__restrict__ npos, const int32_t *__re
 
 // ---------------------------------------------------------------- the tile kernel
 
-struct __align__(16) QMeta {
-    int32_t q;
-    float qn2, qn, thr;
-    int64_t s;
-    uint64_t mask;
-};
-
-__device__ __forceinline__ float bf16_lower_bound(float d2, float qn, float xn, float gK) {
-    const float sn = qn + xn;
-    const float e2 = gK * sn * sn;
-    const float e1 = 3.9139e-3f * sn;   // (2^-8 + 2^-22) / (1 - 2^-8), with margin
-    const float a = d2 - e2;
-    const float lo = (a > 0.f ? sqrtf(a) : 0.f) - e1;
-    return lo * (1.f - 3.82e-6f);
-}
+// Squared-form test of the bf16 lower bound: keep the pair unless
+//   sqrt(max(0, d~^2 - E2)) - E1 > thr,  i.e. unless  d~^2 > (thr + E1)^2 + E2,
+// with E1 = c1 (|q^| + |x^|), E2 = gK (|q^| + |x^|)^2 as derived above.  thr
+// + E1 is inflated by 2^-16 relative, which covers the FP32 evaluation of the
+// right-hand side.  No square root per pair.
+constexpr float kC1 = 3.9139e-3f;   // (2^-8 + 2^-22) / (1 - 2^-8), with margin
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_tile_l2_tc(const __grid_constant__ CUtensorMap xmap, TileArgs a) {
@@ -141,12 +132,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // 1024-byte alignment of the swizzled operands
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int panels = a.dim_p / 64;
-    uint8_t *sA = smem;                                   // panels x 128 rows x 128 B
-    uint8_t *sB = sA + panels * kRows * 128;              // panels x kNQ rows x 128 B
-    QMeta *meta = (QMeta *)(sB + panels * kNQ * 128);     // kNQ
-    float *spath = (float *)(meta + kNQ);                 // kNQ x h
-    float *scent = spath + kNQ * a.h;                     // dim
-    uint64_t *bars = (uint64_t *)(((uintptr_t)(scent + a.dim) + 15) & ~(uintptr_t)15);
+    uint8_t *sA = smem;                                     // panels x 128 rows x 128 B
+    uint8_t *sB = sA + panels * kRows * 128;                // panels x kNQ rows x 128 B
+    uint64_t *smask = (uint64_t *)(sB + panels * kNQ * 128);// kNQ surviving-leaf masks
+    int64_t *sseq = (int64_t *)(smask + kNQ);               // kNQ sequence numbers
+    float4 *sq = (float4 *)(sseq + kNQ);                    // kNQ (|q^|^2, |q^|, thr, id)
+    float *spath = (float *)(sq + kNQ);                     // kNQ x h
+    float *scent = spath + kNQ * a.h;                       // dim_p
+    uint64_t *bars = (uint64_t *)(((uintptr_t)(scent + a.dim_p) + 15) & ~(uintptr_t)15);
     uint32_t *tslot = (uint32_t *)(bars + 2);
     int *sitem = (int *)(tslot + 1);
     int *sabort = sitem + 1;
@@ -165,6 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+    const bool vec4 = (a.dim & 3) == 0 && (((uintptr_t)a.Q) & 15) == 0;
     uint32_t phase = 0;
     for (;;) {
         if (tid == 0) *sitem = atomicAdd(a.work_counter, 1);
@@ -182,33 +176,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int p = 0; p < panels; ++p)
                 tc::tma_load_2d(sA + p * kRows * 128, &xmap, p * 64, pos + rb, &bars[0]);
         }
-        for (int c = tid; c < a.dim; c += kThreads) scent[c] = a.cent[node * a.dim + c];
+        for (int c = tid; c < a.dim_p; c += kThreads) scent[c] = c < a.dim ? a.cent[node * a.dim + c] : 0.f;
         __syncthreads();
-        // ---- queries of the tile: centred, bf16, swizzled; metadata
+        // ---- queries of the tile: centred on the node centroid, bf16, swizzled
         for (int j = warp; j < cnt; j += kThreads / 32) {
             const int32_t e = a.order[start + j];
             const int32_t q = a.eq[e];
             const float *qv = a.Q + (int64_t)q * a.dim;
             float ss = 0.f;
-            for (int k0 = lane * 2; k0 < a.dim_p; k0 += 64) {
-                float v0 = 0.f, v1 = 0.f;
-                if (k0 < a.dim) v0 = qv[k0] - scent[k0];
-                if (k0 + 1 < a.dim) v1 = qv[k0 + 1] - scent[k0 + 1];
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-                *(__nv_bfloat162 *)(sB + tc::sw128_offset(j, k0, kNQ)) = b2;
-                const float2 f = __bfloat1622float2(b2);
-                ss += f.x * f.x + f.y * f.y;
+            for (int k0 = lane * 4; k0 < a.dim_p; k0 += 128) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (vec4 && k0 + 3 < a.dim) {
+                    v = *reinterpret_cast<const float4 *>(qv + k0);
+                } else {
+                    if (k0 < a.dim) v.x = qv[k0];
+                    if (k0 + 1 < a.dim) v.y = qv[k0 + 1];
+                    if (k0 + 2 < a.dim) v.z = qv[k0 + 2];
+                    if (k0 + 3 < a.dim) v.w = qv[k0 + 3];
+                }
+                const float4 c = *reinterpret_cast<const float4 *>(scent + k0);
+                const __nv_bfloat162 b0 = __floats2bfloat162_rn(k0 < a.dim ? v.x - c.x : 0.f,
+                                                                k0 + 1 < a.dim ? v.y - c.y : 0.f);
+                const __nv_bfloat162 b1 = __floats2bfloat162_rn(k0 + 2 < a.dim ? v.z - c.z : 0.f,
+                                                                k0 + 3 < a.dim ? v.w - c.w : 0.f);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const uint32_t *>(&b0);
+                pk.y = *reinterpret_cast<const uint32_t *>(&b1);
+                *reinterpret_cast<uint2 *>(sB + tc::sw128_offset(j, k0, kNQ)) = pk;
+                const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+                ss += f0.x * f0.x + f0.y * f0.y + f1.x * f1.x + f1.y * f1.y;
             }
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
             if (lane == 0) {
-                QMeta m;
-                m.q = q;
-                m.qn2 = ss;
-                m.qn = sqrtf(ss) * (1.f + 1e-6f);
-                m.thr = a.thr[q];
-                m.s = a.qseq[q];
-                m.mask = a.emask[e];
-                meta[j] = m;
+                smask[j] = a.emask[e];
+                sseq[j] = a.qseq[q];
+                sq[j] = make_float4(ss, sqrtf(ss) * (1.f + 1e-6f), a.thr[q], __int_as_float(q));
             }
             if (lane < a.h) spath[j * a.h + lane] = a.path[(int64_t)e * a.h + lane];
         }
@@ -244,41 +246,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tc_fence_after();
         const int quad = warp & 3, half = warp >> 2;
         const int r = quad * 32 + lane;                 // TMEM lane = row of the block
-        const bool valid = rb + r < size;
+        const int nrow = size - rb;                     // rows of the node in this block (may exceed 128)
+        const bool valid = r < nrow;
         const int64_t row = (int64_t)pos + rb + r;
         const int32_t avg = size / a.F;
         int32_t jl = avg > 0 ? (rb + r) / avg : a.F - 1;
         if (jl > a.F - 1) jl = a.F - 1;
-        float T[kMaxHeight];
+        // leaves of the warp's rows: a query whose mask misses all of them is
+        // skipped by the whole warp at once
+        const int rlast = min(quad * 32 + 31, min(nrow, kRows) - 1);
+        uint64_t wmask = 0;
+        if (rlast >= quad * 32) {
+            int32_t j0 = avg > 0 ? (rb + quad * 32) / avg : a.F - 1;
+            int32_t j1 = avg > 0 ? (rb + rlast) / avg : a.F - 1;
+            j0 = min(j0, a.F - 1);
+            j1 = min(j1, a.F - 1);
+            wmask = ((j1 >= 63) ? ~0ull : ((1ull << (j1 + 1)) - 1ull)) & ~((1ull << j0) - 1ull);
+        }
         float xn2 = 0.f, xn = 0.f;
-        int64_t rdel = 0;
+        int64_t rdel = kNever;
         if (valid) {
-#pragma unroll
-            for (int l = 0; l < kMaxHeight; ++l) T[l] = l < a.h ? a.table[(int64_t)l * a.n + row] : 0.f;
             xn2 = a.xn2[row];
             xn = sqrtf(xn2) * (1.f + 1e-6f);
-            rdel = a.row_del[row];
+            if (a.any_deleted) rdel = a.row_del[row];
         }
-        int64_t kept = 0;
         for (int c0 = half * (kNQ / 2); c0 < (half + 1) * (kNQ / 2) && c0 < cnt; c0 += 32) {
             uint32_t v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
             tc::tmem_ld_wait();
             uint32_t passbits = 0;
-#pragma unroll 4
+#pragma unroll
             for (int i = 0; i < 32; ++i) {
                 const int j = c0 + i;
-                if (!valid || j >= cnt) continue;
-                const QMeta &m = meta[j];
-                if (!((m.mask >> jl) & 1ull) || rdel <= m.s) continue;
-                const float dot = __uint_as_float(v[i]);
-                const float d2 = m.qn2 + xn2 - 2.f * dot;
-                if (bf16_lower_bound(d2, m.qn, xn, a.gK) > m.thr) continue;
+                if (j >= cnt) break;
+                const uint64_t m = smask[j];
+                if ((m & wmask) == 0) continue;   // warp-uniform
+                if (!valid || !((m >> jl) & 1ull)) continue;
+                const float4 qm = sq[j];
+                const float d2 = fmaf(-2.f, __uint_as_float(v[i]), qm.x + xn2);
+                const float sn = qm.y + xn;
+                const float t = fmaf(kC1, sn, qm.z) * 1.0000153f;
+                if (d2 > fmaf(t, t, a.gK * sn * sn)) continue;
+                if (rdel <= sseq[j]) continue;
+                // table lower bound (Lemma 1 / 2) on the pair that is left
                 bool ok = true;
-                for (int l = 0; l < a.h; ++l) {
+                for (int l = 0; l < a.h && ok; ++l) {
+                    const float T = a.table[(int64_t)l * a.n + row];
                     const float pl = spath[j * a.h + l];
-                    const float eps = a.epsc * (T[l] + pl + m.thr);
-                    if (fabsf(T[l] - pl) > m.thr + eps) ok = false;
+                    const float eps = a.epsc * (T + pl + qm.z);
+                    if (fabsf(T - pl) > qm.z + eps) ok = false;
                 }
                 if (ok) passbits |= 1u << i;
             }
@@ -289,22 +305,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane >= o) incl += t;
             }
             const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtot == 0) continue;
             unsigned long long base = 0;
-            if (lane == 31 && wtot > 0) base = atomicAdd(a.out_count, (unsigned long long)wtot);
+            if (lane == 31) base = atomicAdd(a.out_count, (unsigned long long)wtot);
             base = __shfl_sync(0xffffffffu, base, 31);
             unsigned long long o = base + (unsigned long long)(incl - np);
             while (passbits) {
                 const int i = __ffs(passbits) - 1;
                 passbits &= passbits - 1;
                 if ((int64_t)o < a.cap) {
-                    a.out_q[o] = meta[c0 + i].q;
+                    a.out_q[o] = __float_as_int(sq[c0 + i].w);
                     a.out_row[o] = (int32_t)row;
                 }
                 ++o;
             }
-            kept += np;
         }
-        (void)kept;
         tc::tc_fence_before();
         __syncthreads();
         phase ^= 1u;
@@ -384,8 +399,9 @@ size_t tile_smem_bytes(int dim_p, int h, int dim) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                  // alignment slack
     b += (size_t)panels * kRows * 128 + (size_t)panels * kNQ * 128;
-    b += sizeof(QMeta) * kNQ + sizeof(float) * kNQ * h + sizeof(float) * dim;
-    b += 16 + 16 + 16 + 16 + 16;
+    b += (size_t)kNQ * (8 + 8 + 16) + sizeof(float) * kNQ * h + sizeof(float) * dim_p;
+    b += 16 + 16 + 16 + 16 + 16 + 16;
+    (void)dim;
     return b;
 }
 
@@ -495,6 +511,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.status = status.get();
         a.epsc = tq.epsc;
         a.gK = (float)(c.dim_p + 4) * 1.1920929e-7f * 1.01f;
+        a.any_deleted = tq.any_deleted;
         k_tile_l2_tc<<<(unsigned)grid, kThreads, smem, st>>>(c.map, a);
         ++*launches;
         check_launch("tensor-core tile");

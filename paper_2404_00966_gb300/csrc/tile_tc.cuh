@@ -32,6 +32,7 @@ struct TileArgs {
     unsigned long long *out_count;
     int *status;
     float epsc, gK;
+    int any_deleted;          // 0: no row has a delete mark, skip the visibility test
 };
 
 struct TcQuery {
@@ -43,6 +44,7 @@ struct TcQuery {
     const int64_t *qseq = nullptr;
     const float *thr = nullptr;
     float epsc = 0.f;
+    int any_deleted = 1;
 };
 
 struct TcRegroup {
