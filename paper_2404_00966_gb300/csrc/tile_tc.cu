@@ -178,41 +178,64 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int c = tid; c < a.dim_p; c += kThreads) scent[c] = c < a.dim ? a.cent[node * a.dim + c] : 0.f;
         __syncthreads();
-        // ---- queries of the tile: centred on the node centroid, bf16, swizzled
-        for (int j = warp; j < cnt; j += kThreads / 32) {
+        // ---- per-query metadata, one thread per query (independent loads)
+        for (int j = tid; j < cnt; j += kThreads) {
             const int32_t e = a.order[start + j];
             const int32_t q = a.eq[e];
-            const float *qv = a.Q + (int64_t)q * a.dim;
-            float ss = 0.f;
+            smask[j] = a.emask[e];
+            sseq[j] = a.qseq[q];
+            sq[j] = make_float4(0.f, 0.f, a.thr[q], __int_as_float(q));
+            for (int l = 0; l < a.h; ++l) spath[j * a.h + l] = a.path[(int64_t)e * a.h + l];
+        }
+        __syncthreads();
+        // ---- query rows: centred on the node centroid, bf16, swizzled.  A warp
+        // takes 4 queries at a time so their row loads are in flight together.
+        for (int j0 = warp * 4; j0 < cnt; j0 += (kThreads / 32) * 4) {
+            float ss[4] = {0.f, 0.f, 0.f, 0.f};
+            const float *qv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u < cnt ? j0 + u : j0;
+                qv[u] = a.Q + (int64_t)__float_as_int(sq[j].w) * a.dim;
+            }
             for (int k0 = lane * 4; k0 < a.dim_p; k0 += 128) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (vec4 && k0 + 3 < a.dim) {
-                    v = *reinterpret_cast<const float4 *>(qv + k0);
-                } else {
-                    if (k0 < a.dim) v.x = qv[k0];
-                    if (k0 + 1 < a.dim) v.y = qv[k0 + 1];
-                    if (k0 + 2 < a.dim) v.z = qv[k0 + 2];
-                    if (k0 + 3 < a.dim) v.w = qv[k0 + 3];
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (vec4 && k0 + 3 < a.dim) {
+                        v[u] = *reinterpret_cast<const float4 *>(qv[u] + k0);
+                    } else {
+                        if (k0 < a.dim) v[u].x = qv[u][k0];
+                        if (k0 + 1 < a.dim) v[u].y = qv[u][k0 + 1];
+                        if (k0 + 2 < a.dim) v[u].z = qv[u][k0 + 2];
+                        if (k0 + 3 < a.dim) v[u].w = qv[u][k0 + 3];
+                    }
                 }
                 const float4 c = *reinterpret_cast<const float4 *>(scent + k0);
-                const __nv_bfloat162 b0 = __floats2bfloat162_rn(k0 < a.dim ? v.x - c.x : 0.f,
-                                                                k0 + 1 < a.dim ? v.y - c.y : 0.f);
-                const __nv_bfloat162 b1 = __floats2bfloat162_rn(k0 + 2 < a.dim ? v.z - c.z : 0.f,
-                                                                k0 + 3 < a.dim ? v.w - c.w : 0.f);
-                uint2 pk;
-                pk.x = *reinterpret_cast<const uint32_t *>(&b0);
-                pk.y = *reinterpret_cast<const uint32_t *>(&b1);
-                *reinterpret_cast<uint2 *>(sB + tc::sw128_offset(j, k0, kNQ)) = pk;
-                const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
-                ss += f0.x * f0.x + f0.y * f0.y + f1.x * f1.x + f1.y * f1.y;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (j0 + u >= cnt) break;
+                    const __nv_bfloat162 b0 = __floats2bfloat162_rn(k0 < a.dim ? v[u].x - c.x : 0.f,
+                                                                    k0 + 1 < a.dim ? v[u].y - c.y : 0.f);
+                    const __nv_bfloat162 b1 = __floats2bfloat162_rn(k0 + 2 < a.dim ? v[u].z - c.z : 0.f,
+                                                                    k0 + 3 < a.dim ? v[u].w - c.w : 0.f);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<const uint32_t *>(&b0);
+                    pk.y = *reinterpret_cast<const uint32_t *>(&b1);
+                    *reinterpret_cast<uint2 *>(sB + tc::sw128_offset(j0 + u, k0, kNQ)) = pk;
+                    const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+                    ss[u] += f0.x * f0.x + f0.y * f0.y + f1.x * f1.x + f1.y * f1.y;
+                }
             }
-            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            if (lane == 0) {
-                smask[j] = a.emask[e];
-                sseq[j] = a.qseq[q];
-                sq[j] = make_float4(ss, sqrtf(ss) * (1.f + 1e-6f), a.thr[q], __int_as_float(q));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                for (int o = 16; o > 0; o >>= 1) ss[u] += __shfl_xor_sync(0xffffffffu, ss[u], o);
+            if (lane < 4 && j0 + lane < cnt) {
+                const float n2 = lane == 0 ? ss[0] : lane == 1 ? ss[1] : lane == 2 ? ss[2] : ss[3];
+                sq[j0 + lane].x = n2;
+                sq[j0 + lane].y = sqrtf(n2) * (1.f + 1e-6f);
             }
-            if (lane < a.h) spath[j * a.h + lane] = a.path[(int64_t)e * a.h + lane];
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
