@@ -35,6 +35,29 @@ __device__ __forceinline__ float warp_vec_dist(const float *__restrict__ q, cons
     return s;
 }
 
+// Same sum with the query already in registers as float4 chunks (NV = dim /
+// 128 per lane); NV = 0 falls back to warp_vec_dist.
+template <bool L2, int NV>
+__device__ __forceinline__ float row_dist_regs(const float4 (&qr)[NV > 0 ? NV : 1], const float *xv, const float *qv,
+                                               int dim, int lane) {
+    if (NV > 0) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(xv);
+        float s = 0.f;
+#pragma unroll
+        for (int v = 0; v < (NV > 0 ? NV : 1); ++v) {
+            const float4 b = __ldg(x4 + v * 32 + lane);
+            const float4 a = qr[v];
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            if (L2) s += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            else s += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        return s;
+    }
+    return warp_vec_dist<L2>(qv, xv, dim, lane);
+}
+
 // Proven relative error bound of the FP32 distance above against the exact
 // distance: with u = 2^-24, any summation order of `dim` non-negative terms,
 // each with up to three roundings, stays within gamma_{dim+2}; the square

@@ -123,16 +123,37 @@ __global__ void k_k_to_i64(const int32_t *k, int64_t nq, int64_t *out) {
 
 // ---------------------------------------------------------------- pivot distances
 
-template <bool L2>
+// A warp takes runs of kPivGroup consecutive entries (query-major, so the
+// query mostly stays in registers); grid-stride over the runs.
+constexpr int kPivGroup = 4;
+
+template <bool L2, int NV>
 __global__ void k_pivdist_vec(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                               int64_t lvl_base, int64_t e0, int64_t e1, float *__restrict__ path, int l) {
     const int lane = threadIdx.x & 31;
-    const int64_t w = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    if (w >= e1) return;
-    const int32_t q = eq[w];
-    const int32_t prow = d.npiv[lvl_base + enode[w]];
-    const float s = warp_vec_dist<L2>(d.Q + (int64_t)q * d.dim, d.X + (int64_t)prow * d.dim, d.dim, lane);
-    if (lane == 0) path[w * d.h + l] = L2 ? sqrtf(s) : s;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float4 qr[NV > 0 ? NV : 1];
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e0 + w * kPivGroup < e1; w += nw) {
+        const int64_t a0 = e0 + w * kPivGroup;
+        const int64_t a1 = a0 + kPivGroup < e1 ? a0 + kPivGroup : e1;
+        int32_t cur = -1;
+        const float *qv = nullptr;
+        for (int64_t e = a0; e < a1; ++e) {
+            const int32_t q = eq[e];
+            if (q != cur) {
+                cur = q;
+                qv = d.Q + (int64_t)q * d.dim;
+                if (NV > 0) {
+                    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+#pragma unroll
+                    for (int v = 0; v < (NV > 0 ? NV : 1); ++v) qr[v] = q4[v * 32 + lane];
+                }
+            }
+            const int32_t prow = d.npiv[lvl_base + enode[e]];
+            const float s = row_dist_regs<L2, NV>(qr, d.X + (int64_t)prow * d.dim, qv, d.dim, lane);
+            if (lane == 0) path[e * d.h + l] = L2 ? sqrtf(s) : s;
+        }
+    }
 }
 
 // Strings: blocks take runs of entries; entries of one query share the
@@ -171,11 +192,11 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
                       const int32_t *__restrict__ kq, const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id,
                       int32_t *tk_n, float *tau) {
     const int lane = threadIdx.x & 31;
-    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (q >= nq) return;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
     const int64_t a = lower_bound_i32(eq, e0, e1, (int32_t)q);
     const int64_t b = lower_bound_i32(eq, a, e1, (int32_t)q + 1);
-    if (a == b) return;
+    if (a == b) continue;
     const int K = kq[q];
     double *D = tk_d + koff[q];
     int64_t *I = tk_id + koff[q];
@@ -226,6 +247,7 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
     if (lane == 0) {
         tk_n[q] = n;
         tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+    }
     }
 }
 
@@ -347,8 +369,8 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
                          int32_t *__restrict__ nq_out, int32_t *__restrict__ nnode_out, float *__restrict__ npath_out,
                          uint64_t *__restrict__ mask_io) {
     const int lane = threadIdx.x & 31;
-    const int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    if (e >= e1) return;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
     const int32_t q = eq[e];
     const int32_t node = enode[e];
     if (MODE == 1) {
@@ -363,7 +385,7 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
                 for (int t = 0; t <= l; ++t) npath_out[o * d.h + t] = path[e * d.h + t];
             }
         }
-        return;
+        continue;
     }
     const float dq = path[e * d.h + l];
     const float thr = thr_q[q];
@@ -380,6 +402,7 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
     if (lane == 0) {
         mask_io[e - e0] = m;
         if (MODE == 0) cnt[e - e0] = __popcll(m);
+    }
     }
 }
 
@@ -477,37 +500,17 @@ __global__ void k_cache_cands(int64_t qa, int64_t qb, int64_t n, int64_t cn, int
 // k) and store its FP32 distance.
 constexpr int kVerifyGroup = 8;
 
-template <bool L2, int NV>
-__device__ __forceinline__ float row_dist_regs(const float4 (&qr)[NV > 0 ? NV : 1], const float *xv, const float *qv,
-                                               int dim, int lane) {
-    if (NV > 0) {
-        const float4 *x4 = reinterpret_cast<const float4 *>(xv);
-        float s = 0.f;
-#pragma unroll
-        for (int v = 0; v < (NV > 0 ? NV : 1); ++v) {
-            const float4 b = __ldg(x4 + v * 32 + lane);
-            const float4 a = qr[v];
-            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
-            if (L2) s += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-            else s += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        return s;
-    }
-    return warp_vec_dist<L2>(qv, xv, dim, lane);
-}
-
 template <bool L2, bool KNN, int NV>
 __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
                              const float *__restrict__ thr_q, float *__restrict__ cdist, uint8_t *__restrict__ keep,
                              unsigned long long *__restrict__ rechecks) {
     const int lane = threadIdx.x & 31;
-    const int64_t c0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kVerifyGroup;
-    if (c0 >= C) return;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float4 qr[NV > 0 ? NV : 1];
+    for (int64_t c0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kVerifyGroup; c0 < C;
+         c0 += nw * kVerifyGroup) {
     const int64_t c1 = c0 + kVerifyGroup < C ? c0 + kVerifyGroup : C;
     int32_t cur = -1;
-    float4 qr[NV > 0 ? NV : 1];
     const float *qv = nullptr;
     for (int64_t c = c0; c < c1; ++c) {
         const int32_t q = cq[c];
@@ -550,6 +553,7 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
             cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
             atomicAdd(rechecks, 1ull);
         }
+    }
     }
 }
 
@@ -980,6 +984,9 @@ struct Runner {
         clk.pool = &i->events;
     }
 
+    unsigned max_blocks = 152 * 8;   // grid cap for the grid-stride kernels (set from the SM count)
+    unsigned cap(unsigned b) const { return b < max_blocks ? b : max_blocks; }
+
     int64_t limit_bytes(int l) const {   // Algorithm 4: size_GPU / ((h - layer + 1) * N_c), layer = l + 1
         return budget / ((int64_t)(h - l) * F);
     }
@@ -999,12 +1006,21 @@ struct Runner {
         const int64_t E = e1 - e0;
         clk.begin(GTS_STAGE_PIVOT_DIST);
         if (d.dim > 0) {
-            if (d.metric == GTS_L2)
-                k_pivdist_vec<true><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
-                                                                              L.path.get(), l);
-            else
-                k_pivdist_vec<false><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0,
-                                                                               e1, L.path.get(), l);
+            const bool aligned = ((uintptr_t)d.Q & 15) == 0;
+            const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
+            const unsigned grid = cap(nblocks((E + kPivGroup - 1) / kPivGroup, kWarpsPerBlock));
+#define GTS_PV(L2V, NVV) \
+    k_pivdist_vec<L2V, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(), l)
+            if (d.metric == GTS_L2) {
+                switch (nv) { case 1: GTS_PV(true, 1); break; case 2: GTS_PV(true, 2); break;
+                              case 3: GTS_PV(true, 3); break; case 4: GTS_PV(true, 4); break;
+                              default: GTS_PV(true, 0); }
+            } else {
+                switch (nv) { case 1: GTS_PV(false, 1); break; case 2: GTS_PV(false, 2); break;
+                              case 3: GTS_PV(false, 3); break; case 4: GTS_PV(false, 4); break;
+                              default: GTS_PV(false, 0); }
+            }
+#undef GTS_PV
         } else {
             const int chunk = 256;
 #define GTS_PIV(WW)                                                                                                  \
@@ -1023,7 +1039,7 @@ struct Runner {
         st_frontier += E;
         if (knn) {
             clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau<<<nblocks(qb.nq, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(),
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(),
                                                                  l, qb.nq, qb.k, koff.get(), tk_d.get(), tk_id.get(),
                                                                  tk_n.get(), thr.get());
             clk.end();
@@ -1076,7 +1092,7 @@ struct Runner {
             DBuf<int32_t> cnt(E, st);
             DBuf<uint64_t> cmask(E, st);
             clk.begin(GTS_STAGE_EXPAND);
-            k_expand<0><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+            k_expand<0><<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), cnt.get(), nullptr,
                                                                    nullptr, nullptr, nullptr, cmask.get());
             clk.end();
@@ -1099,7 +1115,7 @@ struct Runner {
                 N.node.alloc(N.E, st);
                 N.path.alloc(N.E * h, st);
                 clk.begin(GTS_STAGE_EXPAND);
-                k_expand<1><<<nblocks(g1 - g0, kWarpsPerBlock), kT, 0, st>>>(
+                k_expand<1><<<cap(nblocks(g1 - g0, kWarpsPerBlock)), kT, 0, st>>>(
                     d, L.q.get(), L.node.get(), L.path.get(), l, lvl_next, e0 + g0, e0 + g1, thr.get(), nullptr,
                     offg.get(), N.q.get(), N.node.get(), N.path.get(), cmask.get() + g0);
                 clk.end();
@@ -1109,7 +1125,7 @@ struct Runner {
         } else {
             DBuf<uint64_t> mask(E, st);
             clk.begin(GTS_STAGE_EXPAND);
-            k_expand<2><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+            k_expand<2><<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), nullptr, nullptr,
                                                                    nullptr, nullptr, nullptr, mask.get());
             clk.end();
@@ -1202,7 +1218,7 @@ struct Runner {
     void launch_verify_vec(const DBuf<int32_t> &cq, const DBuf<int32_t> &crow, int64_t C, DBuf<float> &cdist,
                            DBuf<uint8_t> &keep) {
         const int64_t warps = (C + kVerifyGroup - 1) / kVerifyGroup;
-        const unsigned grid = nblocks(warps, kWarpsPerBlock);
+        const unsigned grid = cap(nblocks(warps, kWarpsPerBlock));
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
         const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
 #define GTS_VV(NVV)                                                                                          \
@@ -1322,6 +1338,12 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     const int64_t nq = qb.nq;
     Runner R(ix, qb, knn, budget, st);
     R.clk.on = stage_ms != nullptr;
+    {
+        int dev = 0, sms = 0;
+        GTS_CUDA(cudaGetDevice(&dev));
+        GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        R.max_blocks = (unsigned)(sms > 0 ? sms : 1) * 8u;
+    }
     if (precision == GTS_PREC_BF16 && tc_supported(t)) {
         tc_prepare(t, t.tc, st);
         R.use_tc = true;

@@ -43,9 +43,10 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node tile
-constexpr int kNQ = 256;       // MMA N: queries of one tile
+constexpr int kNQ = 128;       // MMA N: queries of one tile
 constexpr int kThreads = 256;  // 8 warps
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 128; // FP32 accumulator: 128 lanes x kNQ columns
+constexpr int kMaxCtasPerSm = 512 / kTmemCols;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -490,10 +491,15 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t smem = tile_smem_bytes(c.dim_p, t.h, t.dim);
     GTS_CUDA(cudaFuncSetAttribute(k_tile_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 1;
-    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_l2_tc, kThreads, smem));
+    // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
+    // TMEM columns, and the occupancy calculator (registers)
+    int smem_sm = 0, occ = 1;
+    GTS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tile_l2_tc, kThreads, smem));
+    int per_sm = (int)(smem_sm / (smem + 1024));
+    if (per_sm > kMaxCtasPerSm) per_sm = kMaxCtasPerSm;
+    if (occ > 0 && per_sm > occ) per_sm = occ;
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;   // TMEM: 2 x 256 columns per SM
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     DBuf<int> counter(1, st), status(1, st);
     DBuf<unsigned long long> count(1, st);
@@ -555,6 +561,8 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
 
 namespace {
 
+constexpr int kSelfN = 256;   // self-test tile: N up to 256, its own TMEM allocation
+
 __global__ void __launch_bounds__(128, 1)
     k_selftest_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16 *__restrict__ B, int N, int K,
                   float *__restrict__ D, int *status) {
@@ -563,10 +571,10 @@ __global__ void __launch_bounds__(128, 1)
     const int panels = K / 64;
     uint8_t *sA = smem;
     uint8_t *sB = sA + panels * kRows * 128;
-    uint64_t *bars = (uint64_t *)(sB + panels * kNQ * 128);
+    uint64_t *bars = (uint64_t *)(sB + panels * kSelfN * 128);
     uint32_t *tslot = (uint32_t *)(bars + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(tslot, kSelfN);
     if (tid == 0) {
         tc::mbar_init(&bars[0], 1);
         tc::mbar_init(&bars[1], 1);
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(128, 1)
         for (int p = 0; p < panels; ++p) tc::tma_load_2d(sA + p * kRows * 128, &amap, p * 64, 0, &bars[0]);
     }
     for (int j = tid; j < N; j += blockDim.x)
-        for (int k = 0; k < K; ++k) *(__nv_bfloat16 *)(sB + tc::sw128_offset(j, k, kNQ)) = B[(int64_t)j * K + k];
+        for (int k = 0; k < K; ++k) *(__nv_bfloat16 *)(sB + tc::sw128_offset(j, k, kSelfN)) = B[(int64_t)j * K + k];
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
     __syncthreads();
@@ -585,11 +593,11 @@ __global__ void __launch_bounds__(128, 1)
         if (!tc::mbar_wait(&bars[0], 0)) {
             atomicExch(status, 1);
         } else {
-            const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, kSelfN);
             for (int s = 0; s < K / 16; ++s) {
                 const int p = s >> 2, w = s & 3;
                 tc::mma_bf16(tmem, tc::sdesc_k_sw128(tc::smem_u32(sA) + p * kRows * 128 + w * 32),
-                             tc::sdesc_k_sw128(tc::smem_u32(sB) + p * kNQ * 128 + w * 32), idesc, s > 0 ? 1u : 0u);
+                             tc::sdesc_k_sw128(tc::smem_u32(sB) + p * kSelfN * 128 + w * 32), idesc, s > 0 ? 1u : 0u);
             }
             tc::mma_commit(&bars[1]);
         }
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(128, 1)
         tc::mbar_wait(&bars[1], 0);
     }
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, kSelfN);
 }
 
 __global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
@@ -626,7 +634,7 @@ __global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
 }  // namespace
 
 void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD) {
-    GTS_REQUIRE(N >= 32 && N <= kNQ && N % 32 == 0, GTS_EINVAL, "N must be a multiple of 32 in 32 .. 256");
+    GTS_REQUIRE(N >= 32 && N <= kSelfN && N % 32 == 0, GTS_EINVAL, "N must be a multiple of 32 in 32 .. 256");
     GTS_REQUIRE(K >= 64 && K <= 256 && K % 64 == 0, GTS_EINVAL, "K must be 64, 128, 192 or 256");
     cudaStream_t st = nullptr;
     DBuf<float> fA((size_t)kRows * K, st), fB((size_t)N * K, st), D((size_t)kRows * N, st);
@@ -638,7 +646,7 @@ void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD) {
     k_f32_to_bf16<<<64, 256, 0, st>>>(fA.get(), (int64_t)kRows * K, bA.get());
     k_f32_to_bf16<<<64, 256, 0, st>>>(fB.get(), (int64_t)N * K, bB.get());
     CUtensorMap m = make_row_map(bA.get(), kRows, K);
-    const size_t smem = 1024 + (size_t)(K / 64) * (kRows + kNQ) * 128 + 64;
+    const size_t smem = 1024 + (size_t)(K / 64) * (kRows + kSelfN) * 128 + 64;
     GTS_CUDA(cudaFuncSetAttribute(k_selftest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_selftest_tc<<<1, 128, smem, st>>>(m, bB.get(), N, K, D.get(), status.get());
     check_launch("tensor-core self-test");
