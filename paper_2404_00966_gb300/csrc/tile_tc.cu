@@ -181,13 +181,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         // ---- per-query metadata, one thread per query (independent loads)
         for (int j = tid; j < cnt; j += kThreads) {
-            const int32_t e = a.order[start + j];
-            const int32_t q = a.eq[e];
-            smask[j] = a.emask[e];
+            const int32_t q = a.gq[start + j];
+            smask[j] = a.gmask[start + j];
             sseq[j] = a.qseq[q];
             sq[j] = make_float4(0.f, 0.f, a.thr[q], __int_as_float(q));
-            for (int l = 0; l < a.h; ++l) spath[j * a.h + l] = a.path[(int64_t)e * a.h + l];
         }
+        for (int t = tid; t < cnt * a.h; t += kThreads) spath[t] = a.gpath[(int64_t)start * a.h + t];
         __syncthreads();
         // ---- query rows: centred on the node centroid, bf16, swizzled.  A warp
         // takes 4 queries at a time so their row loads are in flight together.
@@ -367,13 +366,20 @@ __global__ void k_node_hist(const int32_t *__restrict__ enode, const uint64_t *_
         if (emask[e]) atomicAdd(&ncount[enode[e]], 1);
 }
 
-__global__ void k_node_scatter(const int32_t *__restrict__ enode, const uint64_t *__restrict__ emask, int64_t E,
+// scatter each entry's payload (query, leaf mask, path distances) to its
+// node's slot, so a tile reads its queries' data contiguously
+__global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                               const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int64_t E,
                                const int64_t *__restrict__ noff, int32_t *__restrict__ cursor,
-                               int32_t *__restrict__ order) {
+                               int32_t *__restrict__ gq, uint64_t *__restrict__ gmask, float *__restrict__ gpath) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-        if (!emask[e]) continue;
+        const uint64_t m = emask[e];
+        if (!m) continue;
         const int32_t nd = enode[e];
-        order[noff[nd] + atomicAdd(&cursor[nd], 1)] = (int32_t)e;
+        const int64_t o = noff[nd] + atomicAdd(&cursor[nd], 1);
+        gq[o] = eq[e];
+        gmask[o] = m;
+        for (int l = 0; l < h; ++l) gpath[o * h + l] = path[e * h + l];
     }
 }
 
@@ -457,20 +463,26 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     const int64_t E = tq.E;
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
     DBuf<int32_t> ncount(nn, st), cursor(nn, st);
-    rg.order.alloc(E > 0 ? E : 1, st);
     GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
     GTS_CUDA(cudaMemsetAsync(cursor.get(), 0, nn * 4, st));
     k_node_hist<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, ncount.get());
     DBuf<int64_t> c64(nn + 1, st), noff(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
     k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncount.get(), nn, c64.get());
     exscan(c64.get(), noff.get(), nn + 1, st);
-    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, noff.get(), cursor.get(), rg.order.get());
+    int64_t total_entries = 0;
+    GTS_CUDA(cudaMemcpyAsync(&total_entries, noff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    const int64_t ne = total_entries > 0 ? total_entries : 1;
+    rg.gq.alloc(ne, st);
+    rg.gmask.alloc(ne, st);
+    rg.gpath.alloc(ne * t.h, st);
+    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, E, noff.get(), cursor.get(),
+                                            rg.gq.get(), rg.gmask.get(), rg.gpath.get());
     const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
     k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncount.get(), lsize, nn, nitems.get());
     exscan(nitems.get(), ioff.get(), nn + 1, st);
-    int64_t total_items = 0, total_entries = 0;
+    int64_t total_items = 0;
     GTS_CUDA(cudaMemcpyAsync(&total_items, ioff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
-    GTS_CUDA(cudaMemcpyAsync(&total_entries, noff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
     GTS_CUDA(cudaStreamSynchronize(st));
     rg.n_items = total_items;
     rg.n_entries = total_entries;
@@ -526,10 +538,9 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.Q = tq.Q;
         a.qseq = tq.qseq;
         a.thr = tq.thr;
-        a.eq = tq.eq;
-        a.path = tq.path;
-        a.emask = tq.emask;
-        a.order = rg.order.get();
+        a.gq = rg.gq.get();
+        a.gpath = rg.gpath.get();
+        a.gmask = rg.gmask.get();
         a.items = rg.items.get();
         a.n_items = rg.n_items;
         a.work_counter = counter.get();

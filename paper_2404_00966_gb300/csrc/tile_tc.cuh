@@ -20,10 +20,9 @@ struct TileArgs {
     const float *Q;
     const int64_t *qseq;
     const float *thr;
-    const int32_t *eq;        // entries of the last pivot level (query-major)
-    const float *path;        // [E, h]
-    const uint64_t *emask;    // surviving-leaf masks
-    const int32_t *order;     // entries regrouped by node
+    const int32_t *gq;        // entries of the last pivot level regrouped by node: query,
+    const float *gpath;       // path distances [*, h],
+    const uint64_t *gmask;    // surviving-leaf mask
     const int4 *items;        // (node, first, count, 0) over `order`
     int64_t n_items;
     int *work_counter;
@@ -48,7 +47,9 @@ struct TcQuery {
 };
 
 struct TcRegroup {
-    DBuf<int32_t> order;   // entry ids grouped by node
+    DBuf<int32_t> gq;      // entry payload grouped by node: query,
+    DBuf<uint64_t> gmask;  // surviving-leaf mask,
+    DBuf<float> gpath;     // path distances [*, h]
     DBuf<int4> items;      // (node, first, count, 0)
     int64_t n_items = 0;
     int64_t n_entries = 0; // entries with a surviving leaf
