@@ -86,7 +86,7 @@ typedef struct {
     int32_t precision;       /* gts_precision (L2 only) */
     int32_t result_on_device;/* 1: result arrays are device memory owned by the result */
     int64_t memory_budget;   /* bytes for intermediate frontier and candidate tables: size_GPU of the
-                                two-stage scheduler (Section 5.1, Algorithm 4); 0 = default 8 GiB */
+                                two-stage scheduler (Section 5.1, Algorithm 4); 0 = default 64 GiB */
     const int64_t *seq;      /* optional per-query sequence number (same side as the queries): query i
                                 sees the objects inserted before seq[i] and not deleted before seq[i].
                                 NULL = the current state.  Must not precede the last rebuild. */

@@ -450,7 +450,7 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
                             "query sequence number before the last rebuild or after the current state");
             qb.seq = dseq.get();
         }
-        const int64_t budget = opts && opts->memory_budget > 0 ? opts->memory_budget : ((int64_t)8 << 30);
+        const int64_t budget = opts && opts->memory_budget > 0 ? opts->memory_budget : ((int64_t)64 << 30);
         QueryOut qo;
         run_query(ix, qb, knn, opts ? opts->precision : 0, budget, qo, opts ? opts->stats : nullptr,
                   opts ? opts->stage_ms : nullptr, st);

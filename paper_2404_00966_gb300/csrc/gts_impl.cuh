@@ -169,6 +169,7 @@ struct gts_index {
     uint64_t seed = 0;
     int64_t rebuilds = 0;
     std::vector<cudaEvent_t> events;   // reused by per-stage timing
+    int64_t tc_pairs_hint[2] = {0, 0}; // last tensor-core output size per query batch (range, knn)
     ~gts_index() {
         for (auto e : events) cudaEventDestroy(e);
     }

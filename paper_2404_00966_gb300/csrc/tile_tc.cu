@@ -505,12 +505,15 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     GTS_CUDA(cudaFuncSetAttribute(k_tile_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
     // TMEM columns, and the occupancy calculator (registers)
-    int smem_sm = 0, occ = 1;
+    int smem_sm = 0, regs_sm = 0;
     GTS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tile_l2_tc, kThreads, smem));
+    GTS_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    GTS_CUDA(cudaFuncGetAttributes(&fa, k_tile_l2_tc));
     int per_sm = (int)(smem_sm / (smem + 1024));
+    const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreads;
+    if (regs_cta > 0 && per_sm > regs_sm / regs_cta) per_sm = regs_sm / regs_cta;
     if (per_sm > kMaxCtasPerSm) per_sm = kMaxCtasPerSm;
-    if (occ > 0 && per_sm > occ) per_sm = occ;
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     DBuf<int> counter(1, st), status(1, st);
