@@ -219,6 +219,31 @@ gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *
  * row-major float32; N a multiple of 32 up to 256, K in {64, 128, 192, 256}. */
 gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *D);
 
+/* Exact kNN over objects held on the device, by scanning every object, with
+ * no device memory allocated by the call.  The paper has no counterpart: it is
+ * for callers that cannot allocate while they query -- code running during a
+ * CUDA graph capture, serving threads that must never enter the device
+ * allocator (cudaMalloc may synchronise the device), hosts whose framework
+ * owns all device memory.  The work happens in a fixed 16 MiB array of device
+ * global memory that the library reserves when it is loaded (every GPU that
+ * loads the library holds it until the process exits).
+ *  objects: device float32[n * dim], row-major; object i has id i.
+ *  queries: device float32[nq * dim].  metric: GTS_L1 or GTS_L2.
+ *  k: 1 .. 32, and nq * k <= 2^20 (the array's capacity); larger calls fail
+ *     with GTS_EINVAL and do nothing.
+ *  ids, dist: device int64[nq * k], float32[nq * k]; query i's answers are at
+ *     [i * k, i * k + k) in ascending (distance, id) order, distances from the
+ *     same FP64 sums as the reference definition; when n < k the missing
+ *     slots hold id -1 and distance +inf.
+ *  stream: cudaStream_t (NULL = legacy default stream); returns when done.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. */
+gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gts_metric metric,
+                                const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
+                                void *stream);
+
 void gts_result_free(gts_result *result);
 void gts_free(gts_index *index);
 const char *gts_last_error(void);

@@ -69,7 +69,7 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
-           "gts_last_error", "gts_status_name", "gts_selftest_tc"]
+           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc"]
 
 
 def lib(path: Optional[str] = None):
@@ -93,6 +93,8 @@ def lib(path: Optional[str] = None):
     L.gts_info.argtypes = [P, ctypes.POINTER(_Info)]
     L.gts_tree_level.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     L.gts_table.argtypes = [P, P, P]
+    L.gts_knn_scan_noalloc.argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
+    L.gts_knn_scan_noalloc.restype = ctypes.c_int
     L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
     L.gts_selftest_tc.restype = ctypes.c_int
     L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]

@@ -1,0 +1,196 @@
+// Exact kNN by brute-force scan with no device allocation.
+//
+// Some callers of this library cannot allocate device memory at query time:
+// code that runs while a CUDA graph is being captured (an allocation there is
+// an error or is baked into the graph), latency-critical serving threads that
+// must not call into the allocator (cudaMalloc may synchronise the device and
+// stall every stream), and host frameworks that own all device memory through
+// their own pool and forbid any other allocator.  gts_knn_scan_noalloc serves
+// them: it answers exact kNN over an object set the caller holds on the device
+// by scanning every object, the same brute-force table scan that GTS uses for
+// its cache list, and keeps its intermediate lists in a fixed array in device
+// global memory that the library reserves once, when it is loaded.
+//
+// Scratch: a file-scope __device__ array of kScratchEntries (key, id) pairs
+// (16 MiB).  Every GPU that loads the library holds it until the process exits.
+// Every call uses the same array, so calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on it; serialise them.
+// Nothing in it has to start at zero: each call writes every entry it reads.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "gts_impl.cuh"
+#include "metric.cuh"
+
+namespace gts {
+namespace {
+
+constexpr int64_t kScratchEntries = 1 << 20;
+constexpr int kScanMaxK = 32;
+constexpr int kMaxDevices = 64;
+
+struct ScanPair {
+    double key;
+    int64_t id;
+};
+
+static __device__ __align__(256) ScanPair g_scan_scratch[kScratchEntries];
+
+__device__ __forceinline__ bool pair_less(double ka, int64_t ia, double kb, int64_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// One warp per (query, slice): every lane keeps its own ascending top-k of
+// (FP64 key, id) over the objects it scans, then the warp merges the 32 lists
+// by k rounds of argmin and writes k pairs to the scratch array (+inf padding
+// when the slice holds fewer than k objects).
+__global__ void k_scan_partial(const float *__restrict__ X, int64_t n, int dim, int l2, const float *__restrict__ Q,
+                               int64_t nq, int k, int slices, ScanPair *__restrict__ scratch) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= nq * slices) return;
+    const int64_t q = w / slices;
+    const int p = (int)(w - q * slices);
+    const int64_t o0 = n * p / slices, o1 = n * (p + 1) / slices;
+    const float *qv = Q + q * dim;
+    double kk[kScanMaxK];
+    int64_t ii[kScanMaxK];
+    int len = 0;
+    for (int64_t o = o0 + lane; o < o1; o += 32) {
+        const float *xv = X + o * dim;
+        const double key = l2 ? l2sq_fp64_seq(qv, xv, dim) : l1_fp64_seq(qv, xv, dim);
+        if (len == k && !pair_less(key, o, kk[k - 1], ii[k - 1])) continue;
+        int pos = len < k ? len : k - 1;
+        while (pos > 0 && pair_less(key, o, kk[pos - 1], ii[pos - 1])) {
+            kk[pos] = kk[pos - 1];
+            ii[pos] = ii[pos - 1];
+            --pos;
+        }
+        kk[pos] = key;
+        ii[pos] = o;
+        if (len < k) ++len;
+    }
+    ScanPair *out = scratch + w * k;
+    int head = 0;
+    for (int r = 0; r < k; ++r) {
+        double hk = head < len ? kk[head] : __longlong_as_double(0x7ff0000000000000ll);
+        int64_t hi = head < len ? ii[head] : INT64_MAX;
+        double bk = hk;
+        int64_t bi = hi;
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ok = __shfl_xor_sync(0xffffffffu, bk, off);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (pair_less(ok, oi, bk, bi)) {
+                bk = ok;
+                bi = oi;
+            }
+        }
+        if (lane == 0) out[r] = ScanPair{bk, bi};
+        if (head < len && hk == bk && hi == bi) ++head;
+    }
+}
+
+// One warp per query: merge its `slices` ascending lists of k pairs.
+__global__ void k_scan_merge(const ScanPair *__restrict__ scratch, int64_t nq, int k, int slices, int l2,
+                             int64_t *__restrict__ ids, float *__restrict__ dist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    const ScanPair *lists = scratch + q * slices * k;
+    int head = 0;   // lane s < slices owns list s
+    for (int r = 0; r < k; ++r) {
+        double hk = __longlong_as_double(0x7ff0000000000000ll);
+        int64_t hi = INT64_MAX;
+        if (lane < slices && head < k) {
+            hk = lists[lane * k + head].key;
+            hi = lists[lane * k + head].id;
+        }
+        double bk = hk;
+        int64_t bi = hi;
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ok = __shfl_xor_sync(0xffffffffu, bk, off);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (pair_less(ok, oi, bk, bi)) {
+                bk = ok;
+                bi = oi;
+            }
+        }
+        if (lane < slices && head < k && hk == bk && hi == bi && bi != INT64_MAX) ++head;
+        if (lane == 0) {
+            const bool real = bi != INT64_MAX;
+            ids[q * k + r] = real ? bi : -1;
+            dist[q * k + r] = real ? __double2float_rn(l2 ? __dsqrt_rn(bk) : bk) : __int_as_float(0x7f800000);
+        }
+    }
+}
+
+// Device address of the scratch array, fetched once per device (with that
+// device current) through cudaGetSymbolAddress: in host code the array's name
+// is only a host-side stand-in, not a device address.
+ScanPair *scratch_ptr(int dev) {
+    static std::mutex mu;
+    static ScanPair *ptrs[kMaxDevices] = {nullptr};
+    GTS_REQUIRE(dev >= 0 && dev < kMaxDevices, GTS_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        GTS_CUDA(cudaGetSymbolAddress(&p, g_scan_scratch));
+        GTS_REQUIRE(p != nullptr, GTS_ECUDA, "cudaGetSymbolAddress returned no address");
+        ptrs[dev] = (ScanPair *)p;
+    }
+    return ptrs[dev];
+}
+
+}  // namespace
+
+void knn_scan_noalloc(const float *X, int64_t n, int dim, int metric, const float *Q, int64_t nq, int k,
+                      int64_t *ids, float *dist, cudaStream_t st) {
+    GTS_REQUIRE(metric == GTS_L1 || metric == GTS_L2, GTS_EINVAL, "metric must be GTS_L1 or GTS_L2");
+    GTS_REQUIRE(k >= 1 && k <= kScanMaxK, GTS_EINVAL, "k must be in 1 .. 32");
+    GTS_REQUIRE(dim >= 1, GTS_EINVAL, "dim must be >= 1");
+    GTS_REQUIRE(n >= 0 && n < ((int64_t)1 << 31) && nq >= 0, GTS_EINVAL, "n or nq out of range");
+    GTS_REQUIRE(nq * (int64_t)k <= kScratchEntries, GTS_EINVAL,
+                "nq * k = " + std::to_string(nq * (int64_t)k) + " exceeds the fixed scratch of " +
+                    std::to_string(kScratchEntries) + " entries");
+    GTS_REQUIRE(nq == 0 || (Q && ids && dist), GTS_EINVAL, "NULL query or output pointer");
+    GTS_REQUIRE(n == 0 || X, GTS_EINVAL, "NULL object pointer");
+    if (nq == 0) return;
+    int dev = 0;
+    GTS_CUDA(cudaGetDevice(&dev));
+    ScanPair *scratch = scratch_ptr(dev);
+    // slices per query: as many as fit the scratch, up to one per warp lane
+    int64_t slices = kScratchEntries / (nq * (int64_t)k);
+    if (slices > 32) slices = 32;
+    if (slices > n) slices = n > 0 ? n : 1;
+    if (slices < 1) slices = 1;
+    const int64_t warps = nq * slices;
+    k_scan_partial<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(X, n, dim, metric == GTS_L2, Q, nq, k, (int)slices,
+                                                                scratch);
+    check_launch("scan partial");
+    k_scan_merge<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scratch, nq, k, (int)slices, metric == GTS_L2, ids, dist);
+    check_launch("scan merge");
+    GTS_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace gts
+
+extern "C" gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gts_metric metric,
+                                           const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
+                                           void *stream) {
+    try {
+        gts::knn_scan_noalloc(objects, n, dim, (int)metric, queries, nq, k, ids, dist, (cudaStream_t)stream);
+        return GTS_OK;
+    } catch (const gts::Error &e) {
+        gts::set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        gts::set_last_error(e.what());
+        return GTS_ECUDA;
+    } catch (...) {
+        gts::set_last_error("unknown internal error");
+        return GTS_ECUDA;
+    }
+}
