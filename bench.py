@@ -140,12 +140,13 @@ def algorithmic_bytes(stage: str, st: dict, dim: int, h: int, C: int) -> float:
     """Bytes the algorithm must move for one launch-set of a stage (see the
     design notes for the per-unit figures)."""
     if stage == "tile":
-        # per tile: 128 bf16 rows (dim padded to 64) + their table rows, norms and
-        # delete marks; per (query, node) entry: the FP32 query row, its path
-        # distances and metadata; per kept pair: (query, row) out
+        # per work item (a 128-row block of a last-level node): the rows as split
+        # bf16 (hi + lo), their table entries, norms and delete marks; per
+        # (query, node) entry: the query as split bf16, its path distances and
+        # metadata; per kept pair: (query, row) out
         dim_p = (dim + 63) // 64 * 64
-        return (st["tiles"] * 128 * (dim_p * 2 + h * 4 + 4 + 8)
-                + st["tile_entries"] * (dim * 4 + h * 4 + 8 + 4 + 4 + 8 + 4) + C * 8)
+        return (st["tiles"] * 128 * (4 * dim_p + h * 4 + 4 + 8)
+                + st["tile_entries"] * (4 * dim_p + h * 4 + 8 + 4 + 4 + 8 + 4) + C * 8)
     if stage == "verify":
         return C * (dim * 4 + 4 + 4 + 4)            # candidate row + (query, row) + distance out
     if stage == "leaf_scan":

@@ -121,8 +121,8 @@ enum {
     GTS_STAT_GROUPS = 6,       /* query groups run by the two-stage scheduler */
     GTS_STAT_CACHE_ROWS = 7,   /* cache-list objects compared by brute force */
     GTS_STAT_LAUNCHES = 8,     /* kernels launched by the call */
-    GTS_STAT_TILES = 9,        /* BF16 tensor-core tiles (last-level node x up to 256 queries) */
-    GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries covered by those tiles */
+    GTS_STAT_TILES = 9,        /* BF16 tensor-core work items: 128-row blocks of last-level nodes */
+    GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries run against those blocks */
     GTS_STATS_LEN = 11
 };
 

@@ -49,7 +49,7 @@ int tree_height(int64_t n, int F, int n_pivots) {
 
 size_t Tree::device_bytes() const {
     return X.bytes() + S.bytes() + Soff.bytes() + row_id.bytes() + table.bytes() + row_del.bytes() + npos.bytes() +
-           nsize.bytes() + npiv.bytes() + nlo.bytes() + nhi.bytes() + tc.Xb.bytes() + tc.xn2.bytes() + tc.cent.bytes();
+           nsize.bytes() + npiv.bytes() + nlo.bytes() + nhi.bytes() + tc.Xh.bytes() + tc.Xl.bytes() + tc.xn2.bytes();
 }
 
 namespace {

@@ -114,15 +114,15 @@ struct Objects {           // a view of caller-provided or library objects
     int max_len = 0;       // longest string (strings only)
 };
 
-// Tensor-core copy of the tree rows (built on the first BF16 query):
-// rows centred on their last-level node's centroid, rounded to bf16, padded
-// to a multiple of 64 columns; their squared norms; the TMA descriptor.
+// Tensor-core copy of the tree rows (built on the first BF16 query): every
+// row split into bf16 hi / lo parts (x = x_hi + x_lo to 2^-16), padded to a
+// multiple of 64 columns; the squared norms; the two TMA descriptors.
 struct TcCache {
     bool ready = false;
     int dim_p = 0;
-    DBuf<uint8_t> Xb;
-    DBuf<float> xn2, cent;
-    CUtensorMap map;
+    DBuf<uint8_t> Xh, Xl;
+    DBuf<float> xn2;
+    CUtensorMap map_h, map_l;
 };
 
 struct Tree {

@@ -406,6 +406,59 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
     }
 }
 
+// Last pivot level, tensor-core path: one pass per entry computes d(q, pivot)
+// (query kept in registers across the query's consecutive entries), tests the
+// node's leaf children against [d - t, d + t] (Lemma 1 / 2) into a bit mask,
+// and counts the entries with a surviving leaf per node for the regrouping.
+template <bool L2, int NV>
+__global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                                 int64_t lvl_base, int64_t lvl_next, int64_t e0, int64_t e1,
+                                 float *__restrict__ path, int l, const float *__restrict__ thr_q,
+                                 uint64_t *__restrict__ mask_out, int32_t *__restrict__ ncount) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float4 qr[NV > 0 ? NV : 1];
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e0 + w * kPivGroup < e1; w += nw) {
+        const int64_t a0 = e0 + w * kPivGroup;
+        const int64_t a1 = a0 + kPivGroup < e1 ? a0 + kPivGroup : e1;
+        int32_t cur = -1;
+        const float *qv = nullptr;
+        float thr = 0.f;
+        for (int64_t e = a0; e < a1; ++e) {
+            const int32_t q = eq[e];
+            if (q != cur) {
+                cur = q;
+                qv = d.Q + (int64_t)q * d.dim;
+                thr = thr_q[q];
+                if (NV > 0) {
+                    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+#pragma unroll
+                    for (int v = 0; v < (NV > 0 ? NV : 1); ++v) qr[v] = q4[v * 32 + lane];
+                }
+            }
+            const int32_t node = enode[e];
+            const int32_t prow = d.npiv[lvl_base + node];
+            const float sq = row_dist_regs<L2, NV>(qr, d.X + (int64_t)prow * d.dim, qv, d.dim, lane);
+            const float dq = L2 ? sqrtf(sq) : sq;
+            uint64_t m = 0;
+            for (int j0 = 0; j0 < d.F; j0 += 32) {
+                const int j = j0 + lane;
+                bool keep = false;
+                if (j < d.F) {
+                    const int64_t c = lvl_next + (int64_t)node * d.F + j;
+                    keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+                }
+                m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
+            }
+            if (lane == 0) {
+                path[e * d.h + l] = dq;
+                mask_out[e - e0] = m;
+                if (m) atomicAdd(&ncount[node], 1);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- leaf scan
 
 // Warp per last-level entry: rows of the entry's node, in 32-row strips; a
@@ -1085,6 +1138,10 @@ struct Runner {
 
     void process(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
+        if (use_tc && l == h - 1) {
+            last_level_tc(L, e0, e1, l);
+            return;
+        }
         pivdist(L, e0, e1, l);
         const int64_t E = e1 - e0;
         const int64_t lvl_next = ix->tree.lvl_off[l + 1];
@@ -1168,12 +1225,53 @@ struct Runner {
         }
     }
 
+    // Last pivot level on the tensor-core path: the fused pass computes the
+    // pivot distances, the leaf masks and the per-node counts; the threshold
+    // list then takes this level's pivots (kNN); the tiles follow.
+    void last_level_tc(Level &L, int64_t e0, int64_t e1, int l) {
+        const int64_t E = e1 - e0;
+        const int64_t base = ix->tree.lvl_off[l], lvl_next = ix->tree.lvl_off[l + 1];
+        const int64_t nn = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
+        DBuf<uint64_t> mask(E, st);
+        DBuf<int32_t> ncount(nn, st);
+        GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
+        const bool aligned = ((uintptr_t)d.Q & 15) == 0;
+        const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
+        const unsigned grid = cap(nblocks((E + kPivGroup - 1) / kPivGroup, kWarpsPerBlock));
+        clk.begin(GTS_STAGE_PIVOT_DIST);
+#define GTS_LL(NVV)                                                                                       \
+    k_last_level_vec<true, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, lvl_next, e0, e1, \
+                                                    L.path.get(), l, thr.get(), mask.get(), ncount.get())
+        switch (nv) {
+            case 1: GTS_LL(1); break;
+            case 2: GTS_LL(2); break;
+            case 3: GTS_LL(3); break;
+            case 4: GTS_LL(4); break;
+            default: GTS_LL(0); break;
+        }
+#undef GTS_LL
+        clk.end();
+        check_launch("last level");
+        st_pivots += E;
+        st_frontier += E;
+        if (knn) {
+            clk.begin(GTS_STAGE_THRESHOLD);
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+                                                                      L.path.get(), l, qb.nq, qb.k, koff.get(),
+                                                                      tk_d.get(), tk_id.get(), tk_n.get(), thr.get());
+            clk.end();
+            check_launch("knn threshold");
+        }
+        tc_leaf(L, e0, e1, mask, &ncount);
+    }
+
     // Last level on the tensor cores: regroup the entries by node, run the
     // tiles (leaf scan + bf16 distance prefilter), then finish the kept pairs
     // with the FP32 distance and its FP64 boundary recheck.
-    void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask) {
+    void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
         TcQuery tq;
         tq.E = e1 - e0;
+        tq.nq = qb.nq;
         tq.eq = L.q.get() + e0;
         tq.enode = L.node.get() + e0;
         tq.path = L.path.get() + e0 * h;
@@ -1184,8 +1282,8 @@ struct Runner {
         tq.epsc = d.epsc;
         tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
         TcRegroup rg;
-        clk.begin(GTS_STAGE_OTHER, 7);
-        tc_regroup(ix->tree, tq, rg, st);
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr);
         clk.end();
         st_tiles += rg.n_items;
         st_tile_entries += rg.n_entries;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "gts_impl.cuh"
 
@@ -11,13 +12,13 @@ namespace gts {
 struct TileArgs {
     int dim, dim_p, F, h;
     int64_t n;
-    const float *cent;        // centroids of the last-level nodes [nodes, dim]
-    const float *xn2;         // |x^|^2 of every row (bf16 centred row)
+    const float *xn2;         // |x|^2 of every row (FP64 sum, rounded)
     const float *table;       // [h, n]
     const int64_t *row_del;
     const int32_t *npos, *nsize;
     int64_t lvl_last;         // first node of the last pivot level
-    const float *Q;
+    const __nv_bfloat16 *Qh, *Ql;   // the batch's queries, split bf16 [nq, dim_p]
+    const float *qn2;               // |q|^2
     const int64_t *qseq;
     const float *thr;
     const int32_t *gq;        // entries of the last pivot level regrouped by node: query,
@@ -30,12 +31,13 @@ struct TileArgs {
     int64_t cap;
     unsigned long long *out_count;
     int *status;
-    float epsc, gK;
+    float epsc, cE1, cE2;     // pruning slack; error-bound coefficients
     int any_deleted;          // 0: no row has a delete mark, skip the visibility test
 };
 
 struct TcQuery {
     int64_t E = 0;
+    int64_t nq = 0;
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;
@@ -53,12 +55,15 @@ struct TcRegroup {
     DBuf<int4> items;      // (node, first, count, 0)
     int64_t n_items = 0;
     int64_t n_entries = 0; // entries with a surviving leaf
+    int64_t n_chunks = 0;  // query chunks over all blocks (tensor-core tiles)
 };
 
 bool tc_supported(const Tree &t);
 void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
 // regroup the last-level entries by node into tiles; returns the tile count
-int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st);
+// counts: entries with a surviving leaf per last-level node, if already known
+int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st,
+                   const int32_t *counts = nullptr);
 // run the tiles; returns the number of (query, row) pairs written to out_q/out_row
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
