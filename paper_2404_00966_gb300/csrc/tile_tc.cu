@@ -43,9 +43,9 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node block
-constexpr int kNQ = 64;        // MMA N: queries of one chunk
-constexpr int kThreads = 256;  // 8 warps
-constexpr int kTmemCols = 64;  // FP32 accumulator: 128 lanes x kNQ columns
+constexpr int kNQ = 128;       // MMA N: queries of one chunk
+constexpr int kThreads = 512;  // 16 warps: 4 TMEM lane quadrants x 4 groups of 32 columns
+constexpr int kTmemCols = 256; // two FP32 accumulators of 128 lanes x kNQ columns
 constexpr int kMaxCtasPerSm = 512 / kTmemCols;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -100,6 +100,47 @@ __global__ void k_split_rows(const float *__restrict__ X, int dim, int dim_p, in
 
 // ---------------------------------------------------------------- the tile kernel
 
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+struct ChunkMeta {           // one buffer of per-query data of a chunk
+    uint64_t *mask;          // kNQ surviving-leaf masks
+    int64_t *seq;            // kNQ sequence numbers
+    float4 *q;               // kNQ (|q|^2, |q|, thr, id)
+    float *path;             // kNQ x h
+};
+
+// Stage chunk [start, start + cnt) of a block's queries: per-query data by
+// plain loads (one thread per query), the split bf16 rows by cp.async (four
+// threads per query, 16 bytes per copy, into the 128-byte swizzled layout).
+__device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, ChunkMeta m, uint8_t *sBh,
+                                            uint8_t *sBl, int chunks16) {
+    const int tid = threadIdx.x;
+    for (int j = tid; j < cnt; j += kThreads) {
+        const int32_t q = a.gq[start + j];
+        m.mask[j] = a.gmask[start + j];
+        m.seq[j] = a.qseq[q];
+        const float qn2 = a.qn2[q];
+        m.q[j] = make_float4(qn2, sqrtf(qn2) * (1.f + 1e-6f), a.thr[q], __int_as_float(q));
+    }
+    for (int t = tid; t < cnt * a.h; t += kThreads) m.path[t] = a.gpath[(int64_t)start * a.h + t];
+    const int per_q = 2 * chunks16;                  // 16-byte copies per query (hi and lo)
+    const int tpq = kThreads / kNQ;                  // threads per query
+    for (int j = tid / tpq; j < cnt; j += kThreads / tpq) {
+        const int32_t q = a.gq[start + j];
+        for (int c = tid % tpq; c < per_q; c += tpq) {
+            const int comp = c / chunks16, k16 = c - comp * chunks16;
+            const __nv_bfloat16 *src = (comp ? a.Ql : a.Qh) + (int64_t)q * a.dim_p + k16 * 8;
+            uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (kNQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
+            cp_async16(dst, src);
+        }
+    }
+    cp_async_commit();
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l, TileArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -108,23 +149,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int apanel = kRows * 128, bpanel = kNQ * 128;
     uint8_t *sAh = smem;                                    // panels x 128 rows x 128 B
     uint8_t *sAl = sAh + panels * apanel;
-    uint8_t *sBh = sAl + panels * apanel;                   // panels x kNQ rows x 128 B
-    uint8_t *sBl = sBh + panels * bpanel;
-    uint64_t *smask = (uint64_t *)(sBl + panels * bpanel);  // kNQ surviving-leaf masks
-    int64_t *sseq = (int64_t *)(smask + kNQ);               // kNQ sequence numbers
-    float4 *sq = (float4 *)(sseq + kNQ);                    // kNQ (|q|^2, |q|, thr, id)
-    float *spath = (float *)(sq + kNQ);                     // kNQ x h
-    uint64_t *bars = (uint64_t *)(((uintptr_t)(spath + kNQ * a.h) + 15) & ~(uintptr_t)15);
-    uint32_t *tslot = (uint32_t *)(bars + 2);
+    uint8_t *sB = sAl + panels * apanel;                    // 2 buffers x (hi, lo) x panels x kNQ x 128 B
+    const int bbuf = 2 * panels * bpanel;                   // bytes of one (hi, lo) buffer
+    uint8_t *mbase = sB + 2 * bbuf;
+    const int mbytes = kNQ * (8 + 8 + 16) + ((kNQ * a.h * 4 + 15) / 16) * 16;   // one metadata buffer
+    auto metab = [&](int b) {
+        uint8_t *mp = mbase + b * mbytes;
+        ChunkMeta m;
+        m.mask = (uint64_t *)mp;
+        m.seq = (int64_t *)(mp + kNQ * 8);
+        m.q = (float4 *)(mp + kNQ * 16);
+        m.path = (float *)(mp + kNQ * 32);
+        return m;
+    };
+    uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
+    uint32_t *tslot = (uint32_t *)(bars + 3);
     int *sitem = (int *)(tslot + 1);
     int *sabort = sitem + 1;
-    uint32_t *sphase = (uint32_t *)(sabort + 1);   // phases of the waits that gave up
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
     if (tid == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
+        for (int i = 0; i < 3; ++i) tc::mbar_init(&bars[i], 1);
         tc::mbar_fence_init();
         *sabort = 0;
     }
@@ -134,7 +180,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tslot;
     const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
     const int chunks16 = a.dim_p / 8;                       // 16-byte chunks per bf16 row
-    uint32_t ptma = 0, pmma = 0;                             // barrier phases
+    uint32_t ptma = 0, pmma[2] = {0, 0};                     // barrier phases
+    const int quad = warp & 3, cgrp = warp >> 2;             // TMEM lane quadrant, 32-column group
     for (;;) {
         if (tid == 0) *sitem = atomicAdd(a.work_counter, 1);
         __syncthreads();
@@ -154,7 +201,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         // ---- per-row constants of this block (thread = TMEM lane of its warp quadrant)
-        const int quad = warp & 3, half = warp >> 2;
         const int r = quad * 32 + lane;
         const int nrow = size - rb;
         const bool valid = r < nrow;
@@ -178,94 +224,79 @@ __global__ void __launch_bounds__(kThreads, 1)
             xn = sqrtf(xn2) * (1.f + 1e-6f);
             if (a.any_deleted) rdel = a.row_del[row];
         }
-        bool a_ready = false;
-        for (int c0 = 0; c0 < total; c0 += kNQ) {
-            const int cnt = total - c0 < kNQ ? total - c0 : kNQ;
-            const int start = first + c0;
-            // ---- chunk metadata, one thread per query
-            for (int j = tid; j < cnt; j += kThreads) {
-                const int32_t q = a.gq[start + j];
-                smask[j] = a.gmask[start + j];
-                sseq[j] = a.qseq[q];
-                const float qn2 = a.qn2[q];
-                sq[j] = make_float4(qn2, sqrtf(qn2) * (1.f + 1e-6f), a.thr[q], __int_as_float(q));
-            }
-            for (int t = tid; t < cnt * a.h; t += kThreads) spath[t] = a.gpath[(int64_t)start * a.h + t];
-            __syncthreads();
-            // ---- chunk queries: split bf16 rows copied into the swizzled layout
-            for (int t = tid; t < cnt * 2 * chunks16; t += kThreads) {
-                const int j = t / (2 * chunks16);
-                const int rem = t - j * 2 * chunks16;
-                const int comp = rem / chunks16, k16 = rem - comp * chunks16;
-                const int32_t q = __float_as_int(sq[j].w);
-                const uint4 v = *reinterpret_cast<const uint4 *>((comp ? a.Ql : a.Qh) + (int64_t)q * a.dim_p + k16 * 8);
-                uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * bpanel + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
-                *reinterpret_cast<uint4 *>(dst) = v;
-            }
+        const int nchunks = (total + kNQ - 1) / kNQ;
+        stage_chunk(a, first, total < kNQ ? total : kNQ, metab(0), sB, sB + panels * bpanel, chunks16);
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            const int cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
+            cp_async_wait_all();
             tc::fence_proxy_async_smem();
             __syncthreads();
-            // ---- MMA: one thread, three products per k-step
+            // ---- MMA of chunk c into accumulator b: one thread, three products per k-step
             if (tid == 0) {
                 bool ok = true;
-                if (!a_ready) {
+                if (c == 0) {
                     ok = tc::mbar_wait(&bars[0], ptma);
                     if (!ok) {
                         *sabort = 1;
-                        sphase[0] = ptma;
                         atomicExch(a.status, 1);
                     }
                 }
                 if (ok) {
                     tc::tc_fence_after();
                     const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-                    const uint32_t bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+                    const uint32_t bh = tc::smem_u32(sB + b * bbuf), bl = bh + panels * bpanel;
+                    const uint32_t dt = tmem + (uint32_t)(b * kNQ);
                     const int ksteps = a.dim_p / 16;
                     for (int s = 0; s < ksteps; ++s) {
                         const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
-                        tc::mma_bf16(tmem, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
-                        tc::mma_bf16(tmem, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
-                        tc::mma_bf16(tmem, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+                        tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
+                        tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
+                        tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
                     }
-                    tc::mma_commit(&bars[1]);
+                    tc::mma_commit(&bars[1 + b]);
                 }
             }
-            __syncthreads();
-            if (*sabort) break;
-            if (!a_ready) {
-                a_ready = true;
-                ptma ^= 1u;
+            if (c == 0) ptma ^= 1u;
+            // ---- stage chunk c + 1 into the other buffers while the MMA runs
+            if (c + 1 < nchunks) {
+                const int cn = total - (c + 1) * kNQ < kNQ ? total - (c + 1) * kNQ : kNQ;
+                stage_chunk(a, first + (c + 1) * kNQ, cn, metab(b ^ 1), sB + (b ^ 1) * bbuf,
+                            sB + (b ^ 1) * bbuf + panels * bpanel, chunks16);
             }
-            // ---- epilogue: warp w reads lanes 32 (w % 4) .. +32, columns 32 (w / 4) .. +32
-            if (!tc::mbar_wait(&bars[1], pmma)) {
+            // ---- epilogue of chunk c
+            if (*sabort) break;
+            if (!tc::mbar_wait(&bars[1 + b], pmma[b])) {
                 *sabort = 1;
-                sphase[1] = pmma;
                 atomicExch(a.status, 2);
             }
+            pmma[b] ^= 1u;
             tc::tc_fence_after();
-            const int cc = half * 32;
+            const int cc = cgrp * 32;
             if (cc < cnt) {
+                const ChunkMeta m = metab(b);
                 uint32_t v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cc, v);
+                tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kNQ + cc), v);
                 tc::tmem_ld_wait();
                 uint32_t passbits = 0;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int j = cc + i;
                     if (j >= cnt) break;
-                    const uint64_t m = smask[j];
-                    if ((m & wmask) == 0) continue;   // warp-uniform
-                    if (!valid || !((m >> jl) & 1ull)) continue;
-                    const float4 qm = sq[j];
+                    const uint64_t mk = m.mask[j];
+                    if ((mk & wmask) == 0) continue;   // warp-uniform
+                    if (!valid || !((mk >> jl) & 1ull)) continue;
+                    const float4 qm = m.q[j];
                     const float d2 = fmaf(-2.f, __uint_as_float(v[i]), qm.x + xn2);
                     const float sn = qm.y + xn;
                     const float E = fmaf(a.cE1 * qm.y, xn, a.cE2 * sn * sn);
                     const float t = qm.z * 1.0000039f;
                     if (d2 > fmaf(t, t, E)) continue;
-                    if (rdel <= sseq[j]) continue;
+                    if (rdel <= m.seq[j]) continue;
                     bool ok = true;
                     for (int l = 0; l < a.h && ok; ++l) {
                         const float T = a.table[(int64_t)l * a.n + row];
-                        const float pl = spath[j * a.h + l];
+                        const float pl = m.path[j * a.h + l];
                         const float eps = a.epsc * (T + pl + qm.z);
                         if (fabsf(T - pl) > qm.z + eps) ok = false;
                     }
@@ -287,34 +318,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int i = __ffs(passbits) - 1;
                         passbits &= passbits - 1;
                         if ((int64_t)o < a.cap) {
-                            a.out_q[o] = __float_as_int(sq[cc + i].w);
+                            a.out_q[o] = __float_as_int(m.q[cc + i].w);
                             a.out_row[o] = (int32_t)row;
                         }
                         ++o;
                     }
                 }
             }
-            pmma ^= 1u;
             tc::tc_fence_before();
-            __syncthreads();
         }
+        cp_async_wait_all();
+        __syncthreads();
         if (*sabort) break;
-        if (!a_ready) {   // a block with no query chunk (cannot happen): retire its TMA
-            if (tid == 0 && !tc::mbar_wait(&bars[0], ptma)) {
-                *sabort = 1;
-                sphase[0] = ptma;
-                atomicExch(a.status, 1);
-            }
-            ptma ^= 1u;
-            __syncthreads();
-        }
     }
     __syncthreads();
+    cp_async_wait_all();
     if (*sabort && tid == 0) {
         // let a TMA or MMA still in flight finish (bounded) before the
         // shared memory and the TMEM columns are released
         tc::mbar_wait(&bars[0], ptma);
-        tc::mbar_wait(&bars[1], pmma);
+        tc::mbar_wait(&bars[1], pmma[0]);
+        tc::mbar_wait(&bars[2], pmma[1]);
     }
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
@@ -388,9 +412,9 @@ inline unsigned nblk(int64_t n, int per = 256) {
 size_t tile_smem_bytes(int dim_p, int h) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
-    b += (size_t)2 * panels * kRows * 128 + (size_t)2 * panels * kNQ * 128;
-    b += (size_t)kNQ * (8 + 8 + 16) + sizeof(float) * kNQ * h;
-    b += 16 + 16 + 16 + 16 + 16 + 16;
+    b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
+    b += 2 * ((size_t)kNQ * (8 + 8 + 16) + (((size_t)kNQ * h * 4 + 15) / 16) * 16);
+    b += 3 * 8 + 4 + 4 + 4 + 16;
     return b;
 }
 
