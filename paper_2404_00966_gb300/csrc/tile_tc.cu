@@ -43,10 +43,12 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node block
-constexpr int kNQ = 128;       // MMA N: queries of one chunk
 constexpr int kThreads = 512;  // 16 warps: 4 TMEM lane quadrants x 4 groups of 32 columns
-constexpr int kTmemCols = 256; // two FP32 accumulators of 128 lanes x kNQ columns
-constexpr int kMaxCtasPerSm = 512 / kTmemCols;
+// MMA N (queries per chunk) is a template parameter NQ: 128 up to 128
+// columns, 64 up to 192, 32 up to 256, so that the node block (A, hi and lo)
+// and two chunk buffers (B, hi and lo) fit in shared memory.  TMEM holds two
+// FP32 accumulators of 128 lanes x NQ columns.
+inline int nq_for(int dim_p) { return dim_p <= 128 ? 128 : dim_p <= 192 ? 64 : 32; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -116,6 +118,7 @@ struct ChunkMeta {           // one buffer of per-query data of a chunk
 // Stage chunk [start, start + cnt) of a block's queries: per-query data by
 // plain loads (one thread per query), the split bf16 rows by cp.async (four
 // threads per query, 16 bytes per copy, into the 128-byte swizzled layout).
+template <int NQ>
 __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, ChunkMeta m, uint8_t *sBh,
                                             uint8_t *sBl, int chunks16) {
     const int tid = threadIdx.x;
@@ -128,21 +131,24 @@ __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cn
     }
     for (int t = tid; t < cnt * a.h; t += kThreads) m.path[t] = a.gpath[(int64_t)start * a.h + t];
     const int per_q = 2 * chunks16;                  // 16-byte copies per query (hi and lo)
-    const int tpq = kThreads / kNQ;                  // threads per query
+    const int tpq = kThreads / NQ;                  // threads per query
     for (int j = tid / tpq; j < cnt; j += kThreads / tpq) {
         const int32_t q = a.gq[start + j];
         for (int c = tid % tpq; c < per_q; c += tpq) {
             const int comp = c / chunks16, k16 = c - comp * chunks16;
             const __nv_bfloat16 *src = (comp ? a.Ql : a.Qh) + (int64_t)q * a.dim_p + k16 * 8;
-            uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (kNQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
+            uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (NQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
             cp_async16(dst, src);
         }
     }
     cp_async_commit();
 }
 
+template <int NQ>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l, TileArgs a) {
+    constexpr int kNQ = NQ;
+    constexpr int kTmemCols = 2 * NQ;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int panels = a.dim_p / 64;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (a.any_deleted) rdel = a.row_del[row];
         }
         const int nchunks = (total + kNQ - 1) / kNQ;
-        stage_chunk(a, first, total < kNQ ? total : kNQ, metab(0), sB, sB + panels * bpanel, chunks16);
+        stage_chunk<NQ>(a, first, total < kNQ ? total : kNQ, metab(0), sB, sB + panels * bpanel, chunks16);
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             const int cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---- stage chunk c + 1 into the other buffers while the MMA runs
             if (c + 1 < nchunks) {
                 const int cn = total - (c + 1) * kNQ < kNQ ? total - (c + 1) * kNQ : kNQ;
-                stage_chunk(a, first + (c + 1) * kNQ, cn, metab(b ^ 1), sB + (b ^ 1) * bbuf,
+                stage_chunk<NQ>(a, first + (c + 1) * kNQ, cn, metab(b ^ 1), sB + (b ^ 1) * bbuf,
                             sB + (b ^ 1) * bbuf + panels * bpanel, chunks16);
             }
             // ---- epilogue of chunk c
@@ -409,7 +415,7 @@ inline unsigned nblk(int64_t n, int per = 256) {
     return (unsigned)b;
 }
 
-size_t tile_smem_bytes(int dim_p, int h) {
+size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
@@ -467,7 +473,7 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     GTS_CUDA(cudaStreamSynchronize(st));
     rg.n_items = total_items;
     rg.n_entries = total_entries;
-    rg.n_chunks = (total_entries + kNQ - 1) / kNQ;
+    rg.n_chunks = (total_entries + 127) / 128;
     if (total_items > 0) {
         rg.items.alloc(total_items, st);
         k_fill_items<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, noff.get(), ioff.get(), nn, rg.items.get());
@@ -490,19 +496,21 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int dev = 0, sms = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = tile_smem_bytes(c.dim_p, t.h);
-    GTS_CUDA(cudaFuncSetAttribute(k_tile_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int nq_chunk = nq_for(c.dim_p);
+    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk);
+    auto kern = nq_chunk == 128 ? k_tile_l2_tc<128> : nq_chunk == 64 ? k_tile_l2_tc<64> : k_tile_l2_tc<32>;
+    GTS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
     // TMEM columns, and registers
     int smem_sm = 0, regs_sm = 0;
     GTS_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     GTS_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
     cudaFuncAttributes fa;
-    GTS_CUDA(cudaFuncGetAttributes(&fa, k_tile_l2_tc));
+    GTS_CUDA(cudaFuncGetAttributes(&fa, kern));
     int per_sm = (int)(smem_sm / (smem + 1024));
     const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreads;
     if (regs_cta > 0 && per_sm > regs_sm / regs_cta) per_sm = regs_sm / regs_cta;
-    if (per_sm > kMaxCtasPerSm) per_sm = kMaxCtasPerSm;
+    if (per_sm > 512 / (2 * nq_chunk)) per_sm = 512 / (2 * nq_chunk);   // TMEM columns
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     DBuf<int> counter(1, st), status(1, st);
@@ -552,7 +560,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.cE1 = cE1;
         a.cE2 = cE2;
         a.any_deleted = tq.any_deleted;
-        k_tile_l2_tc<<<(unsigned)grid, kThreads, smem, st>>>(c.map_h, c.map_l, a);
+        kern<<<(unsigned)grid, kThreads, smem, st>>>(c.map_h, c.map_l, a);
         ++*launches;
         check_launch("tensor-core tile");
         unsigned long long hcount = 0;
