@@ -272,12 +272,15 @@ struct LevelOffsets {
     int64_t v[kMaxHeight + 2];
 };
 
+constexpr int kProbeNodes = 4;   // last-level nodes whose rows the kNN probe evaluates
+
 // Probe for kNN (warp per query).  Section 3 notes that MkNNQ(q, k) is
 // MRQ(q, d_k) once d_k is known; the probe bounds d_k from above before the
 // batched descent.  It follows one root-to-last-level path: at every level it
 // computes the distances from q to the pivots of all non-empty children and
-// descends into the child whose pivot is nearest, then computes the distances
-// to up to `cap` rows of the last-level node reached.  Every visible object so
+// descends into the child whose pivot is nearest; at the last pivot level it
+// computes the distances to the rows (up to `cap` in all) of the kProbeNodes
+// nodes with the nearest pivots.  Every visible object so
 // evaluated enters the query's threshold list, so tau_q starts at (an upper
 // bound of) the k-th smallest of them instead of +inf.
 template <bool L2>
@@ -313,8 +316,14 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
         }
     }
     for (int l = 1; l < d.h; ++l) {
-        float best = __int_as_float(0x7f800000);
-        int64_t bnode = -1;
+        // the kProbeNodes children with the nearest pivots (ascending), kept by every lane
+        float bd[kProbeNodes];
+        int64_t bn[kProbeNodes];
+#pragma unroll
+        for (int i = 0; i < kProbeNodes; ++i) {
+            bd[i] = __int_as_float(0x7f800000);
+            bn[i] = -1;
+        }
         for (int j = 0; j < d.F; ++j) {
             const int64_t c = node * d.F + j;
             const int64_t g = lo_off.v[l] + c;
@@ -324,23 +333,41 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             const float dq = L2 ? sqrtf(sq) : sq;
             if (lane == 0 && d.row_del[prow] > s)
                 tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
-            if (dq < best) {
-                best = dq;
-                bnode = c;
+            if (dq < bd[kProbeNodes - 1]) {
+                float vd = dq;
+                int64_t vn = c;
+#pragma unroll
+                for (int i = 0; i < kProbeNodes; ++i) {
+                    if (vd < bd[i]) {
+                        const float td = bd[i];
+                        const int64_t tn = bn[i];
+                        bd[i] = vd;
+                        bn[i] = vn;
+                        vd = td;
+                        vn = tn;
+                    }
+                }
             }
         }
-        if (bnode < 0) break;   // no non-empty child (cannot happen for a non-empty node)
-        node = bnode;
+        if (bn[0] < 0) break;   // no non-empty child (cannot happen for a non-empty node)
+        node = bn[0];
         if (l == d.h - 1) {
-            const int64_t g = lo_off.v[l] + node;
-            const int32_t pos = d.npos[g];
-            const int32_t m = d.nsize[g] < cap ? d.nsize[g] : cap;
-            for (int32_t r = 0; r < m; ++r) {
-                const int64_t row = pos + r;
-                const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
-                const float dv = L2 ? sqrtf(sq) : sq;
-                if (lane == 0 && d.row_del[row] > s)
-                    tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
+            // last pivot level: the rows of the nearest kProbeNodes nodes
+            int budget = cap;
+#pragma unroll
+            for (int i = 0; i < kProbeNodes; ++i) {
+                if (bn[i] < 0 || budget <= 0) continue;
+                const int64_t g = lo_off.v[l] + bn[i];
+                const int32_t pos = d.npos[g];
+                const int32_t m = d.nsize[g] < budget ? d.nsize[g] : budget;
+                budget -= m;
+                for (int32_t r = 0; r < m; ++r) {
+                    const int64_t row = pos + r;
+                    const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
+                    const float dv = L2 ? sqrtf(sq) : sq;
+                    if (lane == 0 && d.row_del[row] > s)
+                        tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
+                }
             }
         }
     }
@@ -1030,6 +1057,8 @@ struct Runner {
     int64_t st_tiles = 0, st_tile_entries = 0;
     StageClock clk;
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
+    DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
+    DBuf<float> tcqn2;
 
     Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
         : ix(i), qb(b), knn(k), budget(bud), st(s) {
@@ -1272,6 +1301,9 @@ struct Runner {
         TcQuery tq;
         tq.E = e1 - e0;
         tq.nq = qb.nq;
+        tq.Qh = (const __nv_bfloat16 *)tcQh.get();
+        tq.Ql = (const __nv_bfloat16 *)tcQl.get();
+        tq.qn2 = tcqn2.get();
         tq.eq = L.q.get() + e0;
         tq.enode = L.node.get() + e0;
         tq.path = L.path.get() + e0 * h;
@@ -1449,6 +1481,9 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     if (precision == GTS_PREC_BF16 && tc_supported(t)) {
         tc_prepare(t, t.tc, st);
         R.use_tc = true;
+        R.clk.begin(GTS_STAGE_OTHER);
+        tc_split_queries(qb.Q, nq, t.dim, t.tc.dim_p, R.tcQh, R.tcQl, R.tcqn2, st);
+        R.clk.end();
     }
     R.h = t.h;
     R.F = t.F;
@@ -1522,7 +1557,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     if (knn && t.n > 0 && nq > 0 && t.dim > 0) {
         LevelOffsets lo_off;
         for (int l = 0; l <= t.h && l < kMaxHeight + 2; ++l) lo_off.v[l] = t.lvl_off[l];
-        const int cap = 512;
+        const int cap = 1024;
         R.clk.begin(GTS_STAGE_THRESHOLD);
         if (t.metric == GTS_L2)
             k_probe_vec<true><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),

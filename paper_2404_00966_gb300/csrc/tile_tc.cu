@@ -109,29 +109,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 struct ChunkMeta {           // one buffer of per-query data of a chunk
-    uint64_t *mask;          // kNQ surviving-leaf masks
-    int64_t *seq;            // kNQ sequence numbers
-    float4 *q;               // kNQ (|q|^2, |q|, thr, id)
-    float *path;             // kNQ x h
+    TileRec *rec;            // NQ records
+    float *path;             // NQ x hp
 };
 
-// Stage chunk [start, start + cnt) of a block's queries: per-query data by
-// plain loads (one thread per query), the split bf16 rows by cp.async (four
-// threads per query, 16 bytes per copy, into the 128-byte swizzled layout).
+// Stage chunk [start, start + cnt) of a block's queries with asynchronous
+// copies only: the records and path distances (contiguous, node-major), and
+// the split bf16 query rows into the 128-byte swizzled layout (each thread
+// first reads the query ids of the rows it copies).
 template <int NQ>
 __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, ChunkMeta m, uint8_t *sBh,
                                             uint8_t *sBl, int chunks16) {
     const int tid = threadIdx.x;
-    for (int j = tid; j < cnt; j += kThreads) {
-        const int32_t q = a.gq[start + j];
-        m.mask[j] = a.gmask[start + j];
-        m.seq[j] = a.qseq[q];
-        const float qn2 = a.qn2[q];
-        m.q[j] = make_float4(qn2, sqrtf(qn2) * (1.f + 1e-6f), a.thr[q], __int_as_float(q));
-    }
-    for (int t = tid; t < cnt * a.h; t += kThreads) m.path[t] = a.gpath[(int64_t)start * a.h + t];
+    const uint8_t *rsrc = reinterpret_cast<const uint8_t *>(a.grec + start);
+    for (int t = tid; t < cnt * 2; t += kThreads) cp_async16(reinterpret_cast<uint8_t *>(m.rec) + t * 16, rsrc + t * 16);
+    const uint8_t *psrc = reinterpret_cast<const uint8_t *>(a.gpath + (int64_t)start * a.hp);
+    const int pch = cnt * a.hp / 4;
+    for (int t = tid; t < pch; t += kThreads) cp_async16(reinterpret_cast<uint8_t *>(m.path) + t * 16, psrc + t * 16);
     const int per_q = 2 * chunks16;                  // 16-byte copies per query (hi and lo)
-    const int tpq = kThreads / NQ;                  // threads per query
+    const int tpq = kThreads / NQ;                   // threads per query
     for (int j = tid / tpq; j < cnt; j += kThreads / tpq) {
         const int32_t q = a.gq[start + j];
         for (int c = tid % tpq; c < per_q; c += tpq) {
@@ -158,14 +154,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sB = sAl + panels * apanel;                    // 2 buffers x (hi, lo) x panels x kNQ x 128 B
     const int bbuf = 2 * panels * bpanel;                   // bytes of one (hi, lo) buffer
     uint8_t *mbase = sB + 2 * bbuf;
-    const int mbytes = kNQ * (8 + 8 + 16) + ((kNQ * a.h * 4 + 15) / 16) * 16;   // one metadata buffer
+    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4;   // one metadata buffer
     auto metab = [&](int b) {
         uint8_t *mp = mbase + b * mbytes;
         ChunkMeta m;
-        m.mask = (uint64_t *)mp;
-        m.seq = (int64_t *)(mp + kNQ * 8);
-        m.q = (float4 *)(mp + kNQ * 16);
-        m.path = (float *)(mp + kNQ * 32);
+        m.rec = (TileRec *)mp;
+        m.path = (float *)(mp + kNQ * sizeof(TileRec));
         return m;
     };
     uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
@@ -289,22 +283,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 32; ++i) {
                     const int j = cc + i;
                     if (j >= cnt) break;
-                    const uint64_t mk = m.mask[j];
+                    const TileRec &rc = m.rec[j];
+                    const uint64_t mk = rc.mask;
                     if ((mk & wmask) == 0) continue;   // warp-uniform
                     if (!valid || !((mk >> jl) & 1ull)) continue;
-                    const float4 qm = m.q[j];
-                    const float d2 = fmaf(-2.f, __uint_as_float(v[i]), qm.x + xn2);
-                    const float sn = qm.y + xn;
-                    const float E = fmaf(a.cE1 * qm.y, xn, a.cE2 * sn * sn);
-                    const float t = qm.z * 1.0000039f;
+                    const float d2 = fmaf(-2.f, __uint_as_float(v[i]), rc.qn2 + xn2);
+                    const float sn = rc.qn + xn;
+                    const float E = fmaf(a.cE1 * rc.qn, xn, a.cE2 * sn * sn);
+                    const float t = rc.thr * 1.0000039f;
                     if (d2 > fmaf(t, t, E)) continue;
-                    if (rdel <= m.seq[j]) continue;
+                    if (rdel <= rc.seq) continue;
                     bool ok = true;
                     for (int l = 0; l < a.h && ok; ++l) {
                         const float T = a.table[(int64_t)l * a.n + row];
-                        const float pl = m.path[j * a.h + l];
-                        const float eps = a.epsc * (T + pl + qm.z);
-                        if (fabsf(T - pl) > qm.z + eps) ok = false;
+                        const float pl = m.path[j * a.hp + l];
+                        const float eps = a.epsc * (T + pl + rc.thr);
+                        if (fabsf(T - pl) > rc.thr + eps) ok = false;
                     }
                     if (ok) passbits |= 1u << i;
                 }
@@ -324,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int i = __ffs(passbits) - 1;
                         passbits &= passbits - 1;
                         if ((int64_t)o < a.cap) {
-                            a.out_q[o] = __float_as_int(m.q[cc + i].w);
+                            a.out_q[o] = m.rec[cc + i].q;
                             a.out_row[o] = (int32_t)row;
                         }
                         ++o;
@@ -358,20 +352,31 @@ __global__ void k_node_hist(const int32_t *__restrict__ enode, const uint64_t *_
         if (emask[e]) atomicAdd(&ncount[enode[e]], 1);
 }
 
-// scatter each entry's payload (query, leaf mask, path distances) to its
-// node's slot, so a tile reads its queries' data contiguously
+// scatter each entry's record (query, threshold, norms, sequence number,
+// leaf mask) and path distances to its node's slot, so a tile reads its
+// queries' data contiguously
 __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
-                               const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int64_t E,
-                               const int64_t *__restrict__ noff, int32_t *__restrict__ cursor,
-                               int32_t *__restrict__ gq, uint64_t *__restrict__ gmask, float *__restrict__ gpath) {
+                               const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int hp,
+                               int64_t E, const float *__restrict__ thr, const float *__restrict__ qn2,
+                               const int64_t *__restrict__ qseq, const int64_t *__restrict__ noff,
+                               int32_t *__restrict__ cursor, TileRec *__restrict__ grec, int32_t *__restrict__ gq,
+                               float *__restrict__ gpath) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t m = emask[e];
         if (!m) continue;
         const int32_t nd = enode[e];
         const int64_t o = noff[nd] + atomicAdd(&cursor[nd], 1);
-        gq[o] = eq[e];
-        gmask[o] = m;
-        for (int l = 0; l < h; ++l) gpath[o * h + l] = path[e * h + l];
+        const int32_t q = eq[e];
+        TileRec r;
+        r.q = q;
+        r.thr = thr[q];
+        r.qn2 = qn2[q];
+        r.qn = sqrtf(r.qn2) * (1.f + 1e-6f);
+        r.seq = qseq[q];
+        r.mask = m;
+        grec[o] = r;
+        gq[o] = q;
+        for (int l = 0; l < hp; ++l) gpath[o * hp + l] = l < h ? path[e * h + l] : 0.f;
     }
 }
 
@@ -419,7 +424,7 @@ size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
-    b += 2 * ((size_t)kNQ * (8 + 8 + 16) + (((size_t)kNQ * h * 4 + 15) / 16) * 16);
+    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4);
     b += 3 * 8 + 4 + 4 + 4 + 16;
     return b;
 }
@@ -443,6 +448,17 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
     c.ready = true;
 }
 
+void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
+                      DBuf<float> &qn2, cudaStream_t st) {
+    Qh.alloc((size_t)(nq > 0 ? nq : 1) * dim_p * 2, st);
+    Ql.alloc((size_t)(nq > 0 ? nq : 1) * dim_p * 2, st);
+    qn2.alloc(nq > 0 ? nq : 1, st);
+    if (nq > 0)
+        k_split_rows<<<nblk(nq * 32), 256, 0, st>>>(Q, dim, dim_p, nq, (__nv_bfloat16 *)Qh.get(),
+                                                   (__nv_bfloat16 *)Ql.get(), qn2.get());
+    check_launch("split queries");
+}
+
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st, const int32_t *counts) {
     const int64_t E = tq.E;
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
@@ -460,11 +476,12 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     GTS_CUDA(cudaMemcpyAsync(&total_entries, noff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
     GTS_CUDA(cudaStreamSynchronize(st));
     const int64_t ne = total_entries > 0 ? total_entries : 1;
+    const int hp = (t.h + 3) & ~3;
+    rg.grec.alloc(ne, st);
     rg.gq.alloc(ne, st);
-    rg.gmask.alloc(ne, st);
-    rg.gpath.alloc(ne * t.h, st);
-    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, E, noff.get(), cursor.get(),
-                                            rg.gq.get(), rg.gmask.get(), rg.gpath.get());
+    rg.gpath.alloc(ne * hp, st);
+    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2, tq.qseq,
+                                            noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(), rg.gpath.get());
     const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
     k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, nn, nitems.get());
     exscan(nitems.get(), ioff.get(), nn + 1, st);
@@ -486,13 +503,6 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st) {
     *launches = 0;
     if (rg.n_items == 0) return 0;
-    // the batch's queries as split bf16 rows and squared norms
-    DBuf<uint8_t> Qh((size_t)tq.nq * c.dim_p * 2, st), Ql((size_t)tq.nq * c.dim_p * 2, st);
-    DBuf<float> qn2(tq.nq, st);
-    k_split_rows<<<nblk(tq.nq * 32), 256, 0, st>>>(tq.Q, t.dim, c.dim_p, tq.nq, (__nv_bfloat16 *)Qh.get(),
-                                                 (__nv_bfloat16 *)Ql.get(), qn2.get());
-    check_launch("split queries");
-    ++*launches;
     int dev = 0, sms = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -540,14 +550,12 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.npos = t.npos.get();
         a.nsize = t.nsize.get();
         a.lvl_last = t.lvl_off[t.h - 1];
-        a.Qh = (const __nv_bfloat16 *)Qh.get();
-        a.Ql = (const __nv_bfloat16 *)Ql.get();
-        a.qn2 = qn2.get();
-        a.qseq = tq.qseq;
-        a.thr = tq.thr;
+        a.Qh = tq.Qh;
+        a.Ql = tq.Ql;
+        a.grec = rg.grec.get();
         a.gq = rg.gq.get();
         a.gpath = rg.gpath.get();
-        a.gmask = rg.gmask.get();
+        a.hp = (t.h + 3) & ~3;
         a.items = rg.items.get();
         a.n_items = rg.n_items;
         a.work_counter = counter.get();

@@ -9,6 +9,16 @@
 
 namespace gts {
 
+// One (query, last-level node) entry in node-major order: everything the tile
+// epilogue needs about the query, 32 bytes (two 16-byte async copies).
+struct __align__(16) TileRec {
+    int32_t q;
+    float thr;       // radius or tau_q
+    float qn2, qn;   // |q|^2 and |q| (rounded up)
+    int64_t seq;     // the query's sequence number
+    uint64_t mask;   // surviving leaves of the node
+};
+
 struct TileArgs {
     int dim, dim_p, F, h;
     int64_t n;
@@ -18,12 +28,10 @@ struct TileArgs {
     const int32_t *npos, *nsize;
     int64_t lvl_last;         // first node of the last pivot level
     const __nv_bfloat16 *Qh, *Ql;   // the batch's queries, split bf16 [nq, dim_p]
-    const float *qn2;               // |q|^2
-    const int64_t *qseq;
-    const float *thr;
-    const int32_t *gq;        // entries of the last pivot level regrouped by node: query,
-    const float *gpath;       // path distances [*, h],
-    const uint64_t *gmask;    // surviving-leaf mask
+    const TileRec *grec;      // entries of the last pivot level regrouped by node
+    const int32_t *gq;        // their queries (for the row copies)
+    const float *gpath;       // their path distances [*, hp], hp = h rounded up to 4
+    int hp;
     const int4 *items;        // (node, first, count, 0) over `order`
     int64_t n_items;
     int *work_counter;
@@ -38,6 +46,8 @@ struct TileArgs {
 struct TcQuery {
     int64_t E = 0;
     int64_t nq = 0;
+    const __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;   // split bf16 queries [nq, dim_p]
+    const float *qn2 = nullptr;                          // |q|^2
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;
@@ -49,9 +59,9 @@ struct TcQuery {
 };
 
 struct TcRegroup {
-    DBuf<int32_t> gq;      // entry payload grouped by node: query,
-    DBuf<uint64_t> gmask;  // surviving-leaf mask,
-    DBuf<float> gpath;     // path distances [*, h]
+    DBuf<TileRec> grec;    // entry records grouped by node
+    DBuf<int32_t> gq;      // their queries
+    DBuf<float> gpath;     // their path distances [*, hp]
     DBuf<int4> items;      // (node, first, count, 0)
     int64_t n_items = 0;
     int64_t n_entries = 0; // entries with a surviving leaf
@@ -60,6 +70,9 @@ struct TcRegroup {
 
 bool tc_supported(const Tree &t);
 void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
+// split a batch's queries into bf16 hi / lo rows [nq, dim_p] and squared norms
+void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
+                      DBuf<float> &qn2, cudaStream_t st);
 // regroup the last-level entries by node into tiles; returns the tile count
 // counts: entries with a surviving leaf per last-level node, if already known
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st,
