@@ -433,55 +433,115 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
     }
 }
 
-// Last pivot level, tensor-core path: one pass per entry computes d(q, pivot)
-// (query kept in registers across the query's consecutive entries), tests the
-// node's leaf children against [d - t, d + t] (Lemma 1 / 2) into a bit mask,
-// and counts the entries with a surviving leaf per node for the regrouping.
+// Last pivot level, tensor-core path: one pass per entry computes d(q, pivot),
+// tests the node's leaf children against [d - t, d + t] (Lemma 1 / 2) into a
+// bit mask, and counts the entries with a surviving leaf per node for the
+// regrouping.  A warp takes kLastGroup consecutive entries and issues each
+// stage's loads for all of them before using any (entry ids, pivot rows,
+// query rows, leaf intervals), so the dependent-load latencies overlap.
+constexpr int kLastGroup = 8;
+
 template <bool L2, int NV>
 __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                                  int64_t lvl_base, int64_t lvl_next, int64_t e0, int64_t e1,
                                  float *__restrict__ path, int l, const float *__restrict__ thr_q,
                                  uint64_t *__restrict__ mask_out, int32_t *__restrict__ ncount) {
+    constexpr int G = kLastGroup;
+    constexpr int V = NV > 0 ? NV : 1;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    float4 qr[NV > 0 ? NV : 1];
-    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e0 + w * kPivGroup < e1; w += nw) {
-        const int64_t a0 = e0 + w * kPivGroup;
-        const int64_t a1 = a0 + kPivGroup < e1 ? a0 + kPivGroup : e1;
-        int32_t cur = -1;
-        const float *qv = nullptr;
-        float thr = 0.f;
-        for (int64_t e = a0; e < a1; ++e) {
-            const int32_t q = eq[e];
-            if (q != cur) {
-                cur = q;
-                qv = d.Q + (int64_t)q * d.dim;
-                thr = thr_q[q];
-                if (NV > 0) {
-                    const float4 *q4 = reinterpret_cast<const float4 *>(qv);
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e0 + w * G < e1; w += nw) {
+        const int64_t a0 = e0 + w * G;
+        const int cnt = (int)(e1 - a0 < G ? e1 - a0 : G);
+        // stage 1: entry ids, nodes, pivots, thresholds (lane i < cnt loads entry i)
+        int32_t my_q = 0, my_node = 0, my_prow = 0;
+        float my_thr = 0.f;
+        if (lane < cnt) {
+            my_q = eq[a0 + lane];
+            my_node = enode[a0 + lane];
+        }
+        if (lane < cnt) {
+            my_prow = d.npiv[lvl_base + my_node];
+            my_thr = thr_q[my_q];
+        }
+        // stage 2: pivot rows and query rows of all entries
+        float4 pr[G][V], qr[G][V];
 #pragma unroll
-                    for (int v = 0; v < (NV > 0 ? NV : 1); ++v) qr[v] = q4[v * 32 + lane];
+        for (int i = 0; i < G; ++i) {
+            const int32_t prow = __shfl_sync(0xffffffffu, my_prow, i);
+            const int32_t q = __shfl_sync(0xffffffffu, my_q, i);
+            if (i < cnt) {
+                if (NV > 0) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(d.X + (int64_t)prow * d.dim);
+                    const float4 *q4 = reinterpret_cast<const float4 *>(d.Q + (int64_t)q * d.dim);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        pr[i][v] = __ldg(p4 + v * 32 + lane);
+                        qr[i][v] = __ldg(q4 + v * 32 + lane);
+                    }
                 }
             }
-            const int32_t node = enode[e];
-            const int32_t prow = d.npiv[lvl_base + node];
-            const float sq = row_dist_regs<L2, NV>(qr, d.X + (int64_t)prow * d.dim, qv, d.dim, lane);
-            const float dq = L2 ? sqrtf(sq) : sq;
-            uint64_t m = 0;
-            for (int j0 = 0; j0 < d.F; j0 += 32) {
-                const int j = j0 + lane;
-                bool keep = false;
-                if (j < d.F) {
+        }
+        // stage 3: distances
+        float dq[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            dq[i] = 0.f;
+            if (i < cnt) {
+                float sq;
+                if (NV > 0) {
+                    sq = 0.f;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const float4 x = pr[i][v], y = qr[i][v];
+                        const float t0 = y.x - x.x, t1 = y.y - x.y, t2 = y.z - x.z, t3 = y.w - x.w;
+                        sq += L2 ? t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3 : fabsf(t0) + fabsf(t1) + fabsf(t2) + fabsf(t3);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                } else {
+                    const int32_t prow = __shfl_sync(0xffffffffu, my_prow, i);
+                    const int32_t q = __shfl_sync(0xffffffffu, my_q, i);
+                    sq = warp_vec_dist<L2>(d.Q + (int64_t)q * d.dim, d.X + (int64_t)prow * d.dim, d.dim, lane);
+                }
+                dq[i] = L2 ? sqrtf(sq) : sq;
+            }
+        }
+        // stage 4: leaf intervals of all entries, then the tests; lane i
+        // collects entry i's mask
+        uint64_t my_mask = 0;
+        for (int j0 = 0; j0 < d.F; j0 += 32) {
+            const int j = j0 + lane;
+            int32_t sz[G];
+            float lo[G], hi[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                const int32_t node = __shfl_sync(0xffffffffu, my_node, i);
+                sz[i] = 0;
+                lo[i] = hi[i] = 0.f;
+                if (i < cnt && j < d.F) {
                     const int64_t c = lvl_next + (int64_t)node * d.F + j;
-                    keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+                    sz[i] = d.nsize[c];
+                    lo[i] = d.nlo[c];
+                    hi[i] = d.nhi[c];
                 }
-                m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
             }
-            if (lane == 0) {
-                path[e * d.h + l] = dq;
-                mask_out[e - e0] = m;
-                if (m) atomicAdd(&ncount[node], 1);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                const float thr = __shfl_sync(0xffffffffu, my_thr, i);
+                const bool keep = i < cnt && j < d.F && sz[i] > 0 && interval_hit(dq[i], thr, lo[i], hi[i], d.epsc);
+                const uint64_t m = (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
+                if (lane == i) my_mask |= m;
             }
+        }
+        float my_dq = 0.f;
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            if (lane == i) my_dq = dq[i];
+        if (lane < cnt) {
+            path[(a0 + lane) * d.h + l] = my_dq;
+            mask_out[a0 + lane - e0] = my_mask;
+            if (my_mask) atomicAdd(&ncount[my_node], 1);
         }
     }
 }
@@ -1266,7 +1326,7 @@ struct Runner {
         GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
         const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
-        const unsigned grid = cap(nblocks((E + kPivGroup - 1) / kPivGroup, kWarpsPerBlock));
+        const unsigned grid = cap(nblocks((E + kLastGroup - 1) / kLastGroup, kWarpsPerBlock));
         clk.begin(GTS_STAGE_PIVOT_DIST);
 #define GTS_LL(NVV)                                                                                       \
     k_last_level_vec<true, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, lvl_next, e0, e1, \

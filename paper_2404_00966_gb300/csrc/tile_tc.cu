@@ -111,6 +111,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 struct ChunkMeta {           // one buffer of per-query data of a chunk
     TileRec *rec;            // NQ records
     float *path;             // NQ x hp
+    float2 *ab;              // NQ (alpha_q, beta_q) of the squared-form bound test
 };
 
 // Stage chunk [start, start + cnt) of a block's queries with asynchronous
@@ -154,12 +155,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sB = sAl + panels * apanel;                    // 2 buffers x (hi, lo) x panels x kNQ x 128 B
     const int bbuf = 2 * panels * bpanel;                   // bytes of one (hi, lo) buffer
     uint8_t *mbase = sB + 2 * bbuf;
-    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4;   // one metadata buffer
+    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + kNQ * 8;   // one metadata buffer
     auto metab = [&](int b) {
         uint8_t *mp = mbase + b * mbytes;
         ChunkMeta m;
         m.rec = (TileRec *)mp;
         m.path = (float *)(mp + kNQ * sizeof(TileRec));
+        m.ab = (float2 *)(mp + kNQ * sizeof(TileRec) + kNQ * a.hp * 4);
         return m;
     };
     uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
@@ -224,6 +226,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             xn = sqrtf(xn2) * (1.f + 1e-6f);
             if (a.any_deleted) rdel = a.row_del[row];
         }
+        // rows outside the node block match no leaf bit
+        const uint64_t rowbit = valid ? (1ull << jl) : 0ull;
+        // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
+        const float gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
         const int nchunks = (total + kNQ - 1) / kNQ;
         stage_chunk<NQ>(a, first, total < kNQ ? total : kNQ, metab(0), sB, sB + panels * bpanel, chunks16);
         for (int c = 0; c < nchunks; ++c) {
@@ -231,6 +237,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
             cp_async_wait_all();
             tc::fence_proxy_async_smem();
+            __syncthreads();
+            {   // per-query constants of the squared-form test (records have landed)
+                const ChunkMeta m = metab(b);
+                for (int j = tid; j < cnt; j += kThreads) {
+                    const TileRec &rc = m.rec[j];
+                    // keep iff d~^2 <= thr^2 + cE1 |q||x| + cE2 (|q| + |x|)^2, with
+                    // d~^2 = |q|^2 + |x|^2 - 2 q.x: alpha = (cE1 + 2 cE2) |q|,
+                    // beta = thr^2 + (cE2 - 1) |q|^2, all rounded up
+                    const float t = rc.thr * 1.0000039f;
+                    const float alpha = __fmul_ru(a.cE1 + 2.f * a.cE2, rc.qn) * 1.000001f;
+                    const float beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(a.cE2 - 1.f, rc.qn2)) +
+                                       4.f * 1.1920929e-7f * (t * t + rc.qn2);
+                    m.ab[j] = make_float2(alpha, beta);
+                }
+            }
             __syncthreads();
             // ---- MMA of chunk c into accumulator b: one thread, three products per k-step
             if (tid == 0) {
@@ -283,15 +304,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 32; ++i) {
                     const int j = cc + i;
                     if (j >= cnt) break;
-                    const TileRec &rc = m.rec[j];
-                    const uint64_t mk = rc.mask;
+                    const uint64_t mk = m.rec[j].mask;
                     if ((mk & wmask) == 0) continue;   // warp-uniform
-                    if (!valid || !((mk >> jl) & 1ull)) continue;
-                    const float d2 = fmaf(-2.f, __uint_as_float(v[i]), rc.qn2 + xn2);
-                    const float sn = rc.qn + xn;
-                    const float E = fmaf(a.cE1 * rc.qn, xn, a.cE2 * sn * sn);
-                    const float t = rc.thr * 1.0000039f;
-                    if (d2 > fmaf(t, t, E)) continue;
+                    if (!(mk & rowbit)) continue;
+                    // d~^2 <= thr^2 + E  <=>  -2 q.x <= beta_q + alpha_q |x| + gamma_x
+                    const float2 ab = m.ab[j];
+                    if (-2.f * __uint_as_float(v[i]) > fmaf(ab.x, xn, ab.y + gx)) continue;
+                    const TileRec &rc = m.rec[j];
                     if (rdel <= rc.seq) continue;
                     bool ok = true;
                     for (int l = 0; l < a.h && ok; ++l) {
@@ -424,7 +443,7 @@ size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
-    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4);
+    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + (size_t)kNQ * 8);
     b += 3 * 8 + 4 + 4 + 4 + 16;
     return b;
 }
