@@ -307,6 +307,145 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# the other workloads (parity-test configurations; not the headline line)
+
+def _dev_strings(S):
+    import torch
+    return (torch.from_numpy(S.data if S.data.size else np.zeros(1, np.uint8)).cuda(),
+            torch.from_numpy(S.offsets).cuda())
+
+
+def run_config(args):
+    """Time one of the other workloads: words (edit range, r = 2), dna (edit
+    range, r = 8), zipf2d (10M 2-D points, L2 range at ~0.01% selectivity,
+    interleaved with stream updates and one batch update)."""
+    import torch
+    import paper_2404_00966_gb300 as gts
+    from paper_2404_00966_gb300 import build_ext
+    import synth
+
+    build_ext.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    wl_name = args.workload
+    prec = args.precision
+    extra = {}
+    if wl_name in ("words", "dna"):
+        wl = synth.words_like() if wl_name == "words" else synth.dna_like()
+        objs = _dev_strings(wl.objects)
+        queries = _dev_strings(wl.queries)
+        radii = torch.from_numpy(wl.radii).cuda()
+        t0 = time.perf_counter()
+        ix = gts.Index.build(objs, "edit", n_pivots=wl.n_pivots, fanout=wl.fanout, root_pivot=0)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        nq = wl.nq
+
+        def step(timing=False):
+            r = ix.range(queries, radii, result_on_device=True, timing=timing)
+            st = r.stats
+            r.free()
+            return st
+        metric = f"range queries/s at oracle-exact results (edit, r={int(wl.radii[0])})"
+        host_q = wl.queries
+    elif wl_name == "zipf2d":
+        wl = synth.zipf_clusters_2d(nq=100_000)
+        Xd = torch.from_numpy(wl.objects).cuda()
+        t0 = time.perf_counter()
+        ix = gts.Index.build(Xd, "l2", fanout=20, root_pivot=0, cache_limit=4096)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        # radius for ~0.01% selectivity: mean 1000th-neighbour distance of 1,000 queries
+        cal = torch.from_numpy(wl.queries[:1000]).cuda()
+        rc = ix.knn(cal, 1000)
+        r = float(np.mean([rc.query(i)[1][-1] for i in range(1000)]))
+        extra["radius"] = r
+        nq = 10_000
+        Qall = torch.from_numpy(wl.queries).cuda()
+        radii = torch.full((nq,), r, dtype=torch.float32, device="cuda")
+        upd = synth.zipf_points(wl.extra["centers"], wl.extra["weights"], 0.01, 10_000, seed=2)
+        bulk = synth.zipf_points(wl.extra["centers"], wl.extra["weights"], 0.01, 500_000, seed=5)
+        drng = np.random.default_rng(3)
+        state = {"round": 0, "next_ins": 0, "update_s": 0.0}
+
+        def step(timing=False):
+            i = state["round"] % 10
+            qb = Qall[i * nq:(i + 1) * nq]
+            res = ix.range(qb, radii, precision=prec, result_on_device=True, timing=timing)
+            st = res.stats
+            res.free()
+            # 10% updates between query batches: 500 inserts + 500 deletes
+            u0 = time.perf_counter()
+            a = state["next_ins"] % 9_500
+            ix.insert(upd[a:a + 500])
+            state["next_ins"] += 500
+            info = ix.info()
+            ix.delete(drng.integers(0, info["next_id"], size=500))
+            if state["round"] == 5:
+                ix.batch_update(bulk)   # one batch update: rebuild with 500,000 more points
+            torch.cuda.synchronize()
+            state["update_s"] += time.perf_counter() - u0
+            state["round"] += 1
+            return st
+        metric = "range queries/s at oracle-exact results (L2, ~0.01% selectivity, 10% stream updates)"
+        host_q = None
+    else:
+        raise SystemExit(f"unknown workload {wl_name}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stage_ms, launches, stats0 = {}, 0, None
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if wl_name == "zipf2d":
+            state["update_s"] = 0.0
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step(timing=True)
+            stats0 = stats0 or st
+            launches += st["launches"]
+            for kk, v in st["stage_ms"].items():
+                stage_ms[kk] = stage_ms.get(kk, 0.0) + v
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if wl_name == "zipf2d":
+        # queries/s over the query work only: the update calls are timed apart
+        qms = ms - 1e3 * state["update_s"]
+        extra["update_ms_per_round"] = round(1e3 * state["update_s"] / args.steps, 3)
+    else:
+        qms = ms
+    value = nq * args.steps / (qms / 1e3)
+    out = {"metric": metric, "value": round(value, 1), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(qms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "int32" if wl_name in ("words", "dna") else ("bf16+f64" if prec == "bf16" else "f32+f64"),
+           "data": "synthetic",
+           "config": {"workload": wl_name, "n": ix.info()["n_tree"], "nq": nq, "build_s": round(build_s, 3),
+                      "precision": prec, **extra},
+           "gpu_launches": int(launches),
+           "stage_ms_per_step": {kk: round(v / args.steps, 4) for kk, v in stage_ms.items()},
+           "counters_per_step": {kk: v for kk, v in stats0.items() if not isinstance(v, dict)},
+           "clocks": clocks.summary()}
+    if not args.no_cpu and host_q is not None:
+        import oracle
+        oracle.build()
+        m = min(host_q.n, args.ref_sample)
+        sub = host_q.take(np.arange(m))
+        t0 = time.perf_counter()
+        oracle.range_query("edit", wl.objects, sub, wl.radii[:m])
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(m / dt, 3), "unit": "queries/s", "cores": oracle.threads(),
+                               "kind": "oracle", "sample": f"{m} queries, brute-force banded edit distance"}
+    ix.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    raise SystemExit("serving workload: not built yet")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -350,11 +489,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "serving"],
+                    help="gauss (the headline line); the others time the remaining configurations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "gauss":
         run_ours(args)
+    elif args.workload == "serving":
+        run_serving(args)
+    else:
+        run_config(args)
 
 
 if __name__ == "__main__":
