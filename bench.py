@@ -316,6 +316,26 @@ def _dev_strings(S):
             torch.from_numpy(S.offsets).cuda())
 
 
+def calibrate_radius(ix, cal, target, torch, iters=24):
+    """Radius whose mean range-result count over the calibration queries is
+    about `target` (bisection in log space)."""
+    ncal = cal.shape[0]
+    rk = ix.knn(cal, int(min(target, 1024)))
+    hi = float(np.max([rk.query(i)[1][-1] for i in range(ncal)])) * 4.0
+    lo = hi / 1e6
+    for _ in range(iters):
+        mid = (lo * hi) ** 0.5
+        res = ix.range(cal, torch.full((ncal,), mid, dtype=torch.float32, device="cuda"))
+        mean = float(res.offsets[-1]) / ncal
+        if mean > target:
+            hi = mid
+        else:
+            lo = mid
+        if abs(mean - target) < 0.02 * target:
+            return mid
+    return (lo * hi) ** 0.5
+
+
 def run_config(args):
     """Time one of the other workloads: words (edit range, r = 2), dna (edit
     range, r = 8), zipf2d (10M 2-D points, L2 range at ~0.01% selectivity,
@@ -356,10 +376,10 @@ def run_config(args):
         ix = gts.Index.build(Xd, "l2", fanout=20, root_pivot=0, cache_limit=4096)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
-        # radius for ~0.01% selectivity: mean 1000th-neighbour distance of 1,000 queries
+        # one global radius with a mean result count of ~1,000 (0.01%) over 1,000
+        # calibration queries: bisection on the range-query counts
         cal = torch.from_numpy(wl.queries[:1000]).cuda()
-        rc = ix.knn(cal, 1000)
-        r = float(np.mean([rc.query(i)[1][-1] for i in range(1000)]))
+        r = calibrate_radius(ix, cal, 1000.0, torch)
         extra["radius"] = r
         nq = 10_000
         Qall = torch.from_numpy(wl.queries).cuda()
