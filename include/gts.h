@@ -244,6 +244,49 @@ gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gt
                                 const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
                                 void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching over one index (no counterpart in the paper; the paper
+ * answers one batch at a time).  Requests are submitted one by one; worker
+ * threads, each with its own CUDA stream, repeatedly form a batch of the
+ * oldest pending requests of one kind and run it with the batched search, so
+ * requests that arrive while others are on the GPU join the next batch and
+ * several batches overlap on the device.  A request is admitted to a batch
+ * only while the projected candidate-table bytes of all admitted requests
+ * (visible objects x 37 bytes each) fit result_budget.  The index must not be
+ * updated while a server runs on it. */
+typedef struct gts_server gts_server;
+
+typedef struct {
+    int32_t max_batch;      /* requests per device batch; 0 = 1024 */
+    int32_t n_streams;      /* worker threads and streams (batches in flight); 0 = 3 */
+    int32_t precision;      /* gts_precision of every batch */
+    int32_t reserved_;
+    int64_t result_budget;  /* admission budget in bytes; 0 = 16 GiB */
+    int64_t memory_budget;  /* size_GPU of each batch's two-stage scheduler; 0 = result_budget / n_streams */
+} gts_serve_opts;
+
+gts_status gts_serve_start(gts_index *index, const gts_serve_opts *opts, gts_server **out);
+
+/* One request: kind 0 = range (param = radius), 1 = kNN (param = k).  query:
+ * host float32[len], len = dim (vectors) or host bytes[len] (strings).  The
+ * query is copied; the ticket identifies the request in gts_serve_wait. */
+gts_status gts_serve_submit(gts_server *server, const void *query, int64_t len, int32_t kind, double param,
+                            int64_t *ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit; GTS_ETIMEOUT if it is not
+ * done in time, and the request stays pending).  On GTS_OK *out holds its
+ * answers (nq = 1, host memory, free with gts_result_free) and *latency_ms
+ * (may be NULL) the time from submit to the answers being ready. */
+gts_status gts_serve_wait(gts_server *server, int64_t ticket, int32_t timeout_ms, gts_result *out,
+                          double *latency_ms);
+
+/* Counters: int64[4] = batches run, requests run, largest batch, largest
+ * projected bytes in flight. */
+gts_status gts_serve_stats(gts_server *server, int64_t *out4);
+
+/* Finish the pending requests, join the workers, free the server. */
+gts_status gts_serve_stop(gts_server *server);
+
 void gts_result_free(gts_result *result);
 void gts_free(gts_index *index);
 const char *gts_last_error(void);

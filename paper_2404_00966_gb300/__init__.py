@@ -60,6 +60,11 @@ class _Result(ctypes.Structure):
                 ("dist", ctypes.c_void_p), ("on_device", ctypes.c_int32), ("priv_", ctypes.c_void_p)]
 
 
+class _ServeOpts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("result_budget", ctypes.c_int64), ("memory_budget", ctypes.c_int64)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("n_tree", ctypes.c_int64), ("n_cache", ctypes.c_int64), ("n_live", ctypes.c_int64),
                 ("next_id", ctypes.c_int64), ("seq", ctypes.c_int64), ("rebuild_seq", ctypes.c_int64),
@@ -69,7 +74,8 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
-           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc"]
+           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc", "gts_serve_start",
+           "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop"]
 
 
 def lib(path: Optional[str] = None):
@@ -93,6 +99,13 @@ def lib(path: Optional[str] = None):
     L.gts_info.argtypes = [P, ctypes.POINTER(_Info)]
     L.gts_tree_level.argtypes = [P, ctypes.c_int, P, P, P, P, P]
     L.gts_table.argtypes = [P, P, P]
+    L.gts_serve_start.argtypes = [P, ctypes.POINTER(_ServeOpts), ctypes.POINTER(P)]
+    L.gts_serve_submit.argtypes = [P, P, I64, I32, ctypes.c_double, ctypes.POINTER(I64)]
+    L.gts_serve_wait.argtypes = [P, I64, I32, ctypes.POINTER(_Result), ctypes.POINTER(ctypes.c_double)]
+    L.gts_serve_stats.argtypes = [P, P]
+    L.gts_serve_stop.argtypes = [P]
+    for f in ["gts_serve_start", "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop"]:
+        getattr(L, f).restype = ctypes.c_int
     L.gts_knn_scan_noalloc.argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
     L.gts_knn_scan_noalloc.restype = ctypes.c_int
     L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
@@ -342,3 +355,50 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching request loop over an index (gts_serve_*)."""
+
+    def __init__(self, index: "Index", max_batch=0, n_streams=0, precision="fp32", result_budget=0,
+                 memory_budget=0):
+        o = _ServeOpts(max_batch=int(max_batch), n_streams=int(n_streams),
+                       precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
+                       result_budget=int(result_budget), memory_budget=int(memory_budget))
+        self._h = ctypes.c_void_p()
+        self.index = index
+        _check(lib().gts_serve_start(index._h, ctypes.byref(o), ctypes.byref(self._h)))
+
+    def submit(self, query, kind: str, param) -> int:
+        """kind 'range' (param = radius) or 'knn' (param = k); returns a ticket."""
+        if isinstance(query, (bytes, bytearray)):
+            buf = np.frombuffer(bytes(query) or b"\0", np.uint8)
+            n = len(query)
+        else:
+            buf = np.ascontiguousarray(query, np.float32)
+            n = buf.size
+        t = ctypes.c_int64()
+        _check(lib().gts_serve_submit(self._h, _ptr(buf), n, 0 if kind == "range" else 1, float(param),
+                                      ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(ids, dist, latency_ms) of a request."""
+        res = _Result()
+        lat = ctypes.c_double()
+        _check(lib().gts_serve_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(res), ctypes.byref(lat)))
+        m = int(np.ctypeslib.as_array(ctypes.cast(res.offsets, ctypes.POINTER(ctypes.c_int64)), (2,))[1])
+        ids = np.ctypeslib.as_array(ctypes.cast(res.ids, ctypes.POINTER(ctypes.c_int64)), (max(m, 1),))[:m].copy()
+        dist = np.ctypeslib.as_array(ctypes.cast(res.dist, ctypes.POINTER(ctypes.c_float)), (max(m, 1),))[:m].copy()
+        lib().gts_result_free(ctypes.byref(res))
+        return ids, dist, float(lat.value)
+
+    def stats(self) -> dict:
+        out = np.zeros(4, np.int64)
+        _check(lib().gts_serve_stats(self._h, _ptr(out)))
+        return dict(batches=int(out[0]), requests=int(out[1]), max_batch=int(out[2]), max_in_flight=int(out[3]))
+
+    def stop(self):
+        if self._h:
+            _check(lib().gts_serve_stop(self._h))
+            self._h = None

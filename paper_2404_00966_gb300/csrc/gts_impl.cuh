@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -169,7 +170,7 @@ struct gts_index {
     uint64_t seed = 0;
     int64_t rebuilds = 0;
     std::vector<cudaEvent_t> events;   // reused by per-stage timing
-    int64_t tc_pairs_hint[2] = {0, 0}; // last tensor-core output size per query batch (range, knn)
+    std::atomic<int64_t> tc_pairs_hint[2] = {{0}, {0}}; // last tensor-core output size per query (x1024)
     ~gts_index() {
         for (auto e : events) cudaEventDestroy(e);
     }

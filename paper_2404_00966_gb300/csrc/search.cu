@@ -1383,12 +1383,12 @@ struct Runner {
         int nl = 0;
         // output capacity: twice the last call's size (per query), at least 1 M
         // pairs; a larger output triggers one relaunch with the exact size
-        const int64_t per_q = ix->tc_pairs_hint[knn ? 1 : 0];
+        const int64_t per_q = ix->tc_pairs_hint[knn ? 1 : 0].load();
         const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
         clk.begin(GTS_STAGE_TILE);
         const int64_t C = tc_run(ix->tree, ix->tree.tc, tq, rg, oq, orow, hint, &nl, st);
         clk.end();
-        if (tq.E > 0 && qb.nq > 0) ix->tc_pairs_hint[knn ? 1 : 0] = std::max<int64_t>(per_q, C * 1024 / qb.nq);
+        if (tq.E > 0 && qb.nq > 0) ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
         ++st_groups;
         if (C == 0) return;
         if (knn) {   // the selection wants query-major order

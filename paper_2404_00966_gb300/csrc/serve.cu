@@ -1,0 +1,334 @@
+// Continuous-batching request loop over one index.
+//
+// Requests (one query each: a range query with its radius or a kNN query
+// with its k) are submitted one at a time from any host thread.  A pool of
+// worker threads, each with its own CUDA stream, repeatedly takes the oldest
+// pending requests of one kind, as many as fit both the batch size and the
+// admission budget, and runs them as one batched search (the same device
+// path as gts_range / gts_knn).  Requests that arrive while batches are on
+// the GPU are admitted into the next batch a worker forms, so several batches
+// overlap on the device.
+//
+// Admission: every request carries a projected device footprint -- an upper
+// bound of the candidate rows it can produce (every visible object) times
+// the bytes one candidate occupies in the search's tables -- and a request
+// is admitted only while the projections of all requests in flight fit the
+// result budget (the oldest request is always admitted when nothing is in
+// flight).  Each batch's own intermediate tables are further bounded by the
+// two-stage scheduler with memory_budget.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gts_impl.cuh"
+
+struct gts_server;
+
+namespace gts {
+namespace {
+
+constexpr int64_t kCandidateBytes = 37;   // (query, row, distance, keep, key) in the candidate tables
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    int64_t ticket;
+    int32_t kind;    // 0 range, 1 kNN
+    float radius;
+    int32_t k;
+    std::vector<uint8_t> payload;   // float32[dim] or string bytes
+    int64_t proj;
+    double t_submit;
+};
+
+struct Done {
+    std::vector<int64_t> ids;
+    std::vector<float> dist;
+    double latency_ms;
+    gts_status status;
+};
+
+}  // namespace
+}  // namespace gts
+
+struct gts_server {
+    gts_index *ix = nullptr;
+    gts_serve_opts opts;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<gts::Request> pending;
+    std::unordered_map<int64_t, gts::Done> done;
+    int64_t next_ticket = 1;
+    bool stopping = false;
+    int64_t in_flight = 0;        // projected bytes of admitted requests
+    int64_t max_in_flight = 0;
+    int64_t batches = 0, requests_run = 0, max_batch_seen = 0;
+    std::vector<std::thread> workers;
+};
+
+namespace gts {
+namespace {
+
+void worker_loop(gts_server *sv, int wid) {
+    cudaSetDevice(sv->ix->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::vector<Request> batch;
+    const int dim = sv->ix->dim;
+    (void)wid;
+    for (;;) {
+        batch.clear();
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
+            if (sv->pending.empty() && sv->stopping) break;
+            // oldest-first batch of one kind, within the batch size and the admission budget
+            const int32_t kind = sv->pending.front().kind;
+            for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)batch.size() < sv->opts.max_batch;) {
+                if (it->kind != kind) {
+                    ++it;
+                    continue;
+                }
+                const bool fits = sv->in_flight + it->proj <= sv->opts.result_budget;
+                if (!fits && !(sv->in_flight == 0 && batch.empty())) break;
+                sv->in_flight += it->proj;
+                batch.push_back(std::move(*it));
+                it = sv->pending.erase(it);
+            }
+            if (sv->in_flight > sv->max_in_flight) sv->max_in_flight = sv->in_flight;
+            if (batch.empty()) {   // nothing admissible yet: wait for a batch to finish
+                sv->cv_done.wait(lk);
+                continue;
+            }
+            sv->batches += 1;
+            sv->requests_run += (int64_t)batch.size();
+            if ((int64_t)batch.size() > sv->max_batch_seen) sv->max_batch_seen = (int64_t)batch.size();
+        }
+        // ---- marshal the batch (host buffers) and run it on this worker's stream
+        const int64_t nb = (int64_t)batch.size();
+        gts_objects qo;
+        std::memset(&qo, 0, sizeof(qo));
+        std::vector<float> qv;
+        std::vector<uint8_t> qs;
+        std::vector<int64_t> qoff;
+        if (dim > 0) {
+            qv.resize((size_t)nb * dim);
+            for (int64_t i = 0; i < nb; ++i) std::memcpy(&qv[(size_t)i * dim], batch[i].payload.data(), (size_t)dim * 4);
+            qo.n = nb;
+            qo.dim = dim;
+            qo.data = qv.data();
+        } else {
+            qoff.resize(nb + 1, 0);
+            for (int64_t i = 0; i < nb; ++i) qoff[i + 1] = qoff[i] + (int64_t)batch[i].payload.size();
+            qs.resize(qoff[nb] > 0 ? qoff[nb] : 1);
+            for (int64_t i = 0; i < nb; ++i)
+                if (!batch[i].payload.empty())
+                    std::memcpy(&qs[qoff[i]], batch[i].payload.data(), batch[i].payload.size());
+            qo.n = nb;
+            qo.dim = 0;
+            qo.data = qs.data();
+            qo.offsets = qoff.data();
+        }
+        gts_query_opts o;
+        std::memset(&o, 0, sizeof(o));
+        o.stream = st;
+        o.precision = sv->opts.precision;
+        o.memory_budget = sv->opts.memory_budget;
+        gts_result res;
+        std::memset(&res, 0, sizeof(res));
+        gts_status s;
+        if (batch[0].kind == 0) {
+            std::vector<float> r(nb);
+            for (int64_t i = 0; i < nb; ++i) r[i] = batch[i].radius;
+            s = gts_range(sv->ix, &qo, r.data(), &o, &res);
+        } else {
+            std::vector<int32_t> k(nb);
+            for (int64_t i = 0; i < nb; ++i) k[i] = batch[i].k;
+            s = gts_knn(sv->ix, &qo, k.data(), &o, &res);
+        }
+        const double t_done = now_ms();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (int64_t i = 0; i < nb; ++i) {
+                Done dn;
+                dn.status = s;
+                dn.latency_ms = t_done - batch[i].t_submit;
+                if (s == GTS_OK) {
+                    const int64_t a = res.offsets[i], b = res.offsets[i + 1];
+                    dn.ids.assign(res.ids + a, res.ids + b);
+                    dn.dist.assign(res.dist + a, res.dist + b);
+                }
+                sv->done.emplace(batch[i].ticket, std::move(dn));
+                sv->in_flight -= batch[i].proj;
+            }
+        }
+        if (s == GTS_OK) gts_result_free(&res);
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    cudaStreamDestroy(st);
+}
+
+template <class F>
+gts_status guard(F &&f) {
+    try {
+        f();
+        return GTS_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return GTS_ECUDA;
+    }
+}
+
+}  // namespace
+}  // namespace gts
+
+using namespace gts;
+
+extern "C" {
+
+gts_status gts_serve_start(gts_index *ix, const gts_serve_opts *opts, gts_server **out) {
+    return guard([&] {
+        GTS_REQUIRE(ix && out, GTS_EINVAL, "NULL argument");
+        std::unique_ptr<gts_server> sv(new gts_server());
+        sv->ix = ix;
+        std::memset(&sv->opts, 0, sizeof(sv->opts));
+        if (opts) sv->opts = *opts;
+        if (sv->opts.max_batch <= 0) sv->opts.max_batch = 1024;
+        if (sv->opts.n_streams <= 0) sv->opts.n_streams = 3;
+        if (sv->opts.result_budget <= 0) sv->opts.result_budget = (int64_t)16 << 30;
+        if (sv->opts.memory_budget <= 0) sv->opts.memory_budget = sv->opts.result_budget / sv->opts.n_streams;
+        GTS_CUDA(cudaSetDevice(ix->device));
+        // warm the tensor-core copy before any worker runs (it is built lazily)
+        if (sv->opts.precision == GTS_PREC_BF16 && ix->metric == GTS_L2 && ix->tree.n > 0) {
+            std::vector<float> q((size_t)ix->dim, 0.f);
+            gts_objects qo;
+            std::memset(&qo, 0, sizeof(qo));
+            qo.n = 1;
+            qo.dim = ix->dim;
+            qo.data = q.data();
+            int32_t k = 1;
+            gts_query_opts o;
+            std::memset(&o, 0, sizeof(o));
+            o.stream = ix->stream;
+            o.precision = GTS_PREC_BF16;
+            gts_result r;
+            if (gts_knn(ix, &qo, &k, &o, &r) == GTS_OK) gts_result_free(&r);
+        }
+        gts_server *p = sv.get();
+        for (int i = 0; i < sv->opts.n_streams; ++i) sv->workers.emplace_back(worker_loop, p, i);
+        *out = sv.release();
+    });
+}
+
+gts_status gts_serve_submit(gts_server *sv, const void *query, int64_t len, int32_t kind, double param,
+                            int64_t *ticket) {
+    return guard([&] {
+        GTS_REQUIRE(sv && ticket, GTS_EINVAL, "NULL argument");
+        GTS_REQUIRE(kind == 0 || kind == 1, GTS_EINVAL, "kind must be 0 (range) or 1 (kNN)");
+        const int dim = sv->ix->dim;
+        Request r;
+        r.kind = kind;
+        if (kind == 0) {
+            GTS_REQUIRE(param >= 0.0 && param == param, GTS_EINVAL, "radius must be >= 0");
+            r.radius = (float)param;
+            r.k = 0;
+        } else {
+            GTS_REQUIRE(param >= 1.0 && param <= 1024.0, GTS_EINVAL, "k must be in 1 .. 1024");
+            r.k = (int32_t)param;
+            r.radius = 0.f;
+        }
+        if (dim > 0) {
+            GTS_REQUIRE(len == dim && query, GTS_EINVAL, "a vector query must have dim coordinates");
+            r.payload.resize((size_t)dim * 4);
+            std::memcpy(r.payload.data(), query, (size_t)dim * 4);
+        } else {
+            GTS_REQUIRE(len >= 0 && len <= kMaxStrLen && (len == 0 || query), GTS_EINVAL, "bad string query");
+            r.payload.assign((const uint8_t *)query, (const uint8_t *)query + len);
+        }
+        const int64_t visible = sv->ix->n_live > 0 ? sv->ix->n_live : 1;
+        r.proj = visible * kCandidateBytes;
+        r.t_submit = now_ms();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            GTS_REQUIRE(!sv->stopping, GTS_EINVAL, "server is stopping");
+            r.ticket = sv->next_ticket++;
+            *ticket = r.ticket;
+            sv->pending.push_back(std::move(r));
+        }
+        sv->cv_work.notify_one();
+    });
+}
+
+gts_status gts_serve_wait(gts_server *sv, int64_t ticket, int32_t timeout_ms, gts_result *out, double *latency_ms) {
+    gts_status inner = GTS_OK;
+    gts_status s = guard([&] {
+        GTS_REQUIRE(sv && out, GTS_EINVAL, "NULL argument");
+        std::unique_lock<std::mutex> lk(sv->mu);
+        auto ready = [&] { return sv->done.count(ticket) > 0; };
+        if (timeout_ms < 0) {
+            sv->cv_done.wait(lk, ready);
+        } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+            throw Error(GTS_ETIMEOUT, "request not finished yet");
+        }
+        Done dn = std::move(sv->done[ticket]);
+        sv->done.erase(ticket);
+        lk.unlock();
+        inner = dn.status;
+        if (latency_ms) *latency_ms = dn.latency_ms;
+        if (dn.status != GTS_OK) throw Error(dn.status, "request failed");
+        const int64_t m = (int64_t)dn.ids.size();
+        out->nq = 1;
+        out->on_device = 0;
+        out->priv_ = nullptr;
+        out->offsets = (int64_t *)std::malloc(16);
+        out->ids = (int64_t *)std::malloc(sizeof(int64_t) * (m > 0 ? m : 1));
+        out->dist = (float *)std::malloc(sizeof(float) * (m > 0 ? m : 1));
+        if (!out->offsets || !out->ids || !out->dist) throw std::bad_alloc();
+        out->offsets[0] = 0;
+        out->offsets[1] = m;
+        if (m) {
+            std::memcpy(out->ids, dn.ids.data(), sizeof(int64_t) * m);
+            std::memcpy(out->dist, dn.dist.data(), sizeof(float) * m);
+        }
+    });
+    (void)inner;
+    return s;
+}
+
+gts_status gts_serve_stats(gts_server *sv, int64_t *out4) {
+    return guard([&] {
+        GTS_REQUIRE(sv && out4, GTS_EINVAL, "NULL argument");
+        std::lock_guard<std::mutex> lk(sv->mu);
+        out4[0] = sv->batches;
+        out4[1] = sv->requests_run;
+        out4[2] = sv->max_batch_seen;
+        out4[3] = sv->max_in_flight;
+    });
+}
+
+gts_status gts_serve_stop(gts_server *sv) {
+    return guard([&] {
+        GTS_REQUIRE(sv, GTS_EINVAL, "NULL argument");
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->stopping = true;
+        }
+        sv->cv_work.notify_all();
+        sv->cv_done.notify_all();
+        for (auto &t : sv->workers) t.join();
+        delete sv;
+    });
+}
+
+}  // extern "C"

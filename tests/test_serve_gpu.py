@@ -1,0 +1,76 @@
+"""Continuous batching (gts_serve_*): every request's answer inside a mixed,
+concurrently submitted stream equals its answer alone (gts_range / gts_knn on
+that one query), and admission never lets the projected bytes in flight
+exceed the budget (beyond one request admitted alone)."""
+import threading
+
+import numpy as np
+import pytest
+
+from synth import small_vectors, words_like
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gts():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_00966_gb300 import build_ext
+    build_ext.build()
+    import paper_2404_00966_gb300 as g
+    return g
+
+
+@pytest.mark.parametrize("metric,prec", [("l2", "fp32"), ("l2", "bf16"), ("l1", "fp32")])
+def test_mixed_stream_equals_alone(gts, metric, prec):
+    X, Q = small_vectors(30011, 64, 240, seed=61)
+    ix = gts.Index.build(X, metric, fanout=12, root_pivot=0)
+    rng = np.random.default_rng(62)
+    kinds = rng.random(240) < 0.5
+    ks = rng.integers(1, 40, size=240)
+    base = ix.knn(Q[:20], 30)
+    radius = float(np.median([base.query(i)[1][-1] for i in range(20)]))
+    proj = X.shape[0] * 37
+    budget = 9 * proj                       # at most nine requests admitted at once
+    sv = gts.Server(ix, max_batch=32, n_streams=3, precision=prec, result_budget=budget)
+    tickets = [None] * 240
+
+    def submit(lo, hi):
+        for i in range(lo, hi):
+            tickets[i] = sv.submit(Q[i], "knn" if kinds[i] else "range", int(ks[i]) if kinds[i] else radius)
+
+    th = [threading.Thread(target=submit, args=(a, a + 80)) for a in (0, 80, 160)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    got = [sv.wait(t) for t in tickets]
+    st = sv.stats()
+    sv.stop()
+    assert st["requests"] == 240 and st["batches"] > 1
+    assert st["max_in_flight"] <= budget
+    for i in range(240):
+        alone = ix.knn(Q[i:i + 1], int(ks[i]), precision=prec) if kinds[i] else \
+            ix.range(Q[i:i + 1], np.float32([radius]), precision=prec)
+        ids, dist = alone.query(0)
+        assert np.array_equal(got[i][0], ids), f"request {i}: ids differ"
+        assert np.allclose(got[i][1], dist, rtol=1e-5, atol=1e-30), f"request {i}: distances differ"
+        assert got[i][2] >= 0.0
+    ix.close()
+
+
+def test_string_requests(gts):
+    wl = words_like(n=3000, nq=60)
+    ix = gts.Index.build(wl.objects, "edit", n_pivots=4, fanout=8, root_pivot=0)
+    sv = gts.Server(ix, max_batch=16, n_streams=2)
+    tk = [sv.submit(wl.queries.get(i), "range" if i % 2 else "knn", 2 if i % 2 else 5) for i in range(60)]
+    got = [sv.wait(t) for t in tk]
+    sv.stop()
+    for i in range(60):
+        q = wl.queries.take([i])
+        alone = ix.range(q, np.float32([2])) if i % 2 else ix.knn(q, 5)
+        ids, dist = alone.query(0)
+        assert np.array_equal(got[i][0], ids) and np.array_equal(got[i][1], dist)
+    ix.close()
