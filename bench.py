@@ -485,7 +485,7 @@ def run_serving(args):
     radius = calibrate_radius(ix, cal, 100.0, torch, iters=16)
     is_knn, ks = synth.mixed_requests(nreq, seed=1)
     arrivals = synth.poisson_arrivals(nreq, args.rate, seed=1)
-    sv = gts.Server(ix, max_batch=args.max_batch, n_streams=3, result_budget=16 << 30)
+    sv = gts.Server(ix, max_batch=args.max_batch, n_streams=3, precision=args.precision, result_budget=16 << 30)
     warm = [sv.submit(wl.queries[nreq + i], "knn", 10) for i in range(64)]
     for t in warm:
         sv.wait(t)
@@ -518,7 +518,7 @@ def run_serving(args):
            "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": "uniform_2Mx256_l1_serving", "n": 2_000_000, "dim": 256, "requests": nreq,
                       "arrival_rate": args.rate, "radius": radius, "build_s": round(build_s, 3),
-                      "max_batch": args.max_batch, "streams": 3},
+                      "max_batch": args.max_batch, "streams": 3, "precision": args.precision},
            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
                           "mean": round(float(lat.mean()), 3), "max": round(float(lat.max()), 3)},
            "offered_span_s": round(float(arrivals[-1]), 4), "server": st, "clocks": clocks.summary()}

@@ -58,7 +58,11 @@ typedef enum { GTS_EDIT = 0, GTS_L1 = 1, GTS_L2 = 2 } gts_metric;
  *                 or of the running k-th distance.
  *  GTS_PREC_BF16: BF16 tensor-core distance tiles with FP32 accumulation and the
  *                 same FP64 recheck against a (wider) proven BF16 bound.
- * L1 and edit distance ignore this field (FP32 + FP64 recheck / exact int). */
+ * L1 has no product form for the tensor cores: with GTS_PREC_BF16 it runs the
+ * same node-major tiles on the CUDA cores in FP32 (the arithmetic and the FP64
+ * recheck of GTS_PREC_FP32, batched by node instead of by candidate); this
+ * needs dim % 4 == 0 and 16-byte aligned query rows, else the plain path runs.
+ * Edit distance ignores this field (exact int). */
 typedef enum { GTS_PREC_FP32 = 0, GTS_PREC_BF16 = 1 } gts_precision;
 
 /* A set of objects: vectors (dim > 0) or byte strings (dim == 0).
@@ -105,7 +109,7 @@ enum {
     GTS_STAGE_VERIFY = 4,     /* metric verification of candidates */
     GTS_STAGE_SELECT = 5,     /* kNN selection with FP64 rechecks */
     GTS_STAGE_OTHER = 6,      /* scans, sorts, regrouping, result assembly */
-    GTS_STAGE_TILE = 7,       /* BF16 tensor-core tiles: leaf scan fused with the distance prefilter */
+    GTS_STAGE_TILE = 7,       /* node-major tiles: leaf scan fused with the distance (filter) */
     GTS_STAGES = 8,
     GTS_STAGES_LEN = 16
 };
@@ -121,9 +125,10 @@ enum {
     GTS_STAT_GROUPS = 6,       /* query groups run by the two-stage scheduler */
     GTS_STAT_CACHE_ROWS = 7,   /* cache-list objects compared by brute force */
     GTS_STAT_LAUNCHES = 8,     /* kernels launched by the call */
-    GTS_STAT_TILES = 9,        /* BF16 tensor-core work items: 128-row blocks of last-level nodes */
+    GTS_STAT_TILES = 9,        /* tile work items: 128-row blocks of last-level nodes */
     GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries run against those blocks */
-    GTS_STATS_LEN = 11
+    GTS_STAT_TILE_PAIRS = 11,  /* (query, row) pairs whose distance the tiles computed */
+    GTS_STATS_LEN = 12
 };
 
 /* Per-query answers in CSR form: the answers of query i are

@@ -171,6 +171,7 @@ struct gts_index {
     int64_t rebuilds = 0;
     std::vector<cudaEvent_t> events;   // reused by per-stage timing
     std::atomic<int64_t> tc_pairs_hint[2] = {{0}, {0}}; // last tensor-core output size per query (x1024)
+    std::atomic<int64_t> l1_pairs_hint[4] = {{0}, {0}, {0}, {0}};  // L1 tiles: range, kNN phases 0..2 (same unit)
     ~gts_index() {
         for (auto e : events) cudaEventDestroy(e);
     }

@@ -26,6 +26,7 @@
 
 #include "gts_impl.cuh"
 #include "metric.cuh"
+#include "tile_l1.cuh"
 #include "tile_tc.cuh"
 
 namespace gts {
@@ -944,6 +945,59 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     if (threadIdx.x == 0) bn[q] = (int32_t)take;
 }
 
+// L1 tiles, range queries: decide the (query, row) pairs the tiles kept from
+// their FP32 distance; a pair within the error band of the radius takes the
+// FP64 distance in the CPU reference's operation order.
+__global__ void k_decide_range_l1(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+                                  float *__restrict__ cdist, int64_t C, const float *__restrict__ thr_q,
+                                  uint8_t *__restrict__ keep, unsigned long long *__restrict__ rechecks) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = cq[c];
+        const float d32 = cdist[c];
+        const float r = thr_q[q];
+        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
+        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        if (hi < r * (1.f - 1e-9f)) {
+            keep[c] = 1;
+        } else if (lo > r * (1.f + 1e-9f)) {
+            keep[c] = 0;
+        } else {
+            const double key = l1_fp64_seq(d.Q + (int64_t)q * d.dim, vrow(d, crow[c]), d.dim);
+            keep[c] = key <= (double)r ? 1 : 0;
+            cdist[c] = __double2float_rn(key);
+            atomicAdd(rechecks, 1ull);
+        }
+    }
+}
+
+// kNN: once a query's answer so far holds k objects, its k-th FP64 distance
+// (rounded up) bounds tau_q from above.
+__global__ void k_tau_from_answer(const int32_t *__restrict__ kq, const int64_t *__restrict__ koff,
+                                  const double *__restrict__ bd, const int32_t *__restrict__ bn, int64_t nq, int l2,
+                                  float *__restrict__ thr) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int K = kq[q];
+        if (bn[q] < K) continue;
+        const double v = bd[koff[q] + K - 1];
+        const float t = __double2float_ru(l2 ? __dsqrt_ru(v) : v);
+        if (t < thr[q]) thr[q] = t;
+    }
+}
+
+__global__ void k_pack_row_dist(const int32_t *__restrict__ row, const float *__restrict__ dist, int64_t C,
+                                uint64_t *__restrict__ out) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x)
+        out[c] = ((uint64_t)(uint32_t)row[c] << 32) | (uint64_t)__float_as_uint(dist[c]);
+}
+
+__global__ void k_unpack_row_dist(const uint64_t *__restrict__ in, int64_t C, int32_t *__restrict__ row,
+                                  float *__restrict__ dist) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        row[c] = (int32_t)(in[c] >> 32);
+        dist[c] = __uint_as_float((uint32_t)in[c]);
+    }
+}
+
 // ---------------------------------------------------------------- results
 
 __global__ void k_range_pack(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
@@ -1117,6 +1171,8 @@ struct Runner {
     int64_t st_tiles = 0, st_tile_entries = 0;
     StageClock clk;
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
+    bool use_l1 = false;   // FP32 CUDA-core tiles at the last level (L1)
+    int64_t st_tile_pairs = 0;
     DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
     DBuf<float> tcqn2;
 
@@ -1227,7 +1283,7 @@ struct Runner {
 
     void process(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
-        if (use_tc && l == h - 1) {
+        if ((use_tc || use_l1) && l == h - 1) {
             last_level_tc(L, e0, e1, l);
             return;
         }
@@ -1328,15 +1384,25 @@ struct Runner {
         const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
         const unsigned grid = cap(nblocks((E + kLastGroup - 1) / kLastGroup, kWarpsPerBlock));
         clk.begin(GTS_STAGE_PIVOT_DIST);
-#define GTS_LL(NVV)                                                                                       \
-    k_last_level_vec<true, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, lvl_next, e0, e1, \
-                                                    L.path.get(), l, thr.get(), mask.get(), ncount.get())
-        switch (nv) {
-            case 1: GTS_LL(1); break;
-            case 2: GTS_LL(2); break;
-            case 3: GTS_LL(3); break;
-            case 4: GTS_LL(4); break;
-            default: GTS_LL(0); break;
+#define GTS_LL(L2V, NVV)                                                                                 \
+    k_last_level_vec<L2V, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, lvl_next, e0, e1, \
+                                                   L.path.get(), l, thr.get(), mask.get(), ncount.get())
+        if (d.metric == GTS_L2) {
+            switch (nv) {
+                case 1: GTS_LL(true, 1); break;
+                case 2: GTS_LL(true, 2); break;
+                case 3: GTS_LL(true, 3); break;
+                case 4: GTS_LL(true, 4); break;
+                default: GTS_LL(true, 0); break;
+            }
+        } else {
+            switch (nv) {
+                case 1: GTS_LL(false, 1); break;
+                case 2: GTS_LL(false, 2); break;
+                case 3: GTS_LL(false, 3); break;
+                case 4: GTS_LL(false, 4); break;
+                default: GTS_LL(false, 0); break;
+            }
         }
 #undef GTS_LL
         clk.end();
@@ -1358,6 +1424,10 @@ struct Runner {
     // tiles (leaf scan + bf16 distance prefilter), then finish the kept pairs
     // with the FP32 distance and its FP64 boundary recheck.
     void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
+        if (use_l1) {
+            l1_leaf(L, e0, e1, mask, ncount);
+            return;
+        }
         TcQuery tq;
         tq.E = e1 - e0;
         tq.nq = qb.nq;
@@ -1379,6 +1449,7 @@ struct Runner {
         clk.end();
         st_tiles += rg.n_items;
         st_tile_entries += rg.n_entries;
+        st_tile_pairs += rg.n_pairs;
         DBuf<int32_t> oq, orow;
         int nl = 0;
         // output capacity: twice the last call's size (per query), at least 1 M
@@ -1405,6 +1476,93 @@ struct Runner {
             verify_and_collect(q2, r2, C);
         } else {
             verify_and_collect(oq, orow, C);
+        }
+    }
+
+    // Last level on the L1 tiles: regroup the entries by node, run the tiles
+    // (leaf mask, visibility and FP32 distance with its error band), then
+    // decide the kept pairs (range) or merge them into the answer (kNN).  kNN
+    // runs the blocks in three phases (1/64, 7/64, 56/64 of them); after each
+    // phase the k-th distance of the answer so far lowers tau_q, so the later
+    // blocks keep few pairs even where the lower bounds prune nothing.
+    void l1_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount) {
+        TcQuery tq;
+        tq.E = e1 - e0;
+        tq.nq = qb.nq;
+        tq.eq = L.q.get() + e0;
+        tq.enode = L.node.get() + e0;
+        tq.path = L.path.get() + e0 * h;
+        tq.emask = mask.get();
+        tq.Q = d.Q;
+        tq.qseq = d.qseq;
+        tq.thr = thr.get();
+        tq.epsc = d.epsc;
+        tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
+        TcRegroup rg;
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr);
+        clk.end();
+        st_tiles += rg.n_items;
+        st_tile_entries += rg.n_entries;
+        st_tile_pairs += rg.n_pairs;
+        L1Query lq;
+        lq.Q = d.Q;
+        lq.thr = thr.get();
+        lq.knn = knn;
+        lq.rel = d.rel;
+        lq.any_deleted = tq.any_deleted;
+        std::vector<int64_t> bounds = {0};
+        if (knn) {
+            for (int64_t f : {64, 8}) {
+                const int64_t b = rg.n_items / f;
+                if (b > bounds.back()) bounds.push_back(b);
+            }
+        }
+        if (rg.n_items > bounds.back()) bounds.push_back(rg.n_items);
+        for (size_t p = 0; p + 1 < bounds.size(); ++p) {
+            const int slot = knn ? 1 + (int)std::min<size_t>(p, 2) : 0;
+            const int64_t per_q = ix->l1_pairs_hint[slot].load();
+            const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
+            DBuf<int32_t> oq, orow;
+            DBuf<float> od;
+            int nl = 0;
+            clk.begin(GTS_STAGE_TILE);
+            const int64_t C = l1_run(ix->tree, lq, rg, bounds[p], bounds[p + 1], oq, orow, od, hint, &nl, st);
+            clk.end();
+            if (qb.nq > 0) ix->l1_pairs_hint[slot].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
+            ++st_groups;
+            if (C == 0) continue;
+            st_cands += C;
+            DBuf<uint8_t> keep(C, st);
+            if (knn) {   // the merge wants query-major order
+                DBuf<uint64_t> v1(C, st), v2(C, st);
+                DBuf<int32_t> q2(C, st), r2(C, st);
+                DBuf<float> d2(C, st);
+                int qbits = 1;
+                while (((int64_t)1 << qbits) < qb.nq) ++qbits;
+                size_t tb = 0;
+                cub::DeviceRadixSort::SortPairs(nullptr, tb, oq.get(), q2.get(), v1.get(), v2.get(), C, 0, qbits, st);
+                DBuf<uint8_t> tmp(tb ? tb : 1, st);
+                clk.begin(GTS_STAGE_OTHER, 3);
+                k_pack_row_dist<<<cap(nblocks(C, kT)), kT, 0, st>>>(orow.get(), od.get(), C, v1.get());
+                GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, oq.get(), q2.get(), v1.get(), v2.get(), C, 0,
+                                                         qbits, st));
+                k_unpack_row_dist<<<cap(nblocks(C, kT)), kT, 0, st>>>(v2.get(), C, r2.get(), d2.get());
+                clk.end();
+                merge_knn(q2, r2, d2, C);
+                clk.begin(GTS_STAGE_THRESHOLD);
+                k_tau_from_answer<<<cap(nblocks(qb.nq, kT)), kT, 0, st>>>(qb.k, koff.get(), bd.get(), bn.get(), qb.nq,
+                                                                         0, thr.get());
+                clk.end();
+                check_launch("L1 tau update");
+            } else {
+                clk.begin(GTS_STAGE_VERIFY);
+                k_decide_range_l1<<<cap(nblocks(C, kT)), kT, 0, st>>>(d, oq.get(), orow.get(), od.get(), C, thr.get(),
+                                                                      keep.get(), counters.get());
+                clk.end();
+                check_launch("L1 range decision");
+                collect(oq, orow, od, keep, C);
+            }
         }
     }
 
@@ -1461,6 +1619,12 @@ struct Runner {
         }
         clk.end();
         check_launch("verify");
+        collect(cq, crow, cdist, keep, C);
+    }
+
+    // Keep the pairs flagged in `keep`: range pairs are appended to the
+    // answer; kNN pairs are merged into each query's answer so far.
+    void collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, DBuf<float> &cdist, DBuf<uint8_t> &keep, int64_t C) {
         DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
         clk.begin(GTS_STAGE_OTHER, 2);
         k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
@@ -1476,20 +1640,7 @@ struct Runner {
             k_compact_cands<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C, pos.get(),
                                                            kq2.get(), krow2.get(), kd2.get());
             clk.end();
-            DBuf<double> ckey(R, st);
-            const unsigned grid = (unsigned)qb.nq;
-            clk.begin(GTS_STAGE_SELECT);
-            if (d.metric == GTS_L2)
-                k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                         bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
-            else if (d.metric == GTS_L1)
-                k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                         bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
-            else
-                k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                           bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
-            clk.end();
-            check_launch("knn merge");
+            merge_knn(kq2, krow2, kd2, R);
         } else {
             DBuf<uint64_t> rk(R, st);
             DBuf<float> rd(R, st);
@@ -1502,6 +1653,25 @@ struct Runner {
             rdists.push_back(std::move(rd));
             rcounts.push_back(R);
         }
+    }
+
+    // merge R query-major (query, row, FP32 distance) candidates into the
+    // per-query answers (exact (key, id) selection with FP64 keys)
+    void merge_knn(DBuf<int32_t> &kq2, DBuf<int32_t> &krow2, DBuf<float> &kd2, int64_t R) {
+        DBuf<double> ckey(R, st);
+        const unsigned grid = (unsigned)qb.nq;
+        clk.begin(GTS_STAGE_SELECT);
+        if (d.metric == GTS_L2)
+            k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
+                                                     bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+        else if (d.metric == GTS_L1)
+            k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
+                                                     bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+        else
+            k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
+                                                       bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+        clk.end();
+        check_launch("knn merge");
     }
 
     void cache_pass() {
@@ -1538,6 +1708,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         R.max_blocks = (unsigned)(sms > 0 ? sms : 1) * 8u;
     }
+    if (precision == GTS_PREC_BF16 && l1_tiles_supported(t, qb.Q)) R.use_l1 = true;
     if (precision == GTS_PREC_BF16 && tc_supported(t)) {
         tc_prepare(t, t.tc, st);
         R.use_tc = true;
@@ -1711,6 +1882,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_LAUNCHES] = R.clk.total_launches();
         stats[GTS_STAT_TILES] = R.st_tiles;
         stats[GTS_STAT_TILE_ENTRIES] = R.st_tile_entries;
+        stats[GTS_STAT_TILE_PAIRS] = R.st_tile_pairs;
     }
 }
 

@@ -389,7 +389,7 @@ __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__
         TileRec r;
         r.q = q;
         r.thr = thr[q];
-        r.qn2 = qn2[q];
+        r.qn2 = qn2 ? qn2[q] : 0.f;
         r.qn = sqrtf(r.qn2) * (1.f + 1e-6f);
         r.seq = qseq[q];
         r.mask = m;
@@ -400,10 +400,16 @@ __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__
 }
 
 // work items: one per 128-row block of every node that has entries
+// (also sums the (query, row) pairs the blocks hold into *pairs)
 __global__ void k_items_per_node(const int32_t *__restrict__ ncount, const int32_t *__restrict__ nsize, int64_t nn,
-                                 int64_t *__restrict__ nitems) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+                                 int64_t *__restrict__ nitems, unsigned long long *__restrict__ pairs) {
+    unsigned long long p = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         nitems[i] = ncount[i] > 0 ? (int64_t)((nsize[i] + kRows - 1) / kRows) : 0;
+        p += (unsigned long long)ncount[i] * (unsigned long long)nsize[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if ((threadIdx.x & 31) == 0 && p) atomicAdd(pairs, p);
     if (blockIdx.x == 0 && threadIdx.x == 0) nitems[nn] = 0;
 }
 
@@ -502,11 +508,16 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2, tq.qseq,
                                             noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(), rg.gpath.get());
     const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
-    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, nn, nitems.get());
+    DBuf<unsigned long long> pairs(1, st);
+    GTS_CUDA(cudaMemsetAsync(pairs.get(), 0, 8, st));
+    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, nn, nitems.get(), pairs.get());
     exscan(nitems.get(), ioff.get(), nn + 1, st);
     int64_t total_items = 0;
+    unsigned long long total_pairs = 0;
     GTS_CUDA(cudaMemcpyAsync(&total_items, ioff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(&total_pairs, pairs.get(), 8, cudaMemcpyDeviceToHost, st));
     GTS_CUDA(cudaStreamSynchronize(st));
+    rg.n_pairs = (int64_t)total_pairs;
     rg.n_items = total_items;
     rg.n_entries = total_entries;
     rg.n_chunks = (total_entries + 127) / 128;

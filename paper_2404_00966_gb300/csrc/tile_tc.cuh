@@ -47,7 +47,7 @@ struct TcQuery {
     int64_t E = 0;
     int64_t nq = 0;
     const __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;   // split bf16 queries [nq, dim_p]
-    const float *qn2 = nullptr;                          // |q|^2
+    const float *qn2 = nullptr;                          // |q|^2 (null: not needed, records get 0)
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;
@@ -66,6 +66,7 @@ struct TcRegroup {
     int64_t n_items = 0;
     int64_t n_entries = 0; // entries with a surviving leaf
     int64_t n_chunks = 0;  // query chunks over all blocks (tensor-core tiles)
+    int64_t n_pairs = 0;   // (query, row) pairs of all blocks: sum over nodes of entries x rows
 };
 
 bool tc_supported(const Tree &t);

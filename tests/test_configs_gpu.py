@@ -113,11 +113,12 @@ def test_uniform_l1_full_size_mixed(env):
     is_knn, ks = synth.mixed_requests(wl.nq, seed=1)
     idx = np.random.default_rng(105).choice(wl.nq, 16, replace=False)
     kq = ks.copy()
-    res = ix.knn(Qd, torch.from_numpy(kq).cuda())
-    _check(res, idx, oracle.knn_query("l1", wl.objects, wl.queries[idx], kq[idx]), "l1")
+    want_k = oracle.knn_query("l1", wl.objects, wl.queries[idx], kq[idx])
     cal = ix.knn(Qd[:200], 100)
     r = np.float32(np.mean([cal.query(i)[1][-1] for i in range(200)]))
     radii = np.full(wl.nq, r, np.float32)
-    res = ix.range(Qd, torch.from_numpy(radii).cuda())
-    _check(res, idx, oracle.range_query("l1", wl.objects, wl.queries[idx], radii[idx]), "l1")
+    want_r = oracle.range_query("l1", wl.objects, wl.queries[idx], radii[idx])
+    for prec in ("bf16", "fp32"):        # node-major FP32 tiles, then the plain path
+        _check(ix.knn(Qd, torch.from_numpy(kq).cuda(), precision=prec), idx, want_k, "l1")
+        _check(ix.range(Qd, torch.from_numpy(radii).cuda(), precision=prec), idx, want_r, "l1")
     ix.close()

@@ -244,6 +244,49 @@ def test_bf16_tiles_parity(gts, dim, dup):
     ix.close()
 
 
+@pytest.mark.parametrize("dim,kind,dup", [(64, "gauss", 0.0), (100, "gauss", 0.2), (256, "uniform", 0.0)])
+def test_l1_tiles_parity(gts, dim, kind, dup):
+    """L1 node-major FP32 tiles (precision="bf16" selects them for L1): blocks
+    of several 128-row slices, chunks of more than 128 queries, a coordinate
+    tail (dim 100), exact copies and ties, kNN run in three phases."""
+    X, Q = vec_case(20011, dim, 300, seed=50 + dim, kind=kind, dup=dup)
+    Q[:3] = X[[5, 9, 20010]]
+    ix = gts.Index.build(X, "l1", fanout=12, root_pivot=7)
+    for k in (1, 10, 57):
+        r = ix.knn(Q, k, precision="bf16")
+        assert r.stats["tile_pairs"] > 0
+        assert_same(r, oracle.knn_query("l1", X, Q, k), "l1", f"L1 tiles knn k={k}")
+    ks = np.random.default_rng(5).integers(1, 100, size=300).astype(np.int32)
+    assert_same(ix.knn(Q, ks, precision="bf16"), oracle.knn_query("l1", X, Q, ks), "l1", "L1 tiles knn mixed k")
+    d = oracle.distances_to("l1", X[:500], Q[4])
+    radii = np.linspace(0.0, 0.9, 300).astype(np.float32) * np.float32(np.median(d))
+    assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l1", X, Q, radii), "l1", "L1 tiles range")
+    ix.close()
+
+
+def test_l1_tiles_concentrated_distances(gts):
+    """Uniform 128-d data: the lower bounds prune almost nothing, every block
+    holds every query, and the kNN phases must lower tau from the probe's."""
+    X, Q = vec_case(30011, 128, 260, seed=61, kind="uniform")
+    ix = gts.Index.build(X, "l1", fanout=20, root_pivot=0)
+    for k in (1, 100):
+        r = ix.knn(Q, k, precision="bf16")
+        assert_same(r, oracle.knn_query("l1", X, Q, k), "l1", f"concentrated knn k={k}")
+    cal = oracle.knn_query("l1", X, Q[:10], 30)
+    radii = np.full(260, np.float32(np.mean(cal[2][cal[0][1:] - 1])), np.float32)
+    assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l1", X, Q, radii), "l1", "concentrated range")
+    ix.close()
+
+
+def test_l1_tiles_fall_back_when_unaligned(gts):
+    X, Q = vec_case(3000, 6, 40, seed=62)
+    ix = gts.Index.build(X, "l1", fanout=6)
+    r = ix.knn(Q, 5, precision="bf16")
+    assert r.stats["tile_pairs"] == 0
+    assert_same(r, oracle.knn_query("l1", X, Q, 5), "l1", "dim 6")
+    ix.close()
+
+
 def test_bf16_precision_same_answers(gts):
     X, Q = vec_case(8000, 64, 120, seed=12)
     ix = gts.Index.build(X, "l2", fanout=10)
@@ -277,7 +320,7 @@ def test_device_inputs_and_results(gts):
 
 # ------------------------------------------------------------------ updates
 
-def _replay(gts, metric, objs_init, pool, seed, cache_limit):
+def _replay(gts, metric, objs_init, pool, seed, cache_limit, precision="fp32"):
     """Insert / delete / query interleaving (Section 4.4) checked against the
     oracle over the objects visible at each query's sequence number."""
     rng = np.random.default_rng(seed)
@@ -324,9 +367,10 @@ def _replay(gts, metric, objs_init, pool, seed, cache_limit):
         qseq = np.full(7, seq, np.int64)
         I, Dl = np.asarray(ins, np.int64), np.asarray(dele, np.int64)
         radii = np.full(7, 2.0 if is_str else 0.8, np.float32)
-        assert_same(ix.range(Qs, radii), oracle.range_query(metric, P, Qs, radii, I, Dl, qseq), metric,
-                    f"update range step {step}")
-        assert_same(ix.knn(Qs, 5), oracle.knn_query(metric, P, Qs, 5, I, Dl, qseq), metric, f"update knn {step}")
+        assert_same(ix.range(Qs, radii, precision=precision), oracle.range_query(metric, P, Qs, radii, I, Dl, qseq),
+                    metric, f"update range step {step}")
+        assert_same(ix.knn(Qs, 5, precision=precision), oracle.knn_query(metric, P, Qs, 5, I, Dl, qseq), metric,
+                    f"update knn {step}")
     # batch update = rebuild
     newb = pool[p:p + 40]
     newobj = strings_from_list(newb) if is_str else np.asarray(newb, np.float32)
@@ -346,7 +390,8 @@ def _replay(gts, metric, objs_init, pool, seed, cache_limit):
     Qs = P.take(np.arange(5)) if is_str else P[:5]
     qseq = np.full(5, seq, np.int64)
     I, Dl = np.asarray(ins, np.int64), np.asarray(dele, np.int64)
-    assert_same(ix.knn(Qs, 8), oracle.knn_query(metric, P, Qs, 8, I, Dl, qseq), metric, "after batch update")
+    assert_same(ix.knn(Qs, 8, precision=precision), oracle.knn_query(metric, P, Qs, 8, I, Dl, qseq), metric,
+                "after batch update")
     ix.close()
 
 
@@ -355,6 +400,13 @@ def test_updates_vectors(gts, cache_limit):
     X, _ = vec_case(1500, 6, 1, seed=14)
     pool, _ = vec_case(400, 6, 1, seed=15)
     _replay(gts, "l2", X, list(pool), seed=16, cache_limit=cache_limit)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_updates_vectors_l1(gts, precision):
+    X, _ = vec_case(1500, 8, 1, seed=24)
+    pool, _ = vec_case(400, 8, 1, seed=25)
+    _replay(gts, "l1", X, list(pool), seed=26, cache_limit=7, precision=precision)
 
 
 def test_updates_strings(gts):

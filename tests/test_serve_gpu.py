@@ -23,7 +23,7 @@ def gts():
     return g
 
 
-@pytest.mark.parametrize("metric,prec", [("l2", "fp32"), ("l2", "bf16"), ("l1", "fp32")])
+@pytest.mark.parametrize("metric,prec", [("l2", "fp32"), ("l2", "bf16"), ("l1", "fp32"), ("l1", "bf16")])
 def test_mixed_stream_equals_alone(gts, metric, prec):
     X, Q = small_vectors(30011, 64, 240, seed=61)
     ix = gts.Index.build(X, metric, fanout=12, root_pivot=0)
