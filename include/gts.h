@@ -217,6 +217,44 @@ gts_status gts_table(const gts_index *index, int64_t *ids, float *table);
  * may be NULL.  Synchronous. */
 gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *ids, float *dist);
 
+/* Launch parameters of the tile kernels and the kNN schedule, held per index.
+ * No counterpart in the paper (its kernels are launched per level with fixed
+ * shapes).  None of them changes a result: every setting returns the same
+ * answers; they trade speed only.
+ *  l1_queries: L1 tiles, queries per chunk (64 or 128; default 64).
+ *  l1_packed:  L1 tiles, 1 = two coordinates per packed FP32 subtraction
+ *              (default), 0 = scalar subtraction (same rounding).
+ *  knn_phases: L1 tile kNN, 1 .. 3 launches over growing shares of the
+ *              node blocks with tau_q lowered from the answer so far in
+ *              between (default 3).
+ *  probe_rows: kNN probe, object rows evaluated before the descent to bound
+ *              the k-th distance, 0 .. 4096 (default 1024).
+ *  tuned:      output only: 1 once gts_autotune has run on the index. */
+typedef struct {
+    int32_t l1_queries;
+    int32_t l1_packed;
+    int32_t knn_phases;
+    int32_t probe_rows;
+    int32_t tuned;
+    int32_t reserved_[3];
+} gts_tuning;
+
+/* Read / replace the index's tuning.  A query copies it when it starts, so a
+ * change affects later queries only.  Out-of-range values: GTS_EINVAL. */
+gts_status gts_get_tuning(gts_index *index, gts_tuning *out);
+gts_status gts_set_tuning(gts_index *index, const gts_tuning *tuning);
+
+/* Autotuner: run the sample batch `queries` (range with `radii`, or kNN with
+ * `k`: exactly one of the two non-NULL, laid out as for gts_range / gts_knn)
+ * `reps` times (1 .. 100) under each candidate setting, coordinate by
+ * coordinate starting from the current one, keep the setting with the
+ * smallest median wall time, store it in the index (tuned = 1) and return it
+ * in *out (may be NULL).  opts as for the query calls (precision, stream,
+ * budget); its stats / stage_ms are ignored.  The answers are discarded.  On
+ * an error the index keeps the best setting found so far. */
+gts_status gts_autotune(gts_index *index, const gts_objects *queries, const float *radii, const int32_t *k,
+                        const gts_query_opts *opts, int32_t reps, gts_tuning *out);
+
 /* Diagnostic, no counterpart in the paper: runs the tensor-core tile
  * primitives of the BF16 L2 path (TMA load with 128-byte swizzle, tcgen05.mma
  * with the accumulator in TMEM, tcgen05.ld) on one 128 x N x K product:

@@ -72,10 +72,18 @@ class _Info(ctypes.Structure):
                 ("dim", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("l1_queries", ctypes.c_int32), ("l1_packed", ctypes.c_int32), ("knn_phases", ctypes.c_int32),
+                ("probe_rows", ctypes.c_int32), ("tuned", ctypes.c_int32), ("reserved_", ctypes.c_int32 * 3)]
+
+
+TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows"]
+
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
            "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc", "gts_serve_start",
-           "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop"]
+           "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop", "gts_get_tuning",
+           "gts_set_tuning", "gts_autotune"]
 
 
 def lib(path: Optional[str] = None):
@@ -104,7 +112,12 @@ def lib(path: Optional[str] = None):
     L.gts_serve_wait.argtypes = [P, I64, I32, ctypes.POINTER(_Result), ctypes.POINTER(ctypes.c_double)]
     L.gts_serve_stats.argtypes = [P, P]
     L.gts_serve_stop.argtypes = [P]
-    for f in ["gts_serve_start", "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop"]:
+    L.gts_get_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
+    L.gts_set_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
+    L.gts_autotune.argtypes = [P, ctypes.POINTER(_Objects), P, P, ctypes.POINTER(_QueryOpts), I32,
+                               ctypes.POINTER(_Tuning)]
+    for f in ["gts_serve_start", "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop",
+              "gts_get_tuning", "gts_set_tuning", "gts_autotune"]:
         getattr(L, f).restype = ctypes.c_int
     L.gts_knn_scan_noalloc.argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
     L.gts_knn_scan_noalloc.restype = ctypes.c_int
@@ -295,6 +308,38 @@ class Index:
             kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
         return self._query(lib().gts_knn, queries, kk, precision, result_on_device, memory_budget, seq, stream,
                            timing)
+
+    def get_tuning(self) -> dict:
+        t = _Tuning()
+        _check(lib().gts_get_tuning(self._h, ctypes.byref(t)))
+        return {f: int(getattr(t, f)) for f in TUNING_FIELDS + ["tuned"]}
+
+    def set_tuning(self, **kw):
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = _Tuning(**{f: int(cur[f]) for f in TUNING_FIELDS})
+        _check(lib().gts_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, queries, k=None, radii=None, precision="fp32", reps=3, memory_budget=0, stream=None) -> dict:
+        """Time the sample batch under each candidate setting and keep the
+        fastest (gts_autotune); returns the chosen setting."""
+        m = _Marshal(queries)
+        n = m.obj.n
+        kk = None if k is None else np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
+        rr = None if radii is None else np.ascontiguousarray(np.broadcast_to(np.asarray(radii, np.float32), (n,)),
+                                                             np.float32)
+        if m.obj.on_device:
+            import torch
+            kk = None if kk is None else torch.from_numpy(kk).cuda()
+            rr = None if rr is None else torch.from_numpy(rr).cuda()
+        opts = _QueryOpts(stream=stream if stream is not None else _stream_of(m.first),
+                          precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
+                          memory_budget=int(memory_budget))
+        out = _Tuning()
+        _check(lib().gts_autotune(self._h, ctypes.byref(m.obj), _ptr(rr) if rr is not None else None,
+                                  _ptr(kk) if kk is not None else None, ctypes.byref(opts), int(reps),
+                                  ctypes.byref(out)))
+        return {f: int(getattr(out, f)) for f in TUNING_FIELDS + ["tuned"]}
 
     def insert(self, objects) -> np.ndarray:
         m = _Marshal(objects)

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -458,6 +459,35 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
     });
 }
 
+void check_tuning(const gts_tuning *t) {
+    GTS_REQUIRE(t != nullptr, GTS_EINVAL, "tuning is NULL");
+    GTS_REQUIRE(t->l1_queries == 64 || t->l1_queries == 128, GTS_EINVAL, "l1_queries must be 64 or 128");
+    GTS_REQUIRE(t->l1_packed == 0 || t->l1_packed == 1, GTS_EINVAL, "l1_packed must be 0 or 1");
+    GTS_REQUIRE(t->knn_phases >= 1 && t->knn_phases <= 3, GTS_EINVAL, "knn_phases must be in 1 .. 3");
+    GTS_REQUIRE(t->probe_rows >= 0 && t->probe_rows <= 4096, GTS_EINVAL, "probe_rows must be in 0 .. 4096");
+}
+
+gts_tuning to_c(const Tuning &t) {
+    gts_tuning o;
+    std::memset(&o, 0, sizeof(o));
+    o.l1_queries = t.l1_queries;
+    o.l1_packed = t.l1_packed;
+    o.knn_phases = t.knn_phases;
+    o.probe_rows = t.probe_rows;
+    o.tuned = t.tuned;
+    return o;
+}
+
+Tuning from_c(const gts_tuning &o, int tuned) {
+    Tuning t;
+    t.l1_queries = o.l1_queries;
+    t.l1_packed = o.l1_packed;
+    t.knn_phases = o.knn_phases;
+    t.probe_rows = o.probe_rows;
+    t.tuned = tuned;
+    return t;
+}
+
 }  // namespace
 }  // namespace gts
 
@@ -704,6 +734,95 @@ gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *
         ensure_device();
         tc_selftest(A, B, N, K, D);
     });
+}
+
+gts_status gts_get_tuning(gts_index *ix, gts_tuning *out) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr && out != nullptr, GTS_EINVAL, "index or output is NULL");
+        std::lock_guard<std::mutex> g(ix->tune_mu);
+        *out = to_c(ix->tuning);
+    });
+}
+
+gts_status gts_set_tuning(gts_index *ix, const gts_tuning *t) {
+    return guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        check_tuning(t);
+        std::lock_guard<std::mutex> g(ix->tune_mu);
+        ix->tuning = from_c(*t, ix->tuning.tuned);
+    });
+}
+
+gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *radii, const int32_t *k,
+                        const gts_query_opts *opts, int32_t reps, gts_tuning *out) {
+    gts_tuning best;
+    gts_status s = guarded([&] {
+        GTS_REQUIRE(ix != nullptr, GTS_EINVAL, "index is NULL");
+        GTS_REQUIRE((radii == nullptr) != (k == nullptr), GTS_EINVAL, "give radii (range) or k (kNN), not both");
+        GTS_REQUIRE(reps >= 1 && reps <= 100, GTS_EINVAL, "reps must be in 1 .. 100");
+        std::lock_guard<std::mutex> g(ix->tune_mu);
+        best = to_c(ix->tuning);
+    });
+    if (s != GTS_OK) return s;
+    const bool knn = k != nullptr;
+    gts_query_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    o.stats = nullptr;
+    o.stage_ms = nullptr;
+    o.result_on_device = 1;
+    // one setting: the median wall time of `reps` runs of the sample batch
+    auto time_it = [&](const gts_tuning &t, double &ms) -> gts_status {
+        gts_status r = gts_set_tuning(ix, &t);
+        if (r != GTS_OK) return r;
+        std::vector<double> v;
+        for (int i = 0; i < reps; ++i) {
+            gts_result res;
+            std::memset(&res, 0, sizeof(res));
+            const auto t0 = std::chrono::steady_clock::now();
+            r = query_common(ix, queries, radii, k, &o, &res, knn);
+            const auto t1 = std::chrono::steady_clock::now();
+            if (r != GTS_OK) return r;
+            gts_result_free(&res);
+            v.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+        }
+        std::sort(v.begin(), v.end());
+        ms = v[v.size() / 2];
+        return GTS_OK;
+    };
+    // coordinate descent over the parameters that apply to this index
+    std::vector<std::pair<int32_t gts_tuning::*, std::vector<int32_t>>> space;
+    if (ix->metric == GTS_L1) {
+        space.push_back({&gts_tuning::l1_queries, {64, 128}});
+        space.push_back({&gts_tuning::l1_packed, {0, 1}});
+        if (knn) space.push_back({&gts_tuning::knn_phases, {1, 2, 3}});
+    }
+    if (knn && ix->metric != GTS_EDIT) space.push_back({&gts_tuning::probe_rows, {0, 256, 1024, 4096}});
+    double best_ms = 0.0;
+    s = time_it(best, best_ms);   // the first run also warms every lazily built structure
+    if (s == GTS_OK) s = time_it(best, best_ms);
+    for (auto &dim : space) {
+        if (s != GTS_OK) break;
+        for (int32_t v : dim.second) {
+            if (best.*(dim.first) == v) continue;
+            gts_tuning t = best;
+            t.*(dim.first) = v;
+            double ms = 0.0;
+            s = time_it(t, ms);
+            if (s != GTS_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    gts_status s2 = guarded([&] {
+        std::lock_guard<std::mutex> g(ix->tune_mu);
+        ix->tuning = from_c(best, s == GTS_OK ? 1 : ix->tuning.tuned);
+        best = to_c(ix->tuning);
+    });
+    if (out) *out = best;
+    return s != GTS_OK ? s : s2;
 }
 
 void gts_result_free(gts_result *r) {

@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -155,6 +156,16 @@ struct Cache {
     int max_len = 0;
 };
 
+// Launch parameters of the tile kernels and of the kNN schedule.  None of
+// them changes a result; gts_autotune picks them by timing.
+struct Tuning {
+    int l1_queries = 64;    // L1 tiles: queries per chunk (64 or 128)
+    int l1_packed = 1;      // L1 tiles: packed f32x2 subtraction
+    int knn_phases = 3;     // L1 tile kNN: phases (1..3)
+    int probe_rows = 1024;  // kNN probe: rows evaluated before the descent (0..4096)
+    int tuned = 0;
+};
+
 }  // namespace gts
 
 struct gts_index {
@@ -170,6 +181,8 @@ struct gts_index {
     uint64_t seed = 0;
     int64_t rebuilds = 0;
     std::vector<cudaEvent_t> events;   // reused by per-stage timing
+    std::mutex tune_mu;
+    gts::Tuning tuning;
     std::atomic<int64_t> tc_pairs_hint[2] = {{0}, {0}}; // last tensor-core output size per query (x1024)
     std::atomic<int64_t> l1_pairs_hint[4] = {{0}, {0}, {0}, {0}};  // L1 tiles: range, kNN phases 0..2 (same unit)
     ~gts_index() {

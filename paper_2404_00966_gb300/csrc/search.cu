@@ -185,6 +185,48 @@ __global__ void k_pivdist_str(Dev d, const int32_t *__restrict__ eq, const int32
 
 // ---------------------------------------------------------------- kNN threshold
 
+// Insert (u, id) into the ascending list D/I of n (<= K) distinct ids if it
+// belongs among the K smallest (u, id).  Warp-cooperative: every lane passes
+// the same arguments and gets the same n back; the duplicate test, the
+// insert position and the shift take n / 32 steps per lane.
+__device__ __forceinline__ void warp_tau_insert(double *D, int64_t *I, int &n, int K, double u, int64_t id,
+                                                int lane) {
+    if (n >= K && !(u < D[K - 1] || (u == D[K - 1] && id < I[K - 1]))) return;
+    bool dup = false;
+    int below = 0;
+    for (int i = lane; i < n; i += 32) {
+        const double di = D[i];
+        const int64_t ii = I[i];
+        dup |= ii == id;
+        below += (di < u || (di == u && ii < id)) ? 1 : 0;
+    }
+    if (__any_sync(0xffffffffu, dup)) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+    const int last = n < K ? n : K - 1;   // entries [below, last) move up one; a full list drops entry K-1
+    for (int top = last - 1; top >= below; top -= 32) {
+        const int i = top - lane;
+        double dv = 0.0;
+        int64_t iv = 0;
+        if (i >= below) {
+            dv = D[i];
+            iv = I[i];
+        }
+        __syncwarp();
+        if (i >= below) {
+            D[i + 1] = dv;
+            I[i + 1] = iv;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        D[below] = u;
+        I[below] = id;
+    }
+    __syncwarp();
+    if (n < K) ++n;
+}
+
 // Warp per query.  The query's list of the k smallest (upper bound, id) of
 // distinct visible pivots seen so far is merged with this level's entries;
 // tau_q = the k-th bound, rounded up to float, or +inf while fewer than k.
@@ -224,25 +266,7 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
             bal &= bal - 1;
             const double u = __shfl_sync(0xffffffffu, ub, src);
             const int64_t iid = __shfl_sync(0xffffffffu, id, src);
-            if (lane == 0) {
-                bool dup = false;
-                for (int i = 0; i < n; ++i)
-                    if (I[i] == iid) { dup = true; break; }
-                const bool fits = n < K || u < D[K - 1] || (u == D[K - 1] && iid < I[K - 1]);
-                if (!dup && fits) {
-                    int p = n < K ? n : K - 1;
-                    while (p > 0 && (D[p - 1] > u || (D[p - 1] == u && I[p - 1] > iid))) {
-                        D[p] = D[p - 1];
-                        I[p] = I[p - 1];
-                        --p;
-                    }
-                    D[p] = u;
-                    I[p] = iid;
-                    if (n < K) ++n;
-                }
-            }
-            n = __shfl_sync(0xffffffffu, n, 0);
-            __syncwarp();
+            warp_tau_insert(D, I, n, K, u, iid, lane);
         }
     }
     if (lane == 0) {
@@ -250,23 +274,6 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
         tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
     }
     }
-}
-
-// Insert (u, id) into the ascending list D/I of n (<= K) distinct ids if it
-// belongs among the K smallest (u, id).  One thread.
-__device__ __forceinline__ void tau_insert(double *D, int64_t *I, int &n, int K, double u, int64_t id) {
-    for (int i = 0; i < n; ++i)
-        if (I[i] == id) return;
-    if (n >= K && !(u < D[K - 1] || (u == D[K - 1] && id < I[K - 1]))) return;
-    int p = n < K ? n : K - 1;
-    while (p > 0 && (D[p - 1] > u || (D[p - 1] == u && I[p - 1] > id))) {
-        D[p] = D[p - 1];
-        I[p] = I[p - 1];
-        --p;
-    }
-    D[p] = u;
-    I[p] = id;
-    if (n < K) ++n;
 }
 
 struct LevelOffsets {
@@ -284,6 +291,68 @@ constexpr int kProbeNodes = 4;   // last-level nodes whose rows the kNN probe ev
 // nodes with the nearest pivots.  Every visible object so
 // evaluated enters the query's threshold list, so tau_q starts at (an upper
 // bound of) the k-th smallest of them instead of +inf.
+// One lane's distance from q to one row (coordinates in increasing order;
+// L2 returns the square).  The FP32 bound of the plain path covers any order.
+template <bool L2>
+__device__ __forceinline__ float lane_vec_dist(const float *__restrict__ q, const float *__restrict__ x, int dim) {
+    float s = 0.f;
+    if ((dim & 3) == 0 && ((((uintptr_t)q) | ((uintptr_t)x)) & 15) == 0) {
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        for (int i = 0; i < (dim >> 2); ++i) {
+            const float4 a = q4[i], b = __ldg(x4 + i);
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            if (L2) s += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+            else s += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        }
+    } else {
+        for (int i = 0; i < dim; ++i) {
+            const float t = q[i] - __ldg(x + i);
+            s += L2 ? t * t : fabsf(t);
+        }
+    }
+    return s;
+}
+
+// Rows [pos, pos + m) into the threshold list, a row per lane.
+template <bool L2>
+__device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_t pos, int32_t m, int64_t s, int K,
+                                           double *D, int64_t *I, int &n, double up, int lane) {
+    for (int32_t r0 = 0; r0 < m; r0 += 32) {
+        const int32_t r = r0 + lane;
+        bool cand = false;
+        double ub = 0.0;
+        int64_t id = 0;
+        if (r < m) {
+            const int64_t row = pos + r;
+            if (d.row_del[row] > s) {
+                const float sq = lane_vec_dist<L2>(qv, d.X + row * d.dim, d.dim);
+                const float dv = L2 ? sqrtf(sq) : sq;
+                ub = (double)dv * up + (double)kAbsFloor;
+                id = d.row_id[row];
+                cand = n < K || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, cand);
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const double u = __shfl_sync(0xffffffffu, ub, src);
+            const int64_t iid = __shfl_sync(0xffffffffu, id, src);
+            warp_tau_insert(D, I, n, K, u, iid, lane);
+        }
+    }
+}
+
+// Probe for kNN (warp per query).  Section 3 notes that MkNNQ(q, k) is
+// MRQ(q, d_k) once d_k is known; the probe bounds d_k from above before the
+// batched descent.  It follows one root-to-last-level path: at every level it
+// computes the distances from q to the pivots of all non-empty children and
+// descends into the child whose pivot is nearest; at the last pivot level it
+// computes the distances to the rows (up to `cap` in all) of the kProbeNodes
+// nodes with the nearest pivots.  Every visible object so evaluated enters
+// the query's threshold list, so tau_q starts at (an upper bound of) the k-th
+// smallest of them instead of +inf.
 template <bool L2>
 __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id, int32_t *tk_n,
@@ -303,18 +372,12 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
         const int32_t prow = d.npiv[lo_off.v[0]];
         const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
         const float dq = L2 ? sqrtf(sq) : sq;
-        if (lane == 0 && d.row_del[prow] > s) tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
+        if (d.row_del[prow] > s) warp_tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow], lane);
     }
     int64_t node = 0;
     if (d.h == 1) {   // one pivot level: the root's own rows
         const int32_t m = d.nsize[lo_off.v[0]] < cap ? d.nsize[lo_off.v[0]] : cap;
-        for (int32_t r = 0; r < m; ++r) {
-            const int64_t row = d.npos[lo_off.v[0]] + r;
-            const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
-            const float dv = L2 ? sqrtf(sq) : sq;
-            if (lane == 0 && d.row_del[row] > s)
-                tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
-        }
+        probe_rows<L2>(d, qv, d.npos[lo_off.v[0]], m, s, K, D, I, n, up, lane);
     }
     for (int l = 1; l < d.h; ++l) {
         // the kProbeNodes children with the nearest pivots (ascending), kept by every lane
@@ -332,8 +395,8 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             const int32_t prow = d.npiv[g];
             const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
             const float dq = L2 ? sqrtf(sq) : sq;
-            if (lane == 0 && d.row_del[prow] > s)
-                tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow]);
+            if (d.row_del[prow] > s)
+                warp_tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow], lane);
             if (dq < bd[kProbeNodes - 1]) {
                 float vd = dq;
                 int64_t vn = c;
@@ -359,16 +422,9 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             for (int i = 0; i < kProbeNodes; ++i) {
                 if (bn[i] < 0 || budget <= 0) continue;
                 const int64_t g = lo_off.v[l] + bn[i];
-                const int32_t pos = d.npos[g];
                 const int32_t m = d.nsize[g] < budget ? d.nsize[g] : budget;
                 budget -= m;
-                for (int32_t r = 0; r < m; ++r) {
-                    const int64_t row = pos + r;
-                    const float sq = warp_vec_dist<L2>(qv, d.X + row * d.dim, d.dim, lane);
-                    const float dv = L2 ? sqrtf(sq) : sq;
-                    if (lane == 0 && d.row_del[row] > s)
-                        tau_insert(D, I, n, K, (double)dv * up + (double)kAbsFloor, d.row_id[row]);
-                }
+                probe_rows<L2>(d, qv, d.npos[g], m, s, K, D, I, n, up, lane);
             }
         }
     }
@@ -1172,6 +1228,7 @@ struct Runner {
     StageClock clk;
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
     bool use_l1 = false;   // FP32 CUDA-core tiles at the last level (L1)
+    Tuning tu;             // launch parameters (a copy of the index's)
     int64_t st_tile_pairs = 0;
     DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
     DBuf<float> tcqn2;
@@ -1511,9 +1568,13 @@ struct Runner {
         lq.knn = knn;
         lq.rel = d.rel;
         lq.any_deleted = tq.any_deleted;
+        lq.queries = tu.l1_queries;
+        lq.packed = tu.l1_packed != 0;
         std::vector<int64_t> bounds = {0};
-        if (knn) {
-            for (int64_t f : {64, 8}) {
+        if (knn && tu.knn_phases > 1) {
+            const int64_t fr[2] = {tu.knn_phases >= 3 ? 64 : 0, 8};
+            for (int64_t f : fr) {
+                if (f == 0) continue;
                 const int64_t b = rg.n_items / f;
                 if (b > bounds.back()) bounds.push_back(b);
             }
@@ -1701,6 +1762,10 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     Cache &c = ix->cache;
     const int64_t nq = qb.nq;
     Runner R(ix, qb, knn, budget, st);
+    {
+        std::lock_guard<std::mutex> g(ix->tune_mu);
+        R.tu = ix->tuning;
+    }
     R.clk.on = stage_ms != nullptr;
     {
         int dev = 0, sms = 0;
@@ -1788,7 +1853,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     if (knn && t.n > 0 && nq > 0 && t.dim > 0) {
         LevelOffsets lo_off;
         for (int l = 0; l <= t.h && l < kMaxHeight + 2; ++l) lo_off.v[l] = t.lvl_off[l];
-        const int cap = 1024;
+        const int cap = R.tu.probe_rows;
         R.clk.begin(GTS_STAGE_THRESHOLD);
         if (t.metric == GTS_L2)
             k_probe_vec<true><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),

@@ -34,10 +34,9 @@ namespace gts {
 namespace {
 
 constexpr int kRowsL1 = 128;   // rows of one node block (the regrouping's block size)
-constexpr int kNQL1 = 128;     // queries of one chunk
+constexpr int kNQL1 = 128;     // queries of one chunk, at most (8 warps x QPT)
 constexpr int kThreadsL1 = 256;
 constexpr int kRPT = 4;        // rows per thread: lane + 32 i
-constexpr int kQPT = 16;       // queries per thread: 16 warp + j
 constexpr int kKC = 32;        // coordinates per pipeline stage
 constexpr int kLd = kKC + 4;   // padded shared-memory row stride (floats): conflict-free 16-byte loads
 
@@ -79,6 +78,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 
 // copy coordinates [k0, k0 + 32) of the block's rows and of the chunk's
 // queries; coordinates past dim and rows / queries past the block are zeros
+template <int NQ>
 __device__ __forceinline__ void stage_slice(const L1Args &a, int64_t row0, int nrow, const int32_t *sq, int cnt,
                                             int k0, float *sX, float *sQ) {
     const int tid = threadIdx.x;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void stage_slice(const L1Args &a, int64_t row0, int n
         cp16(sX + r * kLd + ch * 4, src, v);
     }
 #pragma unroll
-    for (int c = tid; c < kNQL1 * (kKC / 4); c += kThreadsL1) {
+    for (int c = tid; c < NQ * (kKC / 4); c += kThreadsL1) {
         const int j = c >> 3, ch = c & 7, k = k0 + ch * 4;
         const bool v = j < cnt && k < a.dim;
         const float *src = v ? a.Q + (int64_t)sq[j] * a.dim + k : a.Q;
@@ -98,7 +98,43 @@ __device__ __forceinline__ void stage_slice(const L1Args &a, int64_t row0, int n
     }
 }
 
+// acc += |x_0 - q_0| + ... + |x_3 - q_3| in coordinate order.  X2 forms the
+// four differences with two packed FP32 subtractions (sub.rn.f32x2, two
+// IEEE round-to-nearest results per instruction, the same values as four
+// scalar subtractions), so a pair costs 1.5 instead of 2 instructions per
+// coordinate.
+template <bool X2>
+__device__ __forceinline__ float l1_step4(float acc, const float4 &x, const float4 &q) {
+    float d0, d1, d2, d3;
+    if (X2) {
+        asm("{\n\t.reg .b64 xa, qa, ra;\n\t"
+            "mov.b64 xa, {%2, %3};\n\tmov.b64 qa, {%4, %5};\n\t"
+            "sub.rn.f32x2 ra, xa, qa;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+            : "=f"(d0), "=f"(d1)
+            : "f"(x.x), "f"(x.y), "f"(q.x), "f"(q.y));
+        asm("{\n\t.reg .b64 xa, qa, ra;\n\t"
+            "mov.b64 xa, {%2, %3};\n\tmov.b64 qa, {%4, %5};\n\t"
+            "sub.rn.f32x2 ra, xa, qa;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+            : "=f"(d2), "=f"(d3)
+            : "f"(x.z), "f"(x.w), "f"(q.z), "f"(q.w));
+    } else {
+        d0 = x.x - q.x;
+        d1 = x.y - q.y;
+        d2 = x.z - q.z;
+        d3 = x.w - q.w;
+    }
+    acc += fabsf(d0);
+    acc += fabsf(d1);
+    acc += fabsf(d2);
+    acc += fabsf(d3);
+    return acc;
+}
+
+// QPT queries per thread (a chunk of 8 QPT queries); X2: packed subtraction
+template <int QPT, bool X2>
 __global__ void __launch_bounds__(kThreadsL1, 2) k_tile_l1(L1Args a) {
+    constexpr int NQ = 8 * QPT;
+    constexpr int kQPT = QPT;
     extern __shared__ __align__(16) float smem_l1[];
     float *sX = smem_l1;                                 // 2 x [128][kLd]
     float *sQ = sX + 2 * kRowsL1 * kLd;                  // 2 x [128][kLd]
@@ -131,8 +167,8 @@ __global__ void __launch_bounds__(kThreadsL1, 2) k_tile_l1(L1Args a) {
             sRowBit[tid] = tid < nrow ? (1ull << jl) : 0ull;
             sRowDel[tid] = (tid < nrow && a.any_deleted) ? a.row_del[row0 + tid] : kNever;
         }
-        for (int c0 = 0; c0 < total; c0 += kNQL1) {
-            const int cnt = min(kNQL1, total - c0);
+        for (int c0 = 0; c0 < total; c0 += NQ) {
+            const int cnt = min(NQ, total - c0);
             for (int j = tid; j < cnt; j += kThreadsL1) {
                 const TileRec rc = a.grec[first + c0 + j];
                 sRec[j] = rc;
@@ -146,13 +182,13 @@ __global__ void __launch_bounds__(kThreadsL1, 2) k_tile_l1(L1Args a) {
             for (int i = 0; i < kRPT; ++i)
 #pragma unroll
                 for (int j = 0; j < kQPT; ++j) acc[i][j] = 0.f;
-            stage_slice(a, row0, nrow, sQid, cnt, 0, sX, sQ);
+            stage_slice<NQ>(a, row0, nrow, sQid, cnt, 0, sX, sQ);
             cp_commit();
             for (int s = 0; s < nstage; ++s) {
                 const int b = s & 1;
                 if (s + 1 < nstage) {
-                    stage_slice(a, row0, nrow, sQid, cnt, (s + 1) * kKC, sX + (b ^ 1) * kRowsL1 * kLd,
-                                sQ + (b ^ 1) * kNQL1 * kLd);
+                    stage_slice<NQ>(a, row0, nrow, sQid, cnt, (s + 1) * kKC, sX + (b ^ 1) * kRowsL1 * kLd,
+                                    sQ + (b ^ 1) * kNQL1 * kLd);
                     cp_commit();
                     cp_wait<1>();
                 } else {
@@ -162,7 +198,7 @@ __global__ void __launch_bounds__(kThreadsL1, 2) k_tile_l1(L1Args a) {
                 if (active) {
                     const float *xs = sX + b * kRowsL1 * kLd + lane * kLd;
                     const float *qs = sQ + b * kNQL1 * kLd + warp * kQPT * kLd;
-#pragma unroll
+#pragma unroll 1
                     for (int kk = 0; kk < kKC; kk += 4) {
                         float4 xv[kRPT];
 #pragma unroll
@@ -171,14 +207,7 @@ __global__ void __launch_bounds__(kThreadsL1, 2) k_tile_l1(L1Args a) {
                         for (int j = 0; j < kQPT; ++j) {
                             const float4 qv = *reinterpret_cast<const float4 *>(qs + j * kLd + kk);
 #pragma unroll
-                            for (int i = 0; i < kRPT; ++i) {
-                                float s0 = acc[i][j];
-                                s0 += fabsf(xv[i].x - qv.x);
-                                s0 += fabsf(xv[i].y - qv.y);
-                                s0 += fabsf(xv[i].z - qv.z);
-                                s0 += fabsf(xv[i].w - qv.w);
-                                acc[i][j] = s0;
-                            }
+                            for (int i = 0; i < kRPT; ++i) acc[i][j] = l1_step4<X2>(acc[i][j], xv[i], qv);
                         }
                     }
                 }
@@ -254,9 +283,11 @@ int64_t l1_run(const Tree &t, const L1Query &lq, const TcRegroup &rg, int64_t i0
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t smem = l1_smem_bytes();
-    GTS_CUDA(cudaFuncSetAttribute(k_tile_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void (*kern)(L1Args) = lq.queries <= 64 ? (lq.packed ? k_tile_l1<8, true> : k_tile_l1<8, false>)
+                                            : (lq.packed ? k_tile_l1<16, true> : k_tile_l1<16, false>);
+    GTS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_l1, kThreadsL1, smem));
+    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsL1, smem));
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(i1 - i0, (int64_t)sms * per_sm);
     DBuf<int> counter(1, st);
@@ -292,7 +323,7 @@ int64_t l1_run(const Tree &t, const L1Query &lq, const TcRegroup &rg, int64_t i0
         a.out_count = count.get();
         a.rel = lq.rel;
         a.any_deleted = lq.any_deleted;
-        k_tile_l1<<<(unsigned)grid, kThreadsL1, smem, st>>>(a);
+        kern<<<(unsigned)grid, kThreadsL1, smem, st>>>(a);
         ++*launches;
         check_launch("L1 tile");
         unsigned long long hcount = 0;

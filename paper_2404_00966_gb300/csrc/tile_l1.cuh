@@ -12,6 +12,8 @@ struct L1Query {
     bool knn = false;
     float rel = 0.f;              // FP32 relative error bound of one distance
     int any_deleted = 1;
+    int queries = 64;             // queries per chunk: 64 or 128
+    bool packed = true;           // packed f32x2 subtraction
 };
 
 // the tile path needs dim % 4 == 0 and 16-byte aligned rows and queries

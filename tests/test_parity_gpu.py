@@ -287,6 +287,38 @@ def test_l1_tiles_fall_back_when_unaligned(gts):
     ix.close()
 
 
+@pytest.mark.parametrize("metric,prec", [("l1", "bf16"), ("l2", "bf16"), ("l2", "fp32")])
+def test_every_tuning_gives_the_same_answers(gts, metric, prec):
+    X, Q = vec_case(12007, 64, 150, seed=71, kind="uniform" if metric == "l1" else "gauss")
+    ix = gts.Index.build(X, metric, fanout=10, root_pivot=2)
+    ks = np.random.default_rng(72).integers(1, 60, size=150).astype(np.int32)
+    want = oracle.knn_query(metric, X, Q, ks)
+    cal = oracle.knn_query(metric, X, Q[:5], 20)
+    radii = np.full(150, np.float32(np.mean(cal[2][cal[0][1:] - 1])), np.float32)
+    want_r = oracle.range_query(metric, X, Q, radii)
+    for lq in (64, 128):
+        for packed in (0, 1):
+            for phases in (1, 2, 3):
+                for probe in (0, 256, 4096):
+                    if metric != "l1" and (lq, packed, phases) != (128, 1, 3):
+                        continue
+                    ix.set_tuning(l1_queries=lq, l1_packed=packed, knn_phases=phases, probe_rows=probe)
+                    tag = f"{lq}/{packed}/{phases}/{probe}"
+                    assert_same(ix.knn(Q, ks, precision=prec), want, metric, f"knn tuning {tag}")
+                    if probe == 0:
+                        assert_same(ix.range(Q, radii, precision=prec), want_r, metric, f"range tuning {tag}")
+    with pytest.raises(gts.GTSError):
+        ix.set_tuning(knn_phases=4)
+    t = ix.autotune(Q, k=ks, precision=prec, reps=1)
+    assert t["tuned"] == 1 and t["l1_queries"] in (64, 128) and 0 <= t["probe_rows"] <= 4096
+    assert ix.get_tuning() == t
+    assert_same(ix.knn(Q, ks, precision=prec), want, metric, "after autotune")
+    t2 = ix.autotune(Q, radii=radii, precision=prec, reps=1)
+    assert t2["tuned"] == 1
+    assert_same(ix.range(Q, radii, precision=prec), want_r, metric, "after range autotune")
+    ix.close()
+
+
 def test_bf16_precision_same_answers(gts):
     X, Q = vec_case(8000, 64, 120, seed=12)
     ix = gts.Index.build(X, "l2", fanout=10)
