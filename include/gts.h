@@ -128,7 +128,8 @@ enum {
     GTS_STAT_TILES = 9,        /* tile work items: 128-row blocks of last-level nodes */
     GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries run against those blocks */
     GTS_STAT_TILE_PAIRS = 11,  /* (query, row) pairs whose distance the tiles computed */
-    GTS_STATS_LEN = 12
+    GTS_STAT_DENSE_PAIRS = 12, /* (query, pivot) distances computed as dense per-level matrices */
+    GTS_STATS_LEN = 13
 };
 
 /* Per-query answers in CSR form: the answers of query i are

@@ -26,6 +26,7 @@
 
 #include "gts_impl.cuh"
 #include "metric.cuh"
+#include "pivot_dense.cuh"
 #include "tile_l1.cuh"
 #include "tile_tc.cuh"
 
@@ -155,6 +156,14 @@ __global__ void k_pivdist_vec(Dev d, const int32_t *__restrict__ eq, const int32
             if (lane == 0) path[e * d.h + l] = L2 ? sqrtf(s) : s;
         }
     }
+}
+
+// Frontier entries of a level whose distances are in a dense matrix.
+__global__ void k_pivdist_lookup(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode, int64_t e0,
+                                 int64_t e1, const float *__restrict__ dense, int64_t P, float *__restrict__ path,
+                                 int h, int l) {
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x)
+        path[e * h + l] = dense[(int64_t)eq[e] * P + enode[e]];
 }
 
 // Strings: blocks take runs of entries; entries of one query share the
@@ -502,7 +511,8 @@ template <bool L2, int NV>
 __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                                  int64_t lvl_base, int64_t lvl_next, int64_t e0, int64_t e1,
                                  float *__restrict__ path, int l, const float *__restrict__ thr_q,
-                                 uint64_t *__restrict__ mask_out, int32_t *__restrict__ ncount) {
+                                 uint64_t *__restrict__ mask_out, int32_t *__restrict__ ncount,
+                                 const float *__restrict__ dense, int64_t P) {
     constexpr int G = kLastGroup;
     constexpr int V = NV > 0 ? NV : 1;
     const int lane = threadIdx.x & 31;
@@ -521,6 +531,12 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
             my_prow = d.npiv[lvl_base + my_node];
             my_thr = thr_q[my_q];
         }
+        float dq[G];
+        if (dense) {   // distances from the level's dense matrix
+            const float my_d = lane < cnt ? dense[(int64_t)my_q * P + my_node] : 0.f;
+#pragma unroll
+            for (int i = 0; i < G; ++i) dq[i] = __shfl_sync(0xffffffffu, my_d, i);
+        } else {
         // stage 2: pivot rows and query rows of all entries
         float4 pr[G][V], qr[G][V];
 #pragma unroll
@@ -540,7 +556,6 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
             }
         }
         // stage 3: distances
-        float dq[G];
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             dq[i] = 0.f;
@@ -563,6 +578,7 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
                 }
                 dq[i] = L2 ? sqrtf(sq) : sq;
             }
+        }
         }
         // stage 4: leaf intervals of all entries, then the tests; lane i
         // collects entry i's mask
@@ -598,7 +614,34 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
         if (lane < cnt) {
             path[(a0 + lane) * d.h + l] = my_dq;
             mask_out[a0 + lane - e0] = my_mask;
-            if (my_mask) atomicAdd(&ncount[my_node], 1);
+            if (my_mask && ncount) atomicAdd(&ncount[my_node], 1);
+        }
+    }
+}
+
+// Last pivot level with the distances in a dense matrix: a warp per entry,
+// lane j tests child j's interval (Lemma 1 / 2; coalesced loads of the
+// node's children), the ballot is the leaf mask.
+__global__ void k_leaf_masks_dense(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                                   int64_t lvl_next, int64_t e0, int64_t e1, const float *__restrict__ dense,
+                                   int64_t P, float *__restrict__ path, int l, const float *__restrict__ thr_q,
+                                   uint64_t *__restrict__ mask_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
+        const int32_t q = eq[e], node = enode[e];
+        const float dq = dense[(int64_t)q * P + node];
+        const float thr = thr_q[q];
+        const int64_t c0 = lvl_next + (int64_t)node * d.F;
+        uint64_t m = 0;
+        for (int j0 = 0; j0 < d.F; j0 += 32) {
+            const int j = j0 + lane;
+            const bool keep = j < d.F && d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc);
+            m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
+        }
+        if (lane == 0) {
+            path[e * d.h + l] = dq;
+            mask_out[e - e0] = m;
         }
     }
 }
@@ -1229,7 +1272,10 @@ struct Runner {
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
     bool use_l1 = false;   // FP32 CUDA-core tiles at the last level (L1)
     Tuning tu;             // launch parameters (a copy of the index's)
-    int64_t st_tile_pairs = 0;
+    // dense query-to-pivot matrices per level (tile paths): state 0 undecided, 1 ready, 2 not used
+    std::vector<DBuf<float>> dense;
+    std::vector<int> dense_state;
+    int64_t st_tile_pairs = 0, st_dense_pairs = 0;
     DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
     DBuf<float> tcqn2;
 
@@ -1255,8 +1301,53 @@ struct Runner {
         clk.end();
     }
 
+    // The level's dense distance matrix, computed on the first group that
+    // reaches the level if its frontier holds at least a quarter of the
+    // batch's (query, node) pairs and the matrix fits an eighth of the budget.
+    const float *dense_for(int l, int64_t E) {
+        if (!(use_tc || use_l1) || d.dim == 0) return nullptr;
+        if ((int)dense_state.size() < h) {
+            dense_state.assign(h, 0);
+            dense.resize(h);
+        }
+        if (dense_state[l] == 1) return dense[l].get();
+        if (dense_state[l] == 2) return nullptr;
+        const int64_t P = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
+        const int64_t pairs = qb.nq * P;
+        dense_state[l] = 2;
+        if (!dense_supported(d.metric, d.dim, d.X, d.Q) || 4 * E < pairs || pairs * 4 > budget / 8) return nullptr;
+        dense[l].alloc(pairs, st);
+        clk.begin(GTS_STAGE_PIVOT_DIST);
+        dense_pivot_dist(d.metric, d.X, d.dim, d.Q, qb.nq, d.npiv + ix->tree.lvl_off[l], P, dense[l].get(), st);
+        clk.end();
+        st_dense_pairs += pairs;
+        dense_state[l] = 1;
+        return dense[l].get();
+    }
+
     void pivdist(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
+        if (const float *dm = dense_for(l, e1 - e0)) {
+            const int64_t P = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
+            clk.begin(GTS_STAGE_PIVOT_DIST);
+            k_pivdist_lookup<<<cap(nblocks(e1 - e0, kT)), kT, 0, st>>>(L.q.get(), L.node.get(), e0, e1, dm, P,
+                                                                        L.path.get(), h, l);
+            clk.end();
+            check_launch("pivot distance lookup");
+            st_pivots += e1 - e0;
+            st_frontier += e1 - e0;
+            if (knn) {
+                const int64_t base = ix->tree.lvl_off[l];
+                clk.begin(GTS_STAGE_THRESHOLD);
+                k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+                                                                          L.path.get(), l, qb.nq, qb.k, koff.get(),
+                                                                          tk_d.get(), tk_id.get(), tk_n.get(),
+                                                                          thr.get());
+                clk.end();
+                check_launch("knn threshold");
+            }
+            return;
+        }
         const int64_t base = ix->tree.lvl_off[l];
         const int64_t E = e1 - e0;
         clk.begin(GTS_STAGE_PIVOT_DIST);
@@ -1435,16 +1526,38 @@ struct Runner {
         const int64_t base = ix->tree.lvl_off[l], lvl_next = ix->tree.lvl_off[l + 1];
         const int64_t nn = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
         DBuf<uint64_t> mask(E, st);
-        DBuf<int32_t> ncount(nn, st);
-        GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
+        const bool need_counts = !regroup_uses_bits(ix->tree, qb.nq);
+        DBuf<int32_t> ncount(need_counts ? nn : 0, st);
+        if (need_counts) GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
         const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
         const unsigned grid = cap(nblocks((E + kLastGroup - 1) / kLastGroup, kWarpsPerBlock));
+        const float *dm = dense_for(l, E);
+        // with the distances known up front, this level's pivots lower tau_q
+        // before the leaf masks are formed
+        const bool tau_first = dm != nullptr && knn;
+        if (tau_first) {   // k_tau reads this level's distances from the path
+            clk.begin(GTS_STAGE_PIVOT_DIST);
+            k_pivdist_lookup<<<cap(nblocks(E, kT)), kT, 0, st>>>(L.q.get(), L.node.get(), e0, e1, dm, nn,
+                                                                  L.path.get(), h, l);
+            clk.end();
+            clk.begin(GTS_STAGE_THRESHOLD);
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+                                                                      L.path.get(), l, qb.nq, qb.k, koff.get(),
+                                                                      tk_d.get(), tk_id.get(), tk_n.get(), thr.get());
+            clk.end();
+            check_launch("knn threshold");
+        }
         clk.begin(GTS_STAGE_PIVOT_DIST);
 #define GTS_LL(L2V, NVV)                                                                                 \
     k_last_level_vec<L2V, NVV><<<grid, kT, 0, st>>>(d, L.q.get(), L.node.get(), base, lvl_next, e0, e1, \
-                                                   L.path.get(), l, thr.get(), mask.get(), ncount.get())
-        if (d.metric == GTS_L2) {
+                                                   L.path.get(), l, thr.get(), mask.get(),               \
+                                                   need_counts ? ncount.get() : nullptr, dm, nn)
+        if (dm && !need_counts) {
+            k_leaf_masks_dense<<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), lvl_next, e0,
+                                                                                e1, dm, nn, L.path.get(), l, thr.get(),
+                                                                                mask.get());
+        } else if (d.metric == GTS_L2) {
             switch (nv) {
                 case 1: GTS_LL(true, 1); break;
                 case 2: GTS_LL(true, 2); break;
@@ -1466,7 +1579,7 @@ struct Runner {
         check_launch("last level");
         st_pivots += E;
         st_frontier += E;
-        if (knn) {
+        if (knn && !tau_first) {
             clk.begin(GTS_STAGE_THRESHOLD);
             k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
                                                                       L.path.get(), l, qb.nq, qb.k, koff.get(),
@@ -1474,7 +1587,7 @@ struct Runner {
             clk.end();
             check_launch("knn threshold");
         }
-        tc_leaf(L, e0, e1, mask, &ncount);
+        tc_leaf(L, e0, e1, mask, need_counts ? &ncount : nullptr);
     }
 
     // Last level on the tensor cores: regroup the entries by node, run the
@@ -1948,6 +2061,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_TILES] = R.st_tiles;
         stats[GTS_STAT_TILE_ENTRIES] = R.st_tile_entries;
         stats[GTS_STAT_TILE_PAIRS] = R.st_tile_pairs;
+        stats[GTS_STAT_DENSE_PAIRS] = R.st_dense_pairs;
     }
 }
 

@@ -399,6 +399,86 @@ __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__
     }
 }
 
+// Regrouping through a (node x query) bitmap: bit q of row p is set when the
+// entry (q, p) has a surviving leaf.  Row popcounts give the per-node counts,
+// and an entry's slot within its node is the number of set bits before it,
+// so entries of a node land in ascending query order with no contended
+// atomics (each 32-bit word collects at most 32 entries).
+__global__ void k_bits_set(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                           const uint64_t *__restrict__ emask, int64_t E, int64_t nw, uint32_t *__restrict__ bits) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!emask[e]) continue;
+        const int32_t q = eq[e];
+        atomicOr(&bits[(int64_t)enode[e] * nw + (q >> 5)], 1u << (q & 31));
+    }
+}
+
+// block per row: exclusive popcount prefix of the row's words, and the count
+__global__ void k_bits_rows(const uint32_t *__restrict__ bits, int64_t nn, int64_t nw, int32_t *__restrict__ wpre,
+                            int32_t *__restrict__ ncount) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t row = blockIdx.x; row < nn; row += gridDim.x) {
+        if (tid == 0) carry = 0;
+        __syncthreads();
+        for (int64_t w0 = 0; w0 < nw; w0 += blockDim.x) {
+            const int64_t w = w0 + tid;
+            const int32_t c = w < nw ? __popc(bits[row * nw + w]) : 0;
+            int32_t incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) warp_tot[warp] = incl;
+            __syncthreads();
+            int32_t before = carry;
+            for (int i = 0; i < warp; ++i) before += warp_tot[i];
+            if (w < nw) wpre[row * nw + w] = before + incl - c;
+            __syncthreads();
+            if (tid == 0) {
+                int32_t t = 0;
+                for (int i = 0; i < nwarps; ++i) t += warp_tot[i];
+                carry += t;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) ncount[row] = carry;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void write_rec(int64_t e, int64_t o, const int32_t *eq, const uint64_t *emask,
+                                          const float *path, int h, int hp, const float *thr, const float *qn2,
+                                          const int64_t *qseq, TileRec *grec, int32_t *gq, float *gpath) {
+    const int32_t q = eq[e];
+    TileRec r;
+    r.q = q;
+    r.thr = thr[q];
+    r.qn2 = qn2 ? qn2[q] : 0.f;
+    r.qn = sqrtf(r.qn2) * (1.f + 1e-6f);
+    r.seq = qseq[q];
+    r.mask = emask[e];
+    grec[o] = r;
+    gq[o] = q;
+    for (int l = 0; l < hp; ++l) gpath[o * hp + l] = l < h ? path[e * h + l] : 0.f;
+}
+
+__global__ void k_node_scatter_bits(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
+                                    const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int hp,
+                                    int64_t E, const float *__restrict__ thr, const float *__restrict__ qn2,
+                                    const int64_t *__restrict__ qseq, const int64_t *__restrict__ noff,
+                                    const uint32_t *__restrict__ bits, const int32_t *__restrict__ wpre, int64_t nw,
+                                    TileRec *__restrict__ grec, int32_t *__restrict__ gq, float *__restrict__ gpath) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!emask[e]) continue;
+        const int32_t q = eq[e];
+        const int64_t wi = (int64_t)enode[e] * nw + (q >> 5);
+        const int64_t o = noff[enode[e]] + wpre[wi] + __popc(bits[wi] & ((1u << (q & 31)) - 1u));
+        write_rec(e, o, eq, emask, path, h, hp, thr, qn2, qseq, grec, gq, gpath);
+    }
+}
+
 // work items: one per 128-row block of every node that has entries
 // (also sums the (query, row) pairs the blocks hold into *pairs)
 __global__ void k_items_per_node(const int32_t *__restrict__ ncount, const int32_t *__restrict__ nsize, int64_t nn,
@@ -484,16 +564,32 @@ void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8
     check_launch("split queries");
 }
 
+bool regroup_uses_bits(const Tree &t, int64_t nq) {
+    const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
+    return nn * ((nq + 31) / 32) * 8 <= ((int64_t)1 << 30);
+}
+
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st, const int32_t *counts) {
     const int64_t E = tq.E;
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
-    DBuf<int32_t> own(counts ? 0 : nn, st), cursor(nn, st);
-    GTS_CUDA(cudaMemsetAsync(cursor.get(), 0, nn * 4, st));
-    if (!counts) {
-        GTS_CUDA(cudaMemsetAsync(own.get(), 0, nn * 4, st));
-        k_node_hist<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, own.get());
+    // the bitmap form when its two (node x query-word) arrays stay small
+    const int64_t nw = (tq.nq + 31) / 32;
+    const bool use_bits = regroup_uses_bits(t, tq.nq);
+    DBuf<uint32_t> bits(use_bits ? nn * nw : 0, st);
+    DBuf<int32_t> wpre(use_bits ? nn * nw : 0, st);
+    DBuf<int32_t> own((counts && !use_bits) ? 0 : nn, st), cursor(use_bits ? 0 : nn, st);
+    if (use_bits) {
+        GTS_CUDA(cudaMemsetAsync(bits.get(), 0, nn * nw * 4, st));
+        k_bits_set<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, E, nw, bits.get());
+        k_bits_rows<<<(unsigned)std::min<int64_t>(nn, 65535), 256, 0, st>>>(bits.get(), nn, nw, wpre.get(), own.get());
+    } else {
+        GTS_CUDA(cudaMemsetAsync(cursor.get(), 0, nn * 4, st));
+        if (!counts) {
+            GTS_CUDA(cudaMemsetAsync(own.get(), 0, nn * 4, st));
+            k_node_hist<<<nblk(E), 256, 0, st>>>(tq.enode, tq.emask, E, own.get());
+        }
     }
-    const int32_t *ncnt = counts ? counts : own.get();
+    const int32_t *ncnt = (counts && !use_bits) ? counts : own.get();
     DBuf<int64_t> c64(nn + 1, st), noff(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
     k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncnt, nn, c64.get());
     exscan(c64.get(), noff.get(), nn + 1, st);
@@ -505,8 +601,14 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     rg.grec.alloc(ne, st);
     rg.gq.alloc(ne, st);
     rg.gpath.alloc(ne * hp, st);
-    k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2, tq.qseq,
-                                            noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(), rg.gpath.get());
+    if (use_bits)
+        k_node_scatter_bits<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2,
+                                                     tq.qseq, noff.get(), bits.get(), wpre.get(), nw, rg.grec.get(),
+                                                     rg.gq.get(), rg.gpath.get());
+    else
+        k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2,
+                                                tq.qseq, noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(),
+                                                rg.gpath.get());
     const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
     DBuf<unsigned long long> pairs(1, st);
     GTS_CUDA(cudaMemsetAsync(pairs.get(), 0, 8, st));

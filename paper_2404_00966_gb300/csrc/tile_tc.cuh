@@ -74,6 +74,9 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
 // split a batch's queries into bf16 hi / lo rows [nq, dim_p] and squared norms
 void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
                       DBuf<float> &qn2, cudaStream_t st);
+// whether tc_regroup counts entries per node itself (a node x query bitmap),
+// so the caller need not
+bool regroup_uses_bits(const Tree &t, int64_t nq);
 // regroup the last-level entries by node into tiles; returns the tile count
 // counts: entries with a surviving leaf per last-level node, if already known
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st,

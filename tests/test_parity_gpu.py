@@ -238,6 +238,7 @@ def test_bf16_tiles_parity(gts, dim, dup):
     for k in (1, 10, 33):
         r = ix.knn(Q, k, precision="bf16")
         assert_same(r, oracle.knn_query("l2", X, Q, k), "l2", f"bf16 tiles knn k={k}")
+    assert ix.knn(Q, 500, precision="bf16").stats["dense_pairs"] > 0   # wide frontier: dense pivot matrices
     d = oracle.distances_to("l2", X[:500], Q[4])
     radii = np.linspace(0.0, 1.0, 300).astype(np.float32) * np.float32(np.median(d))
     assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l2", X, Q, radii), "l2", "bf16 tiles range")
@@ -271,6 +272,7 @@ def test_l1_tiles_concentrated_distances(gts):
     ix = gts.Index.build(X, "l1", fanout=20, root_pivot=0)
     for k in (1, 100):
         r = ix.knn(Q, k, precision="bf16")
+        assert r.stats["dense_pairs"] > 0           # the per-level dense pivot matrices ran
         assert_same(r, oracle.knn_query("l1", X, Q, k), "l1", f"concentrated knn k={k}")
     cal = oracle.knn_query("l1", X, Q[:10], 30)
     radii = np.full(260, np.float32(np.mean(cal[2][cal[0][1:] - 1])), np.float32)
