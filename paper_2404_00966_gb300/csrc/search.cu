@@ -619,30 +619,22 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
     }
 }
 
-// Last pivot level with the distances in a dense matrix: a warp per entry,
-// lane j tests child j's interval (Lemma 1 / 2; coalesced loads of the
-// node's children), the ballot is the leaf mask.
+// Last pivot level with the distances in a dense matrix: thread per entry,
+// the leaf mask from the node's children intervals (Lemma 1 / 2).
 __global__ void k_leaf_masks_dense(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                                    int64_t lvl_next, int64_t e0, int64_t e1, const float *__restrict__ dense,
                                    int64_t P, float *__restrict__ path, int l, const float *__restrict__ thr_q,
                                    uint64_t *__restrict__ mask_out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t q = eq[e], node = enode[e];
         const float dq = dense[(int64_t)q * P + node];
         const float thr = thr_q[q];
         const int64_t c0 = lvl_next + (int64_t)node * d.F;
         uint64_t m = 0;
-        for (int j0 = 0; j0 < d.F; j0 += 32) {
-            const int j = j0 + lane;
-            const bool keep = j < d.F && d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc);
-            m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
-        }
-        if (lane == 0) {
-            path[e * d.h + l] = dq;
-            mask_out[e - e0] = m;
-        }
+        for (int j = 0; j < d.F; ++j)
+            if (d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc)) m |= 1ull << j;
+        path[e * d.h + l] = dq;
+        mask_out[e - e0] = m;
     }
 }
 
@@ -1554,9 +1546,8 @@ struct Runner {
                                                    L.path.get(), l, thr.get(), mask.get(),               \
                                                    need_counts ? ncount.get() : nullptr, dm, nn)
         if (dm && !need_counts) {
-            k_leaf_masks_dense<<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), lvl_next, e0,
-                                                                                e1, dm, nn, L.path.get(), l, thr.get(),
-                                                                                mask.get());
+            k_leaf_masks_dense<<<cap(nblocks(E, kT)), kT, 0, st>>>(d, L.q.get(), L.node.get(), lvl_next, e0, e1, dm,
+                                                                    nn, L.path.get(), l, thr.get(), mask.get());
         } else if (d.metric == GTS_L2) {
             switch (nv) {
                 case 1: GTS_LL(true, 1); break;
@@ -1604,6 +1595,7 @@ struct Runner {
         tq.Qh = (const __nv_bfloat16 *)tcQh.get();
         tq.Ql = (const __nv_bfloat16 *)tcQl.get();
         tq.qn2 = tcqn2.get();
+        tc_bound_coeffs(ix->tree.tc.dim_p, tq.cE1, tq.cE2);
         tq.eq = L.q.get() + e0;
         tq.enode = L.node.get() + e0;
         tq.path = L.path.get() + e0 * h;

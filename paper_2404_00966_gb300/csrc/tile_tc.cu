@@ -111,7 +111,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 struct ChunkMeta {           // one buffer of per-query data of a chunk
     TileRec *rec;            // NQ records
     float *path;             // NQ x hp
-    float2 *ab;              // NQ (alpha_q, beta_q) of the squared-form bound test
 };
 
 // Stage chunk [start, start + cnt) of a block's queries with asynchronous
@@ -155,16 +154,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sB = sAl + panels * apanel;                    // 2 buffers x (hi, lo) x panels x kNQ x 128 B
     const int bbuf = 2 * panels * bpanel;                   // bytes of one (hi, lo) buffer
     uint8_t *mbase = sB + 2 * bbuf;
-    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + kNQ * 8;   // one metadata buffer
+    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4;   // one metadata buffer
     auto metab = [&](int b) {
         uint8_t *mp = mbase + b * mbytes;
         ChunkMeta m;
         m.rec = (TileRec *)mp;
         m.path = (float *)(mp + kNQ * sizeof(TileRec));
-        m.ab = (float2 *)(mp + kNQ * sizeof(TileRec) + kNQ * a.hp * 4);
         return m;
     };
-    uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
+    uint64_t *bars = (uint64_t *)(mbase + 3 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
     uint32_t *tslot = (uint32_t *)(bars + 3);
     int *sitem = (int *)(tslot + 1);
     int *sabort = sitem + 1;
@@ -231,86 +229,86 @@ __global__ void __launch_bounds__(kThreads, 1)
         // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
         const float gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
         const int nchunks = (total + kNQ - 1) / kNQ;
-        stage_chunk<NQ>(a, first, total < kNQ ? total : kNQ, metab(0), sB, sB + panels * bpanel, chunks16);
+        auto chunk_cnt = [&](int c) { return total - c * kNQ < kNQ ? total - c * kNQ : kNQ; };
+        // MMA of chunk c into accumulator c & 1: one thread, three products per
+        // k-step; the first chunk of a block waits for the block's TMA
+        auto issue = [&](int c) {
+            bool ok = true;
+            if (c == 0) {
+                ok = tc::mbar_wait(&bars[0], ptma);
+                if (!ok) {
+                    *sabort = 1;
+                    atomicExch(a.status, 1);
+                }
+            }
+            if (!ok) return;
+            tc::tc_fence_after();
+            const int b = c & 1;
+            const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
+            const uint32_t bh = tc::smem_u32(sB + b * bbuf), bl = bh + panels * bpanel;
+            const uint32_t dt = tmem + (uint32_t)(b * kNQ);
+            const int ksteps = a.dim_p / 16;
+            for (int s = 0; s < ksteps; ++s) {
+                const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
+                tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
+                tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
+                tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+            }
+            tc::mma_commit(&bars[1 + b]);
+        };
+        // Pipeline: query operands in two buffers, metadata in three; the MMA of
+        // chunk c + 1 runs while the epilogue of chunk c reads accumulator c & 1,
+        // and chunk c + 2 is staged into the operand buffer chunk c has freed.
+        stage_chunk<NQ>(a, first, chunk_cnt(0), metab(0), sB, sB + panels * bpanel, chunks16);
+        cp_async_wait_all();
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) issue(0);
+        ptma ^= 1u;
+        if (nchunks > 1)
+            stage_chunk<NQ>(a, first + kNQ, chunk_cnt(1), metab(1), sB + bbuf, sB + bbuf + panels * bpanel, chunks16);
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
-            const int cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
+            const int cnt = chunk_cnt(c);
+            // ---- issue the MMA of chunk c + 1 (accumulator b ^ 1 was read by the
+            // epilogue of chunk c - 1 before this barrier)
             cp_async_wait_all();
             tc::fence_proxy_async_smem();
+            tc::tc_fence_before();
             __syncthreads();
-            {   // per-query constants of the squared-form test (records have landed)
-                const ChunkMeta m = metab(b);
-                for (int j = tid; j < cnt; j += kThreads) {
-                    const TileRec &rc = m.rec[j];
-                    // keep iff d~^2 <= thr^2 + cE1 |q||x| + cE2 (|q| + |x|)^2, with
-                    // d~^2 = |q|^2 + |x|^2 - 2 q.x: alpha = (cE1 + 2 cE2) |q|,
-                    // beta = thr^2 + (cE2 - 1) |q|^2, all rounded up
-                    const float t = rc.thr * 1.0000039f;
-                    const float alpha = __fmul_ru(a.cE1 + 2.f * a.cE2, rc.qn) * 1.000001f;
-                    const float beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(a.cE2 - 1.f, rc.qn2)) +
-                                       4.f * 1.1920929e-7f * (t * t + rc.qn2);
-                    m.ab[j] = make_float2(alpha, beta);
-                }
-            }
-            __syncthreads();
-            // ---- MMA of chunk c into accumulator b: one thread, three products per k-step
-            if (tid == 0) {
-                bool ok = true;
-                if (c == 0) {
-                    ok = tc::mbar_wait(&bars[0], ptma);
-                    if (!ok) {
-                        *sabort = 1;
-                        atomicExch(a.status, 1);
-                    }
-                }
-                if (ok) {
-                    tc::tc_fence_after();
-                    const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-                    const uint32_t bh = tc::smem_u32(sB + b * bbuf), bl = bh + panels * bpanel;
-                    const uint32_t dt = tmem + (uint32_t)(b * kNQ);
-                    const int ksteps = a.dim_p / 16;
-                    for (int s = 0; s < ksteps; ++s) {
-                        const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
-                        tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
-                        tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
-                        tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
-                    }
-                    tc::mma_commit(&bars[1 + b]);
-                }
-            }
-            if (c == 0) ptma ^= 1u;
-            // ---- stage chunk c + 1 into the other buffers while the MMA runs
-            if (c + 1 < nchunks) {
-                const int cn = total - (c + 1) * kNQ < kNQ ? total - (c + 1) * kNQ : kNQ;
-                stage_chunk<NQ>(a, first + (c + 1) * kNQ, cn, metab(b ^ 1), sB + (b ^ 1) * bbuf,
-                            sB + (b ^ 1) * bbuf + panels * bpanel, chunks16);
-            }
-            // ---- epilogue of chunk c
             if (*sabort) break;
+            if (c + 1 < nchunks && tid == 0) issue(c + 1);
+            // ---- epilogue of chunk c
             if (!tc::mbar_wait(&bars[1 + b], pmma[b])) {
                 *sabort = 1;
                 atomicExch(a.status, 2);
             }
             pmma[b] ^= 1u;
+            // operand buffer b and metadata buffer (c + 2) % 3 are free
+            if (c + 2 < nchunks)
+                stage_chunk<NQ>(a, first + (c + 2) * kNQ, chunk_cnt(c + 2), metab((c + 2) % 3), sB + b * bbuf,
+                                sB + b * bbuf + panels * bpanel, chunks16);
             tc::tc_fence_after();
             const int cc = cgrp * 32;
-            if (cc < cnt) {
-                const ChunkMeta m = metab(b);
+            // columns (queries) of this warp with a surviving leaf among the
+            // warp's 32 rows: lane i tests column cc + i
+            const ChunkMeta m = metab(c % 3);
+            const unsigned live =
+                cc < cnt ? __ballot_sync(0xffffffffu, cc + lane < cnt && (m.rec[cc + lane].mask & wmask) != 0) : 0u;
+            if (live) {   // warp-uniform
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kNQ + cc), v);
                 tc::tmem_ld_wait();
                 uint32_t passbits = 0;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
+                    if (!((live >> i) & 1u)) continue;   // warp-uniform
                     const int j = cc + i;
-                    if (j >= cnt) break;
                     const uint64_t mk = m.rec[j].mask;
-                    if ((mk & wmask) == 0) continue;   // warp-uniform
                     if (!(mk & rowbit)) continue;
                     // d~^2 <= thr^2 + E  <=>  -2 q.x <= beta_q + alpha_q |x| + gamma_x
-                    const float2 ab = m.ab[j];
-                    if (-2.f * __uint_as_float(v[i]) > fmaf(ab.x, xn, ab.y + gx)) continue;
                     const TileRec &rc = m.rec[j];
+                    if (-2.f * __uint_as_float(v[i]) > fmaf(rc.alpha, xn, rc.beta + gx)) continue;
                     if (rdel <= rc.seq) continue;
                     bool ok = true;
                     for (int l = 0; l < a.h && ok; ++l) {
@@ -374,10 +372,21 @@ __global__ void k_node_hist(const int32_t *__restrict__ enode, const uint64_t *_
 // scatter each entry's record (query, threshold, norms, sequence number,
 // leaf mask) and path distances to its node's slot, so a tile reads its
 // queries' data contiguously
+// the per-query constants of the squared-form bound test, all rounded up:
+// keep iff d~^2 <= thr^2 + cE1 |q||x| + cE2 (|q| + |x|)^2 with
+// d~^2 = |q|^2 + |x|^2 - 2 q.x, i.e. -2 q.x <= beta + alpha |x| + gamma_x,
+// alpha = (cE1 + 2 cE2) |q|, beta = thr^2 + (cE2 - 1) |q|^2
+__device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, float cE2, float &alpha, float &beta) {
+    const float qn = sqrtf(qn2) * (1.f + 1e-6f);
+    const float t = thr * 1.0000039f;
+    alpha = __fmul_ru(cE1 + 2.f * cE2, qn) * 1.000001f;
+    beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(cE2 - 1.f, qn2)) + 4.f * 1.1920929e-7f * (t * t + qn2);
+}
+
 __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                                const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int hp,
-                               int64_t E, const float *__restrict__ thr, const float *__restrict__ qn2,
-                               const int64_t *__restrict__ qseq, const int64_t *__restrict__ noff,
+                               int64_t E, const float *__restrict__ thr, const float *__restrict__ qn2, float cE1,
+                               float cE2, const int64_t *__restrict__ qseq, const int64_t *__restrict__ noff,
                                int32_t *__restrict__ cursor, TileRec *__restrict__ grec, int32_t *__restrict__ gq,
                                float *__restrict__ gpath) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
@@ -389,8 +398,7 @@ __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__
         TileRec r;
         r.q = q;
         r.thr = thr[q];
-        r.qn2 = qn2 ? qn2[q] : 0.f;
-        r.qn = sqrtf(r.qn2) * (1.f + 1e-6f);
+        bound_consts(r.thr, qn2 ? qn2[q] : 0.f, cE1, cE2, r.alpha, r.beta);
         r.seq = qseq[q];
         r.mask = m;
         grec[o] = r;
@@ -450,13 +458,13 @@ __global__ void k_bits_rows(const uint32_t *__restrict__ bits, int64_t nn, int64
 
 __device__ __forceinline__ void write_rec(int64_t e, int64_t o, const int32_t *eq, const uint64_t *emask,
                                           const float *path, int h, int hp, const float *thr, const float *qn2,
-                                          const int64_t *qseq, TileRec *grec, int32_t *gq, float *gpath) {
+                                          float cE1, float cE2, const int64_t *qseq, TileRec *grec, int32_t *gq,
+                                          float *gpath) {
     const int32_t q = eq[e];
     TileRec r;
     r.q = q;
     r.thr = thr[q];
-    r.qn2 = qn2 ? qn2[q] : 0.f;
-    r.qn = sqrtf(r.qn2) * (1.f + 1e-6f);
+    bound_consts(r.thr, qn2 ? qn2[q] : 0.f, cE1, cE2, r.alpha, r.beta);
     r.seq = qseq[q];
     r.mask = emask[e];
     grec[o] = r;
@@ -467,15 +475,15 @@ __device__ __forceinline__ void write_rec(int64_t e, int64_t o, const int32_t *e
 __global__ void k_node_scatter_bits(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
                                     const uint64_t *__restrict__ emask, const float *__restrict__ path, int h, int hp,
                                     int64_t E, const float *__restrict__ thr, const float *__restrict__ qn2,
-                                    const int64_t *__restrict__ qseq, const int64_t *__restrict__ noff,
-                                    const uint32_t *__restrict__ bits, const int32_t *__restrict__ wpre, int64_t nw,
+                                    float cE1, float cE2, const int64_t *__restrict__ qseq,
+                                    const int64_t *__restrict__ noff, const uint32_t *__restrict__ bits, const int32_t *__restrict__ wpre, int64_t nw,
                                     TileRec *__restrict__ grec, int32_t *__restrict__ gq, float *__restrict__ gpath) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         if (!emask[e]) continue;
         const int32_t q = eq[e];
         const int64_t wi = (int64_t)enode[e] * nw + (q >> 5);
         const int64_t o = noff[enode[e]] + wpre[wi] + __popc(bits[wi] & ((1u << (q & 31)) - 1u));
-        write_rec(e, o, eq, emask, path, h, hp, thr, qn2, qseq, grec, gq, gpath);
+        write_rec(e, o, eq, emask, path, h, hp, thr, qn2, cE1, cE2, qseq, grec, gq, gpath);
     }
 }
 
@@ -529,12 +537,21 @@ size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
-    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + (size_t)kNQ * 8);
+    b += 3 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4);
     b += 3 * 8 + 4 + 4 + 4 + 16;
     return b;
 }
 
 }  // namespace
+
+void tc_bound_coeffs(int dim_p, float &cE1, float &cE2) {
+    // |d~^2 - d^2| <= cE1 |q||x| + cE2 (|q| + |x|)^2 (see the file comment)
+    const double u23 = 1.0 / 8388608.0;
+    const double kterms = 3.0 * dim_p + 2.0;
+    const double gam = kterms * u23 / (1.0 - kterms * u23);
+    cE1 = (float)(2.02 * (3.01 / 65536.0 + gam) * 1.01);
+    cE2 = (float)(1.0 / 2097152.0);
+}
 
 bool tc_supported(const Tree &t) { return t.metric == GTS_L2 && t.dim > 0 && t.dim <= 256 && t.n > 0; }
 
@@ -603,11 +620,11 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     rg.gpath.alloc(ne * hp, st);
     if (use_bits)
         k_node_scatter_bits<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2,
-                                                     tq.qseq, noff.get(), bits.get(), wpre.get(), nw, rg.grec.get(),
+                                                     tq.cE1, tq.cE2, tq.qseq, noff.get(), bits.get(), wpre.get(), nw, rg.grec.get(),
                                                      rg.gq.get(), rg.gpath.get());
     else
         k_node_scatter<<<nblk(E), 256, 0, st>>>(tq.eq, tq.enode, tq.emask, tq.path, t.h, hp, E, tq.thr, tq.qn2,
-                                                tq.qseq, noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(),
+                                                tq.cE1, tq.cE2, tq.qseq, noff.get(), cursor.get(), rg.grec.get(), rg.gq.get(),
                                                 rg.gpath.get());
     const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
     DBuf<unsigned long long> pairs(1, st);
@@ -658,12 +675,8 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     DBuf<int> counter(1, st), status(1, st);
     DBuf<unsigned long long> count(1, st);
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
-    // |d~^2 - d^2| <= cE1 |q||x| + cE2 (|q| + |x|)^2 (see the file comment)
-    const double u23 = 1.0 / 8388608.0;
-    const double kterms = 3.0 * c.dim_p + 2.0;
-    const double gam = kterms * u23 / (1.0 - kterms * u23);
-    const float cE1 = (float)(2.02 * (3.01 / 65536.0 + gam) * 1.01);
-    const float cE2 = (float)(1.0 / 2097152.0);
+    float cE1 = 0.f, cE2 = 0.f;
+    tc_bound_coeffs(c.dim_p, cE1, cE2);
     for (int attempt = 0; attempt < 2; ++attempt) {
         out_q.alloc(cap, st);
         out_row.alloc(cap, st);

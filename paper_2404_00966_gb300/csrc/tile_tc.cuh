@@ -14,7 +14,7 @@ namespace gts {
 struct __align__(16) TileRec {
     int32_t q;
     float thr;       // radius or tau_q
-    float qn2, qn;   // |q|^2 and |q| (rounded up)
+    float alpha, beta;   // tensor-core bound test: keep iff -2 q.x <= beta + alpha |x| + gamma_x
     int64_t seq;     // the query's sequence number
     uint64_t mask;   // surviving leaves of the node
 };
@@ -48,6 +48,7 @@ struct TcQuery {
     int64_t nq = 0;
     const __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;   // split bf16 queries [nq, dim_p]
     const float *qn2 = nullptr;                          // |q|^2 (null: not needed, records get 0)
+    float cE1 = 0.f, cE2 = 0.f;                          // bf16 error-bound coefficients (tc_bound_coeffs)
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;
@@ -70,6 +71,8 @@ struct TcRegroup {
 };
 
 bool tc_supported(const Tree &t);
+// |d~^2 - d^2| <= cE1 |q||x| + cE2 (|q| + |x|)^2 for the split-bf16 products over dim_p columns
+void tc_bound_coeffs(int dim_p, float &cE1, float &cE2);
 void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
 // split a batch's queries into bf16 hi / lo rows [nq, dim_p] and squared norms
 void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
