@@ -48,6 +48,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// plain arrive (release): orders this thread's earlier shared-memory writes
+// before the phase completes
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// barrier among `count` threads (a multiple of 32) of the CTA, id 1 .. 15
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // ---------------------------------------------------------------- proxies / fences
 
 // make generic-proxy shared-memory writes visible to the async proxy (tensor cores, TMA)

@@ -1,10 +1,12 @@
 // L2 verification on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
 //
 // After the descent, the surviving (query, last-level node) entries are
-// regrouped by node.  A persistent, work-stealing kernel takes one 128-row
-// block of one node at a time (the A operand, loaded once by TMA and kept in
-// shared memory) and runs it against the node's queries in chunks of kNQ (the
-// B operand):
+// regrouped by node.  A persistent, work-stealing, warp-specialised kernel
+// takes one 128-row block of one node at a time (the A operand, loaded once by
+// TMA and kept in shared memory) and runs it against the node's queries in
+// chunks of kNQ (the B operand); producer warps stage the chunks, one thread
+// issues the MMAs and epilogue warps test the results, handing chunks on
+// through mbarriers:
 //   * rows and queries are stored once as split bf16 pairs x = x_hi + x_lo
 //     (x_hi = bf16(x), x_lo = bf16(x - x_hi)); a chunk's query pairs are
 //     copied into shared memory in the 128-byte swizzled layout;
@@ -43,7 +45,6 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node block
-constexpr int kThreads = 512;  // 16 warps: 4 TMEM lane quadrants x 4 groups of 32 columns
 // MMA N (queries per chunk) is a template parameter NQ: 128 up to 128
 // columns, 64 up to 192, 32 up to 256, so that the node block (A, hi and lo)
 // and two chunk buffers (B, hi and lo) fit in shared memory.  TMEM holds two
@@ -105,43 +106,60 @@ __global__ void k_split_rows(const float *__restrict__ X, int dim, int dim_p, in
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-struct ChunkMeta {           // one buffer of per-query data of a chunk
-    TileRec *rec;            // NQ records
-    float *path;             // NQ x hp
+// The per-chunk data the producer hands to the MMA thread and the epilogue.
+struct ChunkDesc {
+    int32_t stop;       // 1: no more work
+    int32_t new_item;   // first chunk of a node block (the block's A operand is loading)
+    int32_t first;      // first record of the chunk
+    int32_t cnt;        // queries in the chunk
+    int32_t pos, size;  // the node's rows [pos, pos + size)
+    int32_t rb;         // first row of the block within the node
+    int32_t pad_;
 };
 
+// Roles: warps 0-15 epilogue (TMEM lane quadrant w % 4, 32 query columns
+// each), warps 16-19 producers, warp 20 (lane 0) the MMA issuer.
+constexpr int kEpiWarps = 16;
+constexpr int kProducers = 128;
+constexpr int kProdWarp0 = kEpiWarps;
+constexpr int kMmaWarp = kEpiWarps + kProducers / 32;
+constexpr int kThreadsWS = (kMmaWarp + 1) * 32;
+
 // Stage chunk [start, start + cnt) of a block's queries with asynchronous
-// copies only: the records and path distances (contiguous, node-major), and
-// the split bf16 query rows into the 128-byte swizzled layout (each thread
-// first reads the query ids of the rows it copies).
+// copies by the producer threads: the records and path distances (contiguous,
+// node-major), and the split bf16 query rows into the 128-byte swizzled
+// layout (each thread first reads the query ids of the rows it copies).
 template <int NQ>
-__device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, ChunkMeta m, uint8_t *sBh,
-                                            uint8_t *sBl, int chunks16) {
-    const int tid = threadIdx.x;
+__device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, TileRec *mrec, float *mpath,
+                                            uint8_t *sBh, uint8_t *sBl, int chunks16, int ptid) {
     const uint8_t *rsrc = reinterpret_cast<const uint8_t *>(a.grec + start);
-    for (int t = tid; t < cnt * 2; t += kThreads) cp_async16(reinterpret_cast<uint8_t *>(m.rec) + t * 16, rsrc + t * 16);
+    for (int t = ptid; t < cnt * 2; t += kProducers) cp_async16(reinterpret_cast<uint8_t *>(mrec) + t * 16, rsrc + t * 16);
     const uint8_t *psrc = reinterpret_cast<const uint8_t *>(a.gpath + (int64_t)start * a.hp);
     const int pch = cnt * a.hp / 4;
-    for (int t = tid; t < pch; t += kThreads) cp_async16(reinterpret_cast<uint8_t *>(m.path) + t * 16, psrc + t * 16);
+    for (int t = ptid; t < pch; t += kProducers) cp_async16(reinterpret_cast<uint8_t *>(mpath) + t * 16, psrc + t * 16);
     const int per_q = 2 * chunks16;                  // 16-byte copies per query (hi and lo)
-    const int tpq = kThreads / NQ;                   // threads per query
-    for (int j = tid / tpq; j < cnt; j += kThreads / tpq) {
-        const int32_t q = a.gq[start + j];
-        for (int c = tid % tpq; c < per_q; c += tpq) {
+    constexpr int tpq = kProducers / NQ;             // threads per query
+    for (int j = ptid / tpq; j < cnt; j += kProducers / tpq) {
+        const int32_t q = a.gq[start + j];           // one id load, then independent copies
+        const __nv_bfloat16 *srch = a.Qh + (int64_t)q * a.dim_p, *srcl = a.Ql + (int64_t)q * a.dim_p;
+        for (int c = ptid % tpq; c < per_q; c += tpq) {
             const int comp = c / chunks16, k16 = c - comp * chunks16;
-            const __nv_bfloat16 *src = (comp ? a.Ql : a.Qh) + (int64_t)q * a.dim_p + k16 * 8;
             uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (NQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
-            cp_async16(dst, src);
+            cp_async16(dst, (comp ? srcl : srch) + k16 * 8);
         }
     }
-    cp_async_commit();
 }
 
+// Warp-specialised persistent kernel: the producer warps stage chunk g into
+// slot g % 2 once the epilogue has released the chunk g - 2 held there; one
+// thread issues the MMAs of chunk g into accumulator g % 2 when its operands
+// have landed; the epilogue warps test chunk g when its MMAs are done and
+// release the slot.  mbarriers carry every hand-off (parity (g / 2) & 1 for
+// the g-th use of a slot), so no block-wide barrier runs per chunk.
 template <int NQ>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsWS, 1)
     k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l, TileArgs a) {
     constexpr int kNQ = NQ;
     constexpr int kTmemCols = 2 * NQ;
@@ -151,169 +169,233 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int apanel = kRows * 128, bpanel = kNQ * 128;
     uint8_t *sAh = smem;                                    // panels x 128 rows x 128 B
     uint8_t *sAl = sAh + panels * apanel;
-    uint8_t *sB = sAl + panels * apanel;                    // 2 buffers x (hi, lo) x panels x kNQ x 128 B
-    const int bbuf = 2 * panels * bpanel;                   // bytes of one (hi, lo) buffer
+    uint8_t *sB = sAl + panels * apanel;                    // 2 slots x (hi, lo) x panels x kNQ x 128 B
+    const int bbuf = 2 * panels * bpanel;                   // bytes of one slot
     uint8_t *mbase = sB + 2 * bbuf;
-    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4;   // one metadata buffer
-    auto metab = [&](int b) {
-        uint8_t *mp = mbase + b * mbytes;
-        ChunkMeta m;
-        m.rec = (TileRec *)mp;
-        m.path = (float *)(mp + kNQ * sizeof(TileRec));
-        return m;
+    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + (int)sizeof(ChunkDesc);
+    auto mrec = [&](int sl) { return (TileRec *)(mbase + sl * mbytes); };
+    auto mpath = [&](int sl) { return (float *)(mbase + sl * mbytes + kNQ * sizeof(TileRec)); };
+    auto mdesc = [&](int sl) {
+        return (ChunkDesc *)(mbase + sl * mbytes + kNQ * sizeof(TileRec) + kNQ * a.hp * 4);
     };
-    uint64_t *bars = (uint64_t *)(mbase + 3 * mbytes);     // [0] TMA, [1] [2] MMA per accumulator
-    uint32_t *tslot = (uint32_t *)(bars + 3);
+    uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // full[2], mma_done[2], epi_done[2], a_full
+    uint64_t *full = bars, *mma_done = bars + 2, *epi_done = bars + 4, *a_full = bars + 6;
+    uint32_t *tslot = (uint32_t *)(bars + 7);
     int *sitem = (int *)(tslot + 1);
-    int *sabort = sitem + 1;
+    volatile int *sabort = sitem + 1;
+    int *a_issued = sitem + 2;     // A loads issued / consumed (for the abort path)
+    int *a_used = sitem + 3;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) tc::mbar_init(&bars[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], kProducers);
+            tc::mbar_init(&mma_done[i], 1);
+            tc::mbar_init(&epi_done[i], kEpiWarps);
+        }
+        tc::mbar_init(a_full, 1);
         tc::mbar_fence_init();
         *sabort = 0;
+        *a_issued = 0;
+        *a_used = 0;
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
     const int chunks16 = a.dim_p / 8;                       // 16-byte chunks per bf16 row
-    uint32_t ptma = 0, pmma[2] = {0, 0};                     // barrier phases
-    const int quad = warp & 3, cgrp = warp >> 2;             // TMEM lane quadrant, 32-column group
-    for (;;) {
-        if (tid == 0) *sitem = atomicAdd(a.work_counter, 1);
-        __syncthreads();
-        const int item = *sitem;
-        if (item >= a.n_items || *sabort) break;
-        const int4 it = a.items[item];
-        const int64_t node = it.x;
-        const int first = it.y, total = it.z;
-        const int rb = it.w * kRows;   // first row of this 128-row block within the node
-        const int64_t g = a.lvl_last + node;
-        const int32_t pos = a.npos[g], size = a.nsize[g];
-        if (tid == 0) {
-            tc::mbar_expect_tx(&bars[0], (uint32_t)(2 * panels * apanel));
-            for (int p = 0; p < panels; ++p) {
-                tc::tma_load_2d(sAh + p * apanel, &map_h, p * 64, pos + rb, &bars[0]);
-                tc::tma_load_2d(sAl + p * apanel, &map_l, p * 64, pos + rb, &bars[0]);
-            }
-        }
-        // ---- per-row constants of this block (thread = TMEM lane of its warp quadrant)
-        const int r = quad * 32 + lane;
-        const int nrow = size - rb;
-        const bool valid = r < nrow;
-        const int64_t row = (int64_t)pos + rb + r;
-        const int32_t avg = size / a.F;
-        int32_t jl = avg > 0 ? (rb + r) / avg : a.F - 1;
-        if (jl > a.F - 1) jl = a.F - 1;
-        const int rlast = min(quad * 32 + 31, min(nrow, kRows) - 1);
-        uint64_t wmask = 0;
-        if (rlast >= quad * 32) {
-            int32_t j0 = avg > 0 ? (rb + quad * 32) / avg : a.F - 1;
-            int32_t j1 = avg > 0 ? (rb + rlast) / avg : a.F - 1;
-            j0 = min(j0, a.F - 1);
-            j1 = min(j1, a.F - 1);
-            wmask = ((j1 >= 63) ? ~0ull : ((1ull << (j1 + 1)) - 1ull)) & ~((1ull << j0) - 1ull);
-        }
-        float xn2 = 0.f, xn = 0.f;
-        int64_t rdel = kNever;
-        if (valid) {
-            xn2 = a.xn2[row];
-            xn = sqrtf(xn2) * (1.f + 1e-6f);
-            if (a.any_deleted) rdel = a.row_del[row];
-        }
-        // rows outside the node block match no leaf bit
-        const uint64_t rowbit = valid ? (1ull << jl) : 0ull;
-        // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
-        const float gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
-        const int nchunks = (total + kNQ - 1) / kNQ;
-        auto chunk_cnt = [&](int c) { return total - c * kNQ < kNQ ? total - c * kNQ : kNQ; };
-        // MMA of chunk c into accumulator c & 1: one thread, three products per
-        // k-step; the first chunk of a block waits for the block's TMA
-        auto issue = [&](int c) {
-            bool ok = true;
-            if (c == 0) {
-                ok = tc::mbar_wait(&bars[0], ptma);
-                if (!ok) {
-                    *sabort = 1;
-                    atomicExch(a.status, 1);
+    auto fail = [&](int code) {
+        *sabort = 1;
+        atomicExch(a.status, code);
+    };
+
+    if (warp >= kProdWarp0 && warp < kMmaWarp) {
+        // ================================================= producer warps
+        const int ptid = tid - kProdWarp0 * 32;
+        uint32_t g = 0;
+        int64_t last_g = -1;   // last chunk of the previous block
+        for (;;) {
+            if (ptid == 0) *sitem = atomicAdd(a.work_counter, 1);
+            tc::named_sync(1, kProducers);
+            const int item = *sitem;
+            tc::named_sync(1, kProducers);
+            const bool stop = item >= a.n_items || *sabort;
+            int4 it = make_int4(0, 0, 0, 0);
+            int32_t pos = 0, size = 0;
+            if (!stop) {
+                it = a.items[item];
+                const int64_t gnode = a.lvl_last + it.x;
+                pos = a.npos[gnode];
+                size = a.nsize[gnode];
+                if (ptid == 0) {
+                    // the previous block's MMAs are done once its last epilogue is
+                    if (last_g >= 0 && !tc::mbar_wait(&epi_done[last_g & 1], (uint32_t)((last_g >> 1) & 1))) fail(3);
+                    tc::mbar_expect_tx(a_full, (uint32_t)(2 * panels * apanel));
+                    for (int pnl = 0; pnl < panels; ++pnl) {
+                        tc::tma_load_2d(sAh + pnl * apanel, &map_h, pnl * 64, pos + it.w * kRows, a_full);
+                        tc::tma_load_2d(sAl + pnl * apanel, &map_l, pnl * 64, pos + it.w * kRows, a_full);
+                    }
+                    ++*a_issued;
                 }
             }
-            if (!ok) return;
-            tc::tc_fence_after();
-            const int b = c & 1;
-            const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-            const uint32_t bh = tc::smem_u32(sB + b * bbuf), bl = bh + panels * bpanel;
-            const uint32_t dt = tmem + (uint32_t)(b * kNQ);
-            const int ksteps = a.dim_p / 16;
-            for (int s = 0; s < ksteps; ++s) {
-                const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
-                tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
-                tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
-                tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+            const int total = it.z;
+            const int nchunks = stop ? 1 : (total + kNQ - 1) / kNQ;
+            for (int c = 0; c < nchunks; ++c, ++g) {
+                const int sl = g & 1;
+                if (g >= 2 && !tc::mbar_wait(&epi_done[sl], ((g - 2) >> 1) & 1)) fail(4);
+                const int cnt = stop ? 0 : (total - c * kNQ < kNQ ? total - c * kNQ : kNQ);
+                if (!stop)
+                    stage_chunk<NQ>(a, it.y + c * kNQ, cnt, mrec(sl), mpath(sl), sB + sl * bbuf,
+                                    sB + sl * bbuf + panels * bpanel, chunks16, ptid);
+                if (ptid == 0) {
+                    ChunkDesc dsc;
+                    dsc.stop = stop ? 1 : 0;
+                    dsc.new_item = c == 0 ? 1 : 0;
+                    dsc.first = it.y + c * kNQ;
+                    dsc.cnt = cnt;
+                    dsc.pos = pos;
+                    dsc.size = size;
+                    dsc.rb = it.w * kRows;
+                    dsc.pad_ = 0;
+                    *mdesc(sl) = dsc;
+                }
+                // the copies have landed and are visible to the tensor cores
+                // (async proxy) before this thread arrives
+                cp_async_wait_all();
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(&full[sl]);
             }
-            tc::mma_commit(&bars[1 + b]);
-        };
-        // Pipeline: query operands in two buffers, metadata in three; the MMA of
-        // chunk c + 1 runs while the epilogue of chunk c reads accumulator c & 1,
-        // and chunk c + 2 is staged into the operand buffer chunk c has freed.
-        stage_chunk<NQ>(a, first, chunk_cnt(0), metab(0), sB, sB + panels * bpanel, chunks16);
+            if (stop) break;
+            last_g = (int64_t)g - 1;
+        }
         cp_async_wait_all();
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) issue(0);
-        ptma ^= 1u;
-        if (nchunks > 1)
-            stage_chunk<NQ>(a, first + kNQ, chunk_cnt(1), metab(1), sB + bbuf, sB + bbuf + panels * bpanel, chunks16);
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            const int cnt = chunk_cnt(c);
-            // ---- issue the MMA of chunk c + 1 (accumulator b ^ 1 was read by the
-            // epilogue of chunk c - 1 before this barrier)
-            cp_async_wait_all();
-            tc::fence_proxy_async_smem();
-            tc::tc_fence_before();
-            __syncthreads();
-            if (*sabort) break;
-            if (c + 1 < nchunks && tid == 0) issue(c + 1);
-            // ---- epilogue of chunk c
-            if (!tc::mbar_wait(&bars[1 + b], pmma[b])) {
-                *sabort = 1;
-                atomicExch(a.status, 2);
+    } else if (warp == kMmaWarp) {
+        // ================================================= MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+            uint32_t a_par = 0;
+            int64_t last_issued = -1;
+            for (uint32_t g = 0;; ++g) {
+                const int sl = g & 1;
+                if (!tc::mbar_wait(&full[sl], (g >> 1) & 1)) {
+                    fail(5);
+                    break;
+                }
+                const ChunkDesc dsc = *mdesc(sl);
+                if (dsc.stop || *sabort) break;
+                tc::fence_proxy_async_smem();
+                if (dsc.new_item) {
+                    if (!tc::mbar_wait(a_full, a_par)) {
+                        fail(1);
+                        break;
+                    }
+                    a_par ^= 1u;
+                    ++*a_used;
+                }
+                tc::tc_fence_after();
+                const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
+                const uint32_t bh = tc::smem_u32(sB + sl * bbuf), bl = bh + panels * bpanel;
+                const uint32_t dt = tmem + (uint32_t)(sl * kNQ);
+                const int ksteps = a.dim_p / 16;
+                for (int s = 0; s < ksteps; ++s) {
+                    const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
+                    tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
+                    tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
+                    tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+                }
+                tc::mma_commit(&mma_done[sl]);
+                last_issued = g;
             }
-            pmma[b] ^= 1u;
-            // operand buffer b and metadata buffer (c + 2) % 3 are free
-            if (c + 2 < nchunks)
-                stage_chunk<NQ>(a, first + (c + 2) * kNQ, chunk_cnt(c + 2), metab((c + 2) % 3), sB + b * bbuf,
-                                sB + b * bbuf + panels * bpanel, chunks16);
+            // on an early exit, let issued MMAs finish before TMEM is released
+            if (last_issued >= 0 && *sabort)
+                tc::mbar_wait(&mma_done[last_issued & 1], (uint32_t)((last_issued >> 1) & 1));
+        }
+    } else if (warp < kEpiWarps) {
+        // ================================================= epilogue warps
+        const int quad = warp & 3;                 // TMEM lane quadrant of this warp
+        const int cc = (warp >> 2) * 32;           // its query columns [cc, cc + 32)
+        const int r = quad * 32 + lane;            // row of the block
+        bool valid = false;
+        int64_t row = 0, rdel = kNever;
+        uint64_t rowbit = 0, wmask = 0;
+        float xn = 0.f, gx = 0.f;
+        for (uint32_t g = 0;; ++g) {
+            const int sl = g & 1;
+            if (!tc::mbar_wait(&full[sl], (g >> 1) & 1)) {
+                fail(6);
+                break;
+            }
+            const ChunkDesc dsc = *mdesc(sl);
+            if (dsc.stop || *sabort) break;
+            if (dsc.new_item) {
+                // per-row constants of this block (thread = TMEM lane of its quadrant)
+                const int nrow = dsc.size - dsc.rb;
+                valid = r < nrow;
+                row = (int64_t)dsc.pos + dsc.rb + r;
+                const int32_t avg = dsc.size / a.F;
+                int32_t jl = avg > 0 ? (dsc.rb + r) / avg : a.F - 1;
+                if (jl > a.F - 1) jl = a.F - 1;
+                const int rlast = min(quad * 32 + 31, min(nrow, kRows) - 1);
+                wmask = 0;
+                if (rlast >= quad * 32) {
+                    int32_t j0 = avg > 0 ? (dsc.rb + quad * 32) / avg : a.F - 1;
+                    int32_t j1 = avg > 0 ? (dsc.rb + rlast) / avg : a.F - 1;
+                    j0 = min(j0, a.F - 1);
+                    j1 = min(j1, a.F - 1);
+                    wmask = ((j1 >= 63) ? ~0ull : ((1ull << (j1 + 1)) - 1ull)) & ~((1ull << j0) - 1ull);
+                }
+                float xn2 = 0.f;
+                xn = 0.f;
+                rdel = kNever;
+                if (valid) {
+                    xn2 = a.xn2[row];
+                    xn = sqrtf(xn2) * (1.f + 1e-6f);
+                    if (a.any_deleted) rdel = a.row_del[row];
+                }
+                // rows outside the node block match no leaf bit
+                rowbit = valid ? (1ull << jl) : 0ull;
+                // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
+                gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
+            }
+            if (!tc::mbar_wait(&mma_done[sl], (g >> 1) & 1)) {
+                fail(2);
+                break;
+            }
             tc::tc_fence_after();
-            const int cc = cgrp * 32;
-            // columns (queries) of this warp with a surviving leaf among the
-            // warp's 32 rows: lane i tests column cc + i
-            const ChunkMeta m = metab(c % 3);
-            const unsigned live =
-                cc < cnt ? __ballot_sync(0xffffffffu, cc + lane < cnt && (m.rec[cc + lane].mask & wmask) != 0) : 0u;
+            const int cnt = dsc.cnt;
+            const TileRec *rec = mrec(sl);
+            const float *pth = mpath(sl);
+            // columns (queries) with a surviving leaf among the warp's 32 rows
+            const unsigned live = (cc < kNQ && cc < cnt)
+                                      ? __ballot_sync(0xffffffffu, cc + lane < cnt && (rec[cc + lane].mask & wmask) != 0)
+                                      : 0u;
             if (live) {   // warp-uniform
                 uint32_t v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kNQ + cc), v);
+                tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * kNQ + cc), v);
                 tc::tmem_ld_wait();
-                uint32_t passbits = 0;
+                // leaf and bound tests of all 32 columns without branches:
+                // d~^2 <= thr^2 + E  <=>  -2 q.x <= beta_q + alpha_q |x| + gamma_x
+                uint32_t cand = 0;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    if (!((live >> i) & 1u)) continue;   // warp-uniform
-                    const int j = cc + i;
-                    const uint64_t mk = m.rec[j].mask;
-                    if (!(mk & rowbit)) continue;
-                    // d~^2 <= thr^2 + E  <=>  -2 q.x <= beta_q + alpha_q |x| + gamma_x
-                    const TileRec &rc = m.rec[j];
-                    if (-2.f * __uint_as_float(v[i]) > fmaf(rc.alpha, xn, rc.beta + gx)) continue;
+                    const TileRec &rc = rec[cc + i];
+                    const bool p = (rc.mask & rowbit) != 0 &&
+                                   -2.f * __uint_as_float(v[i]) <= fmaf(rc.alpha, xn, rc.beta + gx);
+                    cand |= (p ? 1u : 0u) << i;
+                }
+                cand &= live;
+                // the few survivors: visibility and the table lower bound
+                uint32_t passbits = 0;
+                while (cand) {
+                    const int i = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    const TileRec &rc = rec[cc + i];
                     if (rdel <= rc.seq) continue;
                     bool ok = true;
                     for (int l = 0; l < a.h && ok; ++l) {
                         const float T = a.table[(int64_t)l * a.n + row];
-                        const float pl = m.path[j * a.hp + l];
+                        const float pl = pth[(cc + i) * a.hp + l];
                         const float eps = a.epsc * (T + pl + rc.thr);
                         if (fabsf(T - pl) > rc.thr + eps) ok = false;
                     }
@@ -335,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int i = __ffs(passbits) - 1;
                         passbits &= passbits - 1;
                         if ((int64_t)o < a.cap) {
-                            a.out_q[o] = m.rec[cc + i].q;
+                            a.out_q[o] = rec[cc + i].q;
                             a.out_row[o] = (int32_t)row;
                         }
                         ++o;
@@ -343,20 +425,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&epi_done[sl]);
         }
-        cp_async_wait_all();
-        __syncthreads();
-        if (*sabort) break;
     }
     __syncthreads();
-    cp_async_wait_all();
-    if (*sabort && tid == 0) {
-        // let a TMA or MMA still in flight finish (bounded) before the
-        // shared memory and the TMEM columns are released
-        tc::mbar_wait(&bars[0], ptma);
-        tc::mbar_wait(&bars[1], pmma[0]);
-        tc::mbar_wait(&bars[2], pmma[1]);
-    }
+    if (tid == 0 && *a_issued > *a_used) tc::mbar_wait(a_full, (uint32_t)((*a_issued - 1) & 1));   // a TMA still landing
+    tc::tc_fence_after();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
@@ -537,8 +612,8 @@ size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
-    b += 3 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4);
-    b += 3 * 8 + 4 + 4 + 4 + 16;
+    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + 32);
+    b += 7 * 8 + 4 + 4 * 4 + 16;
     return b;
 }
 
@@ -667,7 +742,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     cudaFuncAttributes fa;
     GTS_CUDA(cudaFuncGetAttributes(&fa, kern));
     int per_sm = (int)(smem_sm / (smem + 1024));
-    const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreads;
+    const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreadsWS;
     if (regs_cta > 0 && per_sm > regs_sm / regs_cta) per_sm = regs_sm / regs_cta;
     if (per_sm > 512 / (2 * nq_chunk)) per_sm = 512 / (2 * nq_chunk);   // TMEM columns
     if (per_sm < 1) per_sm = 1;
@@ -713,7 +788,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.cE1 = cE1;
         a.cE2 = cE2;
         a.any_deleted = tq.any_deleted;
-        kern<<<(unsigned)grid, kThreads, smem, st>>>(c.map_h, c.map_l, a);
+        kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(c.map_h, c.map_l, a);
         ++*launches;
         check_launch("tensor-core tile");
         unsigned long long hcount = 0;
