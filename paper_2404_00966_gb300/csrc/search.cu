@@ -1607,7 +1607,7 @@ struct Runner {
         tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
         TcRegroup rg;
         clk.begin(GTS_STAGE_OTHER, 6);
-        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr);
+        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr, ix->tree.tc.dim_p <= 128);
         clk.end();
         st_tiles += rg.n_items;
         st_tile_entries += rg.n_entries;

@@ -48,6 +48,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// add `bytes` to the transaction count of the current phase without arriving
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
 // plain arrive (release): orders this thread's earlier shared-memory writes
 // before the phase completes
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {

@@ -133,22 +133,27 @@ constexpr int kThreadsWS = (kMmaWarp + 1) * 32;
 // layout (each thread first reads the query ids of the rows it copies).
 template <int NQ>
 __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cnt, TileRec *mrec, float *mpath,
-                                            uint8_t *sBh, uint8_t *sBl, int chunks16, int ptid) {
+                                            uint8_t *sBh, uint8_t *sBl, int chunks16, int ptid, int32_t *sqid) {
     const uint8_t *rsrc = reinterpret_cast<const uint8_t *>(a.grec + start);
     for (int t = ptid; t < cnt * 2; t += kProducers) cp_async16(reinterpret_cast<uint8_t *>(mrec) + t * 16, rsrc + t * 16);
     const uint8_t *psrc = reinterpret_cast<const uint8_t *>(a.gpath + (int64_t)start * a.hp);
     const int pch = cnt * a.hp / 4;
     for (int t = ptid; t < pch; t += kProducers) cp_async16(reinterpret_cast<uint8_t *>(mpath) + t * 16, psrc + t * 16);
+    // query ids first (one load per thread), then the rows: consecutive
+    // threads copy consecutive 16-byte pieces of a row, so every warp
+    // instruction reads whole 32-byte sectors
+    tc::named_sync(1, kProducers);   // every producer is done with the previous chunk's ids
+    for (int j = ptid; j < cnt; j += kProducers) sqid[j] = a.gq[start + j];
+    tc::named_sync(1, kProducers);
     const int per_q = 2 * chunks16;                  // 16-byte copies per query (hi and lo)
-    constexpr int tpq = kProducers / NQ;             // threads per query
-    for (int j = ptid / tpq; j < cnt; j += kProducers / tpq) {
-        const int32_t q = a.gq[start + j];           // one id load, then independent copies
-        const __nv_bfloat16 *srch = a.Qh + (int64_t)q * a.dim_p, *srcl = a.Ql + (int64_t)q * a.dim_p;
-        for (int c = ptid % tpq; c < per_q; c += tpq) {
-            const int comp = c / chunks16, k16 = c - comp * chunks16;
-            uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (NQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
-            cp_async16(dst, (comp ? srcl : srch) + k16 * 8);
-        }
+#pragma unroll 4
+    for (int t = ptid; t < cnt * per_q; t += kProducers) {
+        const int j = t / per_q, c = t - j * per_q;
+        const int32_t q = sqid[j];
+        const int comp = c / chunks16, k16 = c - comp * chunks16;
+        const __nv_bfloat16 *src = (comp ? a.Ql : a.Qh) + (int64_t)q * a.dim_p + k16 * 8;
+        uint8_t *dst = (comp ? sBl : sBh) + (k16 >> 3) * (NQ * 128) + j * 128 + (((k16 & 7) ^ (j & 7)) << 4);
+        cp_async16(dst, src);
     }
 }
 
@@ -160,7 +165,8 @@ __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cn
 // the g-th use of a slot), so no block-wide barrier runs per chunk.
 template <int NQ>
 __global__ void __launch_bounds__(kThreadsWS, 1)
-    k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l, TileArgs a) {
+    k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l,
+                 const __grid_constant__ CUtensorMap map_qh, const __grid_constant__ CUtensorMap map_ql, TileArgs a) {
     constexpr int kNQ = NQ;
     constexpr int kTmemCols = 2 * NQ;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -185,6 +191,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     volatile int *sabort = sitem + 1;
     int *a_issued = sitem + 2;     // A loads issued / consumed (for the abort path)
     int *a_used = sitem + 3;
+    int32_t *sqid = sitem + 4;     // the staged chunk's query ids (producers only), kNQ
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
@@ -233,38 +240,85 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     if (last_g >= 0 && !tc::mbar_wait(&epi_done[last_g & 1], (uint32_t)((last_g >> 1) & 1))) fail(3);
                     tc::mbar_expect_tx(a_full, (uint32_t)(2 * panels * apanel));
                     for (int pnl = 0; pnl < panels; ++pnl) {
-                        tc::tma_load_2d(sAh + pnl * apanel, &map_h, pnl * 64, pos + it.w * kRows, a_full);
-                        tc::tma_load_2d(sAl + pnl * apanel, &map_l, pnl * 64, pos + it.w * kRows, a_full);
+                        const int y = pos + (it.w & (kWindowItem - 1)) * kRows;
+                        tc::tma_load_2d(sAh + pnl * apanel, &map_h, pnl * 64, y, a_full);
+                        tc::tma_load_2d(sAl + pnl * apanel, &map_l, pnl * 64, y, a_full);
                     }
                     ++*a_issued;
                 }
             }
             const int total = it.z;
-            const int nchunks = stop ? 1 : (total + kNQ - 1) / kNQ;
-            for (int c = 0; c < nchunks; ++c, ++g) {
+            const bool window = !stop && (it.w & kWindowItem) != 0;
+            const int rbk = it.w & (kWindowItem - 1);
+            // gather mode: chunks of the node's records; window mode: windows of
+            // 128 consecutive query ids (those without an entry are skipped)
+            const int nchunks = stop ? 1 : window ? (int)((a.nq + kNQ - 1) / kNQ) : (total + kNQ - 1) / kNQ;
+            bool first_chunk = true;
+            for (int c = 0; c < nchunks; ++c) {
+                uint32_t word = 0;
+                if (window) {
+                    // this thread's column: query c * 128 + ptid
+                    const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
+                    if (wi < a.nw) word = a.bits[(int64_t)it.x * a.nw + wi];
+                    const unsigned any = __ballot_sync(0xffffffffu, word != 0u);
+                    if ((ptid & 31) == 0) sqid[ptid >> 5] = any ? 1 : 0;
+                    tc::named_sync(1, kProducers);
+                    int nonempty = 0;
+                    for (int i = 0; i < kProducers / 32; ++i) nonempty |= sqid[i];
+                    tc::named_sync(1, kProducers);
+                    if (!nonempty) continue;
+                }
                 const int sl = g & 1;
                 if (g >= 2 && !tc::mbar_wait(&epi_done[sl], ((g - 2) >> 1) & 1)) fail(4);
-                const int cnt = stop ? 0 : (total - c * kNQ < kNQ ? total - c * kNQ : kNQ);
-                if (!stop)
+                int cnt;
+                if (stop) {
+                    cnt = 0;
+                } else if (window) {
+                    cnt = kNQ;
+                    if (ptid == 0) {
+                        tc::mbar_expect_tx_only(&full[sl], (uint32_t)(2 * panels * bpanel));
+                        for (int pnl = 0; pnl < panels; ++pnl) {
+                            tc::tma_load_2d(sB + sl * bbuf + pnl * bpanel, &map_qh, pnl * 64, c * kNQ, &full[sl]);
+                            tc::tma_load_2d(sB + sl * bbuf + (panels + pnl) * bpanel, &map_ql, pnl * 64, c * kNQ,
+                                            &full[sl]);
+                        }
+                    }
+                    // column ptid: its record and path distances, or an empty record
+                    TileRec *mr = mrec(sl) + ptid;
+                    float *mp = mpath(sl) + ptid * a.hp;
+                    if ((word >> (ptid & 31)) & 1u) {
+                        const int64_t wi = (int64_t)it.x * a.nw + (int64_t)c * (kNQ / 32) + (ptid >> 5);
+                        const int64_t o = a.noff[it.x] + a.wpre[wi] + __popc(word & ((1u << (ptid & 31)) - 1u));
+                        *mr = a.grec[o];
+                        for (int l = 0; l < a.hp; ++l) mp[l] = a.gpath[o * a.hp + l];
+                    } else {
+                        mr->mask = 0;
+                        mr->q = c * kNQ + ptid;
+                    }
+                } else {
+                    cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
                     stage_chunk<NQ>(a, it.y + c * kNQ, cnt, mrec(sl), mpath(sl), sB + sl * bbuf,
-                                    sB + sl * bbuf + panels * bpanel, chunks16, ptid);
+                                    sB + sl * bbuf + panels * bpanel, chunks16, ptid, sqid);
+                }
                 if (ptid == 0) {
                     ChunkDesc dsc;
                     dsc.stop = stop ? 1 : 0;
-                    dsc.new_item = c == 0 ? 1 : 0;
+                    dsc.new_item = first_chunk ? 1 : 0;
                     dsc.first = it.y + c * kNQ;
                     dsc.cnt = cnt;
                     dsc.pos = pos;
                     dsc.size = size;
-                    dsc.rb = it.w * kRows;
+                    dsc.rb = rbk * kRows;
                     dsc.pad_ = 0;
                     *mdesc(sl) = dsc;
                 }
+                first_chunk = false;
                 // the copies have landed and are visible to the tensor cores
                 // (async proxy) before this thread arrives
                 cp_async_wait_all();
                 tc::fence_proxy_async_smem();
                 tc::mbar_arrive(&full[sl]);
+                ++g;
             }
             if (stop) break;
             last_g = (int64_t)g - 1;
@@ -576,14 +630,16 @@ __global__ void k_items_per_node(const int32_t *__restrict__ ncount, const int32
     if (blockIdx.x == 0 && threadIdx.x == 0) nitems[nn] = 0;
 }
 
+// win_min: nodes with at least this many entries get window-mode items
 __global__ void k_fill_items(const int32_t *__restrict__ ncount, const int32_t *__restrict__ nsize,
                              const int64_t *__restrict__ noff, const int64_t *__restrict__ ioff, int64_t nn,
-                             int4 *__restrict__ items) {
+                             int64_t win_min, int4 *__restrict__ items) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = ncount[i];
         if (c == 0) continue;
         const int32_t blocks = (nsize[i] + kRows - 1) / kRows;
-        for (int32_t b = 0; b < blocks; ++b) items[ioff[i] + b] = make_int4((int)i, (int)noff[i], c, b);
+        const int flag = c >= win_min ? kWindowItem : 0;
+        for (int32_t b = 0; b < blocks; ++b) items[ioff[i] + b] = make_int4((int)i, (int)noff[i], c, b | flag);
     }
 }
 
@@ -613,7 +669,7 @@ size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
     size_t b = 1024;                                              // alignment slack
     b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
     b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + 32);
-    b += 7 * 8 + 4 + 4 * 4 + 16;
+    b += 7 * 8 + 4 + 4 * 4 + 16 + (size_t)kNQ * 4;
     return b;
 }
 
@@ -661,14 +717,18 @@ bool regroup_uses_bits(const Tree &t, int64_t nq) {
     return nn * ((nq + 31) / 32) * 8 <= ((int64_t)1 << 30);
 }
 
-int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st, const int32_t *counts) {
+int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st, const int32_t *counts,
+                   bool window_ok) {
     const int64_t E = tq.E;
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
     // the bitmap form when its two (node x query-word) arrays stay small
     const int64_t nw = (tq.nq + 31) / 32;
     const bool use_bits = regroup_uses_bits(t, tq.nq);
-    DBuf<uint32_t> bits(use_bits ? nn * nw : 0, st);
-    DBuf<int32_t> wpre(use_bits ? nn * nw : 0, st);
+    DBuf<uint32_t> &bits = rg.bits;
+    DBuf<int32_t> &wpre = rg.wpre;
+    bits.alloc(use_bits ? nn * nw : 0, st);
+    wpre.alloc(use_bits ? nn * nw : 0, st);
+    rg.nw = use_bits ? nw : 0;
     DBuf<int32_t> own((counts && !use_bits) ? 0 : nn, st), cursor(use_bits ? 0 : nn, st);
     if (use_bits) {
         GTS_CUDA(cudaMemsetAsync(bits.get(), 0, nn * nw * 4, st));
@@ -682,7 +742,9 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
         }
     }
     const int32_t *ncnt = (counts && !use_bits) ? counts : own.get();
-    DBuf<int64_t> c64(nn + 1, st), noff(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
+    DBuf<int64_t> c64(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
+    DBuf<int64_t> &noff = rg.noff;
+    noff.alloc(nn + 1, st);
     k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncnt, nn, c64.get());
     exscan(c64.get(), noff.get(), nn + 1, st);
     int64_t total_entries = 0;
@@ -717,7 +779,9 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     rg.n_chunks = (total_entries + 127) / 128;
     if (total_items > 0) {
         rg.items.alloc(total_items, st);
-        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, noff.get(), ioff.get(), nn, rg.items.get());
+        // window mode for nodes holding at least half of the batch
+        const int64_t win_min = (use_bits && window_ok) ? std::max<int64_t>(1, (tq.nq + 1) / 2) : INT64_MAX;
+        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncnt, lsize, noff.get(), ioff.get(), nn, win_min, rg.items.get());
     }
     check_launch("tile regroup");
     return total_items;
@@ -747,6 +811,9 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     if (per_sm > 512 / (2 * nq_chunk)) per_sm = 512 / (2 * nq_chunk);   // TMEM columns
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
+    // the batch's split query rows, for window-mode chunks (TMA, 128 rows)
+    const CUtensorMap map_qh = make_row_map(tq.Qh, tq.nq, c.dim_p);
+    const CUtensorMap map_ql = make_row_map(tq.Ql, tq.nq, c.dim_p);
     DBuf<int> counter(1, st), status(1, st);
     DBuf<unsigned long long> count(1, st);
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
@@ -788,7 +855,12 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.cE1 = cE1;
         a.cE2 = cE2;
         a.any_deleted = tq.any_deleted;
-        kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(c.map_h, c.map_l, a);
+        a.bits = rg.bits.get();
+        a.wpre = rg.wpre.get();
+        a.noff = rg.noff.get();
+        a.nw = rg.nw;
+        a.nq = tq.nq;
+        kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(c.map_h, c.map_l, map_qh, map_ql, a);
         ++*launches;
         check_launch("tensor-core tile");
         unsigned long long hcount = 0;

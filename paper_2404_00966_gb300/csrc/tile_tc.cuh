@@ -32,7 +32,7 @@ struct TileArgs {
     const int32_t *gq;        // their queries (for the row copies)
     const float *gpath;       // their path distances [*, hp], hp = h rounded up to 4
     int hp;
-    const int4 *items;        // (node, first, count, 0) over `order`
+    const int4 *items;        // (node, first, count, row block | kWindowItem) over the records
     int64_t n_items;
     int *work_counter;
     int32_t *out_q, *out_row;
@@ -41,6 +41,12 @@ struct TileArgs {
     int *status;
     float epsc, cE1, cE2;     // pruning slack; error-bound coefficients
     int any_deleted;          // 0: no row has a delete mark, skip the visibility test
+    // window mode (dense nodes): the node x query bitmap of the regrouping
+    const uint32_t *bits;     // [nodes, nw]
+    const int32_t *wpre;      // exclusive popcount prefix of each row's words
+    const int64_t *noff;      // first record of each node
+    int64_t nw;
+    int64_t nq;
 };
 
 struct TcQuery {
@@ -59,7 +65,15 @@ struct TcQuery {
     int any_deleted = 1;
 };
 
+// items of nodes that hold at least half of the batch's queries run in window
+// mode: chunks are windows of 128 consecutive query ids, loaded by TMA
+constexpr int kWindowItem = 1 << 30;
+
 struct TcRegroup {
+    DBuf<uint32_t> bits;   // node x query bitmap (when the regrouping used one)
+    DBuf<int32_t> wpre;
+    DBuf<int64_t> noff;
+    int64_t nw = 0;
     DBuf<TileRec> grec;    // entry records grouped by node
     DBuf<int32_t> gq;      // their queries
     DBuf<float> gpath;     // their path distances [*, hp]
@@ -82,8 +96,10 @@ void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8
 bool regroup_uses_bits(const Tree &t, int64_t nq);
 // regroup the last-level entries by node into tiles; returns the tile count
 // counts: entries with a surviving leaf per last-level node, if already known
+// window_ok: mark dense nodes' items for window mode (tensor-core tiles with
+// 128-query chunks only)
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st,
-                   const int32_t *counts = nullptr);
+                   const int32_t *counts = nullptr, bool window_ok = false);
 // run the tiles; returns the number of (query, row) pairs written to out_q/out_row
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
