@@ -434,8 +434,10 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
         if (knn) {
             GTS_REQUIRE(nq == 0 || k != nullptr, GTS_EINVAL, "k is NULL");
             copy_small_to_device(k, nq, q->on_device != 0, dk, hk, st);
-            for (int64_t i = 0; i < nq; ++i)
+            for (int64_t i = 0; i < nq; ++i) {
                 GTS_REQUIRE(hk[i] >= 1 && hk[i] <= 1024, GTS_EINVAL, "k must be in 1 .. 1024");
+                qb.max_k = std::max<int64_t>(qb.max_k, hk[i]);
+            }
             qb.k = dk.get();
         } else {
             GTS_REQUIRE(nq == 0 || radii != nullptr, GTS_EINVAL, "radii is NULL");
