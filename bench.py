@@ -172,6 +172,16 @@ def algorithmic_bytes(stage: str, st: dict, dim: int, h: int, C: int) -> float:
     return 0.0
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest of the ranks' values (the slowest rank's time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import paper_2404_00966_gb300 as gts
@@ -238,11 +248,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_step = ms / args.steps
     value = world * nq * args.steps / (ms / 1e3)
     # ---- end to end: pinned host queries, host results
@@ -258,11 +264,7 @@ def run_ours(args):
         r = ix.knn(Qh, Kh, precision=prec)
         tot_res = int(r.offsets[-1])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": world * nq * args.steps / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": int(Qh.numel() * 4 + Kh.numel() * 4),
            "d2h_bytes_per_step": int((nq + 1) * 8 + tot_res * 12)}
