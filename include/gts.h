@@ -129,7 +129,8 @@ enum {
     GTS_STAT_TILE_ENTRIES = 10,/* (query, last-level node) entries run against those blocks */
     GTS_STAT_TILE_PAIRS = 11,  /* (query, row) pairs whose distance the tiles computed */
     GTS_STAT_DENSE_PAIRS = 12, /* (query, pivot) distances computed as dense per-level matrices */
-    GTS_STATS_LEN = 13
+    GTS_STAT_DENSE_LAST = 13,  /* 1 if the last level ran as dense matrices (no entry list) */
+    GTS_STATS_LEN = 14
 };
 
 /* Per-query answers in CSR form: the answers of query i are

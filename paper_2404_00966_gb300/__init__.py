@@ -25,7 +25,7 @@ PREC_FP32, PREC_BF16 = 0, 1
 METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
 STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows",
               "launches", "tiles", "tile_entries", "tile_pairs",
-              "dense_pairs"]
+              "dense_pairs", "dense_last"]
 STAGE_NAMES = ["pivot_dist", "threshold", "expand", "leaf_scan", "verify", "select", "other", "tile"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

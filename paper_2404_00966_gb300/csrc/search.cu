@@ -1089,6 +1089,125 @@ __global__ void k_unpack_row_dist(const uint64_t *__restrict__ in, int64_t C, in
     }
 }
 
+// ---------------------------------------------------------------- dense last level
+//
+// When the frontier of the last pivot level covers most (query, node) pairs,
+// it is kept as matrices instead of an entry list: the child masks of the
+// level above, CM[parent][q]; the query-to-pivot distances, DT[node][q]; the
+// leaf masks, M[node][q]; and a node x query bitmap of the pairs with a
+// surviving leaf.  The tiles read these directly (node-major, 128 queries at
+// a time), so no per-entry records are written or regrouped.
+
+__global__ void k_cm_scatter(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode, int64_t e0,
+                             int64_t e1, const uint64_t *__restrict__ cmask, int64_t nq, uint64_t *__restrict__ cm) {
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x)
+        cm[(int64_t)enode[e] * nq + eq[e]] = cmask[e - e0];
+}
+
+// member(node, q): the node's bit in its parent's child mask for q
+__device__ __forceinline__ bool dense_member(const uint64_t *cm, int64_t node, int64_t q, int64_t nq, int F) {
+    return (cm[(node / F) * nq + q] >> (node % F)) & 1ull;
+}
+
+// kNN threshold from this level's pivots (warp per query; the same candidates
+// as k_tau over the entry list: the pivots of the member nodes)
+__global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const uint64_t *__restrict__ cm,
+                            int64_t lvl_base, int64_t nq, const int32_t *__restrict__ kq,
+                            const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id, int32_t *tk_n,
+                            float *tau) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
+        const int K = kq[q];
+        double *Dl = tk_d + koff[q];
+        int64_t *Il = tk_id + koff[q];
+        int n = tk_n[q];
+        const int64_t s = d.qseq[q];
+        const double up = 1.0 + 2.0 * (double)d.rel;
+        for (int64_t p0 = 0; p0 < P; p0 += 32) {
+            const int64_t p = p0 + lane;
+            bool cand = false;
+            double ub = 0.0;
+            int64_t id = 0;
+            if (p < P && dense_member(cm, p, q, nq, d.F)) {
+                const int32_t prow = d.npiv[lvl_base + p];
+                if (prow >= 0 && row_visible(d, prow, s)) {
+                    ub = (double)D[q * P + p] * up + (double)kAbsFloor;
+                    id = d.row_id[prow];
+                    cand = (n < K) || ub < Dl[K - 1] || (ub == Dl[K - 1] && id < Il[K - 1]);
+                }
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, cand);
+            while (bal) {
+                const int src = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const double u = __shfl_sync(0xffffffffu, ub, src);
+                const int64_t iid = __shfl_sync(0xffffffffu, id, src);
+                warp_tau_insert(Dl, Il, n, K, u, iid, lane);
+            }
+        }
+        if (lane == 0) {
+            tk_n[q] = n;
+            tau[q] = n >= K ? __double2float_ru(Dl[K - 1]) : __int_as_float(0x7f800000);
+        }
+    }
+}
+
+// out[c * rows + r] = in[r * cols + c]
+__global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int64_t cols, float *__restrict__ out) {
+    __shared__ float tile[32][33];
+    const int64_t tr = (int64_t)blockIdx.y * 32, tc = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = tr + i, c = tc + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = tc + i, r = tr + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+// Leaf masks of every member pair (Lemma 1 / 2 on the node's children
+// intervals, the same test as the entry kernels), the node x query bitmap of
+// the pairs with a surviving leaf, and the counts of member pairs and of
+// pairs with a surviving leaf.  Block over (node, 256 queries).
+__global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t *__restrict__ cm, int64_t P,
+                             int64_t nq, int64_t lvl_next, const float *__restrict__ thr_q,
+                             uint64_t *__restrict__ M, uint32_t *__restrict__ bits, int64_t nw,
+                             unsigned long long *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t qchunks = (nq + 255) / 256;
+    unsigned long long nmem = 0, nlive = 0;
+    for (int64_t it = blockIdx.x; it < P * qchunks; it += gridDim.x) {
+        const int64_t p = it / qchunks;
+        const int64_t q = (it - p * qchunks) * 256 + threadIdx.x;
+        const bool member = q < nq && dense_member(cm, p, q, nq, d.F);
+        uint64_t m = 0;
+        if (member) {
+            const float dq = DT[p * nq + q];
+            const float thr = thr_q[q];
+            const int64_t c0 = lvl_next + p * d.F;
+            for (int j = 0; j < d.F; ++j)
+                if (d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc))
+                    m |= 1ull << j;
+        }
+        if (q < nq) M[p * nq + q] = m;
+        const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
+        const unsigned mem = __ballot_sync(0xffffffffu, member);
+        const int64_t w = (q - lane) >> 5;   // the warp's word
+        if (lane == 0 && w < nw) bits[p * nw + w] = live;
+        if (lane == 0) {
+            nmem += __popc(mem);
+            nlive += __popc(live);
+        }
+    }
+    if (lane == 0) {
+        if (nmem) atomicAdd(&counts[0], nmem);
+        if (nlive) atomicAdd(&counts[1], nlive);
+    }
+}
+
 // ---------------------------------------------------------------- results
 
 __global__ void k_range_pack(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
@@ -1268,6 +1387,8 @@ struct Runner {
     std::vector<DBuf<float>> dense;
     std::vector<int> dense_state;
     int64_t st_tile_pairs = 0, st_dense_pairs = 0;
+    bool whole_batch = true;   // no level has been split into groups so far
+    int64_t st_dense_last = 0;
     DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
     DBuf<float> tcqn2;
 
@@ -1442,9 +1563,16 @@ struct Runner {
             DBuf<int64_t> off;
             scan_i32(cnt, E, off);
             const int64_t total = d2h_i64(off.get() + E, st);
+            if (use_tc && l == h - 2 && dense_last_ok(total)) {
+                dense_last_level(L, e0, e1, cmask);
+                return;
+            }
             const int64_t entry_bytes = 8 + 4 * (int64_t)h;
             auto gb = groups(off, E, total, limit_bytes(l) / entry_bytes);
-            if (gb.size() > 2) st_groups += (int64_t)gb.size() - 1;
+            if (gb.size() > 2) {
+                st_groups += (int64_t)gb.size() - 1;
+                whole_batch = false;
+            }
             for (size_t g = 0; g + 1 < gb.size(); ++g) {
                 const int64_t g0 = gb[g], g1 = gb[g + 1];
                 int64_t o0 = 0, o1 = 0;
@@ -1584,31 +1712,108 @@ struct Runner {
     // Last level on the tensor cores: regroup the entries by node, run the
     // tiles (leaf scan + bf16 distance prefilter), then finish the kept pairs
     // with the FP32 distance and its FP64 boundary recheck.
-    void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
-        if (use_l1) {
-            l1_leaf(L, e0, e1, mask, ncount);
-            return;
+    // The dense last level applies when the whole batch reaches the level
+    // above the last in one group, every level so far used dense pivot
+    // matrices, the last level's frontier (`total` entries) covers at least a
+    // quarter of its (query, node) pairs, and its matrices fit a quarter of
+    // the budget.
+    bool dense_last_ok(int64_t total) {
+        // (window chunks of 128 queries: the tensor-core tiles with dim_p <= 128)
+        if (!whole_batch || d.dim == 0 || h < 2 || qb.nq == 0 || qb.nq > 2000000 || ix->tree.tc.dim_p > 128)
+            return false;
+        if ((int)dense_state.size() < h) return false;
+        for (int l = 0; l <= h - 2; ++l)
+            if (dense_state[l] != 1) return false;
+        if (!dense_supported(d.metric, d.dim, d.X, d.Q)) return false;
+        const int64_t P = ix->tree.lvl_off[h] - ix->tree.lvl_off[h - 1];
+        const int64_t Pp = ix->tree.lvl_off[h - 1] - ix->tree.lvl_off[h - 2];
+        const int64_t pairs = qb.nq * P;
+        if (4 * total < pairs) return false;
+        const int64_t nw = (qb.nq + 31) / 32;
+        const int64_t bytes = pairs * (4 + 4 + 8) + P * nw * 8 + Pp * qb.nq * 8;
+        return bytes <= budget / 4;
+    }
+
+    void dense_last_level(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &cmask) {
+        const int ll = h - 1;
+        const int64_t nq = qb.nq;
+        const int64_t base = ix->tree.lvl_off[ll];
+        const int64_t P = ix->tree.lvl_off[h] - base;
+        const int64_t Pp = base - ix->tree.lvl_off[ll - 1];
+        // the last level's distances (forced: the frontier is dense)
+        if (dense_state[ll] != 1) {
+            dense[ll].alloc(nq * P, st);
+            clk.begin(GTS_STAGE_PIVOT_DIST);
+            dense_pivot_dist(d.metric, d.X, d.dim, d.Q, nq, d.npiv + base, P, dense[ll].get(), st);
+            clk.end();
+            st_dense_pairs += nq * P;
+            dense_state[ll] = 1;
         }
+        const float *D = dense[ll].get();
+        st_dense_last = 1;
+        DBuf<uint64_t> cm(Pp * nq, st);
+        GTS_CUDA(cudaMemsetAsync(cm.get(), 0, Pp * nq * 8, st));
+        clk.begin(GTS_STAGE_EXPAND);
+        k_cm_scatter<<<cap(nblocks(e1 - e0, kT)), kT, 0, st>>>(L.q.get(), L.node.get(), e0, e1, cmask.get(), nq,
+                                                               cm.get());
+        clk.end();
+        if (knn) {
+            clk.begin(GTS_STAGE_THRESHOLD);
+            k_tau_dense<<<cap(nblocks(nq, kWarpsPerBlock)), kT, 0, st>>>(d, D, P, cm.get(), base, nq, qb.k,
+                                                                         koff.get(), tk_d.get(), tk_id.get(),
+                                                                         tk_n.get(), thr.get());
+            clk.end();
+            check_launch("dense knn threshold");
+        }
+        DBuf<float> DT(nq * P, st);
+        DBuf<uint64_t> M(nq * P, st);
+        TcRegroup rg;
+        rg.nw = (nq + 31) / 32;
+        rg.bits.alloc(P * rg.nw, st);
+        GTS_CUDA(cudaMemsetAsync(rg.bits.get(), 0, P * rg.nw * 4, st));
+        DBuf<unsigned long long> cnt(2, st);
+        GTS_CUDA(cudaMemsetAsync(cnt.get(), 0, 16, st));
+        clk.begin(GTS_STAGE_PIVOT_DIST, 2);
+        {
+            dim3 tb(32, 8), tg((unsigned)((P + 31) / 32), (unsigned)((nq + 31) / 32));
+            k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get());
+            const int64_t items = P * ((nq + 255) / 256);
+            k_leaf_dense<<<(unsigned)std::min<int64_t>(items, (int64_t)max_blocks * 4), 256, 0, st>>>(
+                d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), M.get(), rg.bits.get(), rg.nw,
+                cnt.get());
+        }
+        clk.end();
+        check_launch("dense leaf masks");
+        unsigned long long hc[2] = {0, 0};
+        GTS_CUDA(cudaMemcpyAsync(hc, cnt.get(), 16, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+        st_pivots += (int64_t)hc[0];
+        st_frontier += (int64_t)hc[0];
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_dense_items(ix->tree, nq, M.get(), rg, st);
+        clk.end();
+        TcQuery tq = tc_query_base();
+        tc_finish(tq, rg);
+    }
+
+    TcQuery tc_query_base() {
         TcQuery tq;
-        tq.E = e1 - e0;
         tq.nq = qb.nq;
         tq.Qh = (const __nv_bfloat16 *)tcQh.get();
         tq.Ql = (const __nv_bfloat16 *)tcQl.get();
         tq.qn2 = tcqn2.get();
         tc_bound_coeffs(ix->tree.tc.dim_p, tq.cE1, tq.cE2);
-        tq.eq = L.q.get() + e0;
-        tq.enode = L.node.get() + e0;
-        tq.path = L.path.get() + e0 * h;
-        tq.emask = mask.get();
         tq.Q = d.Q;
         tq.qseq = d.qseq;
         tq.thr = thr.get();
         tq.epsc = d.epsc;
         tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
-        TcRegroup rg;
-        clk.begin(GTS_STAGE_OTHER, 6);
-        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr, ix->tree.tc.dim_p <= 128);
-        clk.end();
+        return tq;
+    }
+
+    // run the regrouped tiles, then finish the kept pairs with the FP32
+    // distance and its FP64 boundary recheck
+    void tc_finish(TcQuery &tq, TcRegroup &rg) {
         st_tiles += rg.n_items;
         st_tile_entries += rg.n_entries;
         st_tile_pairs += rg.n_pairs;
@@ -1621,7 +1826,8 @@ struct Runner {
         clk.begin(GTS_STAGE_TILE);
         const int64_t C = tc_run(ix->tree, ix->tree.tc, tq, rg, oq, orow, hint, &nl, st);
         clk.end();
-        if (tq.E > 0 && qb.nq > 0) ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
+        if (rg.n_items > 0 && qb.nq > 0)
+            ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
         ++st_groups;
         if (C == 0) return;
         if (knn) {   // the selection wants query-major order
@@ -1639,6 +1845,24 @@ struct Runner {
         } else {
             verify_and_collect(oq, orow, C);
         }
+    }
+
+    void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
+        if (use_l1) {
+            l1_leaf(L, e0, e1, mask, ncount);
+            return;
+        }
+        TcQuery tq = tc_query_base();
+        tq.E = e1 - e0;
+        tq.eq = L.q.get() + e0;
+        tq.enode = L.node.get() + e0;
+        tq.path = L.path.get() + e0 * h;
+        tq.emask = mask.get();
+        TcRegroup rg;
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr, ix->tree.tc.dim_p <= 128);
+        clk.end();
+        tc_finish(tq, rg);
     }
 
     // Last level on the L1 tiles: regroup the entries by node, run the tiles
@@ -2054,6 +2278,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_TILE_ENTRIES] = R.st_tile_entries;
         stats[GTS_STAT_TILE_PAIRS] = R.st_tile_pairs;
         stats[GTS_STAT_DENSE_PAIRS] = R.st_dense_pairs;
+        stats[GTS_STAT_DENSE_LAST] = R.st_dense_last;
     }
 }
 

@@ -108,6 +108,8 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, float cE2, float &alpha, float &beta);
+
 // The per-chunk data the producer hands to the MMA thread and the epilogue.
 struct ChunkDesc {
     int32_t stop;       // 1: no more work
@@ -256,10 +258,19 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             bool first_chunk = true;
             for (int c = 0; c < nchunks; ++c) {
                 uint32_t word = 0;
+                TileRec drec;   // dense last level: this column's record, loaded before the slot wait
+                drec.mask = 0;
                 if (window) {
                     // this thread's column: query c * 128 + ptid
                     const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
                     if (wi < a.nw) word = a.bits[(int64_t)it.x * a.nw + wi];
+                    if (a.dmask && ((word >> (ptid & 31)) & 1u)) {
+                        const int64_t q = (int64_t)c * kNQ + ptid;
+                        drec.mask = a.dmask[(int64_t)it.x * a.nq + q];
+                        drec.thr = a.thr_q[q];
+                        drec.alpha = a.qn2_q[q];   // |q|^2 until the constants are formed
+                        drec.seq = a.seq_q[q];
+                    }
                     const unsigned any = __ballot_sync(0xffffffffu, word != 0u);
                     if ((ptid & 31) == 0) sqid[ptid >> 5] = any ? 1 : 0;
                     tc::named_sync(1, kProducers);
@@ -286,7 +297,13 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     // column ptid: its record and path distances, or an empty record
                     TileRec *mr = mrec(sl) + ptid;
                     float *mp = mpath(sl) + ptid * a.hp;
-                    if ((word >> (ptid & 31)) & 1u) {
+                    if (a.dmask) {
+                        // dense last level: the record from the per-query arrays
+                        TileRec r = drec;
+                        r.q = (int32_t)((int64_t)c * kNQ + ptid);
+                        if (r.mask) bound_consts(r.thr, drec.alpha, a.cE1, a.cE2, r.alpha, r.beta);
+                        *mr = r;
+                    } else if ((word >> (ptid & 31)) & 1u) {
                         const int64_t wi = (int64_t)it.x * a.nw + (int64_t)c * (kNQ / 32) + (ptid >> 5);
                         const int64_t o = a.noff[it.x] + a.wpre[wi] + __popc(word & ((1u << (ptid & 31)) - 1u));
                         *mr = a.grec[o];
@@ -447,7 +464,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     const TileRec &rc = rec[cc + i];
                     if (rdel <= rc.seq) continue;
                     bool ok = true;
-                    for (int l = 0; l < a.h && ok; ++l) {
+                    // (the table lower bound can only drop a pair that the
+                    // distance bound already dropped; dense chunks skip it)
+                    for (int l = 0; l < a.h && ok && !a.dmask; ++l) {
                         const float T = a.table[(int64_t)l * a.n + row];
                         const float pl = pth[(cc + i) * a.hp + l];
                         const float eps = a.epsc * (T + pl + rc.thr);
@@ -787,6 +806,41 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     return total_items;
 }
 
+int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegroup &rg, cudaStream_t st) {
+    const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
+    const int64_t nw = rg.nw;
+    DBuf<int32_t> ncnt(nn, st);
+    rg.wpre.alloc(nn * nw, st);
+    k_bits_rows<<<(unsigned)std::min<int64_t>(nn, 65535), 256, 0, st>>>(rg.bits.get(), nn, nw, rg.wpre.get(),
+                                                                         ncnt.get());
+    DBuf<int64_t> c64(nn + 1, st), nitems(nn + 1, st), ioff(nn + 1, st);
+    rg.noff.alloc(nn + 1, st);
+    k_i32_to_i64_tc<<<nblk(nn), 256, 0, st>>>(ncnt.get(), nn, c64.get());
+    exscan(c64.get(), rg.noff.get(), nn + 1, st);
+    const int32_t *lsize = t.nsize.get() + t.lvl_off[t.h - 1];
+    DBuf<unsigned long long> pairs(1, st);
+    GTS_CUDA(cudaMemsetAsync(pairs.get(), 0, 8, st));
+    k_items_per_node<<<nblk(nn), 256, 0, st>>>(ncnt.get(), lsize, nn, nitems.get(), pairs.get());
+    exscan(nitems.get(), ioff.get(), nn + 1, st);
+    int64_t total_items = 0, total_entries = 0;
+    unsigned long long total_pairs = 0;
+    GTS_CUDA(cudaMemcpyAsync(&total_items, ioff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(&total_entries, rg.noff.get() + nn, 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(&total_pairs, pairs.get(), 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    rg.dmask = dmask;
+    rg.n_items = total_items;
+    rg.n_entries = total_entries;
+    rg.n_pairs = (int64_t)total_pairs;
+    rg.n_chunks = 0;
+    if (total_items > 0) {
+        rg.items.alloc(total_items, st);
+        k_fill_items<<<nblk(nn), 256, 0, st>>>(ncnt.get(), lsize, rg.noff.get(), ioff.get(), nn, 0, rg.items.get());
+    }
+    check_launch("dense tile items");
+    return total_items;
+}
+
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st) {
     *launches = 0;
@@ -860,6 +914,10 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.noff = rg.noff.get();
         a.nw = rg.nw;
         a.nq = tq.nq;
+        a.dmask = rg.dmask;
+        a.thr_q = tq.thr;
+        a.qn2_q = tq.qn2;
+        a.seq_q = tq.qseq;
         kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(c.map_h, c.map_l, map_qh, map_ql, a);
         ++*launches;
         check_launch("tensor-core tile");

@@ -47,6 +47,11 @@ struct TileArgs {
     const int64_t *noff;      // first record of each node
     int64_t nw;
     int64_t nq;
+    // dense last level: no records; column q of node p takes its leaf mask
+    // from dmask[p * nq + q] and its query data from the per-query arrays
+    const uint64_t *dmask;    // null: records
+    const float *thr_q, *qn2_q;
+    const int64_t *seq_q;
 };
 
 struct TcQuery {
@@ -70,6 +75,7 @@ struct TcQuery {
 constexpr int kWindowItem = 1 << 30;
 
 struct TcRegroup {
+    const uint64_t *dmask = nullptr;   // dense last level: leaf masks [nodes, nq] (no records)
     DBuf<uint32_t> bits;   // node x query bitmap (when the regrouping used one)
     DBuf<int32_t> wpre;
     DBuf<int64_t> noff;
@@ -100,6 +106,10 @@ bool regroup_uses_bits(const Tree &t, int64_t nq);
 // 128-query chunks only)
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st,
                    const int32_t *counts = nullptr, bool window_ok = false);
+// dense last level: work items for every node with a set bit in the node x
+// query bitmap `bits` ([nodes, nw] words, nw = ceil(nq / 32)), all in window
+// mode; the leaf masks stay in dmask [nodes, nq]
+int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegroup &rg, cudaStream_t st);
 // run the tiles; returns the number of (query, row) pairs written to out_q/out_row
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);

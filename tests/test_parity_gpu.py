@@ -238,8 +238,15 @@ def test_bf16_tiles_parity(gts, dim, dup):
     for k in (1, 10, 33):
         r = ix.knn(Q, k, precision="bf16")
         assert_same(r, oracle.knn_query("l2", X, Q, k), "l2", f"bf16 tiles knn k={k}")
-    assert ix.knn(Q, 500, precision="bf16").stats["dense_pairs"] > 0   # wide frontier: dense pivot matrices
     d = oracle.distances_to("l2", X[:500], Q[4])
+    # wide frontiers: dense pivot matrices and (128-query tiles) the dense last level
+    wide = ix.knn(Q, 500, precision="bf16")
+    assert wide.stats["dense_pairs"] > 0 and wide.stats["dense_last"] == (1 if dim <= 128 else 0)
+    assert_same(wide, oracle.knn_query("l2", X, Q, 500), "l2", "bf16 tiles knn k=500 (dense last level)")
+    big = np.full(300, np.float32(np.median(d)), np.float32)
+    rb = ix.range(Q, big, precision="bf16")
+    assert rb.stats["dense_last"] == (1 if dim <= 128 else 0)
+    assert_same(rb, oracle.range_query("l2", X, Q, big), "l2", "bf16 tiles wide range (dense last level)")
     radii = np.linspace(0.0, 1.0, 300).astype(np.float32) * np.float32(np.median(d))
     assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l2", X, Q, radii), "l2", "bf16 tiles range")
     ix.close()
