@@ -37,10 +37,10 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/):
-# k_tile_l2_tc at half size, 1.202 GB read + write, scaled to the full workload
+# k_tile_l2_tc at half size, 0.480 GB read + write, scaled to the full workload
 # by its (query, node) entries (x 39,831,029 / 18,849,983).  None once the
 # kernel has changed since the counters were taken.
-TRAFFIC = {"kernel": "tile", "bytes_per_launch": 2.54e9}
+TRAFFIC = {"kernel": "tile", "bytes_per_launch": 1.01e9}
 
 
 def workload(scale: float = 1.0):

@@ -842,6 +842,45 @@ __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_
 // rank-th smallest (1-based) value among those enumerated by get(i, &v) for
 // i in [0, M); values are non-negative keys compared as unsigned integers.
 // Whole block; returns the same value in every thread.
+// The same selection with 8-bit digits (half the passes): 256 bins, the bin
+// holding the rank found by a block-wide prefix sum (blockDim.x == 256).
+template <int BITS, class Get>
+__device__ uint64_t block_select8(int64_t M, int64_t rank, Get get, unsigned *hist, int64_t *sh) {
+    __shared__ unsigned wsum[8];
+    uint64_t prefix = 0, pmask = 0;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int shift = BITS - 8; shift >= 0; shift -= 8) {
+        hist[t] = 0;
+        __syncthreads();
+        for (int64_t i = t; i < M; i += blockDim.x) {
+            uint64_t v;
+            if (get(i, v) && (v & pmask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        const unsigned c = hist[t];
+        unsigned incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        unsigned before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const int64_t lo = (int64_t)before + incl - c, hi = (int64_t)before + incl;
+        if (c > 0 && lo < rank && rank <= hi) {   // exactly one bin holds the rank
+            sh[0] = t;
+            sh[1] = rank - lo;
+        }
+        __syncthreads();
+        prefix |= (uint64_t)sh[0] << shift;
+        pmask |= 255ull << shift;
+        rank = sh[1];
+        __syncthreads();
+    }
+    return prefix;
+}
+
 template <int BITS, class Get>
 __device__ uint64_t block_select(int64_t M, int64_t rank, Get get, unsigned *hist, int64_t *sh) {
     uint64_t prefix = 0, pmask = 0;
@@ -897,7 +936,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
                             const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
                             int32_t *__restrict__ bn, double *__restrict__ ckey,
                             unsigned long long *__restrict__ rechecks) {
-    __shared__ unsigned hist[16];
+    __shared__ unsigned hist[256];
     __shared__ int64_t sh[4];
     __shared__ int64_t red[kWarpsPerBlock];
     __shared__ double kk[kKeepCap];
@@ -930,7 +969,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
                 v = __float_as_uint(x);
                 return true;
             };
-            U = block_select<32>((int64_t)nb + M, K, get_hi, hist, sh);
+            U = block_select8<32>((int64_t)nb + M, K, get_hi, hist, sh);
         }
         const float Uf = __uint_as_float((uint32_t)U);
         int64_t kept = 0;
@@ -969,7 +1008,9 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     const int64_t take = total < K ? total : K;
     if (take == 0) return;
     uint64_t Vk = INF, Ik = 0x7fffffffffffffffull;
-    if (total > K) {
+    // few exact keys (the common case): stage them all and sort; else select
+    // the k-th (key, id) first and stage only those up to it
+    if (total > kKeepCap) {
         Vk = block_select<64>((int64_t)nb + M, K, get_key, hist, sh);
         int64_t lt = 0;
         for (int64_t i = threadIdx.x; i < (int64_t)nb + M; i += blockDim.x) {
@@ -1001,10 +1042,11 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     }
     __syncthreads();
     // bitonic sort of the survivors by (key, id)
+    const int staged = nkeep < kKeepCap ? nkeep : kKeepCap;
     int L = 1;
-    while (L < take) L <<= 1;
+    while (L < take || L < staged) L <<= 1;
     for (int i = threadIdx.x; i < L; i += blockDim.x)
-        if (i >= take) {
+        if (i >= staged) {
             kk[i] = __longlong_as_double(0x7ff0000000000000ll);
             ki[i] = 0x7fffffffffffffffll;
         }
