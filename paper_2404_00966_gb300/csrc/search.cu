@@ -930,12 +930,16 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 //  B. the k-th smallest exact (key, id) over answer + kept candidates, ties
 //     to the smaller id, gives exactly min(k, total) survivors, which are
 //     sorted and written back as the new answer.
-template <int METRIC>
+// PASS 0 (L1 / L2): step A; the candidates that need an FP64 key are listed
+// in rlist and get it from k_recheck_keys (a thread per candidate: the
+// sequential FP64 sums then keep every lane of the FP64 pipe busy).  PASS 1:
+// step B (and, for edit distance, the keys from the exact distances).
+template <int METRIC, int PASS>
 __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
                             const float *__restrict__ cdist, int64_t C, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
-                            int32_t *__restrict__ bn, double *__restrict__ ckey,
-                            unsigned long long *__restrict__ rechecks) {
+                            int32_t *__restrict__ bn, double *__restrict__ ckey, int64_t *__restrict__ rlist,
+                            unsigned long long *__restrict__ rcount) {
     __shared__ unsigned hist[256];
     __shared__ int64_t sh[4];
     __shared__ int64_t red[kWarpsPerBlock];
@@ -954,7 +958,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     constexpr bool FLOAT_METRIC = METRIC != GTS_EDIT;
     const float up = 1.f + 2.f * d.rel, dn = 1.f - 2.f * d.rel;
     // ---- A: candidates that can still enter the top k
-    if (FLOAT_METRIC) {
+    if (FLOAT_METRIC && PASS == 0) {
         uint64_t U = 0x7f800000ull;   // +inf as float bits
         if ((int64_t)nb + M > K) {
             auto get_hi = [&](int64_t i, uint64_t &v) -> bool {
@@ -972,21 +976,15 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
             U = block_select8<32>((int64_t)nb + M, K, get_hi, hist, sh);
         }
         const float Uf = __uint_as_float((uint32_t)U);
-        int64_t kept = 0;
         for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
             const float dv = cdist[a + i];
-            double key = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
-            if (dv * dn - kAbsFloor <= Uf && dv != __int_as_float(0x7f800000)) {
-                const float *qv = d.Q + (int64_t)q * d.dim;
-                const float *xv = vrow(d, crow[a + i]);
-                key = METRIC == GTS_L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
-                ++kept;
-            }
-            ckey[a + i] = key;
+            ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
+            if (dv * dn - kAbsFloor <= Uf && dv != __int_as_float(0x7f800000))
+                rlist[atomicAdd(rcount, 1ull)] = a + i;   // its FP64 key comes next
         }
-        kept = block_sum(kept, red);
-        if (threadIdx.x == 0) atomicAdd(rechecks, (unsigned long long)kept);
-    } else {
+        return;
+    }
+    if (!FLOAT_METRIC) {
         for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
             const float dv = cdist[a + i];
             ckey[a + i] = dv == __int_as_float(0x7f800000) ? __longlong_as_double(0x7ff0000000000000ll) : (double)dv;
@@ -1100,6 +1098,25 @@ __global__ void k_decide_range_l1(Dev d, const int32_t *__restrict__ cq, const i
             cdist[c] = __double2float_rn(key);
             atomicAdd(rechecks, 1ull);
         }
+    }
+}
+
+__global__ void k_add_u64(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst) {
+    *dst += *src;
+}
+
+// FP64 keys (the CPU reference's operation order) of the listed candidates,
+// a thread per candidate
+template <int METRIC>
+__global__ void k_recheck_keys(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+                               const int64_t *__restrict__ rlist, const unsigned long long *__restrict__ rcount,
+                               double *__restrict__ ckey) {
+    const int64_t n = (int64_t)*rcount;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = rlist[i];
+        const float *qv = d.Q + (int64_t)cq[c] * d.dim;
+        const float *xv = vrow(d, crow[c]);
+        ckey[c] = METRIC == GTS_L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
     }
 }
 
@@ -2092,16 +2109,31 @@ struct Runner {
     void merge_knn(DBuf<int32_t> &kq2, DBuf<int32_t> &krow2, DBuf<float> &kd2, int64_t R) {
         DBuf<double> ckey(R, st);
         const unsigned grid = (unsigned)qb.nq;
-        clk.begin(GTS_STAGE_SELECT);
-        if (d.metric == GTS_L2)
-            k_knn_merge<GTS_L2><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                     bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
-        else if (d.metric == GTS_L1)
-            k_knn_merge<GTS_L1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                     bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
-        else
-            k_knn_merge<GTS_EDIT><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                       bd.get(), bi.get(), bn.get(), ckey.get(), counters.get());
+        clk.begin(GTS_STAGE_SELECT, 4);
+        if (d.metric == GTS_EDIT) {
+            k_knn_merge<GTS_EDIT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
+                                                          bd.get(), bi.get(), bn.get(), ckey.get(), nullptr, nullptr);
+        } else {
+            // step A lists the candidates that need an FP64 key, a thread per
+            // candidate computes it, step B selects; the list's length is
+            // added to the recheck counter (counters[0])
+            DBuf<int64_t> rlist(R, st);
+            DBuf<unsigned long long> rc(1, st);
+            GTS_CUDA(cudaMemsetAsync(rc.get(), 0, 8, st));
+#define GTS_MERGE(MT)                                                                                            \
+    do {                                                                                                         \
+        k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
+                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get()); \
+        k_recheck_keys<MT><<<cap(nblocks(R, kT)), kT, 0, st>>>(d, kq2.get(), krow2.get(), rlist.get(), rc.get(), \
+                                                              ckey.get());                                     \
+        k_knn_merge<MT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
+                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get()); \
+        k_add_u64<<<1, 1, 0, st>>>(rc.get(), counters.get());                                                   \
+    } while (0)
+            if (d.metric == GTS_L2) GTS_MERGE(GTS_L2);
+            else GTS_MERGE(GTS_L1);
+#undef GTS_MERGE
+        }
         clk.end();
         check_launch("knn merge");
     }
