@@ -213,6 +213,9 @@ def run_ours(args):
     info = ix.info()
     prec = args.precision
     stream = torch.cuda.current_stream()
+    # launch parameters for this index and batch shape (gts_autotune; untimed
+    # setup like the build; every setting returns the same answers)
+    tuning = ix.autotune(Qd, k=np.full(nq, k, np.int32), precision=prec, reps=2) if not args.no_tune else None
 
     def step_prec(p, timing=False):
         r = ix.knn(Qd, Kd, precision=p, result_on_device=True, timing=timing)
@@ -303,7 +306,7 @@ def run_ours(args):
         "config": {"workload": "gauss64_1Mx128_knn10", "n": int(X.shape[0]), "dim": int(dim), "nq": int(nq),
                    "k": k, "fanout": 20, "h": info["h"], "precision": prec,
                    "l2_flush": "inputs larger than L2 (vectors 512 MB + table 16 MB per step)",
-                   "parallelism": f"replicas{world}", "build_s": round(build_s, 3)},
+                   "parallelism": f"replicas{world}", "build_s": round(build_s, 3), "tuning": tuning},
         "e2e": {kk: (round(v, 1) if isinstance(v, float) else v) for kk, v in e2e.items()},
         "gpu_launches": int(launches),
         "roofline": roof,
@@ -596,6 +599,7 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the workload (profiling only)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch parameters")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--requests", type=int, default=20_000, help="serving: number of requests")

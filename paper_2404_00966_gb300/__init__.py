@@ -331,8 +331,8 @@ class Index:
                                                              np.float32)
         if m.obj.on_device:
             import torch
-            kk = None if kk is None else torch.from_numpy(kk).cuda()
-            rr = None if rr is None else torch.from_numpy(rr).cuda()
+            kk = None if kk is None else torch.from_numpy(kk.copy()).cuda()
+            rr = None if rr is None else torch.from_numpy(rr.copy()).cuda()
         opts = _QueryOpts(stream=stream if stream is not None else _stream_of(m.first),
                           precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
                           memory_budget=int(memory_budget))

@@ -261,12 +261,14 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
         double ub = 0.0;
         int64_t id = 0;
         if (e < b) {
-            const int32_t prow = d.npiv[lvl_base + enode[e]];
-            if (row_visible(d, prow, s)) {
-                const float dv = path[e * d.h + l];
-                ub = d.rel > 0.f ? (double)dv * up + (double)kAbsFloor : (double)dv;
-                id = d.row_id[prow];
-                cand = (n < K) || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+            const float dv = path[e * d.h + l];
+            ub = d.rel > 0.f ? (double)dv * up + (double)kAbsFloor : (double)dv;
+            if ((n < K) || ub <= D[K - 1]) {   // the bound test before the pivot's delete mark
+                const int32_t prow = d.npiv[lvl_base + enode[e]];
+                if (row_visible(d, prow, s)) {
+                    id = d.row_id[prow];
+                    cand = (n < K) || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+                }
             }
         }
         unsigned bal = __ballot_sync(0xffffffffu, cand);
@@ -1189,11 +1191,15 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
             double ub = 0.0;
             int64_t id = 0;
             if (p < P && dense_member(cm, p, q, nq, d.F)) {
-                const int32_t prow = d.npiv[lvl_base + p];
-                if (prow >= 0 && row_visible(d, prow, s)) {
-                    ub = (double)D[q * P + p] * up + (double)kAbsFloor;
-                    id = d.row_id[prow];
-                    cand = (n < K) || ub < Dl[K - 1] || (ub == Dl[K - 1] && id < Il[K - 1]);
+                ub = (double)D[q * P + p] * up + (double)kAbsFloor;
+                // the bound test first: most pivots fail it, and then the
+                // pivot's delete mark and id are never read
+                if ((n < K) || ub <= Dl[K - 1]) {
+                    const int32_t prow = d.npiv[lvl_base + p];
+                    if (prow >= 0 && row_visible(d, prow, s)) {
+                        id = d.row_id[prow];
+                        cand = (n < K) || ub < Dl[K - 1] || (ub == Dl[K - 1] && id < Il[K - 1]);
+                    }
                 }
             }
             unsigned bal = __ballot_sync(0xffffffffu, cand);
@@ -1235,21 +1241,32 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
                              int64_t nq, int64_t lvl_next, const float *__restrict__ thr_q,
                              uint64_t *__restrict__ M, uint32_t *__restrict__ bits, int64_t nw,
                              unsigned long long *__restrict__ counts) {
+    __shared__ float slo[64], shi[64];   // the node's children intervals (+inf / -inf: empty child)
     const int lane = threadIdx.x & 31;
     const int64_t qchunks = (nq + 255) / 256;
     unsigned long long nmem = 0, nlive = 0;
+    int64_t cur = -1;
     for (int64_t it = blockIdx.x; it < P * qchunks; it += gridDim.x) {
         const int64_t p = it / qchunks;
         const int64_t q = (it - p * qchunks) * 256 + threadIdx.x;
+        if (p != cur) {   // block-uniform
+            __syncthreads();
+            if (threadIdx.x < d.F) {
+                const int64_t c = lvl_next + p * d.F + threadIdx.x;
+                const bool ne = d.nsize[c] > 0;
+                slo[threadIdx.x] = ne ? d.nlo[c] : __int_as_float(0x7f800000);
+                shi[threadIdx.x] = ne ? d.nhi[c] : __int_as_float(0xff800000);
+            }
+            __syncthreads();
+            cur = p;
+        }
         const bool member = q < nq && dense_member(cm, p, q, nq, d.F);
         uint64_t m = 0;
         if (member) {
             const float dq = DT[p * nq + q];
             const float thr = thr_q[q];
-            const int64_t c0 = lvl_next + p * d.F;
             for (int j = 0; j < d.F; ++j)
-                if (d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc))
-                    m |= 1ull << j;
+                if (shi[j] >= slo[j] && interval_hit(dq, thr, slo[j], shi[j], d.epsc)) m |= 1ull << j;
         }
         if (q < nq) M[p * nq + q] = m;
         const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
