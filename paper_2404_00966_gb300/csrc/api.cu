@@ -188,6 +188,8 @@ void grow(DBuf<T> &b, size_t used, size_t need, cudaStream_t st) {
     size_t cap = std::max<size_t>(need, b.n * 2);
     DBuf<T> nbuf(cap, st);
     if (used) GTS_CUDA(cudaMemcpyAsync(nbuf.get(), b.get(), used * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    GTS_CUDA(cudaStreamSynchronize(st));   // the old buffer is freed synchronously below
+    nbuf.persist();
     b = std::move(nbuf);
 }
 

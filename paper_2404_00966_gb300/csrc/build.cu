@@ -49,7 +49,8 @@ int tree_height(int64_t n, int F, int n_pivots) {
 
 size_t Tree::device_bytes() const {
     return X.bytes() + S.bytes() + Soff.bytes() + row_id.bytes() + table.bytes() + row_del.bytes() + npos.bytes() +
-           nsize.bytes() + npiv.bytes() + nlo.bytes() + nhi.bytes() + tc.Xh.bytes() + tc.Xl.bytes() + tc.xn2.bytes();
+           nsize.bytes() + npiv.bytes() + nlo.bytes() + nhi.bytes() + tc.Xh.bytes() + tc.Xl.bytes() + tc.xn2.bytes() +
+           qg.bytes();
 }
 
 namespace {
@@ -391,6 +392,7 @@ void build_tree(Tree &t, const Objects &objs, const int64_t *d_ids, int metric, 
     }
     check_launch("gather");
     GTS_CUDA(cudaStreamSynchronize(st));
+    t.persist();
 }
 
 }  // namespace gts

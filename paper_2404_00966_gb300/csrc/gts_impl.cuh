@@ -84,7 +84,7 @@ struct DBuf {
     DBuf &operator=(DBuf &&o) noexcept {
         if (this != &o) {
             release();
-            p = o.p; n = o.n; s = o.s;
+            p = o.p; n = o.n; s = o.s; keep = o.keep;
             o.p = nullptr; o.n = 0;
         }
         return *this;
@@ -96,11 +96,19 @@ struct DBuf {
         n = count;
         if (count) GTS_CUDA(cudaMallocAsync((void **)&p, count * sizeof(T), st));
     }
+    // Index-owned buffers outlive the stream they were allocated on (a
+    // caller's stream, a serving worker's): they are released with the
+    // synchronous cudaFree, which needs no stream.
+    void persist() { keep = true; }
     void release() {
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            if (keep) cudaFree(p);
+            else cudaFreeAsync(p, s);
+        }
         p = nullptr;
         n = 0;
     }
+    bool keep = false;
     T *get() const { return p; }
     size_t bytes() const { return n * sizeof(T); }
 };
@@ -142,7 +150,14 @@ struct Tree {
     int max_len = 0;                // longest string
     int64_t n_deleted = 0;          // rows carrying a delete mark
     TcCache tc;
+    DBuf<uint8_t> qg;               // strings: hashed 3-gram counts per row [n, 64] (built on first use)
+    bool qg_ready = false;
     size_t device_bytes() const;
+    void persist() {   // every buffer the index keeps
+        X.persist(); S.persist(); Soff.persist(); row_id.persist(); table.persist(); row_del.persist();
+        npos.persist(); nsize.persist(); npiv.persist(); nlo.persist(); nhi.persist();
+        tc.Xh.persist(); tc.Xl.persist(); tc.xn2.persist(); qg.persist();
+    }
 };
 
 struct Cache {
@@ -182,6 +197,7 @@ struct gts_index {
     int64_t rebuilds = 0;
     std::vector<cudaEvent_t> events;   // reused by per-stage timing
     std::mutex tune_mu;
+    std::mutex prep_mu;   // lazily built per-index data (BF16 split rows, 3-gram counts)
     gts::Tuning tuning;
     std::atomic<int64_t> tc_pairs_hint[2] = {{0}, {0}}; // last tensor-core output size per query (x1024)
     std::atomic<int64_t> l1_pairs_hint[4] = {{0}, {0}, {0}, {0}};  // L1 tiles: range, kNN phases 0..2 (same unit)

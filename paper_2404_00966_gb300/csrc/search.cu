@@ -64,6 +64,8 @@ struct Dev {
     const int64_t *QSoff;
     const int64_t *qseq;
     float rel;     // FP32 relative error bound of one distance (0 for edit distance)
+    const uint8_t *qg;    // strings: hashed 3-gram counts of the tree rows [n, 64]
+    const uint8_t *qgq;   // the same for the batch's queries [nq, 64]
     float epsc;    // pruning slack factor (0 for edit distance)
 };
 
@@ -804,6 +806,42 @@ __global__ void k_compact_cands(const int32_t *__restrict__ cq, const int32_t *_
     }
 }
 
+// ---------------------------------------------------------------- q-gram count filter
+//
+// A lower bound for edit distance from the counts of the strings' 3-grams
+// (Ukkonen 1992, q-gram distance): a substitution changes at most 3 of a
+// string's 3-grams and an insertion or deletion at most 2 old and 3 new ones,
+// so the L1 distance between the two 3-gram count vectors is at most 6 times
+// the edit distance.  Counting the 3-grams in 64 hashed buckets (sums of the
+// exact counts) and capping a count at 255 can only lower that L1 distance,
+// so L1(buckets) > 6 t proves d > t, and such a pair is not verified.
+constexpr int kQgBuckets = 64;
+
+__device__ __forceinline__ uint32_t qgram_bucket(uint32_t a, uint32_t b, uint32_t c) {
+    return ((((a << 16) | (b << 8) | c) * 0x9E3779B1u) >> 26) & (kQgBuckets - 1);
+}
+
+// thread per string: its 64 bucket counts (saturating at 255)
+__global__ void k_qgram_hist(const uint8_t *__restrict__ S, const int64_t *__restrict__ Soff, int64_t n,
+                             uint8_t *__restrict__ out) {
+    __shared__ uint8_t hb[256][kQgBuckets];
+    uint8_t *h = hb[threadIdx.x];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i - threadIdx.x < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i >= n) continue;
+        for (int b = 0; b < kQgBuckets; ++b) h[b] = 0;
+        const uint8_t *s = S + Soff[i];
+        const int64_t len = Soff[i + 1] - Soff[i];
+        for (int64_t j = 0; j + 2 < len; ++j) {
+            const uint32_t b = qgram_bucket(s[j], s[j + 1], s[j + 2]);
+            if (h[b] < 255) ++h[b];
+        }
+        uint32_t *o = reinterpret_cast<uint32_t *>(out + i * kQgBuckets);
+        const uint32_t *hw = reinterpret_cast<const uint32_t *>(h);
+        for (int w = 0; w < kQgBuckets / 4; ++w) o[w] = hw[w];
+    }
+}
+
 template <int W, bool KNN>
 __global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
                              int chunk, const float *__restrict__ thr_q, float *__restrict__ cdist,
@@ -818,12 +856,34 @@ __global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_
         const int m = (int)(d.QSoff[q + 1] - d.QSoff[q]);
         if (m > 0) build_peq<W>(Peq, d.QS + d.QSoff[q], m);
         const float r = thr_q[q];
+        uint32_t qw[kQgBuckets / 4];
+        if (d.qg) {
+#pragma unroll
+            for (int w = 0; w < kQgBuckets / 4; ++w) qw[w] = reinterpret_cast<const uint32_t *>(d.qgq + (int64_t)q * kQgBuckets)[w];
+        }
         for (int64_t c = s + threadIdx.x; c < t; c += blockDim.x) {
             const int64_t row = crow[c];
             if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
                 cdist[c] = __int_as_float(0x7f800000);
                 keep[c] = 0;
                 continue;
+            }
+            if (d.qg && row < d.n && r < 1e9f) {   // the 3-gram bound: d >= L1 / 6
+                const uint4 *ow = reinterpret_cast<const uint4 *>(d.qg + row * kQgBuckets);
+                uint32_t l1 = 0;
+#pragma unroll
+                for (int v = 0; v < kQgBuckets / 16; ++v) {
+                    const uint4 o = ow[v];
+                    l1 = __vsadu4(qw[4 * v], o.x) + l1;
+                    l1 = __vsadu4(qw[4 * v + 1], o.y) + l1;
+                    l1 = __vsadu4(qw[4 * v + 2], o.z) + l1;
+                    l1 = __vsadu4(qw[4 * v + 3], o.w) + l1;
+                }
+                if ((float)l1 > 6.f * r) {
+                    cdist[c] = __int_as_float(0x7f800000);
+                    keep[c] = 0;
+                    continue;
+                }
             }
             const uint8_t *tx;
             int len;
@@ -841,11 +901,9 @@ __global__ void k_verify_str(Dev d, const int32_t *__restrict__ cq, const int32_
 
 __device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
 
-// rank-th smallest (1-based) value among those enumerated by get(i, &v) for
-// i in [0, M); values are non-negative keys compared as unsigned integers.
-// Whole block; returns the same value in every thread.
-// The same selection with 8-bit digits (half the passes): 256 bins, the bin
-// holding the rank found by a block-wide prefix sum (blockDim.x == 256).
+// Selection with 8-bit digits (the rank-th smallest as block_select below,
+// half the passes): 256 bins, the bin holding the rank found by a block-wide
+// prefix sum (blockDim.x == 256).
 template <int BITS, class Get>
 __device__ uint64_t block_select8(int64_t M, int64_t rank, Get get, unsigned *hist, int64_t *sh) {
     __shared__ unsigned wsum[8];
@@ -883,6 +941,9 @@ __device__ uint64_t block_select8(int64_t M, int64_t rank, Get get, unsigned *hi
     return prefix;
 }
 
+// rank-th smallest (1-based) value among those enumerated by get(i, &v) for
+// i in [0, M); values are non-negative keys compared as unsigned integers.
+// Whole block; returns the same value in every thread.
 template <int BITS, class Get>
 __device__ uint64_t block_select(int64_t M, int64_t rank, Get get, unsigned *hist, int64_t *sh) {
     uint64_t prefix = 0, pmask = 0;
@@ -2195,7 +2256,10 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     }
     if (precision == GTS_PREC_BF16 && l1_tiles_supported(t, qb.Q)) R.use_l1 = true;
     if (precision == GTS_PREC_BF16 && tc_supported(t)) {
-        tc_prepare(t, t.tc, st);
+        {
+            std::lock_guard<std::mutex> g(ix->prep_mu);   // concurrent queries build it once
+            tc_prepare(t, t.tc, st);
+        }
         R.use_tc = true;
         R.clk.begin(GTS_STAGE_OTHER);
         tc_split_queries(qb.Q, nq, t.dim, t.tc.dim_p, R.tcQh, R.tcQl, R.tcqn2, st);
@@ -2233,6 +2297,28 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     d.QS = qb.S;
     d.QSoff = qb.Soff;
     d.rel = t.dim > 0 ? fp32_rel_bound(t.dim) : 0.f;
+    d.qg = nullptr;
+    d.qgq = nullptr;
+    DBuf<uint8_t> qgq;
+    if (t.dim == 0 && t.n > 0 && nq > 0) {   // strings: 3-gram counts of the rows (once) and the queries
+        R.clk.begin(GTS_STAGE_OTHER, 2);
+        {
+            std::lock_guard<std::mutex> g(ix->prep_mu);   // concurrent queries build it once
+            if (!t.qg_ready) {
+                t.qg.alloc(t.n * kQgBuckets, st);
+                k_qgram_hist<<<nblocks(t.n, 256), 256, 0, st>>>(t.S.get(), t.Soff.get(), t.n, t.qg.get());
+                GTS_CUDA(cudaStreamSynchronize(st));
+                t.qg.persist();
+                t.qg_ready = true;
+            }
+        }
+        qgq.alloc(nq * kQgBuckets, st);
+        k_qgram_hist<<<nblocks(nq, 256), 256, 0, st>>>(qb.S, qb.Soff, nq, qgq.get());
+        R.clk.end();
+        check_launch("3-gram counts");
+        d.qg = t.qg.get();
+        d.qgq = qgq.get();
+    }
     d.epsc = t.dim > 0 ? 4.f * d.rel : 0.f;
     DBuf<int64_t> qseq(nq, st);
     R.clk.begin(GTS_STAGE_OTHER);

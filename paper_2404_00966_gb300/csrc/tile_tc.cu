@@ -717,6 +717,9 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
     c.map_h = make_row_map(c.Xh.get(), t.n, c.dim_p);
     c.map_l = make_row_map(c.Xl.get(), t.n, c.dim_p);
     GTS_CUDA(cudaStreamSynchronize(st));
+    c.Xh.persist();
+    c.Xl.persist();
+    c.xn2.persist();
     c.ready = true;
 }
 
