@@ -395,7 +395,7 @@ def run_config(args):
         nq = wl.nq
 
         def step(timing=False):
-            r = ix.range(queries, radii, result_on_device=True, timing=timing)
+            r = ix.range(queries, radii, precision=prec, result_on_device=True, timing=timing)
             st = r.stats
             r.free()
             return st

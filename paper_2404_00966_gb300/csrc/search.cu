@@ -28,6 +28,7 @@
 #include "metric.cuh"
 #include "pivot_dense.cuh"
 #include "tile_l1.cuh"
+#include "tile_str.cuh"
 #include "tile_tc.cuh"
 
 namespace gts {
@@ -1519,6 +1520,7 @@ struct Runner {
     StageClock clk;
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
     bool use_l1 = false;   // FP32 CUDA-core tiles at the last level (L1)
+    bool use_qg = false;   // 3-gram filtering tiles at the last level (edit distance)
     Tuning tu;             // launch parameters (a copy of the index's)
     // dense query-to-pivot matrices per level (tile paths): state 0 undecided, 1 ready, 2 not used
     std::vector<DBuf<float>> dense;
@@ -1738,6 +1740,10 @@ struct Runner {
             clk.end();
             if (use_tc) {
                 tc_leaf(L, e0, e1, mask);
+                return;
+            }
+            if (use_qg) {
+                str_leaf(L, e0, e1, mask);
                 return;
             }
             DBuf<int32_t> cnt(E, st);
@@ -2002,6 +2008,55 @@ struct Runner {
         tc_finish(tq, rg);
     }
 
+    // Last level for strings on the 3-gram tiles: regroup the entries by
+    // node, keep the pairs the 3-gram count bound does not exclude, then run
+    // the exact bit-parallel DP on those (query-major for its match masks).
+    void str_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask) {
+        TcQuery tq;
+        tq.E = e1 - e0;
+        tq.nq = qb.nq;
+        tq.eq = L.q.get() + e0;
+        tq.enode = L.node.get() + e0;
+        tq.path = L.path.get() + e0 * h;
+        tq.emask = mask.get();
+        tq.qseq = d.qseq;
+        tq.thr = thr.get();
+        tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
+        TcRegroup rg;
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_regroup(ix->tree, tq, rg, st, nullptr, false);
+        clk.end();
+        st_tiles += rg.n_items;
+        st_tile_entries += rg.n_entries;
+        st_tile_pairs += rg.n_pairs;
+        StrQuery sq;
+        sq.qg = d.qg;
+        sq.qgq = d.qgq;
+        sq.any_deleted = tq.any_deleted;
+        const int64_t per_q = ix->tc_pairs_hint[knn ? 1 : 0].load();
+        const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
+        DBuf<int32_t> oq, orow;
+        int nl = 0;
+        clk.begin(GTS_STAGE_TILE);
+        const int64_t C = qgram_run(ix->tree, sq, rg, oq, orow, hint, &nl, st);
+        clk.end();
+        if (rg.n_items > 0 && qb.nq > 0)
+            ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
+        ++st_groups;
+        if (C == 0) return;
+        DBuf<int32_t> q2(C, st), r2(C, st);
+        int qbits = 1;
+        while (((int64_t)1 << qbits) < qb.nq) ++qbits;
+        size_t tb = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0, qbits, st);
+        DBuf<uint8_t> tmp(tb ? tb : 1, st);
+        clk.begin(GTS_STAGE_OTHER);
+        GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0, qbits,
+                                                 st));
+        clk.end();
+        verify_and_collect(q2, r2, C);
+    }
+
     // Last level on the L1 tiles: regroup the entries by node, run the tiles
     // (leaf mask, visibility and FP32 distance with its error band), then
     // decide the kept pairs (range) or merge them into the answer (kNN).  kNN
@@ -2255,6 +2310,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.max_blocks = (unsigned)(sms > 0 ? sms : 1) * 8u;
     }
     if (precision == GTS_PREC_BF16 && l1_tiles_supported(t, qb.Q)) R.use_l1 = true;
+    if (precision == GTS_PREC_BF16 && t.dim == 0 && t.n > 0 && t.n < ((int64_t)1 << 31)) R.use_qg = true;
     if (precision == GTS_PREC_BF16 && tc_supported(t)) {
         {
             std::lock_guard<std::mutex> g(ix->prep_mu);   // concurrent queries build it once

@@ -60,11 +60,12 @@ def test_dna_full_size(env):
     wl = synth.dna_like()
     objs = (torch.from_numpy(wl.objects.data).cuda(), torch.from_numpy(wl.objects.offsets).cuda())
     ix = g.Index.build(objs, "edit", fanout=wl.fanout, root_pivot=0)
-    res = ix.range((torch.from_numpy(wl.queries.data).cuda(), torch.from_numpy(wl.queries.offsets).cuda()),
-                   torch.from_numpy(wl.radii).cuda())
     idx = np.random.default_rng(102).choice(wl.nq, 12, replace=False)
     want = oracle.range_query("edit", wl.objects, wl.queries.take(idx), wl.radii[idx])
-    _check(res, idx, want, "edit")
+    for prec in ("bf16", "fp32"):   # the 3-gram tiles, then the plain path
+        res = ix.range((torch.from_numpy(wl.queries.data).cuda(), torch.from_numpy(wl.queries.offsets).cuda()),
+                       torch.from_numpy(wl.radii).cuda(), precision=prec)
+        _check(res, idx, want, "edit")
     ix.close()
 
 

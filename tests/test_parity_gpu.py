@@ -93,13 +93,16 @@ def test_vector_range_and_knn(gts, metric, dup):
     ix.close()
 
 
-def test_edit_range_and_knn(gts):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])   # bf16: the 3-gram filtering tiles
+def test_edit_range_and_knn(gts, prec):
     S, Qs = str_case(4000, 80, seed=5)
     ix = gts.Index.build(S, "edit", n_pivots=4, fanout=8, root_pivot=1)
     radii = np.random.default_rng(6).integers(0, 5, size=80).astype(np.float32) + 0.7
-    assert_same(ix.range(Qs, radii), oracle.range_query("edit", S, Qs, radii), "edit", "range")
+    r = ix.range(Qs, radii, precision=prec)
+    assert (r.stats["tiles"] > 0) == (prec == "bf16")
+    assert_same(r, oracle.range_query("edit", S, Qs, radii), "edit", "range")
     for k in (1, 5, 40):
-        assert_same(ix.knn(Qs, k), oracle.knn_query("edit", S, Qs, k), "edit", f"knn k={k}")
+        assert_same(ix.knn(Qs, k, precision=prec), oracle.knn_query("edit", S, Qs, k), "edit", f"knn k={k}")
     ix.close()
 
 
@@ -114,8 +117,11 @@ def test_edit_long_strings_multiword(gts):
                             for _ in range(30)])
     ix = gts.Index.build(S, "edit", fanout=6, root_pivot=0)
     radii = np.full(30, 10.0, np.float32)
-    assert_same(ix.range(Qs, radii), oracle.range_query("edit", S, Qs, radii), "edit", "long range")
-    assert_same(ix.knn(Qs, 12), oracle.knn_query("edit", S, Qs, 12), "edit", "long knn")
+    want_r = oracle.range_query("edit", S, Qs, radii)
+    want_k = oracle.knn_query("edit", S, Qs, 12)
+    for prec in ("fp32", "bf16"):
+        assert_same(ix.range(Qs, radii, precision=prec), want_r, "edit", f"long range {prec}")
+        assert_same(ix.knn(Qs, 12, precision=prec), want_k, "edit", f"long knn {prec}")
     ix.close()
 
 
@@ -123,8 +129,9 @@ def test_words_like_full_size(gts):
     """The 10,000-string / 256-query / radius-2 workload, every query checked."""
     wl = words_like()
     ix = gts.Index.build(wl.objects, "edit", n_pivots=wl.n_pivots, fanout=wl.fanout, root_pivot=0)
-    assert_same(ix.range(wl.queries, wl.radii), oracle.range_query("edit", wl.objects, wl.queries, wl.radii),
-                "edit", "words")
+    want = oracle.range_query("edit", wl.objects, wl.queries, wl.radii)
+    for prec in ("fp32", "bf16"):
+        assert_same(ix.range(wl.queries, wl.radii, precision=prec), want, "edit", f"words {prec}")
     ix.close()
 
 
@@ -450,10 +457,11 @@ def test_updates_vectors_l1(gts, precision):
     _replay(gts, "l1", X, list(pool), seed=26, cache_limit=7, precision=precision)
 
 
-def test_updates_strings(gts):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_updates_strings(gts, prec):
     S, _ = str_case(1200, 1, seed=17, lmin=2, lmax=10)
     P, _ = str_case(400, 1, seed=18, lmin=2, lmax=10)
-    _replay(gts, "edit", S, [P.get(i) for i in range(P.n)], seed=19, cache_limit=9)
+    _replay(gts, "edit", S, [P.get(i) for i in range(P.n)], seed=19, cache_limit=9, precision=prec)
 
 
 def test_query_sequence_numbers_span_updates(gts):
