@@ -231,6 +231,8 @@ gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *
  *              between (default 3).
  *  probe_rows: kNN probe, object rows evaluated before the descent to bound
  *              the k-th distance, 0 .. 4096 (default 1024).
+ *  tc_queries: BF16 tensor-core tiles for dim <= 128, queries per chunk:
+ *              128 (two staging slots, default) or 96 (three slots).
  *  tuned:      output only: 1 once gts_autotune has run on the index. */
 typedef struct {
     int32_t l1_queries;
@@ -238,7 +240,8 @@ typedef struct {
     int32_t knn_phases;
     int32_t probe_rows;
     int32_t tuned;
-    int32_t reserved_[3];
+    int32_t tc_queries;
+    int32_t reserved_[2];
 } gts_tuning;
 
 /* Read / replace the index's tuning.  A query copies it when it starts, so a

@@ -75,10 +75,11 @@ class _Info(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("l1_queries", ctypes.c_int32), ("l1_packed", ctypes.c_int32), ("knn_phases", ctypes.c_int32),
-                ("probe_rows", ctypes.c_int32), ("tuned", ctypes.c_int32), ("reserved_", ctypes.c_int32 * 3)]
+                ("probe_rows", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tc_queries", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32 * 2)]
 
 
-TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows"]
+TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows", "tc_queries"]
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",

@@ -469,6 +469,7 @@ void check_tuning(const gts_tuning *t) {
     GTS_REQUIRE(t->l1_packed == 0 || t->l1_packed == 1, GTS_EINVAL, "l1_packed must be 0 or 1");
     GTS_REQUIRE(t->knn_phases >= 1 && t->knn_phases <= 3, GTS_EINVAL, "knn_phases must be in 1 .. 3");
     GTS_REQUIRE(t->probe_rows >= 0 && t->probe_rows <= 4096, GTS_EINVAL, "probe_rows must be in 0 .. 4096");
+    GTS_REQUIRE(t->tc_queries == 96 || t->tc_queries == 128, GTS_EINVAL, "tc_queries must be 96 or 128");
 }
 
 gts_tuning to_c(const Tuning &t) {
@@ -478,6 +479,7 @@ gts_tuning to_c(const Tuning &t) {
     o.l1_packed = t.l1_packed;
     o.knn_phases = t.knn_phases;
     o.probe_rows = t.probe_rows;
+    o.tc_queries = t.tc_queries;
     o.tuned = t.tuned;
     return o;
 }
@@ -488,6 +490,7 @@ Tuning from_c(const gts_tuning &o, int tuned) {
     t.l1_packed = o.l1_packed;
     t.knn_phases = o.knn_phases;
     t.probe_rows = o.probe_rows;
+    t.tc_queries = o.tc_queries;
     t.tuned = tuned;
     return t;
 }
@@ -802,6 +805,7 @@ gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *
         if (knn) space.push_back({&gts_tuning::knn_phases, {1, 2, 3}});
     }
     if (knn && ix->metric != GTS_EDIT) space.push_back({&gts_tuning::probe_rows, {0, 256, 1024, 4096}});
+    if (ix->metric == GTS_L2 && ix->dim <= 128) space.push_back({&gts_tuning::tc_queries, {128, 96}});
     double best_ms = 0.0;
     s = time_it(best, best_ms);   // the first run also warms every lazily built structure
     if (s == GTS_OK) s = time_it(best, best_ms);

@@ -178,6 +178,7 @@ struct Tuning {
     int l1_packed = 1;      // L1 tiles: packed f32x2 subtraction
     int knn_phases = 3;     // L1 tile kNN: phases (1..3)
     int probe_rows = 1024;  // kNN probe: rows evaluated before the descent (0..4096)
+    int tc_queries = 128;   // tensor-core tiles (dim <= 128): queries per chunk, 128 (2 slots) or 96 (3 slots)
     int tuned = 0;
 };
 

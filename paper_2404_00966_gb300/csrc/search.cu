@@ -1861,7 +1861,7 @@ struct Runner {
     // quarter of its (query, node) pairs, and its matrices fit a quarter of
     // the budget.
     bool dense_last_ok(int64_t total) {
-        // (window chunks of 128 queries: the tensor-core tiles with dim_p <= 128)
+        // (window chunks: the tensor-core tiles with dim_p <= 128)
         if (!whole_batch || d.dim == 0 || h < 2 || qb.nq == 0 || qb.nq > 2000000 || ix->tree.tc.dim_p > 128)
             return false;
         if ((int)dense_state.size() < h) return false;
@@ -1945,6 +1945,7 @@ struct Runner {
         tq.Qh = (const __nv_bfloat16 *)tcQh.get();
         tq.Ql = (const __nv_bfloat16 *)tcQl.get();
         tq.qn2 = tcqn2.get();
+        tq.chunk = tu.tc_queries;
         tc_bound_coeffs(ix->tree.tc.dim_p, tq.cE1, tq.cE2);
         tq.Q = d.Q;
         tq.qseq = d.qseq;

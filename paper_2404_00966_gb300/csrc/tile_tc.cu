@@ -45,11 +45,15 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node block
-// MMA N (queries per chunk) is a template parameter NQ: 128 up to 128
-// columns, 64 up to 192, 32 up to 256, so that the node block (A, hi and lo)
-// and two chunk buffers (B, hi and lo) fit in shared memory.  TMEM holds two
-// FP32 accumulators of 128 lanes x NQ columns.
-inline int nq_for(int dim_p) { return dim_p <= 128 ? 128 : dim_p <= 192 ? 64 : 32; }
+// MMA N (queries per chunk) NQ and the number S of staging slots are template
+// parameters: up to 128 columns, 2 slots of 128 queries or 3 of 96; up to 192
+// columns, 2 slots of 64; up to 256, 2 slots of 32 -- so that the node block
+// (A, hi and lo) and S chunk buffers (B, hi and lo) fit in shared memory.
+// TMEM holds S FP32 accumulators of 128 lanes x NQ columns.
+// (up to 128 columns the tuning chooses: 128 x 2 by default, or 96 x 3)
+inline int nq_for(int dim_p, int pref) { return dim_p <= 128 ? (pref == 96 ? 96 : 128) : dim_p <= 192 ? 64 : 32; }
+inline int slots_for(int nq) { return nq == 96 ? 3 : 2; }
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -63,12 +67,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// bf16 rows [rows, dim_p], box 64 columns x 128 rows, 128-byte swizzle
-CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p) {
+// bf16 rows [rows, dim_p], box 64 columns x box_rows rows, 128-byte swizzle
+CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p, int box_rows = kRows) {
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)dim_p, (cuuint64_t)(rows > 0 ? rows : 1)};
     cuuint64_t strides[1] = {(cuuint64_t)dim_p * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)kRows};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -163,32 +167,33 @@ __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cn
 // slot g % 2 once the epilogue has released the chunk g - 2 held there; one
 // thread issues the MMAs of chunk g into accumulator g % 2 when its operands
 // have landed; the epilogue warps test chunk g when its MMAs are done and
-// release the slot.  mbarriers carry every hand-off (parity (g / 2) & 1 for
-// the g-th use of a slot), so no block-wide barrier runs per chunk.
-template <int NQ>
+// release the slot.  mbarriers carry every hand-off (chunk g uses slot g % S;
+// its barriers' phase parity is (g / S) & 1), so no block-wide barrier runs
+// per chunk.
+template <int NQ, int S>
 __global__ void __launch_bounds__(kThreadsWS, 1)
     k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l,
                  const __grid_constant__ CUtensorMap map_qh, const __grid_constant__ CUtensorMap map_ql, TileArgs a) {
     constexpr int kNQ = NQ;
-    constexpr int kTmemCols = 2 * NQ;
+    constexpr int kTmemCols = pow2_at_least(S * NQ);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int panels = a.dim_p / 64;
     const int apanel = kRows * 128, bpanel = kNQ * 128;
     uint8_t *sAh = smem;                                    // panels x 128 rows x 128 B
     uint8_t *sAl = sAh + panels * apanel;
-    uint8_t *sB = sAl + panels * apanel;                    // 2 slots x (hi, lo) x panels x kNQ x 128 B
+    uint8_t *sB = sAl + panels * apanel;                    // S slots x (hi, lo) x panels x kNQ x 128 B
     const int bbuf = 2 * panels * bpanel;                   // bytes of one slot
-    uint8_t *mbase = sB + 2 * bbuf;
+    uint8_t *mbase = sB + S * bbuf;
     const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + (int)sizeof(ChunkDesc);
     auto mrec = [&](int sl) { return (TileRec *)(mbase + sl * mbytes); };
     auto mpath = [&](int sl) { return (float *)(mbase + sl * mbytes + kNQ * sizeof(TileRec)); };
     auto mdesc = [&](int sl) {
         return (ChunkDesc *)(mbase + sl * mbytes + kNQ * sizeof(TileRec) + kNQ * a.hp * 4);
     };
-    uint64_t *bars = (uint64_t *)(mbase + 2 * mbytes);     // full[2], mma_done[2], epi_done[2], a_full
-    uint64_t *full = bars, *mma_done = bars + 2, *epi_done = bars + 4, *a_full = bars + 6;
-    uint32_t *tslot = (uint32_t *)(bars + 7);
+    uint64_t *bars = (uint64_t *)(mbase + S * mbytes);     // full[S], mma_done[S], epi_done[S], a_full
+    uint64_t *full = bars, *mma_done = bars + S, *epi_done = bars + 2 * S, *a_full = bars + 3 * S;
+    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 1);
     int *sitem = (int *)(tslot + 1);
     volatile int *sabort = sitem + 1;
     int *a_issued = sitem + 2;     // A loads issued / consumed (for the abort path)
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < S; ++i) {
             tc::mbar_init(&full[i], kProducers);
             tc::mbar_init(&mma_done[i], 1);
             tc::mbar_init(&epi_done[i], kEpiWarps);
@@ -239,7 +244,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 size = a.nsize[gnode];
                 if (ptid == 0) {
                     // the previous block's MMAs are done once its last epilogue is
-                    if (last_g >= 0 && !tc::mbar_wait(&epi_done[last_g & 1], (uint32_t)((last_g >> 1) & 1))) fail(3);
+                    if (last_g >= 0 && !tc::mbar_wait(&epi_done[last_g % S], (uint32_t)((last_g / S) & 1))) fail(3);
                     tc::mbar_expect_tx(a_full, (uint32_t)(2 * panels * apanel));
                     for (int pnl = 0; pnl < panels; ++pnl) {
                         const int y = pos + (it.w & (kWindowItem - 1)) * kRows;
@@ -261,9 +266,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 TileRec drec;   // dense last level: this column's record, loaded before the slot wait
                 drec.mask = 0;
                 if (window) {
-                    // this thread's column: query c * 128 + ptid
+                    // this thread's column: query c * NQ + ptid (threads past NQ have none)
                     const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
-                    if (wi < a.nw) word = a.bits[(int64_t)it.x * a.nw + wi];
+                    if (ptid < kNQ && wi < a.nw) word = a.bits[(int64_t)it.x * a.nw + wi];
                     if (a.dmask && ((word >> (ptid & 31)) & 1u)) {
                         const int64_t q = (int64_t)c * kNQ + ptid;
                         drec.mask = a.dmask[(int64_t)it.x * a.nq + q];
@@ -279,8 +284,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     tc::named_sync(1, kProducers);
                     if (!nonempty) continue;
                 }
-                const int sl = g & 1;
-                if (g >= 2 && !tc::mbar_wait(&epi_done[sl], ((g - 2) >> 1) & 1)) fail(4);
+                const int sl = g % S;
+                if (g >= S && !tc::mbar_wait(&epi_done[sl], ((g - S) / S) & 1)) fail(4);
                 int cnt;
                 if (stop) {
                     cnt = 0;
@@ -295,9 +300,11 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                         }
                     }
                     // column ptid: its record and path distances, or an empty record
-                    TileRec *mr = mrec(sl) + ptid;
-                    float *mp = mpath(sl) + ptid * a.hp;
-                    if (a.dmask) {
+                    TileRec *mr = mrec(sl) + (ptid < kNQ ? ptid : 0);
+                    float *mp = mpath(sl) + (ptid < kNQ ? ptid : 0) * a.hp;
+                    if (ptid >= kNQ) {
+                        // no column
+                    } else if (a.dmask) {
                         // dense last level: the record from the per-query arrays
                         TileRec r = drec;
                         r.q = (int32_t)((int64_t)c * kNQ + ptid);
@@ -348,8 +355,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             uint32_t a_par = 0;
             int64_t last_issued = -1;
             for (uint32_t g = 0;; ++g) {
-                const int sl = g & 1;
-                if (!tc::mbar_wait(&full[sl], (g >> 1) & 1)) {
+                const int sl = g % S;
+                if (!tc::mbar_wait(&full[sl], (g / S) & 1)) {
                     fail(5);
                     break;
                 }
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             }
             // on an early exit, let issued MMAs finish before TMEM is released
             if (last_issued >= 0 && *sabort)
-                tc::mbar_wait(&mma_done[last_issued & 1], (uint32_t)((last_issued >> 1) & 1));
+                tc::mbar_wait(&mma_done[last_issued % S], (uint32_t)((last_issued / S) & 1));
         }
     } else if (warp < kEpiWarps) {
         // ================================================= epilogue warps
@@ -392,8 +399,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         uint64_t rowbit = 0, wmask = 0;
         float xn = 0.f, gx = 0.f;
         for (uint32_t g = 0;; ++g) {
-            const int sl = g & 1;
-            if (!tc::mbar_wait(&full[sl], (g >> 1) & 1)) {
+            const int sl = g % S;
+            if (!tc::mbar_wait(&full[sl], (g / S) & 1)) {
                 fail(6);
                 break;
             }
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
                 gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
             }
-            if (!tc::mbar_wait(&mma_done[sl], (g >> 1) & 1)) {
+            if (!tc::mbar_wait(&mma_done[sl], (g / S) & 1)) {
                 fail(2);
                 break;
             }
@@ -683,12 +690,12 @@ inline unsigned nblk(int64_t n, int per = 256) {
     return (unsigned)b;
 }
 
-size_t tile_smem_bytes(int dim_p, int h, int kNQ) {
+size_t tile_smem_bytes(int dim_p, int h, int kNQ, int S) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
-    b += (size_t)2 * panels * kRows * 128 + (size_t)4 * panels * kNQ * 128;
-    b += 2 * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + 32);
-    b += 7 * 8 + 4 + 4 * 4 + 16 + (size_t)kNQ * 4;
+    b += (size_t)2 * panels * kRows * 128 + (size_t)S * 2 * panels * kNQ * 128;
+    b += S * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + 32);
+    b += (3 * S + 1) * 8 + 4 + 4 * 4 + 16 + (size_t)kNQ * 4;
     return b;
 }
 
@@ -851,9 +858,18 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int dev = 0, sms = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int nq_chunk = nq_for(c.dim_p);
-    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk);
-    auto kern = nq_chunk == 128 ? k_tile_l2_tc<128> : nq_chunk == 64 ? k_tile_l2_tc<64> : k_tile_l2_tc<32>;
+    int nq_chunk = nq_for(c.dim_p, tq.chunk), slots = slots_for(nq_chunk);
+    int smem_optin = 0;
+    GTS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (nq_chunk == 96 && tile_smem_bytes(c.dim_p, t.h, 96, 3) > (size_t)smem_optin) {
+        nq_chunk = 128;   // deep trees: the path distances of three slots do not fit, two slots of 128
+        slots = 2;
+    }
+    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk, slots);
+    auto kern = nq_chunk == 96    ? k_tile_l2_tc<96, 3>
+                : nq_chunk == 128 ? k_tile_l2_tc<128, 2>
+                : nq_chunk == 64  ? k_tile_l2_tc<64, 2>
+                                  : k_tile_l2_tc<32, 2>;
     GTS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
     // TMEM columns, and registers
@@ -865,12 +881,12 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int per_sm = (int)(smem_sm / (smem + 1024));
     const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreadsWS;
     if (regs_cta > 0 && per_sm > regs_sm / regs_cta) per_sm = regs_sm / regs_cta;
-    if (per_sm > 512 / (2 * nq_chunk)) per_sm = 512 / (2 * nq_chunk);   // TMEM columns
+    if (per_sm > 512 / pow2_at_least(slots * nq_chunk)) per_sm = 512 / pow2_at_least(slots * nq_chunk);   // TMEM
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     // the batch's split query rows, for window-mode chunks (TMA, 128 rows)
-    const CUtensorMap map_qh = make_row_map(tq.Qh, tq.nq, c.dim_p);
-    const CUtensorMap map_ql = make_row_map(tq.Ql, tq.nq, c.dim_p);
+    const CUtensorMap map_qh = make_row_map(tq.Qh, tq.nq, c.dim_p, nq_chunk);
+    const CUtensorMap map_ql = make_row_map(tq.Ql, tq.nq, c.dim_p, nq_chunk);
     DBuf<int> counter(1, st), status(1, st);
     DBuf<unsigned long long> count(1, st);
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;

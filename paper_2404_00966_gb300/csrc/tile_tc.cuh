@@ -60,6 +60,7 @@ struct TcQuery {
     const __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;   // split bf16 queries [nq, dim_p]
     const float *qn2 = nullptr;                          // |q|^2 (null: not needed, records get 0)
     float cE1 = 0.f, cE2 = 0.f;                          // bf16 error-bound coefficients (tc_bound_coeffs)
+    int chunk = 128;                                     // tensor-core tiles up to 128 columns: 128 or 96 queries
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;

@@ -316,22 +316,44 @@ def test_every_tuning_gives_the_same_answers(gts, metric, prec):
         for packed in (0, 1):
             for phases in (1, 2, 3):
                 for probe in (0, 256, 4096):
-                    if metric != "l1" and (lq, packed, phases) != (128, 1, 3):
+                    if metric != "l1" and (lq, packed, phases) != (128, 1, 3) and (lq, packed, phases, probe) != (
+                            64, 0, 1, 256):
                         continue
-                    ix.set_tuning(l1_queries=lq, l1_packed=packed, knn_phases=phases, probe_rows=probe)
+                    # the (64, 0, 1, 256) setting of L2 also takes the 96-query, 3-slot tensor-core tiles
+                    tcq = 96 if (lq, packed, phases, probe) == (64, 0, 1, 256) else 128
+                    ix.set_tuning(l1_queries=lq, l1_packed=packed, knn_phases=phases, probe_rows=probe,
+                                  tc_queries=tcq)
                     tag = f"{lq}/{packed}/{phases}/{probe}"
                     assert_same(ix.knn(Q, ks, precision=prec), want, metric, f"knn tuning {tag}")
                     if probe == 0:
                         assert_same(ix.range(Q, radii, precision=prec), want_r, metric, f"range tuning {tag}")
     with pytest.raises(gts.GTSError):
         ix.set_tuning(knn_phases=4)
+    with pytest.raises(gts.GTSError):
+        ix.set_tuning(tc_queries=100)
     t = ix.autotune(Q, k=ks, precision=prec, reps=1)
     assert t["tuned"] == 1 and t["l1_queries"] in (64, 128) and 0 <= t["probe_rows"] <= 4096
+    assert t["tc_queries"] in (96, 128)
     assert ix.get_tuning() == t
     assert_same(ix.knn(Q, ks, precision=prec), want, metric, "after autotune")
     t2 = ix.autotune(Q, radii=radii, precision=prec, reps=1)
     assert t2["tuned"] == 1
     assert_same(ix.range(Q, radii, precision=prec), want_r, metric, "after range autotune")
+    ix.close()
+
+
+def test_bf16_tiles_deep_tree(gts):
+    """Ten pivot levels: the tile's per-query path distances do not fit three
+    staging slots, so the kernel runs two slots of 128 queries."""
+    X, Q = vec_case(6007, 64, 160, seed=81)
+    ix = gts.Index.build(X, "l2", n_pivots=10, fanout=3, root_pivot=0)
+    assert ix.info()["h"] == 10
+    ix.set_tuning(tc_queries=96)   # asks for three slots of 96; the kernel falls back to two of 128
+    for k in (1, 7):
+        assert_same(ix.knn(Q, k, precision="bf16"), oracle.knn_query("l2", X, Q, k), "l2", f"deep tree knn k={k}")
+    d = oracle.distances_to("l2", X[:300], Q[1])
+    radii = np.linspace(0.0, 0.8, 160).astype(np.float32) * np.float32(np.median(d))
+    assert_same(ix.range(Q, radii, precision="bf16"), oracle.range_query("l2", X, Q, radii), "l2", "deep tree range")
     ix.close()
 
 
