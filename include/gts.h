@@ -292,6 +292,15 @@ gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gt
                                 const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
                                 void *stream);
 
+/* The same scan without the final stream synchronisation: the call only
+ * enqueues its two kernels on `stream`, so it can be recorded into a CUDA
+ * graph (stream capture) and replayed; results are ready when the stream's
+ * work up to this point has finished.  Argument checks and errors as above
+ * (an argument error enqueues nothing). */
+gts_status gts_knn_scan_noalloc_async(const float *objects, int64_t n, int32_t dim, gts_metric metric,
+                                      const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
+                                      void *stream);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching over one index (no counterpart in the paper; the paper
  * answers one batch at a time).  Requests are submitted one by one; worker

@@ -83,7 +83,8 @@ TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows", "tc_quer
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
-           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc", "gts_serve_start",
+           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc",
+           "gts_knn_scan_noalloc_async", "gts_serve_start",
            "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop", "gts_get_tuning",
            "gts_set_tuning", "gts_autotune"]
 
@@ -121,8 +122,9 @@ def lib(path: Optional[str] = None):
     for f in ["gts_serve_start", "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop",
               "gts_get_tuning", "gts_set_tuning", "gts_autotune"]:
         getattr(L, f).restype = ctypes.c_int
-    L.gts_knn_scan_noalloc.argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
-    L.gts_knn_scan_noalloc.restype = ctypes.c_int
+    for f in ["gts_knn_scan_noalloc", "gts_knn_scan_noalloc_async"]:
+        getattr(L, f).argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
+        getattr(L, f).restype = ctypes.c_int
     L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
     L.gts_selftest_tc.restype = ctypes.c_int
     L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]

@@ -147,7 +147,7 @@ ScanPair *scratch_ptr(int dev) {
 }  // namespace
 
 void knn_scan_noalloc(const float *X, int64_t n, int dim, int metric, const float *Q, int64_t nq, int k,
-                      int64_t *ids, float *dist, cudaStream_t st) {
+                      int64_t *ids, float *dist, cudaStream_t st, bool sync) {
     GTS_REQUIRE(metric == GTS_L1 || metric == GTS_L2, GTS_EINVAL, "metric must be GTS_L1 or GTS_L2");
     GTS_REQUIRE(k >= 1 && k <= kScanMaxK, GTS_EINVAL, "k must be in 1 .. 32");
     GTS_REQUIRE(dim >= 1, GTS_EINVAL, "dim must be >= 1");
@@ -172,16 +172,15 @@ void knn_scan_noalloc(const float *X, int64_t n, int dim, int metric, const floa
     check_launch("scan partial");
     k_scan_merge<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scratch, nq, k, (int)slices, metric == GTS_L2, ids, dist);
     check_launch("scan merge");
-    GTS_CUDA(cudaStreamSynchronize(st));
+    if (sync) GTS_CUDA(cudaStreamSynchronize(st));
 }
 
 }  // namespace gts
 
-extern "C" gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gts_metric metric,
-                                           const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
-                                           void *stream) {
+static gts_status scan_entry(const float *objects, int64_t n, int32_t dim, gts_metric metric, const float *queries,
+                             int64_t nq, int32_t k, int64_t *ids, float *dist, void *stream, bool sync) {
     try {
-        gts::knn_scan_noalloc(objects, n, dim, (int)metric, queries, nq, k, ids, dist, (cudaStream_t)stream);
+        gts::knn_scan_noalloc(objects, n, dim, (int)metric, queries, nq, k, ids, dist, (cudaStream_t)stream, sync);
         return GTS_OK;
     } catch (const gts::Error &e) {
         gts::set_last_error(e.what());
@@ -193,4 +192,16 @@ extern "C" gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int3
         gts::set_last_error("unknown internal error");
         return GTS_ECUDA;
     }
+}
+
+extern "C" gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gts_metric metric,
+                                           const float *queries, int64_t nq, int32_t k, int64_t *ids, float *dist,
+                                           void *stream) {
+    return scan_entry(objects, n, dim, metric, queries, nq, k, ids, dist, stream, true);
+}
+
+extern "C" gts_status gts_knn_scan_noalloc_async(const float *objects, int64_t n, int32_t dim, gts_metric metric,
+                                                 const float *queries, int64_t nq, int32_t k, int64_t *ids,
+                                                 float *dist, void *stream) {
+    return scan_entry(objects, n, dim, metric, queries, nq, k, ids, dist, stream, false);
 }

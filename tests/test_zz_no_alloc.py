@@ -76,3 +76,39 @@ def test_noalloc_scan_fewer_objects_than_k_and_size_limit(env):
     st = g.lib().gts_knn_scan_noalloc(ctypes.c_void_p(Xd.data_ptr()), 5, 8, 2, ctypes.c_void_p(Qd.data_ptr()),
                                       (1 << 20) // 8 + 1, 8, ctypes.c_void_p(0), ctypes.c_void_p(0), None)
     assert st == 1 and b"scratch" in g.lib().gts_last_error()
+
+
+def test_noalloc_scan_replayed_from_a_cuda_graph(env):
+    """The asynchronous entry enqueues only its kernels, so a stream capture
+    records it into a CUDA graph; replays with new query data in the same
+    device buffer answer exactly."""
+    g, torch = env
+    X, Q1 = small_vectors(6007, 48, 64, seed=94)
+    _, Q2 = small_vectors(6007, 48, 64, seed=95)
+    Xd = torch.from_numpy(X).cuda()
+    Qbuf = torch.from_numpy(Q1).cuda()
+    k = 9
+    ids = torch.empty(64 * k, dtype=torch.int64, device="cuda")
+    dist = torch.empty(64 * k, dtype=torch.float32, device="cuda")
+    _scan(g, torch, Xd, Qbuf, 2, k)   # the first call on the device looks up the scratch array, outside capture
+    lib = g.lib()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        st = lib.gts_knn_scan_noalloc_async(ctypes.c_void_p(Xd.data_ptr()), Xd.shape[0], 48, 2,
+                                            ctypes.c_void_p(Qbuf.data_ptr()), 64, k, ctypes.c_void_p(ids.data_ptr()),
+                                            ctypes.c_void_p(dist.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    assert st == 0, lib.gts_last_error().decode()
+    ix = g.Index.build(Xd, "l2", fanout=9, root_pivot=1)
+    for Q in (Q1, Q2):
+        Qbuf.copy_(torch.from_numpy(Q))
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        gi, gd = ids.cpu().numpy().reshape(64, k), dist.cpu().numpy().reshape(64, k)
+        ref = ix.knn(Qbuf, k)
+        for i in range(64):
+            rid, rdist = ref.query(i)
+            assert np.array_equal(gi[i], rid), f"query {i}: ids differ"
+            assert np.allclose(gd[i], rdist, rtol=RTOL, atol=0), f"query {i}: distances differ"
+    ix.close()
