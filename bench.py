@@ -392,7 +392,11 @@ def run_config(args):
     prec = args.precision
     extra = {}
     if wl_name in ("words", "dna"):
-        wl = synth.words_like() if wl_name == "words" else synth.dna_like()
+        if wl_name == "words":
+            wl = synth.words_like()
+        else:   # --scale < 1: fewer seeds and queries (profiling only)
+            wl = synth.dna_like() if args.scale >= 1.0 else synth.dna_like(
+                n_seeds=max(100, int(10_000 * args.scale)), nq=max(100, int(20_000 * args.scale)))
         objs = _dev_strings(wl.objects)
         queries = _dev_strings(wl.queries)
         radii = torch.from_numpy(wl.radii).cuda()
