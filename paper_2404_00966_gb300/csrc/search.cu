@@ -1974,21 +1974,9 @@ struct Runner {
             ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
         ++st_groups;
         if (C == 0) return;
-        if (knn) {   // the selection wants query-major order
-            DBuf<int32_t> q2(C, st), r2(C, st);
-            int qbits = 1;
-            while (((int64_t)1 << qbits) < qb.nq) ++qbits;
-            size_t tb = 0;
-            cub::DeviceRadixSort::SortPairs(nullptr, tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0, qbits, st);
-            DBuf<uint8_t> tmp(tb ? tb : 1, st);
-            clk.begin(GTS_STAGE_OTHER);
-            GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, oq.get(), q2.get(), orow.get(), r2.get(), C, 0,
-                                                     qbits, st));
-            clk.end();
-            verify_and_collect(q2, r2, C);
-        } else {
-            verify_and_collect(oq, orow, C);
-        }
+        // verified in the tiles' node-major order (consecutive pairs share
+        // their object row); kNN pairs kept are put in query order afterwards
+        verify_and_collect(oq, orow, C, /*query_major=*/false);
     }
 
     void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
@@ -2169,7 +2157,10 @@ struct Runner {
 #undef GTS_VV
     }
 
-    void verify_and_collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, int64_t C) {
+    // query_major: the pairs come sorted by query (the kNN merge needs that
+    // order; otherwise the kept pairs are sorted first; strings must come
+    // sorted, the bit-parallel DP keeps one query's match masks per run)
+    void verify_and_collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, int64_t C, bool query_major = true) {
         st_cands += C;
         DBuf<float> cdist(C, st);
         DBuf<uint8_t> keep(C, st);
@@ -2202,12 +2193,13 @@ struct Runner {
         }
         clk.end();
         check_launch("verify");
-        collect(cq, crow, cdist, keep, C);
+        collect(cq, crow, cdist, keep, C, query_major);
     }
 
     // Keep the pairs flagged in `keep`: range pairs are appended to the
     // answer; kNN pairs are merged into each query's answer so far.
-    void collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, DBuf<float> &cdist, DBuf<uint8_t> &keep, int64_t C) {
+    void collect(DBuf<int32_t> &cq, DBuf<int32_t> &crow, DBuf<float> &cdist, DBuf<uint8_t> &keep, int64_t C,
+                 bool query_major = true) {
         DBuf<int64_t> k64(C + 1, st), pos(C + 1, st);
         clk.begin(GTS_STAGE_OTHER, 2);
         k_u8_to_i64<<<nblocks(C, kT), kT, 0, st>>>(keep.get(), C, k64.get());
@@ -2223,7 +2215,25 @@ struct Runner {
             k_compact_cands<<<nblocks(C, kT), kT, 0, st>>>(cq.get(), crow.get(), cdist.get(), keep.get(), C, pos.get(),
                                                            kq2.get(), krow2.get(), kd2.get());
             clk.end();
-            merge_knn(kq2, krow2, kd2, R);
+            if (query_major) {
+                merge_knn(kq2, krow2, kd2, R);
+            } else {   // stable radix sort by query, (row, distance) carried along
+                DBuf<uint64_t> v1(R, st), v2(R, st);
+                DBuf<int32_t> q3(R, st), r3(R, st);
+                DBuf<float> d3(R, st);
+                int qbits = 1;
+                while (((int64_t)1 << qbits) < qb.nq) ++qbits;
+                size_t tb = 0;
+                cub::DeviceRadixSort::SortPairs(nullptr, tb, kq2.get(), q3.get(), v1.get(), v2.get(), R, 0, qbits, st);
+                DBuf<uint8_t> tmp(tb ? tb : 1, st);
+                clk.begin(GTS_STAGE_OTHER, 3);
+                k_pack_row_dist<<<cap(nblocks(R, kT)), kT, 0, st>>>(krow2.get(), kd2.get(), R, v1.get());
+                GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, kq2.get(), q3.get(), v1.get(), v2.get(), R, 0,
+                                                         qbits, st));
+                k_unpack_row_dist<<<cap(nblocks(R, kT)), kT, 0, st>>>(v2.get(), R, r3.get(), d3.get());
+                clk.end();
+                merge_knn(q3, r3, d3, R);
+            }
         } else {
             DBuf<uint64_t> rk(R, st);
             DBuf<float> rd(R, st);
