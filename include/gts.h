@@ -264,8 +264,11 @@ gts_status gts_autotune(gts_index *index, const gts_objects *queries, const floa
  * primitives of the BF16 L2 path (TMA load with 128-byte swizzle, tcgen05.mma
  * with the accumulator in TMEM, tcgen05.ld) on one 128 x N x K product:
  * D[128, N] = bf16(A[128, K]) * bf16(B[N, K])^T in FP32.  A, B, D are host
- * row-major float32; N a multiple of 32 up to 256, K in {64, 128, 192, 256}. */
-gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *D);
+ * row-major float32; N a multiple of 32 up to 256, K in {64, 128, 192, 256}.
+ * a_tmem = 0: A is read from shared memory (TMA); 1: A is first written into
+ * TMEM by tcgen05.st, one row per TMEM lane, as the tile kernel holds its node
+ * blocks. */
+gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, int a_tmem, float *D);
 
 /* Exact kNN over objects held on the device, by scanning every object, with
  * no device memory allocated by the call.  The paper has no counterpart: it is

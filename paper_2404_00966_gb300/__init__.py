@@ -125,7 +125,7 @@ def lib(path: Optional[str] = None):
     for f in ["gts_knn_scan_noalloc", "gts_knn_scan_noalloc_async"]:
         getattr(L, f).argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
         getattr(L, f).restype = ctypes.c_int
-    L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P]
+    L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     L.gts_selftest_tc.restype = ctypes.c_int
     L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]
     L.gts_result_copy.restype = ctypes.c_int
@@ -144,13 +144,13 @@ def lib(path: Optional[str] = None):
     return L
 
 
-def selftest_tc(A, B):
+def selftest_tc(A, B, a_tmem=False):
     """Diagnostic: D = bf16(A) @ bf16(B).T computed by the tensor-core tile
-    primitives (A: [128, K], B: [N, K] float32)."""
+    primitives (A: [128, K], B: [N, K] float32; a_tmem: A read from TMEM)."""
     A = np.ascontiguousarray(A, np.float32)
     B = np.ascontiguousarray(B, np.float32)
     D = np.zeros((A.shape[0], B.shape[0]), np.float32)
-    _check(lib().gts_selftest_tc(_ptr(A), _ptr(B), B.shape[0], A.shape[1], _ptr(D)))
+    _check(lib().gts_selftest_tc(_ptr(A), _ptr(B), B.shape[0], A.shape[1], 1 if a_tmem else 0, _ptr(D)))
     return D
 
 

@@ -735,11 +735,11 @@ gts_status gts_result_copy(const gts_result *r, int64_t *offsets, int64_t *ids, 
     });
 }
 
-gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, float *D) {
+gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, int a_tmem, float *D) {
     return guarded([&] {
         GTS_REQUIRE(A && B && D, GTS_EINVAL, "NULL argument");
         ensure_device();
-        tc_selftest(A, B, N, K, D);
+        tc_selftest(A, B, N, K, a_tmem, D);
     });
 }
 

@@ -132,7 +132,6 @@ struct TcCache {
     int dim_p = 0;
     DBuf<uint8_t> Xh, Xl;
     DBuf<float> xn2;
-    CUtensorMap map_h, map_l;
 };
 
 struct Tree {

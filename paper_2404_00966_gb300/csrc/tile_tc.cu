@@ -45,15 +45,16 @@ namespace gts {
 namespace {
 
 constexpr int kRows = 128;     // MMA M: rows of one node block
-// MMA N (queries per chunk) NQ and the number S of staging slots are template
-// parameters: up to 128 columns, 2 slots of 128 queries or 3 of 96; up to 192
-// columns, 2 slots of 64; up to 256, 2 slots of 32 -- so that the node block
-// (A, hi and lo) and S chunk buffers (B, hi and lo) fit in shared memory.
-// TMEM holds S FP32 accumulators of 128 lanes x NQ columns.
-// (up to 128 columns the tuning chooses: 128 x 2 by default, or 96 x 3)
+// MMA N (queries per chunk) NQ, the number SB of query-row buffers (B, hi and
+// lo) and the number SM of chunk slots (records, path distances and one FP32
+// TMEM accumulator of 128 lanes x NQ columns each) are template parameters:
+// up to 128 columns 128 or 96 queries (the tuning chooses; 128 by default), up
+// to 192 columns 64, up to 256 columns 32; SB = 2 and SM = 4 (3 for 128
+// queries with deep trees), so that the node block (A, hi and lo), the B
+// buffers and the slots fit in shared memory.  A B buffer is released when the
+// MMAs that read it are done, a slot when the epilogue has tested its chunk:
+// the producers restage B while the epilogue still works on older chunks.
 inline int nq_for(int dim_p, int pref) { return dim_p <= 128 ? (pref == 96 ? 96 : 128) : dim_p <= 192 ? 64 : 32; }
-inline int slots_for(int nq) { return nq == 96 ? 3 : 2; }
-__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -68,7 +69,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // bf16 rows [rows, dim_p], box 64 columns x box_rows rows, 128-byte swizzle
-CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p, int box_rows = kRows) {
+CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p, int box_rows) {
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)dim_p, (cuuint64_t)(rows > 0 ? rows : 1)};
     cuuint64_t strides[1] = {(cuuint64_t)dim_p * 2};
@@ -112,12 +113,30 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// (d0, d1) = (a0 + b0, a1 + b1), one packed FP32 addition (round to nearest)
+__device__ __forceinline__ void add2(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// (d0, d1) = (a0 b0 + c0, a1 b1 + c1), one packed FP32 fused multiply-add
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1, float c0,
+                                     float c1) {
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+
 __device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, float cE2, float &alpha, float &beta);
 
 // The per-chunk data the producer hands to the MMA thread and the epilogue.
 struct ChunkDesc {
     int32_t stop;       // 1: no more work
-    int32_t new_item;   // first chunk of a node block (the block's A operand is loading)
+    int32_t new_item;   // first chunk of a node block (the epilogue writes the block's rows into TMEM)
     int32_t first;      // first record of the chunk
     int32_t cnt;        // queries in the chunk
     int32_t pos, size;  // the node's rows [pos, pos + size)
@@ -163,61 +182,69 @@ __device__ __forceinline__ void stage_chunk(const TileArgs &a, int start, int cn
     }
 }
 
-// Warp-specialised persistent kernel: the producer warps stage chunk g into
-// slot g % 2 once the epilogue has released the chunk g - 2 held there; one
-// thread issues the MMAs of chunk g into accumulator g % 2 when its operands
-// have landed; the epilogue warps test chunk g when its MMAs are done and
-// release the slot.  mbarriers carry every hand-off (chunk g uses slot g % S;
-// its barriers' phase parity is (g / S) & 1), so no block-wide barrier runs
-// per chunk.
-template <int NQ, int S>
+// Warp-specialised persistent kernel.  When a node block starts, the epilogue
+// warps write its split rows (A, hi and lo) into TMEM, each thread its own row
+// (TMEM lane = block row); the producer warps stage chunk g's query rows into
+// B buffer g % SB once the MMAs of chunk g - SB are done, and its records into
+// slot g % SM once the epilogue has released chunk g - SM; one thread issues
+// the MMAs of chunk g (A from TMEM, B from shared memory) into accumulator
+// g % SM; the epilogue warps test chunk g when its MMAs are done and release
+// the slot.  mbarriers carry every hand-off (the barriers of slot g % SM;
+// chunk g's phase parity is (g / SM) & 1), so no block-wide barrier runs per
+// chunk.
+//
+// TMEM columns: [0, dim_p / 2) A_hi and [dim_p / 2, dim_p) A_lo (two
+// consecutive coordinates per 32-bit column), then SM accumulators of NQ
+// columns.  With A in TMEM the shared-memory port serves B alone: with both
+// operands in shared memory a 128 x 128 x 16 MMA reads 8 KB, all that the port
+// delivers in the MMA's 64 cycles, and the MMAs ran at about 60 % of the
+// tensor rate.
+template <int NQ, int SB, int SM>
 __global__ void __launch_bounds__(kThreadsWS, 1)
-    k_tile_l2_tc(const __grid_constant__ CUtensorMap map_h, const __grid_constant__ CUtensorMap map_l,
-                 const __grid_constant__ CUtensorMap map_qh, const __grid_constant__ CUtensorMap map_ql, TileArgs a) {
+    k_tile_l2_tc(const __grid_constant__ CUtensorMap map_qh, const __grid_constant__ CUtensorMap map_ql, TileArgs a) {
+    static_assert(SB <= SM, "a B buffer is reused no later than its slot");
     constexpr int kNQ = NQ;
-    constexpr int kTmemCols = pow2_at_least(S * NQ);
+    constexpr int kTmemCols = 512;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int panels = a.dim_p / 64;
-    const int apanel = kRows * 128, bpanel = kNQ * 128;
-    uint8_t *sAh = smem;                                    // panels x 128 rows x 128 B
-    uint8_t *sAl = sAh + panels * apanel;
-    uint8_t *sB = sAl + panels * apanel;                    // S slots x (hi, lo) x panels x kNQ x 128 B
-    const int bbuf = 2 * panels * bpanel;                   // bytes of one slot
-    uint8_t *mbase = sB + S * bbuf;
-    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + (int)sizeof(ChunkDesc);
+    const int bpanel = kNQ * 128;
+    uint8_t *sB = smem;                                     // SB buffers x (hi, lo) x panels x kNQ x 128 B
+    const int bbuf = 2 * panels * bpanel;                   // bytes of one buffer
+    uint8_t *mbase = sB + SB * bbuf;
+    // slot: records [kNQ], path distances [kNQ][hp], bound constants [kNQ / 2][4], descriptor
+    const int mbytes = kNQ * (int)sizeof(TileRec) + kNQ * a.hp * 4 + kNQ * 8 + (int)sizeof(ChunkDesc);
     auto mrec = [&](int sl) { return (TileRec *)(mbase + sl * mbytes); };
     auto mpath = [&](int sl) { return (float *)(mbase + sl * mbytes + kNQ * sizeof(TileRec)); };
+    // columns 2i, 2i + 1 as (alpha_2i, alpha_2i+1, beta_2i, beta_2i+1), for packed FP32 tests
+    auto mab = [&](int sl) { return (float *)(mbase + sl * mbytes + kNQ * sizeof(TileRec) + kNQ * a.hp * 4); };
     auto mdesc = [&](int sl) {
-        return (ChunkDesc *)(mbase + sl * mbytes + kNQ * sizeof(TileRec) + kNQ * a.hp * 4);
+        return (ChunkDesc *)(mbase + sl * mbytes + kNQ * sizeof(TileRec) + kNQ * a.hp * 4 + kNQ * 8);
     };
-    uint64_t *bars = (uint64_t *)(mbase + S * mbytes);     // full[S], mma_done[S], epi_done[S], a_full
-    uint64_t *full = bars, *mma_done = bars + S, *epi_done = bars + 2 * S, *a_full = bars + 3 * S;
-    uint32_t *tslot = (uint32_t *)(bars + 3 * S + 1);
+    uint64_t *bars = (uint64_t *)(mbase + SM * mbytes);    // full[SM], mma_done[SM], epi_done[SM], a_full
+    uint64_t *full = bars, *mma_done = bars + SM, *epi_done = bars + 2 * SM, *a_full = bars + 3 * SM;
+    uint32_t *tslot = (uint32_t *)(bars + 3 * SM + 1);
     int *sitem = (int *)(tslot + 1);
     volatile int *sabort = sitem + 1;
-    int *a_issued = sitem + 2;     // A loads issued / consumed (for the abort path)
-    int *a_used = sitem + 3;
     int32_t *sqid = sitem + 4;     // the staged chunk's query ids (producers only), kNQ
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
     if (tid == 0) {
-        for (int i = 0; i < S; ++i) {
+        for (int i = 0; i < SM; ++i) {
             tc::mbar_init(&full[i], kProducers);
             tc::mbar_init(&mma_done[i], 1);
             tc::mbar_init(&epi_done[i], kEpiWarps);
         }
-        tc::mbar_init(a_full, 1);
+        tc::mbar_init(a_full, kEpiWarps);
         tc::mbar_fence_init();
         *sabort = 0;
-        *a_issued = 0;
-        *a_used = 0;
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t tacc = tmem + (uint32_t)a.dim_p;        // accumulator 0
     const int chunks16 = a.dim_p / 8;                       // 16-byte chunks per bf16 row
     auto fail = [&](int code) {
         *sabort = 1;
@@ -228,7 +255,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         // ================================================= producer warps
         const int ptid = tid - kProdWarp0 * 32;
         uint32_t g = 0;
-        int64_t last_g = -1;   // last chunk of the previous block
         for (;;) {
             if (ptid == 0) *sitem = atomicAdd(a.work_counter, 1);
             tc::named_sync(1, kProducers);
@@ -242,41 +268,48 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 const int64_t gnode = a.lvl_last + it.x;
                 pos = a.npos[gnode];
                 size = a.nsize[gnode];
-                if (ptid == 0) {
-                    // the previous block's MMAs are done once its last epilogue is
-                    if (last_g >= 0 && !tc::mbar_wait(&epi_done[last_g % S], (uint32_t)((last_g / S) & 1))) fail(3);
-                    tc::mbar_expect_tx(a_full, (uint32_t)(2 * panels * apanel));
-                    for (int pnl = 0; pnl < panels; ++pnl) {
-                        const int y = pos + (it.w & (kWindowItem - 1)) * kRows;
-                        tc::tma_load_2d(sAh + pnl * apanel, &map_h, pnl * 64, y, a_full);
-                        tc::tma_load_2d(sAl + pnl * apanel, &map_l, pnl * 64, y, a_full);
-                    }
-                    ++*a_issued;
-                }
             }
             const int total = it.z;
             const bool window = !stop && (it.w & kWindowItem) != 0;
             const int rbk = it.w & (kWindowItem - 1);
             // gather mode: chunks of the node's records; window mode: windows of
-            // 128 consecutive query ids (those without an entry are skipped)
+            // kNQ consecutive query ids (those without an entry are skipped)
             const int nchunks = stop ? 1 : window ? (int)((a.nq + kNQ - 1) / kNQ) : (total + kNQ - 1) / kNQ;
+            // window mode: this thread's column of window c (query c * kNQ +
+            // ptid; threads past kNQ have none): its bitmap word and, for the
+            // dense last level, its leaf mask and query data -- loaded one
+            // window ahead, so the loads overlap the previous window's work
+            struct Col {
+                uint32_t word;
+                uint64_t dmask;
+                float thr, qn2;
+                int64_t seq;
+            };
+            auto load_col = [&](int c) {
+                Col w;
+                w.word = 0;
+                w.dmask = 0;
+                w.thr = w.qn2 = 0.f;
+                w.seq = 0;
+                const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
+                const int64_t q = (int64_t)c * kNQ + ptid;
+                if (ptid < kNQ && wi < a.nw) w.word = a.bits[(int64_t)it.x * a.nw + wi];
+                if (a.dmask && ptid < kNQ && q < a.nq) {
+                    w.dmask = a.dmask[(int64_t)it.x * a.nq + q];
+                    w.thr = a.thr_q[q];
+                    w.qn2 = a.qn2_q[q];
+                    w.seq = a.seq_q[q];
+                }
+                return w;
+            };
+            Col nxt;
+            if (window) nxt = load_col(0);
             bool first_chunk = true;
             for (int c = 0; c < nchunks; ++c) {
-                uint32_t word = 0;
-                TileRec drec;   // dense last level: this column's record, loaded before the slot wait
-                drec.mask = 0;
+                const Col cur = nxt;
                 if (window) {
-                    // this thread's column: query c * NQ + ptid (threads past NQ have none)
-                    const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
-                    if (ptid < kNQ && wi < a.nw) word = a.bits[(int64_t)it.x * a.nw + wi];
-                    if (a.dmask && ((word >> (ptid & 31)) & 1u)) {
-                        const int64_t q = (int64_t)c * kNQ + ptid;
-                        drec.mask = a.dmask[(int64_t)it.x * a.nq + q];
-                        drec.thr = a.thr_q[q];
-                        drec.alpha = a.qn2_q[q];   // |q|^2 until the constants are formed
-                        drec.seq = a.seq_q[q];
-                    }
-                    const unsigned any = __ballot_sync(0xffffffffu, word != 0u);
+                    if (c + 1 < nchunks) nxt = load_col(c + 1);
+                    const unsigned any = __ballot_sync(0xffffffffu, cur.word != 0u);
                     if ((ptid & 31) == 0) sqid[ptid >> 5] = any ? 1 : 0;
                     tc::named_sync(1, kProducers);
                     int nonempty = 0;
@@ -284,45 +317,69 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     tc::named_sync(1, kProducers);
                     if (!nonempty) continue;
                 }
-                const int sl = g % S;
-                if (g >= S && !tc::mbar_wait(&epi_done[sl], ((g - S) / S) & 1)) fail(4);
+                const int sl = g % SM, sb = g % SB;
+                // B buffer sb: the MMAs of chunk g - SB are done (every phase
+                // of full[sl] up to chunk g - SM completed before that)
+                if (g >= SB && !tc::mbar_wait(&mma_done[(g - SB) % SM], ((g - SB) / SM) & 1)) fail(4);
+                if (window && ptid == 0) {
+                    tc::mbar_expect_tx_only(&full[sl], (uint32_t)(2 * panels * bpanel));
+                    for (int pnl = 0; pnl < panels; ++pnl) {
+                        tc::tma_load_2d(sB + sb * bbuf + pnl * bpanel, &map_qh, pnl * 64, c * kNQ, &full[sl]);
+                        tc::tma_load_2d(sB + sb * bbuf + (panels + pnl) * bpanel, &map_ql, pnl * 64, c * kNQ,
+                                        &full[sl]);
+                    }
+                }
+                // slot sl (records, path distances, accumulator): chunk g - SM tested
+                if (g >= SM && !tc::mbar_wait(&epi_done[sl], ((g - SM) / SM) & 1)) fail(7);
                 int cnt;
+                float *ab = mab(sl);
                 if (stop) {
                     cnt = 0;
                 } else if (window) {
                     cnt = kNQ;
-                    if (ptid == 0) {
-                        tc::mbar_expect_tx_only(&full[sl], (uint32_t)(2 * panels * bpanel));
-                        for (int pnl = 0; pnl < panels; ++pnl) {
-                            tc::tma_load_2d(sB + sl * bbuf + pnl * bpanel, &map_qh, pnl * 64, c * kNQ, &full[sl]);
-                            tc::tma_load_2d(sB + sl * bbuf + (panels + pnl) * bpanel, &map_ql, pnl * 64, c * kNQ,
-                                            &full[sl]);
+                    // column ptid: its record, path distances and bound constants, or an empty record
+                    if (ptid < kNQ) {
+                        TileRec *mr = mrec(sl) + ptid;
+                        const bool has = (cur.word >> (ptid & 31)) & 1u;
+                        if (a.dmask) {
+                            // dense last level: the record from the per-query arrays
+                            TileRec r;
+                            r.q = (int32_t)((int64_t)c * kNQ + ptid);
+                            r.thr = cur.thr;
+                            r.seq = cur.seq;
+                            r.mask = has ? cur.dmask : 0ull;
+                            r.alpha = r.beta = 0.f;
+                            if (r.mask) bound_consts(r.thr, cur.qn2, a.cE1, a.cE2, r.alpha, r.beta);
+                            *mr = r;
+                            ab[(ptid >> 1) * 4 + (ptid & 1)] = r.alpha;
+                            ab[(ptid >> 1) * 4 + 2 + (ptid & 1)] = r.beta;
+                        } else if (has) {
+                            const int64_t wi = (int64_t)it.x * a.nw + (int64_t)c * (kNQ / 32) + (ptid >> 5);
+                            const int64_t o =
+                                a.noff[it.x] + a.wpre[wi] + __popc(cur.word & ((1u << (ptid & 31)) - 1u));
+                            const TileRec r = a.grec[o];
+                            *mr = r;
+                            ab[(ptid >> 1) * 4 + (ptid & 1)] = r.alpha;
+                            ab[(ptid >> 1) * 4 + 2 + (ptid & 1)] = r.beta;
+                            float *mp = mpath(sl) + ptid * a.hp;
+                            for (int l = 0; l < a.hp; ++l) mp[l] = a.gpath[o * a.hp + l];
+                        } else {
+                            mr->mask = 0;
+                            mr->q = c * kNQ + ptid;
                         }
-                    }
-                    // column ptid: its record and path distances, or an empty record
-                    TileRec *mr = mrec(sl) + (ptid < kNQ ? ptid : 0);
-                    float *mp = mpath(sl) + (ptid < kNQ ? ptid : 0) * a.hp;
-                    if (ptid >= kNQ) {
-                        // no column
-                    } else if (a.dmask) {
-                        // dense last level: the record from the per-query arrays
-                        TileRec r = drec;
-                        r.q = (int32_t)((int64_t)c * kNQ + ptid);
-                        if (r.mask) bound_consts(r.thr, drec.alpha, a.cE1, a.cE2, r.alpha, r.beta);
-                        *mr = r;
-                    } else if ((word >> (ptid & 31)) & 1u) {
-                        const int64_t wi = (int64_t)it.x * a.nw + (int64_t)c * (kNQ / 32) + (ptid >> 5);
-                        const int64_t o = a.noff[it.x] + a.wpre[wi] + __popc(word & ((1u << (ptid & 31)) - 1u));
-                        *mr = a.grec[o];
-                        for (int l = 0; l < a.hp; ++l) mp[l] = a.gpath[o * a.hp + l];
-                    } else {
-                        mr->mask = 0;
-                        mr->q = c * kNQ + ptid;
                     }
                 } else {
                     cnt = total - c * kNQ < kNQ ? total - c * kNQ : kNQ;
-                    stage_chunk<NQ>(a, it.y + c * kNQ, cnt, mrec(sl), mpath(sl), sB + sl * bbuf,
-                                    sB + sl * bbuf + panels * bpanel, chunks16, ptid, sqid);
+                    stage_chunk<NQ>(a, it.y + c * kNQ, cnt, mrec(sl), mpath(sl), sB + sb * bbuf,
+                                    sB + sb * bbuf + panels * bpanel, chunks16, ptid, sqid);
+                    // the bound constants, once every producer's record copies have landed
+                    cp_async_wait_all();
+                    tc::named_sync(1, kProducers);
+                    for (int j = ptid; j < cnt; j += kProducers) {
+                        const TileRec &r = mrec(sl)[j];
+                        ab[(j >> 1) * 4 + (j & 1)] = r.alpha;
+                        ab[(j >> 1) * 4 + 2 + (j & 1)] = r.beta;
+                    }
                 }
                 if (ptid == 0) {
                     ChunkDesc dsc;
@@ -345,18 +402,18 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 ++g;
             }
             if (stop) break;
-            last_g = (int64_t)g - 1;
         }
         cp_async_wait_all();
     } else if (warp == kMmaWarp) {
         // ================================================= MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
+            const uint32_t alo = tmem + (uint32_t)(a.dim_p / 2);   // A_lo
             uint32_t a_par = 0;
             int64_t last_issued = -1;
             for (uint32_t g = 0;; ++g) {
-                const int sl = g % S;
-                if (!tc::mbar_wait(&full[sl], (g / S) & 1)) {
+                const int sl = g % SM;
+                if (!tc::mbar_wait(&full[sl], (g / SM) & 1)) {
                     fail(5);
                     break;
                 }
@@ -364,43 +421,43 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 if (dsc.stop || *sabort) break;
                 tc::fence_proxy_async_smem();
                 if (dsc.new_item) {
+                    // the block's rows are in TMEM
                     if (!tc::mbar_wait(a_full, a_par)) {
                         fail(1);
                         break;
                     }
                     a_par ^= 1u;
-                    ++*a_used;
                 }
                 tc::tc_fence_after();
-                const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl);
-                const uint32_t bh = tc::smem_u32(sB + sl * bbuf), bl = bh + panels * bpanel;
-                const uint32_t dt = tmem + (uint32_t)(sl * kNQ);
+                const uint32_t bh = tc::smem_u32(sB + (g % SB) * bbuf), bl = bh + panels * bpanel;
+                const uint32_t dt = tacc + (uint32_t)(sl * kNQ);
                 const int ksteps = a.dim_p / 16;
                 for (int s = 0; s < ksteps; ++s) {
-                    const uint32_t ao = (s >> 2) * apanel + (s & 3) * 32, bo = (s >> 2) * bpanel + (s & 3) * 32;
-                    tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
-                    tc::mma_bf16(dt, tc::sdesc_k_sw128(ah + ao), tc::sdesc_k_sw128(bl + bo), idesc, 1u);
-                    tc::mma_bf16(dt, tc::sdesc_k_sw128(al + ao), tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+                    const uint32_t bo = (s >> 2) * bpanel + (s & 3) * 32;
+                    tc::mma_bf16_ts(dt, tmem + 8 * s, tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
+                    tc::mma_bf16_ts(dt, tmem + 8 * s, tc::sdesc_k_sw128(bl + bo), idesc, 1u);
+                    tc::mma_bf16_ts(dt, alo + 8 * s, tc::sdesc_k_sw128(bh + bo), idesc, 1u);
                 }
                 tc::mma_commit(&mma_done[sl]);
                 last_issued = g;
             }
             // on an early exit, let issued MMAs finish before TMEM is released
             if (last_issued >= 0 && *sabort)
-                tc::mbar_wait(&mma_done[last_issued % S], (uint32_t)((last_issued / S) & 1));
+                tc::mbar_wait(&mma_done[last_issued % SM], (uint32_t)((last_issued / SM) & 1));
         }
     } else if (warp < kEpiWarps) {
         // ================================================= epilogue warps
         const int quad = warp & 3;                 // TMEM lane quadrant of this warp
         const int cc = (warp >> 2) * 32;           // its query columns [cc, cc + 32)
         const int r = quad * 32 + lane;            // row of the block
+        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
         bool valid = false;
         int64_t row = 0, rdel = kNever;
         uint64_t rowbit = 0, wmask = 0;
         float xn = 0.f, gx = 0.f;
         for (uint32_t g = 0;; ++g) {
-            const int sl = g % S;
-            if (!tc::mbar_wait(&full[sl], (g / S) & 1)) {
+            const int sl = g % SM;
+            if (!tc::mbar_wait(&full[sl], (g / SM) & 1)) {
                 fail(6);
                 break;
             }
@@ -435,8 +492,38 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 rowbit = valid ? (1ull << jl) : 0ull;
                 // gamma_x = (cE2 - 1) |x|^2, rounded toward +inf (keeps the test conservative)
                 gx = __fmul_ru(a.cE2 - 1.f, xn2) + 4.f * 1.1920929e-7f * xn2;
+                // the row's split coordinates into TMEM (rows outside the block:
+                // zeros).  Every MMA of the previous block is done: this warp
+                // has waited for the previous chunk's.
+                const int ncol = a.dim_p / 4;                  // this warp's share of A's dim_p columns
+                for (int p = 0; p < ncol; p += 16) {
+                    const int col = (warp >> 2) * ncol + p;
+                    const bool lo = col >= a.dim_p / 2;
+                    const int k0 = 2 * (lo ? col - a.dim_p / 2 : col);   // first coordinate
+                    uint32_t v[16];
+                    if (valid) {
+                        const uint4 *src = reinterpret_cast<const uint4 *>((lo ? a.Xl : a.Xh) + row * a.dim_p + k0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint4 x = src[j];
+                            v[4 * j] = x.x;
+                            v[4 * j + 1] = x.y;
+                            v[4 * j + 2] = x.z;
+                            v[4 * j + 3] = x.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = 0u;
+                    }
+                    __syncwarp();   // tcgen05.st is warp-wide
+                    tc::tmem_st16(tmem + tlane + (uint32_t)col, v);
+                }
+                tc::tmem_st_wait();
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(a_full);
             }
-            if (!tc::mbar_wait(&mma_done[sl], (g / S) & 1)) {
+            if (!tc::mbar_wait(&mma_done[sl], (g / SM) & 1)) {
                 fail(2);
                 break;
             }
@@ -450,26 +537,32 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                                       : 0u;
             if (live) {   // warp-uniform
                 uint32_t v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * kNQ + cc), v);
+                tc::tmem_ld32(tacc + tlane + (uint32_t)(sl * kNQ + cc), v);
                 tc::tmem_ld_wait();
-                // leaf and bound tests of all 32 columns without branches:
-                // d~^2 <= thr^2 + E  <=>  -2 q.x <= beta_q + alpha_q |x| + gamma_x
-                uint32_t cand = 0;
+                // bound test of all 32 columns, two at a time in packed FP32:
+                // d~^2 <= thr^2 + E  <=>  -2 q.x <= w = fma(alpha_q, |x|, beta_q + gamma_x)
+                // <=>  t = 2 q.x + w >= 0.  t is rounded once from the exact
+                // sum, so its sign is that of the exact sum, and it is never
+                // -0 (w >= +0 when it is zero): its sign bit marks a failed test.
+                const float4 *abp = reinterpret_cast<const float4 *>(mab(sl) + cc * 2);
+                uint32_t failbits = 0;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const TileRec &rc = rec[cc + i];
-                    const bool p = (rc.mask & rowbit) != 0 &&
-                                   -2.f * __uint_as_float(v[i]) <= fmaf(rc.alpha, xn, rc.beta + gx);
-                    cand |= (p ? 1u : 0u) << i;
+                for (int i = 0; i < 32; i += 2) {
+                    const float4 c4 = abp[i / 2];   // alpha_i, alpha_i+1, beta_i, beta_i+1
+                    float w0, w1, t0, t1;
+                    add2(w0, w1, c4.z, c4.w, gx, gx);
+                    fma2(w0, w1, c4.x, c4.y, xn, xn, w0, w1);
+                    fma2(t0, t1, 2.f, 2.f, __uint_as_float(v[i]), __uint_as_float(v[i + 1]), w0, w1);
+                    failbits |= ((__float_as_uint(t0) >> 31) << i) | ((__float_as_uint(t1) >> 31) << (i + 1));
                 }
-                cand &= live;
-                // the few survivors: visibility and the table lower bound
+                uint32_t cand = ~failbits & live;
+                // the few survivors: the row's leaf, visibility and the table lower bound
                 uint32_t passbits = 0;
                 while (cand) {
                     const int i = __ffs(cand) - 1;
                     cand &= cand - 1;
                     const TileRec &rc = rec[cc + i];
-                    if (rdel <= rc.seq) continue;
+                    if (!(rc.mask & rowbit) || rdel <= rc.seq) continue;
                     bool ok = true;
                     // (the table lower bound can only drop a pair that the
                     // distance bound already dropped; dense chunks skip it)
@@ -509,10 +602,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             if (lane == 0) tc::mbar_arrive(&epi_done[sl]);
         }
     }
+    tc::tc_fence_before();
     __syncthreads();
-    if (tid == 0 && *a_issued > *a_used) tc::mbar_wait(a_full, (uint32_t)((*a_issued - 1) & 1));   // a TMA still landing
     tc::tc_fence_after();
-    __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -690,12 +782,12 @@ inline unsigned nblk(int64_t n, int per = 256) {
     return (unsigned)b;
 }
 
-size_t tile_smem_bytes(int dim_p, int h, int kNQ, int S) {
+size_t tile_smem_bytes(int dim_p, int h, int kNQ, int SB, int SM) {
     const int panels = dim_p / 64;
     size_t b = 1024;                                              // alignment slack
-    b += (size_t)2 * panels * kRows * 128 + (size_t)S * 2 * panels * kNQ * 128;
-    b += S * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + 32);
-    b += (3 * S + 1) * 8 + 4 + 4 * 4 + 16 + (size_t)kNQ * 4;
+    b += (size_t)SB * 2 * panels * kNQ * 128;
+    b += SM * ((size_t)kNQ * sizeof(TileRec) + (size_t)kNQ * ((h + 3) & ~3) * 4 + (size_t)kNQ * 8 + 32);
+    b += (3 * SM + 1) * 8 + 4 + 4 * 4 + 16 + (size_t)kNQ * 4;
     return b;
 }
 
@@ -721,8 +813,6 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
     k_split_rows<<<nblk(t.n * 32), 256, 0, st>>>(t.X.get(), t.dim, c.dim_p, t.n, (__nv_bfloat16 *)c.Xh.get(),
                                                 (__nv_bfloat16 *)c.Xl.get(), c.xn2.get());
     check_launch("split rows");
-    c.map_h = make_row_map(c.Xh.get(), t.n, c.dim_p);
-    c.map_l = make_row_map(c.Xl.get(), t.n, c.dim_p);
     GTS_CUDA(cudaStreamSynchronize(st));
     c.Xh.persist();
     c.Xl.persist();
@@ -858,18 +948,19 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int dev = 0, sms = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int nq_chunk = nq_for(c.dim_p, tq.chunk), slots = slots_for(nq_chunk);
+    const int nq_chunk = nq_for(c.dim_p, tq.chunk);
     int smem_optin = 0;
     GTS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (nq_chunk == 96 && tile_smem_bytes(c.dim_p, t.h, 96, 3) > (size_t)smem_optin) {
-        nq_chunk = 128;   // deep trees: the path distances of three slots do not fit, two slots of 128
-        slots = 2;
-    }
-    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk, slots);
-    auto kern = nq_chunk == 96    ? k_tile_l2_tc<96, 3>
-                : nq_chunk == 128 ? k_tile_l2_tc<128, 2>
-                : nq_chunk == 64  ? k_tile_l2_tc<64, 2>
-                                  : k_tile_l2_tc<32, 2>;
+    // TMEM: A (dim_p columns) and the slots' accumulators share 512 columns:
+    // three slots of 128 queries, four of 96, 64 or 32; as many B buffers
+    const int slots = nq_chunk == 128 ? 3 : 4;
+    GTS_REQUIRE(c.dim_p + slots * nq_chunk <= 512, GTS_ECUDA, "tensor-core tile: TMEM columns");
+    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk, slots, slots);
+    GTS_REQUIRE(smem <= (size_t)smem_optin, GTS_ECUDA, "tensor-core tile: shared memory");
+    auto kern = nq_chunk == 96    ? k_tile_l2_tc<96, 4, 4>
+                : nq_chunk == 128 ? k_tile_l2_tc<128, 3, 3>
+                : nq_chunk == 64  ? k_tile_l2_tc<64, 4, 4>
+                                  : k_tile_l2_tc<32, 4, 4>;
     GTS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
     // TMEM columns, and registers
@@ -881,7 +972,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int per_sm = (int)(smem_sm / (smem + 1024));
     const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kThreadsWS;
     if (regs_cta > 0 && per_sm > regs_sm / regs_cta) per_sm = regs_sm / regs_cta;
-    if (per_sm > 512 / pow2_at_least(slots * nq_chunk)) per_sm = 512 / pow2_at_least(slots * nq_chunk);   // TMEM
+    if (per_sm > 1) per_sm = 1;   // TMEM: every CTA takes all 512 columns
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     // the batch's split query rows, for window-mode chunks (TMA, 128 rows)
@@ -905,6 +996,8 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.h = t.h;
         a.n = t.n;
         a.xn2 = c.xn2.get();
+        a.Xh = reinterpret_cast<const __nv_bfloat16 *>(c.Xh.get());
+        a.Xl = reinterpret_cast<const __nv_bfloat16 *>(c.Xl.get());
         a.table = t.table.get();
         a.row_del = t.row_del.get();
         a.npos = t.npos.get();
@@ -937,7 +1030,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.thr_q = tq.thr;
         a.qn2_q = tq.qn2;
         a.seq_q = tq.qseq;
-        kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(c.map_h, c.map_l, map_qh, map_ql, a);
+        kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(map_qh, map_ql, a);
         ++*launches;
         check_launch("tensor-core tile");
         unsigned long long hcount = 0;
@@ -957,11 +1050,14 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
 
 namespace {
 
-constexpr int kSelfN = 256;   // self-test tile: N up to 256, its own TMEM allocation
+constexpr int kSelfN = 256;   // self-test tile: N up to 256 accumulator columns, then A (a_tmem) in TMEM
 
+// D = A B^T for one 128 x N x K tile, A from shared memory (loaded by TMA) or,
+// with a_tmem, from TMEM (written by the four warps, thread = row, as the
+// tile kernel writes its node blocks).
 __global__ void __launch_bounds__(128, 1)
-    k_selftest_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16 *__restrict__ B, int N, int K,
-                  float *__restrict__ D, int *status) {
+    k_selftest_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16 *__restrict__ A,
+                  const __nv_bfloat16 *__restrict__ B, int N, int K, int a_tmem, float *__restrict__ D, int *status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int panels = K / 64;
@@ -970,7 +1066,7 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t *bars = (uint64_t *)(sB + panels * kSelfN * 128);
     uint32_t *tslot = (uint32_t *)(bars + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tc::tmem_alloc(tslot, kSelfN);
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * kSelfN);
     if (tid == 0) {
         tc::mbar_init(&bars[0], 1);
         tc::mbar_init(&bars[1], 1);
@@ -985,6 +1081,26 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tslot;
+    const uint32_t ta = tmem + kSelfN;   // A in TMEM: K / 2 columns
+    if (a_tmem) {
+        // thread = row = TMEM lane; 16 columns (32 coordinates) per store
+        for (int c = 0; c < K / 2; c += 16) {
+            uint32_t v[16];
+            const uint4 *src = reinterpret_cast<const uint4 *>(A + (int64_t)tid * K + 2 * c);
+            for (int j = 0; j < 4; ++j) {
+                const uint4 x = src[j];
+                v[4 * j] = x.x;
+                v[4 * j + 1] = x.y;
+                v[4 * j + 2] = x.z;
+                v[4 * j + 3] = x.w;
+            }
+            tc::tmem_st16(ta + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        }
+        tc::tmem_st_wait();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
     if (tid == 0) {
         if (!tc::mbar_wait(&bars[0], 0)) {
             atomicExch(status, 1);
@@ -992,8 +1108,12 @@ __global__ void __launch_bounds__(128, 1)
             const uint32_t idesc = tc::idesc_bf16_f32(kRows, kSelfN);
             for (int s = 0; s < K / 16; ++s) {
                 const int p = s >> 2, w = s & 3;
-                tc::mma_bf16(tmem, tc::sdesc_k_sw128(tc::smem_u32(sA) + p * kRows * 128 + w * 32),
-                             tc::sdesc_k_sw128(tc::smem_u32(sB) + p * kSelfN * 128 + w * 32), idesc, s > 0 ? 1u : 0u);
+                const uint64_t bd = tc::sdesc_k_sw128(tc::smem_u32(sB) + p * kSelfN * 128 + w * 32);
+                if (a_tmem)
+                    tc::mma_bf16_ts(tmem, ta + 8 * s, bd, idesc, s > 0 ? 1u : 0u);
+                else
+                    tc::mma_bf16(tmem, tc::sdesc_k_sw128(tc::smem_u32(sA) + p * kRows * 128 + w * 32), bd, idesc,
+                                 s > 0 ? 1u : 0u);
             }
             tc::mma_commit(&bars[1]);
         }
@@ -1019,7 +1139,7 @@ __global__ void __launch_bounds__(128, 1)
         tc::mbar_wait(&bars[1], 0);
     }
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kSelfN);
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * kSelfN);
 }
 
 __global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
@@ -1029,7 +1149,7 @@ __global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
 
 }  // namespace
 
-void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD) {
+void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD) {
     GTS_REQUIRE(N >= 32 && N <= kSelfN && N % 32 == 0, GTS_EINVAL, "N must be a multiple of 32 in 32 .. 256");
     GTS_REQUIRE(K >= 64 && K <= 256 && K % 64 == 0, GTS_EINVAL, "K must be 64, 128, 192 or 256");
     cudaStream_t st = nullptr;
@@ -1041,10 +1161,10 @@ void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD) {
     GTS_CUDA(cudaMemsetAsync(status.get(), 0, 4, st));
     k_f32_to_bf16<<<64, 256, 0, st>>>(fA.get(), (int64_t)kRows * K, bA.get());
     k_f32_to_bf16<<<64, 256, 0, st>>>(fB.get(), (int64_t)N * K, bB.get());
-    CUtensorMap m = make_row_map(bA.get(), kRows, K);
+    CUtensorMap m = make_row_map(bA.get(), kRows, K, kRows);
     const size_t smem = 1024 + (size_t)(K / 64) * (kRows + kSelfN) * 128 + 64;
     GTS_CUDA(cudaFuncSetAttribute(k_selftest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_selftest_tc<<<1, 128, smem, st>>>(m, bB.get(), N, K, D.get(), status.get());
+    k_selftest_tc<<<1, 128, smem, st>>>(m, bA.get(), bB.get(), N, K, a_tmem ? 1 : 0, D.get(), status.get());
     check_launch("tensor-core self-test");
     int hs = 0;
     GTS_CUDA(cudaMemcpyAsync(&hs, status.get(), 4, cudaMemcpyDeviceToHost, st));

@@ -23,6 +23,7 @@ struct TileArgs {
     int dim, dim_p, F, h;
     int64_t n;
     const float *xn2;         // |x|^2 of every row (FP64 sum, rounded)
+    const __nv_bfloat16 *Xh, *Xl;   // every row, split bf16 [n, dim_p]
     const float *table;       // [h, n]
     const int64_t *row_del;
     const int32_t *npos, *nsize;
@@ -114,6 +115,6 @@ int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegro
 // run the tiles; returns the number of (query, row) pairs written to out_q/out_row
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
-void tc_selftest(const float *hA, const float *hB, int N, int K, float *hD);
+void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD);
 
 }  // namespace gts

@@ -223,14 +223,16 @@ def _bf16(x):
     return r.view(np.float32)
 
 
+@pytest.mark.parametrize("a_tmem", [False, True])
 @pytest.mark.parametrize("N,K", [(256, 128), (64, 64), (128, 256), (32, 192)])
-def test_tensor_core_tile_primitives(gts, N, K):
-    """TMA (128-byte swizzle) + tcgen05.mma (TMEM accumulator) + tcgen05.ld
-    against the FP64 product of the same bf16-rounded inputs."""
+def test_tensor_core_tile_primitives(gts, N, K, a_tmem):
+    """TMA (128-byte swizzle) + tcgen05.mma (TMEM accumulator) + tcgen05.ld,
+    with A from shared memory or from TMEM (tcgen05.st, two coordinates per
+    column), against the FP64 product of the same bf16-rounded inputs."""
     rng = np.random.default_rng(N * 1000 + K)
     A = rng.standard_normal((128, K)).astype(np.float32)
     B = rng.standard_normal((N, K)).astype(np.float32)
-    D = gts.selftest_tc(A, B)
+    D = gts.selftest_tc(A, B, a_tmem=a_tmem)
     ref = _bf16(A).astype(np.float64) @ _bf16(B).astype(np.float64).T
     scale = np.abs(_bf16(A)).astype(np.float64) @ np.abs(_bf16(B)).astype(np.float64).T
     err = np.abs(D - ref)
