@@ -82,6 +82,23 @@ CUtensorMap make_row_map(const void *base, int64_t rows, int dim_p, int box_rows
     return m;
 }
 
+// The same rows as (64 coordinates, row, 64-coordinate panel): one box
+// {64, box_rows, dim_p / 64} lands as the panels one after another, each
+// box_rows x 128 bytes in the 128-byte swizzle -- a chunk's rows of all panels
+// in one copy.
+CUtensorMap make_panel_map(const void *base, int64_t rows, int dim_p, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[3] = {64, (cuuint64_t)(rows > 0 ? rows : 1), (cuuint64_t)(dim_p / 64)};
+    cuuint64_t strides[2] = {(cuuint64_t)dim_p * 2, 128};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, (cuuint32_t)(dim_p / 64)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    GTS_REQUIRE(r == CUDA_SUCCESS, GTS_ECUDA, "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string((int)r) + ")");
+    return m;
+}
+
 // ---------------------------------------------------------------- preparation
 
 // Split every float32 row into bf16 hi / lo parts (padded with zeros to
@@ -277,57 +294,54 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             const int nchunks = stop ? 1 : window ? (int)((a.nq + kNQ - 1) / kNQ) : (total + kNQ - 1) / kNQ;
             // window mode: this thread's column of window c (query c * kNQ +
             // ptid; threads past kNQ have none): its bitmap word and, for the
-            // dense last level, its leaf mask and query data -- loaded one
-            // window ahead, so the loads overlap the previous window's work
+            // dense last level, its leaf mask and query data; and lane j's
+            // copy of the window's word j, so that every warp sees on its own
+            // whether the window is empty.  Loaded one window ahead, so the
+            // loads overlap the previous window's work (no barrier runs in
+            // between: a barrier would wait for them).
             struct Col {
-                uint32_t word;
+                uint32_t word, wlane;
                 uint64_t dmask;
-                float thr, qn2;
+                float2 ab;   // the query's bound constants (alpha, beta)
                 int64_t seq;
             };
+            // (windows past the last one read as empty; every load is
+            // predicated, so nothing waits for a load before its use)
             auto load_col = [&](int c) {
                 Col w;
-                w.word = 0;
+                w.word = w.wlane = 0;
                 w.dmask = 0;
-                w.thr = w.qn2 = 0.f;
+                w.ab = make_float2(0.f, 0.f);
                 w.seq = 0;
                 const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
+                const int64_t wl = (int64_t)c * (kNQ / 32) + lane;
                 const int64_t q = (int64_t)c * kNQ + ptid;
-                if (ptid < kNQ && wi < a.nw) w.word = a.bits[(int64_t)it.x * a.nw + wi];
-                if (a.dmask && ptid < kNQ && q < a.nq) {
+                if (window && ptid < kNQ && wi < a.nw) w.word = a.bits[(int64_t)it.x * a.nw + wi];
+                if (window && lane < kNQ / 32 && wl < a.nw) w.wlane = a.bits[(int64_t)it.x * a.nw + wl];
+                if (window && a.dmask && ptid < kNQ && q < a.nq) {
                     w.dmask = a.dmask[(int64_t)it.x * a.nq + q];
-                    w.thr = a.thr_q[q];
-                    w.qn2 = a.qn2_q[q];
+                    w.ab = a.ab_q[q];
                     w.seq = a.seq_q[q];
                 }
                 return w;
             };
-            Col nxt;
-            if (window) nxt = load_col(0);
+            Col nxt = load_col(0);
             bool first_chunk = true;
             for (int c = 0; c < nchunks; ++c) {
                 const Col cur = nxt;
+                nxt = load_col(c + 1);
                 if (window) {
-                    if (c + 1 < nchunks) nxt = load_col(c + 1);
-                    const unsigned any = __ballot_sync(0xffffffffu, cur.word != 0u);
-                    if ((ptid & 31) == 0) sqid[ptid >> 5] = any ? 1 : 0;
-                    tc::named_sync(1, kProducers);
-                    int nonempty = 0;
-                    for (int i = 0; i < kProducers / 32; ++i) nonempty |= sqid[i];
-                    tc::named_sync(1, kProducers);
-                    if (!nonempty) continue;
+                    if (!__any_sync(0xffffffffu, cur.wlane != 0u)) continue;   // the same in every producer warp
                 }
                 const int sl = g % SM, sb = g % SB;
                 // B buffer sb: the MMAs of chunk g - SB are done (every phase
                 // of full[sl] up to chunk g - SM completed before that)
                 if (g >= SB && !tc::mbar_wait(&mma_done[(g - SB) % SM], ((g - SB) / SM) & 1)) fail(4);
                 if (window && ptid == 0) {
+                    // the window's query rows, every panel of hi and of lo
                     tc::mbar_expect_tx_only(&full[sl], (uint32_t)(2 * panels * bpanel));
-                    for (int pnl = 0; pnl < panels; ++pnl) {
-                        tc::tma_load_2d(sB + sb * bbuf + pnl * bpanel, &map_qh, pnl * 64, c * kNQ, &full[sl]);
-                        tc::tma_load_2d(sB + sb * bbuf + (panels + pnl) * bpanel, &map_ql, pnl * 64, c * kNQ,
-                                        &full[sl]);
-                    }
+                    tc::tma_load_3d(sB + sb * bbuf, &map_qh, 0, c * kNQ, 0, &full[sl]);
+                    tc::tma_load_3d(sB + sb * bbuf + panels * bpanel, &map_ql, 0, c * kNQ, 0, &full[sl]);
                 }
                 // slot sl (records, path distances, accumulator): chunk g - SM tested
                 if (g >= SM && !tc::mbar_wait(&epi_done[sl], ((g - SM) / SM) & 1)) fail(7);
@@ -343,13 +357,15 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                         const bool has = (cur.word >> (ptid & 31)) & 1u;
                         if (a.dmask) {
                             // dense last level: the record from the per-query arrays
+                            // (no threshold: only the table test reads it, and
+                            // dense chunks skip that test)
                             TileRec r;
                             r.q = (int32_t)((int64_t)c * kNQ + ptid);
-                            r.thr = cur.thr;
+                            r.thr = 0.f;
                             r.seq = cur.seq;
                             r.mask = has ? cur.dmask : 0ull;
-                            r.alpha = r.beta = 0.f;
-                            if (r.mask) bound_consts(r.thr, cur.qn2, a.cE1, a.cE2, r.alpha, r.beta);
+                            r.alpha = cur.ab.x;
+                            r.beta = cur.ab.y;
                             *mr = r;
                             ab[(ptid >> 1) * 4 + (ptid & 1)] = r.alpha;
                             ab[(ptid >> 1) * 4 + 2 + (ptid & 1)] = r.beta;
@@ -394,10 +410,13 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     *mdesc(sl) = dsc;
                 }
                 first_chunk = false;
-                // the copies have landed and are visible to the tensor cores
-                // (async proxy) before this thread arrives
-                cp_async_wait_all();
-                tc::fence_proxy_async_smem();
+                // gather mode: the copies have landed and are visible to the
+                // tensor cores (async proxy) before this thread arrives (window
+                // mode: B comes by TMA, the async proxy itself)
+                if (!window) {
+                    cp_async_wait_all();
+                    tc::fence_proxy_async_smem();
+                }
                 tc::mbar_arrive(&full[sl]);
                 ++g;
             }
@@ -409,6 +428,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kRows, kNQ);
             const uint32_t alo = tmem + (uint32_t)(a.dim_p / 2);   // A_lo
+            const uint64_t bdesc0 = tc::sdesc_k_sw128(tc::smem_u32(sB));
             uint32_t a_par = 0;
             int64_t last_issued = -1;
             for (uint32_t g = 0;; ++g) {
@@ -419,7 +439,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 }
                 const ChunkDesc dsc = *mdesc(sl);
                 if (dsc.stop || *sabort) break;
-                tc::fence_proxy_async_smem();
                 if (dsc.new_item) {
                     // the block's rows are in TMEM
                     if (!tc::mbar_wait(a_full, a_par)) {
@@ -429,14 +448,21 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     a_par ^= 1u;
                 }
                 tc::tc_fence_after();
-                const uint32_t bh = tc::smem_u32(sB + (g % SB) * bbuf), bl = bh + panels * bpanel;
+                // descriptors of B's k-steps: the start address field holds
+                // address / 16 in 14 bits, and shared addresses stay below
+                // 2^18, so an offset adds to the descriptor without carry
+                const uint64_t bh = bdesc0 + (uint64_t)(((g % SB) * bbuf) >> 4);
+                const uint64_t bl = bh + (uint64_t)((panels * bpanel) >> 4);
                 const uint32_t dt = tacc + (uint32_t)(sl * kNQ);
-                const int ksteps = a.dim_p / 16;
-                for (int s = 0; s < ksteps; ++s) {
-                    const uint32_t bo = (s >> 2) * bpanel + (s & 3) * 32;
-                    tc::mma_bf16_ts(dt, tmem + 8 * s, tc::sdesc_k_sw128(bh + bo), idesc, s > 0);
-                    tc::mma_bf16_ts(dt, tmem + 8 * s, tc::sdesc_k_sw128(bl + bo), idesc, 1u);
-                    tc::mma_bf16_ts(dt, alo + 8 * s, tc::sdesc_k_sw128(bh + bo), idesc, 1u);
+                for (int pnl = 0; pnl < panels; ++pnl) {
+                    const uint64_t po = (uint64_t)((pnl * bpanel) >> 4);
+                    const uint32_t ka = 32 * pnl;   // A columns of the panel (8 per k-step)
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        tc::mma_bf16_ts(dt, tmem + ka + 8 * s, bh + po + 2 * s, idesc, (pnl | s) != 0);
+                        tc::mma_bf16_ts(dt, tmem + ka + 8 * s, bl + po + 2 * s, idesc, 1u);
+                        tc::mma_bf16_ts(dt, alo + ka + 8 * s, bh + po + 2 * s, idesc, 1u);
+                    }
                 }
                 tc::mma_commit(&mma_done[sl]);
                 last_issued = g;
@@ -628,6 +654,16 @@ __device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, fl
     const float t = thr * 1.0000039f;
     alpha = __fmul_ru(cE1 + 2.f * cE2, qn) * 1.000001f;
     beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(cE2 - 1.f, qn2)) + 4.f * 1.1920929e-7f * (t * t + qn2);
+}
+
+// the per-query bound constants (alpha, beta) of the dense last level
+__global__ void k_query_consts(const float *__restrict__ thr, const float *__restrict__ qn2, int64_t nq, float cE1,
+                               float cE2, float2 *__restrict__ ab) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        float al, be;
+        bound_consts(thr[q], qn2 ? qn2[q] : 0.f, cE1, cE2, al, be);
+        ab[q] = make_float2(al, be);
+    }
 }
 
 __global__ void k_node_scatter(const int32_t *__restrict__ eq, const int32_t *__restrict__ enode,
@@ -976,13 +1012,20 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     // the batch's split query rows, for window-mode chunks (TMA, 128 rows)
-    const CUtensorMap map_qh = make_row_map(tq.Qh, tq.nq, c.dim_p, nq_chunk);
-    const CUtensorMap map_ql = make_row_map(tq.Ql, tq.nq, c.dim_p, nq_chunk);
+    const CUtensorMap map_qh = make_panel_map(tq.Qh, tq.nq, c.dim_p, nq_chunk);
+    const CUtensorMap map_ql = make_panel_map(tq.Ql, tq.nq, c.dim_p, nq_chunk);
     DBuf<int> counter(1, st), status(1, st);
     DBuf<unsigned long long> count(1, st);
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
     float cE1 = 0.f, cE2 = 0.f;
     tc_bound_coeffs(c.dim_p, cE1, cE2);
+    // dense last level: the queries' bound constants, once per batch
+    DBuf<float2> abq(rg.dmask ? tq.nq : 1, st);
+    if (rg.dmask) {
+        k_query_consts<<<nblk(tq.nq), 256, 0, st>>>(tq.thr, tq.qn2, tq.nq, cE1, cE2, abq.get());
+        check_launch("query bound constants");
+        ++*launches;
+    }
     for (int attempt = 0; attempt < 2; ++attempt) {
         out_q.alloc(cap, st);
         out_row.alloc(cap, st);
@@ -1027,8 +1070,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.nw = rg.nw;
         a.nq = tq.nq;
         a.dmask = rg.dmask;
-        a.thr_q = tq.thr;
-        a.qn2_q = tq.qn2;
+        a.ab_q = abq.get();
         a.seq_q = tq.qseq;
         kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(map_qh, map_ql, a);
         ++*launches;

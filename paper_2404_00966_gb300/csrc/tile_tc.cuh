@@ -51,7 +51,7 @@ struct TileArgs {
     // dense last level: no records; column q of node p takes its leaf mask
     // from dmask[p * nq + q] and its query data from the per-query arrays
     const uint64_t *dmask;    // null: records
-    const float *thr_q, *qn2_q;
+    const float2 *ab_q;       // per query: the bound constants (alpha, beta)
     const int64_t *seq_q;
 };
 
