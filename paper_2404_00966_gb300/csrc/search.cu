@@ -402,27 +402,53 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             bd[i] = __int_as_float(0x7f800000);
             bn[i] = -1;
         }
-        for (int j = 0; j < d.F; ++j) {
-            const int64_t c = node * d.F + j;
-            const int64_t g = lo_off.v[l] + c;
-            if (d.nsize[g] == 0) continue;
-            const int32_t prow = d.npiv[g];
-            const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
-            const float dq = L2 ? sqrtf(sq) : sq;
-            if (d.row_del[prow] > s)
-                warp_tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow], lane);
-            if (dq < bd[kProbeNodes - 1]) {
-                float vd = dq;
-                int64_t vn = c;
+        // the children 32 at a time, a child per lane: their pivot distances
+        // are computed together, then taken in child order
+        for (int j0 = 0; j0 < d.F; j0 += 32) {
+            const int j = j0 + lane;
+            float dq = 0.f;
+            bool live = false, vis = false;
+            int64_t id = 0;
+            if (j < d.F) {
+                const int64_t g = lo_off.v[l] + node * d.F + j;
+                if (d.nsize[g] != 0) {
+                    const int32_t prow = d.npiv[g];
+                    const float sq = lane_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim);
+                    dq = L2 ? sqrtf(sq) : sq;
+                    live = true;
+                    vis = d.row_del[prow] > s;
+                    if (vis) id = d.row_id[prow];
+                }
+            }
+            // the visible pivots into the threshold list (a register copy of
+            // its K-th bound skips the pivots that cannot enter it)
+            const double ub = (double)dq * up + (double)kAbsFloor;
+            const double kth = n >= K ? D[K - 1] : 0.0;
+            unsigned bal = __ballot_sync(0xffffffffu, vis && (n < K || ub <= kth));
+            while (bal) {
+                const int src = __ffs(bal) - 1;
+                bal &= bal - 1;
+                warp_tau_insert(D, I, n, K, __shfl_sync(0xffffffffu, ub, src), __shfl_sync(0xffffffffu, id, src),
+                                lane);
+            }
+            // the nearest children, in child order (ties keep the earlier child)
+            unsigned lv = __ballot_sync(0xffffffffu, live);
+            while (lv) {
+                const int src = __ffs(lv) - 1;
+                lv &= lv - 1;
+                float vd = __shfl_sync(0xffffffffu, dq, src);
+                int64_t vn = node * d.F + j0 + src;
+                if (vd < bd[kProbeNodes - 1]) {
 #pragma unroll
-                for (int i = 0; i < kProbeNodes; ++i) {
-                    if (vd < bd[i]) {
-                        const float td = bd[i];
-                        const int64_t tn = bn[i];
-                        bd[i] = vd;
-                        bn[i] = vn;
-                        vd = td;
-                        vn = tn;
+                    for (int i = 0; i < kProbeNodes; ++i) {
+                        if (vd < bd[i]) {
+                            const float td = bd[i];
+                            const int64_t tn = bn[i];
+                            bd[i] = vd;
+                            bn[i] = vn;
+                            vd = td;
+                            vn = tn;
+                        }
                     }
                 }
             }
@@ -1227,6 +1253,8 @@ __global__ void k_cm_scatter(const int32_t *__restrict__ eq, const int32_t *__re
         cm[(int64_t)enode[e] * nq + eq[e]] = cmask[e - e0];
 }
 
+constexpr int kTauUnroll = 4;   // pivots per lane whose loads k_tau_dense issues together
+
 // member(node, q): the node's bit in its parent's child mask for q
 __device__ __forceinline__ bool dense_member(const uint64_t *cm, int64_t node, int64_t q, int64_t nq, int F) {
     return (cm[(node / F) * nq + q] >> (node % F)) & 1ull;
@@ -1247,30 +1275,48 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
         int n = tk_n[q];
         const int64_t s = d.qseq[q];
         const double up = 1.0 + 2.0 * (double)d.rel;
-        for (int64_t p0 = 0; p0 < P; p0 += 32) {
-            const int64_t p = p0 + lane;
-            bool cand = false;
-            double ub = 0.0;
-            int64_t id = 0;
-            if (p < P && dense_member(cm, p, q, nq, d.F)) {
-                ub = (double)D[q * P + p] * up + (double)kAbsFloor;
-                // the bound test first: most pivots fail it, and then the
-                // pivot's delete mark and id are never read
-                if ((n < K) || ub <= Dl[K - 1]) {
-                    const int32_t prow = d.npiv[lvl_base + p];
-                    if (prow >= 0 && row_visible(d, prow, s)) {
-                        id = d.row_id[prow];
-                        cand = (n < K) || ub < Dl[K - 1] || (ub == Dl[K - 1] && id < Il[K - 1]);
+        // the list's current K-th bound, kept in a register (read again after inserts)
+        double kth = n >= K ? Dl[K - 1] : 0.0;
+        for (int64_t p0 = 0; p0 < P; p0 += 32 * kTauUnroll) {
+            // kTauUnroll pivots per lane: their membership and distance loads
+            // are issued together, then they are tested in pivot order
+            bool mem[kTauUnroll];
+            float dv[kTauUnroll];
+#pragma unroll
+            for (int u = 0; u < kTauUnroll; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                mem[u] = p < P && dense_member(cm, p, q, nq, d.F);
+                dv[u] = p < P ? D[q * P + p] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kTauUnroll; ++u) {
+                const int64_t p = p0 + 32 * u + lane;
+                bool cand = false;
+                double ub = 0.0;
+                int64_t id = 0;
+                if (mem[u]) {
+                    ub = (double)dv[u] * up + (double)kAbsFloor;
+                    // the bound test first: most pivots fail it, and then the
+                    // pivot's delete mark and id are never read
+                    if ((n < K) || ub <= kth) {
+                        const int32_t prow = d.npiv[lvl_base + p];
+                        if (prow >= 0 && row_visible(d, prow, s)) {
+                            id = d.row_id[prow];
+                            cand = (n < K) || ub < kth || (ub == kth && id < Il[K - 1]);
+                        }
                     }
                 }
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, cand);
-            while (bal) {
-                const int src = __ffs(bal) - 1;
-                bal &= bal - 1;
-                const double u = __shfl_sync(0xffffffffu, ub, src);
-                const int64_t iid = __shfl_sync(0xffffffffu, id, src);
-                warp_tau_insert(Dl, Il, n, K, u, iid, lane);
+                unsigned bal = __ballot_sync(0xffffffffu, cand);
+                if (bal) {
+                    while (bal) {
+                        const int src = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const double uu = __shfl_sync(0xffffffffu, ub, src);
+                        const int64_t iid = __shfl_sync(0xffffffffu, id, src);
+                        warp_tau_insert(Dl, Il, n, K, uu, iid, lane);
+                    }
+                    kth = n >= K ? Dl[K - 1] : 0.0;
+                }
             }
         }
         if (lane == 0) {
@@ -1298,46 +1344,67 @@ __global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int6
 // Leaf masks of every member pair (Lemma 1 / 2 on the node's children
 // intervals, the same test as the entry kernels), the node x query bitmap of
 // the pairs with a surviving leaf, and the counts of member pairs and of
-// pairs with a surviving leaf.  Block over (node, 256 queries).
+// pairs with a surviving leaf.  A block takes one node at a time and all of
+// its queries, 256 per step.
 __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t *__restrict__ cm, int64_t P,
                              int64_t nq, int64_t lvl_next, const float *__restrict__ thr_q,
                              uint64_t *__restrict__ M, uint32_t *__restrict__ bits, int64_t nw,
                              unsigned long long *__restrict__ counts) {
-    __shared__ float slo[64], shi[64];   // the node's children intervals (+inf / -inf: empty child)
+    // the node's children: (lo, hi, |hi|) and the mask of the non-empty ones
+    __shared__ float4 siv[64];
+    __shared__ unsigned long long s_ne;
     const int lane = threadIdx.x & 31;
-    const int64_t qchunks = (nq + 255) / 256;
+    const float epsc = d.epsc;
     unsigned long long nmem = 0, nlive = 0;
-    int64_t cur = -1;
-    for (int64_t it = blockIdx.x; it < P * qchunks; it += gridDim.x) {
-        const int64_t p = it / qchunks;
-        const int64_t q = (it - p * qchunks) * 256 + threadIdx.x;
-        if (p != cur) {   // block-uniform
-            __syncthreads();
-            if (threadIdx.x < d.F) {
-                const int64_t c = lvl_next + p * d.F + threadIdx.x;
-                const bool ne = d.nsize[c] > 0;
-                slo[threadIdx.x] = ne ? d.nlo[c] : __int_as_float(0x7f800000);
-                shi[threadIdx.x] = ne ? d.nhi[c] : __int_as_float(0xff800000);
+    // one node per block iteration, all of its queries: the children are read once
+    for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
+        __syncthreads();   // the previous node's children are no longer read
+        if (threadIdx.x == 0) s_ne = 0ull;
+        __syncthreads();
+        if (threadIdx.x < d.F) {
+            const int64_t c = lvl_next + p * d.F + threadIdx.x;
+            const bool ne = d.nsize[c] > 0;
+            const float lo = ne ? d.nlo[c] : 0.f, hi = ne ? d.nhi[c] : 0.f;
+            siv[threadIdx.x] = make_float4(lo, hi, fabsf(hi), 0.f);
+            if (ne) atomicOr(&s_ne, 1ull << threadIdx.x);
+        }
+        __syncthreads();
+        const uint64_t nonempty = s_ne;
+        for (int64_t q0 = 0; q0 < nq; q0 += blockDim.x) {
+            const int64_t q = q0 + threadIdx.x;
+            const bool member = q < nq && dense_member(cm, p, q, nq, d.F);
+            uint64_t m = 0;
+            if (member) {
+                const float dq = DT[p * nq + q];
+                const float thr = thr_q[q];
+                // interval_hit for every child, its query terms formed once
+                // (the same operations in the same order)
+                const float u = dq - thr, sq = dq + thr;
+                if (epsc > 0.f) {
+#pragma unroll 4
+                    for (int j = 0; j < d.F; ++j) {
+                        const float4 iv = siv[j];
+                        const float eps = epsc * (sq + iv.z);
+                        m |= (uint64_t)((u <= iv.y + eps) & (sq + eps >= iv.x)) << j;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = 0; j < d.F; ++j) {
+                        const float4 iv = siv[j];
+                        m |= (uint64_t)((u <= iv.y + 0.f) & (sq + 0.f >= iv.x)) << j;
+                    }
+                }
+                m &= nonempty;
             }
-            __syncthreads();
-            cur = p;
-        }
-        const bool member = q < nq && dense_member(cm, p, q, nq, d.F);
-        uint64_t m = 0;
-        if (member) {
-            const float dq = DT[p * nq + q];
-            const float thr = thr_q[q];
-            for (int j = 0; j < d.F; ++j)
-                if (shi[j] >= slo[j] && interval_hit(dq, thr, slo[j], shi[j], d.epsc)) m |= 1ull << j;
-        }
-        if (q < nq) M[p * nq + q] = m;
-        const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
-        const unsigned mem = __ballot_sync(0xffffffffu, member);
-        const int64_t w = (q - lane) >> 5;   // the warp's word
-        if (lane == 0 && w < nw) bits[p * nw + w] = live;
-        if (lane == 0) {
-            nmem += __popc(mem);
-            nlive += __popc(live);
+            if (q < nq) M[p * nq + q] = m;
+            const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
+            const unsigned mem = __ballot_sync(0xffffffffu, member);
+            const int64_t w = (q - lane) >> 5;   // the warp's word
+            if (lane == 0 && w < nw) bits[p * nw + w] = live;
+            if (lane == 0) {
+                nmem += __popc(mem);
+                nlive += __popc(live);
+            }
         }
     }
     if (lane == 0) {
@@ -1920,8 +1987,7 @@ struct Runner {
         {
             dim3 tb(32, 8), tg((unsigned)((P + 31) / 32), (unsigned)((nq + 31) / 32));
             k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get());
-            const int64_t items = P * ((nq + 255) / 256);
-            k_leaf_dense<<<(unsigned)std::min<int64_t>(items, (int64_t)max_blocks * 4), 256, 0, st>>>(
+            k_leaf_dense<<<(unsigned)std::min<int64_t>(P, (int64_t)max_blocks), 256, 0, st>>>(
                 d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), M.get(), rg.bits.get(), rg.nw,
                 cnt.get());
         }
