@@ -366,11 +366,12 @@ __device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_
 // computes the distances to the rows (up to `cap` in all) of the kProbeNodes
 // nodes with the nearest pivots.  Every visible object so evaluated enters
 // the query's threshold list, so tau_q starts at (an upper bound of) the k-th
-// smallest of them instead of +inf.
+// smallest of them instead of +inf.  The last-level node the path ended in is
+// the query's key: queries with equal or nearby keys lie in the same region.
 template <bool L2>
 __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id, int32_t *tk_n,
-                            float *tau) {
+                            float *tau, int32_t *__restrict__ key) {
     const int lane = threadIdx.x & 31;
     const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (q >= nq) return;
@@ -471,6 +472,7 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
     if (lane == 0) {
         tk_n[q] = n;
         tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+        if (key) key[q] = (int32_t)node;   // where the path ended: a locality key for the query
     }
 }
 
@@ -1326,13 +1328,14 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
     }
 }
 
-// out[c * rows + r] = in[r * cols + c]
-__global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int64_t cols, float *__restrict__ out) {
+// out[c * rows + r] = in[sel(r) * cols + c], sel(r) = rowsel[r] (or r)
+__global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int64_t cols, float *__restrict__ out,
+                                const int32_t *__restrict__ rowsel) {
     __shared__ float tile[32][33];
     const int64_t tr = (int64_t)blockIdx.y * 32, tc = (int64_t)blockIdx.x * 32;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int64_t r = tr + i, c = tc + threadIdx.x;
-        tile[i][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? in[(rowsel ? (int64_t)rowsel[r] : r) * cols + c] : 0.f;
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -1344,12 +1347,13 @@ __global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int6
 // Leaf masks of every member pair (Lemma 1 / 2 on the node's children
 // intervals, the same test as the entry kernels), the node x query bitmap of
 // the pairs with a surviving leaf, and the counts of member pairs and of
-// pairs with a surviving leaf.  A block takes one node at a time and all of
+// pairs with a surviving leaf.  Queries are taken in column order: position i
+// is query perm[i] (DT, M and the bitmap are in position order).  A block takes one node at a time and all of
 // its queries, 256 per step.
 __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t *__restrict__ cm, int64_t P,
                              int64_t nq, int64_t lvl_next, const float *__restrict__ thr_q,
-                             uint64_t *__restrict__ M, uint32_t *__restrict__ bits, int64_t nw,
-                             unsigned long long *__restrict__ counts) {
+                             const int32_t *__restrict__ perm, uint64_t *__restrict__ M,
+                             uint32_t *__restrict__ bits, int64_t nw, unsigned long long *__restrict__ counts) {
     // the node's children: (lo, hi, |hi|) and the mask of the non-empty ones
     __shared__ float4 siv[64];
     __shared__ unsigned long long s_ne;
@@ -1371,12 +1375,13 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
         __syncthreads();
         const uint64_t nonempty = s_ne;
         for (int64_t q0 = 0; q0 < nq; q0 += blockDim.x) {
-            const int64_t q = q0 + threadIdx.x;
-            const bool member = q < nq && dense_member(cm, p, q, nq, d.F);
+            const int64_t q = q0 + threadIdx.x;                          // column position
+            const int64_t qq = q < nq && perm ? (int64_t)perm[q] : q;    // its query
+            const bool member = q < nq && dense_member(cm, p, qq, nq, d.F);
             uint64_t m = 0;
             if (member) {
                 const float dq = DT[p * nq + q];
-                const float thr = thr_q[q];
+                const float thr = thr_q[qq];
                 // interval_hit for every child, its query terms formed once
                 // (the same operations in the same order)
                 const float u = dq - thr, sq = dq + thr;
@@ -1425,6 +1430,11 @@ __global__ void k_range_pack(const int32_t *__restrict__ cq, const int32_t *__re
         rkey[o] = ((uint64_t)(uint32_t)cq[c] << 32) | (uint64_t)(uint32_t)row_oid(d, crow[c]);
         rdist[o] = cdist[c];
     }
+}
+
+__global__ void k_iota_i32(int32_t *a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
 }
 
 __global__ void k_u8_to_i64(const uint8_t *a, int64_t n, int64_t *b) {
@@ -1597,6 +1607,8 @@ struct Runner {
     int64_t st_dense_last = 0;
     DBuf<uint8_t> tcQh, tcQl;   // the batch's queries as split bf16 rows (tensor-core path)
     DBuf<float> tcqn2;
+    DBuf<int32_t> qkey;         // kNN: the probe's last-level node per query (qkey_ok once written)
+    bool qkey_ok = false;
 
     Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
         : ix(i), qb(b), knn(k), budget(bud), st(s) {
@@ -1975,6 +1987,31 @@ struct Runner {
             clk.end();
             check_launch("dense knn threshold");
         }
+        // kNN: the tiles take the queries in the order of their probe keys, so
+        // the windows of consecutive columns hold queries of one region (a
+        // node's live columns cluster and whole windows drop out)
+        DBuf<int32_t> perm;
+        DBuf<uint8_t> pQh, pQl;
+        DBuf<float> pqn2;
+        if (knn && qkey_ok && nq > 1) {
+            clk.begin(GTS_STAGE_OTHER, 5);
+            DBuf<int32_t> idx(nq, st), key2(nq, st);
+            perm.alloc(nq, st);
+            k_iota_i32<<<nblocks(nq, kT), kT, 0, st>>>(idx.get(), nq);
+            // keys: last-level node indices in [0, P) (a stable sort keeps
+            // equal keys in query order)
+            int kbits = 1;
+            while (kbits < 31 && ((int64_t)1 << kbits) < P) ++kbits;
+            size_t tb = 0;
+            cub::DeviceRadixSort::SortPairs(nullptr, tb, qkey.get(), key2.get(), idx.get(), perm.get(), nq, 0, kbits,
+                                            st);
+            DBuf<uint8_t> tmp(tb > 0 ? tb : 1, st);
+            GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, qkey.get(), key2.get(), idx.get(), perm.get(), nq,
+                                                     0, kbits, st));
+            tc_split_queries(d.Q, nq, d.dim, ix->tree.tc.dim_p, pQh, pQl, pqn2, st, perm.get());
+            clk.end();
+            check_launch("query order");
+        }
         DBuf<float> DT(nq * P, st);
         DBuf<uint64_t> M(nq * P, st);
         TcRegroup rg;
@@ -1986,10 +2023,10 @@ struct Runner {
         clk.begin(GTS_STAGE_PIVOT_DIST, 2);
         {
             dim3 tb(32, 8), tg((unsigned)((P + 31) / 32), (unsigned)((nq + 31) / 32));
-            k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get());
+            k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get(), perm.get());
             k_leaf_dense<<<(unsigned)std::min<int64_t>(P, (int64_t)max_blocks), 256, 0, st>>>(
-                d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), M.get(), rg.bits.get(), rg.nw,
-                cnt.get());
+                d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), perm.get(), M.get(), rg.bits.get(),
+                rg.nw, cnt.get());
         }
         clk.end();
         check_launch("dense leaf masks");
@@ -2002,6 +2039,11 @@ struct Runner {
         tc_dense_items(ix->tree, nq, M.get(), rg, st);
         clk.end();
         TcQuery tq = tc_query_base();
+        if (perm.get()) {
+            tq.perm = perm.get();
+            tq.Qh = (const __nv_bfloat16 *)pQh.get();
+            tq.Ql = (const __nv_bfloat16 *)pQl.get();
+        }
         tc_finish(tq, rg);
     }
 
@@ -2478,6 +2520,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.bi.alloc(ktot, st);
         R.tk_n.alloc(nq, st);
         R.bn.alloc(nq, st);
+        R.qkey.alloc(nq, st);
         GTS_CUDA(cudaMemsetAsync(R.tk_n.get(), 0, nq * 4, st));
         GTS_CUDA(cudaMemsetAsync(R.bn.get(), 0, nq * 4, st));
         R.clk.begin(GTS_STAGE_OTHER);
@@ -2497,11 +2540,12 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         if (t.metric == GTS_L2)
             k_probe_vec<true><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),
                                                                           R.tk_d.get(), R.tk_id.get(), R.tk_n.get(),
-                                                                          R.thr.get());
+                                                                          R.thr.get(), R.qkey.get());
         else
             k_probe_vec<false><<<nblocks(nq, kWarpsPerBlock), kT, 0, st>>>(d, lo_off, nq, cap, qb.k, R.koff.get(),
                                                                            R.tk_d.get(), R.tk_id.get(), R.tk_n.get(),
-                                                                           R.thr.get());
+                                                                           R.thr.get(), R.qkey.get());
+        R.qkey_ok = true;
         R.clk.end();
         check_launch("knn probe");
         R.st_pivots += nq * (int64_t)t.h;

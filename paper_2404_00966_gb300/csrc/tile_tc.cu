@@ -102,16 +102,18 @@ CUtensorMap make_panel_map(const void *base, int64_t rows, int dim_p, int box_ro
 // ---------------------------------------------------------------- preparation
 
 // Split every float32 row into bf16 hi / lo parts (padded with zeros to
-// dim_p columns) and its squared norm, summed in FP64 and rounded once.
+// dim_p columns) and its squared norm, summed in FP64 and rounded once
+// (output row i from input row sel[i] when sel is given).
 __global__ void k_split_rows(const float *__restrict__ X, int dim, int dim_p, int64_t n,
                              __nv_bfloat16 *__restrict__ Xh, __nv_bfloat16 *__restrict__ Xl,
-                             float *__restrict__ n2) {
+                             float *__restrict__ n2, const int32_t *__restrict__ sel) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+        const int64_t src = sel ? (int64_t)sel[row] : row;   // output row `row` takes input row `src`
         double s = 0.0;
         for (int k = lane; k < dim_p; k += 32) {
-            const float v = k < dim ? X[row * dim + k] : 0.f;
+            const float v = k < dim ? X[src * dim + k] : 0.f;
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
             const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
             Xh[row * dim_p + k] = h;
@@ -304,6 +306,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 uint64_t dmask;
                 float2 ab;   // the query's bound constants (alpha, beta)
                 int64_t seq;
+                int32_t qid; // the query of the column
             };
             // (windows past the last one read as empty; every load is
             // predicated, so nothing waits for a load before its use)
@@ -313,6 +316,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 w.dmask = 0;
                 w.ab = make_float2(0.f, 0.f);
                 w.seq = 0;
+                w.qid = (int32_t)((int64_t)c * kNQ + ptid);
                 const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
                 const int64_t wl = (int64_t)c * (kNQ / 32) + lane;
                 const int64_t q = (int64_t)c * kNQ + ptid;
@@ -322,6 +326,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     w.dmask = a.dmask[(int64_t)it.x * a.nq + q];
                     w.ab = a.ab_q[q];
                     w.seq = a.seq_q[q];
+                    if (a.qperm) w.qid = a.qperm[q];
                 }
                 return w;
             };
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                             // (no threshold: only the table test reads it, and
                             // dense chunks skip that test)
                             TileRec r;
-                            r.q = (int32_t)((int64_t)c * kNQ + ptid);
+                            r.q = cur.qid;
                             r.thr = 0.f;
                             r.seq = cur.seq;
                             r.mask = has ? cur.dmask : 0ull;
@@ -656,13 +661,17 @@ __device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, fl
     beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(cE2 - 1.f, qn2)) + 4.f * 1.1920929e-7f * (t * t + qn2);
 }
 
-// the per-query bound constants (alpha, beta) of the dense last level
-__global__ void k_query_consts(const float *__restrict__ thr, const float *__restrict__ qn2, int64_t nq, float cE1,
-                               float cE2, float2 *__restrict__ ab) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+// the bound constants (alpha, beta) and the sequence number of the query in
+// each column position of the dense last level (query perm[i] at position i)
+__global__ void k_query_consts(const float *__restrict__ thr, const float *__restrict__ qn2,
+                               const int64_t *__restrict__ qseq, const int32_t *__restrict__ perm, int64_t nq,
+                               float cE1, float cE2, float2 *__restrict__ ab, int64_t *__restrict__ seq) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = perm ? (int64_t)perm[i] : i;
         float al, be;
         bound_consts(thr[q], qn2 ? qn2[q] : 0.f, cE1, cE2, al, be);
-        ab[q] = make_float2(al, be);
+        ab[i] = make_float2(al, be);
+        seq[i] = qseq[q];
     }
 }
 
@@ -847,7 +856,7 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
     c.Xl.alloc((size_t)t.n * c.dim_p * 2, st);
     c.xn2.alloc(t.n, st);
     k_split_rows<<<nblk(t.n * 32), 256, 0, st>>>(t.X.get(), t.dim, c.dim_p, t.n, (__nv_bfloat16 *)c.Xh.get(),
-                                                (__nv_bfloat16 *)c.Xl.get(), c.xn2.get());
+                                                (__nv_bfloat16 *)c.Xl.get(), c.xn2.get(), nullptr);
     check_launch("split rows");
     GTS_CUDA(cudaStreamSynchronize(st));
     c.Xh.persist();
@@ -857,13 +866,13 @@ void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
 }
 
 void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
-                      DBuf<float> &qn2, cudaStream_t st) {
+                      DBuf<float> &qn2, cudaStream_t st, const int32_t *sel) {
     Qh.alloc((size_t)(nq > 0 ? nq : 1) * dim_p * 2, st);
     Ql.alloc((size_t)(nq > 0 ? nq : 1) * dim_p * 2, st);
     qn2.alloc(nq > 0 ? nq : 1, st);
     if (nq > 0)
         k_split_rows<<<nblk(nq * 32), 256, 0, st>>>(Q, dim, dim_p, nq, (__nv_bfloat16 *)Qh.get(),
-                                                   (__nv_bfloat16 *)Ql.get(), qn2.get());
+                                                   (__nv_bfloat16 *)Ql.get(), qn2.get(), sel);
     check_launch("split queries");
 }
 
@@ -1019,10 +1028,13 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
     float cE1 = 0.f, cE2 = 0.f;
     tc_bound_coeffs(c.dim_p, cE1, cE2);
-    // dense last level: the queries' bound constants, once per batch
+    // dense last level: the queries' bound constants and sequence numbers in
+    // column order, once per batch
     DBuf<float2> abq(rg.dmask ? tq.nq : 1, st);
+    DBuf<int64_t> seqp(rg.dmask ? tq.nq : 1, st);
     if (rg.dmask) {
-        k_query_consts<<<nblk(tq.nq), 256, 0, st>>>(tq.thr, tq.qn2, tq.nq, cE1, cE2, abq.get());
+        k_query_consts<<<nblk(tq.nq), 256, 0, st>>>(tq.thr, tq.qn2, tq.qseq, tq.perm, tq.nq, cE1, cE2, abq.get(),
+                                                    seqp.get());
         check_launch("query bound constants");
         ++*launches;
     }
@@ -1071,7 +1083,8 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.nq = tq.nq;
         a.dmask = rg.dmask;
         a.ab_q = abq.get();
-        a.seq_q = tq.qseq;
+        a.seq_q = seqp.get();
+        a.qperm = tq.perm;
         kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(map_qh, map_ql, a);
         ++*launches;
         check_launch("tensor-core tile");

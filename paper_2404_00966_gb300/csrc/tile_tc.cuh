@@ -51,7 +51,8 @@ struct TileArgs {
     // dense last level: no records; column q of node p takes its leaf mask
     // from dmask[p * nq + q] and its query data from the per-query arrays
     const uint64_t *dmask;    // null: records
-    const float2 *ab_q;       // per query: the bound constants (alpha, beta)
+    const float2 *ab_q;       // per position: the query's bound constants (alpha, beta)
+    const int32_t *qperm;     // position -> query (null: the same)
     const int64_t *seq_q;
 };
 
@@ -62,6 +63,10 @@ struct TcQuery {
     const float *qn2 = nullptr;                          // |q|^2 (null: not needed, records get 0)
     float cE1 = 0.f, cE2 = 0.f;                          // bf16 error-bound coefficients (tc_bound_coeffs)
     int chunk = 128;                                     // tensor-core tiles up to 128 columns: 128 or 96 queries
+    // dense last level: the tiles' column order.  Column (position) i is query
+    // perm[i]; Qh / Ql are then in position order, qn2, qseq and thr in query
+    // order.  Null: position = query.
+    const int32_t *perm = nullptr;
     const int32_t *eq = nullptr, *enode = nullptr;
     const float *path = nullptr;
     const uint64_t *emask = nullptr;
@@ -97,8 +102,9 @@ bool tc_supported(const Tree &t);
 void tc_bound_coeffs(int dim_p, float &cE1, float &cE2);
 void tc_prepare(Tree &t, TcCache &c, cudaStream_t st);
 // split a batch's queries into bf16 hi / lo rows [nq, dim_p] and squared norms
+// (sel: row i of the output is query sel[i]; null: query i)
 void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8_t> &Qh, DBuf<uint8_t> &Ql,
-                      DBuf<float> &qn2, cudaStream_t st);
+                      DBuf<float> &qn2, cudaStream_t st, const int32_t *sel = nullptr);
 // whether tc_regroup counts entries per node itself (a node x query bitmap),
 // so the caller need not
 bool regroup_uses_bits(const Tree &t, int64_t nq);
