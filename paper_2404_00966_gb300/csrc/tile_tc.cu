@@ -291,37 +291,33 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
             const int total = it.z;
             const bool window = !stop && (it.w & kWindowItem) != 0;
             const int rbk = it.w & (kWindowItem - 1);
-            // gather mode: chunks of the node's records; window mode: windows of
-            // kNQ consecutive query ids (those without an entry are skipped)
-            const int nchunks = stop ? 1 : window ? (int)((a.nq + kNQ - 1) / kNQ) : (total + kNQ - 1) / kNQ;
+            // gather mode: chunks of the node's records; window mode: the node's
+            // non-empty windows of kNQ consecutive query ids (from its list)
+            const int32_t *wl = window ? a.wlist + (int64_t)it.x * a.nwin : nullptr;
+            const int nchunks = stop ? 1 : window ? a.wcount[it.x] : (total + kNQ - 1) / kNQ;
             // window mode: this thread's column of window c (query c * kNQ +
             // ptid; threads past kNQ have none): its bitmap word and, for the
-            // dense last level, its leaf mask and query data; and lane j's
-            // copy of the window's word j, so that every warp sees on its own
-            // whether the window is empty.  Loaded one window ahead, so the
-            // loads overlap the previous window's work (no barrier runs in
-            // between: a barrier would wait for them).
+            // dense last level, its leaf mask and query data.  Loaded one
+            // window ahead, so the loads overlap the previous window's work
+            // (no barrier runs in between: a barrier would wait for them).
             struct Col {
-                uint32_t word, wlane;
+                uint32_t word;
                 uint64_t dmask;
                 float2 ab;   // the query's bound constants (alpha, beta)
                 int64_t seq;
                 int32_t qid; // the query of the column
             };
-            // (windows past the last one read as empty; every load is
-            // predicated, so nothing waits for a load before its use)
+            // (every load is predicated, so nothing waits for a load before its use)
             auto load_col = [&](int c) {
                 Col w;
-                w.word = w.wlane = 0;
+                w.word = 0;
                 w.dmask = 0;
                 w.ab = make_float2(0.f, 0.f);
                 w.seq = 0;
                 w.qid = (int32_t)((int64_t)c * kNQ + ptid);
                 const int64_t wi = (int64_t)c * (kNQ / 32) + (ptid >> 5);
-                const int64_t wl = (int64_t)c * (kNQ / 32) + lane;
                 const int64_t q = (int64_t)c * kNQ + ptid;
                 if (window && ptid < kNQ && wi < a.nw) w.word = a.bits[(int64_t)it.x * a.nw + wi];
-                if (window && lane < kNQ / 32 && wl < a.nw) w.wlane = a.bits[(int64_t)it.x * a.nw + wl];
                 if (window && a.dmask && ptid < kNQ && q < a.nq) {
                     w.dmask = a.dmask[(int64_t)it.x * a.nq + q];
                     w.ab = a.ab_q[q];
@@ -330,14 +326,17 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                 }
                 return w;
             };
-            Col nxt = load_col(0);
+            // the window of chunk k + 1 and of chunk k + 2 are read ahead
+            int wnext = (window && nchunks > 0) ? wl[0] : 0;
+            Col nxt = load_col(wnext);
+            int wnn = (window && nchunks > 1) ? wl[1] : 0;
             bool first_chunk = true;
-            for (int c = 0; c < nchunks; ++c) {
+            for (int k = 0; k < nchunks; ++k) {
+                const int c = window ? wnext : k;   // window index, or chunk of the node's records
                 const Col cur = nxt;
-                nxt = load_col(c + 1);
-                if (window) {
-                    if (!__any_sync(0xffffffffu, cur.wlane != 0u)) continue;   // the same in every producer warp
-                }
+                wnext = wnn;
+                nxt = load_col(wnext);
+                wnn = (window && k + 2 < nchunks) ? wl[k + 2] : 0;
                 const int sl = g % SM, sb = g % SB;
                 // B buffer sb: the MMAs of chunk g - SB are done (every phase
                 // of full[sl] up to chunk g - SM completed before that)
@@ -659,6 +658,30 @@ __device__ __forceinline__ void bound_consts(float thr, float qn2, float cE1, fl
     const float t = thr * 1.0000039f;
     alpha = __fmul_ru(cE1 + 2.f * cE2, qn) * 1.000001f;
     beta = __fadd_ru(__fmul_ru(t, t), __fmul_ru(cE2 - 1.f, qn2)) + 4.f * 1.1920929e-7f * (t * t + qn2);
+}
+
+// For every node, its non-empty windows (windows of wpw bitmap words) in
+// ascending order, and their number: a warp per node.
+__global__ void k_window_list(const uint32_t *__restrict__ bits, int64_t nn, int64_t nw, int wpw, int64_t nwin,
+                              int32_t *__restrict__ wl, int32_t *__restrict__ wcnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t node = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; node < nn; node += nwarps) {
+        int cnt = 0;
+        for (int64_t c0 = 0; c0 < nwin; c0 += 32) {
+            const int64_t c = c0 + lane;
+            uint32_t any = 0;
+            if (c < nwin)
+                for (int j = 0; j < wpw; ++j) {
+                    const int64_t w = c * wpw + j;
+                    if (w < nw) any |= bits[node * nw + w];
+                }
+            const unsigned b = __ballot_sync(0xffffffffu, any != 0u);
+            if (any) wl[node * nwin + cnt + __popc(b & ((1u << lane) - 1u))] = (int32_t)c;
+            cnt += __popc(b);
+        }
+        if (lane == 0) wcnt[node] = cnt;
+    }
 }
 
 // the bound constants (alpha, beta) and the sequence number of the query in
@@ -1028,6 +1051,17 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     int64_t cap = cap_hint > 0 ? cap_hint : 1 << 20;
     float cE1 = 0.f, cE2 = 0.f;
     tc_bound_coeffs(c.dim_p, cE1, cE2);
+    // window mode: every node's non-empty windows
+    const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
+    const int64_t nwin = (tq.nq + nq_chunk - 1) / nq_chunk;
+    const bool wl_on = rg.bits.get() != nullptr && rg.nw > 0;
+    DBuf<int32_t> wl(wl_on ? nn * nwin : 1, st), wcnt(wl_on ? nn : 1, st);
+    if (wl_on) {
+        k_window_list<<<nblk(nn * 32), 256, 0, st>>>(rg.bits.get(), nn, rg.nw, nq_chunk / 32, nwin, wl.get(),
+                                                     wcnt.get());
+        check_launch("window lists");
+        ++*launches;
+    }
     // dense last level: the queries' bound constants and sequence numbers in
     // column order, once per batch
     DBuf<float2> abq(rg.dmask ? tq.nq : 1, st);
@@ -1085,6 +1119,9 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.ab_q = abq.get();
         a.seq_q = seqp.get();
         a.qperm = tq.perm;
+        a.wlist = wl.get();
+        a.wcount = wcnt.get();
+        a.nwin = nwin;
         kern<<<(unsigned)grid, kThreadsWS, smem, st>>>(map_qh, map_ql, a);
         ++*launches;
         check_launch("tensor-core tile");

@@ -48,6 +48,10 @@ struct TileArgs {
     const int64_t *noff;      // first record of each node
     int64_t nw;
     int64_t nq;
+    // window mode: each node's non-empty windows in ascending order,
+    // wlist[node * nwin + k] for k < wcount[node]
+    const int32_t *wlist, *wcount;
+    int64_t nwin;
     // dense last level: no records; column q of node p takes its leaf mask
     // from dmask[p * nq + q] and its query data from the per-query arrays
     const uint64_t *dmask;    // null: records
