@@ -239,6 +239,72 @@ __device__ __forceinline__ void warp_tau_insert(double *D, int64_t *I, int &n, i
     if (n < K) ++n;
 }
 
+// A query's threshold list as one warp works on it: the K smallest (bound,
+// id) of distinct objects, ascending.  With K <= 32 the warp holds it in
+// registers (lane i: entry i) between load() and store(); longer lists stay in
+// global memory (warp_tau_insert).  insert() keeps exactly the entries that
+// warp_tau_insert keeps.  Every member function is warp-uniform.
+struct TauList {
+    double *D;
+    int64_t *I;
+    int n, K, lane;
+    bool reg;
+    double rd;    // lane i's entry (register form)
+    int64_t ri;
+    __device__ __forceinline__ void load(double *D_, int64_t *I_, int n_, int K_, int lane_) {
+        D = D_;
+        I = I_;
+        n = n_;
+        K = K_;
+        lane = lane_;
+        reg = K <= 32;
+        rd = __longlong_as_double(0x7ff0000000000000ll);
+        ri = 0x7fffffffffffffffll;
+        if (reg && lane < n) {
+            rd = D[lane];
+            ri = I[lane];
+        }
+    }
+    // entry K - 1 (meaningful once n >= K)
+    __device__ __forceinline__ double kd() const { return reg ? __shfl_sync(0xffffffffu, rd, K - 1) : D[K - 1]; }
+    __device__ __forceinline__ int64_t kid() const {
+        return reg ? (int64_t)__shfl_sync(0xffffffffu, (long long)ri, K - 1) : I[K - 1];
+    }
+    __device__ __forceinline__ void insert(double u, int64_t id) {
+        if (!reg) {
+            warp_tau_insert(D, I, n, K, u, id, lane);
+            return;
+        }
+        if (n >= K) {
+            const double k_d = kd();
+            const int64_t k_i = kid();
+            if (!(u < k_d || (u == k_d && id < k_i))) return;
+        }
+        const bool live = lane < n;
+        if (__any_sync(0xffffffffu, live && ri == id)) return;
+        const int below = __popc(__ballot_sync(0xffffffffu, live && (rd < u || (rd == u && ri < id))));
+        const double pd = __shfl_up_sync(0xffffffffu, rd, 1);
+        const int64_t pi = (int64_t)__shfl_up_sync(0xffffffffu, (long long)ri, 1);
+        const int last = n < K ? n : K - 1;   // entries [below, last) move up one; a full list drops entry K-1
+        if (lane > below && lane <= last) {
+            rd = pd;
+            ri = pi;
+        }
+        if (lane == below) {
+            rd = u;
+            ri = id;
+        }
+        if (n < K) ++n;
+    }
+    __device__ __forceinline__ void store() const {
+        if (reg && lane < n) {
+            D[lane] = rd;
+            I[lane] = ri;
+        }
+        __syncwarp();
+    }
+};
+
 // Warp per query.  The query's list of the k smallest (upper bound, id) of
 // distinct visible pivots seen so far is merged with this level's entries;
 // tau_q = the k-th bound, rounded up to float, or +inf while fewer than k.
@@ -253,24 +319,26 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
     const int64_t b = lower_bound_i32(eq, a, e1, (int32_t)q + 1);
     if (a == b) continue;
     const int K = kq[q];
-    double *D = tk_d + koff[q];
-    int64_t *I = tk_id + koff[q];
-    int n = tk_n[q];
+    TauList L;
+    L.load(tk_d + koff[q], tk_id + koff[q], tk_n[q], K, lane);
     const int64_t s = d.qseq[q];
     const double up = 1.0 + 2.0 * (double)d.rel;
     for (int64_t base = a; base < b; base += 32) {
         const int64_t e = base + lane;
+        const bool full = L.n >= K;
+        const double k_d = full ? L.kd() : 0.0;
+        const int64_t k_i = full ? L.kid() : 0;
         bool cand = false;
         double ub = 0.0;
         int64_t id = 0;
         if (e < b) {
             const float dv = path[e * d.h + l];
             ub = d.rel > 0.f ? (double)dv * up + (double)kAbsFloor : (double)dv;
-            if ((n < K) || ub <= D[K - 1]) {   // the bound test before the pivot's delete mark
+            if (!full || ub <= k_d) {   // the bound test before the pivot's delete mark
                 const int32_t prow = d.npiv[lvl_base + enode[e]];
                 if (row_visible(d, prow, s)) {
                     id = d.row_id[prow];
-                    cand = (n < K) || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+                    cand = !full || ub < k_d || (ub == k_d && id < k_i);
                 }
             }
         }
@@ -280,12 +348,14 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
             bal &= bal - 1;
             const double u = __shfl_sync(0xffffffffu, ub, src);
             const int64_t iid = __shfl_sync(0xffffffffu, id, src);
-            warp_tau_insert(D, I, n, K, u, iid, lane);
+            L.insert(u, iid);
         }
     }
+    L.store();
+    const double k_fin = L.n >= K ? L.kd() : 0.0;
     if (lane == 0) {
-        tk_n[q] = n;
-        tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+        tk_n[q] = L.n;
+        tau[q] = L.n >= K ? __double2float_ru(k_fin) : __int_as_float(0x7f800000);
     }
     }
 }
@@ -330,10 +400,13 @@ __device__ __forceinline__ float lane_vec_dist(const float *__restrict__ q, cons
 
 // Rows [pos, pos + m) into the threshold list, a row per lane.
 template <bool L2>
-__device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_t pos, int32_t m, int64_t s, int K,
-                                           double *D, int64_t *I, int &n, double up, int lane) {
+__device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_t pos, int32_t m, int64_t s,
+                                           TauList &L, double up, int lane) {
     for (int32_t r0 = 0; r0 < m; r0 += 32) {
         const int32_t r = r0 + lane;
+        const bool full = L.n >= L.K;
+        const double k_d = full ? L.kd() : 0.0;
+        const int64_t k_i = full ? L.kid() : 0;
         bool cand = false;
         double ub = 0.0;
         int64_t id = 0;
@@ -344,7 +417,7 @@ __device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_
                 const float dv = L2 ? sqrtf(sq) : sq;
                 ub = (double)dv * up + (double)kAbsFloor;
                 id = d.row_id[row];
-                cand = n < K || ub < D[K - 1] || (ub == D[K - 1] && id < I[K - 1]);
+                cand = !full || ub < k_d || (ub == k_d && id < k_i);
             }
         }
         unsigned bal = __ballot_sync(0xffffffffu, cand);
@@ -353,7 +426,7 @@ __device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_
             bal &= bal - 1;
             const double u = __shfl_sync(0xffffffffu, ub, src);
             const int64_t iid = __shfl_sync(0xffffffffu, id, src);
-            warp_tau_insert(D, I, n, K, u, iid, lane);
+            L.insert(u, iid);
         }
     }
 }
@@ -376,9 +449,8 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
     const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (q >= nq) return;
     const int K = kq[q];
-    double *D = tk_d + koff[q];
-    int64_t *I = tk_id + koff[q];
-    int n = tk_n[q];
+    TauList L;
+    L.load(tk_d + koff[q], tk_id + koff[q], tk_n[q], K, lane);
     const int64_t s = d.qseq[q];
     const float *qv = d.Q + q * d.dim;
     const double up = 1.0 + 2.0 * (double)d.rel;
@@ -387,12 +459,12 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
         const int32_t prow = d.npiv[lo_off.v[0]];
         const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
         const float dq = L2 ? sqrtf(sq) : sq;
-        if (d.row_del[prow] > s) warp_tau_insert(D, I, n, K, (double)dq * up + (double)kAbsFloor, d.row_id[prow], lane);
+        if (d.row_del[prow] > s) L.insert((double)dq * up + (double)kAbsFloor, d.row_id[prow]);
     }
     int64_t node = 0;
     if (d.h == 1) {   // one pivot level: the root's own rows
         const int32_t m = d.nsize[lo_off.v[0]] < cap ? d.nsize[lo_off.v[0]] : cap;
-        probe_rows<L2>(d, qv, d.npos[lo_off.v[0]], m, s, K, D, I, n, up, lane);
+        probe_rows<L2>(d, qv, d.npos[lo_off.v[0]], m, s, L, up, lane);
     }
     for (int l = 1; l < d.h; ++l) {
         // the kProbeNodes children with the nearest pivots (ascending), kept by every lane
@@ -424,13 +496,15 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             // the visible pivots into the threshold list (a register copy of
             // its K-th bound skips the pivots that cannot enter it)
             const double ub = (double)dq * up + (double)kAbsFloor;
-            const double kth = n >= K ? D[K - 1] : 0.0;
-            unsigned bal = __ballot_sync(0xffffffffu, vis && (n < K || ub <= kth));
+            const bool full = L.n >= K;
+            const double kth = full ? L.kd() : 0.0;
+            unsigned bal = __ballot_sync(0xffffffffu, vis && (!full || ub <= kth));
             while (bal) {
                 const int src = __ffs(bal) - 1;
                 bal &= bal - 1;
-                warp_tau_insert(D, I, n, K, __shfl_sync(0xffffffffu, ub, src), __shfl_sync(0xffffffffu, id, src),
-                                lane);
+                const double uu = __shfl_sync(0xffffffffu, ub, src);
+                const int64_t iid = __shfl_sync(0xffffffffu, id, src);
+                L.insert(uu, iid);
             }
             // the nearest children, in child order (ties keep the earlier child)
             unsigned lv = __ballot_sync(0xffffffffu, live);
@@ -465,13 +539,15 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
                 const int64_t g = lo_off.v[l] + bn[i];
                 const int32_t m = d.nsize[g] < budget ? d.nsize[g] : budget;
                 budget -= m;
-                probe_rows<L2>(d, qv, d.npos[g], m, s, K, D, I, n, up, lane);
+                probe_rows<L2>(d, qv, d.npos[g], m, s, L, up, lane);
             }
         }
     }
+    L.store();
+    const double k_fin = L.n >= K ? L.kd() : 0.0;
     if (lane == 0) {
-        tk_n[q] = n;
-        tau[q] = n >= K ? __double2float_ru(D[K - 1]) : __int_as_float(0x7f800000);
+        tk_n[q] = L.n;
+        tau[q] = L.n >= K ? __double2float_ru(k_fin) : __int_as_float(0x7f800000);
         if (key) key[q] = (int32_t)node;   // where the path ended: a locality key for the query
     }
 }
@@ -1272,13 +1348,13 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
         const int K = kq[q];
-        double *Dl = tk_d + koff[q];
-        int64_t *Il = tk_id + koff[q];
-        int n = tk_n[q];
+        TauList L;
+        L.load(tk_d + koff[q], tk_id + koff[q], tk_n[q], K, lane);
         const int64_t s = d.qseq[q];
         const double up = 1.0 + 2.0 * (double)d.rel;
-        // the list's current K-th bound, kept in a register (read again after inserts)
-        double kth = n >= K ? Dl[K - 1] : 0.0;
+        // the list's current K-th entry, kept in registers (read again after inserts)
+        double kth = L.n >= K ? L.kd() : 0.0;
+        int64_t kthid = L.n >= K ? L.kid() : 0;
         for (int64_t p0 = 0; p0 < P; p0 += 32 * kTauUnroll) {
             // kTauUnroll pivots per lane: their membership and distance loads
             // are issued together, then they are tested in pivot order
@@ -1300,11 +1376,11 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                     ub = (double)dv[u] * up + (double)kAbsFloor;
                     // the bound test first: most pivots fail it, and then the
                     // pivot's delete mark and id are never read
-                    if ((n < K) || ub <= kth) {
+                    if ((L.n < K) || ub <= kth) {
                         const int32_t prow = d.npiv[lvl_base + p];
                         if (prow >= 0 && row_visible(d, prow, s)) {
                             id = d.row_id[prow];
-                            cand = (n < K) || ub < kth || (ub == kth && id < Il[K - 1]);
+                            cand = (L.n < K) || ub < kth || (ub == kth && id < kthid);
                         }
                     }
                 }
@@ -1315,15 +1391,18 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                         bal &= bal - 1;
                         const double uu = __shfl_sync(0xffffffffu, ub, src);
                         const int64_t iid = __shfl_sync(0xffffffffu, id, src);
-                        warp_tau_insert(Dl, Il, n, K, uu, iid, lane);
+                        L.insert(uu, iid);
                     }
-                    kth = n >= K ? Dl[K - 1] : 0.0;
+                    kth = L.n >= K ? L.kd() : 0.0;
+                    kthid = L.n >= K ? L.kid() : 0;
                 }
             }
         }
+        L.store();
+        const double k_fin = L.n >= K ? L.kd() : 0.0;
         if (lane == 0) {
-            tk_n[q] = n;
-            tau[q] = n >= K ? __double2float_ru(Dl[K - 1]) : __int_as_float(0x7f800000);
+            tk_n[q] = L.n;
+            tau[q] = L.n >= K ? __double2float_ru(k_fin) : __int_as_float(0x7f800000);
         }
     }
 }
