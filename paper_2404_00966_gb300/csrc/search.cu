@@ -1352,9 +1352,22 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
         L.load(tk_d + koff[q], tk_id + koff[q], tk_n[q], K, lane);
         const int64_t s = d.qseq[q];
         const double up = 1.0 + 2.0 * (double)d.rel;
-        // the list's current K-th entry, kept in registers (read again after inserts)
-        double kth = L.n >= K ? L.kd() : 0.0;
-        int64_t kthid = L.n >= K ? L.kid() : 0;
+        // the list's current K-th entry, kept in registers (read again after
+        // inserts), and an FP32 distance above which a pivot's bound exceeds
+        // it: (double)dv * up + floor <= kth implies dv <= fthr, so the FP64
+        // bound is formed only for the few pivots at or below fthr
+        double kth = 0.0;
+        int64_t kthid = 0;
+        float fthr = __int_as_float(0x7f800000);
+        auto refresh = [&]() {
+            if (L.n >= K) {
+                kth = L.kd();
+                kthid = L.kid();
+                // one float step above the quotient absorbs its FP64 rounding
+                fthr = nextafterf(__double2float_ru((kth - (double)kAbsFloor) / up), __int_as_float(0x7f800000));
+            }
+        };
+        refresh();
         for (int64_t p0 = 0; p0 < P; p0 += 32 * kTauUnroll) {
             // kTauUnroll pivots per lane: their membership and distance loads
             // are issued together, then they are tested in pivot order
@@ -1372,7 +1385,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                 bool cand = false;
                 double ub = 0.0;
                 int64_t id = 0;
-                if (mem[u]) {
+                if (mem[u] && dv[u] <= fthr) {
                     ub = (double)dv[u] * up + (double)kAbsFloor;
                     // the bound test first: most pivots fail it, and then the
                     // pivot's delete mark and id are never read
@@ -1393,8 +1406,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                         const int64_t iid = __shfl_sync(0xffffffffu, id, src);
                         L.insert(uu, iid);
                     }
-                    kth = L.n >= K ? L.kd() : 0.0;
-                    kthid = L.n >= K ? L.kid() : 0;
+                    refresh();
                 }
             }
         }
@@ -1429,12 +1441,40 @@ __global__ void k_transpose_f32(const float *__restrict__ in, int64_t rows, int6
 // pairs with a surviving leaf.  Queries are taken in column order: position i
 // is query perm[i] (DT, M and the bitmap are in position order).  A block takes one node at a time and all of
 // its queries, 256 per step.
+// packed FP32 pairs, round to nearest: (a0 + b0, a1 + b1), (a0 - b0, a1 - b1), (a0 b0, a1 b1)
+__device__ __forceinline__ float2 add2f(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "add.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2f(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "sub.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2f(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, z;\n\tmov.b64 x, {%2, %3};\n\tmov.b64 y, {%4, %5};\n\t"
+        "mul.rn.f32x2 z, x, y;\n\tmov.b64 {%0, %1}, z;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t *__restrict__ cm, int64_t P,
                              int64_t nq, int64_t lvl_next, const float *__restrict__ thr_q,
                              const int32_t *__restrict__ perm, uint64_t *__restrict__ M,
                              uint32_t *__restrict__ bits, int64_t nw, unsigned long long *__restrict__ counts) {
-    // the node's children: (lo, hi, |hi|) and the mask of the non-empty ones
-    __shared__ float4 siv[64];
+    // the node's children two at a time: (hi_j, hi_j+1, |hi_j|, |hi_j+1|) and
+    // (lo_j, lo_j+1) for j = 2 i; and the mask of the non-empty children
+    __shared__ float4 sph[32];
+    __shared__ float2 spl[32];
     __shared__ unsigned long long s_ne;
     const int lane = threadIdx.x & 31;
     const float epsc = d.epsc;
@@ -1444,12 +1484,23 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
         __syncthreads();   // the previous node's children are no longer read
         if (threadIdx.x == 0) s_ne = 0ull;
         __syncthreads();
-        if (threadIdx.x < d.F) {
-            const int64_t c = lvl_next + p * d.F + threadIdx.x;
-            const bool ne = d.nsize[c] > 0;
-            const float lo = ne ? d.nlo[c] : 0.f, hi = ne ? d.nhi[c] : 0.f;
-            siv[threadIdx.x] = make_float4(lo, hi, fabsf(hi), 0.f);
-            if (ne) atomicOr(&s_ne, 1ull << threadIdx.x);
+        if (threadIdx.x < 64) {
+            const int j = threadIdx.x;
+            float lo = 0.f, hi = 0.f;
+            if (j < d.F) {
+                const int64_t c = lvl_next + p * d.F + j;
+                const bool ne = d.nsize[c] > 0;
+                if (ne) {
+                    lo = d.nlo[c];
+                    hi = d.nhi[c];
+                    atomicOr(&s_ne, 1ull << j);
+                }
+            }
+            float *h4 = reinterpret_cast<float *>(&sph[j >> 1]);
+            float *l2 = reinterpret_cast<float *>(&spl[j >> 1]);
+            h4[j & 1] = hi;
+            h4[2 + (j & 1)] = fabsf(hi);
+            l2[j & 1] = lo;
         }
         __syncthreads();
         const uint64_t nonempty = s_ne;
@@ -1461,24 +1512,30 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
             if (member) {
                 const float dq = DT[p * nq + q];
                 const float thr = thr_q[qq];
-                // interval_hit for every child, its query terms formed once
-                // (the same operations in the same order)
+                // interval_hit for two children at a time in packed FP32, its
+                // query terms formed once (the same operations in the same
+                // order): eps = epsc (sq + |hi|), keep iff u <= hi + eps and
+                // sq + eps >= lo.  A failed test shows as the sign bit of
+                // (hi + eps) - u or of (sq + eps) - lo: both differences are
+                // rounded once from the exact ones and are never -0 (eps >= +0,
+                // so hi + eps and sq + eps are not -0).
                 const float u = dq - thr, sq = dq + thr;
-                if (epsc > 0.f) {
-#pragma unroll 4
-                    for (int j = 0; j < d.F; ++j) {
-                        const float4 iv = siv[j];
-                        const float eps = epsc * (sq + iv.z);
-                        m |= (uint64_t)((u <= iv.y + eps) & (sq + eps >= iv.x)) << j;
-                    }
-                } else {
-#pragma unroll 4
-                    for (int j = 0; j < d.F; ++j) {
-                        const float4 iv = siv[j];
-                        m |= (uint64_t)((u <= iv.y + 0.f) & (sq + 0.f >= iv.x)) << j;
-                    }
+                const float2 u2 = make_float2(u, u), sq2 = make_float2(sq, sq);
+                const float2 ec2 = make_float2(epsc, epsc);
+                uint64_t fail = 0;
+#pragma unroll 2
+                for (int j = 0; j < d.F; j += 2) {
+                    const float4 h = sph[j >> 1];
+                    const float2 lo = spl[j >> 1];
+                    const float2 eps = epsc > 0.f ? mul2f(ec2, add2f(sq2, make_float2(h.z, h.w)))
+                                                  : make_float2(0.f, 0.f);
+                    const float2 d1 = sub2f(add2f(make_float2(h.x, h.y), eps), u2);
+                    const float2 d2 = sub2f(add2f(sq2, eps), lo);
+                    const uint32_t f0 = (__float_as_uint(d1.x) | __float_as_uint(d2.x)) >> 31;
+                    const uint32_t f1 = (__float_as_uint(d1.y) | __float_as_uint(d2.y)) >> 31;
+                    fail |= (uint64_t)(f0 | (f1 << 1)) << j;
                 }
-                m &= nonempty;
+                m = ~fail & nonempty;
             }
             if (q < nq) M[p * nq + q] = m;
             const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
