@@ -37,10 +37,10 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/):
-# k_tile_l2_tc at half size, 0.607 GB read + write (node rows and the node x
+# k_tile_l2_tc at half size, 0.459 GB read + write (node rows and the node x
 # query leaf-mask matrix), both of which double at full size.  None once the
 # kernel has changed since the counters were taken.
-TRAFFIC = {"kernel": "tile", "bytes_per_launch": 1.21e9}
+TRAFFIC = {"kernel": "tile", "bytes_per_launch": 0.92e9}
 
 
 def workload(scale: float = 1.0):
