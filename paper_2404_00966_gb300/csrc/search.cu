@@ -833,13 +833,15 @@ __global__ void k_cache_cands(int64_t qa, int64_t qb, int64_t n, int64_t cn, int
 // ---------------------------------------------------------------- verification
 
 // A warp takes kVerifyGroup consecutive candidates (query-major, so they
-// mostly share a query, which then stays in registers).  Range: accept when
+// mostly share a query, which then stays in registers), sums their distances
+// one after another, and then decides them together, a lane per candidate.
+// Range: accept when
 // the FP32 upper bound is below r, reject when the lower bound is above r,
 // otherwise decide in FP64 exactly as the CPU reference does.  kNN: keep the
 // candidate if its lower bound is within the query's threshold tau_q (an
 // upper bound of the k-th distance; a farther candidate cannot be in the top
 // k) and store its FP32 distance.
-constexpr int kVerifyGroup = 8;
+constexpr int kVerifyGroup = 32;   // pairs per warp in k_verify_vec (at most 32: one per lane)
 
 template <bool L2, bool KNN, int NV>
 __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
@@ -851,11 +853,19 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
     for (int64_t c0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * kVerifyGroup; c0 < C;
          c0 += nw * kVerifyGroup) {
     const int64_t c1 = c0 + kVerifyGroup < C ? c0 + kVerifyGroup : C;
+    const int ng = (int)(c1 - c0);
+    // the group's pairs (lane i: pair c0 + i); the warp sums each pair's
+    // distance in turn and lane i keeps pair i's, then the lanes decide
+    // their pairs together
+    const int32_t gq = lane < ng ? cq[c0 + lane] : 0;
+    const int32_t grow = lane < ng ? crow[c0 + lane] : 0;
+    float my_d32 = 0.f;
+    bool my_vis = true;
     int32_t cur = -1;
     const float *qv = nullptr;
-    for (int64_t c = c0; c < c1; ++c) {
-        const int32_t q = cq[c];
-        const int64_t row = crow[c];
+    for (int i = 0; i < ng; ++i) {
+        const int32_t q = __shfl_sync(0xffffffffu, gq, i);
+        const int64_t row = __shfl_sync(0xffffffffu, grow, i);
         if (q != cur) {
             cur = q;
             qv = d.Q + (int64_t)q * d.dim;
@@ -865,17 +875,22 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
                 for (int v = 0; v < (NV > 0 ? NV : 1); ++v) qr[v] = q4[v * 32 + lane];
             }
         }
-        if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
-            if (lane == 0) {
-                cdist[c] = __int_as_float(0x7f800000);
-                keep[c] = 0;
-            }
-            continue;
+        const bool vis = !(row >= d.n && !row_visible(d, row, d.qseq[q]));
+        float sq = 0.f;
+        if (vis) sq = row_dist_regs<L2, NV>(qr, vrow(d, row), qv, d.dim, lane);
+        if (lane == i) {
+            my_vis = vis;
+            my_d32 = L2 ? sqrtf(sq) : sq;
         }
-        const float *xv = vrow(d, row);
-        const float sq = row_dist_regs<L2, NV>(qr, xv, qv, d.dim, lane);
-        const float d32 = L2 ? sqrtf(sq) : sq;
-        if (lane != 0) continue;
+    }
+    if (lane < ng) {
+        const int64_t c = c0 + lane;
+        if (!my_vis) {
+            cdist[c] = __int_as_float(0x7f800000);
+            keep[c] = 0;
+        } else {
+        const int32_t q = gq;
+        const float d32 = my_d32;
         const float r = thr_q[q];
         const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
         const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
@@ -888,11 +903,14 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
         } else if (lo > r * (1.f + 1e-9f)) {
             keep[c] = 0;
         } else {
-            const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+            const float *pqv = d.Q + (int64_t)q * d.dim;
+            const float *xv = vrow(d, (int64_t)grow);
+            const double key = L2 ? l2sq_fp64_seq(pqv, xv, d.dim) : l1_fp64_seq(pqv, xv, d.dim);
             const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
             keep[c] = key <= lim ? 1 : 0;
             cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
             atomicAdd(rechecks, 1ull);
+        }
         }
     }
     }
