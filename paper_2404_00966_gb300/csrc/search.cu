@@ -572,6 +572,41 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
                          uint64_t *__restrict__ mask_io) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (MODE != 1) {
+        // 32 entries per warp step: lane i loads entry i's data, the warp
+        // tests each entry's children in turn (a child per lane), lane i
+        // keeps entry i's mask, and the masks are written together
+        for (int64_t g0 = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; g0 < e1; g0 += nw * 32) {
+            const int64_t eg = g0 + lane;
+            const bool in = eg < e1;
+            const int32_t gnode = in ? enode[eg] : 0;
+            const float gdq = in ? path[eg * d.h + l] : 0.f;
+            const float gthr = in ? thr_q[eq[eg]] : 0.f;
+            const int ne = e1 - g0 < 32 ? (int)(e1 - g0) : 32;
+            uint64_t my_m = 0;
+            for (int i = 0; i < ne; ++i) {
+                const int32_t node = __shfl_sync(0xffffffffu, gnode, i);
+                const float dq = __shfl_sync(0xffffffffu, gdq, i);
+                const float thr = __shfl_sync(0xffffffffu, gthr, i);
+                uint64_t m = 0;
+                for (int j0 = 0; j0 < d.F; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool keep = false;
+                    if (j < d.F) {
+                        const int64_t c = lvl_next + (int64_t)node * d.F + j;
+                        keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+                    }
+                    m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
+                }
+                if (lane == i) my_m = m;
+            }
+            if (in) {
+                mask_io[eg - e0] = my_m;
+                if (MODE == 0) cnt[eg - e0] = __popcll(my_m);
+            }
+        }
+        return;
+    }
     for (int64_t e = e0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); e < e1; e += nw) {
     const int32_t q = eq[e];
     const int32_t node = enode[e];
