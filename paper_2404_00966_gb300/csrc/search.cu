@@ -23,6 +23,7 @@
 // operation order.  The cache list is scanned by brute force (Section 4.4).
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
+#include <unordered_map>
 
 #include "gts_impl.cuh"
 #include "metric.cuh"
@@ -1762,6 +1763,31 @@ struct StageClock {
     }
 };
 
+// Grid of a grid-stride kernel: at most one wave (SMs x the blocks of this
+// kernel that fit on an SM at once), so that no partial second wave runs on
+// a few SMs while the rest idle.
+template <typename Kern>
+unsigned wave_grid(Kern kern, int64_t blocks, int threads) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> per_sm_of;
+    int dev = 0, sms = 0, per_sm = 0;
+    GTS_CUDA(cudaGetDevice(&dev));
+    GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = per_sm_of.find(reinterpret_cast<const void *>(kern));
+        if (it != per_sm_of.end()) {
+            per_sm = it->second;
+        } else {
+            GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+            if (per_sm < 1) per_sm = 1;
+            per_sm_of[reinterpret_cast<const void *>(kern)] = per_sm;
+        }
+    }
+    const int64_t cap = (int64_t)sms * per_sm;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, cap));
+}
+
 struct Runner {
     gts_index *ix;
     const QueryBatch &qb;
@@ -1962,7 +1988,7 @@ struct Runner {
             DBuf<int32_t> cnt(E, st);
             DBuf<uint64_t> cmask(E, st);
             clk.begin(GTS_STAGE_EXPAND);
-            k_expand<0><<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+            k_expand<0><<<wave_grid(k_expand<0>, nblocks((E + 31) / 32, kWarpsPerBlock), kT), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), cnt.get(), nullptr,
                                                                    nullptr, nullptr, nullptr, cmask.get());
             clk.end();
@@ -2002,7 +2028,7 @@ struct Runner {
         } else {
             DBuf<uint64_t> mask(E, st);
             clk.begin(GTS_STAGE_EXPAND);
-            k_expand<2><<<cap(nblocks(E, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
+            k_expand<2><<<wave_grid(k_expand<2>, nblocks((E + 31) / 32, kWarpsPerBlock), kT), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(), l,
                                                                    lvl_next, e0, e1, thr.get(), nullptr, nullptr,
                                                                    nullptr, nullptr, nullptr, mask.get());
             clk.end();
@@ -2170,7 +2196,7 @@ struct Runner {
         clk.end();
         if (knn) {
             clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau_dense<<<cap(nblocks(nq, kWarpsPerBlock)), kT, 0, st>>>(d, D, P, cm.get(), base, nq, qb.k,
+            k_tau_dense<<<wave_grid(k_tau_dense, nblocks(nq, kWarpsPerBlock), kT), kT, 0, st>>>(d, D, P, cm.get(), base, nq, qb.k,
                                                                          koff.get(), tk_d.get(), tk_id.get(),
                                                                          tk_n.get(), thr.get());
             clk.end();
@@ -2213,7 +2239,7 @@ struct Runner {
         {
             dim3 tb(32, 8), tg((unsigned)((P + 31) / 32), (unsigned)((nq + 31) / 32));
             k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get(), perm.get());
-            k_leaf_dense<<<(unsigned)std::min<int64_t>(P, (int64_t)max_blocks), 256, 0, st>>>(
+            k_leaf_dense<<<wave_grid(k_leaf_dense, P, 256), 256, 0, st>>>(
                 d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), perm.get(), M.get(), rg.bits.get(),
                 rg.nw, cnt.get());
         }
@@ -2442,8 +2468,8 @@ struct Runner {
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
         const int nv = (aligned && d.dim % 128 == 0 && d.dim <= 512) ? d.dim / 128 : 0;
 #define GTS_VV(NVV)                                                                                          \
-    k_verify_vec<L2, KNN, NVV><<<grid, kT, 0, st>>>(d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), \
-                                                    counters.get())
+    k_verify_vec<L2, KNN, NVV><<<wave_grid(k_verify_vec<L2, KNN, NVV>, grid, kT), kT, 0, st>>>(                     \
+        d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get())
         switch (nv) {
             case 1: GTS_VV(1); break;
             case 2: GTS_VV(2); break;
