@@ -19,7 +19,7 @@ Readings of the paper used here (each one is also listed in the design notes):
   the tree is unique -- then split by count into Nc children of
   floor(size/Nc) objects each, the last child taking the remainder.
 * Child bounds: the paper keeps min_dis (the child's first distance to the
-  parent pivot); this build also keeps the last one (max), so a child holds
+  parent pivot); this index also keeps the last one (max), so a child holds
   the interval [lo, hi] of its objects' distances to the parent pivot.  An
   empty child has lo = +inf, hi = -inf.
 * Table list (Section 4.2): one row per object in final (leaf) order, with
