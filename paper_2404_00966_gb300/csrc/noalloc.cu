@@ -16,11 +16,16 @@
 // Every call uses the same array, so calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on it; serialise them.
 // Nothing in it has to start at zero: each call writes every entry it reads.
+//
+// Non-finite inputs: a distance that comes out NaN (a NaN coordinate in the
+// object or the query) is ranked as +inf, so such objects sort after every
+// finite one, by id, and never displace a real neighbour.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "gts_impl.cuh"
 #include "metric.cuh"
@@ -30,7 +35,6 @@ namespace {
 
 constexpr int64_t kScratchEntries = 1 << 20;
 constexpr int kScanMaxK = 32;
-constexpr int kMaxDevices = 64;
 
 struct ScanPair {
     double key;
@@ -61,7 +65,8 @@ __global__ void k_scan_partial(const float *__restrict__ X, int64_t n, int dim, 
     int len = 0;
     for (int64_t o = o0 + lane; o < o1; o += 32) {
         const float *xv = X + o * dim;
-        const double key = l2 ? l2sq_fp64_seq(qv, xv, dim) : l1_fp64_seq(qv, xv, dim);
+        double key = l2 ? l2sq_fp64_seq(qv, xv, dim) : l1_fp64_seq(qv, xv, dim);
+        if (key != key) key = __longlong_as_double(0x7ff0000000000000ll);   // NaN ranks as +inf
         if (len == k && !pair_less(key, o, kk[k - 1], ii[k - 1])) continue;
         int pos = len < k ? len : k - 1;
         while (pos > 0 && pair_less(key, o, kk[pos - 1], ii[pos - 1])) {
@@ -127,21 +132,54 @@ __global__ void k_scan_merge(const ScanPair *__restrict__ scratch, int64_t nq, i
     }
 }
 
-// Device address of the scratch array, fetched once per device (with that
-// device current) through cudaGetSymbolAddress: in host code the array's name
-// is only a host-side stand-in, not a device address.
-ScanPair *scratch_ptr(int dev) {
+// Device address of the scratch array.  In host code the array's name is
+// only a host-side stand-in, not a device address, so the address is fetched
+// through cudaGetSymbolAddress, once per CUDA context (with the caller's
+// device current), and cached under the context's unique id: after a
+// cudaDeviceReset the device gets a new primary context, with a new id, and
+// the address is looked up again instead of reusing a stale one.
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_ctx = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_ctx = (CtxGetCurrentFn)f1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f2;
+    });
+    GTS_REQUIRE(get_ctx && get_id, GTS_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+    void *ctx = nullptr;
+    GTS_REQUIRE(get_ctx(&ctx) == 0, GTS_ECUDA, "cuCtxGetCurrent failed");
+    if (!ctx) return 0;
+    unsigned long long id = 0;
+    GTS_REQUIRE(get_id(ctx, &id) == 0, GTS_ECUDA, "cuCtxGetId failed");
+    return id;
+}
+
+ScanPair *scratch_ptr() {
     static std::mutex mu;
-    static ScanPair *ptrs[kMaxDevices] = {nullptr};
-    GTS_REQUIRE(dev >= 0 && dev < kMaxDevices, GTS_EINVAL, "device ordinal out of range");
+    static std::unordered_map<unsigned long long, ScanPair *> ptrs;
     std::lock_guard<std::mutex> lock(mu);
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        GTS_CUDA(cudaGetSymbolAddress(&p, g_scan_scratch));
-        GTS_REQUIRE(p != nullptr, GTS_ECUDA, "cudaGetSymbolAddress returned no address");
-        ptrs[dev] = (ScanPair *)p;
+    unsigned long long ctx = current_context_id();
+    if (ctx != 0) {
+        auto it = ptrs.find(ctx);
+        if (it != ptrs.end()) return it->second;
     }
-    return ptrs[dev];
+    void *p = nullptr;
+    GTS_CUDA(cudaGetSymbolAddress(&p, g_scan_scratch));   // also makes the runtime's context current
+    GTS_REQUIRE(p != nullptr, GTS_ECUDA, "cudaGetSymbolAddress returned no address");
+    ctx = current_context_id();
+    GTS_REQUIRE(ctx != 0, GTS_ECUDA, "no current CUDA context after cudaGetSymbolAddress");
+    ptrs[ctx] = (ScanPair *)p;
+    return (ScanPair *)p;
 }
 
 }  // namespace
@@ -158,9 +196,7 @@ void knn_scan_noalloc(const float *X, int64_t n, int dim, int metric, const floa
     GTS_REQUIRE(nq == 0 || (Q && ids && dist), GTS_EINVAL, "NULL query or output pointer");
     GTS_REQUIRE(n == 0 || X, GTS_EINVAL, "NULL object pointer");
     if (nq == 0) return;
-    int dev = 0;
-    GTS_CUDA(cudaGetDevice(&dev));
-    ScanPair *scratch = scratch_ptr(dev);
+    ScanPair *scratch = scratch_ptr();
     // slices per query: as many as fit the scratch, up to one per warp lane
     int64_t slices = kScratchEntries / (nq * (int64_t)k);
     if (slices > 32) slices = 32;

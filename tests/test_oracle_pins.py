@@ -259,9 +259,16 @@ def _check_index(objects, metric, T):
                 if c:
                     col = table[l - 1, s:s + c]
                     assert T["lo"][l][i] == col.min() and T["hi"][l][i] == col.max()
-                    # siblings were cut from one sorted run: intervals in order
+                    # siblings were cut from one run sorted by (distance, id): intervals in
+                    # order, and where the cut falls inside a run of tied distances the
+                    # earlier child holds the smaller ids
                     if j > 0 and T["size"][l][i - 1]:
                         assert T["hi"][l][i - 1] <= T["lo"][l][i]
+                        if T["hi"][l][i - 1] == T["lo"][l][i]:
+                            ps0, pc0 = T["pos"][l][i - 1], T["size"][l][i - 1]
+                            prev = perm[ps0:ps0 + pc0][table[l - 1, ps0:ps0 + pc0] == T["lo"][l][i]]
+                            cur = perm[s:s + c][col == T["lo"][l][i]]
+                            assert prev.max() < cur.min()
                     # the ancestor pivot's distance, recomputed from scratch
                     p = T["pivot"][l - 1][i // F]
                     objs = objects.take(perm[s:s + c]) if isinstance(objects, Strings) else objects[perm[s:s + c]]
@@ -278,6 +285,43 @@ def _check_index(objects, metric, T):
                     assert p == perm[s:s + c][sc == sc.max()].min()
 
 
+def _check_leaf_order(T):
+    """Rows of a leaf come in the order of the last sort: (distance to the
+    leaf's parent pivot, id) ascending."""
+    h, F = T["h"], T["fanout"]
+    for i in range(F ** h):
+        s, c = T["pos"][h][i], T["size"][h][i]
+        d, ids = T["table"][h - 1, s:s + c], T["perm"][s:s + c]
+        for a in range(c - 1):
+            assert d[a] < d[a + 1] or (d[a] == d[a + 1] and ids[a] < ids[a + 1])
+
+
+def test_index_oracle_tie_order_by_hand():
+    """Every object at the same L1 distance 2 from the root pivot (object 0,
+    the origin): Algorithm 3 sorts the node by (distance, id), so the pivot
+    (distance 0) comes first, the tied objects follow in ascending id, and the
+    even split of 41 objects into 4 children of 10 (the last takes 11) cuts
+    that order into consecutive id ranges -- the whole tree is known by hand."""
+    rng = np.random.default_rng(23)
+    X = np.zeros((41, 6), np.float32)
+    for o in range(1, 41):
+        a, b = rng.choice(6, 2, replace=False)      # two coordinates of 1: |x|_1 = 2 exactly
+        X[o, a] = X[o, b] = 1.0
+    T = build_index(X, "l1", 4, 1, root_pivot=0)
+    assert T["h"] == 1
+    assert T["perm"].tolist() == list(range(41))
+    assert T["size"][1].tolist() == [10, 10, 10, 11] and T["pos"][1].tolist() == [0, 10, 20, 30]
+    assert T["lo"][1].tolist() == [0.0, 2.0, 2.0, 2.0] and T["hi"][1].tolist() == [2.0, 2.0, 2.0, 2.0]
+    assert T["table"][0].tolist() == [0.0] + [2.0] * 40
+    _check_index(X, "l1", T)
+    _check_leaf_order(T)
+    # reversed ids: the same points listed backwards keep the pivot first and
+    # the tied ones in ascending id again
+    Xr = np.concatenate([X[:1], X[1:][::-1]])
+    Tr = build_index(Xr, "l1", 4, 1, root_pivot=0)
+    assert Tr["perm"].tolist() == list(range(41))
+
+
 def test_index_oracle_vectors():
     rng = np.random.default_rng(21)
     X = (rng.standard_normal((700, 5))).astype(np.float32)
@@ -285,8 +329,15 @@ def test_index_oracle_vectors():
     T = build_index(X, "l2", 4, 0, root_pivot=17)
     assert T["h"] == height(700, 4) == 4
     _check_index(X, "l2", T)
+    _check_leaf_order(T)
     T1 = build_index(X, "l1", 6, 2, root_pivot=3)
     _check_index(X, "l1", T1)
+    _check_leaf_order(T1)
+    # integer points: many exactly tied distances at every level
+    Xi = rng.integers(0, 3, size=(500, 3)).astype(np.float32)
+    T2 = build_index(Xi, "l1", 5, 3, root_pivot=11)
+    _check_index(Xi, "l1", T2)
+    _check_leaf_order(T2)
 
 
 def test_index_oracle_strings():
@@ -295,6 +346,7 @@ def test_index_oracle_strings():
     S = strings_from_list(items)
     T = build_index(S, "edit", 5, 3, root_pivot=0)
     _check_index(S, "edit", T)
+    _check_leaf_order(T)
 
 
 def test_height_formula():

@@ -1,12 +1,14 @@
 """Continuous batching (gts_serve_*): every request's answer inside a mixed,
 concurrently submitted stream equals its answer alone (gts_range / gts_knn on
-that one query), and admission never lets the projected bytes in flight
-exceed the budget (beyond one request admitted alone)."""
+that one query) and the CPU oracle's answer, and admission never lets the
+projected bytes in flight exceed the budget (beyond one request admitted
+alone)."""
 import threading
 
 import numpy as np
 import pytest
 
+import oracle
 from synth import small_vectors, words_like
 
 pytestmark = pytest.mark.gpu
@@ -51,12 +53,18 @@ def test_mixed_stream_equals_alone(gts, metric, prec):
     sv.stop()
     assert st["requests"] == 240 and st["batches"] > 1
     assert st["max_in_flight"] <= budget
+    want_k = oracle.knn_query(metric, X, Q, ks)
+    want_r = oracle.range_query(metric, X, Q, np.full(240, radius, np.float32))
     for i in range(240):
         alone = ix.knn(Q[i:i + 1], int(ks[i]), precision=prec) if kinds[i] else \
             ix.range(Q[i:i + 1], np.float32([radius]), precision=prec)
         ids, dist = alone.query(0)
-        assert np.array_equal(got[i][0], ids), f"request {i}: ids differ"
+        assert np.array_equal(got[i][0], ids), f"request {i}: ids differ from the request alone"
         assert np.allclose(got[i][1], dist, rtol=1e-5, atol=1e-30), f"request {i}: distances differ"
+        off, wids, wdist, _ = want_k if kinds[i] else want_r
+        assert np.array_equal(got[i][0], wids[off[i]:off[i + 1]]), f"request {i}: ids differ from the oracle"
+        assert np.allclose(got[i][1], wdist[off[i]:off[i + 1]], rtol=1e-5, atol=1e-30), \
+            f"request {i}: distances differ from the oracle"
         assert got[i][2] >= 0.0
     ix.close()
 
@@ -68,9 +76,14 @@ def test_string_requests(gts):
     tk = [sv.submit(wl.queries.get(i), "range" if i % 2 else "knn", 2 if i % 2 else 5) for i in range(60)]
     got = [sv.wait(t) for t in tk]
     sv.stop()
+    want_r = oracle.range_query("edit", wl.objects, wl.queries, np.full(60, 2, np.float32))
+    want_k = oracle.knn_query("edit", wl.objects, wl.queries, 5)
     for i in range(60):
         q = wl.queries.take([i])
         alone = ix.range(q, np.float32([2])) if i % 2 else ix.knn(q, 5)
         ids, dist = alone.query(0)
         assert np.array_equal(got[i][0], ids) and np.array_equal(got[i][1], dist)
+        off, wids, wdist, _ = want_r if i % 2 else want_k
+        assert np.array_equal(got[i][0], wids[off[i]:off[i + 1]]), f"request {i}: ids differ from the oracle"
+        assert np.array_equal(got[i][1], wdist[off[i]:off[i + 1]].astype(np.float32))
     ix.close()

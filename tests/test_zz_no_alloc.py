@@ -1,8 +1,9 @@
 """gts_knn_scan_noalloc: exact kNN by brute-force scan for callers that cannot
 allocate device memory while they query (graph capture, allocator-free
 serving threads, hosts that own all device memory).  Checked through the C
-ABI against gts_knn on the same objects, on two calls in a row, so a second
-call that reuses the library's fixed scratch array still answers exactly.
+ABI against gts_knn on the same objects and against the CPU oracle, on two
+calls in a row, so a second call that reuses the library's fixed scratch
+array still answers exactly.
 
 This file is collected last on purpose: a failure here comes after every other
 test has run."""
@@ -11,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from synth import small_vectors
 
 pytestmark = pytest.mark.gpu
@@ -53,11 +55,37 @@ def test_noalloc_scan_matches_gts_knn_on_two_calls(env, metric, metric_id):
         Qd = torch.from_numpy(Q).cuda()
         ids, dist = _scan(g, torch, Xd, Qd, metric_id, k)
         ref = ix.knn(Qd, k)
+        off, wids, wdist, _ = oracle.knn_query(metric, X, Q, k)
         for i in range(Q.shape[0]):
             rid, rdist = ref.query(i)
             assert np.array_equal(ids[i], rid), f"query {i}: ids differ"
             assert np.allclose(dist[i], rdist, rtol=RTOL, atol=0), f"query {i}: distances differ"
+            assert np.array_equal(ids[i], wids[off[i]:off[i + 1]]), f"query {i}: ids differ from the oracle"
+            assert np.allclose(dist[i], wdist[off[i]:off[i + 1]], rtol=RTOL, atol=0), \
+                f"query {i}: distances differ from the oracle"
     ix.close()
+
+
+def test_noalloc_scan_nan_object_ranks_last(env):
+    """A NaN coordinate makes that object's distance NaN; the scan ranks it as
+    +inf, so the answers equal the oracle's over the other objects whenever k
+    is at most their count."""
+    g, torch = env
+    X, Q = small_vectors(3001, 32, 40, seed=96)
+    X[1234, 7] = np.nan
+    keep = np.array([i for i in range(3001) if i != 1234])
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    for metric, metric_id in (("l2", 2), ("l1", 1)):
+        for _ in range(2):
+            ids, dist = _scan(g, torch, Xd, Qd, metric_id, 16)
+            off, wids, wdist, _ = oracle.knn_query(metric, X[keep], Q, 16)
+            for i in range(40):
+                assert np.array_equal(ids[i], keep[wids[off[i]:off[i + 1]]]), f"query {i}: ids differ"
+                assert np.allclose(dist[i], wdist[off[i]:off[i + 1]], rtol=RTOL, atol=0)
+    # three objects, one of them NaN, k = 3: the NaN object comes last at +inf
+    Xs = np.array([[0.0, 1.0], [np.nan, 0.0], [2.0, 2.0]], np.float32)
+    ids, dist = _scan(g, torch, torch.from_numpy(Xs).cuda(), torch.zeros((1, 2), device="cuda"), 2, 3)
+    assert ids[0].tolist() == [0, 2, 1] and np.isinf(dist[0][2]) and dist[0][0] == 1.0
 
 
 def test_noalloc_scan_fewer_objects_than_k_and_size_limit(env):
@@ -67,10 +95,12 @@ def test_noalloc_scan_fewer_objects_than_k_and_size_limit(env):
     ids, dist = _scan(g, torch, Xd, Qd, 2, 9)
     ix = g.Index.build(Xd, "l2", fanout=4)
     ref = ix.knn(Qd, 9)
+    off, wids, wdist, _ = oracle.knn_query("l2", X, Q, 9)
     for i in range(3):
         rid, rdist = ref.query(i)
         assert np.array_equal(ids[i][:5], rid) and np.all(ids[i][5:] == -1)
         assert np.allclose(dist[i][:5], rdist, rtol=RTOL) and np.all(np.isinf(dist[i][5:]))
+        assert np.array_equal(ids[i][:5], wids[off[i]:off[i + 1]])
     ix.close()
     # beyond the fixed scratch capacity: rejected with GTS_EINVAL, nothing launched
     st = g.lib().gts_knn_scan_noalloc(ctypes.c_void_p(Xd.data_ptr()), 5, 8, 2, ctypes.c_void_p(Qd.data_ptr()),
@@ -107,8 +137,10 @@ def test_noalloc_scan_replayed_from_a_cuda_graph(env):
         torch.cuda.synchronize()
         gi, gd = ids.cpu().numpy().reshape(64, k), dist.cpu().numpy().reshape(64, k)
         ref = ix.knn(Qbuf, k)
+        off, wids, _, _ = oracle.knn_query("l2", X, Q, k)
         for i in range(64):
             rid, rdist = ref.query(i)
             assert np.array_equal(gi[i], rid), f"query {i}: ids differ"
             assert np.allclose(gd[i], rdist, rtol=RTOL, atol=0), f"query {i}: distances differ"
+            assert np.array_equal(gi[i], wids[off[i]:off[i + 1]]), f"query {i}: ids differ from the oracle"
     ix.close()
