@@ -97,7 +97,25 @@ typedef struct {
     int64_t *stats;          /* optional host int64[GTS_STATS_LEN] of counters, filled on return */
     double *stage_ms;        /* optional host double[GTS_STAGES_LEN]: device time per stage, measured with
                                 CUDA events around every kernel launch of the call (adds the events' cost) */
+    int32_t flags;           /* GTS_QUERY_* bits; 0 = none */
+    int32_t reserved_;
 } gts_query_opts;
+
+/* gts_query_opts.flags */
+enum {
+    /* Diagnostics: also count, into stats[GTS_STAT_TABLE_PASS], the (query,
+     * row) pairs of the leaves that node pruning kept whose table lower bound
+     * max_l |D_l(row) - d(q, p_l)| passes the query's threshold (Lemma 1 /
+     * Lemma 2 over every pivot of the row's path) and that are visible: the
+     * candidates a per-candidate verification must check, C_q summed over the
+     * batch.  Costs an extra pass over those pairs; the answers are unchanged. */
+    GTS_QUERY_COUNT_TABLE_PASS = 1,
+    /* kNN: also return each answer's FP64 key in gts_result.key (L2: the
+     * squared distance summed in FP64 in increasing coordinate order; L1: the
+     * FP64 sum; edit: the integer distance), the key that orders answers with
+     * ties broken by id -- what gts_merge_knn needs to merge shards exactly. */
+    GTS_QUERY_KEYS = 2
+};
 
 /* Stages reported in gts_query_opts.stage_ms (and their launch counts in
  * stage_ms[GTS_STAGES_LEN/2 + stage] as a double). */
@@ -118,7 +136,8 @@ enum {
 enum {
     GTS_STAT_PIVOT_DIST = 0,   /* query-to-pivot distances computed */
     GTS_STAT_FRONTIER = 1,     /* (query, node) entries visited, all levels */
-    GTS_STAT_SCANNED_ROWS = 2, /* table-list rows tested in the leaf scan */
+    GTS_STAT_SCANNED_ROWS = 2, /* table-list rows read by the leaf scan (plain scan: per entry; node-major
+                                  scan: each row block once) */
     GTS_STAT_CANDIDATES = 3,   /* rows that passed the scan (verified with the metric) */
     GTS_STAT_RECHECKS = 4,     /* FP64 boundary rechecks */
     GTS_STAT_RESULTS = 5,      /* returned (query, object) pairs */
@@ -130,7 +149,9 @@ enum {
     GTS_STAT_TILE_PAIRS = 11,  /* (query, row) pairs whose distance the tiles computed */
     GTS_STAT_DENSE_PAIRS = 12, /* (query, pivot) distances computed as dense per-level matrices */
     GTS_STAT_DENSE_LAST = 13,  /* 1 if the last level ran as dense matrices (no entry list) */
-    GTS_STATS_LEN = 14
+    GTS_STAT_TABLE_PASS = 14,  /* with GTS_QUERY_COUNT_TABLE_PASS: pairs passing the table bound; else -1 */
+    GTS_STAT_SCAN_RECORDS = 15,/* node-major table scan: (query, row block) records tested (each read once) */
+    GTS_STATS_LEN = 16
 };
 
 /* Per-query answers in CSR form: the answers of query i are
@@ -146,6 +167,7 @@ typedef struct {
     float *dist;
     int32_t on_device;
     void *priv_;
+    double *key;    /* kNN with GTS_QUERY_KEYS: FP64 key per answer (same side and layout as dist); else NULL */
 } gts_result;
 
 /* Build an index over `objects` (Section 4.3, Algorithms 1-3).
@@ -219,6 +241,34 @@ gts_status gts_table(const gts_index *index, int64_t *ids, float *table);
  * may be NULL.  Synchronous. */
 gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *ids, float *dist);
 
+/* Persistence (checkpoint / resume of an index; the paper rebuilds instead,
+ * Section 4.4).  gts_save writes the whole index state -- node list and table
+ * list (Section 4.2), the objects in leaf order, the cache list and delete
+ * marks with their sequence numbers (Section 4.4), the id bookkeeping and the
+ * tuning -- to `path` (written to path + ".tmp", then renamed).  gts_load
+ * reads it onto the current device (opts: stream and cache_limit are taken,
+ * the rest ignored; may be NULL); the loaded index answers exactly as the
+ * saved one did, at the same sequence numbers.  A file that is not a GTS
+ * index, is truncated or is inconsistent gives GTS_EINVAL before any device
+ * allocation. */
+gts_status gts_save(const gts_index *index, const char *path);
+gts_status gts_load(const char *path, const gts_build_opts *opts, gts_index **out);
+
+/* Merge the answers of indexes over disjoint object sets (shards) for the
+ * same nq queries into the answers one index over their union would give.
+ * parts[p]: host results (on_device = 0); object id i of part p is global id
+ * id_base[p] + i.
+ *  gts_merge_knn: parts from gts_knn with GTS_QUERY_KEYS; query q keeps the
+ *    first k[q] answers in ascending (FP64 key, global id) order (Definition
+ *    2); out carries keys too.
+ *  gts_merge_range: all answers of every part, ascending global id
+ *    (Definition 1).
+ * Host code: no device needed.  out is allocated by the library (host);
+ * release it with gts_result_free. */
+gts_status gts_merge_knn(const gts_result *const *parts, const int64_t *id_base, int32_t n_parts, const int32_t *k,
+                         gts_result *out);
+gts_status gts_merge_range(const gts_result *const *parts, const int64_t *id_base, int32_t n_parts, gts_result *out);
+
 /* Launch parameters of the tile kernels and the kNN schedule, held per index.
  * No counterpart in the paper (its kernels are launched per level with fixed
  * shapes).  None of them changes a result: every setting returns the same
@@ -233,6 +283,12 @@ gts_status gts_result_copy(const gts_result *result, int64_t *offsets, int64_t *
  *              the k-th distance, 0 .. 4096 (default 1024).
  *  tc_queries: BF16 tensor-core tiles for dim <= 128, queries per chunk:
  *              128 (two staging slots, default) or 96 (three slots).
+ *  str_chunk:  edit distance, (query, object) pairs per block of the
+ *              bit-parallel DP kernels (pivot distances and verification):
+ *              64, 128, 256 (default) or 512.
+ *  str_qgram:  edit distance with GTS_PREC_BF16, the 3-gram count filter
+ *              before the DP: 0 = off (the table scan alone), or its queries
+ *              per tile chunk, 32 or 64 (default).
  *  tuned:      output only: 1 once gts_autotune has run on the index. */
 typedef struct {
     int32_t l1_queries;
@@ -241,7 +297,8 @@ typedef struct {
     int32_t probe_rows;
     int32_t tuned;
     int32_t tc_queries;
-    int32_t reserved_[2];
+    int32_t str_chunk;
+    int32_t str_qgram;
 } gts_tuning;
 
 /* Read / replace the index's tuning.  A query copies it when it starts, so a
@@ -260,6 +317,42 @@ gts_status gts_set_tuning(gts_index *index, const gts_tuning *tuning);
 gts_status gts_autotune(gts_index *index, const gts_objects *queries, const float *radii, const int32_t *k,
                         const gts_query_opts *opts, int32_t reps, gts_tuning *out);
 
+/* Cost model of Section 5.3.  An object survives the pivots of the first i
+ * levels with probability p^i, p = P(|X - Y| <= r) for the distances X, Y of
+ * two objects to one pivot (Eq. 2), so a batch of nq queries holds about
+ * S_i = nq * fanout^i * p^i (query, node) pairs at level i, and the search
+ * costs about  sum_{i=1..h} i^2 ceil(S_i / C) log2(fanout)^2  (the form of
+ * Eq. 3, C = the GPU's concurrency in threads), plus the same term for the
+ * objects of the surviving leaves, S_{h+1} = nq * n * p^h, which this index
+ * verifies after its h pivot levels.  p in [0, 1]; returns the estimate in
+ * relative units (only comparisons between shapes are meaningful). */
+double gts_cost_model(int64_t n, int64_t nq, double p, int32_t fanout, int32_t h, double concurrency);
+
+/* An index shape (Section 4.2: node capacity and pivot levels) and how it
+ * fared under gts_autotune_shape. */
+typedef struct {
+    int32_t fanout;      /* N_c */
+    int32_t n_pivots;    /* h */
+    double model_cost;   /* gts_cost_model estimate */
+    double measured_ms;  /* median wall time of the sample batch on this shape */
+} gts_shape;
+
+/* Shape autotuner: estimates p of Eq. 2 from the index's own table list (the
+ * distances of a sample of its objects to the root pivot, all pairs) and the
+ * sample batch's radius (range: the median of `radii`; kNN: the mean k-th
+ * distance of a run of the batch), ranks the shapes fanout in 4 .. 64, h in 1
+ * .. Algorithm 1's height for that fanout, by gts_cost_model, rebuilds the
+ * index with each of the `candidates` (1 .. 16) cheapest shapes and with the
+ * current one, times the sample batch (`reps` runs, median of the wall time;
+ * one untimed warm-up run first) on each, and leaves the index rebuilt with
+ * the fastest.  Ids and answers do not change (every shape answers the same
+ * definition).  out: host gts_shape[candidates + 1] (may be NULL), the shapes
+ * timed, fastest first; *n_out (may be NULL) their number.  On an error the
+ * index holds one of the timed shapes. */
+gts_status gts_autotune_shape(gts_index *index, const gts_objects *queries, const float *radii, const int32_t *k,
+                              const gts_query_opts *opts, int32_t candidates, int32_t reps, gts_shape *out,
+                              int32_t *n_out);
+
 /* Diagnostic, no counterpart in the paper: runs the tensor-core tile
  * primitives of the BF16 L2 path (TMA load with 128-byte swizzle, tcgen05.mma
  * with the accumulator in TMEM, tcgen05.ld) on one 128 x N x K product:
@@ -269,6 +362,15 @@ gts_status gts_autotune(gts_index *index, const gts_objects *queries, const floa
  * TMEM by tcgen05.st, one row per TMEM lane, as the tile kernel holds its node
  * blocks. */
 gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, int a_tmem, float *D);
+
+/* Diagnostic, no counterpart in the paper: checks the bounded waits that
+ * every kernel of this library uses on mbarriers.  One thread waits on a
+ * barrier that another thread of its block arrives on only if `post` is
+ * non-zero; the wait polls at most spin_limit times (1 .. 2^26).  Returns
+ * GTS_OK when the arrival came, GTS_ETIMEOUT when the wait ran out (the
+ * kernel then records the run-out in a status word and returns; the device
+ * stays usable), GTS_EINVAL for a limit out of range. */
+gts_status gts_selftest_wait(int32_t post, uint32_t spin_limit);
 
 /* Exact kNN over objects held on the device, by scanning every object, with
  * no device memory allocated by the call.  The paper has no counterpart: it is
@@ -287,8 +389,13 @@ gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, int a_t
  *     same FP64 sums as the reference definition; when n < k the missing
  *     slots hold id -1 and distance +inf.
  *  stream: cudaStream_t (NULL = legacy default stream); returns when done.
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Non-finite inputs are not rejected (checking them would cost a pass over
+ * the objects): an object whose distance comes out NaN (a NaN coordinate in
+ * it or in the query) ranks as distance +inf, after every finite one, by id.
+ * The first call in a CUDA context (normally: on a device) looks up the
+ * array's device address with cudaGetSymbolAddress and caches it under the
+ * context's id; make that first call before any stream capture.  After a
+ * cudaDeviceReset the next call looks the address up again.
  * All calls share the array: calls whose kernels overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. */
 gts_status gts_knn_scan_noalloc(const float *objects, int64_t n, int32_t dim, gts_metric metric,
@@ -312,8 +419,14 @@ gts_status gts_knn_scan_noalloc_async(const float *objects, int64_t n, int32_t d
  * requests that arrive while others are on the GPU join the next batch and
  * several batches overlap on the device.  A request is admitted to a batch
  * only while the projected candidate-table bytes of all admitted requests
- * (visible objects x 37 bytes each) fit result_budget.  The index must not be
- * updated while a server runs on it. */
+ * fit result_budget.  A request's projection is an upper bound of its
+ * candidate rows times 37 bytes: the descent of Section 5.1 run on the host
+ * over the top pivot levels of the tree (a snapshot of at most 4096 pivots
+ * taken by gts_serve_start; at most 64 pivot distances per request), with
+ * Lemma 1's node test on every child's interval (kNN: with the k-th smallest
+ * distance to the visible pivots evaluated so far, an upper bound of d_k),
+ * summing the rows of the surviving nodes plus the cache list.  The index
+ * must not be updated while a server runs on it. */
 typedef struct gts_server gts_server;
 
 typedef struct {
@@ -340,9 +453,16 @@ gts_status gts_serve_submit(gts_server *server, const void *query, int64_t len, 
 gts_status gts_serve_wait(gts_server *server, int64_t ticket, int32_t timeout_ms, gts_result *out,
                           double *latency_ms);
 
-/* Counters: int64[4] = batches run, requests run, largest batch, largest
- * projected bytes in flight. */
-gts_status gts_serve_stats(gts_server *server, int64_t *out4);
+/* Counters, the first n_out of: batches run, requests run, largest batch,
+ * largest projected bytes in flight, sum of the projected bytes of every
+ * submitted request, requests whose projection was below the worst case
+ * (every visible object a candidate). */
+gts_status gts_serve_stats(gts_server *server, int64_t *out, int32_t n_out);
+
+/* The admission projection of one request (as gts_serve_submit would compute
+ * it) in *bytes, without submitting it. */
+gts_status gts_serve_project(gts_server *server, const void *query, int64_t len, int32_t kind, double param,
+                             int64_t *bytes);
 
 /* Finish the pending requests, join the workers, free the server. */
 gts_status gts_serve_stop(gts_server *server);

@@ -18,14 +18,16 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["GTSError", "Index", "lib", "EDIT", "L1", "L2", "PREC_FP32", "PREC_BF16", "STAT_NAMES"]
+__all__ = ["GTSError", "Index", "ShardedIndex", "Server", "lib", "merge_knn", "merge_range", "cost_model", "EDIT",
+           "L1", "L2", "PREC_FP32", "PREC_BF16", "STAT_NAMES"]
 
 EDIT, L1, L2 = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
+QUERY_COUNT_TABLE_PASS, QUERY_KEYS = 1, 2
 METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
 STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows",
               "launches", "tiles", "tile_entries", "tile_pairs",
-              "dense_pairs", "dense_last"]
+              "dense_pairs", "dense_last", "table_pass", "scan_records"]
 STAGE_NAMES = ["pivot_dist", "threshold", "expand", "leaf_scan", "verify", "select", "other", "tile"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,12 +55,13 @@ class _BuildOpts(ctypes.Structure):
 class _QueryOpts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("precision", ctypes.c_int32), ("result_on_device", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("seq", ctypes.c_void_p), ("stats", ctypes.c_void_p),
-                ("stage_ms", ctypes.c_void_p)]
+                ("stage_ms", ctypes.c_void_p), ("flags", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
     _fields_ = [("nq", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("ids", ctypes.c_void_p),
-                ("dist", ctypes.c_void_p), ("on_device", ctypes.c_int32), ("priv_", ctypes.c_void_p)]
+                ("dist", ctypes.c_void_p), ("on_device", ctypes.c_int32), ("priv_", ctypes.c_void_p),
+                ("key", ctypes.c_void_p)]
 
 
 class _ServeOpts(ctypes.Structure):
@@ -76,17 +79,23 @@ class _Info(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("l1_queries", ctypes.c_int32), ("l1_packed", ctypes.c_int32), ("knn_phases", ctypes.c_int32),
                 ("probe_rows", ctypes.c_int32), ("tuned", ctypes.c_int32), ("tc_queries", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32 * 2)]
+                ("str_chunk", ctypes.c_int32), ("str_qgram", ctypes.c_int32)]
 
 
-TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows", "tc_queries"]
+TUNING_FIELDS = ["l1_queries", "l1_packed", "knn_phases", "probe_rows", "tc_queries", "str_chunk", "str_qgram"]
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("fanout", ctypes.c_int32), ("n_pivots", ctypes.c_int32), ("model_cost", ctypes.c_double),
+                ("measured_ms", ctypes.c_double)]
 
 EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts_batch_update", "gts_rebuild",
            "gts_info", "gts_tree_level", "gts_table", "gts_result_copy", "gts_result_free", "gts_free",
-           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_knn_scan_noalloc",
+           "gts_last_error", "gts_status_name", "gts_selftest_tc", "gts_selftest_wait", "gts_knn_scan_noalloc",
            "gts_knn_scan_noalloc_async", "gts_serve_start",
-           "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop", "gts_get_tuning",
-           "gts_set_tuning", "gts_autotune"]
+           "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_project", "gts_serve_stop", "gts_get_tuning",
+           "gts_set_tuning", "gts_autotune", "gts_cost_model", "gts_autotune_shape", "gts_save", "gts_load",
+           "gts_merge_knn", "gts_merge_range"]
 
 
 def lib(path: Optional[str] = None):
@@ -113,20 +122,33 @@ def lib(path: Optional[str] = None):
     L.gts_serve_start.argtypes = [P, ctypes.POINTER(_ServeOpts), ctypes.POINTER(P)]
     L.gts_serve_submit.argtypes = [P, P, I64, I32, ctypes.c_double, ctypes.POINTER(I64)]
     L.gts_serve_wait.argtypes = [P, I64, I32, ctypes.POINTER(_Result), ctypes.POINTER(ctypes.c_double)]
-    L.gts_serve_stats.argtypes = [P, P]
+    L.gts_serve_stats.argtypes = [P, P, I32]
+    L.gts_serve_project.argtypes = [P, P, I64, I32, ctypes.c_double, P]
     L.gts_serve_stop.argtypes = [P]
     L.gts_get_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
     L.gts_set_tuning.argtypes = [P, ctypes.POINTER(_Tuning)]
     L.gts_autotune.argtypes = [P, ctypes.POINTER(_Objects), P, P, ctypes.POINTER(_QueryOpts), I32,
                                ctypes.POINTER(_Tuning)]
     for f in ["gts_serve_start", "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_stop",
-              "gts_get_tuning", "gts_set_tuning", "gts_autotune"]:
+              "gts_serve_project", "gts_get_tuning", "gts_set_tuning", "gts_autotune", "gts_autotune_shape"]:
         getattr(L, f).restype = ctypes.c_int
     for f in ["gts_knn_scan_noalloc", "gts_knn_scan_noalloc_async"]:
         getattr(L, f).argtypes = [P, I64, I32, ctypes.c_int, P, I64, I32, P, P, P]
         getattr(L, f).restype = ctypes.c_int
     L.gts_selftest_tc.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     L.gts_selftest_tc.restype = ctypes.c_int
+    L.gts_cost_model.argtypes = [I64, I64, ctypes.c_double, I32, I32, ctypes.c_double]
+    L.gts_cost_model.restype = ctypes.c_double
+    L.gts_autotune_shape.argtypes = [P, ctypes.POINTER(_Objects), P, P, ctypes.POINTER(_QueryOpts), I32, I32,
+                                     ctypes.POINTER(_Shape), ctypes.POINTER(I32)]
+    L.gts_save.argtypes = [P, ctypes.c_char_p]
+    L.gts_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_BuildOpts), ctypes.POINTER(P)]
+    L.gts_merge_knn.argtypes = [ctypes.POINTER(ctypes.POINTER(_Result)), P, I32, P, ctypes.POINTER(_Result)]
+    L.gts_merge_range.argtypes = [ctypes.POINTER(ctypes.POINTER(_Result)), P, I32, ctypes.POINTER(_Result)]
+    for f in ["gts_save", "gts_load", "gts_merge_knn", "gts_merge_range"]:
+        getattr(L, f).restype = ctypes.c_int
+    L.gts_selftest_wait.argtypes = [I32, ctypes.c_uint32]
+    L.gts_selftest_wait.restype = ctypes.c_int
     L.gts_result_copy.argtypes = [ctypes.POINTER(_Result), P, P, P]
     L.gts_result_copy.restype = ctypes.c_int
     L.gts_result_free.argtypes = [ctypes.POINTER(_Result)]
@@ -142,6 +164,108 @@ def lib(path: Optional[str] = None):
     if path is None:
         _lib = L
     return L
+
+
+def _host_arrays(res):
+    nq = int(res.nq)
+    offsets = np.ctypeslib.as_array(ctypes.cast(res.offsets, ctypes.POINTER(ctypes.c_int64)), (nq + 1,)).copy()
+    tot = int(offsets[-1])
+    ids = np.ctypeslib.as_array(ctypes.cast(res.ids, ctypes.POINTER(ctypes.c_int64)), (max(tot, 1),))[:tot].copy()
+    dist = np.ctypeslib.as_array(ctypes.cast(res.dist, ctypes.POINTER(ctypes.c_float)), (max(tot, 1),))[:tot].copy()
+    kk = None
+    if res.key:
+        kk = np.ctypeslib.as_array(ctypes.cast(res.key, ctypes.POINTER(ctypes.c_double)), (max(tot, 1),))[:tot].copy()
+    return offsets, ids, dist, kk
+
+
+def _c_result(offsets, ids, dist, keys=None):
+    """A host gts_result viewing numpy arrays (kept alive by the caller)."""
+    r = _Result()
+    r.nq = int(len(offsets) - 1)
+    r.offsets = _ptr(offsets).value
+    r.ids = _ptr(ids).value if ids.size else _ptr(np.zeros(1, np.int64)).value
+    r.dist = _ptr(dist).value if dist.size else _ptr(np.zeros(1, np.float32)).value
+    r.on_device = 0
+    r.priv_ = None
+    r.key = _ptr(keys).value if keys is not None and keys.size else (
+        _ptr(np.zeros(1, np.float64)).value if keys is not None else None)
+    return r
+
+
+def _merge(parts, id_base, k=None):
+    """Merge host CSR answers of shards (gts_merge_knn / gts_merge_range).
+    parts: (offsets, ids, dist[, keys]) tuples; returns (offsets, ids, dist, keys)."""
+    keep, structs = [], []
+    for p in parts:
+        off = np.ascontiguousarray(p[0], np.int64)
+        ids = np.ascontiguousarray(p[1], np.int64)
+        dist = np.ascontiguousarray(p[2], np.float32)
+        keys = np.ascontiguousarray(p[3], np.float64) if len(p) > 3 and p[3] is not None else None
+        keep.append((off, ids, dist, keys))
+        structs.append(_c_result(off, ids, dist, keys))
+    arr = (ctypes.POINTER(_Result) * len(structs))(*[ctypes.pointer(x) for x in structs])
+    base = np.ascontiguousarray(id_base, np.int64)
+    out = _Result()
+    if k is not None:
+        nq = int(len(keep[0][0]) - 1)
+        kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)), np.int32)
+        _check(lib().gts_merge_knn(arr, _ptr(base), len(structs), _ptr(kk), ctypes.byref(out)))
+    else:
+        _check(lib().gts_merge_range(arr, _ptr(base), len(structs), ctypes.byref(out)))
+    res = _host_arrays(out)
+    lib().gts_result_free(ctypes.byref(out))
+    return res
+
+
+def merge_knn(parts, id_base, k):
+    """kNN answers of shards over disjoint object sets -> the first k by
+    (FP64 key, global id); parts carry keys (Index.knn(..., keys=True))."""
+    return _merge(parts, id_base, k)
+
+
+def merge_range(parts, id_base):
+    """Range answers of shards -> all answers in ascending global id."""
+    return _merge(parts, id_base)
+
+
+class ShardedIndex:
+    """One GTS index per contiguous slice of the objects (shards over disjoint
+    object sets, object i of shard s is global id base[s] + i), every query
+    sent to every shard, the answers merged exactly (gts_merge_*)."""
+
+    def __init__(self, shards, bases):
+        self.shards, self.bases = shards, np.asarray(bases, np.int64)
+
+    @classmethod
+    def build(cls, objects, metric: str, n_shards: int, **kw) -> "ShardedIndex":
+        n = int(objects.shape[0])
+        cuts = [n * s // n_shards for s in range(n_shards + 1)]
+        return cls([Index.build(objects[cuts[s]:cuts[s + 1]], metric, **kw) for s in range(n_shards)], cuts[:-1])
+
+    def knn(self, queries, k, **kw) -> Result:
+        parts = []
+        for ix in self.shards:
+            r = ix.knn(queries, k, keys=True, **kw)
+            parts.append((r.offsets, r.ids, r.dist, r.keys))
+        off, ids, dist, keys = merge_knn(parts, self.bases, k)
+        return Result(off, ids, dist, keys=keys)
+
+    def range(self, queries, radii, **kw) -> Result:
+        parts = []
+        for ix in self.shards:
+            r = ix.range(queries, radii, **kw)
+            parts.append((r.offsets, r.ids, r.dist))
+        off, ids, dist, _ = merge_range(parts, self.bases)
+        return Result(off, ids, dist)
+
+    def close(self):
+        for ix in self.shards:
+            ix.close()
+
+
+def cost_model(n: int, nq: int, p: float, fanout: int, h: int, concurrency: float) -> float:
+    """The cost model of Section 5.3 (gts_cost_model)."""
+    return float(lib().gts_cost_model(int(n), int(nq), float(p), int(fanout), int(h), float(concurrency)))
 
 
 def selftest_tc(A, B, a_tmem=False):
@@ -222,10 +346,12 @@ class _Marshal:
 
 
 class Result:
-    """CSR answers: ids/dist[offsets[i]:offsets[i+1]] belong to query i."""
+    """CSR answers: ids/dist[offsets[i]:offsets[i+1]] belong to query i
+    (``keys``: the answers' FP64 keys, kNN with ``keys=True``)."""
 
-    def __init__(self, offsets, ids, dist, stats=None, device_result=None):
+    def __init__(self, offsets, ids, dist, stats=None, device_result=None, keys=None):
         self.offsets, self.ids, self.dist, self.stats = offsets, ids, dist, stats
+        self.keys = keys
         self._dev = device_result
 
     def query(self, i):
@@ -267,7 +393,8 @@ class Index:
                                ctypes.byref(opts), ctypes.byref(h)))
         return cls(h, metric)
 
-    def _query(self, fn, queries, per_query, precision, result_on_device, memory_budget, seq, stream, timing=False):
+    def _query(self, fn, queries, per_query, precision, result_on_device, memory_budget, seq, stream, timing=False,
+               count_table_pass=False, keys=False):
         m = _Marshal(queries)
         stats = np.zeros(len(STAT_NAMES), np.int64)
         stage = np.zeros(2 * len(STAGE_NAMES), np.float64) if timing else None
@@ -275,7 +402,8 @@ class Index:
                           precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
                           result_on_device=1 if result_on_device else 0, memory_budget=int(memory_budget),
                           seq=_ptr(seq).value if seq is not None else None, stats=_ptr(stats).value,
-                          stage_ms=_ptr(stage).value if timing else None)
+                          stage_ms=_ptr(stage).value if timing else None,
+                          flags=(QUERY_COUNT_TABLE_PASS if count_table_pass else 0) | (QUERY_KEYS if keys else 0))
         res = _Result()
         _check(fn(self._h, ctypes.byref(m.obj), _ptr(per_query), ctypes.byref(opts), ctypes.byref(res)))
         st = dict(zip(STAT_NAMES, stats.tolist()))
@@ -286,24 +414,21 @@ class Index:
         nq = int(res.nq)
         if res.on_device:
             return Result(res.offsets, res.ids, res.dist, st, device_result=res)
-        offsets = np.ctypeslib.as_array(ctypes.cast(res.offsets, ctypes.POINTER(ctypes.c_int64)), (nq + 1,)).copy()
-        tot = int(offsets[-1])
-        ids = np.ctypeslib.as_array(ctypes.cast(res.ids, ctypes.POINTER(ctypes.c_int64)), (max(tot, 1),))[:tot].copy()
-        dist = np.ctypeslib.as_array(ctypes.cast(res.dist, ctypes.POINTER(ctypes.c_float)), (max(tot, 1),))[:tot].copy()
+        offsets, ids, dist, kk = _host_arrays(res)
         lib().gts_result_free(ctypes.byref(res))
-        return Result(offsets, ids, dist, st)
+        return Result(offsets, ids, dist, st, keys=kk)
 
     def range(self, queries, radii, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
-              stream=None, timing=False) -> Result:
+              stream=None, timing=False, count_table_pass=False) -> Result:
         if _is_torch(radii):
             r = radii.contiguous()
         else:
             r = np.ascontiguousarray(radii, np.float32)
         return self._query(lib().gts_range, queries, r, precision, result_on_device, memory_budget, seq, stream,
-                           timing)
+                           timing, count_table_pass)
 
     def knn(self, queries, k, precision="fp32", result_on_device=False, memory_budget=0, seq=None,
-            stream=None, timing=False) -> Result:
+            stream=None, timing=False, count_table_pass=False, keys=False) -> Result:
         if _is_torch(k):
             kk = k.contiguous()
         else:
@@ -311,7 +436,21 @@ class Index:
                 queries.n if hasattr(queries, "n") else int(queries[1].shape[0]) - 1)
             kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
         return self._query(lib().gts_knn, queries, kk, precision, result_on_device, memory_budget, seq, stream,
-                           timing)
+                           timing, count_table_pass, keys)
+
+    def save(self, path: str):
+        """Write the whole index to a file (gts_save)."""
+        _check(lib().gts_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, metric: Optional[str] = None, stream=None, cache_limit: int = 0) -> "Index":
+        """Read an index written by save onto the current device (gts_load)."""
+        opts = _BuildOpts(stream=stream, root_pivot=-1, seed=0, cache_limit=int(cache_limit))
+        h = ctypes.c_void_p()
+        _check(lib().gts_load(os.fsencode(path), ctypes.byref(opts), ctypes.byref(h)))
+        ix = cls(h, metric or "")
+        ix.metric = {EDIT: "edit", L1: "l1", L2: "l2"}[ix.info()["metric"]]
+        return ix
 
     def get_tuning(self) -> dict:
         t = _Tuning()
@@ -344,6 +483,32 @@ class Index:
                                   _ptr(kk) if kk is not None else None, ctypes.byref(opts), int(reps),
                                   ctypes.byref(out)))
         return {f: int(getattr(out, f)) for f in TUNING_FIELDS + ["tuned"]}
+
+    def autotune_shape(self, queries, k=None, radii=None, precision="fp32", candidates=4, reps=2,
+                       memory_budget=0, stream=None) -> list:
+        """Rank index shapes (fanout, pivot levels) by the cost model of
+        Section 5.3, rebuild and time the cheapest ones on the sample batch and
+        keep the fastest (gts_autotune_shape); returns the shapes timed,
+        fastest first."""
+        m = _Marshal(queries)
+        n = m.obj.n
+        kk = None if k is None else np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
+        rr = None if radii is None else np.ascontiguousarray(np.broadcast_to(np.asarray(radii, np.float32), (n,)),
+                                                             np.float32)
+        if m.obj.on_device:
+            import torch
+            kk = None if kk is None else torch.from_numpy(kk.copy()).cuda()
+            rr = None if rr is None else torch.from_numpy(rr.copy()).cuda()
+        opts = _QueryOpts(stream=stream if stream is not None else _stream_of(m.first),
+                          precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
+                          memory_budget=int(memory_budget))
+        out = (_Shape * (int(candidates) + 1))()
+        cnt = ctypes.c_int32()
+        _check(lib().gts_autotune_shape(self._h, ctypes.byref(m.obj), _ptr(rr) if rr is not None else None,
+                                        _ptr(kk) if kk is not None else None, ctypes.byref(opts), int(candidates),
+                                        int(reps), out, ctypes.byref(cnt)))
+        return [dict(fanout=out[i].fanout, n_pivots=out[i].n_pivots, model_cost=out[i].model_cost,
+                     measured_ms=out[i].measured_ms) for i in range(cnt.value)]
 
     def insert(self, objects) -> np.ndarray:
         m = _Marshal(objects)
@@ -443,9 +608,22 @@ class Server:
         return ids, dist, float(lat.value)
 
     def stats(self) -> dict:
-        out = np.zeros(4, np.int64)
-        _check(lib().gts_serve_stats(self._h, _ptr(out)))
-        return dict(batches=int(out[0]), requests=int(out[1]), max_batch=int(out[2]), max_in_flight=int(out[3]))
+        out = np.zeros(6, np.int64)
+        _check(lib().gts_serve_stats(self._h, _ptr(out), 6))
+        return dict(batches=int(out[0]), requests=int(out[1]), max_batch=int(out[2]), max_in_flight=int(out[3]),
+                    projected_bytes=int(out[4]), below_worst_case=int(out[5]))
+
+    def project(self, query, kind: str, param) -> int:
+        """The admission projection (bytes) of one request, not submitted."""
+        if isinstance(query, (bytes, bytearray)):
+            buf = np.frombuffer(bytes(query) or b"\0", np.uint8)
+            n = len(query)
+        else:
+            buf = np.ascontiguousarray(query, np.float32)
+            n = buf.size
+        out = np.zeros(1, np.int64)
+        _check(lib().gts_serve_project(self._h, _ptr(buf), n, 0 if kind == "range" else 1, float(param), _ptr(out)))
+        return int(out[0])
 
     def stop(self):
         if self._h:

@@ -50,6 +50,10 @@ gts_status guarded(F &&f) {
     }
 }
 
+}  // namespace
+
+// Throws GTS_ECUDA when no device is usable; sets the stream-ordered pool
+// to keep freed memory cached (once per device).
 void ensure_device() {
     int n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
@@ -68,6 +72,8 @@ void ensure_device() {
         pool_set[dev] = true;
     }
 }
+
+namespace {
 
 __global__ void k_nonfinite(const float *x, int64_t n, int *flag) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -375,12 +381,15 @@ struct ResultPriv {
 void fill_result(gts_result *res, int64_t nq, QueryOut &qo, bool on_device, cudaStream_t st) {
     res->nq = nq;
     res->on_device = on_device ? 1 : 0;
+    res->key = nullptr;
+    const bool keys = qo.key.get() != nullptr;
     if (on_device) {
         auto *p = new ResultPriv();
         p->out = std::move(qo);
         res->offsets = p->out.offsets.get();
         res->ids = p->out.ids.get();
         res->dist = p->out.dist.get();
+        res->key = keys ? p->out.key.get() : nullptr;
         res->priv_ = p;
         return;
     }
@@ -388,20 +397,24 @@ void fill_result(gts_result *res, int64_t nq, QueryOut &qo, bool on_device, cuda
     res->offsets = (int64_t *)std::malloc(sizeof(int64_t) * (nq + 1));
     res->ids = (int64_t *)std::malloc(sizeof(int64_t) * (tot > 0 ? tot : 1));
     res->dist = (float *)std::malloc(sizeof(float) * (tot > 0 ? tot : 1));
+    if (keys) res->key = (double *)std::malloc(sizeof(double) * (tot > 0 ? tot : 1));
     res->priv_ = nullptr;
-    if (!res->offsets || !res->ids || !res->dist) {
+    if (!res->offsets || !res->ids || !res->dist || (keys && !res->key)) {
         std::free(res->offsets);
         std::free(res->ids);
         std::free(res->dist);
+        std::free(res->key);
         res->offsets = nullptr;
         res->ids = nullptr;
         res->dist = nullptr;
+        res->key = nullptr;
         throw std::bad_alloc();
     }
     GTS_CUDA(cudaMemcpyAsync(res->offsets, qo.offsets.get(), (nq + 1) * 8, cudaMemcpyDeviceToHost, st));
     if (tot) {
         GTS_CUDA(cudaMemcpyAsync(res->ids, qo.ids.get(), tot * 8, cudaMemcpyDeviceToHost, st));
         GTS_CUDA(cudaMemcpyAsync(res->dist, qo.dist.get(), tot * 4, cudaMemcpyDeviceToHost, st));
+        if (keys) GTS_CUDA(cudaMemcpyAsync(res->key, qo.key.get(), tot * 8, cudaMemcpyDeviceToHost, st));
     }
     GTS_CUDA(cudaStreamSynchronize(st));
 }
@@ -456,6 +469,8 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
             qb.seq = dseq.get();
         }
         const int64_t budget = opts && opts->memory_budget > 0 ? opts->memory_budget : ((int64_t)64 << 30);
+        qb.count_table_pass = opts && (opts->flags & GTS_QUERY_COUNT_TABLE_PASS) != 0;
+        qb.want_keys = knn && opts && (opts->flags & GTS_QUERY_KEYS) != 0;
         QueryOut qo;
         run_query(ix, qb, knn, opts ? opts->precision : 0, budget, qo, opts ? opts->stats : nullptr,
                   opts ? opts->stage_ms : nullptr, st);
@@ -470,6 +485,10 @@ void check_tuning(const gts_tuning *t) {
     GTS_REQUIRE(t->knn_phases >= 1 && t->knn_phases <= 3, GTS_EINVAL, "knn_phases must be in 1 .. 3");
     GTS_REQUIRE(t->probe_rows >= 0 && t->probe_rows <= 4096, GTS_EINVAL, "probe_rows must be in 0 .. 4096");
     GTS_REQUIRE(t->tc_queries == 96 || t->tc_queries == 128, GTS_EINVAL, "tc_queries must be 96 or 128");
+    GTS_REQUIRE(t->str_chunk == 64 || t->str_chunk == 128 || t->str_chunk == 256 || t->str_chunk == 512, GTS_EINVAL,
+                "str_chunk must be 64, 128, 256 or 512");
+    GTS_REQUIRE(t->str_qgram == 0 || t->str_qgram == 32 || t->str_qgram == 64, GTS_EINVAL,
+                "str_qgram must be 0, 32 or 64");
 }
 
 gts_tuning to_c(const Tuning &t) {
@@ -480,6 +499,8 @@ gts_tuning to_c(const Tuning &t) {
     o.knn_phases = t.knn_phases;
     o.probe_rows = t.probe_rows;
     o.tc_queries = t.tc_queries;
+    o.str_chunk = t.str_chunk;
+    o.str_qgram = t.str_qgram;
     o.tuned = t.tuned;
     return o;
 }
@@ -491,6 +512,8 @@ Tuning from_c(const gts_tuning &o, int tuned) {
     t.knn_phases = o.knn_phases;
     t.probe_rows = o.probe_rows;
     t.tc_queries = o.tc_queries;
+    t.str_chunk = o.str_chunk;
+    t.str_qgram = o.str_qgram;
     t.tuned = tuned;
     return t;
 }
@@ -743,6 +766,13 @@ gts_status gts_selftest_tc(const float *A, const float *B, int N, int K, int a_t
     });
 }
 
+gts_status gts_selftest_wait(int32_t post, uint32_t spin_limit) {
+    return guarded([&] {
+        ensure_device();
+        wait_selftest(post, spin_limit);
+    });
+}
+
 gts_status gts_get_tuning(gts_index *ix, gts_tuning *out) {
     return guarded([&] {
         GTS_REQUIRE(ix != nullptr && out != nullptr, GTS_EINVAL, "index or output is NULL");
@@ -777,6 +807,7 @@ gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *
     if (opts) o = *opts;
     o.stats = nullptr;
     o.stage_ms = nullptr;
+    o.flags = 0;
     o.result_on_device = 1;
     // one setting: the median wall time of `reps` runs of the sample batch
     auto time_it = [&](const gts_tuning &t, double &ms) -> gts_status {
@@ -806,6 +837,10 @@ gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *
     }
     if (knn && ix->metric != GTS_EDIT) space.push_back({&gts_tuning::probe_rows, {0, 256, 1024, 4096}});
     if (ix->metric == GTS_L2 && ix->dim <= 128) space.push_back({&gts_tuning::tc_queries, {128, 96}});
+    if (ix->metric == GTS_EDIT) {
+        space.push_back({&gts_tuning::str_chunk, {64, 128, 256, 512}});
+        if (o.precision == GTS_PREC_BF16) space.push_back({&gts_tuning::str_qgram, {0, 32, 64}});
+    }
     double best_ms = 0.0;
     s = time_it(best, best_ms);   // the first run also warms every lazily built structure
     if (s == GTS_OK) s = time_it(best, best_ms);
@@ -833,6 +868,165 @@ gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *
     return s != GTS_OK ? s : s2;
 }
 
+double gts_cost_model(int64_t n, int64_t nq, double p, int32_t fanout, int32_t h, double concurrency) {
+    if (n < 0 || nq < 0 || fanout < 2 || h < 1 || !(concurrency >= 1.0) || !(p >= 0.0 && p <= 1.0)) return -1.0;
+    const double lf = std::log2((double)fanout);
+    double cost = 0.0, level = (double)nq;   // S_i = nq (fanout p)^i
+    for (int i = 1; i <= h; ++i) {
+        level *= (double)fanout * p;
+        cost += (double)i * i * std::ceil(level / concurrency) * lf * lf;
+    }
+    const double objs = (double)nq * (double)n * std::pow(p, h);   // objects of the surviving leaves
+    cost += (double)(h + 1) * (h + 1) * std::ceil(objs / concurrency) * lf * lf;
+    return cost;
+}
+
+namespace {
+
+// P(|X - Y| <= r) over all pairs of a sample of one pivot's distances (Eq. 2)
+double pair_prob(std::vector<float> x, double r) {
+    std::sort(x.begin(), x.end());
+    const size_t m = x.size();
+    if (m < 2) return 1.0;
+    double within = 0.0;
+    size_t j = 0;
+    for (size_t i = 0; i < m; ++i) {   // pairs (j, i), j < i, with x_i - x_j <= r
+        while ((double)x[i] - (double)x[j] > r) ++j;
+        within += (double)(i - j);
+    }
+    return within / ((double)m * (double)(m - 1) / 2.0);
+}
+
+}  // namespace
+
+gts_status gts_autotune_shape(gts_index *ix, const gts_objects *queries, const float *radii, const int32_t *k,
+                              const gts_query_opts *opts, int32_t candidates, int32_t reps, gts_shape *out,
+                              int32_t *n_out) {
+    std::vector<gts_shape> timed;
+    gts_status s = guarded([&] {
+        GTS_REQUIRE(ix != nullptr && queries != nullptr, GTS_EINVAL, "index or queries is NULL");
+        GTS_REQUIRE((radii == nullptr) != (k == nullptr), GTS_EINVAL, "give radii (range) or k (kNN), not both");
+        GTS_REQUIRE(reps >= 1 && reps <= 100, GTS_EINVAL, "reps must be in 1 .. 100");
+        GTS_REQUIRE(candidates >= 1 && candidates <= 16, GTS_EINVAL, "candidates must be in 1 .. 16");
+        GTS_REQUIRE(queries->n > 0, GTS_EINVAL, "the sample batch is empty");
+        ensure_device();
+        GTS_CUDA(cudaSetDevice(ix->device));
+        const bool knn = k != nullptr;
+        gts_query_opts o;
+        std::memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        o.stats = nullptr;
+        o.stage_ms = nullptr;
+        o.flags = 0;
+        // the radius of Eq. 2: range -> the median radius; kNN -> the mean k-th distance
+        double r = 0.0;
+        {
+            gts_query_opts oh = o;
+            oh.result_on_device = 0;
+            gts_result res;
+            std::memset(&res, 0, sizeof(res));
+            gts_status q = query_common(ix, queries, radii, k, &oh, &res, knn);
+            if (q != GTS_OK) throw Error(q, gts_last_error());
+            if (knn) {
+                double sum = 0.0;
+                int64_t cnt = 0;
+                for (int64_t i = 0; i < res.nq; ++i)
+                    if (res.offsets[i + 1] > res.offsets[i]) {
+                        sum += res.dist[res.offsets[i + 1] - 1];
+                        ++cnt;
+                    }
+                r = cnt ? sum / (double)cnt : 0.0;
+            } else {
+                std::vector<float> hr(queries->n);
+                if (queries->on_device)
+                    GTS_CUDA(cudaMemcpy(hr.data(), radii, queries->n * 4, cudaMemcpyDeviceToHost));
+                else
+                    std::memcpy(hr.data(), radii, queries->n * 4);
+                std::nth_element(hr.begin(), hr.begin() + hr.size() / 2, hr.end());
+                r = hr[hr.size() / 2];
+            }
+            gts_result_free(&res);
+        }
+        // p from the table list: distances of a sample of rows to the root pivot
+        const Tree &t = ix->tree;
+        const int64_t n = t.n;
+        double p = 1.0;
+        if (n > 1) {
+            const int64_t m = std::min<int64_t>(n, 4096);
+            std::vector<float> col(n);
+            GTS_CUDA(cudaMemcpy(col.data(), t.table.get(), n * 4, cudaMemcpyDeviceToHost));
+            std::vector<float> smp(m);
+            for (int64_t i = 0; i < m; ++i) smp[i] = col[(i * n) / m];
+            p = pair_prob(std::move(smp), r);
+        }
+        int sms = 0;
+        GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+        const double C = (double)(sms > 0 ? sms : 1) * 2048.0;
+        const int64_t nq = queries->n;
+        // rank every shape by the model
+        std::vector<gts_shape> all;
+        for (int F : {4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64}) {
+            const int hmax = tree_height(n + ix->cache.count, F, 0);
+            for (int h = 1; h <= hmax; ++h) {
+                gts_shape sh;
+                sh.fanout = F;
+                sh.n_pivots = h;
+                sh.model_cost = gts_cost_model(n, nq, p, F, h, C);
+                sh.measured_ms = 0.0;
+                all.push_back(sh);
+            }
+        }
+        std::stable_sort(all.begin(), all.end(),
+                         [](const gts_shape &a, const gts_shape &b) { return a.model_cost < b.model_cost; });
+        std::vector<gts_shape> cand(all.begin(), all.begin() + std::min<size_t>(all.size(), (size_t)candidates));
+        {
+            gts_shape cur;
+            cur.fanout = ix->F;
+            cur.n_pivots = ix->tree.h;
+            cur.model_cost = gts_cost_model(n, nq, p, ix->F, ix->tree.h, C);
+            cur.measured_ms = 0.0;
+            bool have = false;
+            for (auto &c : cand) have = have || (c.fanout == cur.fanout && c.n_pivots == cur.n_pivots);
+            if (!have) cand.insert(cand.begin(), cur);
+        }
+        o.result_on_device = 1;
+        auto time_shape = [&](gts_shape &sh) {
+            ix->F = sh.fanout;
+            ix->n_pivots_req = sh.n_pivots;
+            rebuild(ix);
+            std::vector<double> v;
+            for (int i = 0; i <= reps; ++i) {   // run 0 warms the lazily built per-index data
+                gts_result res;
+                std::memset(&res, 0, sizeof(res));
+                const auto t0 = std::chrono::steady_clock::now();
+                gts_status q = query_common(ix, queries, radii, k, &o, &res, knn);
+                const auto t1 = std::chrono::steady_clock::now();
+                if (q != GTS_OK) throw Error(q, gts_last_error());
+                gts_result_free(&res);
+                if (i > 0) v.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            std::sort(v.begin(), v.end());
+            sh.measured_ms = v[v.size() / 2];
+        };
+        for (auto &sh : cand) {
+            time_shape(sh);
+            timed.push_back(sh);
+        }
+        std::stable_sort(timed.begin(), timed.end(),
+                         [](const gts_shape &a, const gts_shape &b) { return a.measured_ms < b.measured_ms; });
+        const gts_shape &best = timed.front();
+        if (ix->F != best.fanout || ix->tree.h != best.n_pivots) {
+            ix->F = best.fanout;
+            ix->n_pivots_req = best.n_pivots;
+            rebuild(ix);
+        }
+    });
+    if (out)
+        for (size_t i = 0; i < timed.size(); ++i) out[i] = timed[i];
+    if (n_out) *n_out = (int32_t)timed.size();
+    return s;
+}
+
 void gts_result_free(gts_result *r) {
     if (!r) return;
     if (r->priv_) {
@@ -841,10 +1035,12 @@ void gts_result_free(gts_result *r) {
         std::free(r->offsets);
         std::free(r->ids);
         std::free(r->dist);
+        std::free(r->key);
     }
     r->offsets = nullptr;
     r->ids = nullptr;
     r->dist = nullptr;
+    r->key = nullptr;
     r->priv_ = nullptr;
     r->nq = 0;
 }

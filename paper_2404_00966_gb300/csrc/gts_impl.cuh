@@ -46,6 +46,7 @@ struct Error : std::runtime_error {
 };
 
 void set_last_error(const std::string &msg);
+void ensure_device();   // GTS_ECUDA unless a CUDA device is usable
 
 #define GTS_CUDA(call)                                                                              \
     do {                                                                                            \
@@ -178,6 +179,8 @@ struct Tuning {
     int knn_phases = 3;     // L1 tile kNN: phases (1..3)
     int probe_rows = 1024;  // kNN probe: rows evaluated before the descent (0..4096)
     int tc_queries = 128;   // tensor-core tiles (dim <= 128): queries per chunk, 128 (2 slots) or 96 (3 slots)
+    int str_chunk = 256;    // strings: (query, object) pairs per block of the DP kernels
+    int str_qgram = 64;     // strings: 3-gram filter off (0) or its queries per chunk (32, 64)
     int tuned = 0;
 };
 
@@ -201,6 +204,7 @@ struct gts_index {
     gts::Tuning tuning;
     std::atomic<int64_t> tc_pairs_hint[2] = {{0}, {0}}; // last tensor-core output size per query (x1024)
     std::atomic<int64_t> l1_pairs_hint[4] = {{0}, {0}, {0}, {0}};  // L1 tiles: range, kNN phases 0..2 (same unit)
+    std::atomic<int64_t> scan_pairs_hint[2] = {{0}, {0}};  // table scan: candidates per query (x1024), range / kNN
     ~gts_index() {
         for (auto e : events) cudaEventDestroy(e);
     }
@@ -227,11 +231,14 @@ struct QueryBatch {
     const int64_t *seq = nullptr;    // device or null
     int64_t seq_now = 0;
     int64_t max_k = 0;
+    bool count_table_pass = false;   // diagnostics: count the pairs passing the table bound
+    bool want_keys = false;          // kNN: also return each answer's FP64 key
 };
 
 struct QueryOut {
     DBuf<int64_t> offsets, ids;
     DBuf<float> dist;
+    DBuf<double> key;   // kNN with GTS_QUERY_KEYS: the FP64 key of each answer
     int64_t total = 0;
 };
 

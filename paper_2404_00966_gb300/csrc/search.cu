@@ -31,6 +31,7 @@
 #include "tile_l1.cuh"
 #include "tile_str.cuh"
 #include "tile_tc.cuh"
+#include "scan.cuh"
 
 namespace gts {
 namespace {
@@ -856,6 +857,66 @@ __global__ void k_leafscan(Dev d, const int32_t *__restrict__ eq, const int32_t 
     }
 }
 
+// ---------------------------------------------------------------- diagnostics
+
+// Per-query distances to every pivot level, for the count below.
+struct DenseLevels {
+    const float *D[kMaxHeight];   // level l: [nq, P_l], query-major
+    int64_t P[kMaxHeight];
+};
+
+// Diagnostics (not on the answer path): the dense last level's (query, row)
+// pairs that pass visibility and the table lower bound of Lemma 1 / 2 on
+// every pivot of the row's path, with the search's FP32 slack -- the
+// candidates C_q a per-candidate verification would check.  Thread per
+// (last-level node, column position) pair of the leaf-mask matrix M.
+__global__ void k_count_table_pass_dense(Dev d, DenseLevels dl, const uint64_t *__restrict__ M,
+                                         const int32_t *__restrict__ perm, int64_t P, int64_t nq, int64_t lvl_leaf,
+                                         const float *__restrict__ thr_q, unsigned long long *__restrict__ count) {
+    unsigned long long c = 0;
+    const int64_t total = P * nq;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = M[t];
+        if (!m) continue;
+        const int64_t p = t / nq, pos = t - p * nq;
+        const int64_t q = perm ? (int64_t)perm[pos] : pos;
+        float dq[kMaxHeight];
+        int64_t anc = p;   // the level-l ancestor of node p (Eq. 1: parent = child / F)
+        for (int l = d.h - 1; l >= 0; --l) {
+            dq[l] = dl.D[l][q * dl.P[l] + anc];
+            anc /= d.F;
+        }
+        const float thr = thr_q[q];
+        const int64_t s = d.qseq[q];
+        for (int j = 0; j < d.F; ++j) {
+            if (!((m >> j) & 1ull)) continue;
+            const int64_t leaf = lvl_leaf + p * d.F + j;
+            const int64_t r0 = d.npos[leaf], r1 = r0 + d.nsize[leaf];
+            for (int64_t r = r0; r < r1; ++r) {
+                if (d.row_del[r] <= s) continue;
+                bool pass = true;
+                for (int l = 0; l < d.h && pass; ++l) {
+                    const float T = d.table[(int64_t)l * d.n + r];
+                    const float eps = d.epsc > 0.f ? d.epsc * (T + dq[l] + thr) : 0.f;
+                    if (fabsf(T - dq[l]) > thr + eps) pass = false;
+                }
+                c += pass ? 1 : 0;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+__global__ void k_sum_i32(const int32_t *__restrict__ a, int64_t n, unsigned long long *__restrict__ out) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (unsigned long long)a[i];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // Cache list (Section 4.4): every (query, cache slot) pair of a query range.
 __global__ void k_cache_cands(int64_t qa, int64_t qb, int64_t n, int64_t cn, int32_t *cq, int32_t *crow) {
     const int64_t total = (qb - qa) * cn;
@@ -949,6 +1010,51 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
         }
         }
     }
+    }
+}
+
+// The same verification for vectors of at most 16 dimensions, a thread per
+// pair: at low dimension a warp per pair leaves most lanes idle, while a
+// thread reads its whole row (consecutive pairs of a query read consecutive
+// rows) and sums it in FP32 in coordinate order, within the same error bound.
+template <bool L2, bool KNN>
+__global__ void k_verify_lowdim(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
+                                const float *__restrict__ thr_q, float *__restrict__ cdist,
+                                uint8_t *__restrict__ keep, unsigned long long *__restrict__ rechecks) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = cq[c];
+        const int64_t row = crow[c];
+        if (row >= d.n && !row_visible(d, row, d.qseq[q])) {
+            cdist[c] = __int_as_float(0x7f800000);
+            keep[c] = 0;
+            continue;
+        }
+        const float *qv = d.Q + (int64_t)q * d.dim;
+        const float *xv = vrow(d, row);
+        float sum = 0.f;
+        for (int i = 0; i < d.dim; ++i) {
+            const float t = qv[i] - xv[i];
+            sum = L2 ? fmaf(t, t, sum) : sum + fabsf(t);
+        }
+        const float d32 = L2 ? sqrtf(sum) : sum;
+        const float r = thr_q[q];
+        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
+        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        if (KNN) {
+            cdist[c] = d32;
+            keep[c] = lo <= r ? 1 : 0;
+        } else if (hi < r * (1.f - 1e-9f)) {
+            keep[c] = 1;
+            cdist[c] = d32;
+        } else if (lo > r * (1.f + 1e-9f)) {
+            keep[c] = 0;
+        } else {
+            const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+            const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
+            keep[c] = key <= lim ? 1 : 0;
+            cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
+            atomicAdd(rechecks, 1ull);
+        }
     }
 }
 
@@ -1649,13 +1755,15 @@ __global__ void k_knn_counts(const int32_t *bn, int64_t nq, int64_t *counts) {
 
 __global__ void k_knn_emit(const int64_t *__restrict__ offsets, const int64_t *__restrict__ koff,
                            const double *__restrict__ bd, const int64_t *__restrict__ bi, const int32_t *__restrict__ bn,
-                           int64_t nq, bool l2, int64_t *__restrict__ ids, float *__restrict__ dist) {
+                           int64_t nq, bool l2, int64_t *__restrict__ ids, float *__restrict__ dist,
+                           double *__restrict__ keys) {
     const int64_t q = blockIdx.x;
     if (q >= nq) return;
     for (int i = threadIdx.x; i < bn[q]; i += blockDim.x) {
         const double key = bd[koff[q] + i];
         ids[offsets[q] + i] = bi[koff[q] + i];
         dist[offsets[q] + i] = __double2float_rn(l2 ? __dsqrt_rn(key) : key);
+        if (keys) keys[offsets[q] + i] = key;
     }
 }
 
@@ -1808,11 +1916,13 @@ struct Runner {
     std::vector<int64_t> rcounts;
     DBuf<unsigned long long> counters;   // [0] rechecks, [1] scanned rows
     int64_t st_pivots = 0, st_frontier = 0, st_cands = 0, st_groups = 0, st_cache = 0;
-    int64_t st_tiles = 0, st_tile_entries = 0;
+    int64_t st_tiles = 0, st_tile_entries = 0, st_table_pass = 0;
+    int64_t st_scan_rows = 0, st_scan_records = 0;   // node-major scan: table rows read, records tested
     StageClock clk;
     bool use_tc = false;   // BF16 tensor-core tiles at the last level (L2)
     bool use_l1 = false;   // FP32 CUDA-core tiles at the last level (L1)
     bool use_qg = false;   // 3-gram filtering tiles at the last level (edit distance)
+    bool use_scan = false; // low-dim vectors: node-major table scan + CUDA-core verification
     Tuning tu;             // launch parameters (a copy of the index's)
     // dense query-to-pivot matrices per level (tile paths): state 0 undecided, 1 ready, 2 not used
     std::vector<DBuf<float>> dense;
@@ -1824,6 +1934,7 @@ struct Runner {
     DBuf<float> tcqn2;
     DBuf<int32_t> qkey;         // kNN: the probe's last-level node per query (qkey_ok once written)
     bool qkey_ok = false;
+    DBuf<unsigned long long> tp_count;   // diagnostics: [0] pairs passing the table bound, [1] scratch
 
     Runner(gts_index *i, const QueryBatch &b, bool k, int64_t bud, cudaStream_t s)
         : ix(i), qb(b), knn(k), budget(bud), st(s) {
@@ -1851,7 +1962,7 @@ struct Runner {
     // reaches the level if its frontier holds at least a quarter of the
     // batch's (query, node) pairs and the matrix fits an eighth of the budget.
     const float *dense_for(int l, int64_t E) {
-        if (!(use_tc || use_l1) || d.dim == 0) return nullptr;
+        if (!(use_tc || use_l1 || use_scan) || d.dim == 0) return nullptr;
         if ((int)dense_state.size() < h) {
             dense_state.assign(h, 0);
             dense.resize(h);
@@ -1914,7 +2025,7 @@ struct Runner {
             }
 #undef GTS_PV
         } else {
-            const int chunk = 256;
+            const int chunk = tu.str_chunk;
 #define GTS_PIV(WW)                                                                                                  \
     k_pivdist_str<WW><<<nblocks(E, chunk), 128, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, chunk, L.path.get(), \
                                                          l)
@@ -1977,7 +2088,7 @@ struct Runner {
 
     void process(Level &L, int64_t e0, int64_t e1, int l) {
         if (e1 <= e0) return;
-        if ((use_tc || use_l1) && l == h - 1) {
+        if ((use_tc || use_l1 || use_scan) && l == h - 1) {
             last_level_tc(L, e0, e1, l);
             return;
         }
@@ -2037,6 +2148,7 @@ struct Runner {
                 return;
             }
             if (use_qg) {
+                count_table_pass(L, e0, e1, mask);
                 str_leaf(L, e0, e1, mask);
                 return;
             }
@@ -2052,6 +2164,7 @@ struct Runner {
             DBuf<int64_t> off;
             scan_i32(cnt, E, off);
             const int64_t total = d2h_i64(off.get() + E, st);
+            st_table_pass += total;   // the plain scan's candidates are exactly the pairs passing the bound
             if (total == 0) return;
             const int64_t cand_bytes = 4 + 4 + 4 + 1 + 8 + 16;
             auto gb = groups(off, E, total, (budget / 2) / cand_bytes);
@@ -2253,6 +2366,16 @@ struct Runner {
         clk.begin(GTS_STAGE_OTHER, 6);
         tc_dense_items(ix->tree, nq, M.get(), rg, st);
         clk.end();
+        if (qb.count_table_pass) {
+            DenseLevels dl;
+            for (int l = 0; l < h; ++l) {
+                dl.D[l] = dense[l].get();
+                dl.P[l] = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
+            }
+            k_count_table_pass_dense<<<cap(nblocks(P * nq, kT)), kT, 0, st>>>(
+                d, dl, M.get(), perm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), tp_count.get());
+            check_launch("dense table-pass count");
+        }
         TcQuery tq = tc_query_base();
         if (perm.get()) {
             tq.perm = perm.get();
@@ -2260,6 +2383,21 @@ struct Runner {
             tq.Ql = (const __nv_bfloat16 *)pQl.get();
         }
         tc_finish(tq, rg);
+    }
+
+    // Diagnostics (GTS_QUERY_COUNT_TABLE_PASS): the pairs of the last-level
+    // entries [e0, e1) that pass visibility and the table bound, with the
+    // thresholds the leaf stage is about to use.
+    void count_table_pass(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask) {
+        if (!qb.count_table_pass || e1 <= e0) return;
+        const int64_t E = e1 - e0;
+        DBuf<int32_t> cnt(E, st);
+        k_leafscan<false><<<nblocks(E, kWarpsPerBlock), kT, 0, st>>>(d, L.q.get(), L.node.get(), L.path.get(),
+                                                                     ix->tree.lvl_off[h - 1], e0, e1, mask.get(),
+                                                                     thr.get(), cnt.get(), nullptr, nullptr, nullptr,
+                                                                     tp_count.get() + 1);
+        k_sum_i32<<<cap(nblocks(E, kT)), kT, 0, st>>>(cnt.get(), E, tp_count.get());
+        check_launch("table-pass count");
     }
 
     TcQuery tc_query_base() {
@@ -2303,6 +2441,11 @@ struct Runner {
     }
 
     void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
+        count_table_pass(L, e0, e1, mask);
+        if (use_scan) {
+            scan_leaf(L, e0, e1, mask, ncount);
+            return;
+        }
         if (use_l1) {
             l1_leaf(L, e0, e1, mask, ncount);
             return;
@@ -2318,6 +2461,65 @@ struct Runner {
         tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr, ix->tree.tc.dim_p <= 128);
         clk.end();
         tc_finish(tq, rg);
+    }
+
+    // Last level of low-dimensional vectors: regroup the entries by node, scan
+    // each node block's table rows once against all of its queries (leaf
+    // mask, visibility, Lemma 1 / 2 lower bound), then verify the candidates
+    // with the FP32 distance and its FP64 boundary recheck.
+    void scan_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount) {
+        TcQuery tq;
+        tq.E = e1 - e0;
+        tq.nq = qb.nq;
+        tq.eq = L.q.get() + e0;
+        tq.enode = L.node.get() + e0;
+        tq.path = L.path.get() + e0 * h;
+        tq.emask = mask.get();
+        tq.Q = d.Q;
+        tq.qseq = d.qseq;
+        tq.thr = thr.get();
+        tq.epsc = d.epsc;
+        tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
+        TcRegroup rg;
+        clk.begin(GTS_STAGE_OTHER, 6);
+        tc_regroup(ix->tree, tq, rg, st, ncount ? ncount->get() : nullptr, false);
+        clk.end();
+        st_tiles += rg.n_items;
+        st_tile_entries += rg.n_entries;
+        const int64_t per_q = ix->scan_pairs_hint[knn ? 1 : 0].load();
+        const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
+        ScanQuery sq;
+        sq.epsc = d.epsc;
+        sq.any_deleted = tq.any_deleted;
+        sq.fused_range = !knn;   // range: decide the pairs in the scan (low dimension)
+        sq.Q = d.Q;
+        sq.rel = d.rel;
+        ScanOut so;
+        ScanStats ss;
+        clk.begin(GTS_STAGE_LEAF_SCAN);
+        scan_run(ix->tree, rg, sq, so, hint, ss, st);
+        clk.end();
+        clk.launches[GTS_STAGE_LEAF_SCAN] += ss.launches > 1 ? ss.launches - 1 : 0;
+        st_scan_rows += ss.staged_rows;
+        st_scan_records += ss.records;
+        if (rg.n_items > 0 && qb.nq > 0)
+            ix->scan_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, ss.candidates * 1024 / qb.nq));
+        ++st_groups;
+        if (sq.fused_range) {
+            // the method's candidates are the pairs that passed the table
+            // bound; the accepted ones are answers already, the band pairs get
+            // their FP64 recheck
+            st_cands += ss.candidates - so.n_pairs;
+            if (so.n_accepted > 0) {
+                rkeys.push_back(std::move(so.key));
+                rdists.push_back(std::move(so.dist));
+                rcounts.push_back(so.n_accepted);
+            }
+            if (so.n_pairs > 0) verify_and_collect(so.q, so.row, so.n_pairs, /*query_major=*/false);
+            return;
+        }
+        if (so.n_pairs == 0) return;
+        verify_and_collect(so.q, so.row, so.n_pairs, /*query_major=*/false);
     }
 
     // Last level for strings on the 3-gram tiles: regroup the entries by
@@ -2345,6 +2547,7 @@ struct Runner {
         sq.qg = d.qg;
         sq.qgq = d.qgq;
         sq.any_deleted = tq.any_deleted;
+        sq.queries = tu.str_qgram == 32 ? 32 : 64;
         const int64_t per_q = ix->tc_pairs_hint[knn ? 1 : 0].load();
         const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
         DBuf<int32_t> oq, orow;
@@ -2463,6 +2666,11 @@ struct Runner {
     template <bool L2, bool KNN>
     void launch_verify_vec(const DBuf<int32_t> &cq, const DBuf<int32_t> &crow, int64_t C, DBuf<float> &cdist,
                            DBuf<uint8_t> &keep) {
+        if (d.dim <= kScanMaxDim) {   // a thread per pair
+            k_verify_lowdim<L2, KNN><<<wave_grid(k_verify_lowdim<L2, KNN>, nblocks(C, kT), kT), kT, 0, st>>>(
+                d, cq.get(), crow.get(), C, thr.get(), cdist.get(), keep.get(), counters.get());
+            return;
+        }
         const int64_t warps = (C + kVerifyGroup - 1) / kVerifyGroup;
         const unsigned grid = cap(nblocks(warps, kWarpsPerBlock));
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
@@ -2497,7 +2705,7 @@ struct Runner {
                 else launch_verify_vec<false, false>(cq, crow, C, cdist, keep);
             }
         } else {
-            const int chunk = 256;
+            const int chunk = tu.str_chunk;
 #define GTS_VER(WW)                                                                                              \
     do {                                                                                                         \
         if (knn)                                                                                                 \
@@ -2643,9 +2851,13 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         R.max_blocks = (unsigned)(sms > 0 ? sms : 1) * 8u;
     }
-    if (precision == GTS_PREC_BF16 && l1_tiles_supported(t, qb.Q)) R.use_l1 = true;
-    if (precision == GTS_PREC_BF16 && t.dim == 0 && t.n > 0 && t.n < ((int64_t)1 << 31)) R.use_qg = true;
-    if (precision == GTS_PREC_BF16 && tc_supported(t)) {
+    const bool low_dim = t.dim > 0 && t.dim <= kScanMaxDim && (t.metric == GTS_L1 || t.metric == GTS_L2) &&
+                         t.n > 0 && t.n < ((int64_t)1 << 31);
+    if (precision == GTS_PREC_BF16 && low_dim) R.use_scan = true;
+    if (precision == GTS_PREC_BF16 && !low_dim && l1_tiles_supported(t, qb.Q)) R.use_l1 = true;
+    if (precision == GTS_PREC_BF16 && t.dim == 0 && t.n > 0 && t.n < ((int64_t)1 << 31) && R.tu.str_qgram > 0)
+        R.use_qg = true;
+    if (precision == GTS_PREC_BF16 && !low_dim && tc_supported(t)) {
         {
             std::lock_guard<std::mutex> g(ix->prep_mu);   // concurrent queries build it once
             tc_prepare(t, t.tc, st);
@@ -2721,6 +2933,10 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
     R.thr.alloc(nq, st);
     R.counters.alloc(2, st);
     GTS_CUDA(cudaMemsetAsync(R.counters.get(), 0, 16, st));
+    if (qb.count_table_pass) {
+        R.tp_count.alloc(2, st);
+        GTS_CUDA(cudaMemsetAsync(R.tp_count.get(), 0, 16, st));
+    }
     if (knn) {
         DBuf<int64_t> k64(nq + 1, st);
         R.koff.alloc(nq + 1, st);
@@ -2788,10 +3004,11 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         out.total = d2h_i64(out.offsets.get() + nq, st);
         out.ids.alloc(out.total ? out.total : 1, st);
         out.dist.alloc(out.total ? out.total : 1, st);
+        if (qb.want_keys) out.key.alloc(out.total ? out.total : 1, st);
         R.clk.begin(GTS_STAGE_OTHER);
         k_knn_emit<<<(unsigned)(nq > 0 ? nq : 1), 128, 0, st>>>(out.offsets.get(), R.koff.get(), R.bd.get(),
                                                                 R.bi.get(), R.bn.get(), nq, t.metric == GTS_L2,
-                                                                out.ids.get(), out.dist.get());
+                                                                out.ids.get(), out.dist.get(), out.key.get());
         R.clk.end();
     } else {
         int64_t Rt = 0;
@@ -2829,14 +3046,15 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         out.total = Rt;
     }
     check_launch("assemble");
-    unsigned long long hc[2] = {0, 0};
+    unsigned long long hc[2] = {0, 0}, htp[2] = {0, 0};
     GTS_CUDA(cudaMemcpyAsync(hc, R.counters.get(), 16, cudaMemcpyDeviceToHost, st));
+    if (qb.count_table_pass) GTS_CUDA(cudaMemcpyAsync(htp, R.tp_count.get(), 16, cudaMemcpyDeviceToHost, st));
     GTS_CUDA(cudaStreamSynchronize(st));
     if (stage_ms) R.clk.collect(stage_ms);
     if (stats) {
         stats[GTS_STAT_PIVOT_DIST] = R.st_pivots;
         stats[GTS_STAT_FRONTIER] = R.st_frontier;
-        stats[GTS_STAT_SCANNED_ROWS] = (int64_t)hc[1];
+        stats[GTS_STAT_SCANNED_ROWS] = (int64_t)hc[1] + R.st_scan_rows;
         stats[GTS_STAT_CANDIDATES] = R.st_cands;
         stats[GTS_STAT_RECHECKS] = (int64_t)hc[0];
         stats[GTS_STAT_RESULTS] = out.total;
@@ -2848,6 +3066,8 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         stats[GTS_STAT_TILE_PAIRS] = R.st_tile_pairs;
         stats[GTS_STAT_DENSE_PAIRS] = R.st_dense_pairs;
         stats[GTS_STAT_DENSE_LAST] = R.st_dense_last;
+        stats[GTS_STAT_TABLE_PASS] = qb.count_table_pass ? (int64_t)htp[0] + R.st_table_pass : -1;
+        stats[GTS_STAT_SCAN_RECORDS] = R.st_scan_records;
     }
 }
 

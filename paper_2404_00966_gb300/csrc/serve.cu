@@ -10,15 +10,30 @@
 // overlap on the device.
 //
 // Admission: every request carries a projected device footprint -- an upper
-// bound of the candidate rows it can produce (every visible object) times
-// the bytes one candidate occupies in the search's tables -- and a request
-// is admitted only while the projections of all requests in flight fit the
-// result budget (the oldest request is always admitted when nothing is in
-// flight).  Each batch's own intermediate tables are further bounded by the
-// two-stage scheduler with memory_budget.
+// bound of the candidate rows it can produce times the bytes one candidate
+// occupies in the search's tables -- and a request is admitted only while the
+// projections of all requests in flight fit the result budget (the oldest
+// request is always admitted when nothing is in flight).  Each batch's own
+// intermediate tables are further bounded by the two-stage scheduler with
+// memory_budget.
+//
+// The projection is the descent of Section 5.1 run on the host over the
+// top levels of the tree (a snapshot taken when the server starts, at most
+// 4096 pivots), evaluating at most 64 pivots per request: the request's
+// distances to the pivots of the surviving nodes (FP64, or exact edit
+// distance), the node test of Lemma 1 on every child's [lo, hi] interval
+// (with the radius, or for kNN with the k-th smallest distance to a visible
+// pivot evaluated so far, which bounds d_k from above since the pivots are
+// objects), and the row counts of the nodes that survive at the deepest level
+// reached.
+// Every candidate row of the full search lies in one of those nodes (or in
+// the cache list), so the sum bounds the candidates from above.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
+#include <string>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -55,6 +70,102 @@ struct Done {
     gts_status status;
 };
 
+// Host snapshot of the tree's top `levels` pivot levels (Section 4.2 node
+// list, Eq. 1 numbering) for the admission projection.
+struct TopLevels {
+    int levels = 0, F = 0, dim = 0, metric = 0;
+    std::vector<int64_t> lvl_off;          // first node of levels 0 .. levels
+    std::vector<float> pv;                 // pivot vectors of levels < levels, [node, dim]
+    std::vector<std::string> ps;           // pivot strings
+    std::vector<uint8_t> has_piv, piv_live;
+    std::vector<float> lo, hi;             // every node of levels 1 .. levels
+    std::vector<int64_t> size;             // every node of levels 0 .. levels
+    int64_t cache_rows = 0, n_live = 0;
+};
+
+double host_distance(const TopLevels &t, int64_t node, const uint8_t *q, int64_t len) {
+    if (t.dim > 0) {
+        const float *x = &t.pv[(size_t)node * t.dim];
+        const float *qq = reinterpret_cast<const float *>(q);
+        double s = 0.0;
+        for (int i = 0; i < t.dim; ++i) {
+            const double d = (double)qq[i] - (double)x[i];
+            s += t.metric == GTS_L2 ? d * d : std::fabs(d);
+        }
+        return t.metric == GTS_L2 ? std::sqrt(s) : s;
+    }
+    const std::string &b = t.ps[(size_t)node];   // unit-cost Levenshtein, two rows
+    const int64_t lb = (int64_t)b.size();
+    std::vector<int64_t> prev(lb + 1), cur(lb + 1);
+    for (int64_t j = 0; j <= lb; ++j) prev[j] = j;
+    for (int64_t i = 1; i <= len; ++i) {
+        cur[0] = i;
+        for (int64_t j = 1; j <= lb; ++j)
+            cur[j] = std::min(std::min(prev[j] + 1, cur[j - 1] + 1),
+                              prev[j - 1] + (q[i - 1] != (uint8_t)b[(size_t)j - 1] ? 1 : 0));
+        std::swap(prev, cur);
+    }
+    return (double)prev[lb];
+}
+
+// Upper bound of the candidate rows of one request (see the file comment):
+// the descent of Algorithm 4 / 5 over the snapshot levels, evaluating only the
+// pivots of the nodes that survive (at most kMaxEvals of them per request; past
+// that, or where no radius bound exists yet, the rows of the current frontier
+// are the bound).
+constexpr int kMaxEvals = 64;
+
+int64_t project_rows(const TopLevels &t, const uint8_t *q, int64_t len, int32_t kind, double param) {
+    if (t.levels == 0) return t.n_live + t.cache_rows;
+    std::vector<int64_t> frontier{0}, next;   // node indices within the current level
+    std::vector<double> live;                 // exact distances to the visible pivots evaluated so far
+    std::vector<double> dnode;
+    auto rows_of = [&](int l) {
+        int64_t rows = t.cache_rows;
+        for (int64_t c : frontier) rows += t.size[t.lvl_off[l] + c];
+        return rows;
+    };
+    int evals = 0;
+    const size_t k = kind == 1 ? (size_t)param : 0;
+    for (int l = 0; l < t.levels; ++l) {
+        if (evals + (int)frontier.size() > kMaxEvals) return rows_of(l);
+        dnode.assign(frontier.size(), 0.0);
+        for (size_t i = 0; i < frontier.size(); ++i) {
+            const int64_t v = t.lvl_off[l] + frontier[i];
+            if (!t.has_piv[v]) continue;
+            dnode[i] = host_distance(t, v, q, len);
+            ++evals;
+            if (t.piv_live[v]) live.push_back(dnode[i]);
+        }
+        double r;
+        if (kind == 0) {
+            r = t.dim > 0 ? param : std::floor(param);
+        } else {
+            if (live.size() < k) return rows_of(l);   // no bound on d_k yet: nothing can be pruned
+            std::vector<double> tmp(live);
+            std::nth_element(tmp.begin(), tmp.begin() + (k - 1), tmp.end());
+            r = tmp[k - 1];   // the k-th smallest distance to an object evaluated so far >= d_k
+        }
+        next.clear();
+        for (size_t i = 0; i < frontier.size(); ++i) {
+            const int64_t node = frontier[i], v = t.lvl_off[l] + node;
+            if (!t.has_piv[v]) continue;   // an empty node has no rows
+            const double dq = dnode[i];
+            for (int j = 0; j < t.F; ++j) {
+                const int64_t c = node * t.F + j, cv = t.lvl_off[l + 1] + c;
+                if (t.size[cv] == 0) continue;
+                const double lo = t.lo[cv - 1], hi = t.hi[cv - 1];   // lo/hi hold levels >= 1
+                // at least the search's own FP32 slack, 4 (D + 8) 2^-24 of the same terms
+                const double rel = std::max(1e-5, 8.0 * (t.dim + 8) * 5.9604644775390625e-8);
+                const double slack = t.dim > 0 ? rel * (std::fabs(dq) + r + std::fabs(lo) + std::fabs(hi)) + 1e-6 : 0.0;
+                if (dq - r <= hi + slack && dq + r >= lo - slack) next.push_back(c);
+            }
+        }
+        frontier.swap(next);
+    }
+    return rows_of(t.levels);
+}
+
 }  // namespace
 }  // namespace gts
 
@@ -70,6 +181,8 @@ struct gts_server {
     int64_t in_flight = 0;        // projected bytes of admitted requests
     int64_t max_in_flight = 0;
     int64_t batches = 0, requests_run = 0, max_batch_seen = 0;
+    int64_t proj_total = 0, proj_below_worst = 0;
+    gts::TopLevels top;
     std::vector<std::thread> workers;
 };
 
@@ -176,6 +289,55 @@ void worker_loop(gts_server *sv, int wid) {
     cudaStreamDestroy(st);
 }
 
+// The host snapshot of the top pivot levels: the deepest l <= h whose levels
+// above it hold at most 4096 pivots (Eq. 1: levels 0 .. l-1 hold lvl_off[l] nodes).
+void snapshot_top_levels(gts_index *ix, TopLevels &t) {
+    const Tree &tr = ix->tree;
+    t = TopLevels();
+    t.F = tr.F;
+    t.dim = tr.dim;
+    t.metric = tr.metric;
+    t.cache_rows = ix->cache.count;
+    t.n_live = ix->n_live;
+    if (tr.n == 0 || tr.h < 1) return;
+    int L = 1;
+    while (L < tr.h && tr.lvl_off[L + 1] <= 4096) ++L;
+    t.levels = L;
+    t.lvl_off.assign(tr.lvl_off.begin(), tr.lvl_off.begin() + L + 1);
+    const int64_t nodes = tr.lvl_off[L + 1], npiv = tr.lvl_off[L];
+    std::vector<int32_t> piv(npiv), sz(nodes);
+    t.lo.resize(nodes - 1);
+    t.hi.resize(nodes - 1);
+    GTS_CUDA(cudaMemcpy(piv.data(), tr.npiv.get(), npiv * 4, cudaMemcpyDeviceToHost));
+    GTS_CUDA(cudaMemcpy(sz.data(), tr.nsize.get(), nodes * 4, cudaMemcpyDeviceToHost));
+    GTS_CUDA(cudaMemcpy(t.lo.data(), tr.nlo.get() + 1, (nodes - 1) * 4, cudaMemcpyDeviceToHost));
+    GTS_CUDA(cudaMemcpy(t.hi.data(), tr.nhi.get() + 1, (nodes - 1) * 4, cudaMemcpyDeviceToHost));
+    t.size.assign(sz.begin(), sz.end());
+    t.has_piv.assign(npiv, 0);
+    t.piv_live.assign(npiv, 0);
+    if (t.dim > 0) t.pv.assign((size_t)npiv * t.dim, 0.f);
+    else t.ps.assign(npiv, std::string());
+    for (int64_t v = 0; v < npiv; ++v) {
+        const int32_t row = piv[v];
+        if (row < 0) continue;
+        t.has_piv[v] = 1;
+        int64_t del = 0;
+        GTS_CUDA(cudaMemcpy(&del, tr.row_del.get() + row, 8, cudaMemcpyDeviceToHost));
+        t.piv_live[v] = del == kNever ? 1 : 0;
+        if (t.dim > 0) {
+            GTS_CUDA(cudaMemcpy(&t.pv[(size_t)v * t.dim], tr.X.get() + (int64_t)row * t.dim, (size_t)t.dim * 4,
+                                cudaMemcpyDeviceToHost));
+        } else {
+            int64_t off[2];
+            GTS_CUDA(cudaMemcpy(off, tr.Soff.get() + row, 16, cudaMemcpyDeviceToHost));
+            std::string str((size_t)(off[1] - off[0]), '\0');
+            if (off[1] > off[0])
+                GTS_CUDA(cudaMemcpy(&str[0], tr.S.get() + off[0], (size_t)(off[1] - off[0]), cudaMemcpyDeviceToHost));
+            t.ps[v] = std::move(str);
+        }
+    }
+}
+
 template <class F>
 gts_status guard(F &&f) {
     try {
@@ -225,6 +387,7 @@ gts_status gts_serve_start(gts_index *ix, const gts_serve_opts *opts, gts_server
             gts_result r;
             if (gts_knn(ix, &qo, &k, &o, &r) == GTS_OK) gts_result_free(&r);
         }
+        snapshot_top_levels(ix, sv->top);
         gts_server *p = sv.get();
         for (int i = 0; i < sv->opts.n_streams; ++i) sv->workers.emplace_back(worker_loop, p, i);
         *out = sv.release();
@@ -256,14 +419,16 @@ gts_status gts_serve_submit(gts_server *sv, const void *query, int64_t len, int3
             GTS_REQUIRE(len >= 0 && len <= kMaxStrLen && (len == 0 || query), GTS_EINVAL, "bad string query");
             r.payload.assign((const uint8_t *)query, (const uint8_t *)query + len);
         }
-        const int64_t visible = sv->ix->n_live > 0 ? sv->ix->n_live : 1;
-        r.proj = visible * kCandidateBytes;
+        const int64_t rows = project_rows(sv->top, r.payload.data(), (int64_t)r.payload.size(), kind, param);
+        r.proj = (rows > 0 ? rows : 1) * kCandidateBytes;
         r.t_submit = now_ms();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             GTS_REQUIRE(!sv->stopping, GTS_EINVAL, "server is stopping");
             r.ticket = sv->next_ticket++;
             *ticket = r.ticket;
+            sv->proj_total += r.proj;
+            if (rows < sv->top.n_live + sv->top.cache_rows) sv->proj_below_worst += 1;
             sv->pending.push_back(std::move(r));
         }
         sv->cv_work.notify_one();
@@ -291,6 +456,7 @@ gts_status gts_serve_wait(gts_server *sv, int64_t ticket, int32_t timeout_ms, gt
         out->nq = 1;
         out->on_device = 0;
         out->priv_ = nullptr;
+        out->key = nullptr;
         out->offsets = (int64_t *)std::malloc(16);
         out->ids = (int64_t *)std::malloc(sizeof(int64_t) * (m > 0 ? m : 1));
         out->dist = (float *)std::malloc(sizeof(float) * (m > 0 ? m : 1));
@@ -306,14 +472,29 @@ gts_status gts_serve_wait(gts_server *sv, int64_t ticket, int32_t timeout_ms, gt
     return s;
 }
 
-gts_status gts_serve_stats(gts_server *sv, int64_t *out4) {
+gts_status gts_serve_stats(gts_server *sv, int64_t *out, int32_t n_out) {
     return guard([&] {
-        GTS_REQUIRE(sv && out4, GTS_EINVAL, "NULL argument");
+        GTS_REQUIRE(sv && out && n_out >= 0, GTS_EINVAL, "NULL argument");
         std::lock_guard<std::mutex> lk(sv->mu);
-        out4[0] = sv->batches;
-        out4[1] = sv->requests_run;
-        out4[2] = sv->max_batch_seen;
-        out4[3] = sv->max_in_flight;
+        const int64_t v[6] = {sv->batches, sv->requests_run, sv->max_batch_seen, sv->max_in_flight,
+                              sv->proj_total, sv->proj_below_worst};
+        for (int i = 0; i < n_out && i < 6; ++i) out[i] = v[i];
+    });
+}
+
+gts_status gts_serve_project(gts_server *sv, const void *query, int64_t len, int32_t kind, double param,
+                             int64_t *bytes) {
+    return guard([&] {
+        GTS_REQUIRE(sv && bytes, GTS_EINVAL, "NULL argument");
+        GTS_REQUIRE(kind == 0 || kind == 1, GTS_EINVAL, "kind must be 0 (range) or 1 (kNN)");
+        GTS_REQUIRE(kind == 1 ? (param >= 1.0 && param <= 1024.0) : (param >= 0.0 && param == param), GTS_EINVAL,
+                    "bad radius or k");
+        const int dim = sv->ix->dim;
+        GTS_REQUIRE(dim > 0 ? (len == dim && query) : (len >= 0 && len <= kMaxStrLen && (len == 0 || query)),
+                    GTS_EINVAL, "bad query");
+        const int64_t rows = project_rows(sv->top, (const uint8_t *)query, dim > 0 ? (int64_t)dim * 4 : len, kind,
+                                          param);
+        *bytes = (rows > 0 ? rows : 1) * kCandidateBytes;
     });
 }
 

@@ -12,7 +12,7 @@
 // d > t.  The surviving (query, last-level node) entries are regrouped by
 // node; one CTA takes a block of up to 128 node rows (each thread holds one
 // row's 64-byte bucket vector in registers) and the node's queries in chunks
-// of 64 (their vectors in shared memory); a pair is kept if the row's leaf
+// of 32 or 64 (their vectors in shared memory); a pair is kept if the row's leaf
 // survived for the query, the row is visible
 // at the query's sequence number and the bound does not exclude it.  The
 // kept pairs go on to the exact DP.
@@ -24,9 +24,7 @@ namespace gts {
 namespace {
 
 constexpr int kRowsS = 128;     // rows of one node block (the regrouping's block size)
-constexpr int kNQS = 64;        // queries per chunk
 constexpr int kThreadsS = 256;  // thread = (row tid % 128, query half tid / 128)
-constexpr int kQPTS = kNQS / 2; // queries per thread
 constexpr int kWords = 16;      // 64 one-byte buckets as 16 words
 
 struct StrArgs {
@@ -46,7 +44,11 @@ struct StrArgs {
     unsigned long long *out_count;
 };
 
+// NQS: queries per chunk (32 or 64; a tuning parameter), NQS / 2 per thread
+template <int NQS>
 __global__ void __launch_bounds__(kThreadsS) k_tile_qgram(StrArgs a) {
+    constexpr int kNQS = NQS;
+    constexpr int kQPTS = NQS / 2;
     __shared__ __align__(16) uint32_t sQ[kNQS][kWords + 1];
     __shared__ uint64_t sMask[kNQS];
     __shared__ int64_t sSeq[kNQS];
@@ -153,7 +155,10 @@ int64_t qgram_run(const Tree &t, const StrQuery &sq, const TcRegroup &rg, DBuf<i
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int per_sm = 0;
-    GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qgram, kThreadsS, 0));
+    if (sq.queries == 32)
+        GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qgram<32>, kThreadsS, 0));
+    else
+        GTS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_qgram<64>, kThreadsS, 0));
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = std::min<int64_t>(rg.n_items, (int64_t)sms * per_sm);
     DBuf<int> counter(1, st);
@@ -181,7 +186,10 @@ int64_t qgram_run(const Tree &t, const StrQuery &sq, const TcRegroup &rg, DBuf<i
         a.out_row = out_row.get();
         a.cap = cap;
         a.out_count = count.get();
-        k_tile_qgram<<<(unsigned)grid, kThreadsS, 0, st>>>(a);
+        if (sq.queries == 32)
+            k_tile_qgram<32><<<(unsigned)grid, kThreadsS, 0, st>>>(a);
+        else
+            k_tile_qgram<64><<<(unsigned)grid, kThreadsS, 0, st>>>(a);
         ++*launches;
         check_launch("3-gram tile");
         unsigned long long hcount = 0;

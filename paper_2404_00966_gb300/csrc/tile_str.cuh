@@ -11,6 +11,7 @@ struct StrQuery {
     const uint8_t *qg = nullptr;    // the tree rows' 3-gram bucket counts [n, 64]
     const uint8_t *qgq = nullptr;   // the batch's queries' [nq, 64]
     int any_deleted = 1;
+    int queries = 64;               // queries per tile chunk: 32 or 64
 };
 
 // run the tiles over a regrouping (its records carry each query's threshold);

@@ -1234,12 +1234,41 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tc::tmem_dealloc(tmem, 2 * kSelfN);
 }
 
+// Bounded-wait check: thread 0 waits on an mbarrier of arrival count 1 that
+// thread 32 arrives on only if `post` is set.  Without the arrival the wait
+// gives up after `limit` polls and the kernel records status 1 and returns,
+// as every waiting kernel of this library does when a wait runs out.
+__global__ void k_selftest_wait(int post, uint32_t limit, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 32 && post) tc::mbar_arrive(&bar);
+    if (threadIdx.x == 0) *status = tc::mbar_wait_limit(&bar, 0, limit) ? 0 : 1;
+}
+
 __global__ void k_f32_to_bf16(const float *a, int64_t n, __nv_bfloat16 *b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = __float2bfloat16_rn(a[i]);
 }
 
 }  // namespace
+
+void wait_selftest(int post, uint32_t limit) {
+    GTS_REQUIRE(limit >= 1 && limit <= tc::kSpinLimit, GTS_EINVAL, "spin limit must be in 1 .. 2^26");
+    cudaStream_t st = nullptr;
+    DBuf<int> status(1, st);
+    GTS_CUDA(cudaMemsetAsync(status.get(), 0xff, 4, st));
+    k_selftest_wait<<<1, 64, 0, st>>>(post ? 1 : 0, limit, status.get());
+    check_launch("bounded-wait self-test");
+    int hs = -1;
+    GTS_CUDA(cudaMemcpyAsync(&hs, status.get(), 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    GTS_REQUIRE(hs != -1, GTS_ECUDA, "bounded-wait self-test: status not written");
+    GTS_REQUIRE(hs == 0, GTS_ETIMEOUT, "bounded-wait self-test: the wait ran out after its poll limit");
+}
 
 void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD) {
     GTS_REQUIRE(N >= 32 && N <= kSelfN && N % 32 == 0, GTS_EINVAL, "N must be a multiple of 32 in 32 .. 256");

@@ -126,5 +126,6 @@ int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegro
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
 void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD);
+void wait_selftest(int post, uint32_t limit);
 
 }  // namespace gts

@@ -68,3 +68,24 @@ def test_no_device_means_an_error_not_a_fallback(L):
     with pytest.raises(g.GTSError) as e:
         g.Index.build(X, "l2", fanout=4)
     assert e.value.name == "GTS_ECUDA"
+
+
+def test_cost_model_closed_form(L):
+    """gts_cost_model (Section 5.3) is host arithmetic: S_i = nq (F p)^i per
+    pivot level, S_{h+1} = nq n p^h for the objects of the surviving leaves,
+    cost = sum_i i^2 ceil(S_i / C) log2(F)^2.  Worked by hand for n = 1000,
+    nq = 10, p = 1/2, F = 4, h = 2, C = 8:
+    level 1: S = 20, ceil(20/8) = 3, 1 * 3 * 4 = 12;
+    level 2: S = 40, ceil(40/8) = 5, 4 * 5 * 4 = 80;
+    leaves:  S = 2500, ceil(2500/8) = 313, 9 * 313 * 4 = 11268; total 11360."""
+    import paper_2404_00966_gb300 as g
+    assert g.cost_model(1000, 10, 0.5, 4, 2, 8.0) == 11360.0
+    # nothing survives the first pivot level: no work anywhere
+    assert g.cost_model(1000, 10, 0.0, 4, 3, 8.0) == 0.0
+    # p = 1 (no pruning) with h = 1, F = 2: level 10 * 2 = 20 -> 3 * 1;
+    # leaves 10 * 1000 = 10000 -> 1250 * 4; log2(2)^2 = 1
+    assert g.cost_model(1000, 10, 1.0, 2, 1, 8.0) == 3.0 + 4 * 1250.0
+    # arguments out of range give -1
+    for bad in [(1000, 10, 1.5, 4, 2, 8.0), (1000, 10, 0.5, 1, 2, 8.0), (1000, 10, 0.5, 4, 0, 8.0),
+                (1000, 10, 0.5, 4, 2, 0.0)]:
+        assert g.cost_model(*bad) == -1.0

@@ -74,6 +74,24 @@ def test_build_matches_oracle_tree(gts, metric, F, npiv):
     ix.close()
 
 
+@pytest.mark.parametrize("metric", ["l1", "l2"])
+def test_build_matches_oracle_tree_with_exact_ties(gts, metric):
+    """Integer points in a small cube: exactly tied distances at every level,
+    so the (distance, id) order of the partition decides every cut."""
+    X = np.random.default_rng(5).integers(0, 3, size=(2400, 3)).astype(np.float32)
+    ix = gts.Index.build(X, metric, n_pivots=3, fanout=6, root_pivot=7)
+    T = build_index(X, metric, 6, 3, root_pivot=7)
+    for l in range(T["h"] + 1):
+        g = ix.tree_level(l)
+        assert np.array_equal(g["pos"], T["pos"][l]) and np.array_equal(g["size"], T["size"][l])
+        if l < T["h"]:
+            assert np.array_equal(g["pivot"], T["pivot"][l])
+    ids, tab = ix.table()
+    assert np.array_equal(ids, T["perm"])
+    assert np.array_equal(tab, T["table"])
+    ix.close()
+
+
 # ------------------------------------------------------------------ range / kNN parity
 
 @pytest.mark.parametrize("metric", ["l2", "l1"])
@@ -239,6 +257,21 @@ def test_tensor_core_tile_primitives(gts, N, K, a_tmem):
     assert np.all(err <= (K + 4) * 2.0 ** -23 * scale + 1e-30), float((err / scale).max())
 
 
+def test_bounded_wait_runs_out_and_device_stays_usable(gts):
+    """A wait on an mbarrier that nothing arrives on gives up after its poll
+    limit: the kernel records the run-out and returns, the call reports
+    GTS_ETIMEOUT, and the device answers the next query exactly."""
+    L = gts.lib()
+    assert L.gts_selftest_wait(0, 1 << 14) == 4                 # GTS_ETIMEOUT
+    assert b"ran out" in L.gts_last_error()
+    assert L.gts_selftest_wait(1, 1 << 14) == 0                 # posted: the wait ends
+    assert L.gts_selftest_wait(0, 0) == 1                       # limit out of range: GTS_EINVAL
+    X, Q = vec_case(2003, 16, 20, seed=31)
+    ix = gts.Index.build(X, "l2", fanout=6, root_pivot=2)
+    assert_same(ix.knn(Q, 5), oracle.knn_query("l2", X, Q, 5), "l2", "after a run-out")
+    ix.close()
+
+
 @pytest.mark.parametrize("dim,dup", [(128, 0.0), (100, 0.2), (256, 0.0)])
 def test_bf16_tiles_parity(gts, dim, dup):
     X, Q = vec_case(20011, dim, 300, seed=40 + dim, dup=dup)
@@ -296,12 +329,123 @@ def test_l1_tiles_concentrated_distances(gts):
     ix.close()
 
 
-def test_l1_tiles_fall_back_when_unaligned(gts):
+def test_low_dim_takes_the_table_scan(gts):
     X, Q = vec_case(3000, 6, 40, seed=62)
     ix = gts.Index.build(X, "l1", fanout=6)
     r = ix.knn(Q, 5, precision="bf16")
-    assert r.stats["tile_pairs"] == 0
+    assert r.stats["tile_pairs"] == 0 and r.stats["scanned_rows"] > 0
     assert_same(r, oracle.knn_query("l1", X, Q, 5), "l1", "dim 6")
+    ix.close()
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("dim", [2, 3, 8, 16])
+def test_scan_low_dim_parity(gts, metric, dim):
+    """Node-major table scan + CUDA-core verification (precision="bf16" on
+    vectors of dim <= 16): duplicates and exact ties, radius 0, a ragged last
+    block, every k from 1 to past the 64-record chunk."""
+    X, Q = vec_case(20011, dim, 300, seed=90 + dim, dup=0.2)
+    Q[:3] = X[[5, 9, 20010]]
+    ix = gts.Index.build(X, metric, fanout=8, root_pivot=3)
+    d = oracle.distances_to(metric, X[:500], Q[4])
+    radii = np.concatenate([[0.0, 0.0], np.linspace(0.01, 0.3, 298) * np.median(d)]).astype(np.float32)
+    r = ix.range(Q, radii, precision="bf16", count_table_pass=True)
+    assert r.stats["scanned_rows"] > 0 and r.stats["tile_pairs"] == 0
+    # the scan emits exactly the pairs that pass the table bound
+    assert r.stats["table_pass"] == r.stats["candidates"]
+    assert_same(r, oracle.range_query(metric, X, Q, radii), metric, f"scan range dim {dim}")
+    for k in (1, 10, 90):
+        assert_same(ix.knn(Q, k, precision="bf16"), oracle.knn_query(metric, X, Q, k), metric,
+                    f"scan knn k={k} dim {dim}")
+    ix.close()
+
+
+def test_scan_many_blocks_and_chunks_and_relaunch(gts):
+    """Two pivot levels of fanout 4 over 20,000 2-D points: last-level nodes of
+    5,000 rows (40 row blocks each) with hundreds of query records (several
+    64-record chunks); a wide radius emits more candidates than the first
+    launch's capacity (1 M), so the scan runs again with the exact size."""
+    X, Q = vec_case(20000, 2, 600, seed=97, kind="uniform")
+    ix = gts.Index.build(X, "l2", n_pivots=2, fanout=4, root_pivot=1)
+    radii = np.full(600, 0.25, np.float32)
+    r = ix.range(Q, radii, precision="bf16")
+    assert r.stats["candidates"] > (1 << 20)
+    assert_same(r, oracle.range_query("l2", X, Q, radii), "l2", "wide radius")
+    small = np.full(600, 0.02, np.float32)
+    assert_same(ix.range(Q, small, precision="bf16"), oracle.range_query("l2", X, Q, small), "l2", "small radius")
+    assert_same(ix.knn(Q, 33, precision="bf16"), oracle.knn_query("l2", X, Q, 33), "l2", "knn 33")
+    ix.close()
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_scan_with_stream_updates(gts, metric):
+    """Inserts in the cache list and deletes of tree rows and cache objects:
+    the scan skips deleted rows by their sequence numbers."""
+    X, Q = vec_case(30011, 2, 200, seed=98)
+    ix = gts.Index.build(X, metric, fanout=12, root_pivot=0, cache_limit=100_000)
+    s0 = ix.info()["seq"]
+    extra, _ = vec_case(700, 2, 1, seed=99)
+    ix.insert(extra)
+    dele = np.random.default_rng(100).choice(30011 + 700, 2000, replace=False)
+    assert ix.delete(dele) == 0
+    s1 = ix.info()["seq"]
+    P = np.concatenate([X, extra])
+    ins = np.concatenate([np.full(30011, -1), s0 + np.arange(700)]).astype(np.int64)
+    dl = np.full(P.shape[0], np.iinfo(np.int64).max, np.int64)
+    dl[dele] = s0 + 700 + np.arange(2000)
+    qs = np.full(200, s1, np.int64)
+    d = oracle.distances_to(metric, X[:300], Q[0])
+    radii = np.full(200, np.float32(np.median(d) * 0.1), np.float32)
+    r = ix.range(Q, radii, precision="bf16")
+    assert r.stats["scanned_rows"] > 0
+    assert_same(r, oracle.range_query(metric, P, Q, radii, ins, dl, qs), metric, "scan range with updates")
+    assert_same(ix.knn(Q, 12, precision="bf16"), oracle.knn_query(metric, P, Q, 12, ins, dl, qs), metric,
+                "scan knn with updates")
+    ix.close()
+
+
+@pytest.mark.parametrize("metric,dim", [("l2", 32), ("l1", 3)])
+def test_shape_autotuner_keeps_answers(gts, metric, dim):
+    """gts_autotune_shape ranks (fanout, h) by the cost model, rebuilds and
+    times the cheapest shapes and keeps the fastest: the index ends in that
+    shape, and every shape it timed answers exactly."""
+    X, Q = vec_case(30011, dim, 200, seed=130 + dim)
+    ix = gts.Index.build(X, metric, fanout=20, root_pivot=0)
+    want = oracle.knn_query(metric, X, Q, 10)
+    d = oracle.distances_to(metric, X[:300], Q[0])
+    radii = np.full(200, np.float32(np.median(d) * 0.2), np.float32)
+    want_r = oracle.range_query(metric, X, Q, radii)
+    shapes = ix.autotune_shape(Q, k=10, precision="bf16", candidates=3, reps=1)
+    assert 3 <= len(shapes) <= 4
+    ms = [sh["measured_ms"] for sh in shapes]
+    assert ms == sorted(ms) and all(m > 0 for m in ms)
+    info = ix.info()
+    assert (info["fanout"], info["h"]) == (shapes[0]["fanout"], shapes[0]["n_pivots"])
+    assert_same(ix.knn(Q, 10, precision="bf16"), want, metric, "after shape tuning")
+    assert_same(ix.range(Q, radii, precision="bf16"), want_r, metric, "range after shape tuning")
+    for sh in shapes:
+        j = gts.Index.build(X, metric, n_pivots=sh["n_pivots"], fanout=sh["fanout"], root_pivot=0)
+        assert_same(j.knn(Q, 10, precision="bf16"), want, metric, f"shape {sh}")
+        assert_same(j.range(Q, radii, precision="fp32"), want_r, metric, f"shape {sh} range")
+        j.close()
+    ix.close()
+
+
+@pytest.mark.parametrize("prec,dim", [("fp32", 32), ("bf16", 64), ("bf16", 128)])
+def test_table_pass_count_is_consistent(gts, prec, dim):
+    """The diagnostic count of pairs passing the table bound: on the plain
+    path it equals the scan's candidates; on the tensor-core tiles it is at
+    most the pairs the tiles covered; the answers do not change."""
+    X, Q = vec_case(20011, dim, 200, seed=120 + dim)
+    ix = gts.Index.build(X, "l2", fanout=12, root_pivot=5)
+    want = oracle.knn_query("l2", X, Q, 10)
+    r = ix.knn(Q, 10, precision=prec, count_table_pass=True)
+    assert_same(r, want, "l2", "knn with the count")
+    assert ix.knn(Q, 10, precision=prec).stats["table_pass"] == -1
+    if prec == "fp32":
+        assert r.stats["table_pass"] == r.stats["candidates"]
+    else:
+        assert 0 < r.stats["table_pass"] <= r.stats["tile_pairs"]
     ix.close()
 
 
@@ -503,4 +647,94 @@ def test_query_sequence_numbers_span_updates(gts):
     dele[np.arange(0, 200, 7)] = s0 + 30 + np.arange(len(range(0, 200, 7)))
     qseq = np.array([s0, s0 + 10, s0 + 30, s0 + 35, s1, s1], np.int64)
     assert_same(ix.knn(Q, 7, seq=qseq), oracle.knn_query("l1", P, Q, 7, ins, dele, qseq), "l1", "seq knn")
+    ix.close()
+
+
+# ------------------------------------------------------------------ persistence and shards
+
+@pytest.mark.parametrize("metric", ["l2", "edit"])
+def test_save_load_round_trip(gts, tmp_path, metric):
+    """An index written by gts_save and read by gts_load answers exactly as
+    the saved one, cache list, delete marks and sequence numbers included;
+    updates continue on the loaded index."""
+    if metric == "edit":
+        X, Q = str_case(3000, 40, seed=140)
+        extra, _ = str_case(200, 1, seed=141)
+        radii = np.full(40, 2.0, np.float32)
+    else:
+        X, Q = vec_case(8000, 24, 40, seed=140, dup=0.1)
+        extra, _ = vec_case(200, 24, 1, seed=141)
+        radii = np.full(40, np.float32(np.median(oracle.distances_to("l2", X[:200], Q[0])) * 0.5), np.float32)
+    ix = gts.Index.build(X, metric, fanout=7, root_pivot=3, cache_limit=10_000)
+    s0 = ix.info()["seq"]
+    ix.insert(extra)
+    n = 3000 if metric == "edit" else 8000
+    dele = np.random.default_rng(142).choice(n + 200, 300, replace=False)
+    assert ix.delete(dele) == 0
+    path = str(tmp_path / f"ix_{metric}.gts")
+    ix.save(path)
+    jx = gts.Index.load(path)
+    assert jx.info() == {**ix.info(), "device_bytes": jx.info()["device_bytes"]}
+    if metric == "edit":
+        P = strings_from_list([X.get(i) for i in range(n)] + [extra.get(i) for i in range(200)])
+    else:
+        P = np.concatenate([X, extra])
+    ins = np.concatenate([np.full(n, -1), s0 + np.arange(200)]).astype(np.int64)
+    dl = np.full(n + 200, np.iinfo(np.int64).max, np.int64)
+    dl[dele] = s0 + 200 + np.arange(300)
+    qs = np.full(40, ix.info()["seq"], np.int64)
+    want_r = oracle.range_query(metric, P, Q, radii, ins, dl, qs)
+    want_k = oracle.knn_query(metric, P, Q, 9, ins, dl, qs)
+    for j in (ix, jx):
+        for prec in ("fp32", "bf16"):
+            assert_same(j.range(Q, radii, precision=prec), want_r, metric, f"range {prec}")
+            r = j.knn(Q, 9, precision=prec, keys=True)
+            assert_same(r, want_k, metric, f"knn {prec}")
+            assert np.array_equal(r.keys, want_k[3])              # the exact FP64 (or integer) keys
+    ids = jx.insert(extra)                                        # updates continue on the loaded index
+    assert ids[0] == n + 200
+    ix.close()
+    jx.close()
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_sharded_index_equals_one_index(gts, metric):
+    """Objects split into three shards (one index each), every query sent to
+    every shard, answers merged by gts_merge_*: the same answers as the
+    oracle over the union, exact ties across shards included."""
+    rng = np.random.default_rng(150)
+    X = rng.integers(0, 5, size=(9001, 4)).astype(np.float32)
+    Q = rng.integers(0, 5, size=(60, 4)).astype(np.float32)
+    sh = gts.ShardedIndex.build(X, metric, 3, fanout=6, root_pivot=0)
+    ks = rng.integers(1, 50, size=60).astype(np.int32)
+    for prec in ("fp32", "bf16"):
+        assert_same(sh.knn(Q, ks, precision=prec), oracle.knn_query(metric, X, Q, ks), metric, f"shards knn {prec}")
+        radii = np.full(60, 2.0, np.float32)
+        assert_same(sh.range(Q, radii, precision=prec), oracle.range_query(metric, X, Q, radii), metric,
+                    f"shards range {prec}")
+    sh.close()
+
+
+def test_every_string_tuning_gives_the_same_answers(gts):
+    """Edit distance: every DP block size and 3-gram filter setting (off, 32 or
+    64 queries per chunk) answers exactly; the autotuner searches them."""
+    S, Qs = str_case(5000, 90, seed=160, lmin=6, lmax=40)
+    ix = gts.Index.build(S, "edit", n_pivots=3, fanout=8, root_pivot=2)
+    radii = np.random.default_rng(161).integers(0, 6, size=90).astype(np.float32)
+    want_r = oracle.range_query("edit", S, Qs, radii)
+    want_k = oracle.knn_query("edit", S, Qs, 7)
+    for chunk in (64, 128, 256, 512):
+        for qg in (0, 32, 64):
+            ix.set_tuning(str_chunk=chunk, str_qgram=qg)
+            r = ix.range(Qs, radii, precision="bf16")
+            assert (r.stats["tiles"] > 0) == (qg > 0)
+            assert_same(r, want_r, "edit", f"range chunk {chunk} qgram {qg}")
+            assert_same(ix.knn(Qs, 7, precision="bf16"), want_k, "edit", f"knn chunk {chunk} qgram {qg}")
+    with pytest.raises(gts.GTSError):
+        ix.set_tuning(str_chunk=100)
+    with pytest.raises(gts.GTSError):
+        ix.set_tuning(str_qgram=16)
+    t = ix.autotune(Qs, radii=radii, precision="bf16", reps=1)
+    assert t["str_chunk"] in (64, 128, 256, 512) and t["str_qgram"] in (0, 32, 64)
+    assert_same(ix.range(Qs, radii, precision="bf16"), want_r, "edit", "after autotune")
     ix.close()

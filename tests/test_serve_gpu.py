@@ -87,3 +87,30 @@ def test_string_requests(gts):
         assert np.array_equal(got[i][0], wids[off[i]:off[i + 1]]), f"request {i}: ids differ from the oracle"
         assert np.array_equal(got[i][1], wdist[off[i]:off[i + 1]].astype(np.float32))
     ix.close()
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_admission_projection_bounds_the_candidates(gts, metric):
+    """The projection (host descent over the top pivot levels) is an upper
+    bound of every request's candidates: for a range request at least the
+    pairs that pass the table bound in the full search of that request alone,
+    for kNN at least its answers (the nodes it keeps hold the ball of radius
+    d_k); on clustered data with a small radius it is below the worst case."""
+    X, Q = small_vectors(40009, 4, 60, seed=63)
+    ix = gts.Index.build(X, metric, fanout=6, root_pivot=0)
+    d = np.sort(oracle.distances_to(metric, X[:2000], Q[0]))
+    radius = float(d[20])
+    sv = gts.Server(ix, max_batch=8, n_streams=1)
+    below = 0
+    for i in range(60):
+        for kind, param in (("range", radius), ("knn", 5)):
+            rows = sv.project(Q[i], kind, param) // 37
+            alone = ix.range(Q[i:i + 1], np.float32([param]), count_table_pass=True) if kind == "range" else \
+                ix.knn(Q[i:i + 1], int(param), count_table_pass=True)
+            assert rows >= alone.offsets[1], (i, kind)
+            if kind == "range":
+                assert rows >= alone.stats["table_pass"], i
+            below += rows < 40009
+    sv.stop()
+    assert below >= 60    # the range requests at least: a small radius prunes most nodes
+    ix.close()
