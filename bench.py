@@ -47,7 +47,10 @@ if ROOT not in sys.path:
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-SMS, LANES_PER_SM = 152, 128   # GB300: 152 SMs; 128 FP32 / INT32 lanes per SM
+SMS = 152                     # GB300: 152 SMs
+FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM
+ALU_LANES_PER_SM = 64         # integer / bit-logic ALU pipe: 2 warp instructions per SM cycle (ncu: the ALU
+                              # instructions executed per active SM cycle are exactly 2 x its pipe utilization)
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/):
 # k_tile_l2_tc at half size, 0.459 GB read + write (node rows and the node x
@@ -55,11 +58,11 @@ SMS, LANES_PER_SM = 152, 128   # GB300: 152 SMs; 128 FP32 / INT32 lanes per SM
 # kernel has changed since the counters were taken.
 TRAFFIC = {"kernel": "tile", "bytes_per_launch": 0.92e9}
 
-# Integer (incl. bit-logic) thread instructions per full-DP-equivalent cell of
-# the bit-parallel edit-distance kernels, from one ncu capture of each
-# (sm__sass_thread_inst_executed_op_{integer,bit}_pred_on.sum / cells;
-# profiles/).  None until measured.
-INT_OPS_PER_CELL = {"pivot_dist": None, "verify": None}
+# ALU-pipe thread instructions per full-DP-equivalent cell (|q| x |o| per pair)
+# of the bit-parallel edit-distance kernels: sm__inst_executed_pipe_alu.sum x 32
+# over the cells of every launch of one batch pair of the dna workload at 0.2
+# scale (profiles/dp_str_dna_200k_r8.md).  None once the kernels change.
+INT_OPS_PER_CELL = {"pivot_dist": 0.600, "verify": 0.619}
 
 
 def workload(scale: float = 1.0):
@@ -98,12 +101,12 @@ def tensor_peak():
     return (float(m["bf16_tflops_sustained"]), "measured") if m else (1700.0, "fallback")
 
 
-def alu_peak(sm_mhz):
-    """INT32 / FP32 lane-operation peak (T ops/s) from the unit counts: 152 SMs
-    x 128 lanes x the SM clock (the median sampled under load, else the
-    maximum 2070 MHz)."""
+def alu_peak(sm_mhz, lanes=ALU_LANES_PER_SM):
+    """Lane-operation peak (T thread-instructions/s) of a pipe from the unit
+    counts: 152 SMs x its lanes per SM x the SM clock (the median sampled
+    under load, else the maximum 2070 MHz)."""
     mhz = sm_mhz or 2070.0
-    return SMS * LANES_PER_SM * mhz * 1e6 / 1e12, mhz
+    return SMS * lanes * mhz * 1e6 / 1e12, mhz
 
 
 class ClockSampler:
@@ -474,9 +477,9 @@ def bench_strings(name, args):
     peak, mhz = alu_peak(clocks.get("sm_mhz"))
     if dom in rates and INT_OPS_PER_CELL.get(dom):
         ach = rates[dom] * INT_OPS_PER_CELL[dom] / 1e12
-        out["roofline"] = {"bound": "alu", "kernel": dom, "unit": "T int ops/s", "achieved": round(ach, 3),
-                           "peak": round(peak, 2), "frac": round(ach / peak, 4),
-                           "peak_source": f"{SMS} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz",
+        out["roofline"] = {"bound": "alu", "kernel": dom, "unit": "T ALU-pipe thread instructions/s",
+                           "achieved": round(ach, 3), "peak": round(peak, 2), "frac": round(ach / peak, 4),
+                           "peak_source": f"{SMS} SMs x {ALU_LANES_PER_SM} ALU lanes x {mhz:.0f} MHz (derived)",
                            "int_ops_per_cell": INT_OPS_PER_CELL[dom],
                            "dp_cells_per_s": {kk: round(v, 1) for kk, v in rates.items()}, "traffic": None}
     else:

@@ -342,11 +342,14 @@ typedef struct {
  * sample batch's radius (range: the median of `radii`; kNN: the mean k-th
  * distance of a run of the batch), ranks the shapes fanout in 4 .. 64, h in 1
  * .. Algorithm 1's height for that fanout, by gts_cost_model, rebuilds the
- * index with each of the `candidates` (1 .. 16) cheapest shapes and with the
- * current one, times the sample batch (`reps` runs, median of the wall time;
+ * index with the current shape and with `candidates` (1 .. 16) others -- half
+ * of them (rounded up) the current shape's neighbours (fanout halved or
+ * doubled, one pivot level fewer or more), the rest the model's cheapest --
+ * times the sample batch (`reps` runs, median of the wall time;
  * one untimed warm-up run first) on each, and leaves the index rebuilt with
- * the fastest.  Ids and answers do not change (every shape answers the same
- * definition).  out: host gts_shape[candidates + 1] (may be NULL), the shapes
+ * the fastest.  A shape whose tree or batch does not fit the device is
+ * skipped (reported with measured_ms = +inf).  Ids and answers do not change
+ * (every shape answers the same definition).  out: host gts_shape[candidates + 1] (may be NULL), the shapes
  * timed, fastest first; *n_out (may be NULL) their number.  On an error the
  * index holds one of the timed shapes. */
 gts_status gts_autotune_shape(gts_index *index, const gts_objects *queries, const float *radii, const int32_t *k,

@@ -978,17 +978,29 @@ gts_status gts_autotune_shape(gts_index *ix, const gts_objects *queries, const f
         }
         std::stable_sort(all.begin(), all.end(),
                          [](const gts_shape &a, const gts_shape &b) { return a.model_cost < b.model_cost; });
-        std::vector<gts_shape> cand(all.begin(), all.begin() + std::min<size_t>(all.size(), (size_t)candidates));
-        {
-            gts_shape cur;
-            cur.fanout = ix->F;
-            cur.n_pivots = ix->tree.h;
-            cur.model_cost = gts_cost_model(n, nq, p, ix->F, ix->tree.h, C);
-            cur.measured_ms = 0.0;
-            bool have = false;
-            for (auto &c : cand) have = have || (c.fanout == cur.fanout && c.n_pivots == cur.n_pivots);
-            if (!have) cand.insert(cand.begin(), cur);
-        }
+        // candidates: the current shape, its neighbours (fanout halved /
+        // doubled, one pivot level fewer / more) and the model's cheapest,
+        // `candidates` in all besides the current one
+        std::vector<gts_shape> cand;
+        auto add = [&](int F, int h) {
+            if (F < 2 || F > kMaxFanout || h < 1 || h > tree_height(n + ix->cache.count, F, 0)) return;
+            for (auto &c : cand)
+                if (c.fanout == F && c.n_pivots == h) return;
+            gts_shape sh;
+            sh.fanout = F;
+            sh.n_pivots = h;
+            sh.model_cost = gts_cost_model(n, nq, p, F, h, C);
+            sh.measured_ms = 0.0;
+            cand.push_back(sh);
+        };
+        add(ix->F, ix->tree.h);
+        const int F0 = ix->F, h0 = ix->tree.h;
+        const int nb[][2] = {{F0, h0 - 1}, {F0, h0 + 1}, {F0 * 2, h0 - 1}, {F0 / 2, h0 + 1}, {F0 * 2, h0}, {F0 / 2, h0}};
+        const size_t want = 1 + (size_t)candidates;
+        for (auto &v : nb)
+            if (cand.size() < 1 + ((size_t)candidates + 1) / 2) add(v[0], v[1]);
+        for (auto &sh : all)
+            if (cand.size() < want) add(sh.fanout, sh.n_pivots);
         o.result_on_device = 1;
         auto time_shape = [&](gts_shape &sh) {
             ix->F = sh.fanout;
@@ -1009,9 +1021,22 @@ gts_status gts_autotune_shape(gts_index *ix, const gts_objects *queries, const f
             sh.measured_ms = v[v.size() / 2];
         };
         for (auto &sh : cand) {
-            time_shape(sh);
+            try {
+                time_shape(sh);
+            } catch (const Error &e) {
+                // a shape whose tree or batch does not fit the device is
+                // skipped (recorded with an infinite time); other errors stand
+                if (e.status != GTS_ENOMEM && e.status != GTS_EOVERFLOW) throw;
+                cudaGetLastError();
+                sh.measured_ms = INFINITY;
+            }
             timed.push_back(sh);
         }
+        GTS_REQUIRE(std::isfinite(std::min_element(timed.begin(), timed.end(),
+                                                   [](const gts_shape &a, const gts_shape &b) {
+                                                       return a.measured_ms < b.measured_ms;
+                                                   })->measured_ms),
+                    GTS_ENOMEM, "no candidate shape fits the device");
         std::stable_sort(timed.begin(), timed.end(),
                          [](const gts_shape &a, const gts_shape &b) { return a.measured_ms < b.measured_ms; });
         const gts_shape &best = timed.front();

@@ -88,7 +88,7 @@ struct ScanArgs {
 
 // Per-warp shared-memory layout (bytes), from h, hp and dim.
 struct WarpLayout {
-    int bar, rec, path, del, T, X, leaf, bytes;
+    int bar, rec, path, del, T, X, qrow, toff, leaf, bytes;
 };
 
 __host__ __device__ inline WarpLayout warp_layout(int h, int hp, int dim, bool fused) {
@@ -106,6 +106,10 @@ __host__ __device__ inline WarpLayout warp_layout(int h, int hp, int dim, bool f
     o += h * kTPad * 4;
     L.X = o;
     o += fused ? ((kRowsB * (dim | 1) * 4 + 15) & ~15) : 0;
+    L.qrow = o;                 // fused: the current record's query row
+    o += fused ? kScanMaxDim * 4 : 0;
+    L.toff = o;                 // each column's window offset in T
+    o += kMaxHeight * 4;
     L.leaf = o;
     o += kRowsB;
     L.bytes = (o + 15) & ~15;
@@ -153,6 +157,8 @@ __global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_scan_warps(ScanArgs
     int64_t *del = reinterpret_cast<int64_t *>(wb + L.del);
     float *T = reinterpret_cast<float *>(wb + L.T);
     float *Xs = reinterpret_cast<float *>(wb + L.X);
+    float *qrow = reinterpret_cast<float *>(wb + L.qrow);
+    int *toffs = reinterpret_cast<int *>(wb + L.toff);
     uint8_t *leaf = wb + L.leaf;
     const int xs = a.dim | 1;
     if (lane == 0) {
@@ -224,12 +230,10 @@ __global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_scan_warps(ScanArgs
                 const int rr = e / a.dim, i = e - rr * a.dim;
                 Xs[rr * xs + i] = a.X[g0 * a.dim + e];
             }
+        if (lane < a.h) toffs[lane] = (int)(((int64_t)lane * a.n + g0) & 3) + lane * kTPad;
         __syncwarp();
         staged += (unsigned long long)nr;
         const int nstrips = (nr + 31) >> 5;
-        int toff[kMaxHeight];
-#pragma unroll
-        for (int l = 0; l < kMaxHeight; ++l) toff[l] = l < a.h ? (int)(((int64_t)l * a.n + g0) & 3) + l * kTPad : 0;
         for (int c0 = 0; c0 < cnt; c0 += kRecW) {
             const int k = min(kRecW, cnt - c0);
             ok = __all_sync(kFull, tc::mbar_wait(bar, phase & 1u));
@@ -238,14 +242,11 @@ __global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_scan_warps(ScanArgs
             for (int i = 0; i < k; ++i) {
                 const TileRec rc = rec[i];
                 const float thr = rc.thr;
-                float dq[kMaxHeight];
-#pragma unroll
-                for (int l = 0; l < kMaxHeight; ++l) dq[l] = l < a.h ? path[i * a.hp + l] : 0.f;
-                float qv[FUSED ? kScanMaxDim : 1];
+                const float *dq = path + i * a.hp;   // this record's pivot-distance tile (shared memory)
                 if (FUSED) {
-#pragma unroll
-                    for (int c2 = 0; c2 < kScanMaxDim; ++c2)
-                        qv[c2] = c2 < a.dim ? a.Q[(int64_t)rc.q * a.dim + c2] : 0.f;
+                    __syncwarp();                    // the previous record's query row is read
+                    if (lane < a.dim) qrow[lane] = a.Q[(int64_t)rc.q * a.dim + lane];
+                    __syncwarp();
                 }
                 uint32_t pb[kRowsB / 32], ab[kRowsB / 32];
                 float dv[FUSED ? kRowsB / 32 : 1];
@@ -257,13 +258,14 @@ __global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_scan_warps(ScanArgs
                     const int rr = s * 32 + lane;
                     bool pass = rr < nr && ((rc.mask >> leaf[rr]) & 1ull) && (!a.any_deleted || del[rr] > rc.seq);
                     if (pass) {
-#pragma unroll
-                        for (int l = 0; l < kMaxHeight; ++l) {
-                            if (l < a.h) {
-                                const float Tv = T[toff[l] + rr];
-                                const float eps = a.epsc > 0.f ? a.epsc * (Tv + dq[l] + thr) : 0.f;
-                                if (fabsf(Tv - dq[l]) > thr + eps) pass = false;
-                            }
+                        // loops bounded by the tree's h and the data's dim:
+                        // no predicated-off iterations
+#pragma unroll 2
+                        for (int l = 0; l < a.h; ++l) {
+                            const float Tv = T[toffs[l] + rr];
+                            const float dl = dq[l];
+                            const float eps = a.epsc * (Tv + dl + thr);
+                            if (fabsf(Tv - dl) > thr + eps) pass = false;
                         }
                     }
                     bool take = false;
@@ -274,12 +276,16 @@ __global__ void __launch_bounds__(kThreads, FUSED ? 6 : 8) k_scan_warps(ScanArgs
                             // the pair's FP32 distance and the band decision (the
                             // same bound as the candidate verification)
                             float sum = 0.f;
-#pragma unroll
-                            for (int c2 = 0; c2 < kScanMaxDim; ++c2) {
-                                if (c2 < a.dim) {
-                                    const float t = qv[c2] - Xs[rr * xs + c2];
-                                    sum = a.l2 ? fmaf(t, t, sum) : sum + fabsf(t);
+                            const float *xr = Xs + rr * xs;
+                            if (a.l2) {
+#pragma unroll 2
+                                for (int c2 = 0; c2 < a.dim; ++c2) {
+                                    const float t = qrow[c2] - xr[c2];
+                                    sum = fmaf(t, t, sum);
                                 }
+                            } else {
+#pragma unroll 2
+                                for (int c2 = 0; c2 < a.dim; ++c2) sum += fabsf(qrow[c2] - xr[c2]);
                             }
                             const float d32 = a.l2 ? sqrtf(sum) : sum;
                             const float hi = d32 * (1.f + 2.f * a.rel) + kAbsFloor;

@@ -1739,12 +1739,26 @@ __global__ void k_u8_to_i64(const uint8_t *a, int64_t n, int64_t *b) {
     if (blockIdx.x == 0 && threadIdx.x == 0) b[n] = 0;
 }
 
-__global__ void k_range_counts(const uint64_t *__restrict__ rkey, int64_t R, int64_t *__restrict__ counts,
-                               int64_t *__restrict__ ids) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd((unsigned long long *)&counts[rkey[i] >> 32], 1ull);
-        ids[i] = (int64_t)(rkey[i] & 0xffffffffull);
+// Range answers sorted by (query << 32 | id): query q's answers start at the
+// first key >= q << 32 (a binary search per query, no atomics), and each
+// answer's id is the key's low half.
+__global__ void k_range_offsets(const uint64_t *__restrict__ rkey, int64_t R, int64_t nq,
+                                int64_t *__restrict__ offsets) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = (uint64_t)q << 32;
+        int64_t a = 0, b = R;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (rkey[m] < x) a = m + 1;
+            else b = m;
+        }
+        offsets[q] = a;
     }
+}
+
+__global__ void k_range_ids(const uint64_t *__restrict__ rkey, int64_t R, int64_t *__restrict__ ids) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x)
+        ids[i] = (int64_t)(rkey[i] & 0xffffffffull);
 }
 
 __global__ void k_knn_counts(const int32_t *bn, int64_t nq, int64_t *counts) {
@@ -2196,7 +2210,7 @@ struct Runner {
         const int64_t base = ix->tree.lvl_off[l], lvl_next = ix->tree.lvl_off[l + 1];
         const int64_t nn = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
         DBuf<uint64_t> mask(E, st);
-        const bool need_counts = !regroup_uses_bits(ix->tree, qb.nq);
+        const bool need_counts = !regroup_uses_bits(ix->tree, qb.nq, E);
         DBuf<int32_t> ncount(need_counts ? nn : 0, st);
         if (need_counts) GTS_CUDA(cudaMemsetAsync(ncount.get(), 0, nn * 4, st));
         const bool aligned = ((uintptr_t)d.Q & 15) == 0;
@@ -3025,8 +3039,6 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         }
         R.rkeys.clear();
         R.rdists.clear();
-        DBuf<int64_t> counts(nq + 1, st);
-        GTS_CUDA(cudaMemsetAsync(counts.get(), 0, (nq + 1) * 8, st));
         if (Rt > 0) {
             int qbits = 1;
             while (((int64_t)1 << qbits) < nq) ++qbits;
@@ -3034,15 +3046,15 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
             cub::DeviceRadixSort::SortPairs(nullptr, tb, keys.get(), keys2.get(), dd.get(), out.dist.get(), Rt, 0,
                                             32 + qbits, st);
             DBuf<uint8_t> tmp(tb, st);
-            R.clk.begin(GTS_STAGE_OTHER, 2);
+            R.clk.begin(GTS_STAGE_OTHER, 3);
             GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, keys.get(), keys2.get(), dd.get(), out.dist.get(),
                                                      Rt, 0, 32 + qbits, st));
-            k_range_counts<<<nblocks(Rt, kT), kT, 0, st>>>(keys2.get(), Rt, counts.get(), out.ids.get());
+            k_range_ids<<<R.cap(nblocks(Rt, kT)), kT, 0, st>>>(keys2.get(), Rt, out.ids.get());
+            k_range_offsets<<<nblocks(nq + 1, kT), kT, 0, st>>>(keys2.get(), Rt, nq, out.offsets.get());
             R.clk.end();
+        } else {
+            GTS_CUDA(cudaMemsetAsync(out.offsets.get(), 0, (nq + 1) * 8, st));
         }
-        R.clk.begin(GTS_STAGE_OTHER);
-        exclusive_scan(counts.get(), out.offsets.get(), nq + 1, st);
-        R.clk.end();
         out.total = Rt;
     }
     check_launch("assemble");

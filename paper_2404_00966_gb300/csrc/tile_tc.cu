@@ -899,9 +899,12 @@ void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8
     check_launch("split queries");
 }
 
-bool regroup_uses_bits(const Tree &t, int64_t nq) {
+bool regroup_uses_bits(const Tree &t, int64_t nq, int64_t E) {
+    // the bitmap costs a pass over nodes x query words; it pays when the
+    // entries are dense in it (at least one per four words) and it stays small
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
-    return nn * ((nq + 31) / 32) * 8 <= ((int64_t)1 << 30);
+    const int64_t words = nn * ((nq + 31) / 32);
+    return words * 8 <= ((int64_t)1 << 30) && words <= 4 * E;
 }
 
 int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t st, const int32_t *counts,
@@ -910,7 +913,7 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
     const int64_t nn = t.lvl_off[t.h] - t.lvl_off[t.h - 1];
     // the bitmap form when its two (node x query-word) arrays stay small
     const int64_t nw = (tq.nq + 31) / 32;
-    const bool use_bits = regroup_uses_bits(t, tq.nq);
+    const bool use_bits = regroup_uses_bits(t, tq.nq, E);
     DBuf<uint32_t> &bits = rg.bits;
     DBuf<int32_t> &wpre = rg.wpre;
     bits.alloc(use_bits ? nn * nw : 0, st);

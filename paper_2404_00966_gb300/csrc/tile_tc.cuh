@@ -111,7 +111,7 @@ void tc_split_queries(const float *Q, int64_t nq, int dim, int dim_p, DBuf<uint8
                       DBuf<float> &qn2, cudaStream_t st, const int32_t *sel = nullptr);
 // whether tc_regroup counts entries per node itself (a node x query bitmap),
 // so the caller need not
-bool regroup_uses_bits(const Tree &t, int64_t nq);
+bool regroup_uses_bits(const Tree &t, int64_t nq, int64_t E);
 // regroup the last-level entries by node into tiles; returns the tile count
 // counts: entries with a surviving leaf per last-level node, if already known
 // window_ok: mark dense nodes' items for window mode (tensor-core tiles with
