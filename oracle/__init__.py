@@ -19,8 +19,8 @@ import numpy as np
 
 from synth import Strings
 
-EDIT, L1, L2 = 0, 1, 2
-METRICS = {"edit": EDIT, "l1": L1, "l2": L2}
+EDIT, L1, L2, COS = 0, 1, 2, 3
+METRICS = {"edit": EDIT, "l1": L1, "l2": L2, "cos": COS}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
@@ -56,6 +56,10 @@ def lib():
         L.orc_l2sq.argtypes = [P, P, I64]
         L.orc_l1.restype = ctypes.c_double
         L.orc_l1.argtypes = [P, P, I64]
+        L.orc_cos_key.restype = ctypes.c_double
+        L.orc_cos_key.argtypes = [P, P, I64]
+        L.orc_cos_limit.restype = ctypes.c_double
+        L.orc_cos_limit.argtypes = [ctypes.c_double]
         L.orc_keys_vec.argtypes = [ctypes.c_int, P, I64, I64, P, P]
         L.orc_keys_str.argtypes = [P, P, I64, P, I64, P]
         L.orc_range_vec.argtypes = [ctypes.c_int, P, I64, I64, P, I64, P, P, P, P, P, P, P, P]
@@ -100,6 +104,18 @@ def l1(a, b) -> float:
     return float(lib().orc_l1(_p(a), _p(b), a.shape[0]))
 
 
+def cos_key(a, b) -> float:
+    """1 - cos of the angle between two vectors (FP64 sums, c clamped)."""
+    a = np.ascontiguousarray(a, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    return float(lib().orc_cos_key(_p(a), _p(b), a.shape[0]))
+
+
+def cos_limit(r: float) -> float:
+    """The range limit on the key for an angle r: 1 - cos(min(r, pi))."""
+    return float(lib().orc_cos_limit(float(np.float32(r))))
+
+
 def keys_to_pivot(metric: str, objects, pivot_index: int) -> np.ndarray:
     """Exact keys (FP64 for vectors: d^2 for L2, d for L1; int for edit) from
     object ``pivot_index`` to every object."""
@@ -134,11 +150,15 @@ def distances_to(metric: str, objects, target) -> np.ndarray:
     t = np.ascontiguousarray(target, np.float32)
     out = np.empty(X.shape[0], np.float64)
     lib().orc_keys_vec(m, _p(X), X.shape[0], X.shape[1], _p(t), _p(out))
-    return np.sqrt(out) if m == L2 else out
+    return key_to_distance(metric, out)
 
 
 def key_to_distance(metric: str, keys: np.ndarray) -> np.ndarray:
-    return np.sqrt(keys) if metric == "l2" else keys
+    if metric == "l2":
+        return np.sqrt(keys)
+    if metric == "cos":
+        return np.arccos(1.0 - keys)
+    return keys
 
 
 # ------------------------------------------------------------------ queries

@@ -26,6 +26,14 @@
  *         kNN orders by key (the square root is monotone, and the squared
  *         value keeps distinct FP64 sums distinct).  Reported d = sqrt(key).
  *   l1:   key = sum_i |(double)q_i - (double)x_i|, in increasing i, FP64.
+ *   cos:  the angle between the vectors, d = arccos(c), c = q.x / (|q| |x|)
+ *         (the word cosine distance of Table 2, read as the angular distance,
+ *         a metric on directions).  The three sums q.x, |q|^2, |x|^2 run in
+ *         increasing i in FP64, c = dot / (sqrt(|q|^2) * sqrt(|x|^2)) clamped
+ *         to [-1, 1], key = 1 - c (monotone in the angle).  Range compares
+ *         key <= 1 - cos((double)r) (r clipped to [0, pi]); kNN orders by key.
+ *         Reported d = arccos(1 - key).  Zero vectors have no direction and
+ *         are not accepted by the library.
  *
  * Stream updates (Section 4.4) are modelled by sequence numbers: object o is
  * visible to a query with sequence s iff ins_seq[o] < s < del_seq[o]
@@ -40,7 +48,7 @@
 #include <omp.h>
 #endif
 
-enum { OR_EDIT = 0, OR_L1 = 1, OR_L2 = 2 };
+enum { OR_EDIT = 0, OR_L1 = 1, OR_L2 = 2, OR_COS = 3 };
 
 int orc_threads(void) {
 #ifdef _OPENMP
@@ -126,7 +134,34 @@ double orc_l1(const float *a, const float *b, int64_t dim) {
     return s;
 }
 
+/* 1 - cos of the angle, the three FP64 sums in increasing i, c clamped to [-1, 1]. */
+double orc_cos_key(const float *a, const float *b, int64_t dim) {
+    double dot = 0.0, na = 0.0, nb = 0.0;
+    for (int64_t i = 0; i < dim; ++i) {
+        double x = (double)a[i], y = (double)b[i];
+        double p = x * y;
+        dot = dot + p;
+        double pa = x * x;
+        na = na + pa;
+        double pb = y * y;
+        nb = nb + pb;
+    }
+    double den = sqrt(na) * sqrt(nb);
+    double c = dot / den;
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    return 1.0 - c;
+}
+
+/* the range limit on the key for an angle r */
+double orc_cos_limit(double r) {
+    const double pi = 3.14159265358979323846;
+    if (r > pi) r = pi;
+    return 1.0 - cos(r);
+}
+
 static double vec_key(int metric, const float *q, const float *x, int64_t dim) {
+    if (metric == OR_COS) return orc_cos_key(q, x, dim);
     return metric == OR_L2 ? orc_l2sq(q, x, dim) : orc_l1(q, x, dim);
 }
 
@@ -159,7 +194,7 @@ void orc_range_vec(int metric, const float *X, int64_t n, int64_t dim, const flo
     for (int64_t qi = 0; qi < nq; ++qi) {
         const float *q = Q + qi * dim;
         double r = (double)radii[qi];
-        double lim = metric == OR_L2 ? r * r : r;
+        double lim = metric == OR_L2 ? r * r : (metric == OR_COS ? orc_cos_limit(r) : r);
         int64_t s = qseq ? qseq[qi] : 0;
         int64_t c = 0;
         for (int64_t o = 0; o < n; ++o) {

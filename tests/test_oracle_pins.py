@@ -156,6 +156,90 @@ def test_vector_metric_axioms():
             assert dik <= (dij + djk) * (1 + 1e-12)
 
 
+# ------------------------------------------------------------ angular (cosine) distance
+
+def test_cos_closed_forms():
+    """Norms chosen exact (3-4-5 triangles): c and the key exactly."""
+    e1, e2 = np.float32([1, 0, 0]), np.float32([0, 1, 0])
+    assert oracle.cos_key(e1, e2) == 1.0                       # orthogonal: pi / 2
+    x = np.float32([3, 4])
+    assert oracle.cos_key(x, 4 * x) == 0.0                     # one direction: angle 0
+    assert oracle.cos_key(x, np.float32([-1.5, -2])) == 2.0    # opposite: angle pi
+    assert oracle.cos_key(np.float32([3, 4]), np.float32([4, 3])) == 1.0 - 24.0 / 25.0
+    assert oracle.cos_key(np.float32([3, 4, 0]), np.float32([0, 4, 3])) == 1.0 - 16.0 / 25.0
+    # 45 degrees: c = 1/sqrt(2) within rounding
+    assert abs(oracle.cos_key(np.float32([1, 0]), np.float32([1, 1])) - (1 - 2 ** -0.5)) < 4e-16
+    # the range limit: 1 - cos(r), r clipped at pi
+    assert oracle.cos_limit(0.0) == 0.0
+    assert oracle.cos_limit(4.0) == 2.0 and oracle.cos_limit(np.pi) == oracle.cos_limit(4.0)
+    assert abs(oracle.cos_limit(np.pi / 2) - 1.0) < 1e-7       # float32(pi / 2) is not pi / 2
+    # distances
+    d = oracle.distances_to("cos", np.float32([[3, 4], [4, 3], [-3, -4]]), np.float32([3, 4]))
+    assert d[0] == 0.0 and abs(d[1] - np.arccos(24 / 25)) < 1e-15 and d[2] == np.pi
+
+
+def test_cos_scaling_axioms_and_long_double():
+    rng = np.random.default_rng(6)
+    D = 300
+    P = rng.standard_normal((24, D)).astype(np.float32)
+    for i in range(24):
+        for j in range(24):
+            k = oracle.cos_key(P[i], P[j])
+            # power-of-two scaling changes no rounding: the same key
+            assert oracle.cos_key(4 * P[i], 0.25 * P[j]) == k
+            assert k == oracle.cos_key(P[j], P[i])               # symmetry
+            a, b = P[i].astype(np.longdouble), P[j].astype(np.longdouble)
+            c = (a @ b) / (np.sqrt(a @ a) * np.sqrt(b @ b))
+            # three recursive sums and a few roundings: well within 4 (D + 4) 2^-53
+            assert abs(k - float(1 - c)) <= 4 * (D + 4) * 2.0 ** -53
+    ang = lambda u, v: float(np.arccos(1.0 - oracle.cos_key(u, v)))
+    for i, j, k in itertools.product(range(12), repeat=3):
+        assert ang(P[i], P[k]) <= ang(P[i], P[j]) + ang(P[j], P[k]) + 1e-12
+    assert all(oracle.cos_key(P[i], P[i]) <= 4e-16 for i in range(24))
+
+
+def _exact_cos_order(X, q):
+    """A key with the same order as the cosine, in exact rationals:
+    sign(q.x) (q.x)^2 / |x|^2 (|q| is common to all x)."""
+    out = []
+    for x in X:
+        dot = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(q, x))
+        nx = sum(Fraction(float(b)) ** 2 for b in x)
+        out.append((1 if dot > 0 else (-1 if dot < 0 else 0)) * dot * dot / nx)
+    return out
+
+
+def test_range_and_knn_cos_by_exhaustion():
+    """Integer points: many exactly equal angles.  Range: exactly the objects
+    whose exact cosine clears cos(r) (radii kept off every object's angle);
+    kNN: k members, none of them with a smaller exact cosine than a
+    non-member, in (FP64 key, id) order."""
+    rng = np.random.default_rng(13)
+    n, D, nq = 150, 4, 12
+    X = rng.integers(-3, 4, size=(n, D)).astype(np.float32)
+    X[np.all(X == 0, axis=1)] = 1.0                             # no zero vector
+    Q = rng.integers(-3, 4, size=(nq, D)).astype(np.float32)
+    Q[np.all(Q == 0, axis=1)] = 1.0
+    ks = rng.integers(1, 20, size=nq).astype(np.int32)
+    radii = np.float32(rng.uniform(0.2, 2.5, size=nq))
+    off, ids, dist, keys = oracle.range_query("cos", X, Q, radii)
+    koff, kids, kdist, kkeys = oracle.knn_query("cos", X, Q, ks)
+    for qi in range(nq):
+        q = Q[qi]
+        nq2 = float(q.astype(np.float64) @ q.astype(np.float64))
+        cos_exact = [float(q.astype(np.float64) @ x.astype(np.float64)) / np.sqrt(nq2 * float(x.astype(np.float64) @ x.astype(np.float64))) for x in X]
+        cr = np.cos(np.float64(radii[qi]))
+        assert min(abs(c - cr) for c in cos_exact) > 1e-9       # no object on the boundary
+        want = [o for o in range(n) if cos_exact[o] > cr]
+        assert list(ids[off[qi]:off[qi + 1]]) == want
+        ex = _exact_cos_order(X, q)
+        got = list(kids[koff[qi]:koff[qi + 1]])
+        assert len(got) == min(int(ks[qi]), n)
+        outside = [o for o in range(n) if o not in got]
+        assert min(ex[s] for s in got) >= max(ex[o] for o in outside)
+        assert list(kkeys[koff[qi]:koff[qi + 1]]) == sorted(kkeys[koff[qi]:koff[qi + 1]])
+
+
 # ------------------------------------------------------------ range / kNN sets
 
 def _exact_keys_vec(metric, X, q):
