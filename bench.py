@@ -598,7 +598,7 @@ def bench_zipf2d(args):
     scan_roof = None
     if scan_ms > 0:
         gbs = scan_bytes / (scan_ms / 1e3) / 1e9
-        scan_roof = {"bound": "hbm", "kernel": "k_scan_blocks (stage leaf_scan)", "achieved": round(gbs, 1),
+        scan_roof = {"bound": "hbm", "kernel": "k_scan_warps (stage leaf_scan)", "achieved": round(gbs, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_source": hsrc,
                      "bytes_per_launch": int(scan_bytes), "ms_per_launch": round(scan_ms / max(1.0, stage_launch.get("leaf_scan", 1.0)), 4),
                      "traffic": None}

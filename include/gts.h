@@ -49,8 +49,18 @@ typedef enum {
 /* Distance metrics (Section 3, metric-space axioms; Table 2 of the paper).
  *  GTS_EDIT: unit-cost Levenshtein distance between byte strings.
  *  GTS_L1:   sum_i |q_i - x_i| over float32 vectors.
- *  GTS_L2:   sqrt(sum_i (q_i - x_i)^2) over float32 vectors. */
-typedef enum { GTS_EDIT = 0, GTS_L1 = 1, GTS_L2 = 2 } gts_metric;
+ *  GTS_L2:   sqrt(sum_i (q_i - x_i)^2) over float32 vectors.
+ *  GTS_COS:  the angle between float32 vectors, arccos(q.x / (|q| |x|)) in
+ *            radians (Table 2's word cosine distance, read as the angular
+ *            distance, a metric on directions).  Objects and queries must not
+ *            be zero vectors (GTS_EINVAL).  Exact decisions use the FP64 key
+ *            1 - c, c = q.x / (sqrt(|q|^2) sqrt(|x|^2)) from FP64 sums in
+ *            coordinate order, clamped to [-1, 1]: range keeps key <= 1 -
+ *            cos(r) (r clipped to [0, pi]), kNN orders by (key, id); the
+ *            reported distance is arccos(1 - key).  The index is an L2 tree
+ *            over the unit vectors (the chord 2 sin(angle / 2) orders like the
+ *            angle), so every L2 kernel serves it. */
+typedef enum { GTS_EDIT = 0, GTS_L1 = 1, GTS_L2 = 2, GTS_COS = 3 } gts_metric;
 
 /* Verification precision for L2.  Both give the same result sets:
  *  GTS_PREC_FP32: FP32 CUDA-core distances, FP64 recheck of candidates whose

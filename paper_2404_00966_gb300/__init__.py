@@ -19,12 +19,12 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["GTSError", "Index", "ShardedIndex", "Server", "lib", "merge_knn", "merge_range", "cost_model", "EDIT",
-           "L1", "L2", "PREC_FP32", "PREC_BF16", "STAT_NAMES"]
+           "L1", "L2", "COS", "PREC_FP32", "PREC_BF16", "STAT_NAMES"]
 
-EDIT, L1, L2 = 0, 1, 2
+EDIT, L1, L2, COS = 0, 1, 2, 3
 PREC_FP32, PREC_BF16 = 0, 1
 QUERY_COUNT_TABLE_PASS, QUERY_KEYS = 1, 2
-METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2}
+METRIC_IDS = {"edit": EDIT, "l1": L1, "l2": L2, "cos": COS}
 STAT_NAMES = ["pivot_dist", "frontier", "scanned_rows", "candidates", "rechecks", "results", "groups", "cache_rows",
               "launches", "tiles", "tile_entries", "tile_pairs",
               "dense_pairs", "dense_last", "table_pass", "scan_records"]
@@ -449,7 +449,7 @@ class Index:
         h = ctypes.c_void_p()
         _check(lib().gts_load(os.fsencode(path), ctypes.byref(opts), ctypes.byref(h)))
         ix = cls(h, metric or "")
-        ix.metric = {EDIT: "edit", L1: "l1", L2: "l2"}[ix.info()["metric"]]
+        ix.metric = {EDIT: "edit", L1: "l1", L2: "l2", COS: "cos"}[ix.info()["metric"]]
         return ix
 
     def get_tuning(self) -> dict:

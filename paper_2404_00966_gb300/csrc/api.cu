@@ -80,6 +80,27 @@ __global__ void k_nonfinite(const float *x, int64_t n, int *flag) {
         if (!isfinite(x[i])) *flag = 1;
 }
 
+// Unit vectors for the angular distance: a warp per row sums the squares in
+// FP64, every coordinate is divided in FP64 and rounded to FP32 once (so the
+// rounded vector lies within 2^-24 of the exact unit vector).  A zero row
+// sets *zero (it has no direction).
+__global__ void k_unit_rows(const float *__restrict__ X, int64_t n, int dim, float *__restrict__ out, int *zero) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+        const float *x = X + r * dim;
+        double s = 0.0;
+        for (int i = lane; i < dim; i += 32) s += (double)x[i] * (double)x[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (s == 0.0) {
+            if (lane == 0) *zero = 1;
+            continue;
+        }
+        const double inv = 1.0 / sqrt(s);
+        for (int i = lane; i < dim; i += 32) out[r * dim + i] = (float)((double)x[i] * inv);
+    }
+}
+
 // Device copy of a caller's object set (or a view when it is already on the device).
 struct DevObjects {
     Objects v;
@@ -154,6 +175,20 @@ void load_objects(const gts_objects *o, int want_dim_or_neg, DevObjects &out, cu
     }
 }
 
+// GTS_COS: the unit vectors of a loaded vector set into `unit` (rejects zero rows)
+void unit_vectors(const Objects &v, DBuf<float> &unit, cudaStream_t st, const char *what) {
+    const size_t cnt = (size_t)v.n * v.dim;
+    unit.alloc(cnt > 0 ? cnt : 1, st);
+    if (!cnt) return;
+    DBuf<int> flag(1, st);
+    GTS_CUDA(cudaMemsetAsync(flag.get(), 0, 4, st));
+    k_unit_rows<<<std::min<int64_t>(nb(v.n * 32), 4096), kT, 0, st>>>(v.X, v.n, v.dim, unit.get(), flag.get());
+    int h = 0;
+    GTS_CUDA(cudaMemcpyAsync(&h, flag.get(), 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    GTS_REQUIRE(h == 0, GTS_EINVAL, std::string(what) + ": a zero vector has no angle (GTS_COS)");
+}
+
 template <class T>
 void copy_small_to_device(const T *src, int64_t n, bool on_device, DBuf<T> &dst, std::vector<T> &host,
                           cudaStream_t st) {
@@ -210,8 +245,18 @@ void cache_append(gts_index *ix, const DevObjects &o, int64_t *ids_out) {
     grow(c.del, c.count, need, st);
     if (ix->dim > 0) {
         grow(c.X, (size_t)c.count * ix->dim, (size_t)need * ix->dim, st);
-        GTS_CUDA(cudaMemcpyAsync(c.X.get() + (size_t)c.count * ix->dim, o.v.X, (size_t)m * ix->dim * 4,
+        const float *rows = o.v.X;
+        DBuf<float> unit;
+        if (ix->metric == GTS_COS) {   // unit vectors for the L2 kernels, the raw rows for the FP64 keys
+            unit_vectors(o.v, unit, st, "objects");
+            rows = unit.get();
+            grow(c.Xr, (size_t)c.count * ix->dim, (size_t)need * ix->dim, st);
+            GTS_CUDA(cudaMemcpyAsync(c.Xr.get() + (size_t)c.count * ix->dim, o.v.X, (size_t)m * ix->dim * 4,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+        GTS_CUDA(cudaMemcpyAsync(c.X.get() + (size_t)c.count * ix->dim, rows, (size_t)m * ix->dim * 4,
                                  cudaMemcpyDeviceToDevice, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
     } else {
         if (c.h_Soff.empty()) c.h_Soff.push_back(0);
         const int64_t add = o.h_off[m];
@@ -332,11 +377,17 @@ void rebuild(gts_index *ix) {
     DBuf<float> X;
     DBuf<uint8_t> S;
     DBuf<int64_t> Soff;
+    DBuf<float> Xr;
     if (ix->dim > 0) {
         X.alloc((size_t)(m > 0 ? m : 1) * ix->dim, st);
         k_gather_vec_rows<<<nb(m * (int64_t)ix->dim), kT, 0, st>>>(t.X.get(), c.X.get(), ix->dim, t.n, dsrc.get(), m,
                                                                    X.get());
         o.X = X.get();
+        if (ix->metric == GTS_COS) {
+            Xr.alloc((size_t)(m > 0 ? m : 1) * ix->dim, st);
+            k_gather_vec_rows<<<nb(m * (int64_t)ix->dim), kT, 0, st>>>(t.Xr.get(), c.Xr.get(), ix->dim, t.n,
+                                                                       dsrc.get(), m, Xr.get());
+        }
     } else {
         // lengths on the host from the two offset tables
         std::vector<int64_t> toff(t.n + 1, 0);
@@ -366,7 +417,8 @@ void rebuild(gts_index *ix) {
     ix->rebuilds += 1;
     const int h = tree_height(m, ix->F, ix->n_pivots_req);
     const int64_t root = m > 0 ? (int64_t)(splitmix64(ix->seed + (uint64_t)ix->rebuilds) % (uint64_t)m) : 0;
-    build_tree(nt, o, ids.get(), ix->metric, ix->F, h, root, st);
+    build_tree(nt, o, ids.get(), ix->metric == GTS_COS ? GTS_L2 : ix->metric, ix->F, h, root, st,
+               ix->metric == GTS_COS ? Xr.get() : nullptr);
     ix->tree = std::move(nt);
     ix->cache = Cache();
     ix->rebuild_seq = ix->seq;
@@ -436,6 +488,12 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
         qb.nq = nq;
         qb.dim = ix->dim;
         qb.Q = dq.v.X;
+        DBuf<float> qunit;
+        if (ix->metric == GTS_COS) {   // unit query vectors for the L2 kernels, the raw ones for the FP64 keys
+            unit_vectors(dq.v, qunit, st, "queries");
+            qb.Q = qunit.get();
+            qb.Qr = dq.v.X;
+        }
         qb.S = dq.v.S;
         qb.Soff = dq.v.Soff;
         qb.max_len = dq.v.max_len;
@@ -460,6 +518,20 @@ gts_status query_common(gts_index *ix, const gts_objects *q, const float *radii,
             for (int64_t i = 0; i < nq; ++i)
                 GTS_REQUIRE(std::isfinite(hrad[i]) && hrad[i] >= 0.f, GTS_EINVAL, "radius must be finite and >= 0");
             qb.radii = drad.get();
+        }
+        DBuf<double> dlim;
+        if (!knn && ix->metric == GTS_COS && nq > 0) {
+            // the FP64 limits 1 - cos(r) of the range test, on the host
+            std::vector<double> lim(nq);
+            for (int64_t i = 0; i < nq; ++i) {
+                double r = (double)hrad[i];
+                if (r > 3.14159265358979323846) r = 3.14159265358979323846;
+                lim[i] = 1.0 - std::cos(r);
+            }
+            dlim.alloc(nq, st);
+            GTS_CUDA(cudaMemcpyAsync(dlim.get(), lim.data(), nq * 8, cudaMemcpyHostToDevice, st));
+            GTS_CUDA(cudaStreamSynchronize(st));
+            qb.coslim = dlim.get();
         }
         if (opts && opts->seq) {
             copy_small_to_device(opts->seq, nq, q->on_device != 0, dseq, hseq, st);
@@ -544,7 +616,8 @@ gts_status gts_build(const gts_objects *objects, gts_metric metric, int n_pivots
                      const gts_build_opts *opts, gts_index **out) {
     return guarded([&] {
         GTS_REQUIRE(out != nullptr, GTS_EINVAL, "out is NULL");
-        GTS_REQUIRE(metric == GTS_EDIT || metric == GTS_L1 || metric == GTS_L2, GTS_EINVAL, "unknown metric");
+        GTS_REQUIRE(metric == GTS_EDIT || metric == GTS_L1 || metric == GTS_L2 || metric == GTS_COS, GTS_EINVAL,
+                    "unknown metric");
         GTS_REQUIRE(fanout >= 2 && fanout <= kMaxFanout, GTS_EINVAL, "fanout must be in 2 .. 64");
         GTS_REQUIRE(n_pivots >= 0 && n_pivots <= kMaxHeight, GTS_EINVAL, "n_pivots must be in 0 .. 12");
         GTS_REQUIRE(objects != nullptr, GTS_EINVAL, "objects is NULL");
@@ -571,7 +644,15 @@ gts_status gts_build(const gts_objects *objects, gts_metric metric, int n_pivots
             root = 0;
         }
         const int h = tree_height(n, fanout, n_pivots);
-        build_tree(ix->tree, o.v, nullptr, metric, fanout, h, root, ix->stream);
+        if (metric == GTS_COS) {   // an L2 tree over the unit vectors; the raw rows kept for the FP64 keys
+            DBuf<float> unit;
+            unit_vectors(o.v, unit, ix->stream, "objects");
+            Objects uv = o.v;
+            uv.X = unit.get();
+            build_tree(ix->tree, uv, nullptr, GTS_L2, fanout, h, root, ix->stream, o.v.X);
+        } else {
+            build_tree(ix->tree, o.v, nullptr, metric, fanout, h, root, ix->stream);
+        }
         ix->next_id = n;
         ix->n_live = n;
         refresh_loc(ix.get());
@@ -836,7 +917,8 @@ gts_status gts_autotune(gts_index *ix, const gts_objects *queries, const float *
         if (knn) space.push_back({&gts_tuning::knn_phases, {1, 2, 3}});
     }
     if (knn && ix->metric != GTS_EDIT) space.push_back({&gts_tuning::probe_rows, {0, 256, 1024, 4096}});
-    if (ix->metric == GTS_L2 && ix->dim <= 128) space.push_back({&gts_tuning::tc_queries, {128, 96}});
+    if ((ix->metric == GTS_L2 || ix->metric == GTS_COS) && ix->dim <= 128)
+        space.push_back({&gts_tuning::tc_queries, {128, 96}});
     if (ix->metric == GTS_EDIT) {
         space.push_back({&gts_tuning::str_chunk, {64, 128, 256, 512}});
         if (o.precision == GTS_PREC_BF16) space.push_back({&gts_tuning::str_qgram, {0, 32, 64}});

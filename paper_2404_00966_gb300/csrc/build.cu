@@ -269,9 +269,10 @@ void launch_map_str(const Objects &o, const int32_t *perm, const int32_t *pos_no
 }  // namespace
 
 void build_tree(Tree &t, const Objects &objs, const int64_t *d_ids, int metric, int F, int h, int64_t root,
-                cudaStream_t st) {
+                cudaStream_t st, const float *raw_rows) {
     const int64_t n = objs.n;
     t.metric = metric;
+    t.cosine = raw_rows != nullptr;
     t.dim = objs.dim;
     t.F = F;
     t.h = h;
@@ -375,6 +376,11 @@ void build_tree(Tree &t, const Objects &objs, const int64_t *d_ids, int metric, 
         t.X.alloc((size_t)n * objs.dim, st);
         k_gather_rows<<<blocks_for(n * (int64_t)objs.dim), kThreads, 0, st>>>(objs.X, objs.dim, perm.get(), n,
                                                                              t.X.get());
+        if (raw_rows) {   // angular distance: the raw rows in the same (leaf) order
+            t.Xr.alloc((size_t)(n > 0 ? n : 1) * objs.dim, st);
+            k_gather_rows<<<blocks_for(n * (int64_t)objs.dim), kThreads, 0, st>>>(raw_rows, objs.dim, perm.get(), n,
+                                                                                 t.Xr.get());
+        }
     } else {
         DBuf<int64_t> len(n + 1, st);
         t.Soff.alloc(n + 1, st);

@@ -138,6 +138,11 @@ struct TcCache {
 struct Tree {
     int metric = 0, dim = 0, F = 0, h = 0;
     int64_t n = 0;
+    // angular distance (GTS_COS): the tree is an L2 tree over the unit vectors
+    // X = x / |x| (normalised in FP64, rounded to FP32); Xr keeps the raw rows
+    // (leaf order) for the FP64 keys
+    bool cosine = false;
+    DBuf<float> Xr;
     DBuf<float> X;
     DBuf<uint8_t> S;
     DBuf<int64_t> Soff;
@@ -154,7 +159,7 @@ struct Tree {
     bool qg_ready = false;
     size_t device_bytes() const;
     void persist() {   // every buffer the index keeps
-        X.persist(); S.persist(); Soff.persist(); row_id.persist(); table.persist(); row_del.persist();
+        X.persist(); Xr.persist(); S.persist(); Soff.persist(); row_id.persist(); table.persist(); row_del.persist();
         npos.persist(); nsize.persist(); npiv.persist(); nlo.persist(); nhi.persist();
         tc.Xh.persist(); tc.Xl.persist(); tc.xn2.persist(); qg.persist();
     }
@@ -162,7 +167,8 @@ struct Tree {
 
 struct Cache {
     int64_t count = 0, cap = 0;
-    DBuf<float> X;                   // cap * dim
+    DBuf<float> X;                   // cap * dim (unit vectors for GTS_COS)
+    DBuf<float> Xr;                  // GTS_COS: the raw rows
     DBuf<uint8_t> S;                 // bytes
     DBuf<int64_t> Soff;              // cap + 1
     int64_t s_bytes = 0, s_cap = 0;
@@ -213,8 +219,10 @@ struct gts_index {
 namespace gts {
 
 // build.cu
+// raw_rows: angular distance only -- objs holds the unit vectors, raw_rows
+// the caller's rows in the same order (kept in leaf order as Tree::Xr)
 void build_tree(Tree &t, const Objects &objs, const int64_t *d_ids_or_null, int metric, int F, int h,
-                int64_t root_index, cudaStream_t st);
+                int64_t root_index, cudaStream_t st, const float *raw_rows = nullptr);
 int tree_height(int64_t n, int F, int n_pivots);
 uint64_t splitmix64(uint64_t x);
 
@@ -233,7 +241,17 @@ struct QueryBatch {
     int64_t max_k = 0;
     bool count_table_pass = false;   // diagnostics: count the pairs passing the table bound
     bool want_keys = false;          // kNN: also return each answer's FP64 key
+    // GTS_COS: Q holds the unit query vectors, Qr the raw ones; radii are
+    // angles, coslim[i] = 1 - cos(r_i) (FP64, computed on the host)
+    const float *Qr = nullptr;
+    const double *coslim = nullptr;
 };
+
+// GTS_COS: absolute slack (beyond the FP32 relative bound) of every distance
+// between unit vectors rounded to FP32: each rounded vector lies within 2^-24
+// of the exact one, so a chord moves by at most 2^-23; thresholds carry four
+// times that.
+constexpr float kCosAbsSlack = 4.8e-7f;
 
 struct QueryOut {
     DBuf<int64_t> offsets, ids;

@@ -80,6 +80,23 @@ __device__ __forceinline__ double l2sq_fp64_seq(const float *q, const float *x, 
     return s;
 }
 
+// The angular distance's key, 1 - cos: the three sums q.x, |q|^2, |x|^2 in
+// increasing i, every product and sum rounded on its own, c = dot /
+// (sqrt(|q|^2) sqrt(|x|^2)) clamped to [-1, 1] -- the reference operation
+// order.
+__device__ __forceinline__ double cos_key_fp64_seq(const float *q, const float *x, int dim) {
+    double dot = 0.0, nq = 0.0, nx = 0.0;
+    for (int i = 0; i < dim; ++i) {
+        const double a = (double)q[i], b = (double)x[i];
+        dot = __dadd_rn(dot, __dmul_rn(a, b));
+        nq = __dadd_rn(nq, __dmul_rn(a, a));
+        nx = __dadd_rn(nx, __dmul_rn(b, b));
+    }
+    double c = __ddiv_rn(dot, __dmul_rn(__dsqrt_rn(nq), __dsqrt_rn(nx)));
+    c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+    return __dsub_rn(1.0, c);
+}
+
 __device__ __forceinline__ double l1_fp64_seq(const float *q, const float *x, int dim) {
     double s = 0.0;
     for (int i = 0; i < dim; ++i) s = __dadd_rn(s, fabs(__dsub_rn((double)q[i], (double)x[i])));

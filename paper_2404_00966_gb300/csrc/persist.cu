@@ -29,7 +29,8 @@ namespace gts {
 namespace {
 
 constexpr char kMagic[8] = {'G', 'T', 'S', 'I', 'D', 'X', '0', '1'};
-constexpr int32_t kVersion = 1;
+// version 2 adds the string tunings and, for the angular distance, the raw rows
+constexpr int32_t kVersion = 2;
 
 struct File {
     FILE *f = nullptr;
@@ -134,12 +135,14 @@ extern "C" gts_status gts_save(const gts_index *ix, const char *path) {
             w.pod<int64_t>(ix->rebuilds);
             w.pod<uint64_t>(ix->seed);
             const Tuning &tu = ix->tuning;
-            const int32_t tv[6] = {tu.l1_queries, tu.l1_packed, tu.knn_phases, tu.probe_rows, tu.tc_queries, tu.tuned};
+            const int32_t tv[8] = {tu.l1_queries, tu.l1_packed, tu.knn_phases, tu.probe_rows,
+                                   tu.tc_queries, tu.tuned,      tu.str_chunk,  tu.str_qgram};
             w.raw(tv, sizeof(tv));
             w.host(t.lvl_off);
             const int64_t nodes = t.lvl_off.empty() ? 0 : t.lvl_off.back();
             if (ix->dim > 0) {
                 w.dev(t.X, (size_t)t.n * ix->dim);
+                if (t.cosine) w.dev(t.Xr, (size_t)t.n * ix->dim);
             } else {
                 std::vector<int64_t> soff(t.n + 1, 0);
                 if (t.n) GTS_CUDA(cudaMemcpy(soff.data(), t.Soff.get(), (t.n + 1) * 8, cudaMemcpyDeviceToHost));
@@ -159,6 +162,7 @@ extern "C" gts_status gts_save(const gts_index *ix, const char *path) {
             w.pod<int32_t>(c.max_len);
             if (ix->dim > 0) {
                 w.dev(c.X, (size_t)c.count * ix->dim);
+                if (t.cosine) w.dev(c.Xr, (size_t)c.count * ix->dim);
             } else {
                 w.host(c.h_Soff);
                 w.dev(c.S, (size_t)c.s_bytes);
@@ -193,7 +197,8 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         char magic[8];
         r.raw(magic, 8);
         GTS_REQUIRE(std::memcmp(magic, kMagic, 8) == 0, GTS_EINVAL, "not a GTS index file");
-        GTS_REQUIRE(r.pod<int32_t>() == kVersion, GTS_EINVAL, "unsupported index file version");
+        const int32_t version = r.pod<int32_t>();
+        GTS_REQUIRE(version == 1 || version == kVersion, GTS_EINVAL, "unsupported index file version");
         std::unique_ptr<gts_index> ix(new gts_index());
         ix->metric = r.pod<int32_t>();
         ix->dim = r.pod<int32_t>();
@@ -201,7 +206,7 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         ix->n_pivots_req = r.pod<int32_t>();
         const int32_t h = r.pod<int32_t>();
         const int32_t max_len = r.pod<int32_t>();
-        GTS_REQUIRE(ix->metric >= GTS_EDIT && ix->metric <= GTS_L2 && ix->dim >= 0 &&
+        GTS_REQUIRE(ix->metric >= GTS_EDIT && ix->metric <= (version == 1 ? GTS_L2 : GTS_COS) && ix->dim >= 0 &&
                         (ix->metric == GTS_EDIT) == (ix->dim == 0) && ix->F >= 2 && ix->F <= kMaxFanout && h >= 1 &&
                         h <= kMaxHeight && max_len >= 0 && max_len <= kMaxStrLen,
                     GTS_EINVAL, "index file is corrupt (header)");
@@ -217,14 +222,18 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         GTS_REQUIRE(n >= 0 && n < ((int64_t)1 << 31) && ix->next_id >= n && ix->next_id < ((int64_t)1 << 31) &&
                         n_deleted >= 0 && n_deleted <= n,
                     GTS_EINVAL, "index file is corrupt (sizes)");
-        int32_t tv[6];
-        r.raw(tv, sizeof(tv));
+        int32_t tv[8] = {0, 0, 0, 0, 0, 0, 256, 64};
+        r.raw(tv, version == 1 ? 6 * sizeof(int32_t) : sizeof(tv));
         ix->tuning.l1_queries = tv[0];
         ix->tuning.l1_packed = tv[1];
         ix->tuning.knn_phases = tv[2];
         ix->tuning.probe_rows = tv[3];
         ix->tuning.tc_queries = tv[4];
         ix->tuning.tuned = tv[5];
+        ix->tuning.str_chunk = tv[6];
+        ix->tuning.str_qgram = tv[7];
+        GTS_REQUIRE((tv[6] == 64 || tv[6] == 128 || tv[6] == 256 || tv[6] == 512) && (tv[7] == 0 || tv[7] == 32 || tv[7] == 64),
+                    GTS_EINVAL, "index file is corrupt (tuning)");
         // the device work starts here
         ensure_device();
         GTS_CUDA(cudaGetDevice(&ix->device));
@@ -232,7 +241,9 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         if (opts && opts->cache_limit > 0) ix->cache_limit = opts->cache_limit;
         cudaStream_t st = ix->stream;
         Tree &t = ix->tree;
-        t.metric = ix->metric;
+        // the angular distance is an L2 tree over unit vectors with the raw rows beside
+        t.metric = ix->metric == GTS_COS ? GTS_L2 : ix->metric;
+        t.cosine = ix->metric == GTS_COS;
         t.dim = ix->dim;
         t.F = ix->F;
         t.h = h;
@@ -247,6 +258,7 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         };
         if (ix->dim > 0) {
             expect(r.dev(t.X, 1, st), n * ix->dim, "objects");
+            if (t.cosine) expect(r.dev(t.Xr, 1, st), n * ix->dim, "raw objects");
         } else {
             std::vector<int64_t> soff = r.host<int64_t>();
             expect((int64_t)soff.size(), n + 1, "string offsets");
@@ -269,6 +281,7 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         GTS_REQUIRE(c.count >= 0 && c.count <= ix->next_id, GTS_EINVAL, "index file is corrupt (cache)");
         if (ix->dim > 0) {
             expect(r.dev(c.X, 1, st), c.count * ix->dim, "cache objects");
+            if (t.cosine) expect(r.dev(c.Xr, 1, st), c.count * ix->dim, "raw cache objects");
         } else {
             c.h_Soff = r.host<int64_t>();
             GTS_REQUIRE((int64_t)c.h_Soff.size() == (c.count > 0 ? c.count + 1 : (int64_t)c.h_Soff.size()),
@@ -286,6 +299,7 @@ extern "C" gts_status gts_load(const char *path, const gts_build_opts *opts, gts
         expect(r.dev(c.del, 1, st), c.count, "cache delete marks");
         c.cap = c.count;
         c.X.persist();
+        c.Xr.persist();
         c.S.persist();
         c.id.persist();
         c.ins.persist();

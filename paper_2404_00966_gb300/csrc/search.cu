@@ -70,6 +70,12 @@ struct Dev {
     const uint8_t *qg;    // strings: hashed 3-gram counts of the tree rows [n, 64]
     const uint8_t *qgq;   // the same for the batch's queries [nq, 64]
     float epsc;    // pruning slack factor (0 for edit distance)
+    float absf;    // absolute floor of every FP32 distance bound (angular distance: the unit-vector rounding)
+    // angular distance: the kernels work on unit vectors (X, Q, cX); the FP64
+    // keys come from the raw rows and queries
+    int cosine;
+    const float *Xr, *cXr, *Qr;
+    const double *coslim;   // range: 1 - cos(r) per query
 };
 
 __device__ __forceinline__ const float *vrow(const Dev &d, int64_t row) {
@@ -80,6 +86,28 @@ __device__ __forceinline__ bool row_visible(const Dev &d, int64_t row, int64_t s
     const int64_t c = row - d.n;
     return d.cins[c] < s && s < d.cdel[c];
 }
+__device__ __forceinline__ const float *vrow_raw(const Dev &d, int64_t row) {
+    return row < d.n ? d.Xr + row * d.dim : d.cXr + (row - d.n) * d.dim;
+}
+// The FP64 key of (query, row) in the reference operation order: L2 the
+// squared sum, L1 the sum, angular distance 1 - cos on the raw vectors.
+template <bool L2>
+__device__ __forceinline__ double fp64_key(const Dev &d, int64_t q, int64_t row) {
+    if (d.cosine) return cos_key_fp64_seq(d.Qr + q * d.dim, vrow_raw(d, row), d.dim);
+    const float *qv = d.Q + q * d.dim, *xv = vrow(d, row);
+    return L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+}
+// the range limit on the FP64 key and the reported distance of a key
+template <bool L2>
+__device__ __forceinline__ double fp64_limit(const Dev &d, int64_t q, float r) {
+    if (d.cosine) return d.coslim[q];
+    return L2 ? __dmul_rn((double)r, (double)r) : (double)r;
+}
+__device__ __forceinline__ float key_distance(const Dev &d, bool l2, double key) {
+    if (d.cosine) return __double2float_rn(acos(__dsub_rn(1.0, key)));
+    return __double2float_rn(l2 ? __dsqrt_rn(key) : key);
+}
+
 __device__ __forceinline__ int64_t row_oid(const Dev &d, int64_t row) {
     return row < d.n ? d.row_id[row] : d.cid[row - d.n];
 }
@@ -118,9 +146,19 @@ __global__ void k_root_entries(int32_t *eq, int32_t *enode, int64_t nq) {
         enode[i] = 0;
     }
 }
-__global__ void k_thresholds(const float *radii, int64_t nq, bool floor_r, float *thr) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
-        thr[i] = floor_r ? floorf(radii[i]) : radii[i];
+// Range thresholds in the kernels' distance: the radius (edit distance: its
+// floor); angular distance: the chord sqrt(2 (1 - cos r)) of the FP64 limit,
+// rounded up, plus the unit-vector slack.
+__global__ void k_thresholds(const float *radii, int64_t nq, bool floor_r, const double *coslim, float absf,
+                             float *thr) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        if (coslim) {
+            const double lim = coslim[i];
+            thr[i] = lim < 0.0 ? -1.f : __double2float_ru(__dsqrt_ru(__dmul_ru(2.0, lim))) + absf;
+        } else {
+            thr[i] = floor_r ? floorf(radii[i]) : radii[i];
+        }
+    }
 }
 __global__ void k_k_to_i64(const int32_t *k, int64_t nq, int64_t *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
@@ -335,7 +373,7 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
         int64_t id = 0;
         if (e < b) {
             const float dv = path[e * d.h + l];
-            ub = d.rel > 0.f ? (double)dv * up + (double)kAbsFloor : (double)dv;
+            ub = d.rel > 0.f ? (double)dv * up + (double)d.absf : (double)dv;
             if (!full || ub <= k_d) {   // the bound test before the pivot's delete mark
                 const int32_t prow = d.npiv[lvl_base + enode[e]];
                 if (row_visible(d, prow, s)) {
@@ -417,7 +455,7 @@ __device__ __forceinline__ void probe_rows(const Dev &d, const float *qv, int64_
             if (d.row_del[row] > s) {
                 const float sq = lane_vec_dist<L2>(qv, d.X + row * d.dim, d.dim);
                 const float dv = L2 ? sqrtf(sq) : sq;
-                ub = (double)dv * up + (double)kAbsFloor;
+                ub = (double)dv * up + (double)d.absf;
                 id = d.row_id[row];
                 cand = !full || ub < k_d || (ub == k_d && id < k_i);
             }
@@ -461,7 +499,7 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
         const int32_t prow = d.npiv[lo_off.v[0]];
         const float sq = warp_vec_dist<L2>(qv, d.X + (int64_t)prow * d.dim, d.dim, lane);
         const float dq = L2 ? sqrtf(sq) : sq;
-        if (d.row_del[prow] > s) L.insert((double)dq * up + (double)kAbsFloor, d.row_id[prow]);
+        if (d.row_del[prow] > s) L.insert((double)dq * up + (double)d.absf, d.row_id[prow]);
     }
     int64_t node = 0;
     if (d.h == 1) {   // one pivot level: the root's own rows
@@ -497,7 +535,7 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
             }
             // the visible pivots into the threshold list (a register copy of
             // its K-th bound skips the pivots that cannot enter it)
-            const double ub = (double)dq * up + (double)kAbsFloor;
+            const double ub = (double)dq * up + (double)d.absf;
             const bool full = L.n >= K;
             const double kth = full ? L.kd() : 0.0;
             unsigned bal = __ballot_sync(0xffffffffu, vis && (!full || ub <= kth));
@@ -989,23 +1027,20 @@ __global__ void k_verify_vec(Dev d, const int32_t *__restrict__ cq, const int32_
         const int32_t q = gq;
         const float d32 = my_d32;
         const float r = thr_q[q];
-        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
-        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        const float hi = d32 * (1.f + 2.f * d.rel) + d.absf;
+        const float lo = d32 * (1.f - 2.f * d.rel) - d.absf;
         if (KNN) {
             cdist[c] = d32;
             keep[c] = lo <= r ? 1 : 0;
-        } else if (hi < r * (1.f - 1e-9f)) {
+        } else if (!d.cosine && hi < r * (1.f - 1e-9f)) {   // (angular: the FP64 key decides every kept pair)
             keep[c] = 1;
             cdist[c] = d32;
         } else if (lo > r * (1.f + 1e-9f)) {
             keep[c] = 0;
         } else {
-            const float *pqv = d.Q + (int64_t)q * d.dim;
-            const float *xv = vrow(d, (int64_t)grow);
-            const double key = L2 ? l2sq_fp64_seq(pqv, xv, d.dim) : l1_fp64_seq(pqv, xv, d.dim);
-            const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
-            keep[c] = key <= lim ? 1 : 0;
-            cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
+            const double key = fp64_key<L2>(d, q, (int64_t)grow);
+            keep[c] = key <= fp64_limit<L2>(d, q, r) ? 1 : 0;
+            cdist[c] = key_distance(d, L2, key);
             atomicAdd(rechecks, 1ull);
         }
         }
@@ -1038,21 +1073,20 @@ __global__ void k_verify_lowdim(Dev d, const int32_t *__restrict__ cq, const int
         }
         const float d32 = L2 ? sqrtf(sum) : sum;
         const float r = thr_q[q];
-        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
-        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        const float hi = d32 * (1.f + 2.f * d.rel) + d.absf;
+        const float lo = d32 * (1.f - 2.f * d.rel) - d.absf;
         if (KNN) {
             cdist[c] = d32;
             keep[c] = lo <= r ? 1 : 0;
-        } else if (hi < r * (1.f - 1e-9f)) {
+        } else if (!d.cosine && hi < r * (1.f - 1e-9f)) {   // (angular: the FP64 key decides every kept pair)
             keep[c] = 1;
             cdist[c] = d32;
         } else if (lo > r * (1.f + 1e-9f)) {
             keep[c] = 0;
         } else {
-            const double key = L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
-            const double lim = L2 ? __dmul_rn((double)r, (double)r) : (double)r;
-            keep[c] = key <= lim ? 1 : 0;
-            cdist[c] = __double2float_rn(L2 ? __dsqrt_rn(key) : key);
+            const double key = fp64_key<L2>(d, q, row);
+            keep[c] = key <= fp64_limit<L2>(d, q, r) ? 1 : 0;
+            cdist[c] = key_distance(d, L2, key);
             atomicAdd(rechecks, 1ull);
         }
     }
@@ -1292,11 +1326,15 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
             auto get_hi = [&](int64_t i, uint64_t &v) -> bool {
                 float x;
                 if (i < nb) {
-                    const double ex = METRIC == GTS_L2 ? __dsqrt_rn(BD[i]) : BD[i];
-                    x = __double2float_ru(ex);
+                    // the answer's FP64 key as an upper bound in the kernels' distance
+                    // (angular: the chord sqrt(2 key) of the exact unit vectors, plus
+                    // the unit-vector rounding)
+                    const double ex = d.cosine ? __dsqrt_ru(__dmul_ru(2.0, BD[i]))
+                                               : (METRIC == GTS_L2 ? __dsqrt_rn(BD[i]) : BD[i]);
+                    x = __double2float_ru(ex) + (d.cosine ? d.absf : 0.f);
                 } else {
                     const float dv = cdist[a + i - nb];
-                    x = dv * up + kAbsFloor;
+                    x = dv * up + d.absf;
                 }
                 v = __float_as_uint(x);
                 return true;
@@ -1307,7 +1345,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
         for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
             const float dv = cdist[a + i];
             ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
-            if (dv * dn - kAbsFloor <= Uf && dv != __int_as_float(0x7f800000))
+            if (dv * dn - d.absf <= Uf && dv != __int_as_float(0x7f800000))
                 rlist[atomicAdd(rcount, 1ull)] = a + i;   // its FP64 key comes next
         }
         return;
@@ -1414,8 +1452,8 @@ __global__ void k_decide_range_l1(Dev d, const int32_t *__restrict__ cq, const i
         const int32_t q = cq[c];
         const float d32 = cdist[c];
         const float r = thr_q[q];
-        const float hi = d32 * (1.f + 2.f * d.rel) + kAbsFloor;
-        const float lo = d32 * (1.f - 2.f * d.rel) - kAbsFloor;
+        const float hi = d32 * (1.f + 2.f * d.rel) + d.absf;
+        const float lo = d32 * (1.f - 2.f * d.rel) - d.absf;
         if (hi < r * (1.f - 1e-9f)) {
             keep[c] = 1;
         } else if (lo > r * (1.f + 1e-9f)) {
@@ -1442,9 +1480,7 @@ __global__ void k_recheck_keys(Dev d, const int32_t *__restrict__ cq, const int3
     const int64_t n = (int64_t)*rcount;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = rlist[i];
-        const float *qv = d.Q + (int64_t)cq[c] * d.dim;
-        const float *xv = vrow(d, crow[c]);
-        ckey[c] = METRIC == GTS_L2 ? l2sq_fp64_seq(qv, xv, d.dim) : l1_fp64_seq(qv, xv, d.dim);
+        ckey[c] = fp64_key<METRIC == GTS_L2>(d, cq[c], crow[c]);
     }
 }
 
@@ -1524,7 +1560,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                 kth = L.kd();
                 kthid = L.kid();
                 // one float step above the quotient absorbs its FP64 rounding
-                fthr = nextafterf(__double2float_ru((kth - (double)kAbsFloor) / up), __int_as_float(0x7f800000));
+                fthr = nextafterf(__double2float_ru((kth - (double)d.absf) / up), __int_as_float(0x7f800000));
             }
         };
         refresh();
@@ -1546,7 +1582,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                 double ub = 0.0;
                 int64_t id = 0;
                 if (mem[u] && dv[u] <= fthr) {
-                    ub = (double)dv[u] * up + (double)kAbsFloor;
+                    ub = (double)dv[u] * up + (double)d.absf;
                     // the bound test first: most pivots fail it, and then the
                     // pivot's delete mark and id are never read
                     if ((L.n < K) || ub <= kth) {
@@ -1769,14 +1805,14 @@ __global__ void k_knn_counts(const int32_t *bn, int64_t nq, int64_t *counts) {
 
 __global__ void k_knn_emit(const int64_t *__restrict__ offsets, const int64_t *__restrict__ koff,
                            const double *__restrict__ bd, const int64_t *__restrict__ bi, const int32_t *__restrict__ bn,
-                           int64_t nq, bool l2, int64_t *__restrict__ ids, float *__restrict__ dist,
+                           int64_t nq, bool l2, bool cosine, int64_t *__restrict__ ids, float *__restrict__ dist,
                            double *__restrict__ keys) {
     const int64_t q = blockIdx.x;
     if (q >= nq) return;
     for (int i = threadIdx.x; i < bn[q]; i += blockDim.x) {
         const double key = bd[koff[q] + i];
         ids[offsets[q] + i] = bi[koff[q] + i];
-        dist[offsets[q] + i] = __double2float_rn(l2 ? __dsqrt_rn(key) : key);
+        dist[offsets[q] + i] = __double2float_rn(cosine ? acos(__dsub_rn(1.0, key)) : (l2 ? __dsqrt_rn(key) : key));
         if (keys) keys[offsets[q] + i] = key;
     }
 }
@@ -2505,7 +2541,9 @@ struct Runner {
         ScanQuery sq;
         sq.epsc = d.epsc;
         sq.any_deleted = tq.any_deleted;
-        sq.fused_range = !knn;   // range: decide the pairs in the scan (low dimension)
+        // range: decide the pairs in the scan (low dimension; the angular
+        // distance takes its FP64 key for every pair, so not there)
+        sq.fused_range = !knn && !d.cosine;
         sq.Q = d.Q;
         sq.rel = d.rel;
         ScanOut so;
@@ -2936,6 +2974,14 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         d.qgq = qgq.get();
     }
     d.epsc = t.dim > 0 ? 4.f * d.rel : 0.f;
+    // angular distance: the unit vectors' chords stand within kCosAbsSlack of
+    // the exact unit vectors'; a bound crosses between the two twice at most
+    d.cosine = t.cosine ? 1 : 0;
+    d.absf = t.cosine ? 2.f * kCosAbsSlack : kAbsFloor;
+    d.Xr = t.Xr.get();
+    d.cXr = c.Xr.get();
+    d.Qr = qb.Qr;
+    d.coslim = qb.coslim;
     DBuf<int64_t> qseq(nq, st);
     R.clk.begin(GTS_STAGE_OTHER);
     if (qb.seq)
@@ -2973,7 +3019,8 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.clk.end();
     } else {
         R.clk.begin(GTS_STAGE_OTHER);
-        k_thresholds<<<nblocks(nq, kT), kT, 0, st>>>(qb.radii, nq, t.dim == 0, R.thr.get());
+        k_thresholds<<<nblocks(nq, kT), kT, 0, st>>>(qb.radii, nq, t.dim == 0, t.cosine ? qb.coslim : nullptr,
+                                                      d.absf, R.thr.get());
         R.clk.end();
     }
     check_launch("query setup");
@@ -3022,7 +3069,8 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         R.clk.begin(GTS_STAGE_OTHER);
         k_knn_emit<<<(unsigned)(nq > 0 ? nq : 1), 128, 0, st>>>(out.offsets.get(), R.koff.get(), R.bd.get(),
                                                                 R.bi.get(), R.bn.get(), nq, t.metric == GTS_L2,
-                                                                out.ids.get(), out.dist.get(), out.key.get());
+                                                                t.cosine, out.ids.get(), out.dist.get(),
+                                                                out.key.get());
         R.clk.end();
     } else {
         int64_t Rt = 0;

@@ -74,6 +74,7 @@ struct Done {
 // list, Eq. 1 numbering) for the admission projection.
 struct TopLevels {
     int levels = 0, F = 0, dim = 0, metric = 0;
+    bool cosine = false;                   // angular distance: pivots are unit vectors, distances chords
     std::vector<int64_t> lvl_off;          // first node of levels 0 .. levels
     std::vector<float> pv;                 // pivot vectors of levels < levels, [node, dim]
     std::vector<std::string> ps;           // pivot strings
@@ -117,6 +118,18 @@ constexpr int kMaxEvals = 64;
 
 int64_t project_rows(const TopLevels &t, const uint8_t *q, int64_t len, int32_t kind, double param) {
     if (t.levels == 0) return t.n_live + t.cache_rows;
+    std::vector<float> unit;
+    if (t.cosine) {   // the descent runs on chords between unit vectors, as the tree does
+        const float *qq = reinterpret_cast<const float *>(q);
+        double s = 0.0;
+        for (int i = 0; i < t.dim; ++i) s += (double)qq[i] * (double)qq[i];
+        if (!(s > 0.0)) return t.n_live + t.cache_rows;
+        const double inv = 1.0 / std::sqrt(s);
+        unit.resize(t.dim);
+        for (int i = 0; i < t.dim; ++i) unit[i] = (float)((double)qq[i] * inv);
+        q = reinterpret_cast<const uint8_t *>(unit.data());
+        if (kind == 0) param = std::sqrt(2.0 * (1.0 - std::cos(std::min(param, 3.14159265358979323846)))) + 1e-6;
+    }
     std::vector<int64_t> frontier{0}, next;   // node indices within the current level
     std::vector<double> live;                 // exact distances to the visible pivots evaluated so far
     std::vector<double> dnode;
@@ -297,6 +310,7 @@ void snapshot_top_levels(gts_index *ix, TopLevels &t) {
     t.F = tr.F;
     t.dim = tr.dim;
     t.metric = tr.metric;
+    t.cosine = tr.cosine;
     t.cache_rows = ix->cache.count;
     t.n_live = ix->n_live;
     if (tr.n == 0 || tr.h < 1) return;
@@ -372,8 +386,10 @@ gts_status gts_serve_start(gts_index *ix, const gts_serve_opts *opts, gts_server
         if (sv->opts.memory_budget <= 0) sv->opts.memory_budget = sv->opts.result_budget / sv->opts.n_streams;
         GTS_CUDA(cudaSetDevice(ix->device));
         // warm the tensor-core copy before any worker runs (it is built lazily)
-        if (sv->opts.precision == GTS_PREC_BF16 && ix->metric == GTS_L2 && ix->tree.n > 0) {
+        if (sv->opts.precision == GTS_PREC_BF16 && (ix->metric == GTS_L2 || ix->metric == GTS_COS) &&
+            ix->tree.n > 0) {
             std::vector<float> q((size_t)ix->dim, 0.f);
+            q[0] = 1.f;   // (the angular distance has no zero vector)
             gts_objects qo;
             std::memset(&qo, 0, sizeof(qo));
             qo.n = 1;
