@@ -15,11 +15,13 @@ threshold, the list-table bound, verification and selection, all on the GPU.
   events around every launch of each stage (on the query stream), plus one
   untimed call that counts the (query, row) pairs passing the table lower
   bound (C_q); the tile stage's algorithmic work is 2 D C_q flops.
-* `other_workloads` (single-GPU runs): the other four configurations, each
+* `other_workloads` (single-GPU runs): the other configurations, each
   timed on its own with its build and rebuild times -- words_10k_r2 and
   dna_1M_r8 (edit distance, range), zipf2d_10M (10^7 2-D points, range
   queries with stream inserts / deletes and a batch update inside the timed
-  region), uniform_2Mx256_l1 (served Poisson arrivals, p50 / p99).
+  region), wordvec_200kx300_cos (angular-distance kNN over 200,000
+  word-vector-like rows of dim 300), uniform_2Mx256_l1 (served Poisson
+  arrivals, p50 / p99).
 
 The index (X 512 MB, table 16 MB) is larger than L2 (129 MB), so no explicit
 flush runs between steps.
@@ -686,6 +688,82 @@ def bench_serving(args):
     return out
 
 
+def bench_wordvec(args):
+    """wordvec_200000x300_cos_knn10: angular-distance kNN over word-vector-like
+    data (the Vector data's shape), BF16 tiles on the unit vectors and the
+    FP64 key 1 - cos of every answer."""
+    import torch
+    import paper_2404_00966_gb300 as gts
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    stream = torch.cuda.current_stream()
+    prec = args.precision
+    wl = synth.word_vectors() if args.scale >= 1.0 else synth.word_vectors(n=max(20_000, int(200_000 * args.scale)))
+    X, Q, k = wl.objects, wl.queries, int(wl.k[0])
+    nq, dim = Q.shape
+    Xd = torch.from_numpy(X).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    Kd = torch.from_numpy(wl.k).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = gts.Index.build(Xd, "cos", fanout=wl.fanout, root_pivot=0)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix.rebuild()
+    torch.cuda.synchronize()
+    rebuild_s = time.perf_counter() - t0
+    tuning = ix.autotune(Qd, k=wl.k, precision=prec, reps=2) if not args.no_tune else None
+
+    def step(timing=False, count=False):
+        r = ix.knn(Qd, Kd, precision=prec, result_on_device=True, timing=timing, count_table_pass=count)
+        st = r.stats
+        r.free()
+        return st
+    ms, launches, stats0, clocks = _timed_steps(step, args.other_steps, args.warmup, stream, local)
+    stage_ms, stage_launch, _ = stage_pass(step, args.other_steps, stream)
+    cq = step(count=True)["table_pass"]
+    dom = max(stage_ms, key=lambda s_: stage_ms[s_])
+    out = {"metric": "kNN queries/s at oracle-exact results (angular distance, k=10)",
+           "value": round(nq * args.other_steps / (ms / 1e3), 1), "unit": "queries/s", "steps": args.other_steps,
+           "warmup": args.warmup, "ms_per_step": round(ms / args.other_steps, 4),
+           "dtype": "bf16+f64" if prec == "bf16" else "f32+f64",
+           "config": {"workload": wl.name, "n": int(X.shape[0]), "dim": int(dim), "nq": int(nq), "k": k,
+                      "fanout": wl.fanout, "h": ix.info()["h"], "precision": prec, "tuning": tuning},
+           "build_s": round(build_s, 3), "rebuild_s": round(rebuild_s, 3),
+           "gpu_launches": int(launches), "stage_ms_per_step": {kk: round(v, 4) for kk, v in stage_ms.items()},
+           "counters_per_step": {**{kk: v for kk, v in stats0.items() if not isinstance(v, dict)},
+                                 "table_pass": int(cq)},
+           "clocks": clocks}
+    if dom == "tile" and prec == "bf16" and stage_ms[dom] > 0:
+        tf, tsrc = tensor_peak()
+        sec = stage_ms[dom] / 1e3
+        ach = cq * 2 * dim / sec / 1e12
+        cov = stats0["tile_pairs"] * 2 * dim / sec / 1e12
+        out["roofline"] = {"bound": "tensor", "kernel": "k_tile_l2_tc (stage tile)", "achieved": round(ach, 2),
+                           "peak": tf, "unit": "TFLOP/s", "frac": round(ach / tf, 5), "peak_source": tsrc,
+                           "traffic": None, "ms_per_step": round(stage_ms[dom], 4),
+                           "covered_tflops": round(cov, 1), "executed_tflops": round(3 * cov, 1)}
+    else:
+        out["roofline"] = {"bound": "latency", "kernel": dom, "achieved": None, "peak": None, "frac": None,
+                           "traffic": None, "ms_per_step": round(stage_ms[dom], 4)}
+    ix.close()
+    del Xd, Qd
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.knn_query("cos", X, Q[:8], 10)
+        per_q = (time.perf_counter() - t0) / 8
+        m = int(max(8, min(nq, args.other_cpu_seconds / max(per_q, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.knn_query("cos", X, Q[:m], 10)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(m / dt, 3), "unit": "queries/s", "cores": oracle.threads(),
+                               "kind": "oracle", "sample": f"{m} queries, brute-force FP64 angular kNN"}
+    return out
+
+
 def run_others(args):
     """Each remaining configuration timed on its own; a failure is recorded
     in its entry and does not stop the others."""
@@ -694,6 +772,7 @@ def run_others(args):
     for name, fn in (("words_10k_r2", lambda: bench_strings("words", args)),
                      ("dna_1M_r8", lambda: bench_strings("dna", args)),
                      ("zipf2d_10M", lambda: bench_zipf2d(args)),
+                     ("wordvec_200kx300_cos", lambda: bench_wordvec(args)),
                      ("uniform_2Mx256_l1_serving", lambda: bench_serving(args))):
         t0 = time.perf_counter()
         try:
@@ -715,6 +794,8 @@ def run_config(args):
         out = bench_strings(args.workload, args)
     elif args.workload == "zipf2d":
         out = bench_zipf2d(args)
+    elif args.workload == "wordvec":
+        out = bench_wordvec(args)
     else:
         out = bench_serving(args)
     out.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"})
@@ -768,7 +849,7 @@ def main():
     ap.add_argument("--requests", type=int, default=20_000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50_000.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=1024, help="serving: requests per device batch")
-    ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "serving"],
+    ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "wordvec", "serving"],
                     help="gauss (the headline line); the others time the remaining configurations alone")
     ap.add_argument("--no-others", action="store_true", help="headline only: skip the other workloads")
     ap.add_argument("--other-steps", type=int, default=5, help="timed steps of the other workloads")

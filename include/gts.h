@@ -67,7 +67,9 @@ typedef enum { GTS_EDIT = 0, GTS_L1 = 1, GTS_L2 = 2, GTS_COS = 3 } gts_metric;
  *                 FP32 distance lies within a proven error bound of the radius
  *                 or of the running k-th distance.
  *  GTS_PREC_BF16: BF16 tensor-core distance tiles with FP32 accumulation and the
- *                 same FP64 recheck against a (wider) proven BF16 bound.
+ *                 same FP64 recheck against a (wider) proven BF16 bound
+ *                 (17 <= dim <= 448; vectors of at most 16 dimensions take the
+ *                 node-major table scan, wider ones the FP32 path).
  * L1 has no product form for the tensor cores: with GTS_PREC_BF16 it runs the
  * same node-major tiles on the CUDA cores in FP32 (the arithmetic and the FP64
  * recheck of GTS_PREC_FP32, batched by node instead of by candidate); this

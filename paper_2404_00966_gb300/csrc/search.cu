@@ -1296,12 +1296,36 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 // in rlist and get it from k_recheck_keys (a thread per candidate: the
 // sequential FP64 sums then keep every lane of the FP64 pipe busy).  PASS 1:
 // step B (and, for edit distance, the keys from the exact distances).
+// Tensor-core tile estimates to distance intervals: from the tile's q.x~,
+// d~^2 = (|q|^2 + |x|^2) - 2 q.x~ (the tile's own operation order) is within
+// E = cE1 |q||x| + cE2 (|q| + |x|)^2 of d^2 (the tile kernel's bound, taken
+// here with 2 cE2), so d lies in [sqrt(d~^2 - E), sqrt(d~^2 + E)], each end
+// rounded outwards.  lo overwrites the input.
+__global__ void k_tile_intervals(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow, int64_t C,
+                                 const float *__restrict__ qn2, const float *__restrict__ xn2, float cE1, float cE2,
+                                 float *__restrict__ qxlo, float *__restrict__ hi) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const float q2 = qn2[cq[c]], x2 = xn2[crow[c]];
+        const float qn = __fmul_ru(__fsqrt_ru(q2), 1.f + 1e-6f);
+        const float xn = __fmul_ru(__fsqrt_ru(x2), 1.f + 1e-6f);
+        const float sn = __fadd_ru(qn, xn);
+        const float E = __fadd_ru(__fmul_ru(cE1, __fmul_ru(qn, xn)), __fmul_ru(2.f * cE2, __fmul_ru(sn, sn)));
+        const float v = fmaf(-2.f, qxlo[c], q2 + x2);
+        hi[c] = __fsqrt_ru(__fadd_ru(v, E));
+        const float l = __fsub_rd(v, E);
+        qxlo[c] = l > 0.f ? __fsqrt_rd(l) : 0.f;
+    }
+}
+
+// With chi (tensor-core tiles' kNN pairs, no FP32 verification): candidate
+// i's distance lies in [cdist[i], chi[i]] instead of within the FP32 band of
+// cdist[i].
 template <int METRIC, int PASS>
 __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
                             const float *__restrict__ cdist, int64_t C, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
                             int32_t *__restrict__ bn, double *__restrict__ ckey, int64_t *__restrict__ rlist,
-                            unsigned long long *__restrict__ rcount) {
+                            unsigned long long *__restrict__ rcount, const float *__restrict__ chi) {
     __shared__ unsigned hist[256];
     __shared__ int64_t sh[4];
     __shared__ int64_t red[kWarpsPerBlock];
@@ -1333,8 +1357,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
                                                : (METRIC == GTS_L2 ? __dsqrt_rn(BD[i]) : BD[i]);
                     x = __double2float_ru(ex) + (d.cosine ? d.absf : 0.f);
                 } else {
-                    const float dv = cdist[a + i - nb];
-                    x = dv * up + d.absf;
+                    x = chi ? chi[a + i - nb] + d.absf : cdist[a + i - nb] * up + d.absf;
                 }
                 v = __float_as_uint(x);
                 return true;
@@ -1345,7 +1368,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
         for (int64_t i = threadIdx.x; i < M; i += blockDim.x) {
             const float dv = cdist[a + i];
             ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
-            if (dv * dn - d.absf <= Uf && dv != __int_as_float(0x7f800000))
+            if ((chi ? dv : dv * dn) - d.absf <= Uf && dv != __int_as_float(0x7f800000))
                 rlist[atomicAdd(rcount, 1ull)] = a + i;   // its FP64 key comes next
         }
         return;
@@ -2478,16 +2501,50 @@ struct Runner {
         // pairs; a larger output triggers one relaunch with the exact size
         const int64_t per_q = ix->tc_pairs_hint[knn ? 1 : 0].load();
         const int64_t hint = std::max<int64_t>(1 << 20, 2 * per_q * (qb.nq > 0 ? qb.nq : 1) / 1024);
+        // kNN: the tiles also give each kept pair's q.x~, whose proven distance
+        // interval stands in for the FP32 distance (the answers' distances
+        // come from their FP64 keys), so the pairs skip the FP32 verification
+        DBuf<float> od2;
         clk.begin(GTS_STAGE_TILE);
-        const int64_t C = tc_run(ix->tree, ix->tree.tc, tq, rg, oq, orow, hint, &nl, st);
+        const int64_t C = tc_run(ix->tree, ix->tree.tc, tq, rg, oq, orow, hint, &nl, st, knn ? &od2 : nullptr);
         clk.end();
         if (rg.n_items > 0 && qb.nq > 0)
             ix->tc_pairs_hint[knn ? 1 : 0].store(std::max<int64_t>(per_q, C * 1024 / qb.nq));
         ++st_groups;
         if (C == 0) return;
+        if (knn) {
+            st_cands += C;
+            knn_from_intervals(oq, orow, od2, C, tq);
+            return;
+        }
         // verified in the tiles' node-major order (consecutive pairs share
-        // their object row); kNN pairs kept are put in query order afterwards
+        // their object row); range pairs kept are then sorted by query and id
         verify_and_collect(oq, orow, C, /*query_major=*/false);
+    }
+
+    // kNN pairs of the tensor-core tiles with their estimates d~^2: put them
+    // in query order, turn each estimate into its distance interval, and
+    // merge (FP64 keys for the candidates whose interval reaches the k-th
+    // upper bound)
+    void knn_from_intervals(DBuf<int32_t> &cq, DBuf<int32_t> &crow, DBuf<float> &cd2, int64_t C, const TcQuery &tq) {
+        DBuf<uint64_t> v1(C, st), v2(C, st);
+        DBuf<int32_t> q3(C, st), r3(C, st);
+        DBuf<float> d3(C, st), hi(C, st);
+        int qbits = 1;
+        while (((int64_t)1 << qbits) < qb.nq) ++qbits;
+        size_t tb = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, tb, cq.get(), q3.get(), v1.get(), v2.get(), C, 0, qbits, st);
+        DBuf<uint8_t> tmp(tb ? tb : 1, st);
+        clk.begin(GTS_STAGE_OTHER, 4);
+        k_pack_row_dist<<<cap(nblocks(C, kT)), kT, 0, st>>>(crow.get(), cd2.get(), C, v1.get());
+        GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, cq.get(), q3.get(), v1.get(), v2.get(), C, 0, qbits,
+                                                 st));
+        k_unpack_row_dist<<<cap(nblocks(C, kT)), kT, 0, st>>>(v2.get(), C, r3.get(), d3.get());
+        k_tile_intervals<<<cap(nblocks(C, kT)), kT, 0, st>>>(q3.get(), r3.get(), C, tq.qn2, ix->tree.tc.xn2.get(),
+                                                            tq.cE1, tq.cE2, d3.get(), hi.get());
+        clk.end();
+        check_launch("tile intervals");
+        merge_knn(q3, r3, d3, C, hi.get());
     }
 
     void tc_leaf(Level &L, int64_t e0, int64_t e1, DBuf<uint64_t> &mask, DBuf<int32_t> *ncount = nullptr) {
@@ -2833,13 +2890,15 @@ struct Runner {
 
     // merge R query-major (query, row, FP32 distance) candidates into the
     // per-query answers (exact (key, id) selection with FP64 keys)
-    void merge_knn(DBuf<int32_t> &kq2, DBuf<int32_t> &krow2, DBuf<float> &kd2, int64_t R) {
+    void merge_knn(DBuf<int32_t> &kq2, DBuf<int32_t> &krow2, DBuf<float> &kd2, int64_t R,
+                   const float *chi = nullptr) {
         DBuf<double> ckey(R, st);
         const unsigned grid = (unsigned)qb.nq;
         clk.begin(GTS_STAGE_SELECT, 4);
         if (d.metric == GTS_EDIT) {
             k_knn_merge<GTS_EDIT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
-                                                          bd.get(), bi.get(), bn.get(), ckey.get(), nullptr, nullptr);
+                                                          bd.get(), bi.get(), bn.get(), ckey.get(), nullptr, nullptr,
+                                                          nullptr);
         } else {
             // step A lists the candidates that need an FP64 key, a thread per
             // candidate computes it, step B selects; the list's length is
@@ -2850,11 +2909,13 @@ struct Runner {
 #define GTS_MERGE(MT)                                                                                            \
     do {                                                                                                         \
         k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
-                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get()); \
+                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get(),  \
+                                                chi);                                                             \
         k_recheck_keys<MT><<<cap(nblocks(R, kT)), kT, 0, st>>>(d, kq2.get(), krow2.get(), rlist.get(), rc.get(), \
                                                               ckey.get());                                     \
         k_knn_merge<MT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
-                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get()); \
+                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get(),  \
+                                                chi);                                                             \
         k_add_u64<<<1, 1, 0, st>>>(rc.get(), counters.get());                                                   \
     } while (0)
             if (d.metric == GTS_L2) GTS_MERGE(GTS_L2);

@@ -47,14 +47,28 @@ namespace {
 constexpr int kRows = 128;     // MMA M: rows of one node block
 // MMA N (queries per chunk) NQ, the number SB of query-row buffers (B, hi and
 // lo) and the number SM of chunk slots (records, path distances and one FP32
-// TMEM accumulator of 128 lanes x NQ columns each) are template parameters:
-// up to 128 columns 128 or 96 queries (the tuning chooses; 128 by default), up
-// to 192 columns 64, up to 256 columns 32; SB = 2 and SM = 4 (3 for 128
-// queries with deep trees), so that the node block (A, hi and lo), the B
-// buffers and the slots fit in shared memory.  A B buffer is released when the
-// MMAs that read it are done, a slot when the epilogue has tested its chunk:
-// the producers restage B while the epilogue still works on older chunks.
-inline int nq_for(int dim_p, int pref) { return dim_p <= 128 ? (pref == 96 ? 96 : 128) : dim_p <= 192 ? 64 : 32; }
+// TMEM accumulator of 128 lanes x NQ columns each) are template parameters,
+// chosen so that the node block (dim_p TMEM columns, hi and lo) and the SM
+// accumulators fit TMEM's 512 columns and the SB buffers and the slots fit
+// shared memory:
+//   dim_p <= 128: 128 queries (SB = SM = 3) or 96 (4, 4), the tuning chooses;
+//   192: 64 (4, 4);  256: 32 (4, 4);  320: 64 (2, 3);  384: 32 (2, 4);
+//   448: 32 (2, 2).
+// A B buffer is released when the MMAs that read it are done, a slot when the
+// epilogue has tested its chunk: the producers restage B while the epilogue
+// still works on older chunks.
+struct TileShape {
+    int nq, sb, sm;
+};
+inline TileShape shape_for(int dim_p, int pref) {
+    if (dim_p <= 128) return pref == 96 ? TileShape{96, 4, 4} : TileShape{128, 3, 3};
+    if (dim_p <= 192) return {64, 4, 4};
+    if (dim_p <= 256) return {32, 4, 4};
+    if (dim_p <= 320) return {64, 2, 3};
+    if (dim_p <= 384) return {32, 2, 4};
+    return {32, 2, 2};
+}
+inline int nq_for(int dim_p, int pref) { return shape_for(dim_p, pref).nq; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -616,14 +630,26 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     if (lane == 31) base = atomicAdd(a.out_count, (unsigned long long)wtot);
                     base = __shfl_sync(0xffffffffu, base, 31);
                     unsigned long long o = base + (unsigned long long)(incl - np);
-                    while (passbits) {
-                        const int i = __ffs(passbits) - 1;
-                        passbits &= passbits - 1;
-                        if ((int64_t)o < a.cap) {
-                            a.out_q[o] = rec[cc + i].q;
-                            a.out_row[o] = (int32_t)row;
+                    // the columns with a kept pair in any lane, in order (warp-
+                    // uniform); kNN reads each one's q.x from the accumulator
+                    // again (the slot is not yet released), one TMEM column
+                    unsigned cols = __reduce_or_sync(0xffffffffu, passbits);
+                    while (cols) {
+                        const int i = __ffs(cols) - 1;
+                        cols &= cols - 1;
+                        uint32_t qx = 0u;
+                        if (a.out_qx) {
+                            qx = tc::tmem_ld1(tacc + tlane + (uint32_t)(sl * kNQ + cc + i));
+                            tc::tmem_ld_wait();
                         }
-                        ++o;
+                        if ((passbits >> i) & 1u) {
+                            if ((int64_t)o < a.cap) {
+                                a.out_q[o] = rec[cc + i].q;
+                                a.out_row[o] = (int32_t)row;
+                                if (a.out_qx) a.out_qx[o] = __uint_as_float(qx);
+                            }
+                            ++o;
+                        }
                     }
                 }
             }
@@ -870,7 +896,7 @@ void tc_bound_coeffs(int dim_p, float &cE1, float &cE2) {
     cE2 = (float)(1.0 / 2097152.0);
 }
 
-bool tc_supported(const Tree &t) { return t.metric == GTS_L2 && t.dim > 0 && t.dim <= 256 && t.n > 0; }
+bool tc_supported(const Tree &t) { return t.metric == GTS_L2 && t.dim > 0 && t.dim <= 448 && t.n > 0; }
 
 void tc_prepare(Tree &t, TcCache &c, cudaStream_t st) {
     if (c.ready) return;
@@ -1013,25 +1039,27 @@ int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegro
 }
 
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
-               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st) {
+               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st, DBuf<float> *out_qx) {
     *launches = 0;
     if (rg.n_items == 0) return 0;
     int dev = 0, sms = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     GTS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int nq_chunk = nq_for(c.dim_p, tq.chunk);
+    const TileShape shp = shape_for(c.dim_p, tq.chunk);
+    const int nq_chunk = shp.nq;
     int smem_optin = 0;
     GTS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // TMEM: A (dim_p columns) and the slots' accumulators share 512 columns:
-    // three slots of 128 queries, four of 96, 64 or 32; as many B buffers
-    const int slots = nq_chunk == 128 ? 3 : 4;
-    GTS_REQUIRE(c.dim_p + slots * nq_chunk <= 512, GTS_ECUDA, "tensor-core tile: TMEM columns");
-    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk, slots, slots);
+    // TMEM: A (dim_p columns) and the slots' accumulators share 512 columns
+    GTS_REQUIRE(c.dim_p + shp.sm * nq_chunk <= 512, GTS_ECUDA, "tensor-core tile: TMEM columns");
+    const size_t smem = tile_smem_bytes(c.dim_p, t.h, nq_chunk, shp.sb, shp.sm);
     GTS_REQUIRE(smem <= (size_t)smem_optin, GTS_ECUDA, "tensor-core tile: shared memory");
-    auto kern = nq_chunk == 96    ? k_tile_l2_tc<96, 4, 4>
-                : nq_chunk == 128 ? k_tile_l2_tc<128, 3, 3>
-                : nq_chunk == 64  ? k_tile_l2_tc<64, 4, 4>
-                                  : k_tile_l2_tc<32, 4, 4>;
+    void (*kern)(const CUtensorMap, const CUtensorMap, TileArgs) =
+        nq_chunk == 96    ? k_tile_l2_tc<96, 4, 4>
+        : nq_chunk == 128 ? k_tile_l2_tc<128, 3, 3>
+        : shp.sb == 4     ? (nq_chunk == 64 ? k_tile_l2_tc<64, 4, 4> : k_tile_l2_tc<32, 4, 4>)
+        : nq_chunk == 64  ? k_tile_l2_tc<64, 2, 3>
+        : shp.sm == 4     ? k_tile_l2_tc<32, 2, 4>
+                          : k_tile_l2_tc<32, 2, 2>;
     GTS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: shared memory (each CTA also has 1 KB reserved), the 512
     // TMEM columns, and registers
@@ -1078,6 +1106,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
     for (int attempt = 0; attempt < 2; ++attempt) {
         out_q.alloc(cap, st);
         out_row.alloc(cap, st);
+        if (out_qx) out_qx->alloc(cap, st);
         GTS_CUDA(cudaMemsetAsync(counter.get(), 0, 4, st));
         GTS_CUDA(cudaMemsetAsync(status.get(), 0, 4, st));
         GTS_CUDA(cudaMemsetAsync(count.get(), 0, 8, st));
@@ -1106,6 +1135,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.work_counter = counter.get();
         a.out_q = out_q.get();
         a.out_row = out_row.get();
+        a.out_qx = out_qx ? out_qx->get() : nullptr;
         a.cap = cap;
         a.out_count = count.get();
         a.status = status.get();

@@ -37,6 +37,7 @@ struct TileArgs {
     int64_t n_items;
     int *work_counter;
     int32_t *out_q, *out_row;
+    float *out_qx;            // null, or each kept pair's q.x~ (d~^2 = |q|^2 + |x|^2 - 2 q.x~ is within E of d^2)
     int64_t cap;
     unsigned long long *out_count;
     int *status;
@@ -123,8 +124,11 @@ int64_t tc_regroup(const Tree &t, const TcQuery &tq, TcRegroup &rg, cudaStream_t
 // mode; the leaf masks stay in dmask [nodes, nq]
 int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegroup &rg, cudaStream_t st);
 // run the tiles; returns the number of (query, row) pairs written to out_q/out_row
+// (and, given out_qx, each pair's q.x~: d~^2 = |q|^2 + |x|^2 - 2 q.x~ is within
+// tc_bound_coeffs' E of d^2)
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
-               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st);
+               DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st,
+               DBuf<float> *out_qx = nullptr);
 void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD);
 void wait_selftest(int post, uint32_t limit);
 

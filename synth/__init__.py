@@ -57,7 +57,7 @@ def strings_from_list(items) -> Strings:
 class Workload:
     """One synthetic workload: objects, queries and the query parameters."""
     name: str
-    metric: str                      # "edit" | "l1" | "l2"
+    metric: str                      # "edit" | "l1" | "l2" | "cos"
     objects: object                  # np.ndarray [n, dim] float32, or Strings
     queries: object                  # same kind as objects
     kind: str                        # "range" | "knn" | "mixed"
@@ -218,6 +218,29 @@ def uniform_cube(n: int = 2_000_000, dim: int = 256, nq: int = 20_000, seed: int
     qrng = np.random.Generator(np.random.PCG64(qseed))
     Q = qrng.random((nq, dim), dtype=np.float32)
     return Workload(f"uniform_{n}x{dim}_l1", "l1", X, Q, "mixed", fanout=fanout)
+
+
+def word_vectors(n: int = 200_000, dim: int = 300, n_centers: int = 500, nq: int = 10_000, k: int = 10,
+                 seed: int = 0, qseed: int = 1, fanout: int = 20) -> Workload:
+    """``n`` float32 vectors shaped like word embeddings: a shared mean
+    direction, ``n_centers`` topic clusters, and per-coordinate scales that
+    fall as (j + 1)^-0.3 (an anisotropic spectrum); ``nq`` queries from the
+    same law.  Angular (cosine) kNN with ``k``.  Stands in for Vector (Table
+    2: 200K x 300, cosine)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    scale = (np.arange(dim) + 1.0) ** -0.3
+    mean = 0.5 * rng.standard_normal(dim) * scale
+    centers = rng.standard_normal((n_centers, dim)) * scale
+    lab = rng.integers(0, n_centers, size=n)
+    X = np.empty((n, dim), dtype=np.float32)
+    step = 1 << 16
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        X[s:e] = (mean + centers[lab[s:e]] + 0.6 * rng.standard_normal((e - s, dim)) * scale).astype(np.float32)
+    qrng = np.random.Generator(np.random.PCG64(qseed))
+    qlab = qrng.integers(0, n_centers, size=nq)
+    Q = (mean + centers[qlab] + 0.6 * qrng.standard_normal((nq, dim)) * scale).astype(np.float32)
+    return Workload(f"wordvec_{n}x{dim}_cos_knn{k}", "cos", X, Q, "knn", k=np.full(nq, k, np.int32), fanout=fanout)
 
 
 def poisson_arrivals(m: int, rate_qps: float, seed: int) -> np.ndarray:

@@ -12,6 +12,9 @@ times, checked against the CPU oracle (brute force, FP64 or exact integers):
   with the 500,000-point batch update after the third round; per round 200
   queries (184 random, the 16 with the most answers) checked at the round's
   sequence number, on every path.
+* wordvec_200000x300_cos_knn10 (2 * 10^5 x 300, angular distance, k = 10):
+  1,024 of the 10,000 queries, drawn at random, with their FP64 keys, on the
+  BF16 path after autotuning and on the plain FP32 path.
 * uniform_2Mx256_l1 (2 * 10^6 x 256 L1): 256 kNN queries (random and the
   largest k) and 256 range queries (random and the most answers) of the mixed
   batch; then the serving loop under 20,000 Poisson arrivals at 50,000/s and
@@ -85,6 +88,22 @@ def test_gauss_full_size_every_query(env):
     ix.autotune(Qd, k=np.full(wl.nq, 10, np.int32), precision="bf16", reps=2)
     _compare(ix.knn(Qd, 10, precision="bf16"), every, want, "l2", "bf16 tiles, tuned")
     _compare(ix.knn(Qd, 10, precision="fp32"), every, want, "l2", "plain fp32")
+    ix.close()
+
+
+def test_wordvec_full_size(env):
+    g, torch = env
+    wl = synth.word_vectors()
+    ix = g.Index.build(torch.from_numpy(wl.objects).cuda(), "cos", fanout=wl.fanout, root_pivot=0)
+    Qd = torch.from_numpy(wl.queries).cuda()
+    idx = _pick(wl.nq, 1024, [], seed=103)
+    want = oracle.knn_query("cos", wl.objects, wl.queries[idx], 10)
+    ix.autotune(Qd, k=wl.k, precision="bf16", reps=2)
+    for prec in ("bf16", "fp32"):
+        r = ix.knn(Qd, 10, precision=prec, keys=True)
+        _compare(r, idx, want, "cos", f"wordvec {prec}")
+        keys = np.concatenate([r.keys[r.offsets[i]:r.offsets[i + 1]] for i in idx])
+        assert np.array_equal(keys, want[3]), f"wordvec {prec}: FP64 keys differ"
     ix.close()
 
 

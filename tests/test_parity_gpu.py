@@ -272,11 +272,14 @@ def test_bounded_wait_runs_out_and_device_stays_usable(gts):
     ix.close()
 
 
-@pytest.mark.parametrize("dim,dup", [(128, 0.0), (100, 0.2), (256, 0.0)])
+@pytest.mark.parametrize("dim,dup", [(128, 0.0), (100, 0.2), (256, 0.0), (300, 0.1), (384, 0.0), (448, 0.0)])
 def test_bf16_tiles_parity(gts, dim, dup):
+    """Every tile shape: 128 queries per chunk (dim <= 128), 64 (dim_p 192 and
+    320), 32 (dim_p 256, 384 and 448)."""
     X, Q = vec_case(20011, dim, 300, seed=40 + dim, dup=dup)
     Q[:3] = X[[5, 9, 20010]]
     ix = gts.Index.build(X, "l2", fanout=12, root_pivot=7)
+    assert ix.knn(Q[:4], 3, precision="bf16").stats["tiles"] > 0     # the tensor-core tiles run
     for k in (1, 10, 33):
         r = ix.knn(Q, k, precision="bf16")
         assert_same(r, oracle.knn_query("l2", X, Q, k), "l2", f"bf16 tiles knn k={k}")
