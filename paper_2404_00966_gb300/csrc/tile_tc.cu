@@ -630,26 +630,29 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     if (lane == 31) base = atomicAdd(a.out_count, (unsigned long long)wtot);
                     base = __shfl_sync(0xffffffffu, base, 31);
                     unsigned long long o = base + (unsigned long long)(incl - np);
-                    // the columns with a kept pair in any lane, in order (warp-
-                    // uniform); kNN reads each one's q.x from the accumulator
-                    // again (the slot is not yet released), one TMEM column
-                    unsigned cols = __reduce_or_sync(0xffffffffu, passbits);
-                    while (cols) {
-                        const int i = __ffs(cols) - 1;
-                        cols &= cols - 1;
-                        uint32_t qx = 0u;
-                        if (a.out_qx) {
-                            qx = tc::tmem_ld1(tacc + tlane + (uint32_t)(sl * kNQ + cc + i));
-                            tc::tmem_ld_wait();
-                        }
-                        if ((passbits >> i) & 1u) {
-                            if ((int64_t)o < a.cap) {
-                                a.out_q[o] = rec[cc + i].q;
-                                a.out_row[o] = (int32_t)row;
-                                if (a.out_qx) a.out_qx[o] = __uint_as_float(qx);
+                    while (passbits) {
+                        const int i = __ffs(passbits) - 1;
+                        passbits &= passbits - 1;
+                        if ((int64_t)o < a.cap) {
+                            a.out_q[o] = rec[cc + i].q;
+                            a.out_row[o] = (int32_t)row;
+                            if (a.out_qx) {
+                                // q.x of column i, picked from the registers by a
+                                // select tree on the bits of i (an indexed load
+                                // would put v in local memory)
+                                float e16[16], e8[8], e4[4], e2[2];
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) e16[k] = __uint_as_float((i & 1) ? v[2 * k + 1] : v[2 * k]);
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) e8[k] = (i & 2) ? e16[2 * k + 1] : e16[2 * k];
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) e4[k] = (i & 4) ? e8[2 * k + 1] : e8[2 * k];
+#pragma unroll
+                                for (int k = 0; k < 2; ++k) e2[k] = (i & 8) ? e4[2 * k + 1] : e4[2 * k];
+                                a.out_qx[o] = (i & 16) ? e2[1] : e2[0];
                             }
-                            ++o;
                         }
+                        ++o;
                     }
                 }
             }
