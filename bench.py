@@ -55,10 +55,10 @@ ALU_LANES_PER_SM = 64         # integer / bit-logic ALU pipe: 2 warp instruction
                               # instructions executed per active SM cycle are exactly 2 x its pipe utilization)
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/):
-# k_tile_l2_tc at half size, 0.459 GB read + write (node rows and the node x
-# query leaf-mask matrix), both of which double at full size.  None once the
-# kernel has changed since the counters were taken.
-TRAFFIC = {"kernel": "tile", "bytes_per_launch": 0.92e9}
+# k_tile_l2_tc at half size, 0.467 GB read + write (node rows, the node x
+# query leaf-mask matrix and the kept pairs' q.x), all of which double at full
+# size.  None once the kernel has changed since the counters were taken.
+TRAFFIC = {"kernel": "tile", "bytes_per_launch": 0.934e9}
 
 # ALU-pipe thread instructions per full-DP-equivalent cell (|q| x |o| per pair)
 # of the bit-parallel edit-distance kernels: sm__inst_executed_pipe_alu.sum x 32

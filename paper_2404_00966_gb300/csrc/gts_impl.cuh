@@ -133,6 +133,10 @@ struct TcCache {
     int dim_p = 0;
     DBuf<uint8_t> Xh, Xl;
     DBuf<float> xn2;
+    // every pivot level's pivots as split rows (node order; empty nodes: zero rows)
+    bool piv_ready = false;
+    DBuf<uint8_t> Ph, Pl;
+    DBuf<float> pn2;
 };
 
 struct Tree {

@@ -70,6 +70,10 @@ struct Dev {
     const uint8_t *qg;    // strings: hashed 3-gram counts of the tree rows [n, 64]
     const uint8_t *qgq;   // the same for the batch's queries [nq, 64]
     float epsc;    // pruning slack factor (0 for edit distance)
+    // absolute slack of each pivot level's query-to-pivot distances: 0 for
+    // FP32 distances (their error is within epsc's relative bound), the
+    // tensor-core bound for levels whose dense matrix the tensor cores computed
+    float lslack[kMaxHeight];
     float absf;    // absolute floor of every FP32 distance bound (angular distance: the unit-vector rounding)
     // angular distance: the kernels work on unit vectors (X, Q, cX); the FP64
     // keys come from the raw rows and queries
@@ -373,7 +377,7 @@ __global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__re
         int64_t id = 0;
         if (e < b) {
             const float dv = path[e * d.h + l];
-            ub = d.rel > 0.f ? (double)dv * up + (double)d.absf : (double)dv;
+            ub = d.rel > 0.f ? (double)dv * up + (double)d.absf + (double)d.lslack[l] : (double)dv;
             if (!full || ub <= k_d) {   // the bound test before the pivot's delete mark
                 const int32_t prow = d.npiv[lvl_base + enode[e]];
                 if (row_visible(d, prow, s)) {
@@ -594,8 +598,8 @@ __global__ void k_probe_vec(Dev d, LevelOffsets lo_off, int64_t nq, int cap, con
 
 // ---------------------------------------------------------------- expansion
 
-__device__ __forceinline__ bool interval_hit(float dq, float thr, float lo, float hi, float epsc) {
-    const float eps = epsc > 0.f ? epsc * (dq + thr + fabsf(hi)) : 0.f;
+__device__ __forceinline__ bool interval_hit(float dq, float thr, float lo, float hi, float epsc, float abs_slack) {
+    const float eps = (epsc > 0.f ? epsc * (dq + thr + fabsf(hi)) : 0.f) + abs_slack;
     return (dq - thr <= hi + eps) && (dq + thr + eps >= lo);
 }
 
@@ -634,7 +638,7 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
                     bool keep = false;
                     if (j < d.F) {
                         const int64_t c = lvl_next + (int64_t)node * d.F + j;
-                        keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+                        keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc, d.lslack[l]);
                     }
                     m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
                 }
@@ -672,7 +676,7 @@ __global__ void k_expand(Dev d, const int32_t *__restrict__ eq, const int32_t *_
         bool keep = false;
         if (j < d.F) {
             const int64_t c = lvl_next + (int64_t)node * d.F + j;
-            keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc);
+            keep = d.nsize[c] > 0 && interval_hit(dq, thr, d.nlo[c], d.nhi[c], d.epsc, d.lslack[l]);
         }
         m |= (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
     }
@@ -699,6 +703,7 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
                                  const float *__restrict__ dense, int64_t P) {
     constexpr int G = kLastGroup;
     constexpr int V = NV > 0 ? NV : 1;
+    const float lab = dense ? d.lslack[l] : 0.f;   // the slack of the dense matrix's distances
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; e0 + w * G < e1; w += nw) {
@@ -786,7 +791,7 @@ __global__ void k_last_level_vec(Dev d, const int32_t *__restrict__ eq, const in
 #pragma unroll
             for (int i = 0; i < G; ++i) {
                 const float thr = __shfl_sync(0xffffffffu, my_thr, i);
-                const bool keep = i < cnt && j < d.F && sz[i] > 0 && interval_hit(dq[i], thr, lo[i], hi[i], d.epsc);
+                const bool keep = i < cnt && j < d.F && sz[i] > 0 && interval_hit(dq[i], thr, lo[i], hi[i], d.epsc, lab);
                 const uint64_t m = (uint64_t)__ballot_sync(0xffffffffu, keep) << j0;
                 if (lane == i) my_mask |= m;
             }
@@ -816,7 +821,8 @@ __global__ void k_leaf_masks_dense(Dev d, const int32_t *__restrict__ eq, const 
         const int64_t c0 = lvl_next + (int64_t)node * d.F;
         uint64_t m = 0;
         for (int j = 0; j < d.F; ++j)
-            if (d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc)) m |= 1ull << j;
+            if (d.nsize[c0 + j] > 0 && interval_hit(dq, thr, d.nlo[c0 + j], d.nhi[c0 + j], d.epsc, d.lslack[l]))
+                m |= 1ull << j;
         path[e * d.h + l] = dq;
         mask_out[e - e0] = m;
     }
@@ -871,7 +877,7 @@ __global__ void k_leafscan(Dev d, const int32_t *__restrict__ eq, const int32_t 
                     for (int t = 0; t < kMaxHeight; ++t) {
                         if (t < d.h) {
                             const float T = d.table[(int64_t)t * d.n + row];
-                            const float eps = d.epsc > 0.f ? d.epsc * (T + dq[t] + thr) : 0.f;
+                            const float eps = (d.epsc > 0.f ? d.epsc * (T + dq[t] + thr) : 0.f) + d.lslack[t];
                             if (fabsf(T - dq[t]) > thr + eps) pass = false;
                         }
                     }
@@ -936,7 +942,7 @@ __global__ void k_count_table_pass_dense(Dev d, DenseLevels dl, const uint64_t *
                 bool pass = true;
                 for (int l = 0; l < d.h && pass; ++l) {
                     const float T = d.table[(int64_t)l * d.n + r];
-                    const float eps = d.epsc > 0.f ? d.epsc * (T + dq[l] + thr) : 0.f;
+                    const float eps = (d.epsc > 0.f ? d.epsc * (T + dq[l] + thr) : 0.f) + d.lslack[l];
                     if (fabsf(T - dq[l]) > thr + eps) pass = false;
                 }
                 c += pass ? 1 : 0;
@@ -1565,6 +1571,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                             float *tau) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float lab = d.lslack[d.h - 1];   // the last pivot level's absolute slack
     for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
         const int K = kq[q];
         TauList L;
@@ -1583,7 +1590,8 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                 kth = L.kd();
                 kthid = L.kid();
                 // one float step above the quotient absorbs its FP64 rounding
-                fthr = nextafterf(__double2float_ru((kth - (double)d.absf) / up), __int_as_float(0x7f800000));
+                fthr = nextafterf(__double2float_ru((kth - (double)d.absf - (double)lab) / up),
+                                  __int_as_float(0x7f800000));
             }
         };
         refresh();
@@ -1605,7 +1613,7 @@ __global__ void k_tau_dense(Dev d, const float *__restrict__ D, int64_t P, const
                 double ub = 0.0;
                 int64_t id = 0;
                 if (mem[u] && dv[u] <= fthr) {
-                    ub = (double)dv[u] * up + (double)d.absf;
+                    ub = (double)dv[u] * up + (double)d.absf + (double)lab;
                     // the bound test first: most pivots fail it, and then the
                     // pivot's delete mark and id are never read
                     if ((L.n < K) || ub <= kth) {
@@ -1733,21 +1741,24 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
                 const float thr = thr_q[qq];
                 // interval_hit for two children at a time in packed FP32, its
                 // query terms formed once (the same operations in the same
-                // order): eps = epsc (sq + |hi|), keep iff u <= hi + eps and
-                // sq + eps >= lo.  A failed test shows as the sign bit of
-                // (hi + eps) - u or of (sq + eps) - lo: both differences are
-                // rounded once from the exact ones and are never -0 (eps >= +0,
-                // so hi + eps and sq + eps are not -0).
+                // order): eps = epsc (sq + |hi|) + the level's absolute slack,
+                // keep iff u <= hi + eps and sq + eps >= lo.  A failed test
+                // shows as the sign bit of (hi + eps) - u or of (sq + eps) -
+                // lo: both differences are rounded once from the exact ones
+                // and are never -0 (eps >= +0, so hi + eps and sq + eps are
+                // not -0).
                 const float u = dq - thr, sq = dq + thr;
                 const float2 u2 = make_float2(u, u), sq2 = make_float2(sq, sq);
                 const float2 ec2 = make_float2(epsc, epsc);
+                const float2 lab2 = make_float2(d.lslack[d.h - 1], d.lslack[d.h - 1]);
                 uint64_t fail = 0;
 #pragma unroll 2
                 for (int j = 0; j < d.F; j += 2) {
                     const float4 h = sph[j >> 1];
                     const float2 lo = spl[j >> 1];
-                    const float2 eps = epsc > 0.f ? mul2f(ec2, add2f(sq2, make_float2(h.z, h.w)))
-                                                  : make_float2(0.f, 0.f);
+                    const float2 eps = add2f(epsc > 0.f ? mul2f(ec2, add2f(sq2, make_float2(h.z, h.w)))
+                                                        : make_float2(0.f, 0.f),
+                                             lab2);
                     const float2 d1 = sub2f(add2f(make_float2(h.x, h.y), eps), u2);
                     const float2 d2 = sub2f(add2f(sq2, eps), lo);
                     const uint32_t f0 = (__float_as_uint(d1.x) | __float_as_uint(d2.x)) >> 31;
@@ -2031,6 +2042,20 @@ struct Runner {
         clk.end();
     }
 
+    // Level l's query-to-pivot matrix: on the tensor cores when the batch
+    // runs the BF16 tiles (with the level's absolute slack), else in FP32.
+    void level_matrix(int l, float *out) {
+        const int64_t P = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
+        clk.begin(GTS_STAGE_PIVOT_DIST);
+        if (use_tc && tc_dense_supported(ix->tree, ix->tree.tc) && ix->tree.tc.piv_ready) {
+            d.lslack[l] = tc_dense_dist(ix->tree, ix->tree.tc, l, (const __nv_bfloat16 *)tcQh.get(),
+                                        (const __nv_bfloat16 *)tcQl.get(), tcqn2.get(), d.Q, qb.nq, out, st);
+        } else {
+            dense_pivot_dist(d.metric, d.X, d.dim, d.Q, qb.nq, d.npiv + ix->tree.lvl_off[l], P, out, st);
+        }
+        clk.end();
+    }
+
     // The level's dense distance matrix, computed on the first group that
     // reaches the level if its frontier holds at least a quarter of the
     // batch's (query, node) pairs and the matrix fits an eighth of the budget.
@@ -2047,9 +2072,7 @@ struct Runner {
         dense_state[l] = 2;
         if (!dense_supported(d.metric, d.dim, d.X, d.Q) || 4 * E < pairs || pairs * 4 > budget / 8) return nullptr;
         dense[l].alloc(pairs, st);
-        clk.begin(GTS_STAGE_PIVOT_DIST);
-        dense_pivot_dist(d.metric, d.X, d.dim, d.Q, qb.nq, d.npiv + ix->tree.lvl_off[l], P, dense[l].get(), st);
-        clk.end();
+        level_matrix(l, dense[l].get());
         st_dense_pairs += pairs;
         dense_state[l] = 1;
         return dense[l].get();
@@ -2366,9 +2389,7 @@ struct Runner {
         // the last level's distances (forced: the frontier is dense)
         if (dense_state[ll] != 1) {
             dense[ll].alloc(nq * P, st);
-            clk.begin(GTS_STAGE_PIVOT_DIST);
-            dense_pivot_dist(d.metric, d.X, d.dim, d.Q, nq, d.npiv + base, P, dense[ll].get(), st);
-            clk.end();
+            level_matrix(ll, dense[ll].get());
             st_dense_pairs += nq * P;
             dense_state[ll] = 1;
         }
@@ -2485,6 +2506,7 @@ struct Runner {
         tq.qseq = d.qseq;
         tq.thr = thr.get();
         tq.epsc = d.epsc;
+        for (int l = 0; l < kMaxHeight; ++l) tq.lslack[l] = d.lslack[l];
         tq.any_deleted = ix->tree.n_deleted > 0 ? 1 : 0;
         return tq;
     }
@@ -2974,6 +2996,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         {
             std::lock_guard<std::mutex> g(ix->prep_mu);   // concurrent queries build it once
             tc_prepare(t, t.tc, st);
+            if (tc_dense_supported(t, t.tc)) tc_prepare_pivots(t, t.tc, st);
         }
         R.use_tc = true;
         R.clk.begin(GTS_STAGE_OTHER);
@@ -3035,6 +3058,7 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         d.qgq = qgq.get();
     }
     d.epsc = t.dim > 0 ? 4.f * d.rel : 0.f;
+    for (int l = 0; l < kMaxHeight; ++l) d.lslack[l] = 0.f;
     // angular distance: the unit vectors' chords stand within kCosAbsSlack of
     // the exact unit vectors'; a bound crosses between the two twice at most
     d.cosine = t.cosine ? 1 : 0;

@@ -29,6 +29,8 @@
 //   | d~^2 - d^2 | <= E = cE1 |q| |x| + cE2 (|q| + |x|)^2,
 //   cE1 = 2.02 (3.01 * 2^-16 + gamma_{3K+2}(2^-23)),  cE2 = 2^-21,
 // and d <= thr is possible only if d~^2 <= thr^2 + E.
+#include <cstring>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -124,10 +126,11 @@ __global__ void k_split_rows(const float *__restrict__ X, int dim, int dim_p, in
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
-        const int64_t src = sel ? (int64_t)sel[row] : row;   // output row `row` takes input row `src`
+        // output row `row` takes input row `src` (a negative src: a zero row)
+        const int64_t src = sel ? (int64_t)sel[row] : row;
         double s = 0.0;
         for (int k = lane; k < dim_p; k += 32) {
-            const float v = k < dim ? X[src * dim + k] : 0.f;
+            const float v = k < dim && src >= 0 ? X[src * dim + k] : 0.f;
             const __nv_bfloat16 h = __float2bfloat16_rn(v);
             const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
             Xh[row * dim_p + k] = h;
@@ -613,7 +616,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
                     for (int l = 0; l < a.h && ok && !a.dmask; ++l) {
                         const float T = a.table[(int64_t)l * a.n + row];
                         const float pl = pth[(cc + i) * a.hp + l];
-                        const float eps = a.epsc * (T + pl + rc.thr);
+                        const float eps = a.epsc * (T + pl + rc.thr) + a.lslack[l];
                         if (fabsf(T - pl) > rc.thr + eps) ok = false;
                     }
                     if (ok) passbits |= 1u << i;
@@ -1143,6 +1146,7 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         a.out_count = count.get();
         a.status = status.get();
         a.epsc = tq.epsc;
+        for (int l = 0; l < kMaxHeight; ++l) a.lslack[l] = tq.lslack[l];
         a.cE1 = cE1;
         a.cE2 = cE2;
         a.any_deleted = tq.any_deleted;
@@ -1172,6 +1176,280 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
         cap = (int64_t)hcount;
     }
     throw Error(GTS_ECUDA, "tensor-core tile: output count changed between launches");
+}
+
+// ---------------------------------------------------------------- dense pivot distances
+
+namespace {
+
+constexpr int kDenseQ = 128;   // queries per CTA (MMA N)
+
+struct DenseTcArgs {
+    const __nv_bfloat16 *Ph, *Pl;   // the level's pivots, split bf16 rows [P, dim_p]
+    const float *pn2, *pnu;         // their squared norms (FP64 sums, rounded) and norms rounded up
+    const float *qn2, *qnu;         // the same for the queries
+    const int32_t *piv;             // pivot row of each node (-1: empty), for the exact recomputation
+    const float *X, *Q;             // FP32 rows and queries
+    int dim, dim_p;
+    int64_t P, nq;
+    float cE1, cE2;
+    float *out;                     // [nq, P]
+    unsigned *slack;                // the largest |d~ - d| bound written (float bits)
+    int *status;
+};
+
+// PTX approximations; every use below checks its own result (a residual),
+// so no error bound of theirs is relied on
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// |x| rounded up, for the error bound
+__global__ void k_norms_up(const float *__restrict__ n2, int64_t n, float *__restrict__ nu) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        nu[i] = __fmul_ru(__fsqrt_ru(n2[i]), 1.f + 1e-6f);
+}
+
+// D[q, p] for 128 pivots x 128 queries per CTA: the pivots' split rows into
+// TMEM (TMEM lane = pivot), the queries' by one TMA copy into shared memory,
+// three MMAs per 16-wide k-step, then per entry d~^2 = (|p|^2 + |q|^2) -
+// 2 p.q~ with |d~^2 - d^2| <= E (the tile kernel's bound, here with 2 cE2).
+// The entry stores t ~ sqrt(d~^2) and the level's absolute slack takes an
+// upper bound of |t - d|: |t - sqrt(d~^2)| <= |t^2 - d~^2| / t (the residual
+// of t, computed by one fused multiply-add) and |sqrt(d~^2) - d| = |d~^2 -
+// d^2| / (sqrt(d~^2) + d) <= E / ((1 + sqrt(15 / 16)) sqrt(d~^2)) when d~^2 >
+// 16 E (d >= sqrt(d~^2 - E)), with 1 / t from an approximate reciprocal
+// checked by its own residual (0.5085 covers 1 / (1 + sqrt(15 / 16)) and
+// 1 / (1 - 2^-13)).  An entry near the pivot (d~^2 <= 16 E, or a bound above
+// 2^-12 (|p| + |q|), where the product form cancels) is recomputed in FP32 as
+// the sum of squared differences instead, within the FP32 relative bound the
+// search allows for any distance, and adds nothing to the slack.
+// Warp w: TMEM lane quadrant w % 4 (32 pivots); A columns (w / 4 = 0: hi,
+// 1: lo) and accumulator columns [64 (w / 4), 64 (w / 4) + 64).
+__global__ void __launch_bounds__(256, 1)
+    k_dense_tc(const __grid_constant__ CUtensorMap map_qh, const __grid_constant__ CUtensorMap map_ql, DenseTcArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int panels = a.dim_p / 64;
+    const int bpanel = kDenseQ * 128;
+    uint8_t *sB = smem;                                   // hi panels, then lo panels
+    uint64_t *bars = (uint64_t *)(sB + 2 * panels * bpanel);
+    uint32_t *tslot = (uint32_t *)(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int ncols = a.dim_p + kDenseQ <= 256 ? 256 : 512;
+    const int64_t p0 = (int64_t)blockIdx.x * kRows, q0 = (int64_t)blockIdx.y * kDenseQ;
+    if (warp == 0) tc::tmem_alloc(tslot, ncols);
+    if (tid == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::mbar_fence_init();
+        tc::mbar_expect_tx(&bars[0], (uint32_t)(2 * panels * bpanel));
+        tc::tma_load_3d(sB, &map_qh, 0, (int32_t)q0, 0, &bars[0]);
+        tc::tma_load_3d(sB + panels * bpanel, &map_ql, 0, (int32_t)q0, 0, &bars[0]);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t tacc = tmem + (uint32_t)a.dim_p;
+    const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+    // A: this thread's pivot row, hi in columns [0, dim_p / 2), lo after
+    const int64_t p = p0 + quad * 32 + lane;
+    const bool pv = p < a.P;
+    for (int c = 0; c < a.dim_p / 2; c += 16) {
+        const int col = half * (a.dim_p / 2) + c;
+        uint32_t v[16];
+        if (pv) {
+            const uint4 *src = reinterpret_cast<const uint4 *>((half ? a.Pl : a.Ph) + p * a.dim_p + 2 * c);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint4 x = src[j];
+                v[4 * j] = x.x;
+                v[4 * j + 1] = x.y;
+                v[4 * j + 2] = x.z;
+                v[4 * j + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0u;
+        }
+        tc::tmem_st16(tmem + tlane + (uint32_t)col, v);
+    }
+    tc::tmem_st_wait();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (tid == 0) {
+        if (!tc::mbar_wait(&bars[0], 0)) {
+            atomicExch(a.status, 1);
+        } else {
+            const uint32_t idesc = tc::idesc_bf16_f32(kRows, kDenseQ);
+            const uint32_t alo = tmem + (uint32_t)(a.dim_p / 2);
+            const uint64_t bh = tc::sdesc_k_sw128(tc::smem_u32(sB));
+            const uint64_t bl = bh + (uint64_t)((panels * bpanel) >> 4);
+            for (int pnl = 0; pnl < panels; ++pnl) {
+                const uint64_t po = (uint64_t)((pnl * bpanel) >> 4);
+                const uint32_t ka = 32 * pnl;
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    tc::mma_bf16_ts(tacc, tmem + ka + 8 * s4, bh + po + 2 * s4, idesc, (pnl | s4) != 0);
+                    tc::mma_bf16_ts(tacc, tmem + ka + 8 * s4, bl + po + 2 * s4, idesc, 1u);
+                    tc::mma_bf16_ts(tacc, alo + ka + 8 * s4, bh + po + 2 * s4, idesc, 1u);
+                }
+            }
+            tc::mma_commit(&bars[1]);
+        }
+    }
+    __syncthreads();
+    // (warp-uniform: the TMEM loads below are warp-wide)
+    const bool ok = __all_sync(0xffffffffu, *(volatile int *)a.status == 0 && tc::mbar_wait(&bars[1], 0));
+    tc::tc_fence_after();
+    float umax = 0.f;
+    if (ok) {
+        const float p2 = pv ? a.pn2[p] : 0.f;
+        const float pn = pv ? a.pnu[p] : 0.f;
+        const int32_t prow = pv ? a.piv[p] : -1;
+        for (int c0 = half * (kDenseQ / 2); c0 < (half + 1) * (kDenseQ / 2); c0 += 32) {
+            uint32_t v[32];
+            tc::tmem_ld32(tacc + tlane + (uint32_t)c0, v);
+            tc::tmem_ld_wait();
+            uint32_t redo = 0;   // entries near the pivot, recomputed below
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int64_t q = q0 + c0 + i;
+                if (!pv || q >= a.nq) continue;
+                const float q2 = a.qn2[q], qn = a.qnu[q];
+                const float sn = __fadd_ru(pn, qn);
+                const float E = __fadd_ru(__fmul_ru(a.cE1, __fmul_ru(pn, qn)), __fmul_ru(2.f * a.cE2, __fmul_ru(sn, sn)));
+                const float d2 = fmaf(-2.f, __uint_as_float(v[i]), p2 + q2);
+                bool near = !(d2 > 16.f * E);
+                float t = 0.f, u = 0.f;
+                if (!near) {
+                    t = sqrt_approx(d2);
+                    const float r = fabsf(fmaf(t, t, -d2));               // |t^2 - d~^2|, one rounding
+                    const float inv = rcp_approx(t);
+                    const float e = fabsf(fmaf(-t, inv, 1.f));            // 1 - t inv
+                    const float ih = __fmul_ru(inv, __fadd_ru(1.f, __fadd_ru(2.f * e, 2.384185791015625e-7f)));
+                    const float e1 = __fmul_ru(__fmul_ru(r, 1.0000002f), ih);   // >= |t - sqrt(d~^2)|
+                    u = __fadd_ru(e1, __fmul_ru(__fmul_ru(E, ih), 0.5085f));
+                    // (written so that a NaN anywhere counts as near)
+                    near = !(e1 <= 1.220703125e-4f * t) || !(u <= 2.44140625e-4f * sn);
+                }
+                if (near && prow >= 0) {
+                    redo |= 1u << i;
+                } else {
+                    if (!near) umax = fmaxf(umax, u);
+                    a.out[q * a.P + p] = near ? sqrtf(fmaxf(d2, 0.f)) : t;   // (near with no pivot: an empty node)
+                }
+            }
+            while (redo) {   // near the pivot: the sum of squared differences in FP32
+                const int i = __ffs(redo) - 1;
+                redo &= redo - 1;
+                const int64_t q = q0 + c0 + i;
+                const float *xr = a.X + (int64_t)prow * a.dim, *qr = a.Q + q * a.dim;
+                float sum = 0.f;
+                for (int k = 0; k < a.dim; ++k) {
+                    const float d = qr[k] - xr[k];
+                    sum = fmaf(d, d, sum);
+                }
+                a.out[q * a.P + p] = sqrtf(sum);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+    if (lane == 0 && umax > 0.f) atomicMax(a.slack, __float_as_uint(umax));
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && !ok) {   // let an issued copy or MMA land before TMEM and shared memory go
+        tc::mbar_wait(&bars[0], 0);
+        tc::mbar_wait(&bars[1], 0);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// (at least 80 KB: at most two CTAs per SM, as many as TMEM holds)
+size_t dense_tc_smem(int dim_p) {
+    const size_t b = 1024 + 2 * (size_t)(dim_p / 64) * kDenseQ * 128 + 64;
+    return b < 81920 ? 81920 : b;
+}
+
+}  // namespace
+
+bool tc_dense_supported(const Tree &t, const TcCache &c) {
+    return c.ready && c.dim_p > 0 && c.dim_p <= 256 && t.h >= 1;
+}
+
+void tc_prepare_pivots(const Tree &t, TcCache &c, cudaStream_t st) {
+    if (c.piv_ready) return;
+    const int64_t nodes = t.lvl_off[t.h];   // every pivot level's nodes
+    c.Ph.alloc((size_t)(nodes > 0 ? nodes : 1) * c.dim_p * 2, st);
+    c.Pl.alloc((size_t)(nodes > 0 ? nodes : 1) * c.dim_p * 2, st);
+    c.pn2.alloc(nodes > 0 ? nodes : 1, st);
+    if (nodes > 0)
+        k_split_rows<<<nblk(nodes * 32), 256, 0, st>>>(t.X.get(), t.dim, c.dim_p, nodes, (__nv_bfloat16 *)c.Ph.get(),
+                                                       (__nv_bfloat16 *)c.Pl.get(), c.pn2.get(), t.npiv.get());
+    check_launch("split pivots");
+    GTS_CUDA(cudaStreamSynchronize(st));
+    c.Ph.persist();
+    c.Pl.persist();
+    c.pn2.persist();
+    c.piv_ready = true;
+}
+
+float tc_dense_dist(const Tree &t, const TcCache &c, int level, const __nv_bfloat16 *Qh, const __nv_bfloat16 *Ql,
+                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st) {
+    const int64_t base = t.lvl_off[level], P = t.lvl_off[level + 1] - base;
+    if (P == 0 || nq == 0) return 0.f;
+    const size_t smem = dense_tc_smem(c.dim_p);
+    GTS_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const CUtensorMap mh = make_panel_map(Qh, nq, c.dim_p, kDenseQ);
+    const CUtensorMap ml = make_panel_map(Ql, nq, c.dim_p, kDenseQ);
+    DBuf<unsigned> slack(1, st);
+    DBuf<int> status(1, st);
+    DBuf<float> pnu(P, st), qnu(nq, st);
+    k_norms_up<<<nblk(P), 256, 0, st>>>(c.pn2.get() + base, P, pnu.get());
+    k_norms_up<<<nblk(nq), 256, 0, st>>>(qn2, nq, qnu.get());
+    GTS_CUDA(cudaMemsetAsync(slack.get(), 0, 4, st));
+    GTS_CUDA(cudaMemsetAsync(status.get(), 0, 4, st));
+    DenseTcArgs a;
+    a.Ph = reinterpret_cast<const __nv_bfloat16 *>(c.Ph.get()) + base * c.dim_p;
+    a.Pl = reinterpret_cast<const __nv_bfloat16 *>(c.Pl.get()) + base * c.dim_p;
+    a.pn2 = c.pn2.get() + base;
+    a.pnu = pnu.get();
+    a.qn2 = qn2;
+    a.qnu = qnu.get();
+    a.piv = t.npiv.get() + base;
+    a.X = t.X.get();
+    a.Q = Q;
+    a.dim = t.dim;
+    a.dim_p = c.dim_p;
+    a.P = P;
+    a.nq = nq;
+    tc_bound_coeffs(c.dim_p, a.cE1, a.cE2);
+    a.out = out;
+    a.slack = slack.get();
+    a.status = status.get();
+    const dim3 grid((unsigned)((P + kRows - 1) / kRows), (unsigned)((nq + kDenseQ - 1) / kDenseQ));
+    k_dense_tc<<<grid, 256, smem, st>>>(mh, ml, a);
+    check_launch("dense pivot distances (tensor cores)");
+    unsigned hs = 0;
+    int hst = 0;
+    GTS_CUDA(cudaMemcpyAsync(&hs, slack.get(), 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaMemcpyAsync(&hst, status.get(), 4, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+    GTS_REQUIRE(hst == 0, GTS_ETIMEOUT, "dense pivot distances: a bounded mbarrier wait ran out");
+    float f;
+    std::memcpy(&f, &hs, 4);
+    return f;
 }
 
 // ---------------------------------------------------------------- self-test

@@ -42,6 +42,7 @@ struct TileArgs {
     unsigned long long *out_count;
     int *status;
     float epsc, cE1, cE2;     // pruning slack; error-bound coefficients
+    float lslack[kMaxHeight]; // absolute slack of each level's query-to-pivot distances
     int any_deleted;          // 0: no row has a delete mark, skip the visibility test
     // window mode (dense nodes): the node x query bitmap of the regrouping
     const uint32_t *bits;     // [nodes, nw]
@@ -79,6 +80,7 @@ struct TcQuery {
     const int64_t *qseq = nullptr;
     const float *thr = nullptr;
     float epsc = 0.f;
+    float lslack[kMaxHeight] = {};   // absolute slack of each level's path distances
     int any_deleted = 1;
 };
 
@@ -129,6 +131,15 @@ int64_t tc_dense_items(const Tree &t, int64_t nq, const uint64_t *dmask, TcRegro
 int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegroup &rg, DBuf<int32_t> &out_q,
                DBuf<int32_t> &out_row, int64_t cap_hint, int *launches, cudaStream_t st,
                DBuf<float> *out_qx = nullptr);
+// Dense query-to-pivot distances of one pivot level on the tensor cores
+// (dim_p <= 256, after tc_prepare and tc_prepare_pivots): out[q, p] for the
+// batch's split queries; returns the level's absolute slack, an upper bound of
+// |out - d| over the entries not recomputed in FP32 (those are within the FP32
+// relative bound)
+bool tc_dense_supported(const Tree &t, const TcCache &c);
+void tc_prepare_pivots(const Tree &t, TcCache &c, cudaStream_t st);
+float tc_dense_dist(const Tree &t, const TcCache &c, int level, const __nv_bfloat16 *Qh, const __nv_bfloat16 *Ql,
+                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st);
 void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD);
 void wait_selftest(int post, uint32_t limit);
 
