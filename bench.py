@@ -713,6 +713,10 @@ def bench_wordvec(args):
     ix.rebuild()
     torch.cuda.synchronize()
     rebuild_s = time.perf_counter() - t0
+    # untimed setup like the build: the index shape by the cost model and a
+    # timed sample batch (pruning is weak on these 300-dimensional directions,
+    # so shallower trees with larger node blocks win), then launch parameters
+    shapes = ix.autotune_shape(Qd[:2000], k=10, precision=prec, candidates=4, reps=1) if not args.no_tune else None
     tuning = ix.autotune(Qd, k=wl.k, precision=prec, reps=2) if not args.no_tune else None
 
     def step(timing=False, count=False):
@@ -729,7 +733,8 @@ def bench_wordvec(args):
            "warmup": args.warmup, "ms_per_step": round(ms / args.other_steps, 4),
            "dtype": "bf16+f64" if prec == "bf16" else "f32+f64",
            "config": {"workload": wl.name, "n": int(X.shape[0]), "dim": int(dim), "nq": int(nq), "k": k,
-                      "fanout": wl.fanout, "h": ix.info()["h"], "precision": prec, "tuning": tuning},
+                      "fanout": ix.info()["fanout"], "h": ix.info()["h"], "precision": prec, "tuning": tuning,
+                      "shapes_timed": shapes},
            "build_s": round(build_s, 3), "rebuild_s": round(rebuild_s, 3),
            "gpu_launches": int(launches), "stage_ms_per_step": {kk: round(v, 4) for kk, v in stage_ms.items()},
            "counters_per_step": {**{kk: v for kk, v in stats0.items() if not isinstance(v, dict)},

@@ -1302,6 +1302,179 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 // in rlist and get it from k_recheck_keys (a thread per candidate: the
 // sequential FP64 sums then keep every lane of the FP64 pipe busy).  PASS 1:
 // step B (and, for edit distance, the keys from the exact distances).
+// Warp-per-query forms of the two selection steps of k_knn_merge for k <= 32
+// (a block per query spends most of its time in barriers at these sizes).
+//  Step A: U = the k-th smallest upper bound over answer + candidates (k
+//  rounds at most: the smallest value above the last one and its
+//  multiplicity), then every candidate whose lower bound is <= U is listed
+//  for its FP64 key -- the same U and the same list as the block form.
+constexpr int kBoundStage = 1024;   // candidate bounds a warp stages in shared memory
+
+template <int METRIC>
+__global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int32_t *__restrict__ cq,
+                                                        const float *__restrict__ cdist, int64_t C,
+                                                        const int32_t *__restrict__ kq,
+                                                        const int64_t *__restrict__ koff,
+                                                        const double *__restrict__ bd,
+                                                        const int32_t *__restrict__ bn, double *__restrict__ ckey,
+                                                        int64_t *__restrict__ rlist,
+                                                        unsigned long long *__restrict__ rcount,
+                                                        const float *__restrict__ chi, int64_t nq) {
+    __shared__ uint32_t sx[8][kBoundStage];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    const int64_t a = lower_bound_i32(cq, 0, C, (int32_t)q);
+    const int64_t b = lower_bound_i32(cq, a, C, (int32_t)q + 1);
+    if (a == b) return;
+    const int64_t M = b - a;
+    const int K = kq[q];
+    const int nb = bn[q];
+    const float up = 1.f + 2.f * d.rel, dn = 1.f - 2.f * d.rel;
+    // upper bounds as float bits (x >= +0: bit order is value order)
+    auto cand_bits = [&](int64_t i) -> uint32_t {
+        return __float_as_uint(chi ? chi[a + i] + d.absf : cdist[a + i] * up + d.absf);
+    };
+    uint32_t U = 0x7f800000u;
+    if ((int64_t)nb + M > K) {
+        // the answer's bounds, one per lane (nb <= k <= 32), formed once
+        uint32_t ans = 0xffffffffu;
+        if (lane < nb) {
+            const double v = bd[koff[q] + lane];
+            const double ex = d.cosine ? __dsqrt_ru(__dmul_ru(2.0, v)) : (METRIC == GTS_L2 ? __dsqrt_rn(v) : v);
+            ans = __float_as_uint(__double2float_ru(ex) + (d.cosine ? d.absf : 0.f));
+        }
+        const bool staged = M <= kBoundStage;
+        if (staged)
+            for (int64_t i = lane; i < M; i += 32) sx[w][i] = cand_bits(i);
+        __syncwarp();
+        auto val = [&](int64_t i) -> uint32_t { return staged ? sx[w][i] : cand_bits(i); };
+        int remaining = K;
+        bool first = true;
+        uint32_t prev = 0;
+        for (;;) {
+            uint32_t mn = lane < nb && (first || ans > prev) ? ans : 0xffffffffu;
+            for (int64_t i = lane; i < M; i += 32) {
+                const uint32_t x = val(i);
+                if ((first || x > prev) && x < mn) mn = x;
+            }
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            if (mn == 0xffffffffu) break;
+            unsigned cnt = lane < nb && ans == mn ? 1u : 0u;
+            for (int64_t i = lane; i < M; i += 32) cnt += val(i) == mn ? 1u : 0u;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if ((int)cnt >= remaining) {
+                U = mn;
+                break;
+            }
+            remaining -= (int)cnt;
+            prev = mn;
+            first = false;
+        }
+    }
+    const float Uf = __uint_as_float(U);
+    for (int64_t i = lane; i < M; i += 32) {
+        const float dv = cdist[a + i];
+        ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
+        if ((chi ? dv : dv * dn) - d.absf <= Uf && dv != __int_as_float(0x7f800000))
+            rlist[atomicAdd(rcount, 1ull)] = a + i;
+    }
+}
+
+//  Step B: the first min(k, finite keys) in (key, id) order over answer +
+//  candidates with an FP64 key, when there are at most 64 of them (staged in
+//  shared memory, then a warp bitonic sort, two entries per lane); a query
+//  with more is flagged in `more` for the block form, untouched.
+constexpr int kSelWarpCap = 64;
+
+__device__ __forceinline__ bool key_id_less(uint64_t ka, int64_t ia, uint64_t kb, int64_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+template <int METRIC>
+__global__ void __launch_bounds__(256) k_knn_select_warp(Dev d, const int32_t *__restrict__ cq,
+                                                         const int32_t *__restrict__ crow, int64_t C,
+                                                         const int32_t *__restrict__ kq,
+                                                         const int64_t *__restrict__ koff, double *__restrict__ bd,
+                                                         int64_t *__restrict__ bi, int32_t *__restrict__ bn,
+                                                         const double *__restrict__ ckey, int64_t nq,
+                                                         uint8_t *__restrict__ more) {
+    __shared__ uint64_t sk[8][kSelWarpCap];
+    __shared__ int64_t si[8][kSelWarpCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    if (lane == 0) more[q] = 0;
+    const int64_t a = lower_bound_i32(cq, 0, C, (int32_t)q);
+    const int64_t b = lower_bound_i32(cq, a, C, (int32_t)q + 1);
+    if (a == b) return;
+    const int64_t M = b - a;
+    const int K = kq[q];
+    const int nb = bn[q];
+    double *BD = bd + koff[q];
+    int64_t *BI = bi + koff[q];
+    const uint64_t INF = 0x7ff0000000000000ull;
+    const int64_t n = (int64_t)nb + M;
+    int total = 0;
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t i = base + lane;
+        uint64_t v = INF;
+        if (i < n) v = i < nb ? dbits(BD[i]) : dbits(ckey[a + i - nb]);
+        const bool fin = v < INF;
+        const unsigned bal = __ballot_sync(0xffffffffu, fin);
+        const int slot = total + __popc(bal & ((1u << lane) - 1u));
+        if (fin && slot < kSelWarpCap) {
+            sk[w][slot] = v;
+            si[w][slot] = i < nb ? BI[i] : row_oid(d, crow[a + i - nb]);
+        }
+        total += __popc(bal);
+    }
+    if (total > kSelWarpCap) {
+        if (lane == 0) more[q] = 1;
+        return;
+    }
+    __syncwarp();
+    uint64_t k0 = lane < total ? sk[w][lane] : ~0ull, k1 = lane + 32 < total ? sk[w][lane + 32] : ~0ull;
+    int64_t i0 = lane < total ? si[w][lane] : INT64_MAX, i1 = lane + 32 < total ? si[w][lane + 32] : INT64_MAX;
+    // bitonic sort of the 64 entries e = lane + 32 r by (key, id), ascending
+    for (int k2 = 2; k2 <= 64; k2 <<= 1) {
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            if (j == 32) {   // (only with k2 = 64: ascending) entries lane and lane + 32
+                if (key_id_less(k1, i1, k0, i0)) {
+                    const uint64_t tk = k0;
+                    k0 = k1;
+                    k1 = tk;
+                    const int64_t ti = i0;
+                    i0 = i1;
+                    i1 = ti;
+                }
+                continue;
+            }
+            const bool lower = (lane & j) == 0;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                uint64_t &kr = r ? k1 : k0;
+                int64_t &ir = r ? i1 : i0;
+                const int e = lane + 32 * r;
+                const bool asc = (e & k2) == 0;
+                const uint64_t pk = __shfl_xor_sync(0xffffffffu, kr, j);
+                const int64_t pi = __shfl_xor_sync(0xffffffffu, ir, j);
+                const bool take_other = lower == asc ? key_id_less(pk, pi, kr, ir) : key_id_less(kr, ir, pk, pi);
+                if (take_other) {
+                    kr = pk;
+                    ir = pi;
+                }
+            }
+        }
+    }
+    const int take = total < K ? total : K;   // <= 32: entries 0 .. take - 1 are every lane's first
+    if (lane < take) {
+        BD[lane] = __longlong_as_double((long long)k0);
+        BI[lane] = i0;
+    }
+    if (lane == 0) bn[q] = take;
+}
+
 // Tensor-core tile estimates to distance intervals: from the tile's q.x~,
 // d~^2 = (|q|^2 + |x|^2) - 2 q.x~ (the tile's own operation order) is within
 // E = cE1 |q||x| + cE2 (|q| + |x|)^2 of d^2 (the tile kernel's bound, taken
@@ -1331,7 +1504,8 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
                             const float *__restrict__ cdist, int64_t C, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
                             int32_t *__restrict__ bn, double *__restrict__ ckey, int64_t *__restrict__ rlist,
-                            unsigned long long *__restrict__ rcount, const float *__restrict__ chi) {
+                            unsigned long long *__restrict__ rcount, const float *__restrict__ chi,
+                            const uint8_t *__restrict__ only) {
     __shared__ unsigned hist[256];
     __shared__ int64_t sh[4];
     __shared__ int64_t red[kWarpsPerBlock];
@@ -1339,6 +1513,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     __shared__ int64_t ki[kKeepCap];
     __shared__ int nkeep;
     const int32_t q = blockIdx.x;
+    if (only && !only[q]) return;   // (the warp kernel finished this query)
     const int64_t a = lower_bound_i32(cq, 0, C, q);
     const int64_t b = lower_bound_i32(cq, a, C, q + 1);
     if (a == b) return;
@@ -2920,7 +3095,7 @@ struct Runner {
         if (d.metric == GTS_EDIT) {
             k_knn_merge<GTS_EDIT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
                                                           bd.get(), bi.get(), bn.get(), ckey.get(), nullptr, nullptr,
-                                                          nullptr);
+                                                          nullptr, nullptr);
         } else {
             // step A lists the candidates that need an FP64 key, a thread per
             // candidate computes it, step B selects; the list's length is
@@ -2928,16 +3103,29 @@ struct Runner {
             DBuf<int64_t> rlist(R, st);
             DBuf<unsigned long long> rc(1, st);
             GTS_CUDA(cudaMemsetAsync(rc.get(), 0, 8, st));
+            // k <= 32: a warp per query for both selection steps (step B falls
+            // back to the block form for a query with more than 64 keys)
+            const bool warp_sel = qb.max_k <= 32;
+            const unsigned wgrid = (unsigned)((qb.nq + 7) / 8);
+            DBuf<uint8_t> more(warp_sel ? qb.nq : 1, st);
 #define GTS_MERGE(MT)                                                                                            \
     do {                                                                                                         \
-        k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
-                                                bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get(),  \
-                                                chi);                                                             \
+        if (warp_sel)                                                                                            \
+            k_knn_bound_warp<MT><<<wgrid, 256, 0, st>>>(d, kq2.get(), kd2.get(), R, qb.k, koff.get(), bd.get(),  \
+                                                        bn.get(), ckey.get(), rlist.get(), rc.get(), chi, qb.nq); \
+        else                                                                                                     \
+            k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(), \
+                                                    bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(),      \
+                                                    rc.get(), chi, nullptr);                                     \
         k_recheck_keys<MT><<<cap(nblocks(R, kT)), kT, 0, st>>>(d, kq2.get(), krow2.get(), rlist.get(), rc.get(), \
                                                               ckey.get());                                     \
+        if (warp_sel)                                                                                            \
+            k_knn_select_warp<MT><<<wgrid, 256, 0, st>>>(d, kq2.get(), krow2.get(), R, qb.k, koff.get(),         \
+                                                         bd.get(), bi.get(), bn.get(), ckey.get(), qb.nq,        \
+                                                         more.get());                                            \
         k_knn_merge<MT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
                                                 bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get(),  \
-                                                chi);                                                             \
+                                                chi, warp_sel ? more.get() : nullptr);                            \
         k_add_u64<<<1, 1, 0, st>>>(rc.get(), counters.get());                                                   \
     } while (0)
             if (d.metric == GTS_L2) GTS_MERGE(GTS_L2);

@@ -14,7 +14,7 @@ times, checked against the CPU oracle (brute force, FP64 or exact integers):
   sequence number, on every path.
 * wordvec_200000x300_cos_knn10 (2 * 10^5 x 300, angular distance, k = 10):
   1,024 of the 10,000 queries, drawn at random, with their FP64 keys, on the
-  BF16 path after autotuning and on the plain FP32 path.
+  BF16 path after the shape and launch autotuners and on the plain FP32 path.
 * uniform_2Mx256_l1 (2 * 10^6 x 256 L1): 256 kNN queries (random and the
   largest k) and 256 range queries (random and the most answers) of the mixed
   batch; then the serving loop under 20,000 Poisson arrivals at 50,000/s and
@@ -98,6 +98,7 @@ def test_wordvec_full_size(env):
     Qd = torch.from_numpy(wl.queries).cuda()
     idx = _pick(wl.nq, 1024, [], seed=103)
     want = oracle.knn_query("cos", wl.objects, wl.queries[idx], 10)
+    ix.autotune_shape(Qd[:2000], k=10, precision="bf16", candidates=4, reps=1)   # as bench.py does
     ix.autotune(Qd, k=wl.k, precision="bf16", reps=2)
     for prec in ("bf16", "fp32"):
         r = ix.knn(Qd, 10, precision=prec, keys=True)
