@@ -1878,6 +1878,9 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
     __shared__ float4 sph[32];
     __shared__ float2 spl[32];
     __shared__ unsigned long long s_ne;
+    // the same children in order, for the sorted form (below)
+    __shared__ float s_hi[64], s_lo[64];
+    __shared__ int s_sorted, s_j0;
     const int lane = threadIdx.x & 31;
     const float epsc = d.epsc;
     unsigned long long nmem = 0, nlive = 0;
@@ -1903,9 +1906,37 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
             h4[j & 1] = hi;
             h4[2 + (j & 1)] = fabsf(hi);
             l2[j & 1] = lo;
+            s_hi[j] = hi;
+            s_lo[j] = lo;
         }
         __syncthreads();
         const uint64_t nonempty = s_ne;
+        // Sorted form: the build cuts a node's rows, in ascending distance to
+        // its pivot, into consecutive children, so the non-empty children
+        // are a suffix whose [lo, hi] rise with j.  Then the children that
+        // pass the test with one eps >= every child's (the one of the largest
+        // hi) are the range [ja, jb] found by two binary searches -- a
+        // superset of the per-child test's, so no surviving leaf is lost.
+        // Checked per node; a node that is not so ordered takes the per-child
+        // test.
+        if (threadIdx.x < 32) {
+            bool bad = false;
+            for (int j = threadIdx.x; j + 1 < d.F; j += 32) {
+                const bool ne0 = (nonempty >> j) & 1ull, ne1 = (nonempty >> (j + 1)) & 1ull;
+                if (ne0 && (!ne1 || s_hi[j] > s_hi[j + 1] || s_lo[j] > s_lo[j + 1] || s_lo[j] < 0.f ||
+                            s_hi[j] < s_lo[j]))
+                    bad = true;
+            }
+            bad = __any_sync(0xffffffffu, bad);
+            if (threadIdx.x == 0) {
+                s_sorted = !bad && nonempty != 0ull && s_hi[d.F - 1] >= s_lo[d.F - 1];
+                s_j0 = nonempty ? __ffsll((long long)nonempty) - 1 : d.F;
+            }
+        }
+        __syncthreads();
+        const bool sorted = s_sorted != 0;
+        const int j0 = s_j0;
+        const float himax = s_hi[d.F - 1];
         for (int64_t q0 = 0; q0 < nq; q0 += blockDim.x) {
             const int64_t q = q0 + threadIdx.x;                          // column position
             const int64_t qq = q < nq && perm ? (int64_t)perm[q] : q;    // its query
@@ -1923,24 +1954,47 @@ __global__ void k_leaf_dense(Dev d, const float *__restrict__ DT, const uint64_t
                 // and are never -0 (eps >= +0, so hi + eps and sq + eps are
                 // not -0).
                 const float u = dq - thr, sq = dq + thr;
-                const float2 u2 = make_float2(u, u), sq2 = make_float2(sq, sq);
-                const float2 ec2 = make_float2(epsc, epsc);
-                const float2 lab2 = make_float2(d.lslack[d.h - 1], d.lslack[d.h - 1]);
-                uint64_t fail = 0;
+                if (sorted) {
+                    const float eps = (epsc > 0.f ? epsc * (sq + himax) : 0.f) + d.lslack[d.h - 1];
+                    // ja: the first child with (hi + eps) - u >= +0; jb + 1: the
+                    // first with (sq + eps) - lo < 0 (sign bits, as below)
+                    int a0 = j0, a1 = d.F;
+                    while (a0 < a1) {
+                        const int mid = (a0 + a1) >> 1;
+                        if (__float_as_uint((s_hi[mid] + eps) - u) >> 31) a0 = mid + 1;
+                        else a1 = mid;
+                    }
+                    const int ja = a0;
+                    a0 = j0;
+                    a1 = d.F;
+                    while (a0 < a1) {
+                        const int mid = (a0 + a1) >> 1;
+                        if (__float_as_uint((sq + eps) - s_lo[mid]) >> 31) a1 = mid;
+                        else a0 = mid + 1;
+                    }
+                    const int jb = a0 - 1;
+                    if (ja <= jb)
+                        m = ((jb >= 63) ? ~0ull : ((1ull << (jb + 1)) - 1ull)) & ~((1ull << ja) - 1ull) & nonempty;
+                } else {
+                    const float2 u2 = make_float2(u, u), sq2 = make_float2(sq, sq);
+                    const float2 ec2 = make_float2(epsc, epsc);
+                    const float2 lab2 = make_float2(d.lslack[d.h - 1], d.lslack[d.h - 1]);
+                    uint64_t fail = 0;
 #pragma unroll 2
-                for (int j = 0; j < d.F; j += 2) {
-                    const float4 h = sph[j >> 1];
-                    const float2 lo = spl[j >> 1];
-                    const float2 eps = add2f(epsc > 0.f ? mul2f(ec2, add2f(sq2, make_float2(h.z, h.w)))
-                                                        : make_float2(0.f, 0.f),
-                                             lab2);
-                    const float2 d1 = sub2f(add2f(make_float2(h.x, h.y), eps), u2);
-                    const float2 d2 = sub2f(add2f(sq2, eps), lo);
-                    const uint32_t f0 = (__float_as_uint(d1.x) | __float_as_uint(d2.x)) >> 31;
-                    const uint32_t f1 = (__float_as_uint(d1.y) | __float_as_uint(d2.y)) >> 31;
-                    fail |= (uint64_t)(f0 | (f1 << 1)) << j;
+                    for (int j = 0; j < d.F; j += 2) {
+                        const float4 h = sph[j >> 1];
+                        const float2 lo = spl[j >> 1];
+                        const float2 eps = add2f(epsc > 0.f ? mul2f(ec2, add2f(sq2, make_float2(h.z, h.w)))
+                                                            : make_float2(0.f, 0.f),
+                                                 lab2);
+                        const float2 d1 = sub2f(add2f(make_float2(h.x, h.y), eps), u2);
+                        const float2 d2 = sub2f(add2f(sq2, eps), lo);
+                        const uint32_t f0 = (__float_as_uint(d1.x) | __float_as_uint(d2.x)) >> 31;
+                        const uint32_t f1 = (__float_as_uint(d1.y) | __float_as_uint(d2.y)) >> 31;
+                        fail |= (uint64_t)(f0 | (f1 << 1)) << j;
+                    }
+                    m = ~fail & nonempty;
                 }
-                m = ~fail & nonempty;
             }
             if (q < nq) M[p * nq + q] = m;
             const unsigned live = __ballot_sync(0xffffffffu, m != 0ull);
