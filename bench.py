@@ -59,6 +59,11 @@ ALU_LANES_PER_SM = 64         # integer / bit-logic ALU pipe: 2 warp instruction
 # query leaf-mask matrix and the kept pairs' q.x), all of which double at full
 # size.  None once the kernel has changed since the counters were taken.
 TRAFFIC = {"kernel": "tile", "bytes_per_launch": 0.934e9}
+# the zipf2d table scan (k_scan_warps, fused range form): DRAM read + write of
+# one launch over a 10,000-query batch from its ncu capture
+# (profiles/scan_warps_zipf2d_10M.md), 227.1 + 101.6 MB.  None once the kernel
+# changes.
+SCAN_TRAFFIC = 328.7e6
 
 # ALU-pipe thread instructions per full-DP-equivalent cell (|q| x |o| per pair)
 # of the bit-parallel edit-distance kernels: sm__inst_executed_pipe_alu.sum x 32
@@ -602,8 +607,9 @@ def bench_zipf2d(args):
         gbs = scan_bytes / (scan_ms / 1e3) / 1e9
         scan_roof = {"bound": "hbm", "kernel": "k_scan_warps (stage leaf_scan)", "achieved": round(gbs, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "peak_source": hsrc,
-                     "bytes_per_launch": int(scan_bytes), "ms_per_launch": round(scan_ms / max(1.0, stage_launch.get("leaf_scan", 1.0)), 4),
-                     "traffic": None}
+                     "bytes_per_launch": int(scan_bytes),
+                     "ms_per_launch": round(scan_ms / max(1.0, stage_launch.get("leaf_scan", 1.0)), 4),
+                     "traffic": SCAN_TRAFFIC}
     out = {"metric": "range queries/s at oracle-exact results (L2, ~0.01% selectivity, 10% stream updates "
                      "and a 500,000-point batch update inside the timed region)",
            "value": round(10 * nb / (ms / 1e3), 1), "unit": "queries/s", "steps": 10, "warmup": args.warmup,

@@ -1302,6 +1302,13 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 // in rlist and get it from k_recheck_keys (a thread per candidate: the
 // sequential FP64 sums then keep every lane of the FP64 pipe busy).  PASS 1:
 // step B (and, for edit distance, the keys from the exact distances).
+// the first index of each query's run in the query-sorted candidates (and C
+// at nq): one binary search per query, shared by the selection kernels
+__global__ void k_query_runs(const int32_t *__restrict__ cq, int64_t C, int64_t nq, int64_t *__restrict__ qoff) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= nq; q += (int64_t)gridDim.x * blockDim.x)
+        qoff[q] = q == nq ? C : lower_bound_i32(cq, 0, C, (int32_t)q);
+}
+
 // Warp-per-query forms of the two selection steps of k_knn_merge for k <= 32
 // (a block per query spends most of its time in barriers at these sizes).
 //  Step A: U = the k-th smallest upper bound over answer + candidates (k
@@ -1311,7 +1318,7 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 constexpr int kBoundStage = 1024;   // candidate bounds a warp stages in shared memory
 
 template <int METRIC>
-__global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int32_t *__restrict__ cq,
+__global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int64_t *__restrict__ qoff,
                                                         const float *__restrict__ cdist, int64_t C,
                                                         const int32_t *__restrict__ kq,
                                                         const int64_t *__restrict__ koff,
@@ -1324,8 +1331,7 @@ __global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int32_t *__
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (q >= nq) return;
-    const int64_t a = lower_bound_i32(cq, 0, C, (int32_t)q);
-    const int64_t b = lower_bound_i32(cq, a, C, (int32_t)q + 1);
+    const int64_t a = qoff[q], b = qoff[q + 1];
     if (a == b) return;
     const int64_t M = b - a;
     const int K = kq[q];
@@ -1373,11 +1379,26 @@ __global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int32_t *__
         }
     }
     const float Uf = __uint_as_float(U);
-    for (int64_t i = lane; i < M; i += 32) {
+    // the candidates whose lower bound reaches U: counted first, then one
+    // atomic per warp reserves their places in the list (a counter that every
+    // warp hits once per candidate serialises)
+    auto listed = [&](int64_t i) -> bool {
         const float dv = cdist[a + i];
-        ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
-        if ((chi ? dv : dv * dn) - d.absf <= Uf && dv != __int_as_float(0x7f800000))
-            rlist[atomicAdd(rcount, 1ull)] = a + i;
+        return (chi ? dv : dv * dn) - d.absf <= Uf && dv != __int_as_float(0x7f800000);
+    };
+    unsigned cnt = 0;
+    for (int64_t i = lane; i < M; i += 32) cnt += listed(i) ? 1u : 0u;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(rcount, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int64_t i0 = 0; i0 < M; i0 += 32) {
+        const int64_t i = i0 + lane;
+        const bool l = i < M && listed(i);
+        if (i < M) ckey[a + i] = __longlong_as_double(0x7ff0000000000000ll);   // +inf: not a candidate
+        const unsigned bal = __ballot_sync(0xffffffffu, l);
+        if (l) rlist[base + __popc(bal & ((1u << lane) - 1u))] = a + i;
+        base += __popc(bal);
     }
 }
 
@@ -1392,7 +1413,7 @@ __device__ __forceinline__ bool key_id_less(uint64_t ka, int64_t ia, uint64_t kb
 }
 
 template <int METRIC>
-__global__ void __launch_bounds__(256) k_knn_select_warp(Dev d, const int32_t *__restrict__ cq,
+__global__ void __launch_bounds__(256) k_knn_select_warp(Dev d, const int64_t *__restrict__ qoff,
                                                          const int32_t *__restrict__ crow, int64_t C,
                                                          const int32_t *__restrict__ kq,
                                                          const int64_t *__restrict__ koff, double *__restrict__ bd,
@@ -1405,8 +1426,7 @@ __global__ void __launch_bounds__(256) k_knn_select_warp(Dev d, const int32_t *_
     const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (q >= nq) return;
     if (lane == 0) more[q] = 0;
-    const int64_t a = lower_bound_i32(cq, 0, C, (int32_t)q);
-    const int64_t b = lower_bound_i32(cq, a, C, (int32_t)q + 1);
+    const int64_t a = qoff[q], b = qoff[q + 1];
     if (a == b) return;
     const int64_t M = b - a;
     const int K = kq[q];
@@ -1500,7 +1520,7 @@ __global__ void k_tile_intervals(const int32_t *__restrict__ cq, const int32_t *
 // i's distance lies in [cdist[i], chi[i]] instead of within the FP32 band of
 // cdist[i].
 template <int METRIC, int PASS>
-__global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
+__global__ void k_knn_merge(Dev d, const int64_t *__restrict__ qoff, const int32_t *__restrict__ crow,
                             const float *__restrict__ cdist, int64_t C, const int32_t *__restrict__ kq,
                             const int64_t *__restrict__ koff, double *__restrict__ bd, int64_t *__restrict__ bi,
                             int32_t *__restrict__ bn, double *__restrict__ ckey, int64_t *__restrict__ rlist,
@@ -1514,8 +1534,7 @@ __global__ void k_knn_merge(Dev d, const int32_t *__restrict__ cq, const int32_t
     __shared__ int nkeep;
     const int32_t q = blockIdx.x;
     if (only && !only[q]) return;   // (the warp kernel finished this query)
-    const int64_t a = lower_bound_i32(cq, 0, C, q);
-    const int64_t b = lower_bound_i32(cq, a, C, q + 1);
+    const int64_t a = qoff[q], b = qoff[q + 1];
     if (a == b) return;
     const int64_t M = b - a;
     const int K = kq[q];
@@ -1734,8 +1753,10 @@ __global__ void k_cm_scatter(const int32_t *__restrict__ eq, const int32_t *__re
 constexpr int kTauUnroll = 4;   // pivots per lane whose loads k_tau_dense issues together
 
 // member(node, q): the node's bit in its parent's child mask for q
+// (node indices of one level fit 32 bits: a 32-bit division, far cheaper than a 64-bit one)
 __device__ __forceinline__ bool dense_member(const uint64_t *cm, int64_t node, int64_t q, int64_t nq, int F) {
-    return (cm[(node / F) * nq + q] >> (node % F)) & 1ull;
+    const uint32_t nu = (uint32_t)node, par = nu / (uint32_t)F, rem = nu - par * (uint32_t)F;
+    return (cm[(int64_t)par * nq + q] >> rem) & 1ull;
 }
 
 // kNN threshold from this level's pivots (warp per query; the same candidates
@@ -3145,9 +3166,11 @@ struct Runner {
                    const float *chi = nullptr) {
         DBuf<double> ckey(R, st);
         const unsigned grid = (unsigned)qb.nq;
-        clk.begin(GTS_STAGE_SELECT, 4);
+        DBuf<int64_t> qoff(qb.nq + 1, st);
+        clk.begin(GTS_STAGE_SELECT, 5);
+        k_query_runs<<<cap(nblocks(qb.nq + 1, kT)), kT, 0, st>>>(kq2.get(), R, qb.nq, qoff.get());
         if (d.metric == GTS_EDIT) {
-            k_knn_merge<GTS_EDIT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
+            k_knn_merge<GTS_EDIT, 1><<<grid, kT, 0, st>>>(d, qoff.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),
                                                           bd.get(), bi.get(), bn.get(), ckey.get(), nullptr, nullptr,
                                                           nullptr, nullptr);
         } else {
@@ -3165,19 +3188,19 @@ struct Runner {
 #define GTS_MERGE(MT)                                                                                            \
     do {                                                                                                         \
         if (warp_sel)                                                                                            \
-            k_knn_bound_warp<MT><<<wgrid, 256, 0, st>>>(d, kq2.get(), kd2.get(), R, qb.k, koff.get(), bd.get(),  \
+            k_knn_bound_warp<MT><<<wgrid, 256, 0, st>>>(d, qoff.get(), kd2.get(), R, qb.k, koff.get(), bd.get(),  \
                                                         bn.get(), ckey.get(), rlist.get(), rc.get(), chi, qb.nq); \
         else                                                                                                     \
-            k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(), \
+            k_knn_merge<MT, 0><<<grid, kT, 0, st>>>(d, qoff.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(), \
                                                     bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(),      \
                                                     rc.get(), chi, nullptr);                                     \
         k_recheck_keys<MT><<<cap(nblocks(R, kT)), kT, 0, st>>>(d, kq2.get(), krow2.get(), rlist.get(), rc.get(), \
                                                               ckey.get());                                     \
         if (warp_sel)                                                                                            \
-            k_knn_select_warp<MT><<<wgrid, 256, 0, st>>>(d, kq2.get(), krow2.get(), R, qb.k, koff.get(),         \
+            k_knn_select_warp<MT><<<wgrid, 256, 0, st>>>(d, qoff.get(), krow2.get(), R, qb.k, koff.get(),         \
                                                          bd.get(), bi.get(), bn.get(), ckey.get(), qb.nq,        \
                                                          more.get());                                            \
-        k_knn_merge<MT, 1><<<grid, kT, 0, st>>>(d, kq2.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
+        k_knn_merge<MT, 1><<<grid, kT, 0, st>>>(d, qoff.get(), krow2.get(), kd2.get(), R, qb.k, koff.get(),     \
                                                 bd.get(), bi.get(), bn.get(), ckey.get(), rlist.get(), rc.get(),  \
                                                 chi, warp_sel ? more.get() : nullptr);                            \
         k_add_u64<<<1, 1, 0, st>>>(rc.get(), counters.get());                                                   \
