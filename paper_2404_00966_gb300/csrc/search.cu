@@ -349,18 +349,24 @@ struct TauList {
     }
 };
 
+// the first index of each query's run in the query-sorted entries or candidates
+// (and C at nq): one binary search per query, shared by the selection kernels
+__global__ void k_query_runs(const int32_t *__restrict__ cq, int64_t C, int64_t nq, int64_t *__restrict__ qoff) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= nq; q += (int64_t)gridDim.x * blockDim.x)
+        qoff[q] = q == nq ? C : lower_bound_i32(cq, 0, C, (int32_t)q);
+}
+
 // Warp per query.  The query's list of the k smallest (upper bound, id) of
 // distinct visible pivots seen so far is merged with this level's entries;
 // tau_q = the k-th bound, rounded up to float, or +inf while fewer than k.
-__global__ void k_tau(Dev d, const int32_t *__restrict__ eq, const int32_t *__restrict__ enode, int64_t lvl_base,
+__global__ void k_tau(Dev d, const int64_t *__restrict__ qrun, const int32_t *__restrict__ enode, int64_t lvl_base,
                       int64_t e0, int64_t e1, const float *__restrict__ path, int l, int64_t nq,
                       const int32_t *__restrict__ kq, const int64_t *__restrict__ koff, double *tk_d, int64_t *tk_id,
                       int32_t *tk_n, float *tau) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
-    const int64_t a = lower_bound_i32(eq, e0, e1, (int32_t)q);
-    const int64_t b = lower_bound_i32(eq, a, e1, (int32_t)q + 1);
+    const int64_t a = e0 + qrun[q], b = e0 + qrun[q + 1];
     if (a == b) continue;
     const int K = kq[q];
     TauList L;
@@ -1302,13 +1308,6 @@ __device__ __forceinline__ int64_t block_sum(int64_t v, int64_t *red) {
 // in rlist and get it from k_recheck_keys (a thread per candidate: the
 // sequential FP64 sums then keep every lane of the FP64 pipe busy).  PASS 1:
 // step B (and, for edit distance, the keys from the exact distances).
-// the first index of each query's run in the query-sorted candidates (and C
-// at nq): one binary search per query, shared by the selection kernels
-__global__ void k_query_runs(const int32_t *__restrict__ cq, int64_t C, int64_t nq, int64_t *__restrict__ qoff) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= nq; q += (int64_t)gridDim.x * blockDim.x)
-        qoff[q] = q == nq ? C : lower_bound_i32(cq, 0, C, (int32_t)q);
-}
-
 // Warp-per-query forms of the two selection steps of k_knn_merge for k <= 32
 // (a block per query spends most of its time in barriers at these sizes).
 //  Step A: U = the k-th smallest upper bound over answer + candidates (k
@@ -2342,7 +2341,8 @@ struct Runner {
             if (knn) {
                 const int64_t base = ix->tree.lvl_off[l];
                 clk.begin(GTS_STAGE_THRESHOLD);
-                k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+                k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, query_runs(L, e0, e1), L.node.get(), base,
+                                                                          e0, e1,
                                                                           L.path.get(), l, qb.nq, qb.k, koff.get(),
                                                                           tk_d.get(), tk_id.get(), tk_n.get(),
                                                                           thr.get());
@@ -2388,7 +2388,8 @@ struct Runner {
         st_frontier += E;
         if (knn) {
             clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1, L.path.get(),
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, query_runs(L, e0, e1), L.node.get(), base,
+                                                                          e0, e1, L.path.get(),
                                                                  l, qb.nq, qb.k, koff.get(), tk_d.get(), tk_id.get(),
                                                                  tk_n.get(), thr.get());
             clk.end();
@@ -2558,7 +2559,8 @@ struct Runner {
                                                                   L.path.get(), h, l);
             clk.end();
             clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, query_runs(L, e0, e1), L.node.get(), base,
+                                                                          e0, e1,
                                                                       L.path.get(), l, qb.nq, qb.k, koff.get(),
                                                                       tk_d.get(), tk_id.get(), tk_n.get(), thr.get());
             clk.end();
@@ -2596,7 +2598,8 @@ struct Runner {
         st_frontier += E;
         if (knn && !tau_first) {
             clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, L.q.get(), L.node.get(), base, e0, e1,
+            k_tau<<<cap(nblocks(qb.nq, kWarpsPerBlock)), kT, 0, st>>>(d, query_runs(L, e0, e1), L.node.get(), base,
+                                                                          e0, e1,
                                                                       L.path.get(), l, qb.nq, qb.k, koff.get(),
                                                                       tk_d.get(), tk_id.get(), tk_n.get(), thr.get());
             clk.end();
@@ -3158,6 +3161,15 @@ struct Runner {
             rdists.push_back(std::move(rd));
             rcounts.push_back(R);
         }
+    }
+
+    // the first entry of each query's run among entries [e0, e1) of a
+    // query-sorted level (relative to e0), for the per-query threshold kernel
+    DBuf<int64_t> qrun_buf;
+    const int64_t *query_runs(Level &L, int64_t e0, int64_t e1) {
+        qrun_buf.alloc(qb.nq + 1, st);
+        k_query_runs<<<cap(nblocks(qb.nq + 1, kT)), kT, 0, st>>>(L.q.get() + e0, e1 - e0, qb.nq, qrun_buf.get());
+        return qrun_buf.get();
     }
 
     // merge R query-major (query, row, FP32 distance) candidates into the
