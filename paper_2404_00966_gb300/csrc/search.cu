@@ -1349,24 +1349,66 @@ __global__ void __launch_bounds__(256) k_knn_bound_warp(Dev d, const int64_t *__
             const double ex = d.cosine ? __dsqrt_ru(__dmul_ru(2.0, v)) : (METRIC == GTS_L2 ? __dsqrt_rn(v) : v);
             ans = __float_as_uint(__double2float_ru(ex) + (d.cosine ? d.absf : 0.f));
         }
-        const bool staged = M <= kBoundStage;
-        if (staged)
-            for (int64_t i = lane; i < M; i += 32) sx[w][i] = cand_bits(i);
+        // U' = the k-th smallest of the 32 lane minima: a subset's k-th
+        // smallest, so U' >= U, and every value <= U is <= U'.  Only those
+        // are staged (a few dozen, typically); the exact rounds run on them.
+        uint32_t lmin = lane < nb ? ans : 0xffffffffu;
+        for (int64_t i = lane; i < M; i += 32) lmin = min(lmin, cand_bits(i));
+        uint32_t srt = lmin;   // ascending across lanes (bitonic)
+        for (int k2 = 2; k2 <= 32; k2 <<= 1)
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                const uint32_t o = __shfl_xor_sync(0xffffffffu, srt, j);
+                const bool lower = (lane & j) == 0, asc = (lane & k2) == 0;
+                srt = lower == asc ? min(srt, o) : max(srt, o);
+            }
+        const uint32_t Up = __shfl_sync(0xffffffffu, srt, K - 1);
+        int ns = 0;   // values <= U' staged
+        {
+            const bool keep = lane < nb && ans <= Up;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) sx[w][__popc(bal & ((1u << lane) - 1u))] = ans;
+            ns = __popc(bal);
+        }
+        for (int64_t i0 = 0; i0 < M; i0 += 32) {
+            const int64_t i = i0 + lane;
+            const uint32_t x = i < M ? cand_bits(i) : 0xffffffffu;
+            const bool keep = i < M && x <= Up;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int slot = ns + __popc(bal & ((1u << lane) - 1u));
+            if (keep && slot < kBoundStage) sx[w][slot] = x;
+            ns += __popc(bal);
+        }
         __syncwarp();
-        auto val = [&](int64_t i) -> uint32_t { return staged ? sx[w][i] : cand_bits(i); };
+        const bool staged = ns <= kBoundStage;
+        // the k-th smallest over the staged values (or, past the stage's
+        // capacity, over every value): k rounds at most, each the smallest
+        // value above the last one and its multiplicity
         int remaining = K;
         bool first = true;
         uint32_t prev = 0;
         for (;;) {
-            uint32_t mn = lane < nb && (first || ans > prev) ? ans : 0xffffffffu;
-            for (int64_t i = lane; i < M; i += 32) {
-                const uint32_t x = val(i);
-                if ((first || x > prev) && x < mn) mn = x;
+            uint32_t mn = 0xffffffffu;
+            if (staged) {
+                for (int i = lane; i < ns; i += 32) {
+                    const uint32_t x = sx[w][i];
+                    if ((first || x > prev) && x < mn) mn = x;
+                }
+            } else {
+                if (lane < nb && (first || ans > prev)) mn = ans;
+                for (int64_t i = lane; i < M; i += 32) {
+                    const uint32_t x = cand_bits(i);
+                    if ((first || x > prev) && x < mn) mn = x;
+                }
             }
             mn = __reduce_min_sync(0xffffffffu, mn);
             if (mn == 0xffffffffu) break;
-            unsigned cnt = lane < nb && ans == mn ? 1u : 0u;
-            for (int64_t i = lane; i < M; i += 32) cnt += val(i) == mn ? 1u : 0u;
+            unsigned cnt = 0;
+            if (staged) {
+                for (int i = lane; i < ns; i += 32) cnt += sx[w][i] == mn ? 1u : 0u;
+            } else {
+                cnt = lane < nb && ans == mn ? 1u : 0u;
+                for (int64_t i = lane; i < M; i += 32) cnt += cand_bits(i) == mn ? 1u : 0u;
+            }
             cnt = __reduce_add_sync(0xffffffffu, cnt);
             if ((int)cnt >= remaining) {
                 U = mn;
