@@ -1791,6 +1791,7 @@ __global__ void k_cm_scatter(const int32_t *__restrict__ eq, const int32_t *__re
         cm[(int64_t)enode[e] * nq + eq[e]] = cmask[e - e0];
 }
 
+constexpr int64_t kDenseTcMinPivots = 2048;   // the smallest level whose dense matrix runs on the tensor cores
 constexpr int kTauUnroll = 4;   // pivots per lane whose loads k_tau_dense issues together
 
 // member(node, q): the node's bit in its parent's child mask for q
@@ -2338,7 +2339,10 @@ struct Runner {
     void level_matrix(int l, float *out) {
         const int64_t P = ix->tree.lvl_off[l + 1] - ix->tree.lvl_off[l];
         clk.begin(GTS_STAGE_PIVOT_DIST);
-        if (use_tc && tc_dense_supported(ix->tree, ix->tree.tc) && ix->tree.tc.piv_ready) {
+        // (levels of fewer than kDenseTcMinPivots pivots: the FP32 kernel, which
+        // needs no host round trip for the slack and is as fast at that size)
+        if (use_tc && P >= kDenseTcMinPivots && tc_dense_supported(ix->tree, ix->tree.tc) &&
+            ix->tree.tc.piv_ready) {
             d.lslack[l] = tc_dense_dist(ix->tree, ix->tree.tc, l, (const __nv_bfloat16 *)tcQh.get(),
                                         (const __nv_bfloat16 *)tcQl.get(), tcqn2.get(), d.Q, qb.nq, out, st);
         } else {
