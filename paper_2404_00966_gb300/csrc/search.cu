@@ -2685,29 +2685,6 @@ struct Runner {
         const int64_t base = ix->tree.lvl_off[ll];
         const int64_t P = ix->tree.lvl_off[h] - base;
         const int64_t Pp = base - ix->tree.lvl_off[ll - 1];
-        // the last level's distances (forced: the frontier is dense)
-        if (dense_state[ll] != 1) {
-            dense[ll].alloc(nq * P, st);
-            level_matrix(ll, dense[ll].get());
-            st_dense_pairs += nq * P;
-            dense_state[ll] = 1;
-        }
-        const float *D = dense[ll].get();
-        st_dense_last = 1;
-        DBuf<uint64_t> cm(Pp * nq, st);
-        GTS_CUDA(cudaMemsetAsync(cm.get(), 0, Pp * nq * 8, st));
-        clk.begin(GTS_STAGE_EXPAND);
-        k_cm_scatter<<<cap(nblocks(e1 - e0, kT)), kT, 0, st>>>(L.q.get(), L.node.get(), e0, e1, cmask.get(), nq,
-                                                               cm.get());
-        clk.end();
-        if (knn) {
-            clk.begin(GTS_STAGE_THRESHOLD);
-            k_tau_dense<<<wave_grid(k_tau_dense, nblocks(nq, kWarpsPerBlock), kT), kT, 0, st>>>(d, D, P, cm.get(), base, nq, qb.k,
-                                                                         koff.get(), tk_d.get(), tk_id.get(),
-                                                                         tk_n.get(), thr.get());
-            clk.end();
-            check_launch("dense knn threshold");
-        }
         // kNN: the tiles take the queries in the order of their probe keys, so
         // the windows of consecutive columns hold queries of one region (a
         // node's live columns cluster and whole windows drop out)
@@ -2733,7 +2710,44 @@ struct Runner {
             clk.end();
             check_launch("query order");
         }
+        // the last level's distances (forced: the frontier is dense), in query
+        // order (D) and transposed by position (DT); on the tensor cores both
+        // come from the one kernel
         DBuf<float> DT(nq * P, st);
+        bool have_dt = false;
+        if (dense_state[ll] != 1) {
+            dense[ll].alloc(nq * P, st);
+            if (use_tc && P >= kDenseTcMinPivots && tc_dense_supported(ix->tree, ix->tree.tc) &&
+                ix->tree.tc.piv_ready) {
+                clk.begin(GTS_STAGE_PIVOT_DIST);
+                d.lslack[ll] = tc_dense_dist(
+                    ix->tree, ix->tree.tc, ll, (const __nv_bfloat16 *)(perm.get() ? pQh.get() : tcQh.get()),
+                    (const __nv_bfloat16 *)(perm.get() ? pQl.get() : tcQl.get()), perm.get() ? pqn2.get() : tcqn2.get(),
+                    d.Q, nq, dense[ll].get(), st, perm.get(), DT.get());
+                clk.end();
+                have_dt = true;
+            } else {
+                level_matrix(ll, dense[ll].get());
+            }
+            st_dense_pairs += nq * P;
+            dense_state[ll] = 1;
+        }
+        const float *D = dense[ll].get();
+        st_dense_last = 1;
+        DBuf<uint64_t> cm(Pp * nq, st);
+        GTS_CUDA(cudaMemsetAsync(cm.get(), 0, Pp * nq * 8, st));
+        clk.begin(GTS_STAGE_EXPAND);
+        k_cm_scatter<<<cap(nblocks(e1 - e0, kT)), kT, 0, st>>>(L.q.get(), L.node.get(), e0, e1, cmask.get(), nq,
+                                                               cm.get());
+        clk.end();
+        if (knn) {
+            clk.begin(GTS_STAGE_THRESHOLD);
+            k_tau_dense<<<wave_grid(k_tau_dense, nblocks(nq, kWarpsPerBlock), kT), kT, 0, st>>>(d, D, P, cm.get(), base, nq, qb.k,
+                                                                         koff.get(), tk_d.get(), tk_id.get(),
+                                                                         tk_n.get(), thr.get());
+            clk.end();
+            check_launch("dense knn threshold");
+        }
         DBuf<uint64_t> M(nq * P, st);
         TcRegroup rg;
         rg.nw = (nq + 31) / 32;
@@ -2744,7 +2758,7 @@ struct Runner {
         clk.begin(GTS_STAGE_PIVOT_DIST, 2);
         {
             dim3 tb(32, 8), tg((unsigned)((P + 31) / 32), (unsigned)((nq + 31) / 32));
-            k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get(), perm.get());
+            if (!have_dt) k_transpose_f32<<<tg, tb, 0, st>>>(D, nq, P, DT.get(), perm.get());
             k_leaf_dense<<<wave_grid(k_leaf_dense, P, 256), 256, 0, st>>>(
                 d, DT.get(), cm.get(), P, nq, ix->tree.lvl_off[h], thr.get(), perm.get(), M.get(), rg.bits.get(),
                 rg.nw, cnt.get());

@@ -1193,7 +1193,12 @@ struct DenseTcArgs {
     int dim, dim_p;
     int64_t P, nq;
     float cE1, cE2;
-    float *out;                     // [nq, P]
+    float *out;                     // [nq, P]: out[query * P + p]
+    // optional: the columns (B rows) are positions, position j holding query
+    // perm[j] (null: j), and outT[p * nq + j] receives the same entries
+    // transposed (the layout of the dense leaf masks)
+    const int32_t *perm;
+    float *outT;
     unsigned *slack;                // the largest |d~ - d| bound written (float bits)
     int *status;
 };
@@ -1322,11 +1327,14 @@ __global__ void __launch_bounds__(256, 1)
             tc::tmem_ld32(tacc + tlane + (uint32_t)c0, v);
             tc::tmem_ld_wait();
             uint32_t redo = 0;   // entries near the pivot, recomputed below
+            float tv[32];        // this thread's 32 entries, for the transposed copy
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const int64_t q = q0 + c0 + i;
-                if (!pv || q >= a.nq) continue;
-                const float q2 = a.qn2[q], qn = a.qnu[q];
+                const int64_t j = q0 + c0 + i;   // column (position)
+                tv[i] = 0.f;
+                if (!pv || j >= a.nq) continue;
+                const int64_t q = a.perm ? (int64_t)a.perm[j] : j;
+                const float q2 = a.qn2[j], qn = a.qnu[j];
                 const float sn = __fadd_ru(pn, qn);
                 const float E = __fadd_ru(__fmul_ru(a.cE1, __fmul_ru(pn, qn)), __fmul_ru(2.f * a.cE2, __fmul_ru(sn, sn)));
                 const float d2 = fmaf(-2.f, __uint_as_float(v[i]), p2 + q2);
@@ -1347,13 +1355,29 @@ __global__ void __launch_bounds__(256, 1)
                     redo |= 1u << i;
                 } else {
                     if (!near) umax = fmaxf(umax, u);
-                    a.out[q * a.P + p] = near ? sqrtf(fmaxf(d2, 0.f)) : t;   // (near with no pivot: an empty node)
+                    const float val = near ? sqrtf(fmaxf(d2, 0.f)) : t;   // (near with no pivot: an empty node)
+                    a.out[q * a.P + p] = val;
+                    tv[i] = val;
+                }
+            }
+            if (a.outT && pv) {   // (entries recomputed below are rewritten there)
+                float *dst = a.outT + p * a.nq + q0 + c0;
+                const int64_t nv = a.nq - (q0 + c0) < 32 ? a.nq - (q0 + c0) : 32;
+                if (nv == 32 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4)
+                        *reinterpret_cast<float4 *>(dst + i) = make_float4(tv[i], tv[i + 1], tv[i + 2], tv[i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < nv) dst[i] = tv[i];
                 }
             }
             while (redo) {   // near the pivot: the sum of squared differences in FP32
                 const int i = __ffs(redo) - 1;
                 redo &= redo - 1;
-                const int64_t q = q0 + c0 + i;
+                const int64_t j = q0 + c0 + i;
+                const int64_t q = a.perm ? (int64_t)a.perm[j] : j;
                 const float *xr = a.X + (int64_t)prow * a.dim, *qr = a.Q + q * a.dim;
                 float sum = 0.f;
                 for (int k = 0; k < a.dim; ++k) {
@@ -1361,6 +1385,7 @@ __global__ void __launch_bounds__(256, 1)
                     sum = fmaf(d, d, sum);
                 }
                 a.out[q * a.P + p] = sqrtf(sum);
+                if (a.outT) a.outT[p * a.nq + j] = sqrtf(sum);
             }
         }
     }
@@ -1406,7 +1431,8 @@ void tc_prepare_pivots(const Tree &t, TcCache &c, cudaStream_t st) {
 }
 
 float tc_dense_dist(const Tree &t, const TcCache &c, int level, const __nv_bfloat16 *Qh, const __nv_bfloat16 *Ql,
-                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st) {
+                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st, const int32_t *perm,
+                    float *outT) {
     const int64_t base = t.lvl_off[level], P = t.lvl_off[level + 1] - base;
     if (P == 0 || nq == 0) return 0.f;
     const size_t smem = dense_tc_smem(c.dim_p);
@@ -1436,6 +1462,8 @@ float tc_dense_dist(const Tree &t, const TcCache &c, int level, const __nv_bfloa
     a.nq = nq;
     tc_bound_coeffs(c.dim_p, a.cE1, a.cE2);
     a.out = out;
+    a.perm = perm;
+    a.outT = outT;
     a.slack = slack.get();
     a.status = status.get();
     const dim3 grid((unsigned)((P + kRows - 1) / kRows), (unsigned)((nq + kDenseQ - 1) / kDenseQ));

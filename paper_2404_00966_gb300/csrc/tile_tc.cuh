@@ -135,11 +135,14 @@ int64_t tc_run(const Tree &t, const TcCache &c, const TcQuery &tq, const TcRegro
 // (dim_p <= 256, after tc_prepare and tc_prepare_pivots): out[q, p] for the
 // batch's split queries; returns the level's absolute slack, an upper bound of
 // |out - d| over the entries not recomputed in FP32 (those are within the FP32
-// relative bound)
+// relative bound).  With perm, the split queries (Qh, Ql, qn2) are in position
+// order, position j holding query perm[j]; outT (if given) receives the
+// matrix transposed by position, outT[p * nq + j].
 bool tc_dense_supported(const Tree &t, const TcCache &c);
 void tc_prepare_pivots(const Tree &t, TcCache &c, cudaStream_t st);
 float tc_dense_dist(const Tree &t, const TcCache &c, int level, const __nv_bfloat16 *Qh, const __nv_bfloat16 *Ql,
-                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st);
+                    const float *qn2, const float *Q, int64_t nq, float *out, cudaStream_t st,
+                    const int32_t *perm = nullptr, float *outT = nullptr);
 void tc_selftest(const float *hA, const float *hB, int N, int K, int a_tmem, float *hD);
 void wait_selftest(int post, uint32_t limit);
 
