@@ -205,15 +205,32 @@ void copy_small_to_device(const T *src, int64_t n, bool on_device, DBuf<T> &dst,
     }
 }
 
+__global__ void k_scatter_marks(int64_t *dst, const int64_t *pos, const int64_t *val, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[pos[i]] = val[i];
+}
+
+// loc[id] = tree row of every id after a build (-1: none), scattered on the
+// device and copied back in one transfer
+__global__ void k_loc_scatter(const int64_t *__restrict__ row_id, int64_t n, int64_t *__restrict__ loc) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        loc[row_id[r]] = r;
+}
+__global__ void k_fill_loc(int64_t *a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = -1;
+}
+
 void refresh_loc(gts_index *ix) {
     Tree &t = ix->tree;
-    std::vector<int64_t> ids(t.n);
-    if (t.n) {
-        GTS_CUDA(cudaMemcpyAsync(ids.data(), t.row_id.get(), t.n * 8, cudaMemcpyDeviceToHost, ix->stream));
-        GTS_CUDA(cudaStreamSynchronize(ix->stream));
-    }
+    cudaStream_t st = ix->stream;
     ix->loc.assign(ix->next_id, -1);
-    for (int64_t r = 0; r < t.n; ++r) ix->loc[ids[r]] = r;
+    if (t.n == 0 || ix->next_id == 0) return;
+    DBuf<int64_t> locd(ix->next_id, st);
+    k_fill_loc<<<std::min<int64_t>(nb(ix->next_id), 4096), kT, 0, st>>>(locd.get(), ix->next_id);
+    k_loc_scatter<<<std::min<int64_t>(nb(t.n), 4096), kT, 0, st>>>(t.row_id.get(), t.n, locd.get());
+    GTS_CUDA(cudaMemcpyAsync(ix->loc.data(), locd.get(), ix->next_id * 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
 }
 
 // ---------------------------------------------------------------- cache list
@@ -286,14 +303,25 @@ void cache_append(gts_index *ix, const DevObjects &o, int64_t *ids_out) {
 
 // ---------------------------------------------------------------- rebuild
 
-__global__ void k_visible_rows(const int64_t *row_del, const int64_t *row_id, int64_t n, int *flag, uint64_t *key,
-                               int64_t *val) {
+// sort keys of the tree rows: the id of a visible row, `none` (above every
+// id) for a deleted one
+__global__ void k_visible_rows(const int64_t *row_del, const int64_t *row_id, int64_t n, uint64_t none,
+                               uint64_t *key, int64_t *val) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const bool vis = row_del[r] == kNever;
-        flag[r] = vis ? 1 : 0;
-        key[r] = vis ? (uint64_t)row_id[r] : ~0ull;
+        key[r] = vis ? (uint64_t)row_id[r] : none;
         val[r] = r;
     }
+}
+// the number of keys below `none` in the sorted keys (a binary search)
+__global__ void k_count_below(const uint64_t *key, int64_t n, uint64_t none, int64_t *out) {
+    int64_t a = 0, b = n;
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (key[m] < none) a = m + 1;
+        else b = m;
+    }
+    *out = a;
 }
 
 __global__ void k_gather_vec_rows(const float *X, const float *cX, int dim, int64_t n_tree, const int64_t *src,
@@ -339,37 +367,47 @@ void rebuild(gts_index *ix) {
     cudaStream_t st = ix->stream;
     Tree &t = ix->tree;
     Cache &c = ix->cache;
-    // visible tree rows in id order, then visible cache slots (their ids are newer)
-    std::vector<int64_t> src;
-    src.reserve(t.n + c.count);
+    // visible tree rows in id order (sorted on the device by id, over the
+    // bits the ids use), then visible cache slots (their ids are newer)
+    int64_t vis = 0;
+    DBuf<int64_t> val2(t.n > 0 ? t.n : 1, st);
     if (t.n) {
-        DBuf<int> flag(t.n, st);
+        int idbits = 1;
+        while (idbits < 62 && ((int64_t)1 << idbits) <= ix->next_id) ++idbits;
+        const uint64_t none = (uint64_t)1 << idbits;
         DBuf<uint64_t> key(t.n, st), key2(t.n, st);
-        DBuf<int64_t> val(t.n, st), val2(t.n, st);
-        k_visible_rows<<<nb(t.n), kT, 0, st>>>(t.row_del.get(), t.row_id.get(), t.n, flag.get(), key.get(), val.get());
+        DBuf<int64_t> val(t.n, st), cnt(1, st);
+        k_visible_rows<<<nb(t.n), kT, 0, st>>>(t.row_del.get(), t.row_id.get(), t.n, none, key.get(), val.get());
         size_t tb = 0;
-        cub::DeviceRadixSort::SortPairs(nullptr, tb, key.get(), key2.get(), val.get(), val2.get(), t.n, 0, 64, st);
+        cub::DeviceRadixSort::SortPairs(nullptr, tb, key.get(), key2.get(), val.get(), val2.get(), t.n, 0,
+                                        idbits + 1, st);
         DBuf<uint8_t> tmp(tb, st);
         GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, key.get(), key2.get(), val.get(), val2.get(), t.n, 0,
-                                                 64, st));
-        std::vector<uint64_t> hk(t.n);
-        std::vector<int64_t> hv(t.n);
-        GTS_CUDA(cudaMemcpyAsync(hk.data(), key2.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
-        GTS_CUDA(cudaMemcpyAsync(hv.data(), val2.get(), t.n * 8, cudaMemcpyDeviceToHost, st));
+                                                 idbits + 1, st));
+        k_count_below<<<1, 1, 0, st>>>(key2.get(), t.n, none, cnt.get());
+        GTS_CUDA(cudaMemcpyAsync(&vis, cnt.get(), 8, cudaMemcpyDeviceToHost, st));
         GTS_CUDA(cudaStreamSynchronize(st));
-        for (int64_t i = 0; i < t.n; ++i)
-            if (hk[i] != ~0ull) src.push_back(hv[i]);
     }
+    std::vector<int64_t> csrc;   // visible cache slots, as sources t.n + slot
     if (c.count) {
         std::vector<int64_t> cdel(c.count);
         GTS_CUDA(cudaMemcpyAsync(cdel.data(), c.del.get(), c.count * 8, cudaMemcpyDeviceToHost, st));
         GTS_CUDA(cudaStreamSynchronize(st));
-        for (int64_t s = 0; s < c.count; ++s)
-            if (cdel[s] == kNever) src.push_back(t.n + s);
+        for (int64_t s2 = 0; s2 < c.count; ++s2)
+            if (cdel[s2] == kNever) csrc.push_back(t.n + s2);
     }
-    const int64_t m = (int64_t)src.size();
+    const int64_t m = vis + (int64_t)csrc.size();
     DBuf<int64_t> dsrc(m > 0 ? m : 1, st), ids(m > 0 ? m : 1, st);
-    if (m) GTS_CUDA(cudaMemcpyAsync(dsrc.get(), src.data(), m * 8, cudaMemcpyHostToDevice, st));
+    if (vis) GTS_CUDA(cudaMemcpyAsync(dsrc.get(), val2.get(), vis * 8, cudaMemcpyDeviceToDevice, st));
+    if (!csrc.empty())
+        GTS_CUDA(cudaMemcpyAsync(dsrc.get() + vis, csrc.data(), csrc.size() * 8, cudaMemcpyHostToDevice, st));
+    // strings size their rows on the host: the sources there too
+    std::vector<int64_t> src;
+    if (ix->dim == 0 && m > 0) {
+        src.resize(m);
+        GTS_CUDA(cudaMemcpyAsync(src.data(), dsrc.get(), m * 8, cudaMemcpyDeviceToHost, st));
+        GTS_CUDA(cudaStreamSynchronize(st));
+    }
     k_gather_ids<<<nb(m), kT, 0, st>>>(t.row_id.get(), c.id.get(), t.n, dsrc.get(), m, ids.get());
     Objects o;
     o.n = m;
@@ -713,13 +751,20 @@ gts_status gts_delete(gts_index *ix, const int64_t *ids, int64_t m, int64_t *n_m
             ix->n_live -= 1;
         }
         cudaStream_t st = ix->stream;
+        // the delete marks: (position, sequence) pairs to the device in one
+        // copy per list, then scattered
         for (int k = 0; k < 2; ++k) {
             auto &pos = k == 0 ? tree_rows : cache_slots;
             auto &sq = k == 0 ? tree_seq : cache_seq;
+            if (pos.empty()) continue;
             int64_t *dst = k == 0 ? ix->tree.row_del.get() : ix->cache.del.get();
-            for (size_t i = 0; i < pos.size(); ++i)
-                GTS_CUDA(cudaMemcpyAsync(dst + pos[i], &sq[i], 8, cudaMemcpyHostToDevice, st));
+            const int64_t cnt = (int64_t)pos.size();
+            DBuf<int64_t> dp(2 * cnt, st);
+            GTS_CUDA(cudaMemcpyAsync(dp.get(), pos.data(), cnt * 8, cudaMemcpyHostToDevice, st));
+            GTS_CUDA(cudaMemcpyAsync(dp.get() + cnt, sq.data(), cnt * 8, cudaMemcpyHostToDevice, st));
+            k_scatter_marks<<<nb(cnt), kT, 0, st>>>(dst, dp.get(), dp.get() + cnt, cnt);
         }
+        check_launch("delete marks");
         GTS_CUDA(cudaStreamSynchronize(st));
     });
     if (n_missing) *n_missing = missing;
