@@ -8,10 +8,13 @@ common module is ``synth`` (seeded inputs, no method arithmetic).
 ``oracle.c`` holds the plain definitions (brute force over every visible
 object, FP64 or integer metric; Section 3, Definitions 1 and 2).  ``index.py``
 holds Algorithms 1-3 (index construction) written step by step in numpy.
+The multi-column functions at the end define the summed distance of the
+closing remark of Section 5.2 and answer its queries by brute force.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -240,3 +243,71 @@ def knn_query(metric: str, objects, queries, k, ins_seq=None, del_seq=None, qseq
     sel = np.concatenate([np.arange(cap[i], cap[i] + counts[i]) for i in range(nq)]) if nq else np.zeros(0, np.int64)
     sel = sel.astype(np.int64)
     return offsets, ids[sel], key_to_distance(metric, keys[sel]), keys[sel]
+
+
+# ------------------------------------------------------------ multi-column
+
+def column_distances(metric: str, objects, target) -> np.ndarray:
+    """FP64 column distance from ``target`` to every object for a
+    multi-column query: sqrt of the FP64 key for L2, the key for L1, and for
+    the angle the C library's acos of 1 - key (Python's ``math.acos``)."""
+    m = METRICS[metric]
+    if m == EDIT:
+        raise ValueError("multi-column queries take vector columns")
+    X = np.ascontiguousarray(objects, np.float32)
+    t = np.ascontiguousarray(target, np.float32)
+    keys = np.empty(X.shape[0], np.float64)
+    lib().orc_keys_vec(m, _p(X), X.shape[0], X.shape[1], _p(t), _p(keys))
+    if metric == "l2":
+        return np.sqrt(keys)
+    if metric == "cos":
+        return np.array([math.acos(1.0 - float(x)) for x in keys], np.float64)
+    return keys
+
+
+def multi_sums(metrics, columns, queries, qi: int) -> np.ndarray:
+    """Distance of every object from query ``qi`` over several columns (the
+    closing remark of Section 5.2): the column distances summed in column
+    order in FP64, starting from 0."""
+    s = np.zeros(np.asarray(columns[0]).shape[0], np.float64)
+    for metric, X, Q in zip(metrics, columns, queries):
+        s = s + column_distances(metric, X, np.asarray(Q)[qi])
+    return s
+
+
+def multi_range(metrics, columns, queries, radii, live=None):
+    """Brute-force multi-column MRQ (Definition 1 over the summed distance):
+    per query every live object whose sum is <= r, ascending id.  ``live``:
+    optional bool mask over the ids.  Returns ``(offsets, ids, sums)``."""
+    nq = int(np.asarray(queries[0]).shape[0])
+    radii = np.asarray(radii, np.float32)
+    offsets, ids, sums = [0], [], []
+    for q in range(nq):
+        s = multi_sums(metrics, columns, queries, q)
+        keep = s <= float(radii[q])
+        if live is not None:
+            keep &= live
+        sel = np.nonzero(keep)[0]
+        ids.append(sel)
+        sums.append(s[sel])
+        offsets.append(offsets[-1] + sel.shape[0])
+    cat = (lambda a, t: np.concatenate(a).astype(t) if a else np.zeros(0, t))
+    return np.asarray(offsets, np.int64), cat(ids, np.int64), cat(sums, np.float64)
+
+
+def multi_knn(metrics, columns, queries, k, live=None):
+    """Brute-force multi-column MkNNQ (Definition 2 over the summed
+    distance): per query the first min(k, live objects) in ascending
+    (sum, id) order.  Returns ``(offsets, ids, sums)``."""
+    nq = int(np.asarray(queries[0]).shape[0])
+    k = np.broadcast_to(np.asarray(k, np.int64), (nq,))
+    offsets, ids, sums = [0], [], []
+    for q in range(nq):
+        s = multi_sums(metrics, columns, queries, q)
+        cand = np.arange(s.shape[0]) if live is None else np.nonzero(live)[0]
+        order = cand[np.lexsort((cand, s[cand]))][: int(k[q])]
+        ids.append(order)
+        sums.append(s[order])
+        offsets.append(offsets[-1] + order.shape[0])
+    cat = (lambda a, t: np.concatenate(a).astype(t) if a else np.zeros(0, t))
+    return np.asarray(offsets, np.int64), cat(ids, np.int64), cat(sums, np.float64)
