@@ -281,6 +281,36 @@ gts_status gts_merge_knn(const gts_result *const *parts, const int64_t *id_base,
                          gts_result *out);
 gts_status gts_merge_range(const gts_result *const *parts, const int64_t *id_base, int32_t n_parts, gts_result *out);
 
+/* Multi-column queries (Section 5.2, closing remark): cols[0 .. m), 1 <= m
+ * <= 64, are indexes over the same objects, one per column (object id i of every column
+ * describes the same object), each with its own vector metric (L1, L2 or
+ * angular; not edit distance).  The distance of object o from query q is
+ * the sum over columns j, in column order and in FP64, of the column
+ * distances d_j(q_j, o_j): sqrt(key) for L2, the key for L1, acos(1 - key)
+ * (the C library's acos) for the angle, each key in the single-column
+ * operation order of GTS_QUERY_KEYS.
+ *  queries: m host object sets (on_device = 0), all with the same nq;
+ *    queries[j] has column j's dim; row i of every set is query i.
+ *  gts_multi_range: answers with sum <= radii[i] (finite, >= 0; Definition
+ *    1), ascending id.  The candidates are the union of the columns' range answers at
+ *    radius radii[i] / m rounded up (pigeonhole principle).
+ *  gts_multi_knn: k[i] in 1 .. 1024; the first min(k[i], live objects)
+ *    answers in ascending (sum, id) order (Definition 2), by Fagin's
+ *    threshold algorithm over the columns' kNN answers with k' doubling from
+ *    k[i] up to 1024; a query that is still open there sums every live
+ *    object (a full scan).
+ *  opts: stream, precision and memory_budget pass to the column searches;
+ *    seq must be NULL (the current state) and result_on_device 0; stats,
+ *    stage_ms and flags are ignored.
+ * Every column must hold the same live ids: GTS_EINVAL when their live
+ * counts differ or an answer of one column is not live in another.  out
+ * (host) carries dist = (float)sum and key = the FP64 sum; release it with
+ * gts_result_free. */
+gts_status gts_multi_range(gts_index *const *cols, int32_t m, const gts_objects *queries, const float *radii,
+                           const gts_query_opts *opts, gts_result *out);
+gts_status gts_multi_knn(gts_index *const *cols, int32_t m, const gts_objects *queries, const int32_t *k,
+                         const gts_query_opts *opts, gts_result *out);
+
 /* Launch parameters of the tile kernels and the kNN schedule, held per index.
  * No counterpart in the paper (its kernels are launched per level with fixed
  * shapes).  None of them changes a result: every setting returns the same

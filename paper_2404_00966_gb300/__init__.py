@@ -95,7 +95,7 @@ EXPORTS = ["gts_build", "gts_range", "gts_knn", "gts_insert", "gts_delete", "gts
            "gts_knn_scan_noalloc_async", "gts_serve_start",
            "gts_serve_submit", "gts_serve_wait", "gts_serve_stats", "gts_serve_project", "gts_serve_stop", "gts_get_tuning",
            "gts_set_tuning", "gts_autotune", "gts_cost_model", "gts_autotune_shape", "gts_save", "gts_load",
-           "gts_merge_knn", "gts_merge_range"]
+           "gts_merge_knn", "gts_merge_range", "gts_multi_range", "gts_multi_knn"]
 
 
 def lib(path: Optional[str] = None):
@@ -145,6 +145,10 @@ def lib(path: Optional[str] = None):
     L.gts_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_BuildOpts), ctypes.POINTER(P)]
     L.gts_merge_knn.argtypes = [ctypes.POINTER(ctypes.POINTER(_Result)), P, I32, P, ctypes.POINTER(_Result)]
     L.gts_merge_range.argtypes = [ctypes.POINTER(ctypes.POINTER(_Result)), P, I32, ctypes.POINTER(_Result)]
+    L.gts_multi_range.argtypes = [P, I32, ctypes.POINTER(_Objects), P, ctypes.POINTER(_QueryOpts),
+                                  ctypes.POINTER(_Result)]
+    L.gts_multi_knn.argtypes = [P, I32, ctypes.POINTER(_Objects), P, ctypes.POINTER(_QueryOpts),
+                                ctypes.POINTER(_Result)]
     for f in ["gts_save", "gts_load", "gts_merge_knn", "gts_merge_range"]:
         getattr(L, f).restype = ctypes.c_int
     L.gts_selftest_wait.argtypes = [I32, ctypes.c_uint32]
@@ -261,6 +265,37 @@ class ShardedIndex:
     def close(self):
         for ix in self.shards:
             ix.close()
+
+
+def _multi(fn, columns, queries, per_query, precision, memory_budget):
+    if len(columns) != len(queries):
+        raise ValueError("one query set per column")
+    ms = [_Marshal(np.ascontiguousarray(q, np.float32)) for q in queries]
+    objs = (_Objects * len(ms))(*[m.obj for m in ms])
+    hs = (ctypes.c_void_p * len(columns))(*[c._h.value for c in columns])
+    opts = _QueryOpts(precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
+                      memory_budget=int(memory_budget))
+    res = _Result()
+    _check(fn(hs, len(columns), objs, _ptr(per_query), ctypes.byref(opts), ctypes.byref(res)))
+    offsets, ids, dist, kk = _host_arrays(res)
+    lib().gts_result_free(ctypes.byref(res))
+    return Result(offsets, ids, dist, keys=kk)
+
+
+def multi_range(columns, queries, radii, precision="fp32", memory_budget=0) -> Result:
+    """Multi-column range query (gts_multi_range): ``columns`` are indexes
+    over the same ids, ``queries`` one host [nq, dim_j] array per column; an
+    answer's distance is the sum of its column distances (``keys``: the FP64
+    sums)."""
+    r = np.ascontiguousarray(radii, np.float32)
+    return _multi(lib().gts_multi_range, columns, queries, r, precision, memory_budget)
+
+
+def multi_knn(columns, queries, k, precision="fp32", memory_budget=0) -> Result:
+    """Multi-column kNN query (gts_multi_knn), answers in ascending (sum, id)."""
+    n = int(np.asarray(queries[0]).shape[0])
+    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
+    return _multi(lib().gts_multi_knn, columns, queries, kk, precision, memory_budget)
 
 
 def cost_model(n: int, nq: int, p: float, fanout: int, h: int, concurrency: float) -> float:

@@ -12,6 +12,7 @@
 #include <new>
 
 #include "gts_impl.cuh"
+#include "metric.cuh"
 #include "tile_tc.cuh"
 
 namespace gts {
@@ -362,6 +363,62 @@ __global__ void k_gather_ids(const int64_t *row_id, const int64_t *cid, int64_t 
         ids[i] = s < n_tree ? row_id[s] : cid[s - n_tree];
     }
 }
+
+// FP64 keys of (query, object) pairs for random access (multi-column
+// queries): the reference operation order of each metric (L2: the squared
+// sum; L1: the sum; angular distance: 1 - cos on the raw vectors); rows <
+// n_tree are tree rows, the rest cache slots.
+__global__ void k_pair_keys(const float *__restrict__ Q, int dim, int metric, const float *__restrict__ X,
+                            const float *__restrict__ cX, int64_t n_tree, const int32_t *__restrict__ pq,
+                            const int64_t *__restrict__ prow, int64_t n, double *__restrict__ keys) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const float *q = Q + (int64_t)pq[j] * dim;
+        const int64_t r = prow[j];
+        const float *x = r < n_tree ? X + r * dim : cX + (r - n_tree) * dim;
+        keys[j] = metric == GTS_COS ? cos_key_fp64_seq(q, x, dim)
+                  : metric == GTS_L2 ? l2sq_fp64_seq(q, x, dim)
+                                     : l1_fp64_seq(q, x, dim);
+    }
+}
+
+}  // namespace
+
+void pair_keys(gts_index *ix, const gts_objects *queries, const std::vector<int32_t> &pq,
+               const std::vector<int64_t> &pid, std::vector<double> &keys) {
+    GTS_REQUIRE(ix->dim > 0, GTS_EINVAL, "multi-column queries take vector columns (L1, L2, angular)");
+    GTS_CUDA(cudaSetDevice(ix->device));
+    cudaStream_t st = ix->stream;
+    const int64_t n = (int64_t)pq.size();
+    keys.assign(n, 0.0);
+    if (n == 0) return;
+    DevObjects dq;
+    load_objects(queries, ix->dim, dq, st, "queries");
+    const Tree &t = ix->tree;
+    const Cache &c = ix->cache;
+    std::vector<int64_t> rows(n);
+    for (int64_t j = 0; j < n; ++j) {
+        const int64_t id = pid[j];
+        GTS_REQUIRE(id >= 0 && id < (int64_t)ix->loc.size() && ix->loc[id] != -1, GTS_EINVAL,
+                    "object " + std::to_string(id) + " is not live in every column");
+        GTS_REQUIRE(pq[j] >= 0 && pq[j] < dq.v.n, GTS_EINVAL, "query index out of range");
+        const int64_t L = ix->loc[id];
+        rows[j] = L >= 0 ? L : t.n + (-(L + 2));
+    }
+    DBuf<int32_t> dpq(n, st);
+    DBuf<int64_t> drow(n, st);
+    DBuf<double> dk(n, st);
+    GTS_CUDA(cudaMemcpyAsync(dpq.get(), pq.data(), n * 4, cudaMemcpyHostToDevice, st));
+    GTS_CUDA(cudaMemcpyAsync(drow.get(), rows.data(), n * 8, cudaMemcpyHostToDevice, st));
+    const bool cosr = ix->metric == GTS_COS;
+    k_pair_keys<<<std::min<int64_t>(nb(n), 4096), kT, 0, st>>>(
+        dq.v.X, ix->dim, ix->metric, cosr ? t.Xr.get() : t.X.get(), cosr ? c.Xr.get() : c.X.get(), t.n, dpq.get(),
+        drow.get(), n, dk.get());
+    check_launch("pair keys");
+    GTS_CUDA(cudaMemcpyAsync(keys.data(), dk.get(), n * 8, cudaMemcpyDeviceToHost, st));
+    GTS_CUDA(cudaStreamSynchronize(st));
+}
+
+namespace {
 
 void rebuild(gts_index *ix) {
     cudaStream_t st = ix->stream;

@@ -222,6 +222,12 @@ struct gts_index {
 
 namespace gts {
 
+// api.cu
+// FP64 keys of the pairs (queries row pq[j], object id pid[j]) of one index
+// (vector metrics), computed on the device; GTS_EINVAL when an id is not live
+void pair_keys(gts_index *ix, const gts_objects *queries, const std::vector<int32_t> &pq,
+               const std::vector<int64_t> &pid, std::vector<double> &keys);
+
 // build.cu
 // raw_rows: angular distance only -- objs holds the unit vectors, raw_rows
 // the caller's rows in the same order (kept in leaf order as Tree::Xr)

@@ -62,6 +62,18 @@ def test_argument_errors_are_reported_before_any_device_work(L):
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
+def test_multi_column_argument_errors_without_a_device(L):
+    import paper_2404_00966_gb300 as g
+    res = g._Result()
+    assert L.gts_multi_range(None, 1, None, None, None, ctypes.byref(res)) == 1
+    assert b"NULL" in L.gts_last_error()
+    hs = (ctypes.c_void_p * 1)(None)
+    q = (g._Objects * 1)()
+    assert L.gts_multi_knn(hs, 0, q, None, None, ctypes.byref(res)) == 1
+    assert b"columns" in L.gts_last_error()
+    assert L.gts_multi_knn(hs, 1, q, None, None, ctypes.byref(res)) == 1
+
+
 def test_no_device_means_an_error_not_a_fallback(L):
     import paper_2404_00966_gb300 as g
     X = np.random.default_rng(0).random((50, 4), dtype=np.float32)

@@ -1,0 +1,161 @@
+"""Multi-column queries through the C ABI (gts_multi_range / gts_multi_knn)
+against the oracle's brute force over the summed distance (the closing remark
+of Section 5.2: one index per column, pigeonhole principle for ranges,
+Fagin's threshold algorithm for kNN).
+
+Ids and offsets must match exactly and the FP64 sums bit for bit: every
+column key is the single-column FP64 key, and both sides take sqrt and the C
+library's acos of the same keys and add them in column order.
+
+Inputs: three columns of one object set -- L2 over 24 dimensions, the angle
+over 300 (the tensor-core tiles), L1 over 16 -- with duplicated objects (ties
+broken by id), and a case whose columns disagree (independent data per
+column, so the threshold algorithm needs several rounds of k' doubling).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import small_vectors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gts():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_00966_gb300 import build_ext
+    build_ext.build()
+    import paper_2404_00966_gb300 as g
+    return g
+
+
+METRICS = ["l2", "cos", "l1"]
+DIMS = [24, 300, 16]
+
+
+def columns(n, nq, seed, correlated):
+    """Per column (objects, queries); with ``correlated`` every column is a
+    projection of one latent vector, so the columns rank objects alike."""
+    rng = np.random.default_rng(seed)
+    Xs, Qs = [], []
+    latent, qlat = small_vectors(n, 8, nq, seed, kind="gauss", dup_frac=0.0)
+    for j, d in enumerate(DIMS):
+        if correlated:
+            W = rng.standard_normal((8, d)).astype(np.float32)
+            X = latent @ W + 0.05 * rng.standard_normal((n, d)).astype(np.float32)
+            Q = qlat @ W + 0.05 * rng.standard_normal((nq, d)).astype(np.float32)
+        else:
+            X, Q = small_vectors(n, d, nq, seed + 17 * j + 1, kind="gauss", dup_frac=0.0)
+        Xs.append(np.ascontiguousarray(X, np.float32))
+        Qs.append(np.ascontiguousarray(Q, np.float32))
+    dup = rng.choice(n, size=2 * (n // 50), replace=False)
+    for X in Xs:                                              # the same objects duplicated in every column
+        X[dup[: n // 50]] = X[dup[n // 50:]]
+    for Q, X in zip(Qs, Xs):
+        Q[0] = X[dup[0]]                                       # a query on a duplicated object
+    return Xs, Qs
+
+
+def sum_radii(Xs, Qs, frac, seed):
+    rng = np.random.default_rng(seed)
+    sample = rng.choice(Xs[0].shape[0], size=min(300, Xs[0].shape[0]), replace=False)
+    S = [x[sample] for x in Xs]
+    return np.array([np.quantile(oracle.multi_sums(METRICS, S, Qs, i), frac) for i in range(Qs[0].shape[0])],
+                    np.float32)
+
+
+def assert_same(res, want, label):
+    off, ids, sums = want
+    assert np.array_equal(res.offsets, off), f"{label}: per-query counts differ"
+    assert np.array_equal(res.ids, ids), f"{label}: ids differ"
+    assert np.array_equal(res.keys, sums), f"{label}: FP64 sums differ"
+    assert np.array_equal(res.dist, sums.astype(np.float32)), f"{label}: FP32 distances differ"
+
+
+@pytest.mark.parametrize("correlated", [True, False])
+def test_multi_range_and_knn(gts, correlated):
+    Xs, Qs = columns(5000, 40, seed=11 + correlated, correlated=correlated)
+    cols = [gts.Index.build(X, m, fanout=8, root_pivot=3) for X, m in zip(Xs, METRICS)]
+    radii = sum_radii(Xs, Qs, 0.01, seed=2)
+    radii[0] = 0.0                                            # the duplicated object and its copy only
+    radii[1] = np.float32(1e6)                                # every object
+    want_r = oracle.multi_range(METRICS, Xs, Qs, radii)
+    ks = np.random.default_rng(5).integers(1, 30, size=40).astype(np.int32)
+    ks[2] = 1024                                              # the largest k
+    want_k = oracle.multi_knn(METRICS, Xs, Qs, ks)
+    for prec in ("fp32", "bf16"):
+        assert_same(gts.multi_range(cols, Qs, radii, precision=prec), want_r, f"range {prec}")
+        assert_same(gts.multi_knn(cols, Qs, ks, precision=prec), want_k, f"knn {prec}")
+    assert list(want_r[1][want_r[0][0]:want_r[0][1]]) == sorted(want_r[1][want_r[0][0]:want_r[0][1]])
+    for c in cols:
+        c.close()
+
+
+def test_k_beyond_the_live_objects(gts):
+    Xs, Qs = columns(700, 6, seed=51, correlated=False)
+    cols = [gts.Index.build(X, m, fanout=5) for X, m in zip(Xs, METRICS)]
+    ks = np.array([1000, 700, 699, 1, 1024, 350], np.int32)
+    assert_same(gts.multi_knn(cols, Qs, ks), oracle.multi_knn(METRICS, Xs, Qs, ks), "k >= n")
+    with pytest.raises(gts.GTSError):
+        gts.multi_knn(cols, Qs, 1025)
+    for c in cols:
+        c.close()
+
+
+def test_one_column_matches_the_single_column_oracle(gts):
+    Xs, Qs = columns(3000, 25, seed=21, correlated=False)
+    ix = gts.Index.build(Xs[2], "l1", fanout=10)
+    got = gts.multi_knn([ix], [Qs[2]], 12)
+    want = oracle.knn_query("l1", Xs[2], Qs[2], 12)
+    assert np.array_equal(got.offsets, want[0]) and np.array_equal(got.ids, want[1])
+    assert np.array_equal(got.keys, want[3])
+    ix.close()
+
+
+def test_multi_after_updates(gts):
+    """Inserts and deletes applied to every column alike: the answers are the
+    oracle's over the live objects."""
+    Xs, Qs = columns(3000, 20, seed=31, correlated=True)
+    extra, _ = columns(200, 1, seed=32, correlated=True)
+    cols = [gts.Index.build(X, m, fanout=6, cache_limit=100) for X, m in zip(Xs, METRICS)]
+    for c, e in zip(cols, extra):
+        c.insert(e[:80])                                      # the cache list
+    dele = np.random.default_rng(3).choice(3080, 90, replace=False)
+    for c in cols:
+        assert c.delete(dele) == 0
+    for c, e in zip(cols, extra):
+        c.batch_update(e[80:], np.zeros(0, np.int64))         # a rebuild
+    P = [np.concatenate([X, e]) for X, e in zip(Xs, extra)]
+    live = np.ones(3200, bool)
+    live[dele] = False
+    radii = sum_radii(P, Qs, 0.02, seed=4)
+    assert_same(gts.multi_range(cols, Qs, radii), oracle.multi_range(METRICS, P, Qs, radii, live=live), "range")
+    assert_same(gts.multi_knn(cols, Qs, 9), oracle.multi_knn(METRICS, P, Qs, 9, live=live), "knn")
+    for c in cols:
+        c.close()
+
+
+def test_multi_argument_errors(gts):
+    Xs, Qs = columns(800, 4, seed=41, correlated=False)
+    a = gts.Index.build(Xs[0], "l2")
+    b = gts.Index.build(Xs[2], "l1")
+    with pytest.raises(gts.GTSError):                         # query dims swapped
+        gts.multi_knn([a, b], [Qs[2], Qs[0]], 3)
+    with pytest.raises(gts.GTSError):                         # different numbers of queries
+        gts.multi_knn([a, b], [Qs[0], Qs[2][:2]], 3)
+    with pytest.raises(ValueError):
+        gts.multi_knn([a, b], [Qs[0]], 3)
+    b.delete(np.array([5]))
+    with pytest.raises(gts.GTSError):                         # live counts differ
+        gts.multi_range([a, b], [Qs[0], Qs[2]], np.full(4, 1e6, np.float32))
+    a.delete(np.array([6]))                                   # same counts, different ids
+    with pytest.raises(gts.GTSError):
+        gts.multi_range([a, b], [Qs[0], Qs[2]], np.full(4, 1e6, np.float32))
+    c = gts.Index.build(Xs[2], "l1")
+    r = gts.multi_knn([c], [Qs[2]], 3)                        # the library still answers after the errors
+    assert np.array_equal(r.ids, oracle.knn_query("l1", Xs[2], Qs[2], 3)[1])
+    for i in (a, b, c):
+        i.close()
