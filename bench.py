@@ -775,6 +775,66 @@ def bench_wordvec(args):
     return out
 
 
+def bench_multicol(args):
+    """multicol_200000_l2x128_cos300_knn10: multi-column kNN over an L2
+    column and an angular column of one object set (distance = the sum of
+    the two), through gts_multi_knn: host queries in, host answers out, the
+    threshold algorithm's rounds and random accesses inside the timed call."""
+    import torch
+    import paper_2404_00966_gb300 as gts
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    prec = args.precision
+    wl = synth.multi_columns() if args.scale >= 1.0 else synth.multi_columns(n=max(20_000, int(200_000 * args.scale)))
+    nq, k = int(wl.queries[0].shape[0]), int(wl.k[0])
+    cols, shapes = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for X, m in zip(wl.objects, wl.metrics):
+        cols.append(gts.Index.build(torch.from_numpy(X).cuda(), m, fanout=wl.fanout, root_pivot=0))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    if not args.no_tune:   # untimed setup: each column's shape by the cost model and a sample batch
+        for ix, Q in zip(cols, wl.queries):
+            shapes.append(ix.autotune_shape(torch.from_numpy(Q[:2000]).cuda(), k=k, precision=prec, candidates=4,
+                                            reps=1))
+
+    def step():
+        return gts.multi_knn(cols, wl.queries, wl.k, precision=prec)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for _ in range(args.other_steps):
+            r = step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    out = {"metric": "multi-column kNN queries/s at oracle-exact results (L2 + angle, k=10)",
+           "value": round(nq * args.other_steps / dt, 1), "unit": "queries/s", "steps": args.other_steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.other_steps, 3),
+           "dtype": "bf16+f64" if prec == "bf16" else "f32+f64", "timing": "host wall clock around the call",
+           "config": {"workload": wl.name, "n": int(wl.objects[0].shape[0]), "columns": wl.metrics,
+                      "dims": [int(x.shape[1]) for x in wl.objects], "nq": nq, "k": k, "precision": prec,
+                      "shapes": shapes},
+           "answers": int(r.offsets[-1]), "build_s": round(build_s, 3), "clocks": clocks.summary()}
+    for ix in cols:
+        ix.close()
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.multi_knn(wl.metrics, wl.objects, [q[:2] for q in wl.queries], k)
+        per_q = (time.perf_counter() - t0) / 2
+        m = int(max(2, min(nq, args.other_cpu_seconds / max(per_q, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.multi_knn(wl.metrics, wl.objects, [q[:m] for q in wl.queries], k)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(m / dt, 3), "unit": "queries/s", "cores": oracle.threads(),
+                               "kind": "oracle", "sample": f"{m} queries, brute-force FP64 summed distances"}
+    return out
+
+
 def run_others(args):
     """Each remaining configuration timed on its own; a failure is recorded
     in its entry and does not stop the others."""
@@ -784,6 +844,7 @@ def run_others(args):
                      ("dna_1M_r8", lambda: bench_strings("dna", args)),
                      ("zipf2d_10M", lambda: bench_zipf2d(args)),
                      ("wordvec_200kx300_cos", lambda: bench_wordvec(args)),
+                     ("multicol_200k_l2x128_cos300", lambda: bench_multicol(args)),
                      ("uniform_2Mx256_l1_serving", lambda: bench_serving(args))):
         t0 = time.perf_counter()
         try:
@@ -796,7 +857,7 @@ def run_others(args):
 
 
 def run_config(args):
-    """One of the other workloads alone (--workload words|dna|zipf2d|serving)."""
+    """One of the other workloads alone (--workload words|dna|zipf2d|wordvec|multicol|serving)."""
     import torch
     from paper_2404_00966_gb300 import build_ext
     build_ext.build()
@@ -807,6 +868,8 @@ def run_config(args):
         out = bench_zipf2d(args)
     elif args.workload == "wordvec":
         out = bench_wordvec(args)
+    elif args.workload == "multicol":
+        out = bench_multicol(args)
     else:
         out = bench_serving(args)
     out.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"})
@@ -860,7 +923,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20_000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50_000.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=1024, help="serving: requests per device batch")
-    ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "wordvec", "serving"],
+    ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "wordvec", "multicol",
+                                                         "serving"],
                     help="gauss (the headline line); the others time the remaining configurations alone")
     ap.add_argument("--no-others", action="store_true", help="headline only: skip the other workloads")
     ap.add_argument("--other-steps", type=int, default=5, help="timed steps of the other workloads")

@@ -297,11 +297,13 @@ gts_status gts_merge_range(const gts_result *const *parts, const int64_t *id_bas
  *  gts_multi_knn: k[i] in 1 .. 1024; the first min(k[i], live objects)
  *    answers in ascending (sum, id) order (Definition 2), by Fagin's
  *    threshold algorithm over the columns' kNN answers with k' doubling from
- *    k[i] up to 1024; a query that is still open there sums every live
+ *    2 k[i] up to 1024; a query that is still open there sums every live
  *    object (a full scan).
- *  opts: stream, precision and memory_budget pass to the column searches;
- *    seq must be NULL (the current state) and result_on_device 0; stats,
- *    stage_ms and flags are ignored.
+ *  opts: precision and memory_budget pass to the column searches, which
+ *    run concurrently, each on a host thread and a non-blocking stream of its
+ *    own made for the call (opts->stream is not used; the call returns when
+ *    all of it is done); seq must be NULL (the current state) and
+ *    result_on_device 0; stats, stage_ms and flags are ignored.
  * Every column must hold the same live ids: GTS_EINVAL when their live
  * counts differ or an answer of one column is not live in another.  out
  * (host) carries dist = (float)sum and key = the FP64 sum; release it with

@@ -60,7 +60,7 @@ void ensure_device() {
     cudaError_t e = cudaGetDeviceCount(&n);
     if (e != cudaSuccess || n == 0)
         throw Error(GTS_ECUDA, std::string("no usable CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 devices"));
-    static bool pool_set[64] = {false};
+    static std::atomic<bool> pool_set[64] = {};
     int dev = 0;
     GTS_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && !pool_set[dev]) {
@@ -384,10 +384,9 @@ __global__ void k_pair_keys(const float *__restrict__ Q, int dim, int metric, co
 }  // namespace
 
 void pair_keys(gts_index *ix, const gts_objects *queries, const std::vector<int32_t> &pq,
-               const std::vector<int64_t> &pid, std::vector<double> &keys) {
+               const std::vector<int64_t> &pid, std::vector<double> &keys, cudaStream_t st) {
     GTS_REQUIRE(ix->dim > 0, GTS_EINVAL, "multi-column queries take vector columns (L1, L2, angular)");
     GTS_CUDA(cudaSetDevice(ix->device));
-    cudaStream_t st = ix->stream;
     const int64_t n = (int64_t)pq.size();
     keys.assign(n, 0.0);
     if (n == 0) return;

@@ -224,9 +224,10 @@ namespace gts {
 
 // api.cu
 // FP64 keys of the pairs (queries row pq[j], object id pid[j]) of one index
-// (vector metrics), computed on the device; GTS_EINVAL when an id is not live
+// (vector metrics), computed on the device on stream st; GTS_EINVAL when an
+// id is not live
 void pair_keys(gts_index *ix, const gts_objects *queries, const std::vector<int32_t> &pq,
-               const std::vector<int64_t> &pid, std::vector<double> &keys);
+               const std::vector<int64_t> &pid, std::vector<double> &keys, cudaStream_t st);
 
 // build.cu
 // raw_rows: angular distance only -- objs holds the unit vectors, raw_rows

@@ -16,14 +16,19 @@
 //
 // Every sum is the FP64 column distances (L2: sqrt of the FP64 key; L1: the
 // key; angular: the C library's acos(1 - key)) added in column order from 0.
-// Column searches run on the device through the single-column entry points;
-// the combination (unions, threshold tests, selection) is host bookkeeping.
+// Column searches run on the device through the single-column entry points,
+// the columns concurrently (one host thread and one non-blocking stream per
+// column); the combination (unions, threshold tests, selection) is host
+// bookkeeping.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <future>
 #include <limits>
-#include <unordered_map>
+#include <memory>
+#include <thread>
 #include <vector>
 
 #include "gts_impl.cuh"
@@ -40,6 +45,9 @@ double column_distance(int metric, double key) {
 // Owns one column's host result.
 struct ColResult {
     gts_result r{};
+    ColResult() = default;
+    ColResult(const ColResult &) = delete;
+    ColResult &operator=(const ColResult &) = delete;
     ~ColResult() { gts_result_free(&r); }
 };
 
@@ -50,9 +58,47 @@ void raise_status(gts_status s, const char *what) {
 struct Columns {
     std::vector<gts_index *> ix;
     std::vector<int> metric;
+    std::vector<cudaStream_t> stream;   // one non-blocking stream per column, owned
     int64_t nq = 0, n_live = 0;
     gts_query_opts base{};
+    Columns() = default;
+    Columns(const Columns &) = delete;
+    Columns &operator=(const Columns &) = delete;
+    Columns(Columns &&o) noexcept
+        : ix(std::move(o.ix)), metric(std::move(o.metric)), stream(std::move(o.stream)), nq(o.nq),
+          n_live(o.n_live), base(o.base) {
+        o.stream.clear();
+    }
+    ~Columns() {
+        for (cudaStream_t st : stream) cudaStreamDestroy(st);
+    }
+    // column j's options: the caller's, on the column's own stream
+    gts_query_opts opts(int j, int32_t flags) const {
+        gts_query_opts o = base;
+        o.stream = stream[j];
+        o.flags = flags;
+        return o;
+    }
 };
+
+// f(j) for every column j, each on a thread of its own; the first error is
+// rethrown once every column has finished.
+template <class F>
+void for_columns(int m, F &&f) {
+    if (m == 1) {
+        f(0);
+        return;
+    }
+    std::vector<std::future<void>> fs;
+    for (int j = 0; j < m; ++j) fs.push_back(std::async(std::launch::async, [&f, j] { f(j); }));
+    std::exception_ptr first;
+    for (auto &x : fs) try {
+            x.get();
+        } catch (...) {
+            if (!first) first = std::current_exception();
+        }
+    if (first) std::rethrow_exception(first);
+}
 
 Columns check_columns(gts_index *const *cols, int32_t m, const gts_objects *queries, const gts_query_opts *opts) {
     GTS_REQUIRE(cols != nullptr && queries != nullptr, GTS_EINVAL, "columns or queries NULL");
@@ -82,23 +128,81 @@ Columns check_columns(gts_index *const *cols, int32_t m, const gts_objects *quer
         c.ix.push_back(ix);
         c.metric.push_back(ix->metric);
     }
+    for (int32_t j = 0; j < m; ++j) {
+        GTS_CUDA(cudaSetDevice(c.ix[j]->device));
+        cudaStream_t st = nullptr;
+        GTS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        c.stream.push_back(st);
+    }
     return c;
 }
 
-// Sums of the column distances of the pairs (query pq[j] of `queries`, id pid[j]).
+int host_threads() {
+    static const int t = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    return t;
+}
+
+// f(begin, end) over [0, n) in contiguous chunks of at least `grain` items,
+// one host thread per chunk (up to host_threads()); the first error is
+// rethrown after every chunk has finished.
+template <class F>
+void parallel_for(int64_t n, int64_t grain, F &&f) {
+    const int64_t T = std::min<int64_t>(host_threads(), (n + grain - 1) / grain);
+    if (T <= 1) {
+        if (n > 0) f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    std::vector<std::exception_ptr> err(T);
+    for (int64_t t = 0; t < T; ++t)
+        th.emplace_back([&, t] {
+            try {
+                f(n * t / T, n * (t + 1) / T);
+            } catch (...) {
+                err[t] = std::current_exception();
+            }
+        });
+    for (auto &x : th) x.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
+}
+
+// Sums of the column distances of the pairs (query pq[p] of `queries`, id
+// pid[p]): each column's keys on its own stream, converted to distances in
+// its thread, then added in column order from 0.
 std::vector<double> pair_sums(const Columns &c, const gts_objects *queries, const std::vector<int32_t> &pq,
                               const std::vector<int64_t> &pid) {
-    std::vector<double> sum(pq.size(), 0.0), keys;
-    for (size_t j = 0; j < c.ix.size(); ++j) {
-        pair_keys(c.ix[j], &queries[j], pq, pid, keys);
-        for (size_t p = 0; p < pq.size(); ++p) sum[p] += column_distance(c.metric[j], keys[p]);
-    }
+    const int m = (int)c.ix.size();
+    const int64_t n = (int64_t)pq.size();
+    std::vector<std::vector<double>> dist(m);
+    for_columns(m, [&](int j) {
+        pair_keys(c.ix[j], &queries[j], pq, pid, dist[j], c.stream[j]);
+        double *d = dist[j].data();
+        const int metric = c.metric[j];
+        parallel_for(n, 1 << 14, [&](int64_t b, int64_t e) {
+            for (int64_t p = b; p < e; ++p) d[p] = column_distance(metric, d[p]);
+        });
+    });
+    std::vector<double> sum(n);
+    parallel_for(n, 1 << 15, [&](int64_t b, int64_t e) {
+        for (int64_t p = b; p < e; ++p) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += dist[j][p];
+            sum[p] = s;
+        }
+    });
     return sum;
 }
 
-void host_result(gts_result *out, int64_t nq, const std::vector<int64_t> &off, const std::vector<int64_t> &ids,
-                 const std::vector<double> &sums) {
-    const int64_t total = (int64_t)ids.size();
+// A host result from per-query answers, allocated for gts_result_free.
+struct Answers {
+    std::vector<int64_t> off;                 // nq + 1
+    std::vector<int64_t> ids;
+    std::vector<double> sums;
+};
+
+void host_result(gts_result *out, int64_t nq, const Answers &a) {
+    const int64_t total = (int64_t)a.ids.size();
     out->nq = nq;
     out->on_device = 0;
     out->priv_ = nullptr;
@@ -110,12 +214,12 @@ void host_result(gts_result *out, int64_t nq, const std::vector<int64_t> &off, c
         gts_result_free(out);
         throw Error(GTS_ENOMEM, "host allocation failed");
     }
-    std::memcpy(out->offsets, off.data(), sizeof(int64_t) * (nq + 1));
-    for (int64_t i = 0; i < total; ++i) {
-        out->ids[i] = ids[i];
-        out->dist[i] = (float)sums[i];
-        out->key[i] = sums[i];
+    std::memcpy(out->offsets, a.off.data(), sizeof(int64_t) * (nq + 1));
+    if (total) {
+        std::memcpy(out->ids, a.ids.data(), sizeof(int64_t) * total);
+        std::memcpy(out->key, a.sums.data(), sizeof(double) * total);
     }
+    for (int64_t i = 0; i < total; ++i) out->dist[i] = (float)a.sums[i];
 }
 
 // Rows `rows` of every column's queries, gathered on the host.
@@ -137,6 +241,44 @@ struct SubQueries {
     }
 };
 
+// Per query i, the ids all columns returned for it (res[j] rows i), sorted
+// and without repeats: cand[off[i] .. off[i] + cnt[i]).
+void union_ids(const std::vector<ColResult> &res, int64_t nq, std::vector<int64_t> &off, std::vector<int64_t> &cand,
+               std::vector<int64_t> &cnt) {
+    off.assign(nq + 1, 0);
+    for (const auto &r : res)
+        for (int64_t i = 0; i < nq; ++i) off[i + 1] += r.r.offsets[i + 1] - r.r.offsets[i];
+    for (int64_t i = 0; i < nq; ++i) off[i + 1] += off[i];
+    cand.resize(off[nq]);
+    cnt.resize(nq);
+    parallel_for(nq, 256, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            int64_t *w = cand.data() + off[i];
+            for (const auto &r : res) w = std::copy(r.r.ids + r.r.offsets[i], r.r.ids + r.r.offsets[i + 1], w);
+            int64_t *s = cand.data() + off[i];
+            std::sort(s, w);
+            cnt[i] = std::unique(s, w) - s;
+        }
+    });
+}
+
+// The pairs (i, cand[off[i] + t]), t < cnt[i], flattened in query order.
+void flatten_pairs(const std::vector<int64_t> &off, const std::vector<int64_t> &cand, const std::vector<int64_t> &cnt,
+                   std::vector<int64_t> &poff, std::vector<int32_t> &pq, std::vector<int64_t> &pid) {
+    const int64_t nq = (int64_t)cnt.size();
+    poff.assign(nq + 1, 0);
+    for (int64_t i = 0; i < nq; ++i) poff[i + 1] = poff[i] + cnt[i];
+    pq.resize(poff[nq]);
+    pid.resize(poff[nq]);
+    parallel_for(nq, 256, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i)
+            for (int64_t t = 0; t < cnt[i]; ++t) {
+                pq[poff[i] + t] = (int32_t)i;
+                pid[poff[i] + t] = cand[off[i] + t];
+            }
+    });
+}
+
 void multi_range(const Columns &c, const gts_objects *queries, const float *radii, gts_result *out) {
     const int64_t nq = c.nq;
     const int m = (int)c.ix.size();
@@ -152,44 +294,62 @@ void multi_range(const Columns &c, const gts_objects *queries, const float *radi
         if ((double)f < t) f = std::nextafter(f, std::numeric_limits<float>::infinity());
         rcol[q] = f;
     }
-    // union of the column answers, per query ascending id
-    std::vector<std::vector<int64_t>> cand(nq);
-    for (int j = 0; j < m; ++j) {
-        ColResult r;
-        raise_status(gts_range(c.ix[j], &queries[j], rcol.data(), &c.base, &r.r), "column range query");
-        for (int64_t q = 0; q < nq; ++q)
-            cand[q].insert(cand[q].end(), r.r.ids + r.r.offsets[q], r.r.ids + r.r.offsets[q + 1]);
-    }
+    std::vector<ColResult> res(m);
+    for_columns(m, [&](int j) {
+        const gts_query_opts o = c.opts(j, 0);
+        raise_status(gts_range(c.ix[j], &queries[j], rcol.data(), &o, &res[j].r), "column range query");
+    });
+    std::vector<int64_t> off, cand, cnt, poff, pid;
     std::vector<int32_t> pq;
-    std::vector<int64_t> pid;
-    for (int64_t q = 0; q < nq; ++q) {
-        std::sort(cand[q].begin(), cand[q].end());
-        cand[q].erase(std::unique(cand[q].begin(), cand[q].end()), cand[q].end());
-        for (int64_t id : cand[q]) {
-            pq.push_back((int32_t)q);
-            pid.push_back(id);
-        }
-    }
+    union_ids(res, nq, off, cand, cnt);
+    flatten_pairs(off, cand, cnt, poff, pq, pid);
     const std::vector<double> sum = pair_sums(c, queries, pq, pid);
-    std::vector<int64_t> off(nq + 1, 0), ids;
-    std::vector<double> sums;
-    for (size_t p = 0; p < pq.size(); ++p)
-        if (sum[p] <= (double)radii[pq[p]]) {
-            ids.push_back(pid[p]);
-            sums.push_back(sum[p]);
-            ++off[pq[p] + 1];
+    // keep the pairs whose sum is <= r (ascending id within each query)
+    std::vector<int64_t> kept(nq);
+    parallel_for(nq, 256, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            int64_t w = poff[i];
+            for (int64_t p = poff[i]; p < poff[i + 1]; ++p)
+                if (sum[p] <= (double)radii[i]) ++w;
+            kept[i] = w - poff[i];
         }
-    for (int64_t q = 0; q < nq; ++q) off[q + 1] += off[q];
-    host_result(out, nq, off, ids, sums);
+    });
+    Answers a;
+    a.off.assign(nq + 1, 0);
+    for (int64_t i = 0; i < nq; ++i) a.off[i + 1] = a.off[i] + kept[i];
+    a.ids.resize(a.off[nq]);
+    a.sums.resize(a.off[nq]);
+    parallel_for(nq, 256, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            int64_t w = a.off[i];
+            for (int64_t p = poff[i]; p < poff[i + 1]; ++p)
+                if (sum[p] <= (double)radii[i]) {
+                    a.ids[w] = pid[p];
+                    a.sums[w++] = sum[p];
+                }
+        }
+    });
+    host_result(out, nq, a);
 }
 
 constexpr int64_t kMaxK = 1024;   // the single-column kNN limit
+
+using Best = std::vector<std::pair<double, int64_t>>;   // (sum, id), ascending
+using Seen = std::vector<std::pair<int64_t, double>>;   // (id, sum), ascending id
+
+// The first k of n (sum, id) pairs in ascending order.
+Best best_k(Best v, int64_t k) {
+    const size_t kk = std::min<size_t>((size_t)k, v.size());
+    std::partial_sort(v.begin(), v.begin() + kk, v.end());
+    v.resize(kk);
+    return v;
+}
 
 // kNN by random access to every live object (the columns' lists at the k'
 // limit did not settle the threshold test), queries in chunks of at most
 // 2^24 pairs.
 void full_scan(const Columns &c, const gts_objects *queries, const int32_t *k, const std::vector<int64_t> &rows,
-               std::vector<std::vector<std::pair<double, int64_t>>> &answer) {
+               std::vector<Best> &answer) {
     std::vector<int64_t> live;
     const std::vector<int64_t> &loc = c.ix[0]->loc;
     for (int64_t id = 0; id < (int64_t)loc.size(); ++id)
@@ -198,26 +358,25 @@ void full_scan(const Columns &c, const gts_objects *queries, const int32_t *k, c
     const int64_t per = std::max<int64_t>(1, ((int64_t)1 << 24) / std::max<int64_t>(n, 1));
     for (size_t c0 = 0; c0 < rows.size(); c0 += per) {
         const std::vector<int64_t> chunk(rows.begin() + c0, rows.begin() + std::min(rows.size(), c0 + (size_t)per));
+        const int64_t nc = (int64_t)chunk.size();
         SubQueries sub(c, queries, chunk);
-        std::vector<int32_t> pq;
-        std::vector<int64_t> pid;
-        pq.reserve(chunk.size() * n);
-        pid.reserve(chunk.size() * n);
-        for (size_t i = 0; i < chunk.size(); ++i)
-            for (int64_t id : live) {
-                pq.push_back((int32_t)i);
-                pid.push_back(id);
-            }
+        std::vector<int32_t> pq(nc * n);
+        std::vector<int64_t> pid(nc * n);
+        parallel_for(nc, 1, [&](int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; ++i)
+                for (int64_t p = 0; p < n; ++p) {
+                    pq[i * n + p] = (int32_t)i;
+                    pid[i * n + p] = live[p];
+                }
+        });
         const std::vector<double> sum = pair_sums(c, sub.obj.data(), pq, pid);
-        for (size_t i = 0; i < chunk.size(); ++i) {
-            const int64_t q = chunk[i];
-            std::vector<std::pair<double, int64_t>> v(n);
-            for (int64_t p = 0; p < n; ++p) v[p] = {sum[i * n + p], live[p]};
-            const size_t kk = std::min<size_t>((size_t)k[q], v.size());
-            std::partial_sort(v.begin(), v.begin() + kk, v.end());
-            v.resize(kk);
-            answer[q] = std::move(v);
-        }
+        parallel_for(nc, 1, [&](int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; ++i) {
+                Best v(n);
+                for (int64_t p = 0; p < n; ++p) v[p] = {sum[i * n + p], live[p]};
+                answer[chunk[i]] = best_k(std::move(v), k[chunk[i]]);
+            }
+        });
     }
 }
 
@@ -227,59 +386,104 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
     GTS_REQUIRE(nq == 0 || k != nullptr, GTS_EINVAL, "k NULL");
     for (int64_t q = 0; q < nq; ++q) GTS_REQUIRE(k[q] >= 1 && k[q] <= kMaxK, GTS_EINVAL, "k must be in 1 .. 1024");
     // k' stops at the single-column limit; a query whose threshold test
-    // still fails there takes the full scan below
+    // still fails there takes the full scan
     const int64_t kmax = std::min<int64_t>(std::max<int64_t>(c.n_live, 1), kMaxK);
-    std::vector<int64_t> full;
-    std::vector<std::unordered_map<int64_t, double>> seen(nq);
-    std::vector<std::vector<std::pair<double, int64_t>>> answer(nq);
-    std::vector<int64_t> active(nq);
+    std::vector<Seen> seen(nq);
+    std::vector<Best> answer(nq);
+    std::vector<int64_t> active(nq), full;
     std::vector<int32_t> kp(nq);
+    // k' starts at 2k: the threshold test rarely holds at k' = k, since the
+    // k-th best sum must fall below the sum of the columns' k'-th distances
     for (int64_t q = 0; q < nq; ++q) {
         active[q] = q;
-        kp[q] = (int32_t)std::min<int64_t>(k[q], kmax);
+        kp[q] = (int32_t)std::min<int64_t>(2 * (int64_t)k[q], kmax);
     }
-    gts_query_opts o = c.base;
-    o.flags = GTS_QUERY_KEYS;
-    while (!active.empty()) {
+    for (int round = 0; !active.empty(); ++round) {
         const int64_t na = (int64_t)active.size();
-        SubQueries sub(c, queries, active);
+        const bool first = round == 0;  // nothing seen yet
+        std::unique_ptr<SubQueries> sub;
+        const gts_objects *qo = queries;
+        if (na != nq) {                 // else every query, in order: no gather
+            sub.reset(new SubQueries(c, queries, active));
+            qo = sub->obj.data();
+        }
         std::vector<int32_t> ka(na);
         for (int64_t i = 0; i < na; ++i) ka[i] = kp[active[i]];
-        // sorted access: each column's k' nearest; T = sum of the k'-th distances
+        // sorted access: each column's k' nearest
+        std::vector<ColResult> res(m);
+        for_columns(m, [&](int j) {
+            const gts_query_opts o = c.opts(j, GTS_QUERY_KEYS);
+            raise_status(gts_knn(c.ix[j], &qo[j], ka.data(), &o, &res[j].r), "column kNN query");
+        });
+        // T = the sum of the columns' k'-th distances (column order); a column
+        // that returned fewer than k' answers, or all live objects, returned
+        // every object
         std::vector<double> T(na, 0.0);
         std::vector<char> all_seen(na, 0);
-        std::vector<int32_t> pq;
-        std::vector<int64_t> pid;
         for (int j = 0; j < m; ++j) {
-            ColResult r;
-            raise_status(gts_knn(c.ix[j], &sub.obj[j], ka.data(), &o, &r.r), "column kNN query");
+            const gts_result &r = res[j].r;
             for (int64_t i = 0; i < na; ++i) {
-                const int64_t a = r.r.offsets[i], b = r.r.offsets[i + 1];
+                const int64_t a = r.offsets[i], b = r.offsets[i + 1];
                 if (b - a < ka[i] || b - a >= c.n_live) all_seen[i] = 1;
-                if (b > a) T[i] += column_distance(c.metric[j], r.r.key[b - 1]);
-                auto &s = seen[active[i]];
-                for (int64_t p = a; p < b; ++p)
-                    if (s.emplace(r.r.ids[p], -1.0).second) {   // first sight: random access below
-                        pq.push_back((int32_t)i);
-                        pid.push_back(r.r.ids[p]);
-                    }
+                if (b > a) T[i] += column_distance(c.metric[j], r.key[b - 1]);
             }
         }
-        // random access: the full sum of every object seen for the first time
-        const std::vector<double> sum = pair_sums(c, sub.obj.data(), pq, pid);
-        for (size_t p = 0; p < pq.size(); ++p) seen[active[pq[p]]][pid[p]] = sum[p];
+        // random access for the ids not seen in an earlier round
+        std::vector<int64_t> off, cand, cnt, poff, pid;
+        std::vector<int32_t> pq;
+        union_ids(res, na, off, cand, cnt);
+        if (!first)
+            parallel_for(na, 256, [&](int64_t b, int64_t e) {
+                for (int64_t i = b; i < e; ++i) {
+                    int64_t *s = cand.data() + off[i];
+                    const Seen &S = seen[active[i]];
+                    int64_t w = 0;
+                    size_t t = 0;
+                    for (int64_t u = 0; u < cnt[i]; ++u) {
+                        while (t < S.size() && S[t].first < s[u]) ++t;
+                        if (t < S.size() && S[t].first == s[u]) continue;
+                        s[w++] = s[u];
+                    }
+                    cnt[i] = w;
+                }
+            });
+        flatten_pairs(off, cand, cnt, poff, pq, pid);
+        const std::vector<double> sum = pair_sums(c, qo, pq, pid);
+        // merge into each query's seen set; settled once the k-th best sum is
+        // below T (an unseen object's sum is at least T)
+        std::vector<char> settled(na, 0);
+        parallel_for(na, 64, [&](int64_t b, int64_t e) {
+            for (int64_t i = b; i < e; ++i) {
+                const int64_t q = active[i];
+                Seen &S = seen[q];
+                Seen merged;
+                merged.reserve(S.size() + cnt[i]);
+                size_t a = 0;
+                int64_t t = poff[i];
+                while (a < S.size() || t < poff[i + 1]) {
+                    if (t == poff[i + 1] || (a < S.size() && S[a].first < pid[t]))
+                        merged.push_back(S[a++]);
+                    else {
+                        merged.emplace_back(pid[t], sum[t]);
+                        ++t;
+                    }
+                }
+                S.swap(merged);
+                Best v(S.size());
+                for (size_t u = 0; u < S.size(); ++u) v[u] = {S[u].second, S[u].first};
+                v = best_k(std::move(v), k[q]);
+                if (all_seen[i] || ((int64_t)v.size() == k[q] && v.back().first < T[i])) {
+                    answer[q] = std::move(v);
+                    settled[i] = 1;
+                    Seen().swap(S);
+                }
+            }
+        });
         std::vector<int64_t> next;
         for (int64_t i = 0; i < na; ++i) {
             const int64_t q = active[i];
-            std::vector<std::pair<double, int64_t>> v;
-            v.reserve(seen[q].size());
-            for (const auto &e : seen[q]) v.emplace_back(e.second, e.first);
-            const size_t kk = std::min<size_t>((size_t)k[q], v.size());
-            std::partial_sort(v.begin(), v.begin() + kk, v.end());
-            v.resize(kk);
-            if (all_seen[i] || (kk == (size_t)k[q] && v.back().first < T[i])) {
-                answer[q] = std::move(v);
-            } else if (kp[q] >= kmax) {
+            if (settled[i]) continue;
+            if (kp[q] >= kmax) {
                 full.push_back(q);
             } else {
                 kp[q] = (int32_t)std::min<int64_t>(2 * (int64_t)kp[q], kmax);
@@ -289,16 +493,19 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
         active.swap(next);
     }
     if (!full.empty()) full_scan(c, queries, k, full, answer);
-    std::vector<int64_t> off(nq + 1, 0), ids;
-    std::vector<double> sums;
-    for (int64_t q = 0; q < nq; ++q) {
-        for (const auto &e : answer[q]) {
-            sums.push_back(e.first);
-            ids.push_back(e.second);
-        }
-        off[q + 1] = (int64_t)ids.size();
-    }
-    host_result(out, nq, off, ids, sums);
+    Answers a;
+    a.off.assign(nq + 1, 0);
+    for (int64_t q = 0; q < nq; ++q) a.off[q + 1] = a.off[q] + (int64_t)answer[q].size();
+    a.ids.resize(a.off[nq]);
+    a.sums.resize(a.off[nq]);
+    parallel_for(nq, 1024, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q)
+            for (size_t t = 0; t < answer[q].size(); ++t) {
+                a.sums[a.off[q] + t] = answer[q][t].first;
+                a.ids[a.off[q] + t] = answer[q][t].second;
+            }
+    });
+    host_result(out, nq, a);
 }
 
 template <class F>

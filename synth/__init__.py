@@ -243,6 +243,54 @@ def word_vectors(n: int = 200_000, dim: int = 300, n_centers: int = 500, nq: int
     return Workload(f"wordvec_{n}x{dim}_cos_knn{k}", "cos", X, Q, "knn", k=np.full(nq, k, np.int32), fanout=fanout)
 
 
+@dataclasses.dataclass
+class MultiWorkload:
+    """Several columns of one object set, one index per column: row i of
+    every column describes object i."""
+    name: str
+    metrics: list                    # per column "l1" | "l2" | "cos"
+    objects: list                    # per column np.ndarray [n, dim_j] float32
+    queries: list                    # per column np.ndarray [nq, dim_j] float32
+    k: np.ndarray                    # int32[nq]
+    fanout: int = 20
+
+
+def multi_columns(n: int = 200_000, nq: int = 10_000, k: int = 10, n_centers: int = 500, latent: int = 16,
+                  seed: int = 0, qseed: int = 1, fanout: int = 20) -> MultiWorkload:
+    """Two columns of ``n`` objects, like items with an image embedding (L2,
+    128 dimensions) and a text embedding (angle, 300 dimensions, the word
+    vectors' anisotropic law): both columns of an object derive from its
+    topic (one of ``n_centers``) and a ``latent``-dimensional offset of its
+    own through a fixed linear map per column, plus independent column noise.
+    The L2 column is scaled so that its distances are of the order of the
+    angles (about 1), so both columns weigh in the sum.  ``nq`` queries from
+    the same law; kNN with ``k``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    C0 = rng.standard_normal((n_centers, 128))
+    W0 = 0.25 * rng.standard_normal((latent, 128))
+    scale = (np.arange(300) + 1.0) ** -0.3
+    mean = 0.5 * rng.standard_normal(300) * scale
+    C1 = rng.standard_normal((n_centers, 300)) * scale
+    W1 = 0.25 * rng.standard_normal((latent, 300)) * scale
+
+    def draw(r, m):
+        X0 = np.empty((m, 128), np.float32)
+        X1 = np.empty((m, 300), np.float32)
+        step = 1 << 16
+        for s in range(0, m, step):
+            e = min(m, s + step)
+            lab = r.integers(0, n_centers, size=e - s)
+            z = r.standard_normal((e - s, latent))
+            X0[s:e] = 0.07 * (C0[lab] + z @ W0 + 0.5 * r.standard_normal((e - s, 128)))
+            X1[s:e] = mean + C1[lab] + z @ W1 + 0.5 * r.standard_normal((e - s, 300)) * scale
+        return X0, X1
+
+    X0, X1 = draw(rng, n)
+    Q0, Q1 = draw(np.random.Generator(np.random.PCG64(qseed)), nq)
+    return MultiWorkload(f"multicol_{n}_l2x128_cos300_knn{k}", ["l2", "cos"], [X0, X1], [Q0, Q1],
+                         np.full(nq, k, np.int32), fanout=fanout)
+
+
 def poisson_arrivals(m: int, rate_qps: float, seed: int) -> np.ndarray:
     """Open-loop arrival times (seconds from 0) of ``m`` requests at mean rate
     ``rate_qps``."""

@@ -15,6 +15,9 @@ times, checked against the CPU oracle (brute force, FP64 or exact integers):
 * wordvec_200000x300_cos_knn10 (2 * 10^5 x 300, angular distance, k = 10):
   1,024 of the 10,000 queries, drawn at random, with their FP64 keys, on the
   BF16 path after the shape and launch autotuners and on the plain FP32 path.
+* multicol_200000_l2x128_cos300_knn10 (2 * 10^5 objects, an L2 column of
+  128 and an angular column of 300 dimensions, distance = their sum): 48 of
+  the 10,000 queries, kNN on both paths and a range query, FP64 sums exact.
 * uniform_2Mx256_l1 (2 * 10^6 x 256 L1): 256 kNN queries (random and the
   largest k) and 256 range queries (random and the most answers) of the mixed
   batch; then the serving loop under 20,000 Poisson arrivals at 50,000/s and
@@ -106,6 +109,37 @@ def test_wordvec_full_size(env):
         keys = np.concatenate([r.keys[r.offsets[i]:r.offsets[i + 1]] for i in idx])
         assert np.array_equal(keys, want[3]), f"wordvec {prec}: FP64 keys differ"
     ix.close()
+
+
+def test_multicol_full_size(env):
+    """The multi-column workload at full size (200,000 objects, an L2 column
+    of 128 and an angular column of 300 dimensions), each column shaped as
+    bench.py does: the whole 10,000-query batch runs, 48 sampled queries are
+    compared with the oracle's brute force over the summed distance (kNN, and
+    a range at 1.05 times the oracle's 10th sum)."""
+    g, torch = env
+    wl = synth.multi_columns()
+    cols = [g.Index.build(torch.from_numpy(X).cuda(), m, fanout=wl.fanout, root_pivot=0)
+            for X, m in zip(wl.objects, wl.metrics)]
+    for ix, Q in zip(cols, wl.queries):
+        ix.autotune_shape(torch.from_numpy(Q[:2000]).cuda(), k=10, precision="bf16", candidates=4, reps=1)
+    idx = _pick(wl.queries[0].shape[0], 48, [], seed=104)
+    qs = [Q[idx] for Q in wl.queries]
+    want = oracle.multi_knn(wl.metrics, wl.objects, qs, 10)
+    for prec in ("bf16", "fp32"):
+        r = g.multi_knn(cols, wl.queries, wl.k, precision=prec)
+        assert np.array_equal(np.diff(r.offsets), np.full(wl.queries[0].shape[0], 10))
+        ids = np.concatenate([r.ids[r.offsets[i]:r.offsets[i + 1]] for i in idx])
+        sums = np.concatenate([r.keys[r.offsets[i]:r.offsets[i + 1]] for i in idx])
+        assert np.array_equal(ids, want[1]), f"multicol {prec}: ids differ"
+        assert np.array_equal(sums, want[2]), f"multicol {prec}: FP64 sums differ"
+    radii = (1.05 * want[2][9::10]).astype(np.float32)
+    want_r = oracle.multi_range(wl.metrics, wl.objects, qs, radii)
+    r = g.multi_range(cols, qs, radii, precision="bf16")
+    assert np.array_equal(r.offsets, want_r[0]) and np.array_equal(r.ids, want_r[1])
+    assert np.array_equal(r.keys, want_r[2])
+    for ix in cols:
+        ix.close()
 
 
 def test_dna_full_size(env):
