@@ -63,6 +63,7 @@ def lib():
         L.orc_cos_key.argtypes = [P, P, I64]
         L.orc_cos_limit.restype = ctypes.c_double
         L.orc_cos_limit.argtypes = [ctypes.c_double]
+        L.orc_cos_angles.argtypes = [P, I64, P]
         L.orc_keys_vec.argtypes = [ctypes.c_int, P, I64, I64, P, P]
         L.orc_keys_str.argtypes = [P, P, I64, P, I64, P]
         L.orc_range_vec.argtypes = [ctypes.c_int, P, I64, I64, P, I64, P, P, P, P, P, P, P, P]
@@ -250,7 +251,8 @@ def knn_query(metric: str, objects, queries, k, ins_seq=None, del_seq=None, qseq
 def column_distances(metric: str, objects, target) -> np.ndarray:
     """FP64 column distance from ``target`` to every object for a
     multi-column query: sqrt of the FP64 key for L2, the key for L1, and for
-    the angle the C library's acos of 1 - key (Python's ``math.acos``)."""
+    the angle the C library's acos of 1 - key (the function Python's
+    ``math.acos`` calls, run in a C loop)."""
     m = METRICS[metric]
     if m == EDIT:
         raise ValueError("multi-column queries take vector columns")
@@ -261,7 +263,9 @@ def column_distances(metric: str, objects, target) -> np.ndarray:
     if metric == "l2":
         return np.sqrt(keys)
     if metric == "cos":
-        return np.array([math.acos(1.0 - float(x)) for x in keys], np.float64)
+        out = np.empty_like(keys)
+        lib().orc_cos_angles(_p(keys), keys.shape[0], _p(out))
+        return out
     return keys
 
 

@@ -160,6 +160,12 @@ double orc_cos_limit(double r) {
     return 1.0 - cos(r);
 }
 
+/* Angles of FP64 cosine keys: acos(1 - key) from the C library, element by
+ * element (the multi-column sum of Section 5.2's closing remark adds these). */
+void orc_cos_angles(const double *keys, int64_t n, double *out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = acos(1.0 - keys[i]);
+}
+
 static double vec_key(int metric, const float *q, const float *x, int64_t dim) {
     if (metric == OR_COS) return orc_cos_key(q, x, dim);
     return metric == OR_L2 ? orc_l2sq(q, x, dim) : orc_l1(q, x, dim);

@@ -99,5 +99,9 @@ def test_live_mask_and_k_beyond_n():
     assert np.all(np.diff(off) == live.sum())
     with pytest.raises(ValueError):
         oracle.column_distances("edit", X, Q[0])
+    # the C loop calls the same function as math.acos
+    keys = oracle.keys_to_pivot("cos", np.concatenate([X, -X[:1]]), 0)
+    ang = oracle.column_distances("cos", np.concatenate([X, -X[:1]]), X[0])
+    assert all(ang[i] == math.acos(1.0 - keys[i]) for i in range(keys.shape[0]))
     # antipodal rows: pi, up to acos's sqrt-like sensitivity at -1 to the FP64 rounding of cos
     assert math.isclose(oracle.column_distances("cos", -X[:1], X[0])[0], math.pi, rel_tol=0, abs_tol=1e-7)
