@@ -16,7 +16,7 @@ times, checked against the CPU oracle (brute force, FP64 or exact integers):
   1,024 of the 10,000 queries, drawn at random, with their FP64 keys, on the
   BF16 path after the shape and launch autotuners and on the plain FP32 path.
 * multicol_200000_l2x128_cos300_knn10 (2 * 10^5 objects, an L2 column of
-  128 and an angular column of 300 dimensions, distance = their sum): 48 of
+  128 and an angular column of 300 dimensions, distance = their sum): 256 of
   the 10,000 queries, kNN on both paths and a range query, FP64 sums exact.
 * uniform_2Mx256_l1 (2 * 10^6 x 256 L1): 256 kNN queries (random and the
   largest k) and 256 range queries (random and the most answers) of the mixed
@@ -114,7 +114,7 @@ def test_wordvec_full_size(env):
 def test_multicol_full_size(env):
     """The multi-column workload at full size (200,000 objects, an L2 column
     of 128 and an angular column of 300 dimensions), each column shaped as
-    bench.py does: the whole 10,000-query batch runs, 48 sampled queries are
+    bench.py does: the whole 10,000-query batch runs, 256 sampled queries are
     compared with the oracle's brute force over the summed distance (kNN, and
     a range at 1.05 times the oracle's 10th sum)."""
     g, torch = env
@@ -123,7 +123,7 @@ def test_multicol_full_size(env):
             for X, m in zip(wl.objects, wl.metrics)]
     for ix, Q in zip(cols, wl.queries):
         ix.autotune_shape(torch.from_numpy(Q[:2000]).cuda(), k=10, precision="bf16", candidates=4, reps=1)
-    idx = _pick(wl.queries[0].shape[0], 48, [], seed=104)
+    idx = _pick(wl.queries[0].shape[0], 256, [], seed=104)
     qs = [Q[idx] for Q in wl.queries]
     want = oracle.multi_knn(wl.metrics, wl.objects, qs, 10)
     for prec in ("bf16", "fp32"):
