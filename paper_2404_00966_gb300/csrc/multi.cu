@@ -59,13 +59,14 @@ struct Columns {
     std::vector<gts_index *> ix;
     std::vector<int> metric;
     std::vector<cudaStream_t> stream;   // one non-blocking stream per column, owned
+    bool distinct = true;               // no index serves two columns
     int64_t nq = 0, n_live = 0;
     gts_query_opts base{};
     Columns() = default;
     Columns(const Columns &) = delete;
     Columns &operator=(const Columns &) = delete;
     Columns(Columns &&o) noexcept
-        : ix(std::move(o.ix)), metric(std::move(o.metric)), stream(std::move(o.stream)), nq(o.nq),
+        : ix(std::move(o.ix)), metric(std::move(o.metric)), stream(std::move(o.stream)), distinct(o.distinct), nq(o.nq),
           n_live(o.n_live), base(o.base) {
         o.stream.clear();
     }
@@ -81,12 +82,14 @@ struct Columns {
     }
 };
 
-// f(j) for every column j, each on a thread of its own; the first error is
-// rethrown once every column has finished.
+// f(j) for every column j, each on a thread of its own (in turn when an
+// index serves two columns: an index is used by one thread at a time); the
+// first error is rethrown once every column has finished.
 template <class F>
-void for_columns(int m, F &&f) {
-    if (m == 1) {
-        f(0);
+void for_columns(const Columns &c, F &&f) {
+    const int m = (int)c.ix.size();
+    if (m == 1 || !c.distinct) {
+        for (int j = 0; j < m; ++j) f(j);
         return;
     }
     std::vector<std::future<void>> fs;
@@ -128,6 +131,9 @@ Columns check_columns(gts_index *const *cols, int32_t m, const gts_objects *quer
         c.ix.push_back(ix);
         c.metric.push_back(ix->metric);
     }
+    for (int32_t j = 0; j < m; ++j)
+        for (int32_t i = 0; i < j; ++i)
+            if (c.ix[i] == c.ix[j]) c.distinct = false;
     for (int32_t j = 0; j < m; ++j) {
         GTS_CUDA(cudaSetDevice(c.ix[j]->device));
         cudaStream_t st = nullptr;
@@ -175,7 +181,7 @@ std::vector<double> pair_sums(const Columns &c, const gts_objects *queries, cons
     const int m = (int)c.ix.size();
     const int64_t n = (int64_t)pq.size();
     std::vector<std::vector<double>> dist(m);
-    for_columns(m, [&](int j) {
+    for_columns(c, [&](int j) {
         pair_keys(c.ix[j], &queries[j], pq, pid, dist[j], c.stream[j]);
         double *d = dist[j].data();
         const int metric = c.metric[j];
@@ -295,7 +301,7 @@ void multi_range(const Columns &c, const gts_objects *queries, const float *radi
         rcol[q] = f;
     }
     std::vector<ColResult> res(m);
-    for_columns(m, [&](int j) {
+    for_columns(c, [&](int j) {
         const gts_query_opts o = c.opts(j, 0);
         raise_status(gts_range(c.ix[j], &queries[j], rcol.data(), &o, &res[j].r), "column range query");
     });
@@ -411,7 +417,7 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
         for (int64_t i = 0; i < na; ++i) ka[i] = kp[active[i]];
         // sorted access: each column's k' nearest
         std::vector<ColResult> res(m);
-        for_columns(m, [&](int j) {
+        for_columns(c, [&](int j) {
             const gts_query_opts o = c.opts(j, GTS_QUERY_KEYS);
             raise_status(gts_knn(c.ix[j], &qo[j], ka.data(), &o, &res[j].r), "column kNN query");
         });

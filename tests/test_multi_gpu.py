@@ -138,6 +138,22 @@ def test_multi_after_updates(gts):
         c.close()
 
 
+def test_one_index_for_two_columns(gts):
+    """The same index given twice (its columns run in turn): every distance
+    doubles exactly, so the answers are the single column's at twice the
+    distance -- and the oracle's duplicated-column sum."""
+    Xs, Qs = columns(4000, 30, seed=61, correlated=False)
+    a = gts.Index.build(Xs[0], "l2", fanout=9)
+    got = gts.multi_knn([a, a], [Qs[0], Qs[0]], 8)
+    assert_same(got, oracle.multi_knn(["l2", "l2"], [Xs[0], Xs[0]], [Qs[0], Qs[0]], 8), "knn")
+    single = oracle.knn_query("l2", Xs[0], Qs[0], 8)
+    assert np.array_equal(got.ids, single[1]) and np.array_equal(got.keys, 2.0 * single[2])
+    radii = 2.0 * np.array([np.quantile(oracle.distances_to("l2", Xs[0], q), 0.01) for q in Qs[0]], np.float32)
+    assert_same(gts.multi_range([a, a], [Qs[0], Qs[0]], radii),
+                oracle.multi_range(["l2", "l2"], [Xs[0], Xs[0]], [Qs[0], Qs[0]], radii), "range")
+    a.close()
+
+
 def test_multi_argument_errors(gts):
     Xs, Qs = columns(800, 4, seed=41, correlated=False)
     a = gts.Index.build(Xs[0], "l2")
