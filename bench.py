@@ -649,7 +649,8 @@ def bench_serving(args):
     radius = calibrate_radius(ix, cal, 100.0, torch, iters=16)
     is_knn, ks = synth.mixed_requests(nreq, seed=1)
     arrivals = synth.poisson_arrivals(nreq, args.rate, seed=1)
-    sv = gts.Server(ix, max_batch=args.max_batch, n_streams=3, precision=args.precision, result_budget=16 << 30)
+    sv = gts.Server(ix, max_batch=args.max_batch, n_streams=args.serve_streams, precision=args.precision,
+                    result_budget=16 << 30, batch_quantum=args.batch_quantum)
     warm = [sv.submit(wl.queries[nreq + i], "knn", 10) for i in range(64)]
     for t in warm:
         sv.wait(t)
@@ -679,7 +680,8 @@ def bench_serving(args):
            "value": round(nreq / span, 1), "unit": "requests/s", "steps": 1, "warmup": 1,
            "ms_per_step": round(1e3 * span, 2), "dtype": "f32+f64",
            "config": {"workload": "uniform_2Mx256_l1_serving", "n": 2_000_000, "dim": 256, "requests": nreq,
-                      "arrival_rate": args.rate, "radius": radius, "max_batch": args.max_batch, "streams": 3,
+                      "arrival_rate": args.rate, "radius": radius, "max_batch": args.max_batch,
+                      "streams": args.serve_streams, "batch_quantum": args.batch_quantum,
                       "precision": args.precision},
            "build_s": round(build_s, 3),
            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
@@ -923,6 +925,10 @@ def main():
     ap.add_argument("--requests", type=int, default=20_000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50_000.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-batch", type=int, default=1024, help="serving: requests per device batch")
+    ap.add_argument("--serve-streams", type=int, default=2, help="serving: worker streams (batches in flight)")
+    ap.add_argument("--batch-quantum", type=int, default=64,
+                    help="serving: cut batches down to a multiple of this many requests (0 = no rounding); "
+                         "64 = the L1 tiles' query chunk")
     ap.add_argument("--workload", default="gauss", choices=["gauss", "words", "dna", "zipf2d", "wordvec", "multicol",
                                                          "serving"],
                     help="gauss (the headline line); the others time the remaining configurations alone")

@@ -481,7 +481,9 @@ typedef struct {
     int32_t max_batch;      /* requests per device batch; 0 = 1024 */
     int32_t n_streams;      /* worker threads and streams (batches in flight); 0 = 3 */
     int32_t precision;      /* gts_precision of every batch */
-    int32_t reserved_;
+    int32_t batch_quantum;  /* a batch of more than this many requests is cut down to a multiple of it (the
+                               rest waits at the head of the queue), so the tiles' query chunks run full;
+                               0 or 1 = no rounding */
     int64_t result_budget;  /* admission budget in bytes; 0 = 16 GiB */
     int64_t memory_budget;  /* size_GPU of each batch's two-stage scheduler; 0 = result_budget / n_streams */
 } gts_serve_opts;

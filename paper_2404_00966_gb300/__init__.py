@@ -66,7 +66,8 @@ class _Result(ctypes.Structure):
 
 class _ServeOpts(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32), ("result_budget", ctypes.c_int64), ("memory_budget", ctypes.c_int64)]
+                ("batch_quantum", ctypes.c_int32), ("result_budget", ctypes.c_int64),
+                ("memory_budget", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
@@ -610,10 +611,11 @@ class Server:
     """Continuous-batching request loop over an index (gts_serve_*)."""
 
     def __init__(self, index: "Index", max_batch=0, n_streams=0, precision="fp32", result_budget=0,
-                 memory_budget=0):
+                 memory_budget=0, batch_quantum=0):
         o = _ServeOpts(max_batch=int(max_batch), n_streams=int(n_streams),
                        precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
-                       result_budget=int(result_budget), memory_budget=int(memory_budget))
+                       batch_quantum=int(batch_quantum), result_budget=int(result_budget),
+                       memory_budget=int(memory_budget))
         self._h = ctypes.c_void_p()
         self.index = index
         _check(lib().gts_serve_start(index._h, ctypes.byref(o), ctypes.byref(self._h)))

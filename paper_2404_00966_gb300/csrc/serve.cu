@@ -228,6 +228,18 @@ void worker_loop(gts_server *sv, int wid) {
                 batch.push_back(std::move(*it));
                 it = sv->pending.erase(it);
             }
+            // a batch above the quantum keeps a multiple of it; the newest
+            // requests go back to the head of the queue, in order
+            const size_t bq = sv->opts.batch_quantum > 1 ? (size_t)sv->opts.batch_quantum : 0;
+            if (bq && batch.size() > bq && batch.size() % bq != 0) {
+                const size_t keep = batch.size() / bq * bq;
+                for (size_t i = batch.size(); i-- > keep;) {
+                    sv->in_flight -= batch[i].proj;
+                    sv->pending.push_front(std::move(batch[i]));
+                }
+                batch.resize(keep);
+                sv->cv_work.notify_one();
+            }
             if (sv->in_flight > sv->max_in_flight) sv->max_in_flight = sv->in_flight;
             if (batch.empty()) {   // nothing admissible yet: wait for a batch to finish
                 sv->cv_done.wait(lk);

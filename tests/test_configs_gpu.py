@@ -246,7 +246,8 @@ def test_uniform_l1_full_size_mixed_and_served(env):
         _compare(res_r[p], idx_r, want_r, "l1", f"l1 range {p}")
     # served: open-loop Poisson arrivals through the continuous-batching loop
     arrivals = synth.poisson_arrivals(nreq, 50_000.0, seed=1)
-    sv = g.Server(ix, max_batch=1024, n_streams=3, precision="bf16", result_budget=16 << 30)
+    sv = g.Server(ix, max_batch=1024, n_streams=2, precision="bf16", result_budget=16 << 30,
+                  batch_quantum=64)   # as bench.py serves
     tickets = []
     start = time.perf_counter()
     for i in range(nreq):

@@ -25,8 +25,9 @@ def gts():
     return g
 
 
-@pytest.mark.parametrize("metric,prec", [("l2", "fp32"), ("l2", "bf16"), ("l1", "fp32"), ("l1", "bf16")])
-def test_mixed_stream_equals_alone(gts, metric, prec):
+@pytest.mark.parametrize("metric,prec,quantum", [("l2", "fp32", 0), ("l2", "bf16", 0), ("l1", "fp32", 0),
+                                                 ("l1", "bf16", 0), ("l1", "bf16", 4), ("l2", "bf16", 4)])
+def test_mixed_stream_equals_alone(gts, metric, prec, quantum):
     X, Q = small_vectors(30011, 64, 240, seed=61)
     ix = gts.Index.build(X, metric, fanout=12, root_pivot=0)
     rng = np.random.default_rng(62)
@@ -36,7 +37,7 @@ def test_mixed_stream_equals_alone(gts, metric, prec):
     radius = float(np.median([base.query(i)[1][-1] for i in range(20)]))
     proj = X.shape[0] * 37
     budget = 9 * proj                       # at most nine requests admitted at once
-    sv = gts.Server(ix, max_batch=32, n_streams=3, precision=prec, result_budget=budget)
+    sv = gts.Server(ix, max_batch=32, n_streams=3, precision=prec, result_budget=budget, batch_quantum=quantum)
     tickets = [None] * 240
 
     def submit(lo, hi):
@@ -53,6 +54,8 @@ def test_mixed_stream_equals_alone(gts, metric, prec):
     sv.stop()
     assert st["requests"] == 240 and st["batches"] > 1
     assert st["max_in_flight"] <= budget
+    if quantum:   # batches above the quantum are cut to a multiple of it
+        assert st["max_batch"] <= 4 or st["max_batch"] % quantum == 0
     want_k = oracle.knn_query(metric, X, Q, ks)
     want_r = oracle.range_query(metric, X, Q, np.full(240, radius, np.float32))
     for i in range(240):
