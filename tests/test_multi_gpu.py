@@ -154,6 +154,28 @@ def test_one_index_for_two_columns(gts):
     a.close()
 
 
+def test_multi_empty_inputs(gts):
+    """No queries; indexes with no objects; every object deleted."""
+    Xs, Qs = columns(600, 5, seed=71, correlated=False)
+    cols = [gts.Index.build(X, m, fanout=6) for X, m in zip(Xs, METRICS)]
+    none = [q[:0] for q in Qs]
+    for r in (gts.multi_knn(cols, none, 3), gts.multi_range(cols, none, np.zeros(0, np.float32))):
+        assert list(r.offsets) == [0] and r.ids.size == 0
+    for c in cols:
+        c.delete(np.arange(600))
+    r = gts.multi_knn(cols, Qs, 4)
+    assert np.array_equal(r.offsets, np.zeros(6, np.int64)) and r.ids.size == 0
+    r = gts.multi_range(cols, Qs, np.full(5, 1e6, np.float32))
+    assert np.array_equal(r.offsets, np.zeros(6, np.int64))
+    for c in cols:
+        c.close()
+    empty = [gts.Index.build(X[:0], m) for X, m in zip(Xs, METRICS)]
+    r = gts.multi_knn(empty, Qs, 2)
+    assert np.array_equal(r.offsets, np.zeros(6, np.int64))
+    for c in empty:
+        c.close()
+
+
 def test_multi_argument_errors(gts):
     Xs, Qs = columns(800, 4, seed=41, correlated=False)
     a = gts.Index.build(Xs[0], "l2")
