@@ -806,10 +806,12 @@ def bench_multicol(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    launches = 0
     with ClockSampler(local) as clocks:
         t0 = time.perf_counter()
         for _ in range(args.other_steps):
             r = step()
+            launches += r.stats["launches"]
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     out = {"metric": "multi-column kNN queries/s at oracle-exact results (L2 + angle, k=10)",
@@ -819,7 +821,8 @@ def bench_multicol(args):
            "config": {"workload": wl.name, "n": int(wl.objects[0].shape[0]), "columns": wl.metrics,
                       "dims": [int(x.shape[1]) for x in wl.objects], "nq": nq, "k": k, "precision": prec,
                       "shapes": shapes},
-           "answers": int(r.offsets[-1]), "build_s": round(build_s, 3), "clocks": clocks.summary()}
+           "answers": int(r.offsets[-1]), "build_s": round(build_s, 3), "gpu_launches": int(launches),
+           "counters_per_step": r.stats, "clocks": clocks.summary()}
     for ix in cols:
         ix.close()
     if not args.no_cpu:

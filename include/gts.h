@@ -303,8 +303,11 @@ gts_status gts_merge_range(const gts_result *const *parts, const int64_t *id_bas
  *    run concurrently, each on a host thread and a non-blocking stream of its
  *    own made for the call (opts->stream is not used; the call returns when
  *    all of it is done; an index given for several columns serves them in
- *    turn); seq must be NULL (the current state) and
- *    result_on_device 0; stats, stage_ms and flags are ignored.
+ *    turn); seq must be NULL (the current state) and result_on_device 0;
+ *    stats, when given, receives the column searches' counters summed over
+ *    columns and rounds (GTS_STAT_LAUNCHES also counts the random-access
+ *    kernels), GTS_STAT_RESULTS = the multi-column answers and
+ *    GTS_STAT_TABLE_PASS = -1; stage_ms and flags are ignored.
  * Every column must hold the same live ids: GTS_EINVAL when their live
  * counts differ or an answer of one column is not live in another.  out
  * (host) carries dist = (float)sum and key = the FP64 sum; release it with

@@ -274,13 +274,14 @@ def _multi(fn, columns, queries, per_query, precision, memory_budget):
     ms = [_Marshal(np.ascontiguousarray(q, np.float32)) for q in queries]
     objs = (_Objects * len(ms))(*[m.obj for m in ms])
     hs = (ctypes.c_void_p * len(columns))(*[c._h.value for c in columns])
+    stats = np.zeros(len(STAT_NAMES), np.int64)
     opts = _QueryOpts(precision=PREC_BF16 if precision in ("bf16", PREC_BF16) else PREC_FP32,
-                      memory_budget=int(memory_budget))
+                      memory_budget=int(memory_budget), stats=_ptr(stats).value)
     res = _Result()
     _check(fn(hs, len(columns), objs, _ptr(per_query), ctypes.byref(opts), ctypes.byref(res)))
     offsets, ids, dist, kk = _host_arrays(res)
     lib().gts_result_free(ctypes.byref(res))
-    return Result(offsets, ids, dist, keys=kk)
+    return Result(offsets, ids, dist, dict(zip(STAT_NAMES, stats.tolist())), keys=kk)
 
 
 def multi_range(columns, queries, radii, precision="fp32", memory_budget=0) -> Result:

@@ -21,6 +21,7 @@
 // column); the combination (unions, threshold tests, selection) is host
 // bookkeeping.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -62,23 +63,43 @@ struct Columns {
     bool distinct = true;               // no index serves two columns
     int64_t nq = 0, n_live = 0;
     gts_query_opts base{};
+    int64_t *user_stats = nullptr;      // the caller's counters, filled on return
+    // per column, its searches' counters summed (written by its own thread only)
+    mutable std::vector<std::array<int64_t, GTS_STATS_LEN>> acc;
     Columns() = default;
     Columns(const Columns &) = delete;
     Columns &operator=(const Columns &) = delete;
     Columns(Columns &&o) noexcept
-        : ix(std::move(o.ix)), metric(std::move(o.metric)), stream(std::move(o.stream)), distinct(o.distinct), nq(o.nq),
-          n_live(o.n_live), base(o.base) {
+        : ix(std::move(o.ix)), metric(std::move(o.metric)), stream(std::move(o.stream)), distinct(o.distinct),
+          nq(o.nq), n_live(o.n_live), base(o.base), user_stats(o.user_stats), acc(std::move(o.acc)) {
         o.stream.clear();
     }
     ~Columns() {
         for (cudaStream_t st : stream) cudaStreamDestroy(st);
     }
-    // column j's options: the caller's, on the column's own stream
-    gts_query_opts opts(int j, int32_t flags) const {
+    // column j's options: the caller's, on the column's own stream, its
+    // counters into st
+    gts_query_opts opts(int j, int32_t flags, int64_t *st) const {
         gts_query_opts o = base;
         o.stream = stream[j];
         o.flags = flags;
+        o.stats = st;
         return o;
+    }
+    void add(int j, const int64_t *st) const {
+        for (int s = 0; s < GTS_STATS_LEN; ++s)
+            if (st[s] > 0) acc[j][s] += st[s];
+    }
+    // the caller's counters: the columns' sums, the multi-column answers
+    void report(int64_t results) const {
+        if (!user_stats) return;
+        for (int s = 0; s < GTS_STATS_LEN; ++s) {
+            int64_t t = 0;
+            for (const auto &a : acc) t += a[s];
+            user_stats[s] = t;
+        }
+        user_stats[GTS_STAT_RESULTS] = results;
+        user_stats[GTS_STAT_TABLE_PASS] = -1;
     }
 };
 
@@ -108,6 +129,8 @@ Columns check_columns(gts_index *const *cols, int32_t m, const gts_objects *quer
     GTS_REQUIRE(m >= 1 && m <= 64, GTS_EINVAL, "number of columns must be 1 .. 64");
     Columns c;
     if (opts) c.base = *opts;
+    c.user_stats = c.base.stats;
+    c.acc.assign(m, std::array<int64_t, GTS_STATS_LEN>{});
     GTS_REQUIRE(c.base.seq == nullptr, GTS_EINVAL, "multi-column queries run on the current state (seq must be NULL)");
     GTS_REQUIRE(c.base.result_on_device == 0, GTS_EINVAL, "multi-column results are host memory");
     c.base.stats = nullptr;
@@ -183,6 +206,7 @@ std::vector<double> pair_sums(const Columns &c, const gts_objects *queries, cons
     std::vector<std::vector<double>> dist(m);
     for_columns(c, [&](int j) {
         pair_keys(c.ix[j], &queries[j], pq, pid, dist[j], c.stream[j]);
+        if (n > 0) c.acc[j][GTS_STAT_LAUNCHES] += 1;   // k_pair_keys
         double *d = dist[j].data();
         const int metric = c.metric[j];
         parallel_for(n, 1 << 14, [&](int64_t b, int64_t e) {
@@ -302,8 +326,10 @@ void multi_range(const Columns &c, const gts_objects *queries, const float *radi
     }
     std::vector<ColResult> res(m);
     for_columns(c, [&](int j) {
-        const gts_query_opts o = c.opts(j, 0);
+        int64_t st[GTS_STATS_LEN] = {};
+        const gts_query_opts o = c.opts(j, 0, st);
         raise_status(gts_range(c.ix[j], &queries[j], rcol.data(), &o, &res[j].r), "column range query");
+        c.add(j, st);
     });
     std::vector<int64_t> off, cand, cnt, poff, pid;
     std::vector<int32_t> pq;
@@ -335,6 +361,7 @@ void multi_range(const Columns &c, const gts_objects *queries, const float *radi
                 }
         }
     });
+    c.report((int64_t)a.ids.size());
     host_result(out, nq, a);
 }
 
@@ -418,8 +445,10 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
         // sorted access: each column's k' nearest
         std::vector<ColResult> res(m);
         for_columns(c, [&](int j) {
-            const gts_query_opts o = c.opts(j, GTS_QUERY_KEYS);
+            int64_t st[GTS_STATS_LEN] = {};
+            const gts_query_opts o = c.opts(j, GTS_QUERY_KEYS, st);
             raise_status(gts_knn(c.ix[j], &qo[j], ka.data(), &o, &res[j].r), "column kNN query");
+            c.add(j, st);
         });
         // T = the sum of the columns' k'-th distances (column order); a column
         // that returned fewer than k' answers, or all live objects, returned
@@ -511,6 +540,7 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
                 a.ids[a.off[q] + t] = answer[q][t].second;
             }
     });
+    c.report((int64_t)a.ids.size());
     host_result(out, nq, a);
 }
 

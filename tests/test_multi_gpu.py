@@ -87,8 +87,13 @@ def test_multi_range_and_knn(gts, correlated):
     ks[2] = 1024                                              # the largest k
     want_k = oracle.multi_knn(METRICS, Xs, Qs, ks)
     for prec in ("fp32", "bf16"):
-        assert_same(gts.multi_range(cols, Qs, radii, precision=prec), want_r, f"range {prec}")
-        assert_same(gts.multi_knn(cols, Qs, ks, precision=prec), want_k, f"knn {prec}")
+        rr = gts.multi_range(cols, Qs, radii, precision=prec)
+        assert_same(rr, want_r, f"range {prec}")
+        rk = gts.multi_knn(cols, Qs, ks, precision=prec)
+        assert_same(rk, want_k, f"knn {prec}")
+        for r, want in ((rr, want_r), (rk, want_k)):   # counters: the columns' searches summed
+            assert r.stats["results"] == want[1].shape[0] and r.stats["table_pass"] == -1
+            assert r.stats["launches"] > len(METRICS) and r.stats["pivot_dist"] > 0
     assert list(want_r[1][want_r[0][0]:want_r[0][1]]) == sorted(want_r[1][want_r[0][0]:want_r[0][1]])
     for c in cols:
         c.close()
