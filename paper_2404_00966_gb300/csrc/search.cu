@@ -1104,6 +1104,67 @@ __global__ void k_verify_lowdim(Dev d, const int32_t *__restrict__ cq, const int
     }
 }
 
+// Cache list (Section 4.4), range queries over vectors of at most 16
+// dimensions: every (query, cache slot) pair of the queries [qa, qb) is
+// verified as k_verify_lowdim verifies it (the same FP32 sum in coordinate
+// order, the same band, the same FP64 decision), and the kept pairs go
+// straight into the answer keys (query << 32 | id) and distances, a warp's
+// kept pairs at one atomic -- no candidate list is written.  rkey / rdist
+// hold (qb - qa) * cn entries, at least the pairs kept.
+template <bool L2>
+__global__ void k_cache_range_lowdim(Dev d, int64_t qa, int64_t qb, int64_t cn, const float *__restrict__ thr_q,
+                                     uint64_t *__restrict__ rkey, float *__restrict__ rdist,
+                                     unsigned long long *__restrict__ count,
+                                     unsigned long long *__restrict__ rechecks) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (qb - qa) * cn;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // base is the warp's first pair: every lane runs the same iterations
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int64_t i = base + lane;
+        bool kept = false;
+        float dist = 0.f;
+        int64_t q = 0, row = 0;
+        if (i < total) {
+            q = qa + i / cn;
+            row = d.n + i % cn;
+            if (row_visible(d, row, d.qseq[q])) {
+                const float *qv = d.Q + q * d.dim;
+                const float *xv = vrow(d, row);
+                float sum = 0.f;
+                for (int k = 0; k < d.dim; ++k) {
+                    const float t = qv[k] - xv[k];
+                    sum = L2 ? fmaf(t, t, sum) : sum + fabsf(t);
+                }
+                const float d32 = L2 ? sqrtf(sum) : sum;
+                const float r = thr_q[q];
+                const float hi = d32 * (1.f + 2.f * d.rel) + d.absf;
+                const float lo = d32 * (1.f - 2.f * d.rel) - d.absf;
+                if (!d.cosine && hi < r * (1.f - 1e-9f)) {   // (angular: the FP64 key decides every kept pair)
+                    kept = true;
+                    dist = d32;
+                } else if (!(lo > r * (1.f + 1e-9f))) {
+                    const double key = fp64_key<L2>(d, q, row);
+                    kept = key <= fp64_limit<L2>(d, q, r);
+                    dist = key_distance(d, L2, key);
+                    atomicAdd(rechecks, 1ull);
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, kept);
+        if (m) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (kept) {
+                const unsigned long long o = b + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+                rkey[o] = ((uint64_t)(uint32_t)q << 32) | (uint64_t)(uint32_t)row_oid(d, row);
+                rdist[o] = dist;
+            }
+        }
+    }
+}
+
 __global__ void k_compact_cands(const int32_t *__restrict__ cq, const int32_t *__restrict__ crow,
                                 const float *__restrict__ cdist, const uint8_t *__restrict__ keep, int64_t C,
                                 const int64_t *__restrict__ pos, int32_t *__restrict__ oq, int32_t *__restrict__ orow,
@@ -2101,13 +2162,23 @@ __global__ void k_u8_to_i64(const uint8_t *a, int64_t n, int64_t *b) {
     if (blockIdx.x == 0 && threadIdx.x == 0) b[n] = 0;
 }
 
-// Range answers sorted by (query << 32 | id): query q's answers start at the
-// first key >= q << 32 (a binary search per query, no atomics), and each
-// answer's id is the key's low half.
-__global__ void k_range_offsets(const uint64_t *__restrict__ rkey, int64_t R, int64_t nq,
+// Range answer keys (query << 32 | id), as the kernels emit them, repacked
+// to (query << idbits | id) with every id < 2^idbits, so that the sort by
+// (query, id) runs over the bits in use only.
+__global__ void k_repack_keys(const uint64_t *__restrict__ in, int64_t n, int idbits, uint64_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = in[i];
+        out[i] = ((k >> 32) << idbits) | (k & 0xffffffffull);
+    }
+}
+
+// Range answers sorted by (query << idbits | id): query q's answers start at
+// the first key >= q << idbits (a binary search per query, no atomics), and
+// each answer's id is the key's low idbits bits.
+__global__ void k_range_offsets(const uint64_t *__restrict__ rkey, int64_t R, int64_t nq, int idbits,
                                 int64_t *__restrict__ offsets) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= nq; q += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = (uint64_t)q << 32;
+        const uint64_t x = (uint64_t)q << idbits;
         int64_t a = 0, b = R;
         while (a < b) {
             const int64_t m = (a + b) >> 1;
@@ -2118,9 +2189,10 @@ __global__ void k_range_offsets(const uint64_t *__restrict__ rkey, int64_t R, in
     }
 }
 
-__global__ void k_range_ids(const uint64_t *__restrict__ rkey, int64_t R, int64_t *__restrict__ ids) {
+__global__ void k_range_ids(const uint64_t *__restrict__ rkey, int64_t R, int idbits, int64_t *__restrict__ ids) {
+    const uint64_t mask = (1ull << idbits) - 1ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x)
-        ids[i] = (int64_t)(rkey[i] & 0xffffffffull);
+        ids[i] = (int64_t)(rkey[i] & mask);
 }
 
 __global__ void k_knn_counts(const int32_t *bn, int64_t nq, int64_t *counts) {
@@ -3290,9 +3362,37 @@ struct Runner {
         if (cn == 0) return;
         int64_t qchunk = ((budget / 2) / 40) / cn;
         if (qchunk < 1) qchunk = 1;
+        // range queries over low-dimensional vectors: verified and kept in
+        // one pass (the general path writes every pair as a candidate first)
+        const bool fused = !knn && d.dim > 0 && d.dim <= kScanMaxDim;
         for (int64_t qa = 0; qa < qb.nq; qa += qchunk) {
             const int64_t qe = qa + qchunk < qb.nq ? qa + qchunk : qb.nq;
             const int64_t C = (qe - qa) * cn;
+            if (fused) {
+                st_cache += C;
+                DBuf<uint64_t> rk(C, st);
+                DBuf<float> rd(C, st);
+                DBuf<unsigned long long> kept(1, st);
+                GTS_CUDA(cudaMemsetAsync(kept.get(), 0, 8, st));
+                clk.begin(GTS_STAGE_VERIFY);
+                if (d.metric == GTS_L2)
+                    k_cache_range_lowdim<true><<<wave_grid(k_cache_range_lowdim<true>, nblocks(C, kT), kT), kT, 0,
+                                                 st>>>(d, qa, qe, cn, thr.get(), rk.get(), rd.get(), kept.get(),
+                                                       counters.get());
+                else
+                    k_cache_range_lowdim<false><<<wave_grid(k_cache_range_lowdim<false>, nblocks(C, kT), kT), kT,
+                                                  0, st>>>(d, qa, qe, cn, thr.get(), rk.get(), rd.get(), kept.get(),
+                                                           counters.get());
+                clk.end();
+                check_launch("cache range");
+                const int64_t R = d2h_i64(reinterpret_cast<const int64_t *>(kept.get()), st);
+                if (R > 0) {
+                    rkeys.push_back(std::move(rk));
+                    rdists.push_back(std::move(rd));
+                    rcounts.push_back(R);
+                }
+                continue;
+            }
             DBuf<int32_t> cq(C, st), crow(C, st);
             clk.begin(GTS_STAGE_OTHER);
             k_cache_cands<<<nblocks(C, kT), kT, 0, st>>>(qa, qe, ix->tree.n, cn, cq.get(), crow.get());
@@ -3501,12 +3601,19 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
         DBuf<float> dd(Rt ? Rt : 1, st);
         out.dist.alloc(Rt ? Rt : 1, st);
         out.ids.alloc(Rt ? Rt : 1, st);
+        // ids are below next_id (< 2^31): the keys keep idbits id bits
+        int idbits = 1;
+        while (idbits < 32 && ((int64_t)1 << idbits) < ix->next_id) ++idbits;
         int64_t o = 0;
+        R.clk.begin(GTS_STAGE_OTHER, (int)R.rkeys.size());
         for (size_t i = 0; i < R.rkeys.size(); ++i) {
-            GTS_CUDA(cudaMemcpyAsync(keys.get() + o, R.rkeys[i].get(), R.rcounts[i] * 8, cudaMemcpyDeviceToDevice, st));
+            k_repack_keys<<<R.cap(nblocks(R.rcounts[i], kT)), kT, 0, st>>>(R.rkeys[i].get(), R.rcounts[i], idbits,
+                                                                         keys.get() + o);
             GTS_CUDA(cudaMemcpyAsync(dd.get() + o, R.rdists[i].get(), R.rcounts[i] * 4, cudaMemcpyDeviceToDevice, st));
             o += R.rcounts[i];
         }
+        R.clk.end();
+        check_launch("repack range keys");
         R.rkeys.clear();
         R.rdists.clear();
         if (Rt > 0) {
@@ -3514,13 +3621,13 @@ void run_query(gts_index *ix, const QueryBatch &qb, bool knn, int precision, int
             while (((int64_t)1 << qbits) < nq) ++qbits;
             size_t tb = 0;
             cub::DeviceRadixSort::SortPairs(nullptr, tb, keys.get(), keys2.get(), dd.get(), out.dist.get(), Rt, 0,
-                                            32 + qbits, st);
+                                            idbits + qbits, st);
             DBuf<uint8_t> tmp(tb, st);
             R.clk.begin(GTS_STAGE_OTHER, 3);
             GTS_CUDA(cub::DeviceRadixSort::SortPairs(tmp.get(), tb, keys.get(), keys2.get(), dd.get(), out.dist.get(),
-                                                     Rt, 0, 32 + qbits, st));
-            k_range_ids<<<R.cap(nblocks(Rt, kT)), kT, 0, st>>>(keys2.get(), Rt, out.ids.get());
-            k_range_offsets<<<nblocks(nq + 1, kT), kT, 0, st>>>(keys2.get(), Rt, nq, out.offsets.get());
+                                                     Rt, 0, idbits + qbits, st));
+            k_range_ids<<<R.cap(nblocks(Rt, kT)), kT, 0, st>>>(keys2.get(), Rt, idbits, out.ids.get());
+            k_range_offsets<<<nblocks(nq + 1, kT), kT, 0, st>>>(keys2.get(), Rt, nq, idbits, out.offsets.get());
             R.clk.end();
         } else {
             GTS_CUDA(cudaMemsetAsync(out.offsets.get(), 0, (nq + 1) * 8, st));
