@@ -225,8 +225,15 @@ __global__ void k_fill_loc(int64_t *a, int64_t n) {
 void refresh_loc(gts_index *ix) {
     Tree &t = ix->tree;
     cudaStream_t st = ix->stream;
-    ix->loc.assign(ix->next_id, -1);
-    if (t.n == 0 || ix->next_id == 0) return;
+    if (t.n == 0 || ix->next_id == 0) {
+        ix->loc.assign(ix->next_id, -1);
+        return;
+    }
+    // room for the stream inserts until the next rebuild (at most the cache
+    // limit), so no insert has to move the whole table
+    const size_t need = (size_t)ix->next_id + (size_t)std::max<int64_t>(ix->cache_limit, 0);
+    if (ix->loc.capacity() < need) ix->loc.reserve(need + (size_t)ix->next_id / 8);
+    ix->loc.resize(ix->next_id);   // every entry is overwritten by the copy below
     DBuf<int64_t> locd(ix->next_id, st);
     k_fill_loc<<<std::min<int64_t>(nb(ix->next_id), 4096), kT, 0, st>>>(locd.get(), ix->next_id);
     k_loc_scatter<<<std::min<int64_t>(nb(t.n), 4096), kT, 0, st>>>(t.row_id.get(), t.n, locd.get());
