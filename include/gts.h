@@ -289,7 +289,8 @@ gts_status gts_merge_range(const gts_result *const *parts, const int64_t *id_bas
  * distances d_j(q_j, o_j): sqrt(key) for L2, the key for L1, acos(1 - key)
  * (the C library's acos) for the angle, each key in the single-column
  * operation order of GTS_QUERY_KEYS.
- *  queries: m host object sets (on_device = 0), all with the same nq;
+ *  queries: m object sets, all with the same nq and on the same side (host,
+ *    or device, copied to the host once; radii / k on the same side);
  *    queries[j] has column j's dim; row i of every set is query i.
  *  gts_multi_range: answers with sum <= radii[i] (finite, >= 0; Definition
  *    1), ascending id.  The candidates are the union of the columns' range answers at

@@ -271,7 +271,7 @@ class ShardedIndex:
 def _multi(fn, columns, queries, per_query, precision, memory_budget):
     if len(columns) != len(queries):
         raise ValueError("one query set per column")
-    ms = [_Marshal(np.ascontiguousarray(q, np.float32)) for q in queries]
+    ms = [_Marshal(q if _is_torch(q) else np.ascontiguousarray(q, np.float32)) for q in queries]
     objs = (_Objects * len(ms))(*[m.obj for m in ms])
     hs = (ctypes.c_void_p * len(columns))(*[c._h.value for c in columns])
     stats = np.zeros(len(STAT_NAMES), np.int64)
@@ -286,17 +286,20 @@ def _multi(fn, columns, queries, per_query, precision, memory_budget):
 
 def multi_range(columns, queries, radii, precision="fp32", memory_budget=0) -> Result:
     """Multi-column range query (gts_multi_range): ``columns`` are indexes
-    over the same ids, ``queries`` one host [nq, dim_j] array per column; an
-    answer's distance is the sum of its column distances (``keys``: the FP64
-    sums)."""
-    r = np.ascontiguousarray(radii, np.float32)
+    over the same ids, ``queries`` one [nq, dim_j] array per column (numpy,
+    or torch tensors with ``radii`` on the same device); an answer's distance
+    is the sum of its column distances (``keys``: the FP64 sums)."""
+    r = radii.contiguous() if _is_torch(radii) else np.ascontiguousarray(radii, np.float32)
     return _multi(lib().gts_multi_range, columns, queries, r, precision, memory_budget)
 
 
 def multi_knn(columns, queries, k, precision="fp32", memory_budget=0) -> Result:
     """Multi-column kNN query (gts_multi_knn), answers in ascending (sum, id)."""
-    n = int(np.asarray(queries[0]).shape[0])
-    kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
+    if _is_torch(k):
+        kk = k.contiguous()
+    else:
+        n = int(queries[0].shape[0])
+        kk = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (n,)), np.int32)
     return _multi(lib().gts_multi_knn, columns, queries, kk, precision, memory_budget)
 
 

@@ -142,7 +142,8 @@ Columns check_columns(gts_index *const *cols, int32_t m, const gts_objects *quer
         GTS_REQUIRE(ix->dim > 0 && ix->metric != GTS_EDIT, GTS_EINVAL,
                     "multi-column queries take vector columns (L1, L2, angular)");
         const gts_objects &q = queries[j];
-        GTS_REQUIRE(q.on_device == 0, GTS_EINVAL, "multi-column queries are host rows");
+        GTS_REQUIRE(q.on_device == queries[0].on_device, GTS_EINVAL,
+                    "every column's queries must be on the same side");
         GTS_REQUIRE(q.dim == ix->dim, GTS_EINVAL, "column " + std::to_string(j) + ": query dim does not match");
         GTS_REQUIRE(q.n >= 0 && (q.n == 0 || q.data != nullptr), GTS_EINVAL, "column queries: bad n or NULL data");
         if (j == 0) {
@@ -544,6 +545,38 @@ void multi_knn(const Columns &c, const gts_objects *queries, const int32_t *k, g
     host_result(out, nq, a);
 }
 
+// Device-resident queries (and their per-query array, on the same side)
+// copied to the host once: the combination works on host rows.
+struct HostSide {
+    std::vector<std::vector<float>> rows;
+    std::vector<gts_objects> obj;
+    std::vector<uint8_t> per_query;
+    const gts_objects *queries;
+    const void *pq;
+    HostSide(gts_index *const *cols, int32_t m, const gts_objects *q, const void *per, size_t elem)
+        : queries(q), pq(per) {
+        if (!cols || !q || m < 1 || m > 64 || !q[0].on_device) return;
+        GTS_REQUIRE(cols[0] != nullptr, GTS_EINVAL, "column index NULL");
+        GTS_CUDA(cudaSetDevice(cols[0]->device));
+        rows.resize(m);
+        obj.resize(m);
+        for (int32_t j = 0; j < m; ++j) {
+            GTS_REQUIRE(q[j].on_device && q[j].dim > 0 && q[j].n >= 0 && (q[j].n == 0 || q[j].data), GTS_EINVAL,
+                        "multi-column queries: bad device query set");
+            const size_t cnt = (size_t)q[j].n * q[j].dim;
+            rows[j].resize(cnt + 1);
+            if (cnt) GTS_CUDA(cudaMemcpy(rows[j].data(), q[j].data, cnt * 4, cudaMemcpyDefault));
+            obj[j] = gts_objects{q[j].n, q[j].dim, 0, rows[j].data(), nullptr};
+        }
+        queries = obj.data();
+        if (per && q[0].n > 0) {
+            per_query.resize((size_t)q[0].n * elem);
+            GTS_CUDA(cudaMemcpy(per_query.data(), per, per_query.size(), cudaMemcpyDefault));
+            pq = per_query.data();
+        }
+    }
+};
+
 template <class F>
 gts_status guarded_multi(gts_result *out, F &&f) {
     try {
@@ -572,12 +605,18 @@ extern "C" {
 
 gts_status gts_multi_range(gts_index *const *cols, int32_t m, const gts_objects *queries, const float *radii,
                            const gts_query_opts *opts, gts_result *out) {
-    return guarded_multi(out, [&] { multi_range(check_columns(cols, m, queries, opts), queries, radii, out); });
+    return guarded_multi(out, [&] {
+        const HostSide h(cols, m, queries, radii, sizeof(float));
+        multi_range(check_columns(cols, m, h.queries, opts), h.queries, (const float *)h.pq, out);
+    });
 }
 
 gts_status gts_multi_knn(gts_index *const *cols, int32_t m, const gts_objects *queries, const int32_t *k,
                          const gts_query_opts *opts, gts_result *out) {
-    return guarded_multi(out, [&] { multi_knn(check_columns(cols, m, queries, opts), queries, k, out); });
+    return guarded_multi(out, [&] {
+        const HostSide h(cols, m, queries, k, sizeof(int32_t));
+        multi_knn(check_columns(cols, m, h.queries, opts), h.queries, (const int32_t *)h.pq, out);
+    });
 }
 
 }  // extern "C"

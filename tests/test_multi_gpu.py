@@ -159,6 +159,23 @@ def test_one_index_for_two_columns(gts):
     a.close()
 
 
+def test_multi_device_queries(gts):
+    """Device-resident query sets, radii and k give the host call's answers."""
+    torch = pytest.importorskip("torch")
+    Xs, Qs = columns(2000, 12, seed=81, correlated=True)
+    cols = [gts.Index.build(X, m, fanout=7) for X, m in zip(Xs, METRICS)]
+    Qd = [torch.from_numpy(q).cuda() for q in Qs]
+    ks = np.arange(1, 13, dtype=np.int32)
+    radii = sum_radii(Xs, Qs, 0.02, seed=9)
+    assert_same(gts.multi_knn(cols, Qd, torch.from_numpy(ks).cuda()), oracle.multi_knn(METRICS, Xs, Qs, ks), "knn")
+    assert_same(gts.multi_range(cols, Qd, torch.from_numpy(radii).cuda()),
+                oracle.multi_range(METRICS, Xs, Qs, radii), "range")
+    with pytest.raises(gts.GTSError):        # the sets on different sides
+        gts.multi_knn(cols, [Qd[0], Qs[1], Qs[2]], 3)
+    for c in cols:
+        c.close()
+
+
 def test_multi_empty_inputs(gts):
     """No queries; indexes with no objects; every object deleted."""
     Xs, Qs = columns(600, 5, seed=71, correlated=False)
