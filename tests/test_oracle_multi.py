@@ -105,3 +105,21 @@ def test_live_mask_and_k_beyond_n():
     assert all(ang[i] == math.acos(1.0 - keys[i]) for i in range(keys.shape[0]))
     # antipodal rows: pi, up to acos's sqrt-like sensitivity at -1 to the FP64 rounding of cos
     assert math.isclose(oracle.column_distances("cos", -X[:1], X[0])[0], math.pi, rel_tol=0, abs_tol=1e-7)
+
+
+def test_knn_is_the_range_at_its_kth_sum():
+    """Definitions 1 and 2 over the summed distance agree: a query's k nearest
+    are the range answers at its k-th sum, up to ties at that sum (which the
+    kNN order breaks by id)."""
+    X, Q = gauss(700, 5, 12), gauss(9, 5, 13)
+    Y, R = gauss(700, 3, 14), gauss(9, 3, 15)
+    mets = ["l1", "l2"]
+    off, ids, sums = oracle.multi_knn(mets, [X, Y], [Q, R], 17)
+    radii = np.array([sums[off[i + 1] - 1] for i in range(9)], np.float32)
+    roff, rids, rsums = oracle.multi_range(mets, [X, Y], [Q, R], np.nextafter(radii, np.float32(np.inf)))
+    for i in range(9):
+        ki, ks = ids[off[i]:off[i + 1]], sums[off[i]:off[i + 1]]
+        ri, rs = rids[roff[i]:roff[i + 1]], rsums[roff[i]:roff[i + 1]]
+        assert set(ki) <= set(ri)                                 # every kNN answer is inside the radius
+        assert np.all(rs[~np.isin(ri, ki)] >= ks[-1])             # the rest are no nearer than the k-th
+        assert np.all(np.diff(ks) >= 0)
